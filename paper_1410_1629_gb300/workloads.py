@@ -1,0 +1,278 @@
+"""Seeded synthetic inputs for the transport library and its CPU oracle.
+
+This module only builds inputs (density grids, optical properties, sources,
+instruments and run settings).  It holds none of the transport arithmetic and
+imports neither the CUDA binding nor the oracle, so both can be fed the same
+arrays.  Every generator is deterministic for a given seed
+(``numpy.random.default_rng``).
+
+Workloads (shapes and value ranges follow the spiral-galaxy example of the
+SKIRT paper, Sect. 2.5 and its ski file, and the component table, Table 1):
+
+* ``uniform_cube``: uniform dust cube, central isotropic point source, one
+  face-on frame (the plain-method case).
+* ``disk_galaxy``: double-exponential stellar disk inside a double-exponential
+  dust disk on a cartesian grid, several wavelengths with smooth synthetic
+  optical properties, three frames at inclinations 0, 60 and 90 degrees.
+* ``clumpy_octree``: Gaussian dust clumps binned onto an adaptive octree
+  (Sect. 2.4), Plummer bulge plus exponential disk.
+* ``lognormal_cube``: log-normal density field for gradient checks.
+* ``batch_models``: many small independent models for the batched launcher.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import List, Optional
+
+import numpy as np
+
+
+@dataclass
+class Grid:
+    """Dust grid.  ``kind`` is ``"cartesian"`` (density float32 [nz, ny, nx],
+    x fastest) or ``"octree"`` (``child`` int32 per node: index of the first of
+    eight children, or -(leaf + 1) for a leaf; density float32 per leaf)."""
+    kind: str
+    bounds: np.ndarray  # float64 [xmin, xmax, ymin, ymax, zmin, zmax]
+    density: np.ndarray
+    child: Optional[np.ndarray] = None
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.density.size)
+
+    @property
+    def shape(self):
+        """(nx, ny, nz) for cartesian grids."""
+        nz, ny, nx = self.density.shape
+        return nx, ny, nz
+
+
+@dataclass
+class Source:
+    """Emission component: ``point`` (center), ``expdisk`` (center, scale_r =
+    hR, scale_z = hz, disk in the xy plane) or ``plummer`` (center, scale_r =
+    a).  ``lum``: luminosity per wavelength."""
+    kind: str
+    center: tuple
+    lum: np.ndarray
+    scale_r: float = 0.0
+    scale_z: float = 0.0
+
+
+@dataclass
+class Instrument:
+    """Frame instrument with parallel projection.  Angles in radians;
+    ``half_x``/``half_y`` are half-widths of the field; ``channels`` is 1
+    (total) or 3 (total, direct, scattered)."""
+    inclination: float
+    azimuth: float
+    position_angle: float
+    nx: int
+    ny: int
+    half_x: float
+    half_y: float
+    center_x: float = 0.0
+    center_y: float = 0.0
+    bilinear: bool = False
+    channels: int = 1
+
+
+@dataclass
+class Run:
+    """Run settings: total packets per wavelength and termination rule."""
+    n_per_lambda: int
+    seed: int = 0
+    w_min: float = 1e-4
+    max_events: int = 1000
+    weight_cut: bool = True
+
+
+@dataclass
+class Problem:
+    name: str
+    grid: Grid
+    wavelengths: np.ndarray
+    kappa: np.ndarray
+    albedo: np.ndarray
+    g: np.ndarray
+    sources: List[Source]
+    instruments: List[Instrument]
+    run: Run
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_lambda(self) -> int:
+        return int(len(self.kappa))
+
+
+def _f64(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def cartesian_grid(bounds, density) -> Grid:
+    return Grid("cartesian", _f64(bounds), np.ascontiguousarray(density, dtype=np.float32))
+
+
+def cell_centres(bounds, shape):
+    """Cell-centre coordinates (x [nx], y [ny], z [nz]) of a cartesian grid."""
+    nx, ny, nz = shape
+    b = np.asarray(bounds, dtype=np.float64)
+    xs = b[0] + (np.arange(nx) + 0.5) * (b[1] - b[0]) / nx
+    ys = b[2] + (np.arange(ny) + 0.5) * (b[3] - b[2]) / ny
+    zs = b[4] + (np.arange(nz) + 0.5) * (b[5] - b[4]) / nz
+    return xs, ys, zs
+
+
+def synthetic_optics(wavelengths_um, kappa_v):
+    """Smooth synthetic dust optics with x = ln(lambda / 0.55 um):
+    kappa = kappa_V exp(-1.3 x), albedo = clip(0.6 - 0.1 x^2, 0.3, 0.8),
+    g = clip(0.6 - 0.15 x, 0, 0.9)."""
+    x = np.log(np.asarray(wavelengths_um, dtype=np.float64) / 0.55)
+    kappa = kappa_v * np.exp(-1.3 * x)
+    albedo = np.clip(0.6 - 0.1 * x * x, 0.3, 0.8)
+    g = np.clip(0.6 - 0.15 * x, 0.0, 0.9)
+    return kappa, albedo, g
+
+
+def face_on(n, half, bilinear=False, channels=1) -> Instrument:
+    """Frame looking down the +z axis; image x = model x, image y = model y."""
+    return Instrument(0.0, -math.pi / 2, 0.0, n, n, half, half, bilinear=bilinear, channels=channels)
+
+
+# ---------------------------------------------------------------- workloads
+def uniform_cube(n_cells=32, half=1.0, axis_tau=1.0, albedo=0.6, g=0.5, n_pix=64,
+                 n_packets=100_000, channels=1, source_pos=(0.0, 0.0, 0.0), rho=1.0) -> Problem:
+    """Uniform cube [-half, half]^3 with ``n_cells``^3 cells.  ``axis_tau`` is
+    the optical depth along the full x axis through the centre, so
+    kappa rho = axis_tau / (2 half).  Central isotropic point source of unit
+    luminosity; one face-on frame covering the cube."""
+    b = [-half, half] * 3
+    dens = np.full((n_cells,) * 3, rho, dtype=np.float32)
+    kappa = axis_tau / (2.0 * half) / rho if rho > 0 else 1.0
+    return Problem(
+        name=f"uniform_cube_{n_cells}",
+        grid=cartesian_grid(b, dens),
+        wavelengths=_f64([0.55]),
+        kappa=_f64([kappa]), albedo=_f64([albedo]), g=_f64([g]),
+        sources=[Source("point", tuple(float(c) for c in source_pos), _f64([1.0]))],
+        instruments=[face_on(n_pix, half, channels=channels)],
+        run=Run(n_per_lambda=n_packets),
+    )
+
+
+def disk_galaxy(n_cells=256, n_lambda=10, n_pix=512, n_packets_total=100_000_000,
+                face_on_tau_v=0.5, channels=1) -> Problem:
+    """Edge-on disk galaxy.  Domain x, y in [-25, 25] kpc, z in [-3, 3] kpc.
+    Dust rho = exp(-R/6 - |z|/0.2) sampled at cell centres, kappa_V chosen so
+    that the face-on V-band optical depth through the centre is
+    kappa_V * rho0 * 2 hz = ``face_on_tau_v``.  Stars: exponential disk
+    hR = 4 kpc, hz = 0.35 kpc, unit luminosity per wavelength.  Wavelengths
+    log-spaced 0.15 - 2.2 um.  Three ``n_pix``^2 frames at inclinations 0, 60
+    and 90 degrees (azimuth -90 degrees), half-width 25 kpc.  The total packet
+    count is split equally over the wavelengths."""
+    bounds = [-25.0, 25.0, -25.0, 25.0, -3.0, 3.0]
+    xs, ys, zs = cell_centres(bounds, (n_cells, n_cells, n_cells))
+    R = np.sqrt(xs[None, None, :] ** 2 + ys[None, :, None] ** 2)
+    dens = np.exp(-R / 6.0 - np.abs(zs)[:, None, None] / 0.2).astype(np.float32)
+    wl = np.geomspace(0.15, 2.2, n_lambda)
+    kappa, albedo, g = synthetic_optics(wl, face_on_tau_v / (2.0 * 0.2))
+    instr = [Instrument(math.radians(inc), -math.pi / 2, 0.0, n_pix, n_pix, 25.0, 25.0, channels=channels)
+             for inc in (0.0, 60.0, 90.0)]
+    return Problem(
+        name=f"disk_galaxy_{n_cells}",
+        grid=cartesian_grid(bounds, dens),
+        wavelengths=wl, kappa=kappa, albedo=albedo, g=g,
+        sources=[Source("expdisk", (0.0, 0.0, 0.0), np.ones(n_lambda), scale_r=4.0, scale_z=0.35)],
+        instruments=instr,
+        run=Run(n_per_lambda=max(1, n_packets_total // n_lambda)),
+    )
+
+
+def lognormal_cube(n_cells=64, sigma_ln=1.0, mean_axis_tau=2.0, smooth_cells=2.0, seed=4,
+                   albedo=0.5, g=0.6, n_pix=128, n_packets=10_000_000, max_events=20) -> Problem:
+    """Log-normal density on [-1, 1]^3: G = Gaussian-smoothed white noise,
+    rho = exp(sigma_ln G / std(G)), scaled so that the mean full-axis column
+    optical depth (kappa = 1) is ``mean_axis_tau``.  Central point source,
+    face-on bilinear frame, termination after ``max_events`` events only."""
+    from scipy.ndimage import gaussian_filter
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal((n_cells,) * 3)
+    G = gaussian_filter(noise, smooth_cells, mode="wrap")
+    rho = np.exp(sigma_ln * G / G.std())
+    dz = 2.0 / n_cells
+    column = rho.sum(axis=0) * dz  # kappa = 1
+    rho *= mean_axis_tau / column.mean()
+    return Problem(
+        name=f"lognormal_cube_{n_cells}",
+        grid=cartesian_grid([-1.0, 1.0] * 3, rho.astype(np.float32)),
+        wavelengths=_f64([0.55]), kappa=_f64([1.0]), albedo=_f64([albedo]), g=_f64([g]),
+        sources=[Source("point", (0.0, 0.0, 0.0), _f64([1.0]))],
+        instruments=[face_on(n_pix, 1.0, bilinear=True)],
+        run=Run(n_per_lambda=n_packets, max_events=max_events, weight_cut=False),
+        meta={"seed": seed},
+    )
+
+
+def with_density(problem: Problem, density) -> Problem:
+    """Copy of ``problem`` with a different density array (same grid shape)."""
+    grid = replace(problem.grid, density=np.ascontiguousarray(density, dtype=np.float32))
+    return replace(problem, grid=grid)
+
+
+def with_packets(problem: Problem, n_per_lambda: int) -> Problem:
+    return replace(problem, run=replace(problem.run, n_per_lambda=int(n_per_lambda)))
+
+
+# ---------------------------------------------------------------- octrees
+def build_octree(bounds, refine, leaf_value, max_level):
+    """Octree by recursive 2x2x2 subdivision (Sect. 2.4), built level by level.
+
+    ``refine(lo, hi, level) -> bool[N]`` decides which of N nodes (boxes
+    lo[N, 3], hi[N, 3]) are split; nodes at ``max_level`` are never split.
+    ``leaf_value(lo, hi) -> float[N]`` gives the density of leaves.  Returns a
+    :class:`Grid` with ``child`` (int32 per node: first child index, children
+    contiguous in octant order bit0 = x upper, bit1 = y upper, bit2 = z upper;
+    or -(leaf + 1)) and per-leaf density, plus the leaf boxes."""
+    b = np.asarray(bounds, dtype=np.float64)
+    lo = b[[0, 2, 4]][None, :].copy()
+    hi = b[[1, 3, 5]][None, :].copy()
+    child_parts, leaf_lo, leaf_hi = [], [], []
+    n_nodes_before = 0
+    n_leaves = 0
+    level = 0
+    octs = np.array([[(o >> a) & 1 for a in range(3)] for o in range(8)], dtype=np.float64)
+    while lo.shape[0]:
+        n = lo.shape[0]
+        split = np.zeros(n, dtype=bool) if level >= max_level else np.asarray(refine(lo, hi, level), dtype=bool)
+        child = np.empty(n, dtype=np.int64)
+        n_split = int(split.sum())
+        first_next = n_nodes_before + n
+        child[split] = first_next + 8 * np.arange(n_split)
+        leaf_ids = n_leaves + np.arange(n - n_split)
+        child[~split] = -(leaf_ids + 1)
+        n_leaves += n - n_split
+        child_parts.append(child)
+        leaf_lo.append(lo[~split])
+        leaf_hi.append(hi[~split])
+        plo, phi = lo[split], hi[split]
+        mid = 0.5 * (plo + phi)
+        upper = np.tile(octs, (n_split, 1)) > 0
+        clo = np.where(upper, np.repeat(mid, 8, axis=0), np.repeat(plo, 8, axis=0))
+        chi = np.where(upper, np.repeat(phi, 8, axis=0), np.repeat(mid, 8, axis=0))
+        n_nodes_before += n
+        lo, hi = clo, chi
+        level += 1
+    child = np.concatenate(child_parts)
+    if child.max(initial=0) > np.iinfo(np.int32).max or n_leaves > np.iinfo(np.int32).max:
+        raise ValueError("octree too large for int32 node indices")
+    llo = np.concatenate(leaf_lo)
+    lhi = np.concatenate(leaf_hi)
+    dens = np.asarray(leaf_value(llo, lhi), dtype=np.float32)
+    g = Grid("octree", _f64(bounds), np.ascontiguousarray(dens), child.astype(np.int32))
+    return g, llo, lhi
+
+
+def octree_problem_like(problem: Problem, grid: Grid) -> Problem:
+    return replace(problem, grid=grid)

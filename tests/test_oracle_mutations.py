@@ -1,0 +1,60 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case compiles a copy of the oracle with one planted mistake (a dropped
+term, a wrong sign, a transposed index ...) and runs the pin module expected to
+catch it against that copy; the module must fail.  CPU only.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "rt_oracle.cpp")
+
+MUTATIONS = {
+    # continuous absorption without the (1 - albedo) factor
+    "absorption_albedo": ("T dep = T(1.0 - alb) * L", "T dep = T(1.0) * L", "test_oracle_transport.py"),
+    # peel-off phase function evaluated at the wrong cosine sign
+    "peel_phase_sign": ("hg_phase(P.g[lam], k.x * f.kobs.x + k.y * f.kobs.y + k.z * f.kobs.z)",
+                        "hg_phase(P.g[lam], -(k.x * f.kobs.x + k.y * f.kobs.y + k.z * f.kobs.z))",
+                        "test_oracle_transport.py"),
+    # interaction drawn without forcing (plain exponential optical depth)
+    "unforced": ("const T tau_star = -log1p(-T(u[0]) * one_minus_E);", "const T tau_star = -log1p(-T(u[0]));",
+                 "test_oracle_transport.py"),
+    # pixel index transposed
+    "pixel_transpose": ("int64_t pix = (int64_t)iy * f.nx + (int64_t)ix;\n        tally",
+                        "int64_t pix = (int64_t)ix * f.nx + (int64_t)iy;\n        tally", "test_oracle_transport.py"),
+    # deposit into the next cell along the path
+    "absorption_index": ("tally.absorb(lam, segs[i].cell, dep);",
+                         "tally.absorb(lam, segs[i + 1 < segs.size() ? i + 1 : i].cell, dep);",
+                         "test_oracle_transport.py"),
+    # Philox round uses the wrong product half
+    "philox_half": ("uint32_t n0 = hi1 ^ c[1] ^ k0;", "uint32_t n0 = hi0 ^ c[1] ^ k0;", "test_oracle_rng.py"),
+    # walk always steps towards +axis
+    "walk_direction": ("idx[axis] += comp(k, axis) > 0 ? 1 : -1;", "idx[axis] += 1;", "test_oracle_geometry.py"),
+    # azimuth drawn over half a turn
+    "half_azimuth": ("return rotate_dir(k, hg_sample(g, u1), 2.0 * M_PI * u2);",
+                     "return rotate_dir(k, hg_sample(g, u1), M_PI * u2);", "test_oracle_optics.py"),
+    # derivative of exp with the wrong sign
+    "dual_exp_sign": ("inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, e * a.d}; }",
+                      "inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, -e * a.d}; }",
+                      "test_oracle_transport.py"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new, module = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    cpp = tmp_path / f"{name}.cpp"
+    so = tmp_path / f"{name}.so"
+    cpp.write_text(src.replace(old, new, 1))
+    subprocess.run(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+                    str(cpp), "-o", str(so)], check=True)
+    env = dict(os.environ, RT_ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", module)], env=env, capture_output=True, text=True, cwd=ROOT)
+    assert r.returncode == 1, f"mutation {name} was not caught:\n{r.stdout[-2000:]}"
