@@ -1,0 +1,325 @@
+"""Benchmark: photon-packet Monte Carlo transport on the edge-on disk galaxy.
+
+Workload (one step): 1e8 photon packets (1e7 at each of 10 wavelengths) through
+a 256^3 cartesian dust grid (double-exponential dust disk), double-exponential
+stellar disk, three 512^2 frames at inclinations 0/60/90 degrees, forced
+scattering, continuous absorption and peel-off (FP32 geometry, FP64
+accumulators).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the baseline arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "photon packets/s & cell crossings/s at 1e-4 vs FP64 oracle; adjoint/forward ratio"
+UNIT = "packets/s"
+L2_FLUSH_BYTES = 256 << 20
+# algorithmic bytes: forced-path crossing = 4 B density + 16 B FP64 absorption RMW;
+# peel-off crossing = 4 B density; peel-off deposit = 16 B FP64 pixel RMW
+BYTES_PATH_CROSSING, BYTES_PEEL_CROSSING, BYTES_DEPOSIT = 20, 4, 16
+
+
+def workload():
+    from paper_1410_1629_gb300 import workloads as W
+    return W.disk_galaxy()
+
+
+def workload_config(prob, world):
+    return {"workload": "edge-on disk galaxy: 256^3 cartesian grid, 10 wavelengths 0.15-2.2 um, 1e8 packets/step "
+                        "(1e7 per wavelength) per GPU, 3 frames 512^2 at i=0/60/90 deg",
+            "grid": "cartesian 256x256x256 float32", "n_lambda": prob.n_lambda,
+            "packets_per_step_per_gpu": int(prob.run.n_per_lambda * prob.n_lambda),
+            "detectors": "3 x 512x512 x 10 lambda, float64",
+            "l2": "flushed between timed steps (256 MiB write); absorption tallies (1.34 GB) exceed L2",
+            "parallelism": f"packet-id ranges sharded over {world} GPU(s), no collective on the data path"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.device), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(prob, seconds, threads):
+    """Time the oracle (as it stands) on a bounded sample of the workload."""
+    from oracle import oracle as O
+    O.build()
+    probe = 50
+    t0 = time.perf_counter()
+    O.run(prob, probe, n_threads=threads, n_norm=prob.run.n_per_lambda)
+    dt = time.perf_counter() - t0
+    per_packet = dt / (probe * prob.n_lambda)
+    n = int(max(probe, min(prob.run.n_per_lambda, seconds / max(per_packet, 1e-9) / prob.n_lambda)))
+    t0 = time.perf_counter()
+    r = O.run(prob, n, n_threads=threads, n_norm=prob.run.n_per_lambda)
+    dt = time.perf_counter() - t0
+    packets = n * prob.n_lambda
+    return packets / dt, packets, dt, int(r["counters"][0])
+
+
+def run_reference(args, prob, world, rank):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    per_step = []
+    total_packets = 0
+    for i in range(args.warmup + args.steps):
+        rate, packets, dt, _ = oracle_sample(prob, args.reference_step_seconds, threads)
+        if i >= args.warmup:
+            per_step.append(dt)
+            total_packets += packets
+    value = total_packets / sum(per_step)
+    sample = (f"first {total_packets // (args.steps * prob.n_lambda)} packet ids per wavelength of the "
+              f"workload per step (all 10 wavelengths), FP64 oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(per_step) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(prob, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, prob, world, rank, local_rank):
+    import torch
+    from paper_1410_1629_gb300 import rt
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+    device = local_rank
+    torch.cuda.set_device(device)
+    stream = torch.cuda.Stream(device)
+    n = prob.run.n_per_lambda
+    first = rank * n
+    n_norm = world * n
+    sim = rt.Simulation(prob, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{device}")
+
+    def step(ev0, ev1):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            sim.reset(stream=stream)
+            ev0.record(stream)
+            sim.launch(n, first, prob.run.seed, stream=stream, n_norm=n_norm)
+            ev1.record(stream)
+
+    for _ in range(args.warmup):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        step(e0, e1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device)
+    clocks.start()
+    times, counts = [], []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        step(e0, e1)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        counts.append(sim.stats())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_total = sum(times)
+    if dist:
+        t = torch.tensor([t_total], dtype=torch.float64, device=f"cuda:{device}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    packets_step = n * prob.n_lambda
+    value = world * packets_step * args.steps / t_total
+    st = counts[-1]
+    crossings_step = st["crossings"]
+    path_cross = st["path_crossings"]
+    peel_cross = crossings_step - path_cross
+    deposits = st["peeloffs"]
+    bytes_launch = BYTES_PATH_CROSSING * path_cross + BYTES_PEEL_CROSSING * peel_cross + BYTES_DEPOSIT * deposits
+    mean_launch = t_total / args.steps
+    peak, peak_kind = peaks()
+    achieved = bytes_launch / mean_launch / 1e9
+    conservation = abs(st["emitted"] - st["escaped"] - st["absorbed"] - st["truncated"]) / st["emitted"]
+
+    # end to end through the C ABI with host buffers: upload the grid, set up,
+    # launch, read every image and the absorption field back to pinned memory
+    e2e = None
+    if not args.skip_e2e:
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        dens_host = torch.from_numpy(np.ascontiguousarray(prob.grid.density)).pin_memory()
+        img_host = [torch.empty(sim.image_shape(q), dtype=torch.float64).pin_memory()
+                    for q in range(len(prob.instruments))]
+        ab_host = torch.empty((prob.n_lambda, prob.grid.n_cells), dtype=torch.float64).pin_memory()
+        ctx = rt.rt_context_create(device)
+        try:
+            e2e_times = []
+            for i in range(e2e_steps + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                d = rt.rt_grid_desc()
+                d.kind = rt.RT_GRID_CARTESIAN
+                d.bounds[:] = [float(b) for b in prob.grid.bounds]
+                d.nz, d.ny, d.nx = prob.grid.density.shape
+                d.density = dens_host.data_ptr()
+                rt.rt_create_grid(ctx, d)
+                rt.rt_set_optics(ctx, 0, prob.kappa, prob.albedo, prob.g, prob.wavelengths)
+                rt.rt_add_sources(ctx, [rt.source_desc(s) for s in prob.sources], [s.lum for s in prob.sources])
+                rt.rt_add_instruments(ctx, [rt.instrument_desc(q) for q in prob.instruments])
+                o = rt.rt_default_opts()
+                o.n_norm = n_norm
+                rt.rt_launch_packets(ctx, n, first, prob.run.seed, o, stream.cuda_stream)
+                for q, buf in enumerate(img_host):
+                    rt.rt_read_images(ctx, q, buf.data_ptr(), buf.numel(), 0, stream.cuda_stream)
+                rt.rt_read_absorption(ctx, ab_host.data_ptr(), ab_host.numel(), 0, stream.cuda_stream)
+                torch.cuda.synchronize()
+                if i > 0:  # the first pass is a warm-up
+                    e2e_times.append(time.perf_counter() - t0)
+        finally:
+            rt.rt_context_destroy(ctx)
+        te = sum(e2e_times)
+        if dist:
+            t = torch.tensor([te], dtype=torch.float64, device=f"cuda:{device}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        h2d = dens_host.numel() * 4 + 8 * prob.n_lambda * (3 + len(prob.sources))
+        d2h = sum(b.numel() for b in img_host) * 8 + ab_host.numel() * 8
+        e2e = {"value": world * packets_step * len(e2e_times) / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": len(e2e_times),
+               "includes": "rt_create_grid from pinned host density, optics, sources, instruments, launch, "
+                           "rt_read_images and rt_read_absorption to pinned host memory"}
+    sim.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        threads = os.cpu_count() or 1
+        rate, packets, dt, _ = oracle_sample(prob, args.cpu_seconds, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {packets // prob.n_lambda} packet ids per wavelength of the workload "
+                         f"({packets} packets, {dt:.1f} s), FP64 oracle, all host threads"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": workload_config(prob, world),
+                "crossings_per_s": world * crossings_step * args.steps / t_total,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": args.traffic,
+                             "peak_source": f"{peak_kind} hbm_gbs",
+                             "algorithmic_bytes_per_launch": int(bytes_launch),
+                             "kernel": "k_forward<cartesian>", "launch_ms": 1e3 * mean_launch},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                "clocks": clk,
+                "checks": {"conservation_rel": conservation, "path_crossings": int(path_cross),
+                           "peel_crossings": int(peel_cross), "peeloffs": int(deposits),
+                           "events": int(st["events"])}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--reference-step-seconds", type=float, default=8.0)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per launch of the forward kernel from an ncu capture (scaled)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    prob = workload()
+    if args.impl == "reference":
+        run_reference(args, prob, world, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    try:
+        run_gpu(args, prob, world, rank, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

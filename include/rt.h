@@ -1,0 +1,237 @@
+/*
+ * rt.h - C ABI of the GB300 photon-packet Monte Carlo dust radiative transfer
+ * library (librt_gb300.so).
+ *
+ * The operation is the transport loop of a SKIRT-style simulation (Camps &
+ * Baes, "SKIRT: an advanced dust radiative transfer code with a user-friendly
+ * architecture"): photon packets are emitted by the sources, walk straight
+ * through the cells of a dust grid accumulating optical depth, interact by
+ * forced scattering, deposit absorbed luminosity continuously along their
+ * path, scatter with a Henyey-Greenstein phase function, and at emission and
+ * at every scattering "peel off" a fraction of their luminosity towards every
+ * frame instrument (Sect. 1: peel-off, continuous absorption, forced
+ * scattering; Sect. 2.2: sources, dust system, grid, instruments; Sect. 2.3:
+ * albedo and asymmetry parameter g; Sect. 2.4: cartesian grids and octrees).
+ *
+ * The simulation set-up of Sect. 2.2 (wavelength grid, stellar system, dust
+ * system with its grid, instrument system) and the construct / setup / run
+ * phases of Sect. 3.2 map onto the calls below:
+ *   rt_context_create -> rt_create_grid -> rt_set_optics -> rt_add_sources ->
+ *   rt_add_instruments -> rt_launch_packets (any number of times) ->
+ *   rt_read_images / rt_read_absorption / rt_read_stats.
+ *
+ * Conventions for every call
+ *   - Return value: RT_OK (0) or a negative rt_status.  No call aborts,
+ *     traps or prints.  rt_last_error() gives a message for the last failure.
+ *   - Ownership: the library owns all device state of a context.  Input
+ *     arrays are copied during the call; the caller keeps ownership of its
+ *     buffers and may free them when the call returns.  Output buffers belong
+ *     to the caller.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Launches are asynchronous.  Errors raised by
+ *     asynchronous work surface at the next synchronising call (rt_read_* to
+ *     host memory, rt_read_stats, rt_synchronize).
+ *   - A context is bound to one CUDA device and is not thread-safe.
+ *
+ * Units: lengths in any consistent unit; kappa is the extinction cross
+ * section per unit density per unit length; images hold luminosity per
+ * steradian per pixel (divide by distance^2 for flux); absorption holds
+ * absorbed luminosity per cell.
+ */
+#ifndef RT_GB300_H
+#define RT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_ctx_s* rt_ctx;
+typedef int32_t rt_status;
+
+enum {
+  RT_OK = 0,
+  RT_ERR_ARG = -1,          /* invalid argument (null pointer, bad size, value out of range)  */
+  RT_ERR_STATE = -2,        /* call out of order (e.g. launch before rt_set_optics)            */
+  RT_ERR_OOM = -3,          /* device or host allocation failed                                */
+  RT_ERR_CUDA = -4,         /* a CUDA runtime call failed; see rt_last_error                   */
+  RT_ERR_TIMEOUT = -5,      /* a bounded device wait ran out                                   */
+  RT_ERR_DEVICE_FLAG = -6   /* a kernel's own bounds check fired; results are not valid        */
+};
+
+enum { RT_GRID_CARTESIAN = 0, RT_GRID_OCTREE = 1 };
+enum { RT_SOURCE_POINT = 0, RT_SOURCE_EXPDISK = 1, RT_SOURCE_PLUMMER = 2 };
+enum { RT_DEPOSIT_NEAREST = 0, RT_DEPOSIT_BILINEAR = 1 };
+
+/* Dust grid (Sect. 2.2: constant density per cell; Sect. 2.4: grid kinds).
+ *   kind RT_GRID_CARTESIAN: nx*ny*nz equal cells spanning `bounds`;
+ *       density float32 [nz][ny][nx] (x fastest); cell id = ix + nx*(iy + ny*iz).
+ *   kind RT_GRID_OCTREE: recursive 2x2x2 subdivision of `bounds` at box
+ *       midpoints; child int32 [n_nodes], node 0 the root: child[n] >= 0 is
+ *       the index of the first of n's eight contiguous children (octant
+ *       o = bit0 x-upper | bit1 y-upper | bit2 z-upper), child[n] < 0 marks a
+ *       leaf with leaf id -(child[n] + 1); density float32 [n_leaves];
+ *       cell id = leaf id.  Depth at most 24.
+ *   bounds: xmin, xmax, ymin, ymax, zmin, zmax (FP64; the kernels use FP32).
+ *   Pointers are host pointers unless on_device = 1.  Data is copied. */
+typedef struct {
+  int32_t kind;
+  int32_t nx, ny, nz;
+  double bounds[6];
+  const float* density;
+  int64_t n_nodes;
+  const int32_t* child;
+  int64_t n_leaves;
+  int32_t on_device;
+  int32_t reserved;
+} rt_grid_desc;
+
+/* Emission component (Sect. 2.2 stellar system, Sect. 3.4 position sampling,
+ * Table 1(a) geometries).  RT_SOURCE_POINT: at `center`.  RT_SOURCE_EXPDISK:
+ * double-exponential disk in the plane z = center[2], scale length scale_r,
+ * scale height scale_z.  RT_SOURCE_PLUMMER: Plummer sphere of scale radius
+ * scale_r.  Emission is isotropic.  luminosity: host float64 [n_lambda]. */
+typedef struct {
+  int32_t kind;
+  int32_t reserved;
+  double center[3];
+  double scale_r, scale_z;
+  const double* luminosity;
+} rt_source_desc;
+
+/* Frame instrument with parallel projection (Sect. 2.2; the parameters of
+ * the FrameInstrument of the Sect. 2.5 example).  Direction to the observer
+ * k = (sin i cos a, sin i sin a, cos i); image axes before the position angle
+ * w: ex = (-sin a, cos a, 0), ey = (-cos i cos a, -cos i sin a, sin i); the
+ * position angle turns them to cos w ex - sin w ey and sin w ex + cos w ey.
+ * Pixel of image coordinate X: floor((X - center_x + half_x) nx / (2 half_x)).
+ * channels = 1: total only; channels = 3: total, direct (emission peel-off),
+ * scattered (scattering peel-off).  Image layout float64
+ * [channels][n_lambda][ny][nx]. */
+typedef struct {
+  double inclination, azimuth, position_angle; /* radians */
+  int32_t nx, ny;
+  double half_x, half_y;
+  double center_x, center_y;
+  int32_t deposit;   /* RT_DEPOSIT_NEAREST or RT_DEPOSIT_BILINEAR (pixel centres) */
+  int32_t channels;  /* 1 or 3 */
+} rt_instrument_desc;
+
+/* One peel-off deposit into the total channel (debug records, nearest
+ * deposit only): packet id, wavelength index, event (0 = emission),
+ * instrument, pixel iy*nx + ix, value. */
+typedef struct {
+  uint64_t packet;
+  int32_t lambda, event, instrument, reserved;
+  int64_t pixel;
+  double value;
+} rt_record;
+
+/* Launch options.  Zero-initialise and set what you need; rt_default_opts
+ * fills the defaults (w_min 1e-4, max_events 1000, weight cut on, both
+ * peel-offs on). */
+typedef struct {
+  double w_min;         /* terminate when L < w_min * L0 (if weight_cut)                   */
+  int32_t max_events;   /* terminate after this many scattering events (>= 1)              */
+  int32_t weight_cut;   /* 1: weight rule + event cap; 0: event cap only                   */
+  int32_t peel_emission;
+  int32_t peel_scatter;
+  uint64_t n_norm;      /* packets per wavelength for the weight L_tot/n_norm; 0 = n_per_lambda */
+  uint32_t model_id;    /* second Philox key word                                          */
+  int32_t block_size;   /* threads per block; 0 = library choice                           */
+  rt_record* records;   /* device buffer for debug records, or NULL                        */
+  int64_t records_capacity;
+  uint64_t record_stride; /* record only packets whose id is a multiple of this (0, 1: all)  */
+} rt_launch_opts;
+
+/* Tallies since the last rt_reset_tallies. */
+typedef struct {
+  double emitted, escaped, absorbed, truncated; /* luminosity                              */
+  uint64_t crossings;   /* cell segments visited by forced paths and peel-off paths        */
+  uint64_t path_crossings; /* of which on forced paths (first pass)                         */
+  uint64_t events;      /* forced scattering events                                        */
+  uint64_t peeloffs;    /* peel-off paths (one per instrument per emission / scattering)   */
+  uint64_t packets;
+  uint64_t records;     /* debug records produced (may exceed the capacity)                */
+  int32_t device_flags; /* non-zero if a kernel bounds check fired                         */
+  int32_t reserved;
+} rt_stats;
+
+/* Library version string (static storage). */
+const char* rt_version(void);
+
+/* Create a context on CUDA device `device`.  *out receives the handle.
+ * Errors: RT_ERR_ARG (null out, bad device), RT_ERR_CUDA, RT_ERR_OOM. */
+rt_status rt_context_create(int32_t device, rt_ctx* out);
+
+/* Destroy a context and free all its device memory.  NULL is accepted. */
+rt_status rt_context_destroy(rt_ctx ctx);
+
+/* Message for the last failed call on ctx (static "" if none); owned by the
+ * context, valid until the next call on it.  ctx NULL gives the message of the
+ * last failed rt_context_create. */
+const char* rt_last_error(rt_ctx ctx);
+
+/* Fill *opts with the defaults. */
+void rt_default_opts(rt_launch_opts* opts);
+
+/* Dust grid (Sect. 2.2, 2.4).  Replaces any previous grid of the context,
+ * drops optics, sources, instruments and tallies.  *grid_id receives 0.
+ * Errors: RT_ERR_ARG (sizes <= 0, bounds not increasing, octree child index
+ * out of range, negative density), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_create_grid(rt_ctx ctx, const rt_grid_desc* desc, int32_t* grid_id);
+
+/* Optical properties per wavelength (Sect. 2.3): kappa (>= 0), albedo in
+ * [0, 1], HG asymmetry g in (-1, 1); host float64 arrays [n_lambda],
+ * 1 <= n_lambda <= 64; `lambda` (wavelengths) may be NULL.  Resets tallies.
+ * Errors: RT_ERR_ARG, RT_ERR_STATE (no grid). */
+rt_status rt_set_optics(rt_ctx ctx, int32_t grid_id, int32_t n_lambda, const double* lambda,
+                        const double* kappa, const double* albedo, const double* g);
+
+/* Append n emission components (Sect. 2.2 stellar system); at most 16 in
+ * total.  Each luminosity array has n_lambda entries >= 0.
+ * Errors: RT_ERR_ARG, RT_ERR_STATE (no optics). */
+rt_status rt_add_sources(rt_ctx ctx, int32_t n, const rt_source_desc* sources);
+
+/* Append n frame instruments (Sect. 2.2); at most 16 in total.  ids (may be
+ * NULL) receives their indices.  Allocates and zeroes their images.
+ * Errors: RT_ERR_ARG (pixels <= 0, half widths <= 0, channels not 1 or 3),
+ * RT_ERR_STATE (no optics), RT_ERR_OOM. */
+rt_status rt_add_instruments(rt_ctx ctx, int32_t n, const rt_instrument_desc* instruments, int32_t* ids);
+
+/* Run n_per_lambda packets at every wavelength, with packet ids
+ * [first_packet_id, first_packet_id + n_per_lambda), Philox key (seed,
+ * opts->model_id).  Tallies accumulate across launches until
+ * rt_reset_tallies, so id ranges can be split over launches.  Asynchronous
+ * on `stream`.  opts may be NULL (defaults).  seed must be < 2^32.
+ * Errors: RT_ERR_ARG, RT_ERR_STATE (no sources or no optics), RT_ERR_CUDA. */
+rt_status rt_launch_packets(rt_ctx ctx, uint64_t n_per_lambda, uint64_t first_packet_id, uint64_t seed,
+                            const rt_launch_opts* opts, void* stream);
+
+/* Zero images, absorption and statistics (asynchronous on stream). */
+rt_status rt_reset_tallies(rt_ctx ctx, void* stream);
+
+/* Copy the absorbed luminosity, float64 [n_lambda][n_cells], into dst.
+ * n_elems must equal n_lambda * n_cells.  dst_on_device = 1: device pointer,
+ * asynchronous on stream; 0: host pointer, returns when the copy is done.
+ * Errors: RT_ERR_ARG (size mismatch), RT_ERR_STATE, RT_ERR_CUDA. */
+rt_status rt_read_absorption(rt_ctx ctx, double* dst, size_t n_elems, int32_t dst_on_device, void* stream);
+
+/* Copy instrument `instrument_id`'s image, float64 [channels][n_lambda][ny][nx],
+ * into dst; n_elems must match.  Same conventions as rt_read_absorption. */
+rt_status rt_read_images(rt_ctx ctx, int32_t instrument_id, double* dst, size_t n_elems, int32_t dst_on_device,
+                         void* stream);
+
+/* Synchronise the context's work and read the statistics.
+ * Errors: RT_ERR_CUDA, RT_ERR_DEVICE_FLAG (stats are still written). */
+rt_status rt_read_stats(rt_ctx ctx, rt_stats* out);
+
+/* Wait for all work queued on `stream` and report asynchronous errors. */
+rt_status rt_synchronize(rt_ctx ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_GB300_H */

@@ -486,8 +486,11 @@ void grid_path(const Grid& G, const V3<T>& x, const V3d& k, int64_t start_cell,
       double ka = comp(k, axis);
       double plane = ka > 0 ? box.hi[axis] : box.lo[axis];
       if ((ka > 0 && plane >= G.hi[axis]) || (ka < 0 && plane <= G.lo[axis])) break;
+      // exit point on the face crossed, the other coordinates kept inside the
+      // leaf so that rounding never steps back across a face already crossed
       double p[3];
-      for (int a = 0; a < 3; ++a) p[a] = val(comp(x, a)) + val(t) * comp(k, a);
+      for (int a = 0; a < 3; ++a)
+        p[a] = std::min(box.hi[a], std::max(box.lo[a], val(comp(x, a)) + val(t) * comp(k, a)));
       p[axis] = plane;
       leaf = G.octree_locate(p, k, &box);
     }
@@ -527,7 +530,22 @@ Problem make_problem(const or_problem& in) {
 }
 
 // ---------------------------------------------------------------- tallies
-// Accumulates into plain arrays (double runs).
+// Lock-free add to a double shared between threads (compare-and-swap loop).
+inline void shared_add(double* p, double v) {
+  uint64_t* u = reinterpret_cast<uint64_t*>(p);
+  uint64_t old = __atomic_load_n(u, __ATOMIC_RELAXED);
+  while (true) {
+    double cur;
+    std::memcpy(&cur, &old, sizeof cur);
+    const double nv = cur + v;
+    uint64_t nu;
+    std::memcpy(&nu, &nv, sizeof nu);
+    if (__atomic_compare_exchange_n(u, &old, nu, true, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) return;
+  }
+}
+
+// Accumulates into plain arrays (double runs).  With `shared_abs` set, the
+// absorption tallies of all threads go to one array (large grids).
 struct ArrayTally {
   const Problem* P;
   std::vector<std::vector<double>> images;
@@ -535,6 +553,8 @@ struct ArrayTally {
   std::vector<double> absorption;
   std::vector<int64_t> absorption_counts;
   bool want_abs = false, want_counts = false;
+  double* shared_abs = nullptr;
+  int64_t* shared_abs_counts = nullptr;
   NSum emitted, escaped, absorbed, truncated;
   uint64_t crossings = 0, events = 0, peeloffs = 0, packets = 0;
   std::vector<or_record>* records = nullptr;
@@ -548,7 +568,7 @@ struct ArrayTally {
       images.emplace_back(n, 0.0);
       image_counts.emplace_back(counts ? n : 0, 0);
     }
-    if (abs) {
+    if (abs && !shared_abs) {
       absorption.assign((size_t)prob.n_lambda * prob.grid.n_cells(), 0.0);
       if (counts) absorption_counts.assign(absorption.size(), 0);
     }
@@ -564,6 +584,11 @@ struct ArrayTally {
     absorbed.add(value);
     if (!want_abs) return;
     size_t i = (size_t)lam * P->grid.n_cells() + cell;
+    if (shared_abs) {
+      shared_add(&shared_abs[i], value);
+      if (shared_abs_counts) __atomic_fetch_add(&shared_abs_counts[i], 1, __ATOMIC_RELAXED);
+      return;
+    }
     absorption[i] += value;
     if (want_counts) absorption_counts[i] += 1;
   }
@@ -864,7 +889,16 @@ int32_t or_run(const or_problem* prob, const or_opts* opts, or_output* out) {
   const bool want_counts = out->image_counts != nullptr || out->absorption_counts != nullptr;
   std::vector<ArrayTally> tallies((size_t)n_threads);
   std::vector<std::vector<or_record>> recs(1);
-  for (int t = 0; t < n_threads; ++t) tallies[t].init(P, want_abs, want_counts);
+  // private absorption arrays per thread unless that needs more than 2 GiB
+  const double abs_bytes = (double)P.n_lambda * (double)P.grid.n_cells() * (want_counts ? 16.0 : 8.0);
+  const bool shared = want_abs && n_threads > 1 && abs_bytes * n_threads > 2.0 * (1 << 30);
+  for (int t = 0; t < n_threads; ++t) {
+    if (shared) {
+      tallies[t].shared_abs = out->absorption;
+      tallies[t].shared_abs_counts = out->absorption_counts;
+    }
+    tallies[t].init(P, want_abs, want_counts);
+  }
   if (out->records) tallies[0].records = &recs[0];
   // static interleaved chunks: deterministic for a given thread count
   const int64_t chunk = 64;
@@ -911,7 +945,7 @@ int32_t or_run(const or_problem* prob, const or_opts* opts, or_output* out) {
         for (size_t i = 0; i < T.image_counts[q].size(); ++i) dst[i] += T.image_counts[q][i];
       }
     }
-    if (want_abs) {
+    if (want_abs && !shared) {
       for (size_t i = 0; i < T.absorption.size(); ++i) out->absorption[i] += T.absorption[i];
       if (out->absorption_counts)
         for (size_t i = 0; i < T.absorption_counts.size(); ++i) out->absorption_counts[i] += T.absorption_counts[i];

@@ -1,0 +1,563 @@
+// Host side of the C ABI declared in include/rt.h: context and device-memory
+// management, argument validation, uploads, launches and read-back.
+//
+// The call sequence follows the simulation phases of the SKIRT paper
+// (Sect. 3.2: construction, setup, run): the grid, optics, sources and
+// instruments are copied to the device once (setup); rt_launch_packets runs
+// packets (run); rt_read_* return the tallies.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "rt_internal.h"
+
+using namespace rtk;
+
+namespace {
+
+struct HostSource {
+  rt_source_desc desc;
+  std::vector<double> lum;
+};
+
+struct HostInstr {
+  rt_instrument_desc desc;
+  double* d_image = nullptr;
+  size_t n_elems = 0;
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct rt_ctx_s {
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  // grid
+  bool has_grid = false;
+  int grid_kind = 0;
+  int nx = 0, ny = 0, nz = 0;
+  double bounds[6] = {0};
+  long long n_cells = 0;
+  long long n_nodes = 0;
+  float* d_density = nullptr;
+  int32_t* d_child = nullptr;
+  // optics
+  int n_lambda = 0;
+  std::vector<double> kappa, albedo, g;
+  // sources, instruments
+  std::vector<HostSource> sources;
+  std::vector<HostInstr> instr;
+  // device tables and tallies
+  double* d_absorption = nullptr;
+  DevLambda* d_lam = nullptr;
+  DevSource* d_src = nullptr;
+  double* d_src_cum = nullptr;
+  DevInstr* d_instr = nullptr;
+  double* d_stats = nullptr;
+  unsigned long long* d_counters = nullptr;
+  unsigned long long* d_work = nullptr;
+  int* d_flags = nullptr;
+  bool tables_dirty = true;
+};
+
+namespace {
+
+rt_status fail(rt_ctx ctx, rt_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf; else g_create_error = buf;
+  return code;
+}
+
+rt_status cuda_fail(rt_ctx ctx, cudaError_t e, const char* what) {
+  return fail(ctx, e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define RT_CUDA(ctx, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+rt_status set_device(rt_ctx ctx) {
+  RT_CUDA(ctx, cudaSetDevice(ctx->device));
+  return RT_OK;
+}
+
+void free_grid(rt_ctx c) {
+  dfree(c->d_density);
+  dfree(c->d_child);
+  dfree(c->d_absorption);
+  c->has_grid = false;
+}
+
+void free_problem(rt_ctx c) {
+  for (auto& q : c->instr) dfree(q.d_image);
+  c->instr.clear();
+  c->sources.clear();
+  c->n_lambda = 0;
+  dfree(c->d_absorption);
+  c->tables_dirty = true;
+}
+
+rt_status zero_tallies(rt_ctx c, cudaStream_t s) {
+  for (auto& q : c->instr) RT_CUDA(c, cudaMemsetAsync(q.d_image, 0, q.n_elems * sizeof(double), s));
+  if (c->d_absorption)
+    RT_CUDA(c, cudaMemsetAsync(c->d_absorption, 0, (size_t)c->n_lambda * c->n_cells * sizeof(double), s));
+  RT_CUDA(c, cudaMemsetAsync(c->d_stats, 0, 4 * sizeof(double), s));
+  RT_CUDA(c, cudaMemsetAsync(c->d_counters, 0, 8 * sizeof(unsigned long long), s));
+  RT_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), s));
+  return RT_OK;
+}
+
+// Frame axes from inclination, azimuth and position angle (FP64 on the host).
+void frame_axes(const rt_instrument_desc& d, double kobs[3], double ex[3], double ey[3]) {
+  const double st = std::sin(d.inclination), ct = std::cos(d.inclination);
+  const double sp = std::sin(d.azimuth), cp = std::cos(d.azimuth);
+  const double so = std::sin(d.position_angle), co = std::cos(d.position_angle);
+  kobs[0] = st * cp; kobs[1] = st * sp; kobs[2] = ct;
+  const double a[3] = {-sp, cp, 0.0};
+  const double b[3] = {-ct * cp, -ct * sp, st};
+  for (int i = 0; i < 3; ++i) {
+    ex[i] = co * a[i] - so * b[i];
+    ey[i] = so * a[i] + co * b[i];
+  }
+}
+
+// Rebuild the small device tables (per-wavelength optics, sources, instruments).
+rt_status upload_tables(rt_ctx c, cudaStream_t s) {
+  if (!c->tables_dirty) return RT_OK;
+  std::vector<DevLambda> lam((size_t)c->n_lambda);
+  for (int l = 0; l < c->n_lambda; ++l) {
+    DevLambda& L = lam[l];
+    std::memset(&L, 0, sizeof L);
+    L.kappa = (float)c->kappa[l];
+    L.g = (float)c->g[l];
+    L.albedo = c->albedo[l];
+    double tot = 0.0;
+    for (auto& src : c->sources) tot += src.lum[l];
+    L.lum_total = tot;
+  }
+  const int ns = (int)c->sources.size();
+  std::vector<DevSource> src((size_t)ns);
+  std::vector<double> cum((size_t)c->n_lambda * ns);
+  for (int i = 0; i < ns; ++i) {
+    const rt_source_desc& d = c->sources[i].desc;
+    std::memset(&src[i], 0, sizeof(DevSource));
+    src[i].kind = d.kind;
+    for (int a = 0; a < 3; ++a) src[i].center[a] = d.center[a];
+    src[i].scale_r = d.scale_r;
+    src[i].scale_z = d.scale_z;
+  }
+  for (int l = 0; l < c->n_lambda; ++l) {
+    double tot = 0.0, run = 0.0;
+    for (int i = 0; i < ns; ++i) tot += c->sources[i].lum[l];
+    for (int i = 0; i < ns; ++i) {
+      run += c->sources[i].lum[l];
+      cum[(size_t)l * ns + i] = run / tot;
+    }
+  }
+  std::vector<DevInstr> ins(c->instr.size());
+  for (size_t q = 0; q < c->instr.size(); ++q) {
+    const rt_instrument_desc& d = c->instr[q].desc;
+    double kobs[3], ex[3], ey[3];
+    frame_axes(d, kobs, ex, ey);
+    DevInstr& I = ins[q];
+    std::memset(&I, 0, sizeof I);
+    for (int a = 0; a < 3; ++a) { I.kobs[a] = (float)kobs[a]; I.ex[a] = (float)ex[a]; I.ey[a] = (float)ey[a]; }
+    I.off_x = (float)(d.half_x - d.center_x);
+    I.off_y = (float)(d.half_y - d.center_y);
+    I.sx = (float)(d.nx / (2.0 * d.half_x));
+    I.sy = (float)(d.ny / (2.0 * d.half_y));
+    I.nx = d.nx; I.ny = d.ny;
+    I.bilinear = d.deposit == RT_DEPOSIT_BILINEAR;
+    I.channels = d.channels;
+    I.image = c->instr[q].d_image;
+  }
+  dfree(c->d_lam); dfree(c->d_src); dfree(c->d_src_cum); dfree(c->d_instr);
+  RT_CUDA(c, cudaMalloc(&c->d_lam, std::max<size_t>(1, lam.size()) * sizeof(DevLambda)));
+  RT_CUDA(c, cudaMalloc(&c->d_src, std::max<size_t>(1, src.size()) * sizeof(DevSource)));
+  RT_CUDA(c, cudaMalloc(&c->d_src_cum, std::max<size_t>(1, cum.size()) * sizeof(double)));
+  RT_CUDA(c, cudaMalloc(&c->d_instr, std::max<size_t>(1, ins.size()) * sizeof(DevInstr)));
+  // synchronous copies: the host vectors go out of scope on return
+  if (!lam.empty()) RT_CUDA(c, cudaMemcpy(c->d_lam, lam.data(), lam.size() * sizeof(DevLambda), cudaMemcpyHostToDevice));
+  if (!src.empty()) RT_CUDA(c, cudaMemcpy(c->d_src, src.data(), src.size() * sizeof(DevSource), cudaMemcpyHostToDevice));
+  if (!cum.empty()) RT_CUDA(c, cudaMemcpy(c->d_src_cum, cum.data(), cum.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (!ins.empty()) RT_CUDA(c, cudaMemcpy(c->d_instr, ins.data(), ins.size() * sizeof(DevInstr), cudaMemcpyHostToDevice));
+  (void)s;
+  c->tables_dirty = false;
+  return RT_OK;
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+}  // namespace
+
+extern "C" {
+
+const char* rt_version(void) { return "rt_gb300 1.0 (sm_103a)"; }
+
+rt_status rt_context_create(int32_t device, rt_ctx* out) {
+  if (!out) return fail(nullptr, RT_ERR_ARG, "rt_context_create: out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return fail(nullptr, RT_ERR_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+  if (device < 0 || device >= n) return fail(nullptr, RT_ERR_ARG, "device %d out of range [0, %d)", device, n);
+  rt_ctx c = new (std::nothrow) rt_ctx_s();
+  if (!c) return fail(nullptr, RT_ERR_OOM, "host allocation failed");
+  c->device = device;
+  e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_work, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_flags, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(c->d_flags, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    rt_context_destroy(c);
+    return fail(nullptr, RT_ERR_CUDA, "context set-up: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return RT_OK;
+}
+
+rt_status rt_context_destroy(rt_ctx c) {
+  if (!c) return RT_OK;
+  cudaSetDevice(c->device);
+  free_problem(c);
+  free_grid(c);
+  dfree(c->d_lam); dfree(c->d_src); dfree(c->d_src_cum); dfree(c->d_instr);
+  dfree(c->d_stats); dfree(c->d_counters); dfree(c->d_work); dfree(c->d_flags);
+  delete c;
+  return RT_OK;
+}
+
+const char* rt_last_error(rt_ctx c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void rt_default_opts(rt_launch_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->w_min = 1e-4;
+  o->max_events = 1000;
+  o->weight_cut = 1;
+  o->peel_emission = 1;
+  o->peel_scatter = 1;
+}
+
+rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (!d || !d->density) return fail(c, RT_ERR_ARG, "rt_create_grid: null descriptor or density");
+  for (int a = 0; a < 3; ++a)
+    if (!(is_finite(d->bounds[2 * a]) && is_finite(d->bounds[2 * a + 1]) && d->bounds[2 * a] < d->bounds[2 * a + 1]))
+      return fail(c, RT_ERR_ARG, "rt_create_grid: bounds on axis %d are not increasing", a);
+  long long n_cells = 0, n_nodes = 0;
+  if (d->kind == RT_GRID_CARTESIAN) {
+    if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0) return fail(c, RT_ERR_ARG, "rt_create_grid: cell counts must be > 0");
+    n_cells = (long long)d->nx * d->ny * d->nz;
+    if (n_cells > (1ll << 31) - 1) return fail(c, RT_ERR_ARG, "rt_create_grid: more than 2^31-1 cells");
+  } else if (d->kind == RT_GRID_OCTREE) {
+    if (!d->child || d->n_nodes <= 0 || d->n_leaves <= 0)
+      return fail(c, RT_ERR_ARG, "rt_create_grid: octree needs child[] and counts > 0");
+    if (d->n_nodes > (1ll << 31) - 1 || d->n_leaves > (1ll << 31) - 1)
+      return fail(c, RT_ERR_ARG, "rt_create_grid: octree too large for int32 indices");
+    n_cells = d->n_leaves;
+    n_nodes = d->n_nodes;
+  } else {
+    return fail(c, RT_ERR_ARG, "rt_create_grid: unknown grid kind %d", d->kind);
+  }
+  std::vector<int32_t> child_host;
+  if (d->kind == RT_GRID_OCTREE) {
+    // validate the tree on the host: every child block in range, every leaf id in range
+    child_host.resize((size_t)n_nodes);
+    if (d->on_device) {
+      if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+      RT_CUDA(c, cudaMemcpy(child_host.data(), d->child, n_nodes * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(child_host.data(), d->child, n_nodes * sizeof(int32_t));
+    }
+    for (long long i = 0; i < n_nodes; ++i) {
+      const long long v = child_host[i];
+      if (v >= 0 && (v == 0 || v + 8 > n_nodes))
+        return fail(c, RT_ERR_ARG, "rt_create_grid: node %lld has child block %lld out of range", i, v);
+      if (v < 0 && (-v - 1) >= n_cells)
+        return fail(c, RT_ERR_ARG, "rt_create_grid: node %lld has leaf id %lld out of range", i, -v - 1);
+    }
+  }
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  free_problem(c);
+  free_grid(c);
+  const cudaMemcpyKind kind = d->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  RT_CUDA(c, cudaMalloc(&c->d_density, (size_t)n_cells * sizeof(float)));
+  RT_CUDA(c, cudaMemcpy(c->d_density, d->density, (size_t)n_cells * sizeof(float), kind));
+  if (d->kind == RT_GRID_OCTREE) {
+    RT_CUDA(c, cudaMalloc(&c->d_child, (size_t)n_nodes * sizeof(int32_t)));
+    RT_CUDA(c, cudaMemcpy(c->d_child, child_host.data(), (size_t)n_nodes * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
+  c->grid_kind = d->kind;
+  c->nx = d->nx; c->ny = d->ny; c->nz = d->nz;
+  std::memcpy(c->bounds, d->bounds, sizeof c->bounds);
+  c->n_cells = n_cells;
+  c->n_nodes = n_nodes;
+  c->has_grid = true;
+  c->tables_dirty = true;
+  if (grid_id) *grid_id = 0;
+  return RT_OK;
+}
+
+rt_status rt_set_optics(rt_ctx c, int32_t grid_id, int32_t n_lambda, const double* lambda, const double* kappa,
+                        const double* albedo, const double* g) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  (void)lambda;
+  if (!c->has_grid) return fail(c, RT_ERR_STATE, "rt_set_optics: no grid");
+  if (grid_id != 0) return fail(c, RT_ERR_ARG, "rt_set_optics: unknown grid id %d", grid_id);
+  if (n_lambda < 1 || n_lambda > kMaxLambda) return fail(c, RT_ERR_ARG, "rt_set_optics: n_lambda must be 1..%d", kMaxLambda);
+  if (!kappa || !albedo || !g) return fail(c, RT_ERR_ARG, "rt_set_optics: null array");
+  for (int l = 0; l < n_lambda; ++l) {
+    if (!(is_finite(kappa[l]) && kappa[l] >= 0)) return fail(c, RT_ERR_ARG, "rt_set_optics: kappa[%d] invalid", l);
+    if (!(albedo[l] >= 0 && albedo[l] <= 1)) return fail(c, RT_ERR_ARG, "rt_set_optics: albedo[%d] not in [0,1]", l);
+    if (!(g[l] > -1 && g[l] < 1)) return fail(c, RT_ERR_ARG, "rt_set_optics: g[%d] not in (-1,1)", l);
+  }
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  free_problem(c);
+  c->n_lambda = n_lambda;
+  c->kappa.assign(kappa, kappa + n_lambda);
+  c->albedo.assign(albedo, albedo + n_lambda);
+  c->g.assign(g, g + n_lambda);
+  const size_t n_abs = (size_t)n_lambda * c->n_cells;
+  RT_CUDA(c, cudaMalloc(&c->d_absorption, n_abs * sizeof(double)));
+  RT_CUDA(c, cudaMemset(c->d_absorption, 0, n_abs * sizeof(double)));
+  RT_CUDA(c, cudaMemset(c->d_stats, 0, 4 * sizeof(double)));
+  RT_CUDA(c, cudaMemset(c->d_counters, 0, 8 * sizeof(unsigned long long)));
+  c->tables_dirty = true;
+  return RT_OK;
+}
+
+rt_status rt_add_sources(rt_ctx c, int32_t n, const rt_source_desc* s) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (c->n_lambda == 0) return fail(c, RT_ERR_STATE, "rt_add_sources: set optics first");
+  if (n < 0 || (n > 0 && !s)) return fail(c, RT_ERR_ARG, "rt_add_sources: bad count or null array");
+  if ((int)c->sources.size() + n > kMaxSources) return fail(c, RT_ERR_ARG, "rt_add_sources: at most %d sources", kMaxSources);
+  for (int i = 0; i < n; ++i) {
+    const rt_source_desc& d = s[i];
+    if (d.kind < RT_SOURCE_POINT || d.kind > RT_SOURCE_PLUMMER) return fail(c, RT_ERR_ARG, "source %d: unknown kind", i);
+    if (!d.luminosity) return fail(c, RT_ERR_ARG, "source %d: null luminosity", i);
+    if (d.kind != RT_SOURCE_POINT && !(d.scale_r > 0)) return fail(c, RT_ERR_ARG, "source %d: scale_r must be > 0", i);
+    if (d.kind == RT_SOURCE_EXPDISK && !(d.scale_z > 0)) return fail(c, RT_ERR_ARG, "source %d: scale_z must be > 0", i);
+    for (int a = 0; a < 3; ++a) if (!is_finite(d.center[a])) return fail(c, RT_ERR_ARG, "source %d: bad centre", i);
+    for (int l = 0; l < c->n_lambda; ++l)
+      if (!(is_finite(d.luminosity[l]) && d.luminosity[l] >= 0)) return fail(c, RT_ERR_ARG, "source %d: bad luminosity", i);
+  }
+  for (int i = 0; i < n; ++i) {
+    HostSource h;
+    h.desc = s[i];
+    h.lum.assign(s[i].luminosity, s[i].luminosity + c->n_lambda);
+    h.desc.luminosity = nullptr;
+    c->sources.push_back(h);
+  }
+  c->tables_dirty = true;
+  return RT_OK;
+}
+
+rt_status rt_add_instruments(rt_ctx c, int32_t n, const rt_instrument_desc* q, int32_t* ids) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (c->n_lambda == 0) return fail(c, RT_ERR_STATE, "rt_add_instruments: set optics first");
+  if (n < 0 || (n > 0 && !q)) return fail(c, RT_ERR_ARG, "rt_add_instruments: bad count or null array");
+  if ((int)c->instr.size() + n > kMaxInstruments)
+    return fail(c, RT_ERR_ARG, "rt_add_instruments: at most %d instruments", kMaxInstruments);
+  for (int i = 0; i < n; ++i) {
+    const rt_instrument_desc& d = q[i];
+    if (d.nx <= 0 || d.ny <= 0 || (long long)d.nx * d.ny > (1ll << 28))
+      return fail(c, RT_ERR_ARG, "instrument %d: bad pixel counts", i);
+    if (!(d.half_x > 0 && d.half_y > 0)) return fail(c, RT_ERR_ARG, "instrument %d: half widths must be > 0", i);
+    if (d.channels != 1 && d.channels != 3) return fail(c, RT_ERR_ARG, "instrument %d: channels must be 1 or 3", i);
+    if (d.deposit != RT_DEPOSIT_NEAREST && d.deposit != RT_DEPOSIT_BILINEAR)
+      return fail(c, RT_ERR_ARG, "instrument %d: unknown deposit mode", i);
+    if (!(is_finite(d.inclination) && is_finite(d.azimuth) && is_finite(d.position_angle) && is_finite(d.center_x) &&
+          is_finite(d.center_y)))
+      return fail(c, RT_ERR_ARG, "instrument %d: non-finite angle or centre", i);
+  }
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  for (int i = 0; i < n; ++i) {
+    HostInstr h;
+    h.desc = q[i];
+    h.n_elems = (size_t)q[i].channels * c->n_lambda * q[i].ny * q[i].nx;
+    RT_CUDA(c, cudaMalloc(&h.d_image, h.n_elems * sizeof(double)));
+    RT_CUDA(c, cudaMemset(h.d_image, 0, h.n_elems * sizeof(double)));
+    if (ids) ids[i] = (int32_t)c->instr.size();
+    c->instr.push_back(h);
+  }
+  c->tables_dirty = true;
+  return RT_OK;
+}
+
+rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_packet_id, uint64_t seed,
+                            const rt_launch_opts* opts, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (!c->has_grid || c->n_lambda == 0) return fail(c, RT_ERR_STATE, "rt_launch_packets: grid and optics required");
+  if (c->sources.empty()) return fail(c, RT_ERR_STATE, "rt_launch_packets: no sources");
+  if (seed >> 32) return fail(c, RT_ERR_ARG, "rt_launch_packets: seed must be < 2^32");
+  rt_launch_opts o;
+  rt_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.max_events < 1) return fail(c, RT_ERR_ARG, "rt_launch_packets: max_events must be >= 1");
+  if (!(o.w_min >= 0 && o.w_min < 1)) return fail(c, RT_ERR_ARG, "rt_launch_packets: w_min must be in [0, 1)");
+  if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32))
+    return fail(c, RT_ERR_ARG, "rt_launch_packets: block_size must be a multiple of 32 in [32, 256]");
+  if (o.records && o.records_capacity < 0) return fail(c, RT_ERR_ARG, "rt_launch_packets: negative record capacity");
+  for (int l = 0; l < c->n_lambda; ++l) {
+    double tot = 0;
+    for (auto& s : c->sources) tot += s.lum[l];
+    if (!(tot > 0)) return fail(c, RT_ERR_ARG, "rt_launch_packets: zero total luminosity at wavelength %d", l);
+  }
+  if (n_per_lambda == 0) return RT_OK;
+  const unsigned long long n_total = n_per_lambda * (unsigned long long)c->n_lambda;
+  if (n_total / (unsigned long long)c->n_lambda != n_per_lambda || n_total > (1ull << 62))
+    return fail(c, RT_ERR_ARG, "rt_launch_packets: packet count overflow");
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  rt_status st = upload_tables(c, s);
+  if (st != RT_OK) return st;
+  FwdParams p;
+  std::memset(&p, 0, sizeof p);
+  p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
+  for (int a = 0; a < 3; ++a) {
+    p.lo[a] = (float)c->bounds[2 * a];
+    p.hi[a] = (float)c->bounds[2 * a + 1];
+    const int n = a == 0 ? c->nx : (a == 1 ? c->ny : c->nz);
+    if (c->grid_kind == RT_GRID_CARTESIAN) {
+      const double d = (c->bounds[2 * a + 1] - c->bounds[2 * a]) / n;
+      p.d[a] = (float)d;
+      p.inv_d[a] = (float)(1.0 / d);
+    }
+  }
+  p.density = c->d_density;
+  p.child = c->d_child;
+  p.n_cells = c->n_cells;
+  p.n_lambda = c->n_lambda;
+  p.n_sources = (int)c->sources.size();
+  p.n_instr = (int)c->instr.size();
+  p.lam = c->d_lam;
+  p.src = c->d_src;
+  p.src_cum = c->d_src_cum;
+  p.instr = c->d_instr;
+  p.absorption = c->d_absorption;
+  p.n_per_lambda = n_per_lambda;
+  p.first_id = first_packet_id;
+  p.n_total = n_total;
+  p.n_norm = o.n_norm ? o.n_norm : n_per_lambda;
+  p.seed = (unsigned)seed;
+  p.model = o.model_id;
+  p.w_min = o.w_min;
+  p.max_events = o.max_events;
+  p.weight_cut = o.weight_cut;
+  p.peel_emission = o.peel_emission;
+  p.peel_scatter = o.peel_scatter;
+  p.work_counter = c->d_work;
+  p.stats = c->d_stats;
+  p.counters = c->d_counters;
+  p.records = o.records;
+  p.records_cap = o.records ? o.records_capacity : 0;
+  p.record_stride = o.record_stride;
+  p.flags = c->d_flags;
+  cudaError_t e = launch_forward(p, c->grid_kind, o.block_size, c->num_sms, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "forward launch");
+  return RT_OK;
+}
+
+rt_status rt_reset_tallies(rt_ctx c, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  return zero_tallies(c, (cudaStream_t)stream);
+}
+
+static rt_status copy_out(rt_ctx c, double* dst, const double* src, size_t n, int32_t on_device, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (on_device) {
+    RT_CUDA(c, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    RT_CUDA(c, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(c, cudaStreamSynchronize(s));
+  }
+  return RT_OK;
+}
+
+rt_status rt_read_absorption(rt_ctx c, double* dst, size_t n_elems, int32_t on_device, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (!c->d_absorption) return fail(c, RT_ERR_STATE, "rt_read_absorption: no optics set");
+  if (!dst) return fail(c, RT_ERR_ARG, "rt_read_absorption: null destination");
+  const size_t n = (size_t)c->n_lambda * c->n_cells;
+  if (n_elems != n) return fail(c, RT_ERR_ARG, "rt_read_absorption: n_elems %zu != %zu", n_elems, n);
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  return copy_out(c, dst, c->d_absorption, n, on_device, stream);
+}
+
+rt_status rt_read_images(rt_ctx c, int32_t id, double* dst, size_t n_elems, int32_t on_device, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (id < 0 || id >= (int)c->instr.size()) return fail(c, RT_ERR_ARG, "rt_read_images: unknown instrument %d", id);
+  if (!dst) return fail(c, RT_ERR_ARG, "rt_read_images: null destination");
+  const size_t n = c->instr[id].n_elems;
+  if (n_elems != n) return fail(c, RT_ERR_ARG, "rt_read_images: n_elems %zu != %zu", n_elems, n);
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  return copy_out(c, dst, c->instr[id].d_image, n, on_device, stream);
+}
+
+rt_status rt_read_stats(rt_ctx c, rt_stats* out) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (!out) return fail(c, RT_ERR_ARG, "rt_read_stats: null output");
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  RT_CUDA(c, cudaDeviceSynchronize());
+  double st[4];
+  unsigned long long cn[8];
+  int flags = 0;
+  RT_CUDA(c, cudaMemcpy(st, c->d_stats, sizeof st, cudaMemcpyDeviceToHost));
+  RT_CUDA(c, cudaMemcpy(cn, c->d_counters, sizeof cn, cudaMemcpyDeviceToHost));
+  RT_CUDA(c, cudaMemcpy(&flags, c->d_flags, sizeof flags, cudaMemcpyDeviceToHost));
+  std::memset(out, 0, sizeof *out);
+  out->emitted = st[0]; out->escaped = st[1]; out->absorbed = st[2]; out->truncated = st[3];
+  out->crossings = cn[0]; out->path_crossings = cn[5]; out->events = cn[1]; out->peeloffs = cn[2]; out->packets = cn[3]; out->records = cn[4];
+  out->device_flags = flags;
+  if (flags) return fail(c, RT_ERR_DEVICE_FLAG, "a kernel bounds check fired (flags 0x%x)", flags);
+  return RT_OK;
+}
+
+rt_status rt_synchronize(rt_ctx c, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  RT_CUDA(c, cudaStreamSynchronize((cudaStream_t)stream));
+  RT_CUDA(c, cudaGetLastError());
+  return RT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+// Internal definitions shared by the host side of the C ABI (rt_api.cu) and the
+// kernels.  Not part of the public interface (include/rt.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rt.h"
+
+namespace rtk {
+
+constexpr int kMaxLambda = 64;
+constexpr int kMaxSources = 16;
+constexpr int kMaxInstruments = 16;
+constexpr int kMaxOctreeDepth = 24;
+
+// Per-wavelength optical properties (Sect. 2.3) and source luminosity total.
+struct DevLambda {
+  float kappa;        // extinction per unit density per unit length (FP32 for the walk)
+  float g;            // HG asymmetry parameter
+  float pad0, pad1;
+  double albedo;
+  double lum_total;   // sum of the sources' luminosities at this wavelength
+};
+
+// Emission component (Sect. 3.4); positions are sampled in FP64.
+struct DevSource {
+  int kind;
+  int pad;
+  double center[3];
+  double scale_r, scale_z;
+};
+
+// Frame instrument (Sect. 2.2): FP32 projection axes and pixel mapping.
+struct DevInstr {
+  float kobs[3], ex[3], ey[3];
+  float off_x, off_y;  // half width minus field centre
+  float sx, sy;        // pixels per unit length: n / (2 half)
+  int nx, ny;
+  int bilinear, channels;
+  double* image;       // [channels][n_lambda][ny][nx]
+};
+
+// Everything a forward launch needs, passed by value.
+struct FwdParams {
+  // dust grid
+  int nx, ny, nz;
+  int pad0;
+  float lo[3], hi[3], d[3], inv_d[3];
+  const float* density;
+  const int32_t* child;  // octree only
+  long long n_cells;
+  // problem
+  int n_lambda, n_sources, n_instr;
+  int pad1;
+  const DevLambda* lam;
+  const DevSource* src;
+  const double* src_cum;  // [n_lambda][n_sources] cumulative luminosity fractions
+  const DevInstr* instr;
+  double* absorption;     // [n_lambda][n_cells]
+  // run
+  unsigned long long n_per_lambda, first_id, n_total, n_norm;
+  unsigned int seed, model;
+  double w_min;
+  int max_events, weight_cut, peel_emission, peel_scatter;
+  unsigned long long* work_counter;
+  double* stats;                  // emitted, escaped, absorbed, truncated
+  unsigned long long* counters;   // crossings, events, peeloffs, packets, records, path crossings
+  rt_record* records;
+  long long records_cap;
+  unsigned long long record_stride;
+  int* flags;
+};
+
+enum DeviceFlag : int { kFlagCellRange = 1, kFlagOctreeDepth = 2, kFlagWalkSteps = 4 };
+// Upper bound on the cells one straight octree walk may visit before the
+// kernel flags an error and stops the walk (3 * 2^depth covers any ray for
+// the depths used; this is a safety net, not a tuning knob).
+constexpr unsigned kMaxWalkSteps = 1u << 22;
+
+// Launchers (rt_forward.cu).
+cudaError_t launch_forward(const FwdParams& p, int grid_kind, int block_size, int num_sms, cudaStream_t stream);
+
+}  // namespace rtk

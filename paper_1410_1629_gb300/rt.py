@@ -1,0 +1,373 @@
+"""Thin ctypes binding of the C ABI in ``include/rt.h`` (``librt_gb300.so``).
+
+Every function here has the name of the C function it wraps and only
+marshals arguments: all transport work runs in the library's CUDA kernels.
+A non-zero status raises :class:`RTError` with the library's message.  If the
+library is missing and cannot be built, :func:`lib` raises: there is no CPU
+fallback.
+
+PyTorch is used for device memory (output tensors) and streams
+(``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+RT_OK, RT_ERR_ARG, RT_ERR_STATE, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_DEVICE_FLAG = 0, -1, -2, -3, -4, -5, -6
+RT_GRID_CARTESIAN, RT_GRID_OCTREE = 0, 1
+RT_SOURCE_POINT, RT_SOURCE_EXPDISK, RT_SOURCE_PLUMMER = 0, 1, 2
+RT_DEPOSIT_NEAREST, RT_DEPOSIT_BILINEAR = 0, 1
+
+_SOURCE_KIND = {"point": RT_SOURCE_POINT, "expdisk": RT_SOURCE_EXPDISK, "plummer": RT_SOURCE_PLUMMER}
+
+
+class RTError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"rt status {status}: {message}")
+        self.status = status
+
+
+class rt_grid_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("bounds", ctypes.c_double * 6), ("density", ctypes.c_void_p), ("n_nodes", ctypes.c_int64),
+                ("child", ctypes.c_void_p), ("n_leaves", ctypes.c_int64), ("on_device", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class rt_source_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("center", ctypes.c_double * 3),
+                ("scale_r", ctypes.c_double), ("scale_z", ctypes.c_double),
+                ("luminosity", ctypes.POINTER(ctypes.c_double))]
+
+
+class rt_instrument_desc(ctypes.Structure):
+    _fields_ = [("inclination", ctypes.c_double), ("azimuth", ctypes.c_double), ("position_angle", ctypes.c_double),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("half_x", ctypes.c_double),
+                ("half_y", ctypes.c_double), ("center_x", ctypes.c_double), ("center_y", ctypes.c_double),
+                ("deposit", ctypes.c_int32), ("channels", ctypes.c_int32)]
+
+
+class rt_record(ctypes.Structure):
+    _fields_ = [("packet", ctypes.c_uint64), ("lambda_", ctypes.c_int32), ("event", ctypes.c_int32),
+                ("instrument", ctypes.c_int32), ("reserved", ctypes.c_int32), ("pixel", ctypes.c_int64),
+                ("value", ctypes.c_double)]
+
+
+RECORD_DTYPE = np.dtype([("pid", "<u8"), ("lam", "<i4"), ("event", "<i4"), ("instr", "<i4"),
+                         ("pad", "<i4"), ("pixel", "<i8"), ("value", "<f8")])
+
+
+class rt_launch_opts(ctypes.Structure):
+    _fields_ = [("w_min", ctypes.c_double), ("max_events", ctypes.c_int32), ("weight_cut", ctypes.c_int32),
+                ("peel_emission", ctypes.c_int32), ("peel_scatter", ctypes.c_int32), ("n_norm", ctypes.c_uint64),
+                ("model_id", ctypes.c_uint32), ("block_size", ctypes.c_int32), ("records", ctypes.c_void_p),
+                ("records_capacity", ctypes.c_int64), ("record_stride", ctypes.c_uint64)]
+
+
+class rt_stats(ctypes.Structure):
+    _fields_ = [("emitted", ctypes.c_double), ("escaped", ctypes.c_double), ("absorbed", ctypes.c_double),
+                ("truncated", ctypes.c_double), ("crossings", ctypes.c_uint64), ("path_crossings", ctypes.c_uint64), ("events", ctypes.c_uint64),
+                ("peeloffs", ctypes.c_uint64), ("packets", ctypes.c_uint64), ("records", ctypes.c_uint64),
+                ("device_flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+# name -> (restype, argtypes): the exported symbols of include/rt.h
+SIGNATURES = {
+    "rt_version": (ctypes.c_char_p, []),
+    "rt_context_create": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "rt_context_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "rt_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "rt_default_opts": (None, [ctypes.POINTER(rt_launch_opts)]),
+    "rt_create_grid": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rt_grid_desc), ctypes.POINTER(ctypes.c_int32)]),
+    "rt_set_optics": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 4),
+    "rt_add_sources": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(rt_source_desc)]),
+    "rt_add_instruments": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(rt_instrument_desc),
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    "rt_launch_packets": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.POINTER(rt_launch_opts), ctypes.c_void_p]),
+    "rt_reset_tallies": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "rt_read_absorption": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
+                                            ctypes.c_void_p]),
+    "rt_read_images": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                        ctypes.c_int32, ctypes.c_void_p]),
+    "rt_read_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rt_stats)]),
+    "rt_synchronize": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib():
+    """Load librt_gb300.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB_PATH
+            if not _build.up_to_date():
+                try:
+                    path = _build.build()
+                except Exception as exc:  # no toolkit: the extension does not exist
+                    raise RuntimeError(f"librt_gb300.so is not built and cannot be built: {exc}") from exc
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(ctx, status):
+    if status != RT_OK:
+        msg = lib().rt_last_error(ctx)
+        raise RTError(status, msg.decode() if msg else "")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------- C functions
+def rt_version() -> str:
+    return lib().rt_version().decode()
+
+
+def rt_context_create(device: int = 0):
+    h = ctypes.c_void_p()
+    st = lib().rt_context_create(int(device), ctypes.byref(h))
+    if st != RT_OK:
+        raise RTError(st, lib().rt_last_error(None).decode())
+    return h
+
+
+def rt_context_destroy(ctx):
+    lib().rt_context_destroy(ctx)
+
+
+def rt_last_error(ctx) -> str:
+    return lib().rt_last_error(ctx).decode()
+
+
+def rt_default_opts() -> rt_launch_opts:
+    o = rt_launch_opts()
+    lib().rt_default_opts(ctypes.byref(o))
+    return o
+
+
+def rt_create_grid(ctx, desc: rt_grid_desc) -> int:
+    gid = ctypes.c_int32()
+    _check(ctx, lib().rt_create_grid(ctx, ctypes.byref(desc), ctypes.byref(gid)))
+    return gid.value
+
+
+def rt_set_optics(ctx, grid_id, kappa, albedo, g, wavelengths=None):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (kappa, albedo, g)]
+    wl = np.ascontiguousarray(wavelengths, dtype=np.float64) if wavelengths is not None else None
+    n = arrs[0].size
+    _check(ctx, lib().rt_set_optics(ctx, int(grid_id), n, wl.ctypes.data if wl is not None else None,
+                                    arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data))
+
+
+def rt_add_sources(ctx, descs, luminosities):
+    n = len(descs)
+    arr = (rt_source_desc * max(1, n))()
+    keep = []
+    for i, (d, lum) in enumerate(zip(descs, luminosities)):
+        la = np.ascontiguousarray(lum, dtype=np.float64)
+        keep.append(la)
+        d.luminosity = la.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        arr[i] = d
+    _check(ctx, lib().rt_add_sources(ctx, n, arr))
+
+
+def rt_add_instruments(ctx, descs):
+    n = len(descs)
+    arr = (rt_instrument_desc * max(1, n))(*descs)
+    ids = (ctypes.c_int32 * max(1, n))()
+    _check(ctx, lib().rt_add_instruments(ctx, n, arr, ids))
+    return list(ids[:n])
+
+
+def rt_launch_packets(ctx, n_per_lambda, first_packet_id=0, seed=0, opts=None, stream=None):
+    o = opts if opts is not None else rt_default_opts()
+    _check(ctx, lib().rt_launch_packets(ctx, int(n_per_lambda), int(first_packet_id), int(seed), ctypes.byref(o),
+                                        _stream_ptr(stream)))
+
+
+def rt_reset_tallies(ctx, stream=None):
+    _check(ctx, lib().rt_reset_tallies(ctx, _stream_ptr(stream)))
+
+
+def rt_read_absorption(ctx, dst_ptr, n_elems, on_device, stream=None):
+    _check(ctx, lib().rt_read_absorption(ctx, dst_ptr, int(n_elems), int(on_device), _stream_ptr(stream)))
+
+
+def rt_read_images(ctx, instrument_id, dst_ptr, n_elems, on_device, stream=None):
+    _check(ctx, lib().rt_read_images(ctx, int(instrument_id), dst_ptr, int(n_elems), int(on_device),
+                                     _stream_ptr(stream)))
+
+
+def rt_read_stats(ctx) -> rt_stats:
+    s = rt_stats()
+    _check(ctx, lib().rt_read_stats(ctx, ctypes.byref(s)))
+    return s
+
+
+def rt_synchronize(ctx, stream=None):
+    _check(ctx, lib().rt_synchronize(ctx, _stream_ptr(stream)))
+
+
+# ---------------------------------------------------------------- descriptors from workloads
+def grid_desc(grid, on_device_arrays=None):
+    """rt_grid_desc for a workloads.Grid (host arrays; kept alive by the returned tuple)."""
+    d = rt_grid_desc()
+    d.bounds[:] = [float(b) for b in np.asarray(grid.bounds, dtype=np.float64)]
+    dens = np.ascontiguousarray(grid.density, dtype=np.float32)
+    keep = [dens]
+    d.density = dens.ctypes.data
+    if grid.kind == "cartesian":
+        d.kind = RT_GRID_CARTESIAN
+        nz, ny, nx = dens.shape
+        d.nx, d.ny, d.nz = nx, ny, nz
+    else:
+        d.kind = RT_GRID_OCTREE
+        child = np.ascontiguousarray(grid.child, dtype=np.int32)
+        keep.append(child)
+        d.child = child.ctypes.data
+        d.n_nodes = child.size
+        d.n_leaves = dens.size
+    return d, keep
+
+
+def source_desc(src):
+    d = rt_source_desc()
+    d.kind = _SOURCE_KIND[src.kind]
+    d.center[:] = [float(c) for c in src.center]
+    d.scale_r = float(src.scale_r)
+    d.scale_z = float(src.scale_z)
+    return d
+
+
+def instrument_desc(q):
+    d = rt_instrument_desc()
+    d.inclination, d.azimuth, d.position_angle = float(q.inclination), float(q.azimuth), float(q.position_angle)
+    d.nx, d.ny = int(q.nx), int(q.ny)
+    d.half_x, d.half_y = float(q.half_x), float(q.half_y)
+    d.center_x, d.center_y = float(q.center_x), float(q.center_y)
+    d.deposit = RT_DEPOSIT_BILINEAR if q.bilinear else RT_DEPOSIT_NEAREST
+    d.channels = int(q.channels)
+    return d
+
+
+class Simulation:
+    """A context set up from a :class:`workloads.Problem`: grid, optics,
+    sources and instruments uploaded once; packets launched any number of
+    times; tallies read into torch tensors or numpy arrays."""
+
+    def __init__(self, problem, device: int = 0):
+        self.problem = problem
+        self.device = int(device)
+        self.ctx = rt_context_create(self.device)
+        try:
+            desc, keep = grid_desc(problem.grid)
+            self.grid_id = rt_create_grid(self.ctx, desc)
+            del keep
+            rt_set_optics(self.ctx, self.grid_id, problem.kappa, problem.albedo, problem.g, problem.wavelengths)
+            rt_add_sources(self.ctx, [source_desc(s) for s in problem.sources], [s.lum for s in problem.sources])
+            self.instrument_ids = rt_add_instruments(self.ctx, [instrument_desc(q) for q in problem.instruments])
+        except Exception:
+            self.close()
+            raise
+        self.n_lambda = problem.n_lambda
+        self.n_cells = problem.grid.n_cells
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            rt_context_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def opts(self, **kw) -> rt_launch_opts:
+        o = rt_default_opts()
+        run = self.problem.run
+        o.w_min = run.w_min
+        o.max_events = run.max_events
+        o.weight_cut = int(run.weight_cut)
+        for k, v in kw.items():
+            if k == "records":
+                o.records = v
+            elif not hasattr(o, k):
+                raise TypeError(f"unknown launch option {k}")
+            else:
+                setattr(o, k, v)
+        return o
+
+    def launch(self, n_per_lambda=None, first_id=0, seed=None, stream=None, **opts):
+        n = self.problem.run.n_per_lambda if n_per_lambda is None else n_per_lambda
+        s = self.problem.run.seed if seed is None else seed
+        rt_launch_packets(self.ctx, n, first_id, s, self.opts(**opts), stream)
+
+    def reset(self, stream=None):
+        rt_reset_tallies(self.ctx, stream)
+
+    def image_shape(self, q):
+        ins = self.problem.instruments[q]
+        return (ins.channels, self.n_lambda, ins.ny, ins.nx)
+
+    def images(self, device=True, stream=None):
+        """Images per instrument: torch float64 tensors on the device (or numpy on the host)."""
+        out = []
+        for q in range(len(self.problem.instruments)):
+            shape = self.image_shape(q)
+            n = int(np.prod(shape))
+            if device:
+                import torch
+                t = torch.empty(shape, dtype=torch.float64, device=f"cuda:{self.device}")
+                rt_read_images(self.ctx, q, t.data_ptr(), n, 1, stream)
+            else:
+                t = np.empty(shape, dtype=np.float64)
+                rt_read_images(self.ctx, q, t.ctypes.data, n, 0, stream)
+            out.append(t)
+        return out
+
+    def absorption(self, device=True, stream=None):
+        shape = (self.n_lambda, self.n_cells)
+        n = shape[0] * shape[1]
+        if device:
+            import torch
+            t = torch.empty(shape, dtype=torch.float64, device=f"cuda:{self.device}")
+            rt_read_absorption(self.ctx, t.data_ptr(), n, 1, stream)
+        else:
+            t = np.empty(shape, dtype=np.float64)
+            rt_read_absorption(self.ctx, t.ctypes.data, n, 0, stream)
+        return t
+
+    def stats(self) -> dict:
+        return rt_read_stats(self.ctx).as_dict()

@@ -1,0 +1,150 @@
+"""GPU parity: the CUDA transport library against the FP64 oracle on the same
+seeded inputs and the same Philox streams, called through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1410_1629_gb300 import rt
+from paper_1410_1629_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU-only machines
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import parity as PAR  # noqa: E402
+
+
+def _assert_ok(rep):
+    assert rep["ok"], rep
+
+
+def test_uniform_cube_full_size():
+    """Plain method: 32^3 uniform cube, axis tau 1, albedo 0.6, g 0.5, 1e5
+    packets, 64^2 face-on frame."""
+    prob = W.uniform_cube()
+    n = prob.run.n_per_lambda
+    g = PAR.gpu_run(prob, n, records_cap=4_000_000)
+    o = PAR.oracle_run(prob, n, records_cap=4_000_000)
+    rep = PAR.compare(g, o, prob)
+    print(rep)
+    _assert_ok(rep)
+    assert rep["pixels"][0]["corrected"]["bins"] > 50
+    assert rep["cells"]["bins"] > 1000
+    assert rep["crossings_rel"] < 1e-5
+    assert abs(rep["events_diff"]) <= 10
+    # the rare flips are a tiny fraction of all contributions
+    assert rep["flips"] + rep["gpu_only"] + rep["oracle_only"] <= 1e-4 * rep["records"] + 10
+    assert rep["conservation_gpu"] < 1e-6
+
+
+def test_disk_galaxy_reduced():
+    """Several wavelengths and three frames (0, 60, 90 degrees) on a 64^3 disk."""
+    prob = W.disk_galaxy(n_cells=64, n_lambda=3, n_pix=64)
+    n = 20000
+    g = PAR.gpu_run(prob, n, records_cap=6_000_000)
+    o = PAR.oracle_run(prob, n, records_cap=6_000_000)
+    rep = PAR.compare(g, o, prob)
+    print(rep)
+    _assert_ok(rep)
+    assert sum(p["corrected"]["bins"] for p in rep["pixels"]) > 100
+
+
+def test_octree_parity():
+    rng = np.random.default_rng(21)
+    grid, _, _ = W.build_octree([-1, 1] * 3, lambda lo, hi, l: rng.uniform(size=len(lo)) < (0.8 if l < 2 else 0.4),
+                                lambda lo, hi: rng.lognormal(0.0, 1.0, len(lo)), 5)
+    prob = W.uniform_cube(axis_tau=2.0, channels=3)
+    prob.grid = grid
+    n = 50000
+    g = PAR.gpu_run(prob, n, records_cap=4_000_000)
+    o = PAR.oracle_run(prob, n, records_cap=4_000_000)
+    rep = PAR.compare(g, o, prob)
+    print(rep)
+    _assert_ok(rep)
+
+
+@pytest.mark.parametrize("case", ["no_scattering", "dust_free", "offset_source", "plummer_outside"])
+def test_special_cases(case):
+    if case == "no_scattering":
+        prob = W.uniform_cube(albedo=0.0, channels=3)
+    elif case == "dust_free":
+        prob = W.uniform_cube(rho=0.0, channels=3)
+    elif case == "offset_source":
+        prob = W.uniform_cube(source_pos=(0.3, -0.5, 0.2), channels=3, g=-0.4)
+    else:
+        prob = W.uniform_cube(channels=3)
+        prob.sources = [W.Source("plummer", (0.0, 0.0, 0.0), np.ones(1), scale_r=1.5)]
+    n = 20000
+    g = PAR.gpu_run(prob, n, records_cap=2_000_000)
+    o = PAR.oracle_run(prob, n, records_cap=2_000_000)
+    rep = PAR.compare(g, o, prob)
+    print(case, rep)
+    _assert_ok(rep)
+    if case == "no_scattering":
+        assert np.all(g["images"][0][2] == 0.0) and g["stats"][3] == 0.0
+    if case == "dust_free":
+        assert g["stats"][1] == g["stats"][0] and g["stats"][2] == 0.0
+        assert abs(g["images"][0][0, 0, 32, 32] - 1 / (4 * math.pi)) < 1e-12
+
+
+def test_bilinear_count_only_termination():
+    prob = W.lognormal_cube(n_cells=16, n_pix=32, n_packets=20000, max_events=20)
+    n = prob.run.n_per_lambda
+    g = PAR.gpu_run(prob, n)
+    o = PAR.oracle_run(prob, n)
+    rep = PAR.compare(g, o, prob, use_records=False)
+    print(rep)
+    _assert_ok(rep)
+
+
+def test_split_launches_equal_one_launch():
+    """Packet-id ranges are independent: [0, n) + [n, 2n) equals [0, 2n)."""
+    prob = W.uniform_cube(channels=3)
+    n = 20000
+    sim = rt.Simulation(prob)
+    sim.launch(n, 0, 0, n_norm=2 * n)
+    sim.launch(n, n, 0, n_norm=2 * n)
+    a = sim.images()[0].cpu().numpy()
+    sa = sim.stats()
+    sim.reset()
+    sim.launch(2 * n, 0, 0)
+    b = sim.images()[0].cpu().numpy()
+    sb = sim.stats()
+    sim.close()
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-18)
+    assert sa["crossings"] == sb["crossings"] and sa["events"] == sb["events"]
+
+
+def test_state_and_argument_errors():
+    ctx = rt.rt_context_create(0)
+    try:
+        with pytest.raises(rt.RTError) as e:
+            rt.rt_launch_packets(ctx, 10)
+        assert e.value.status == rt.RT_ERR_STATE
+        d, keep = rt.grid_desc(W.uniform_cube(n_cells=4).grid)
+        rt.rt_create_grid(ctx, d)
+        with pytest.raises(rt.RTError) as e:
+            rt.rt_set_optics(ctx, 0, [1.0], [1.5], [0.0])
+        assert e.value.status == rt.RT_ERR_ARG
+        rt.rt_set_optics(ctx, 0, [1.0], [0.5], [0.0])
+        with pytest.raises(rt.RTError) as e:
+            rt.rt_add_instruments(ctx, [rt.instrument_desc(W.Instrument(0, 0, 0, 0, 8, 1, 1))])
+        assert e.value.status == rt.RT_ERR_ARG
+        with pytest.raises(rt.RTError) as e:
+            rt.rt_read_images(ctx, 3, 0, 10, 0)
+        assert e.value.status == rt.RT_ERR_ARG
+        bad = rt.rt_grid_desc()
+        bad.kind = rt.RT_GRID_OCTREE
+        bad.bounds[:] = [-1, 1, -1, 1, -1, 1]
+        child = np.array([5, -1, -2], dtype=np.int32)  # child block out of range
+        dens = np.ones(2, np.float32)
+        bad.child, bad.density, bad.n_nodes, bad.n_leaves = child.ctypes.data, dens.ctypes.data, 3, 2
+        with pytest.raises(rt.RTError) as e:
+            rt.rt_create_grid(ctx, bad)
+        assert e.value.status == rt.RT_ERR_ARG
+        del keep
+    finally:
+        rt.rt_context_destroy(ctx)
