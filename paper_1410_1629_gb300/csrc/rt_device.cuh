@@ -43,7 +43,7 @@ __device__ __forceinline__ uint4 draw_block(unsigned long long pid, int lam, int
 __device__ __forceinline__ double u01(uint32_t r) { return ((double)r + 0.5) * 0x1p-32; }
 
 // ---------------------------------------------------------------- scattering
-constexpr float kInv4Pi = 0.0795774715459476679f;
+constexpr double kInv4PiD = 0.0795774715459476679;
 
 // Henyey-Greenstein phase function, normalised to a mean of 1 over the sphere.
 __device__ __forceinline__ float hg_phase(float g, float mu) {

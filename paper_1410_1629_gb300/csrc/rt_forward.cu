@@ -35,7 +35,7 @@ __device__ __forceinline__ void peel_all(const FwdParams& P, float3 x, float3 k,
   for (int q = 0; q < P.n_instr; ++q) {
     const DevInstr& I = P.instr[q];
     const float3 kobs = make_float3(I.kobs[0], I.kobs[1], I.kobs[2]);
-    const float w = scattered ? hg_phase(g, k.x * kobs.x + k.y * kobs.y + k.z * kobs.z) * kInv4Pi : kInv4Pi;
+    const float phase = scattered ? hg_phase(g, k.x * kobs.x + k.y * kobs.y + k.z * kobs.z) : 1.0f;
     float tau = 0.0f;
     const unsigned n = Walker<GRID>::walk(P, x, kobs, ref, [&](int c, float, float ds, const CellRef&) {
       tau = fmaf(kappa * __ldg(&P.density[c]), ds, tau);
@@ -43,7 +43,7 @@ __device__ __forceinline__ void peel_all(const FwdParams& P, float3 x, float3 k,
     });
     acc.crossings += n;
     acc.peeloffs += 1;
-    const double value = L * (double)w * exp(-(double)tau);
+    const double value = L * kInv4PiD * (double)phase * exp(-(double)tau);
     const float fx = (dot3(x, I.ex) + I.off_x) * I.sx;
     const float fy = (dot3(x, I.ey) + I.off_y) * I.sy;
     const size_t plane = (size_t)I.ny * I.nx;

@@ -85,7 +85,12 @@ def flip_corrected_images(gpu, ora, problem):
     for b in only_o:
         imgs[o["instr"][b]][o["lam"][b]].reshape(-1)[o["pixel"][b]] += o["value"][b]
     rel = np.abs(g["value"][ig] - o["value"][io]) / np.maximum(np.abs(o["value"][io]), 1e-300)
-    report = {"records": int(len(o)), "flips": int(flip.sum()), "gpu_only": int(len(only_g)),
+    worst = np.argsort(rel)[::-1][:3]
+    report = {"worst_records": [{"pid": int(o["pid"][io[w]]), "lam": int(o["lam"][io[w]]),
+                                 "event": int(o["event"][io[w]]), "instr": int(o["instr"][io[w]]),
+                                 "gpu": float(g["value"][ig[w]]), "oracle": float(o["value"][io[w]])}
+                                for w in worst if rel[w] > 1e-3],
+              "records": int(len(o)), "flips": int(flip.sum()), "gpu_only": int(len(only_g)),
               "oracle_only": int(len(only_o)), "record_rel_p999": float(np.quantile(rel, 0.999)) if len(rel) else 0.0,
               "record_rel_max": float(rel.max()) if len(rel) else 0.0}
     return imgs, report
@@ -93,15 +98,25 @@ def flip_corrected_images(gpu, ora, problem):
 
 def bin_check(gpu_vals, ora_vals, counts, min_count=1000, rtol=1e-4):
     mask = counts >= min_count
-    rel = np.abs(gpu_vals[mask] - ora_vals[mask]) / np.abs(ora_vals[mask])
+    diff = np.abs(gpu_vals[mask] - ora_vals[mask])
+    rel = np.where(diff == 0, 0.0, diff / np.maximum(np.abs(ora_vals[mask]), 1e-300))
     return {"bins": int(mask.sum()), "violations": int((rel > rtol).sum()),
             "max_rel": float(rel.max()) if rel.size else 0.0}
 
 
-def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_records=True):
+def block_sum(a, b):
+    """Sum over b x b pixel blocks of the last two axes."""
+    ny, nx = a.shape[-2:]
+    return a.reshape(a.shape[:-2] + (ny // b, b, nx // b, b)).sum(axis=(-3, -1))
+
+
+def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_records=True, block=8):
     rep = {}
     st_g, st_o = gpu["stats"], ora["stats"]
-    rep["totals_rel"] = (np.abs(st_g - st_o) / np.abs(st_o).clip(1e-300)).tolist()
+    # emitted, escaped and absorbed relative to themselves; the truncated
+    # remainder (a small fraction) relative to the emitted luminosity
+    scale = np.array([st_o[0], st_o[1], st_o[2], st_o[0]])
+    rep["totals_rel"] = (np.abs(st_g - st_o) / np.abs(scale).clip(1e-300)).tolist()
     img_tot_g = sum(im[0].sum() for im in gpu["images"])
     img_tot_o = sum(im[0].sum() for im in ora["images"])
     rep["image_total_rel"] = float(abs(img_tot_g - img_tot_o) / img_tot_o)
@@ -120,10 +135,16 @@ def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_rec
     for q, im in enumerate(imgs):
         raw = bin_check(gpu["images"][q][0], ora["images"][q][0], ora["image_counts"][q][0], min_count, rtol)
         cor = bin_check(im, ora["images"][q][0], ora["image_counts"][q][0], min_count, rtol)
-        rep["pixels"].append({"raw": raw, "corrected": cor})
+        entry = {"raw": raw, "corrected": cor}
+        ny, nx = im.shape[-2:]
+        if block and ny % block == 0 and nx % block == 0:
+            entry["blocks"] = bin_check(block_sum(im, block), block_sum(ora["images"][q][0], block),
+                                        block_sum(ora["image_counts"][q][0], block), min_count, rtol)
+        rep["pixels"].append(entry)
     rep["cells"] = bin_check(gpu["absorption"], ora["absorption"], ora["absorption_counts"], min_count, rtol)
     ok = (max(rep["totals_rel"]) <= tot_rtol and rep["image_total_rel"] <= tot_rtol
           and rep["absorption_total_rel"] <= tot_rtol and rep["cells"]["violations"] == 0
-          and all(p["corrected"]["violations"] == 0 for p in rep["pixels"]))
+          and all(p["corrected"]["violations"] == 0 for p in rep["pixels"])
+          and all(p.get("blocks", {"violations": 0})["violations"] == 0 for p in rep["pixels"]))
     rep["ok"] = bool(ok)
     return rep
