@@ -36,14 +36,18 @@ L2_FLUSH_BYTES = 256 << 20
 BYTES_PATH_CROSSING, BYTES_PEEL_CROSSING, BYTES_DEPOSIT = 20, 4, 16
 
 
-def workload():
+def workload(packets=None):
     from paper_1410_1629_gb300 import workloads as W
+    if packets:
+        return W.disk_galaxy(n_packets_total=int(packets))
     return W.disk_galaxy()
 
 
 def workload_config(prob, world):
-    return {"workload": "edge-on disk galaxy: 256^3 cartesian grid, 10 wavelengths 0.15-2.2 um, 1e8 packets/step "
-                        "(1e7 per wavelength) per GPU, 3 frames 512^2 at i=0/60/90 deg",
+    packets = prob.run.n_per_lambda * prob.n_lambda
+    return {"workload": f"edge-on disk galaxy: 256^3 cartesian grid, 10 wavelengths 0.15-2.2 um, {packets:.0e} "
+                        f"packets/step ({prob.run.n_per_lambda:.0e} per wavelength) per GPU, 3 frames 512^2 at "
+                        f"i=0/60/90 deg",
             "grid": "cartesian 256x256x256 float32", "n_lambda": prob.n_lambda,
             "packets_per_step_per_gpu": int(prob.run.n_per_lambda * prob.n_lambda),
             "detectors": "3 x 512x512 x 10 lambda, float64",
@@ -297,6 +301,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-step-seconds", type=float, default=8.0)
+    ap.add_argument("--packets", type=float, default=None,
+                    help="packets per step (default 1e8, the workload's size); smaller values are for profiling")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the forward kernel from an ncu capture (scaled)")
     args = ap.parse_args()
@@ -305,7 +311,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    prob = workload()
+    prob = workload(args.packets)
     if args.impl == "reference":
         run_reference(args, prob, world, rank)
         return

@@ -129,6 +129,16 @@ typedef struct {
   double value;
 } rt_record;
 
+/* Per-event state of one traced packet (event 0 = emission): position and
+ * direction after / before the event, interaction cell, weight after the
+ * event, optical depth of the forced path and the drawn tau*. */
+typedef struct {
+  int32_t event, reserved;
+  int64_t cell;
+  double x[3], k[3];
+  double L, tau_path, tau_star;
+} rt_trace_row;
+
 /* Launch options.  Zero-initialise and set what you need; rt_default_opts
  * fills the defaults (w_min 1e-4, max_events 1000, weight cut on, both
  * peel-offs on). */
@@ -140,10 +150,16 @@ typedef struct {
   int32_t peel_scatter;
   uint64_t n_norm;      /* packets per wavelength for the weight L_tot/n_norm; 0 = n_per_lambda */
   uint32_t model_id;    /* second Philox key word                                          */
-  int32_t block_size;   /* threads per block; 0 = library choice                           */
+  int32_t block_size;   /* reserved; set to 0                                               */
   rt_record* records;   /* device buffer for debug records, or NULL                        */
   int64_t records_capacity;
   uint64_t record_stride; /* record only packets whose id is a multiple of this (0, 1: all)  */
+  rt_trace_row* trace;  /* device buffer: per-event trace of packet trace_packet, or NULL    */
+  int64_t trace_capacity;
+  uint64_t trace_packet;
+  int32_t trace_lambda;
+  int32_t control_lanes; /* per-event work of a warp waits until this many of its lanes need it
+                            (1..32; 0 = library choice)                                    */
 } rt_launch_opts;
 
 /* Tallies since the last rt_reset_tallies. */

@@ -94,6 +94,8 @@ class OrOutput(ctypes.Structure):
                 ("records_n", ctypes.c_int64)]
 
 
+TRACE_DTYPE = np.dtype([("event", "<i4"), ("pad", "<i4"), ("cell", "<i8"), ("x", "<f8", 3), ("k", "<f8", 3),
+                        ("L", "<f8"), ("tau_path", "<f8"), ("tau_star", "<f8")])
 RECORD_DTYPE = np.dtype([("pid", "<u8"), ("lam", "<i4"), ("event", "<i4"), ("instr", "<i4"),
                          ("pad", "<i4"), ("pixel", "<i8"), ("value", "<f8")])
 
@@ -130,6 +132,9 @@ def lib():
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
             L.or_run.restype = ctypes.c_int32
             L.or_run.argtypes = [ctypes.POINTER(OrProblem), ctypes.POINTER(OrOpts), ctypes.POINTER(OrOutput)]
+            L.or_trace.restype = ctypes.c_int64
+            L.or_trace.argtypes = [ctypes.POINTER(OrProblem), ctypes.POINTER(OrOpts), ctypes.c_uint64,
+                                   ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64]
             L.or_vjp.restype = ctypes.c_int32
             L.or_vjp.argtypes = [ctypes.POINTER(OrProblem), ctypes.POINTER(OrOpts),
                                  ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
@@ -301,6 +306,16 @@ def vjp(problem, cells, n_per_lambda, adj_images=None, adj_absorption=None, firs
     if rc != 0:
         raise ValueError(f"or_vjp failed with status {rc}")
     return grad
+
+
+def trace(problem, pid, lam=0, seed=0, model_id=0, n_norm=1, w_min=1e-4, max_events=1000, weight_cut=True,
+          peel_emission=True, peel_scatter=True):
+    """Per-event state (position, direction, cell, weight, tau_path, tau*) of one packet."""
+    m = _Marshalled(problem)
+    o = _opts(1, 0, n_norm, seed, model_id, w_min, max_events, weight_cut, peel_emission, peel_scatter, 1)
+    rows = np.zeros(max_events + 2, dtype=TRACE_DTYPE)
+    n = lib().or_trace(ctypes.byref(m.problem), ctypes.byref(o), int(pid), int(lam), rows.ctypes.data, rows.size)
+    return rows[:min(n, rows.size)].copy()
 
 
 # ---------------------------------------------------------------- unit entry points

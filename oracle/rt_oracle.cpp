@@ -202,6 +202,14 @@ typedef struct {
   int32_t pad;
 } or_opts;
 
+// Per-event state of one traced packet (event 0 = emission).
+typedef struct {
+  int32_t event, pad;
+  int64_t cell;
+  double x[3], k[3];
+  double L, tau_path, tau_star;
+} or_trace_row;
+
 typedef struct {
   uint64_t pid;
   int32_t lam, event, instr, pad;
@@ -725,6 +733,11 @@ struct Transport {
   }
 
   uint64_t tally_crossings = 0, tally_peeloffs = 0, tally_events = 0;
+  std::vector<or_trace_row>* trace = nullptr;
+  void trace_row(int event, int64_t cell, const V3<T>& x, const V3d& k, const T& L, double tp, double ts) {
+    if (!trace) return;
+    trace->push_back({event, 0, cell, {val(x.x), val(x.y), val(x.z)}, {k.x, k.y, k.z}, val(L), tp, ts});
+  }
   T t_emitted = T(0.0), t_escaped = T(0.0), t_truncated = T(0.0);
 
   void run_packet(uint64_t pid, int lam) {
@@ -738,6 +751,7 @@ struct Transport {
     T L = T(L0);
     t_emitted = t_emitted + L;
     int64_t cell = -1;
+    trace_row(0, -1, x, k, L, 0.0, 0.0);
     if (O.peel_emission) peel(x, cell, lam, L, false, k, pid, 0);
     for (int j = 1;; ++j) {
       // (a) the forced path to the boundary
@@ -748,6 +762,7 @@ struct Transport {
         tau[i + 1] = tau[i] + T(kap) * rho(segs[i].cell) * (segs[i].s_out - segs[i].s_in);
       const T tau_path = tau[segs.size()];
       if (val(tau_path) <= 0.0) {
+        trace_row(j, -1, x, k, L, 0.0, 0.0);
         t_escaped = t_escaped + L;
         return;
       }
@@ -787,6 +802,7 @@ struct Transport {
       }
       // (d) scattered weight and peel-off
       L = T(alb) * L * one_minus_E;
+      trace_row(j, cell, x, k, L, val(tau_path), val(tau_star));
       tally_events += 1;
       if (O.peel_scatter) peel(x, cell, lam, L, true, k, pid, j);
       // (e) Henyey-Greenstein direction
@@ -959,6 +975,20 @@ int32_t or_run(const or_problem* prob, const or_opts* opts, or_output* out) {
     out->records_n = (int64_t)recs[0].size();
   }
   return 0;
+}
+
+// Per-event trace of one packet; returns the number of rows (<= cap written).
+int64_t or_trace(const or_problem* prob, const or_opts* opts, uint64_t pid, int32_t lam, or_trace_row* rows,
+                 int64_t cap) {
+  Problem P = make_problem(*prob);
+  ArrayTally T;
+  T.init(P, false, false);
+  std::vector<or_trace_row> tr;
+  Transport<double, ArrayTally> t(P, *opts, DensityOf<double>{&P.grid}, T);
+  t.trace = &tr;
+  t.run_packet(pid, lam);
+  for (int64_t i = 0; i < (int64_t)tr.size() && i < cap; ++i) rows[i] = tr[(size_t)i];
+  return (int64_t)tr.size();
 }
 
 // Vector-Jacobian product by forward-mode dual numbers, one seeded cell at a

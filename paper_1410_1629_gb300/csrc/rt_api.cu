@@ -67,6 +67,7 @@ struct rt_ctx_s {
   unsigned long long* d_work = nullptr;
   int* d_flags = nullptr;
   bool tables_dirty = true;
+  double emitted = 0.0;  // luminosity emitted since the last reset (host-side sum)
 };
 
 namespace {
@@ -126,6 +127,7 @@ rt_status zero_tallies(rt_ctx c, cudaStream_t s) {
   RT_CUDA(c, cudaMemsetAsync(c->d_stats, 0, 4 * sizeof(double), s));
   RT_CUDA(c, cudaMemsetAsync(c->d_counters, 0, 8 * sizeof(unsigned long long), s));
   RT_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), s));
+  c->emitted = 0.0;
   return RT_OK;
 }
 
@@ -352,6 +354,7 @@ rt_status rt_set_optics(rt_ctx c, int32_t grid_id, int32_t n_lambda, const doubl
   RT_CUDA(c, cudaMemset(c->d_absorption, 0, n_abs * sizeof(double)));
   RT_CUDA(c, cudaMemset(c->d_stats, 0, 4 * sizeof(double)));
   RT_CUDA(c, cudaMemset(c->d_counters, 0, 8 * sizeof(unsigned long long)));
+  c->emitted = 0.0;
   c->tables_dirty = true;
   return RT_OK;
 }
@@ -428,8 +431,8 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   if (opts) o = *opts;
   if (o.max_events < 1) return fail(c, RT_ERR_ARG, "rt_launch_packets: max_events must be >= 1");
   if (!(o.w_min >= 0 && o.w_min < 1)) return fail(c, RT_ERR_ARG, "rt_launch_packets: w_min must be in [0, 1)");
-  if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32))
-    return fail(c, RT_ERR_ARG, "rt_launch_packets: block_size must be a multiple of 32 in [32, 256]");
+  if (o.control_lanes < 0 || o.control_lanes > 32)
+    return fail(c, RT_ERR_ARG, "rt_launch_packets: control_lanes must be in [0, 32]");
   if (o.records && o.records_capacity < 0) return fail(c, RT_ERR_ARG, "rt_launch_packets: negative record capacity");
   for (int l = 0; l < c->n_lambda; ++l) {
     double tot = 0;
@@ -485,9 +488,20 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   p.records = o.records;
   p.records_cap = o.records ? o.records_capacity : 0;
   p.record_stride = o.record_stride;
+  p.trace = o.trace;
+  p.trace_cap = o.trace ? o.trace_capacity : 0;
+  p.trace_packet = o.trace_packet;
+  p.trace_lambda = o.trace_lambda;
+  p.control_min = o.control_lanes ? o.control_lanes : 8;
   p.flags = c->d_flags;
-  cudaError_t e = launch_forward(p, c->grid_kind, o.block_size, c->num_sms, s);
+  cudaError_t e = launch_forward(p, c->grid_kind, 0, c->num_sms, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "forward launch");
+  // every packet starts with L0 = L_tot / n_norm
+  for (int l = 0; l < c->n_lambda; ++l) {
+    double tot = 0.0;
+    for (auto& src : c->sources) tot += src.lum[l];
+    c->emitted += (double)n_per_lambda * (tot / (double)p.n_norm);
+  }
   return RT_OK;
 }
 
@@ -544,7 +558,7 @@ rt_status rt_read_stats(rt_ctx c, rt_stats* out) {
   RT_CUDA(c, cudaMemcpy(cn, c->d_counters, sizeof cn, cudaMemcpyDeviceToHost));
   RT_CUDA(c, cudaMemcpy(&flags, c->d_flags, sizeof flags, cudaMemcpyDeviceToHost));
   std::memset(out, 0, sizeof *out);
-  out->emitted = st[0]; out->escaped = st[1]; out->absorbed = st[2]; out->truncated = st[3];
+  out->emitted = c->emitted; out->escaped = st[1]; out->absorbed = st[2]; out->truncated = st[3];
   out->crossings = cn[0]; out->path_crossings = cn[5]; out->events = cn[1]; out->peeloffs = cn[2]; out->packets = cn[3]; out->records = cn[4];
   out->device_flags = flags;
   if (flags) return fail(c, RT_ERR_DEVICE_FLAG, "a kernel bounds check fired (flags 0x%x)", flags);

@@ -1,14 +1,27 @@
-// Forward transport kernel: emission, peel-off, forced scattering with
-// continuous absorption, Henyey-Greenstein scattering and termination for a
-// stream of photon packets (SKIRT paper, Sect. 1 and Sect. 2.2-2.4).
+// Forward transport kernel for cartesian grids: emission, peel-off, forced
+// scattering with continuous absorption, Henyey-Greenstein scattering and
+// termination for a stream of photon packets (SKIRT paper, Sect. 1 and
+// Sect. 2.2-2.4).
 //
-// Execution model: a persistent grid (a few blocks per SM); every warp takes
-// 32 consecutive packet indices from a global counter at a time, so a launch
-// adapts to the uneven cost of packets.  Packets are ordered wavelength-major,
-// so at any time the absorption tallies being updated are one wavelength's
-// slice.  Geometry, the walk and the phase function are FP32; the cumulative
-// optical depth of the forced path (which places the interaction), the packet
-// weight and every accumulator are FP64.
+// Execution model.  A persistent grid of warps; every lane carries one packet
+// through a small state machine.  The expensive part of the method is the
+// straight cell walk: per packet a peel-off walk per instrument at emission and
+// at every scattering, and two walks of the forced path per scattering (the
+// first accumulates the optical depth to the boundary and deposits absorption,
+// the second stops at the interaction).  The main loop advances every walking
+// lane by exactly one cell crossing per iteration, whichever of these walks it
+// is in, so the warp stays converged on the hot path.  The per-event work
+// (emission, forced-scattering inversion, weight update, deposits, the
+// Henyey-Greenstein draw, fetching the next packet) is deferred until enough
+// lanes of the warp need it and is then done for those lanes together;
+// packets are fetched with one atomic per warp.
+//
+// Precision.  Geometry, the walk and the phase function are FP32.  The
+// cumulative optical depth of the forced path is held as an unevaluated sum
+// of two FP32 numbers updated by an error-free two-sum (about 2^-46 relative),
+// bit-identical in both walks, so the interaction cell is always found; the
+// inversion remainder, E = exp(-tau), tau*, packet weights and every
+// accumulator are FP64.
 #include <cuda_runtime.h>
 
 #include "rt_device.cuh"
@@ -18,67 +31,182 @@ namespace rtk {
 
 namespace {
 
-struct Acc {
-  double emitted = 0.0, escaped = 0.0, absorbed = 0.0, truncated = 0.0;
-  unsigned long long crossings = 0, path_crossings = 0, events = 0, peeloffs = 0, packets = 0;
+constexpr int kBlock = 256;
+
+enum Phase : int {
+  kFetch = 0,      // needs a new packet
+  kPeelEmit = 1,   // peel-off walk at emission (instrument q)
+  kPath1 = 2,      // forced path, first walk
+  kPath2 = 3,      // forced path, second walk (stops at the interaction)
+  kPeelScat = 4,   // peel-off walk at a scattering (instrument q)
+  kExit = 5        // no packets left
 };
 
-__device__ __forceinline__ float dot3(float3 a, const float* b) { return a.x * b[0] + a.y * b[1] + a.z * b[2]; }
+// Error-free transformation: a + b = s + e exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
 
-// Peel-off towards every instrument from x (in cell `ref`) with weight
-// L * factor * exp(-tau(x -> observer)); factor = 1/(4 pi) for emission and
-// Phi(k . k_obs)/(4 pi) for scattering.
-template <int GRID>
-__device__ __forceinline__ void peel_all(const FwdParams& P, float3 x, float3 k, const CellRef& ref, int lam,
-                                         float kappa, float g, double L, bool scattered,
-                                         unsigned long long pid, int event, Acc& acc) {
-  for (int q = 0; q < P.n_instr; ++q) {
-    const DevInstr& I = P.instr[q];
-    const float3 kobs = make_float3(I.kobs[0], I.kobs[1], I.kobs[2]);
-    const float phase = scattered ? hg_phase(g, k.x * kobs.x + k.y * kobs.y + k.z * kobs.z) : 1.0f;
-    float tau = 0.0f;
-    const unsigned n = Walker<GRID>::walk(P, x, kobs, ref, [&](int c, float, float ds, const CellRef&) {
-      tau = fmaf(kappa * __ldg(&P.density[c]), ds, tau);
-      return true;
-    });
-    acc.crossings += n;
-    acc.peeloffs += 1;
-    const double value = L * kInv4PiD * (double)phase * exp(-(double)tau);
-    const float fx = (dot3(x, I.ex) + I.off_x) * I.sx;
-    const float fy = (dot3(x, I.ey) + I.off_y) * I.sy;
-    const size_t plane = (size_t)I.ny * I.nx;
-    const int ch = scattered ? 2 : 1;
-    if (!I.bilinear) {
-      const float fix = floorf(fx), fiy = floorf(fy);
-      if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) continue;
-      const int ix = (int)fix, iy = (int)fiy;
-      const size_t pix = (size_t)iy * I.nx + ix;
-      atomicAdd(&I.image[(size_t)lam * plane + pix], value);
-      if (I.channels == 3) atomicAdd(&I.image[((size_t)ch * P.n_lambda + lam) * plane + pix], value);
-      if (P.records && (P.record_stride <= 1 || pid % P.record_stride == 0)) {
-        const unsigned long long slot = atomicAdd(&P.counters[4], 1ull);
-        if ((long long)slot < P.records_cap) {
-          rt_record r;
-          r.packet = pid; r.lambda = lam; r.event = event; r.instrument = q; r.reserved = 0;
-          r.pixel = (int64_t)pix; r.value = value;
-          P.records[slot] = r;
-        }
+__device__ __forceinline__ float inv_or_zero(float d) { return d != 0.0f ? 1.0f / d : 0.0f; }
+
+// ---------------------------------------------------------------- walk state
+// Cartesian walk: current cell indices, entry parameter t of the current
+// segment and the parameters of the next plane on each axis.  The ray is
+// (origin x of the lane, inverse direction id; id_a = 0 marks d_a = 0).
+struct WalkCart {
+  int ix, iy, iz, cell;
+  float t, tx, ty, tz;
+};
+
+__device__ __forceinline__ float plane_t(const FwdParams& P, int a, int i, float xa, float ida) {
+  return (fmaf((float)i, P.d[a], P.lo[a]) - xa) * ida;
+}
+
+// Start a cartesian walk from x along d.  known: x lies in cell (ci, cj, ck);
+// otherwise locate x or find the entry point.  Returns false if the ray
+// misses the grid.
+__device__ __forceinline__ bool walk_init(const FwdParams& P, float3 x, float3 d, float3 id, bool known, int ci,
+                                          int cj, int ck, WalkCart& w) {
+  w.t = 0.0f;
+  if (known) {
+    w.ix = ci; w.iy = cj; w.iz = ck;
+  } else {
+    int entry = -1;
+    float3 p = x;
+    if (!inside_box(P, x)) {
+      const float3 ik = make_float3(id.x != 0.0f ? id.x : RT_INF, id.y != 0.0f ? id.y : RT_INF,
+                                    id.z != 0.0f ? id.z : RT_INF);
+      if (!ray_box_entry(P, x, d, ik, w.t, entry)) return false;
+      p = make_float3(fmaf(w.t, d.x, x.x), fmaf(w.t, d.y, x.y), fmaf(w.t, d.z, x.z));
+    }
+    w.ix = min(max(__float2int_rd((p.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
+    w.iy = min(max(__float2int_rd((p.y - P.lo[1]) * P.inv_d[1]), 0), P.ny - 1);
+    w.iz = min(max(__float2int_rd((p.z - P.lo[2]) * P.inv_d[2]), 0), P.nz - 1);
+    if (entry == 0) w.ix = d.x > 0.0f ? 0 : P.nx - 1;
+    if (entry == 1) w.iy = d.y > 0.0f ? 0 : P.ny - 1;
+    if (entry == 2) w.iz = d.z > 0.0f ? 0 : P.nz - 1;
+  }
+  w.tx = id.x != 0.0f ? plane_t(P, 0, w.ix + (id.x > 0.0f), x.x, id.x) : RT_INF;
+  w.ty = id.y != 0.0f ? plane_t(P, 1, w.iy + (id.y > 0.0f), x.y, id.y) : RT_INF;
+  w.tz = id.z != 0.0f ? plane_t(P, 2, w.iz + (id.z > 0.0f), x.z, id.z) : RT_INF;
+  w.cell = w.ix + P.nx * (w.iy + P.ny * w.iz);
+  return true;
+}
+
+// Move to the next cell through face `axis`; false when the ray leaves the grid.
+__device__ __forceinline__ bool walk_advance(const FwdParams& P, float3 x, float3 id, int axis, WalkCart& w) {
+  if (axis == 0) {
+    const int s = id.x > 0.0f ? 1 : -1;
+    w.ix += s;
+    if ((unsigned)w.ix >= (unsigned)P.nx) return false;
+    w.cell += s;
+    w.tx = plane_t(P, 0, w.ix + (s > 0), x.x, id.x);
+  } else if (axis == 1) {
+    const int s = id.y > 0.0f ? 1 : -1;
+    w.iy += s;
+    if ((unsigned)w.iy >= (unsigned)P.ny) return false;
+    w.cell += s * P.nx;
+    w.ty = plane_t(P, 1, w.iy + (s > 0), x.y, id.y);
+  } else {
+    const int s = id.z > 0.0f ? 1 : -1;
+    w.iz += s;
+    if ((unsigned)w.iz >= (unsigned)P.nz) return false;
+    w.cell += s * P.nx * P.ny;
+    w.tz = plane_t(P, 2, w.iz + (s > 0), x.z, id.z);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------- lane state
+struct Lane {
+  unsigned long long pid;
+  int lam, event, phase, q;
+  double L, L_cut;      // weight, termination threshold w_min * L0
+  float kappa;          // extinction per unit density at this wavelength
+  float u_mu, u_phi;    // the event's Henyey-Greenstein uniforms
+  float3 x, k;          // position, direction of travel
+  int ci, cj, ck;       // cell of x (valid when has_cell)
+  bool has_cell;
+  bool walking;
+  float3 id;            // inverse direction of the current walk
+  WalkCart w;
+  float th, tl;         // optical depth of the current walk (pair on forced paths)
+  float aux0, aux1;     // path 1: deposit weight; path 2: tau* as a float pair
+};
+
+struct BlockTally {
+  double escaped, absorbed, truncated;
+  unsigned long long events, peeloffs, packets, crossings, path_crossings;
+};
+
+__device__ __forceinline__ void trace_row(const FwdParams& P, const Lane& s, int event, int cell, double L,
+                                          double tau_path, double tau_star) {
+  if (!P.trace || s.pid != P.trace_packet || s.lam != P.trace_lambda || event >= P.trace_cap) return;
+  rt_trace_row r;
+  r.event = event; r.reserved = 0; r.cell = cell;
+  r.x[0] = s.x.x; r.x[1] = s.x.y; r.x[2] = s.x.z;
+  r.k[0] = s.k.x; r.k[1] = s.k.y; r.k[2] = s.k.z;
+  r.L = L; r.tau_path = tau_path; r.tau_star = tau_star;
+  P.trace[event] = r;
+}
+
+// Start a walk from the lane's position along d.
+__device__ __forceinline__ void start_walk(const FwdParams& P, Lane& s, float3 d) {
+  s.id = make_float3(inv_or_zero(d.x), inv_or_zero(d.y), inv_or_zero(d.z));
+  s.th = 0.0f;
+  s.tl = 0.0f;
+  s.walking = walk_init(P, s.x, d, s.id, s.has_cell, s.ci, s.cj, s.ck, s.w);
+}
+
+__device__ __forceinline__ float3 instr_dir(const DevInstr& I) { return make_float3(I.kobs[0], I.kobs[1], I.kobs[2]); }
+
+// Deposit a finished peel-off into instrument q's image(s).
+__device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane& s, bool scattered) {
+  const DevInstr& I = P.instr[s.q];
+  float phase = 1.0f;
+  if (scattered) {
+    const float g = P.lam[s.lam].g;
+    phase = hg_phase(g, s.k.x * I.kobs[0] + s.k.y * I.kobs[1] + s.k.z * I.kobs[2]);
+  }
+  const float tau = s.th;
+  const double value = tau < 80.0f ? s.L * kInv4PiD * (double)(phase * expf(-tau))
+                                   : s.L * kInv4PiD * (double)phase * exp(-(double)tau);
+  const float fx = (s.x.x * I.ex[0] + s.x.y * I.ex[1] + s.x.z * I.ex[2] + I.off_x) * I.sx;
+  const float fy = (s.x.x * I.ey[0] + s.x.y * I.ey[1] + s.x.z * I.ey[2] + I.off_y) * I.sy;
+  const size_t plane = (size_t)I.ny * I.nx;
+  const int ch = scattered ? 2 : 1;
+  if (!I.bilinear) {
+    const float fix = floorf(fx), fiy = floorf(fy);
+    if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) return;
+    const size_t pix = (size_t)(int)fiy * I.nx + (int)fix;
+    atomicAdd(&I.image[(size_t)s.lam * plane + pix], value);
+    if (I.channels == 3) atomicAdd(&I.image[((size_t)ch * P.n_lambda + s.lam) * plane + pix], value);
+    if (P.records && (P.record_stride <= 1 || s.pid % P.record_stride == 0)) {
+      const unsigned long long slot = atomicAdd(&P.counters[4], 1ull);
+      if ((long long)slot < P.records_cap) {
+        rt_record r;
+        r.packet = s.pid; r.lambda = s.lam; r.event = scattered ? s.event : 0; r.instrument = s.q;
+        r.reserved = 0; r.pixel = (int64_t)pix; r.value = value;
+        P.records[slot] = r;
       }
-    } else {
-      const float gx = fx - 0.5f, gy = fy - 0.5f;
-      const float x0 = floorf(gx), y0 = floorf(gy);
-      const float tx = gx - x0, ty = gy - y0;
+    }
+  } else {
+    const float gx = fx - 0.5f, gy = fy - 0.5f;
+    const float x0 = floorf(gx), y0 = floorf(gy);
+    const float tx = gx - x0, ty = gy - y0;
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
+    for (int dy = 0; dy < 2; ++dy) {
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-          const float fix = x0 + dx, fiy = y0 + dy;
-          if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) continue;
-          const double v = value * (double)((dx ? tx : 1.0f - tx) * (dy ? ty : 1.0f - ty));
-          const size_t pix = (size_t)(int)fiy * I.nx + (int)fix;
-          atomicAdd(&I.image[(size_t)lam * plane + pix], v);
-          if (I.channels == 3) atomicAdd(&I.image[((size_t)ch * P.n_lambda + lam) * plane + pix], v);
-        }
+      for (int dx = 0; dx < 2; ++dx) {
+        const float fix = x0 + dx, fiy = y0 + dy;
+        if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) continue;
+        const double v = value * (double)((dx ? tx : 1.0f - tx) * (dy ? ty : 1.0f - ty));
+        const size_t pix = (size_t)(int)fiy * I.nx + (int)fix;
+        atomicAdd(&I.image[(size_t)s.lam * plane + pix], v);
+        if (I.channels == 3) atomicAdd(&I.image[((size_t)ch * P.n_lambda + s.lam) * plane + pix], v);
       }
     }
   }
@@ -86,16 +214,16 @@ __device__ __forceinline__ void peel_all(const FwdParams& P, float3 x, float3 k,
 
 // Emission (Sect. 3.4): source component by luminosity, position from its
 // geometry (FP64, rounded to FP32), isotropic direction.
-__device__ __forceinline__ void emit(const FwdParams& P, unsigned long long pid, int lam, float3& x, float3& k) {
-  const uint4 r0 = draw_block(pid, lam, 0, 0, P.seed, P.model);
-  const uint4 r1 = draw_block(pid, lam, 0, 1, P.seed, P.model);
+__device__ __forceinline__ void emit(const FwdParams& P, Lane& s) {
+  const uint4 r0 = draw_block(s.pid, s.lam, 0, 0, P.seed, P.model);
+  const uint4 r1 = draw_block(s.pid, s.lam, 0, 1, P.seed, P.model);
   const double u0 = u01(r0.x), u1 = u01(r0.y), u2 = u01(r0.z), u3 = u01(r0.w);
   const double u4 = u01(r1.x), u5 = u01(r1.y), u6 = u01(r1.z), u7 = u01(r1.w);
-  int s = P.n_sources - 1;
+  int src = P.n_sources - 1;
   for (int i = 0; i < P.n_sources; ++i) {
-    if (u0 < P.src_cum[lam * P.n_sources + i]) { s = i; break; }
+    if (u0 < P.src_cum[s.lam * P.n_sources + i]) { src = i; break; }
   }
-  const DevSource S = P.src[s];
+  const DevSource S = P.src[src];
   double px = S.center[0], py = S.center[1], pz = S.center[2];
   if (S.kind == RT_SOURCE_EXPDISK) {
     const double R = -S.scale_r * log(u1 * u2);
@@ -111,169 +239,262 @@ __device__ __forceinline__ void emit(const FwdParams& P, unsigned long long pid,
     sincospi(2.0 * u3, &sp, &cp);
     px += r * st * cp; py += r * st * sp; pz += r * ct;
   }
-  x = make_float3((float)px, (float)py, (float)pz);
+  s.x = make_float3((float)px, (float)py, (float)pz);
   const float mu = (float)(2.0 * u6 - 1.0);
   const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
   float sp, cp;
   sincospif((float)(2.0 * u7), &sp, &cp);
-  k = make_float3(st * cp, st * sp, mu);
+  s.k = make_float3(st * cp, st * sp, mu);
 }
 
-template <int GRID>
-__device__ void run_packet(const FwdParams& P, unsigned long long pid, int lam, Acc& acc) {
-  const DevLambda LP = P.lam[lam];
-  const float kappa = LP.kappa, g = LP.g;
-  const double albedo = LP.albedo;
-  const double L0 = LP.lum_total / (double)P.n_norm;
-  float3 x, k;
-  emit(P, pid, lam, x, k);
-  double L = L0;
-  acc.emitted += L0;
-  acc.packets += 1;
-  CellRef cell;
-  cell.cell = -1;
-  if (P.peel_emission) peel_all<GRID>(P, x, k, cell, lam, kappa, g, L, false, pid, 0, acc);
-  double* __restrict__ absorb = P.absorption + (size_t)lam * P.n_cells;
-  for (int j = 1;; ++j) {
-    // forced path, first pass: optical depth to the boundary and continuous absorption
-    const float wabs = (float)((1.0 - albedo) * L);
-    double tau = 0.0;
-    float tauf = 0.0f;
-    const unsigned n = Walker<GRID>::walk(P, x, k, cell, [&](int c, float, float ds, const CellRef&) {
-      const float dt = kappa * __ldg(&P.density[c]) * ds;
-      if (dt > 0.0f) {
-        const float dep = wabs * __expf(-tauf) * -expm1f(-dt);
-        atomicAdd(&absorb[c], (double)dep);
-      }
-      tauf += dt;
-      tau += (double)dt;
-      return true;
-    });
-    acc.crossings += n;
-    acc.path_crossings += n;
-    if (!(tau > 0.0)) {
-      acc.escaped += L;
-      return;
-    }
-    const double E = exp(-tau);
-    const double one_minus_E = -expm1(-tau);
-    acc.escaped += L * E;
-    acc.absorbed += (1.0 - albedo) * L * one_minus_E;
-    // forced scattering: invert the cumulative optical depth (FP64)
-    const uint4 r = draw_block(pid, lam, j, 0, P.seed, P.model);
-    const double tau_star = -log1p(-u01(r.x) * one_minus_E);
-    double tau2 = 0.0;
-    bool found = false;
-    float s_star = 0.0f, last_out = 0.0f;
-    CellRef hit, last;
-    hit.cell = -1;
-    last.cell = -1;
-    Walker<GRID>::walk(P, x, k, cell, [&](int c, float t_in, float ds, const CellRef& ref) {
-      const float kr = kappa * __ldg(&P.density[c]);
-      const float dt = kr * ds;
-      const double t_next = tau2 + (double)dt;
-      if (t_next > tau2) { last = ref; last_out = t_in + ds; }
-      if (t_next > tau_star) {
-        hit = ref;
-        s_star = t_in + (float)(tau_star - tau2) / kr;
-        found = true;
-        return false;
-      }
-      tau2 = t_next;
-      return true;
-    });
-    if (!found) { hit = last; s_star = last_out; }
-    if (hit.cell < 0) {  // cannot happen with tau > 0; keep the packet well defined
-      acc.truncated += L;
-      return;
-    }
-    x = make_float3(fmaf(s_star, k.x, x.x), fmaf(s_star, k.y, x.y), fmaf(s_star, k.z, x.z));
-    {
-      float lo[3], hi[3];
-      Walker<GRID>::box(P, hit, lo, hi);
-      x.x = fminf(fmaxf(x.x, lo[0]), hi[0]);
-      x.y = fminf(fmaxf(x.y, lo[1]), hi[1]);
-      x.z = fminf(fmaxf(x.z, lo[2]), hi[2]);
-    }
-    cell = hit;
-    L = albedo * L * one_minus_E;
-    acc.events += 1;
-    if (P.peel_scatter) peel_all<GRID>(P, x, k, cell, lam, kappa, g, L, true, pid, j, acc);
-    // Henyey-Greenstein direction
-    const float mu = hg_sample(g, (float)u01(r.y));
-    float sp, cp;
-    sincospif((float)(2.0 * u01(r.z)), &sp, &cp);
-    k = rotate_dir(k, mu, sp, cp);
-    if ((P.weight_cut && L < P.w_min * L0) || j >= P.max_events) {
-      acc.truncated += L;
-      return;
-    }
+__device__ __forceinline__ void start_path(const FwdParams& P, Lane& s) {
+  s.phase = kPath1;
+  start_walk(P, s, s.k);
+  s.aux0 = (float)((1.0 - P.lam[s.lam].albedo) * s.L);
+}
+
+// After the scattering peel-offs: new direction, then terminate or start the
+// next forced path.
+__device__ __forceinline__ void after_scattering(const FwdParams& P, Lane& s, BlockTally* bt) {
+  const float g = P.lam[s.lam].g;
+  const float mu = hg_sample(g, s.u_mu);
+  float sp, cp;
+  sincospif(2.0f * s.u_phi, &sp, &cp);
+  s.k = rotate_dir(s.k, mu, sp, cp);
+  if ((P.weight_cut && s.L < s.L_cut) || s.event >= P.max_events) {
+    atomicAdd(&bt->truncated, s.L);
+    s.phase = kFetch;
+    return;
   }
+  s.event += 1;
+  start_path(P, s);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-template <int GRID>
-__global__ void __launch_bounds__(256) k_forward(const FwdParams P) {
-  const int lane = threadIdx.x & 31;
-  Acc acc;
+// Per-event work for a lane whose walk has finished, or that needs a packet
+// (then `w` is its packet index).  Loops until the lane walks again, waits
+// for a packet, or has no work left.
+__device__ void control(const FwdParams& P, Lane& s, unsigned long long w, BlockTally* bt) {
   while (true) {
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(P.work_counter, 32ull);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= P.n_total) break;
-    const unsigned long long w = base + lane;
-    if (w < P.n_total) {
-      const int lam = (int)(w / P.n_per_lambda);
-      const unsigned long long pid = P.first_id + (w - (unsigned long long)lam * P.n_per_lambda);
-      run_packet<GRID>(P, pid, lam, acc);
+    switch (s.phase) {
+      case kFetch: {
+        if (w >= P.n_total) { s.phase = kExit; return; }
+        s.lam = (int)(w / P.n_per_lambda);
+        s.pid = P.first_id + (w - (unsigned long long)s.lam * P.n_per_lambda);
+        w = ~0ull;
+        const DevLambda LP = P.lam[s.lam];
+        const double L0 = LP.lum_total / (double)P.n_norm;
+        s.kappa = LP.kappa;
+        s.L = L0;
+        s.L_cut = P.w_min * L0;
+        s.event = 0;
+        s.has_cell = false;
+        emit(P, s);
+        atomicAdd(&bt->packets, 1ull);
+        trace_row(P, s, 0, -1, L0, 0.0, 0.0);
+        if (P.peel_emission && P.n_instr > 0) {
+          s.phase = kPeelEmit;
+          s.q = 0;
+          start_walk(P, s, instr_dir(P.instr[0]));
+        } else {
+          s.event = 1;
+          start_path(P, s);
+        }
+        break;
+      }
+      case kPeelEmit:
+      case kPeelScat: {
+        const bool scattered = s.phase == kPeelScat;
+        peel_deposit(P, s, scattered);
+        atomicAdd(&bt->peeloffs, 1ull);
+        s.q += 1;
+        if (s.q < P.n_instr) {
+          start_walk(P, s, instr_dir(P.instr[s.q]));
+        } else if (!scattered) {
+          s.event = 1;
+          start_path(P, s);
+        } else {
+          after_scattering(P, s, bt);
+        }
+        break;
+      }
+      case kPath1: {
+        const double tau = (double)s.th + (double)s.tl;
+        if (!(tau > 0.0)) {
+          trace_row(P, s, s.event, -1, s.L, 0.0, 0.0);
+          atomicAdd(&bt->escaped, s.L);
+          s.phase = kFetch;
+          return;
+        }
+        const double albedo = P.lam[s.lam].albedo;
+        const double E = exp(-tau);
+        const double one_minus_E = -expm1(-tau);
+        atomicAdd(&bt->escaped, s.L * E);
+        atomicAdd(&bt->absorbed, (1.0 - albedo) * s.L * one_minus_E);
+        const uint4 r = draw_block(s.pid, s.lam, s.event, 0, P.seed, P.model);
+        const double tau_star = -log1p(-u01(r.x) * one_minus_E);
+        s.u_mu = (float)u01(r.y);
+        s.u_phi = (float)u01(r.z);
+        s.aux0 = (float)tau_star;
+        s.aux1 = (float)(tau_star - (double)s.aux0);
+        s.L = albedo * s.L * one_minus_E;  // weight after the scattering
+        s.phase = kPath2;
+        start_walk(P, s, s.k);
+        break;
+      }
+      case kPath2: {
+        // the walk stopped in the interaction cell; w.t holds s*
+        const float s_star = s.w.t;
+        float3 x = make_float3(fmaf(s_star, s.k.x, s.x.x), fmaf(s_star, s.k.y, s.x.y), fmaf(s_star, s.k.z, s.x.z));
+        const float lo0 = fmaf((float)s.w.ix, P.d[0], P.lo[0]), hi0 = fmaf((float)(s.w.ix + 1), P.d[0], P.lo[0]);
+        const float lo1 = fmaf((float)s.w.iy, P.d[1], P.lo[1]), hi1 = fmaf((float)(s.w.iy + 1), P.d[1], P.lo[1]);
+        const float lo2 = fmaf((float)s.w.iz, P.d[2], P.lo[2]), hi2 = fmaf((float)(s.w.iz + 1), P.d[2], P.lo[2]);
+        x.x = fminf(fmaxf(x.x, lo0), hi0);
+        x.y = fminf(fmaxf(x.y, lo1), hi1);
+        x.z = fminf(fmaxf(x.z, lo2), hi2);
+        s.x = x;
+        s.ci = s.w.ix; s.cj = s.w.iy; s.ck = s.w.iz;
+        s.has_cell = true;
+        atomicAdd(&bt->events, 1ull);
+        trace_row(P, s, s.event, s.w.cell, s.L, 0.0, (double)s.aux0 + (double)s.aux1);
+        if (P.peel_scatter && P.n_instr > 0) {
+          s.phase = kPeelScat;
+          s.q = 0;
+          start_walk(P, s, instr_dir(P.instr[0]));
+        } else {
+          after_scattering(P, s, bt);
+        }
+        break;
+      }
+      default:
+        return;
     }
-    __syncwarp();
+    if (s.phase == kFetch || s.phase == kExit) return;
+    if (s.walking) return;
   }
-  const double s0 = warp_sum(acc.emitted), s1 = warp_sum(acc.escaped), s2 = warp_sum(acc.absorbed),
-               s3 = warp_sum(acc.truncated);
-  const unsigned long long c0 = warp_sum(acc.crossings), c1 = warp_sum(acc.events), c2 = warp_sum(acc.peeloffs),
-                           c3 = warp_sum(acc.packets), c4 = warp_sum(acc.path_crossings);
-  if (lane == 0) {
-    atomicAdd(&P.stats[0], s0); atomicAdd(&P.stats[1], s1);
-    atomicAdd(&P.stats[2], s2); atomicAdd(&P.stats[3], s3);
-    atomicAdd(&P.counters[0], c0); atomicAdd(&P.counters[1], c1);
-    atomicAdd(&P.counters[2], c2); atomicAdd(&P.counters[3], c3);
-    atomicAdd(&P.counters[5], c4);
+}
+
+// One cell crossing of the lane's current walk.
+__device__ __forceinline__ void walk_step(const FwdParams& P, Lane& s, unsigned& n_path, unsigned& n_peel) {
+  WalkCart& w = s.w;
+  float te = w.tx;
+  int axis = 0;
+  if (w.ty < te) { te = w.ty; axis = 1; }
+  if (w.tz < te) { te = w.tz; axis = 2; }
+  const float texit = fmaxf(te, w.t);
+  const float ds = texit - w.t;
+  const float kr = s.kappa * __ldg(&P.density[w.cell]);
+  const float dt = kr * ds;
+  if (s.phase == kPath2) {
+    float nh, e;
+    two_sum(s.th, dt, nh, e);
+    const float nl = s.tl + e;
+    if ((nh - s.aux0) + (nl - s.aux1) > 0.0f) {
+      // interaction in this cell: s* = t_in + (tau* - tau_before) / (kappa rho)
+      const double rem = (((double)s.aux0 - (double)s.th) + (double)s.aux1) - (double)s.tl;
+      w.t = w.t + (float)rem / kr;
+      s.walking = false;
+      return;
+    }
+    s.th = nh;
+    s.tl = nl;
+  } else if (s.phase == kPath1) {
+    ++n_path;
+    if (dt > 0.0f) {
+      const float dep = s.aux0 * __expf(-s.th) * -expm1f(-dt);
+      atomicAdd(&P.absorption[(size_t)s.lam * P.n_cells + w.cell], (double)dep);
+    }
+    float nh, e;
+    two_sum(s.th, dt, nh, e);
+    s.th = nh;
+    s.tl += e;
+  } else {
+    ++n_peel;
+    s.th += dt;
+  }
+  w.t = texit;
+  if (!walk_advance(P, s.x, s.id, axis, w)) {
+    s.walking = false;
+    if (s.phase == kPath2) {
+      // not reachable: the pair sums of both walks are identical and tau* is
+      // below the path's optical depth; keep the packet at the path's end
+      atomicOr(P.flags, kFlagNoInteraction);
+      w.ix = min(max(w.ix, 0), P.nx - 1);
+      w.iy = min(max(w.iy, 0), P.ny - 1);
+      w.iz = min(max(w.iz, 0), P.nz - 1);
+      w.cell = w.ix + P.nx * (w.iy + P.ny * w.iz);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_forward_cartesian(const FwdParams P) {
+  __shared__ BlockTally bt;
+  if (threadIdx.x == 0) {
+    bt.escaped = bt.absorbed = bt.truncated = 0.0;
+    bt.events = bt.peeloffs = bt.packets = bt.crossings = bt.path_crossings = 0ull;
+  }
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  Lane s;
+  s.phase = kFetch;
+  s.walking = false;
+  unsigned n_path = 0, n_peel = 0;
+  while (true) {
+    const bool idle = !s.walking && s.phase != kExit;
+    const unsigned need = __ballot_sync(0xffffffffu, idle);
+    const unsigned walkers = __ballot_sync(0xffffffffu, s.walking);
+    if (need == 0u && walkers == 0u) break;
+    if (walkers == 0u || __popc(need) >= P.control_min) {
+      // packets for every lane that needs one: one atomic per warp
+      const unsigned fetch = __ballot_sync(0xffffffffu, idle && s.phase == kFetch);
+      unsigned long long w = ~0ull;
+      if (fetch) {
+        unsigned long long base = 0;
+        const int leader = __ffs(fetch) - 1;
+        if ((int)lane == leader) base = atomicAdd(P.work_counter, (unsigned long long)__popc(fetch));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (idle && s.phase == kFetch) w = base + __popc(fetch & lt_mask);
+      }
+      if (idle) control(P, s, w, &bt);
+      if ((n_path | n_peel) & 0xC0000000u) {  // keep the 32-bit lane counters far from overflow
+        atomicAdd(&bt.crossings, (unsigned long long)n_path + n_peel);
+        atomicAdd(&bt.path_crossings, (unsigned long long)n_path);
+        n_path = n_peel = 0;
+      }
+    }
+    if (s.walking) walk_step(P, s, n_path, n_peel);
+  }
+  atomicAdd(&bt.crossings, (unsigned long long)n_path + n_peel);
+  atomicAdd(&bt.path_crossings, (unsigned long long)n_path);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&P.stats[1], bt.escaped);
+    atomicAdd(&P.stats[2], bt.absorbed);
+    atomicAdd(&P.stats[3], bt.truncated);
+    atomicAdd(&P.counters[0], bt.crossings);
+    atomicAdd(&P.counters[1], bt.events);
+    atomicAdd(&P.counters[2], bt.peeloffs);
+    atomicAdd(&P.counters[3], bt.packets);
+    atomicAdd(&P.counters[5], bt.path_crossings);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_forward(const FwdParams& p, int grid_kind, int block_size, int num_sms, cudaStream_t stream) {
-  if (block_size <= 0) block_size = 256;
+  (void)block_size;
+  if (grid_kind != RT_GRID_CARTESIAN) return launch_forward_octree(p, num_sms, stream);
   cudaError_t e = cudaMemsetAsync(p.work_counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  if (grid_kind == RT_GRID_OCTREE) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward<RT_GRID_OCTREE>, block_size, 0);
-  } else {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward<RT_GRID_CARTESIAN>, block_size, 0);
-  }
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward_cartesian, kBlock, 0);
   if (e != cudaSuccess) return e;
   per_sm = per_sm < 1 ? 1 : per_sm;
-  unsigned long long warps_needed = (p.n_total + 31) / 32;
   unsigned long long blocks = (unsigned long long)num_sms * per_sm;
-  const unsigned long long max_useful = (warps_needed * 32 + block_size - 1) / block_size;
-  if (blocks > max_useful) blocks = max_useful;
+  const unsigned long long useful = (p.n_total + kBlock - 1) / kBlock;
+  if (blocks > useful) blocks = useful;
   if (blocks < 1) blocks = 1;
-  if (grid_kind == RT_GRID_OCTREE) {
-    k_forward<RT_GRID_OCTREE><<<(unsigned)blocks, block_size, 0, stream>>>(p);
-  } else {
-    k_forward<RT_GRID_CARTESIAN><<<(unsigned)blocks, block_size, 0, stream>>>(p);
-  }
+  k_forward_cartesian<<<(unsigned)blocks, kBlock, 0, stream>>>(p);
   return cudaGetLastError();
 }
 

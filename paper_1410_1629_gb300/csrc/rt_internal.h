@@ -72,10 +72,15 @@ struct FwdParams {
   rt_record* records;
   long long records_cap;
   unsigned long long record_stride;
+  rt_trace_row* trace;
+  long long trace_cap;
+  unsigned long long trace_packet;
+  int trace_lambda;
+  int control_min;  // lanes that must wait for per-event work before a warp runs it
   int* flags;
 };
 
-enum DeviceFlag : int { kFlagCellRange = 1, kFlagOctreeDepth = 2, kFlagWalkSteps = 4 };
+enum DeviceFlag : int { kFlagCellRange = 1, kFlagOctreeDepth = 2, kFlagWalkSteps = 4, kFlagNoInteraction = 8 };
 // Upper bound on the cells one straight octree walk may visit before the
 // kernel flags an error and stops the walk (3 * 2^depth covers any ray for
 // the depths used; this is a safety net, not a tuning knob).
@@ -83,5 +88,6 @@ constexpr unsigned kMaxWalkSteps = 1u << 22;
 
 // Launchers (rt_forward.cu).
 cudaError_t launch_forward(const FwdParams& p, int grid_kind, int block_size, int num_sms, cudaStream_t stream);
+cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t stream);
 
 }  // namespace rtk

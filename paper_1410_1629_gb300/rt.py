@@ -63,11 +63,23 @@ RECORD_DTYPE = np.dtype([("pid", "<u8"), ("lam", "<i4"), ("event", "<i4"), ("ins
                          ("pad", "<i4"), ("pixel", "<i8"), ("value", "<f8")])
 
 
+class rt_trace_row(ctypes.Structure):
+    _fields_ = [("event", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cell", ctypes.c_int64),
+                ("x", ctypes.c_double * 3), ("k", ctypes.c_double * 3), ("L", ctypes.c_double),
+                ("tau_path", ctypes.c_double), ("tau_star", ctypes.c_double)]
+
+
+TRACE_DTYPE = np.dtype([("event", "<i4"), ("pad", "<i4"), ("cell", "<i8"), ("x", "<f8", 3), ("k", "<f8", 3),
+                        ("L", "<f8"), ("tau_path", "<f8"), ("tau_star", "<f8")])
+
+
 class rt_launch_opts(ctypes.Structure):
     _fields_ = [("w_min", ctypes.c_double), ("max_events", ctypes.c_int32), ("weight_cut", ctypes.c_int32),
                 ("peel_emission", ctypes.c_int32), ("peel_scatter", ctypes.c_int32), ("n_norm", ctypes.c_uint64),
                 ("model_id", ctypes.c_uint32), ("block_size", ctypes.c_int32), ("records", ctypes.c_void_p),
-                ("records_capacity", ctypes.c_int64), ("record_stride", ctypes.c_uint64)]
+                ("records_capacity", ctypes.c_int64), ("record_stride", ctypes.c_uint64),
+                ("trace", ctypes.c_void_p), ("trace_capacity", ctypes.c_int64), ("trace_packet", ctypes.c_uint64),
+                ("trace_lambda", ctypes.c_int32), ("control_lanes", ctypes.c_int32)]
 
 
 class rt_stats(ctypes.Structure):
@@ -321,8 +333,8 @@ class Simulation:
         o.max_events = run.max_events
         o.weight_cut = int(run.weight_cut)
         for k, v in kw.items():
-            if k == "records":
-                o.records = v
+            if k in ("records", "trace"):
+                setattr(o, k, v)
             elif not hasattr(o, k):
                 raise TypeError(f"unknown launch option {k}")
             else:

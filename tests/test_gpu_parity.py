@@ -90,7 +90,7 @@ def test_special_cases(case):
     if case == "no_scattering":
         assert np.all(g["images"][0][2] == 0.0) and g["stats"][3] == 0.0
     if case == "dust_free":
-        assert g["stats"][1] == g["stats"][0] and g["stats"][2] == 0.0
+        assert abs(g["stats"][1] - g["stats"][0]) < 1e-12 * g["stats"][0] and g["stats"][2] == 0.0
         assert abs(g["images"][0][0, 0, 32, 32] - 1 / (4 * math.pi)) < 1e-12 * n
 
 
@@ -152,3 +152,19 @@ def test_state_and_argument_errors():
         del keep
     finally:
         rt.rt_context_destroy(ctx)
+
+
+def test_control_lanes_do_not_change_results():
+    """The warp's deferral threshold for per-event work only reorders work:
+    results agree to FP64 summation order for every setting."""
+    prob = W.disk_galaxy(n_cells=32, n_lambda=2, n_pix=32)
+    ref = None
+    for lanes in (1, 8, 32):
+        g = PAR.gpu_run(prob, 5000, control_lanes=lanes)
+        if ref is None:
+            ref = g
+            continue
+        for a, b in zip(g["images"], ref["images"]):
+            np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-20)
+        np.testing.assert_allclose(g["absorption"], ref["absorption"], rtol=1e-12, atol=1e-20)
+        assert np.array_equal(g["counters"], ref["counters"])
