@@ -15,7 +15,9 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-OUT_DIR = os.path.join(HERE, "_build")
+# RT_BUILD_DIR selects another build directory (e.g. for a debug or variant
+# build); RT_NVCC_FLAGS adds nvcc flags (space separated).
+OUT_DIR = os.environ.get("RT_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB_NAME = "librt_gb300.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -52,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         return LIB_PATH
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
-    flags = NVCC_FLAGS + ARCH + list(extra_flags or [])
+    flags = NVCC_FLAGS + ARCH + list(extra_flags or []) + os.environ.get("RT_NVCC_FLAGS", "").split()
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")

@@ -492,7 +492,15 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   p.trace_cap = o.trace ? o.trace_capacity : 0;
   p.trace_packet = o.trace_packet;
   p.trace_lambda = o.trace_lambda;
-  p.control_min = o.control_lanes ? o.control_lanes : 8;
+  p.control_min = o.control_lanes ? o.control_lanes : 16;
+  p.inv_n_per_lambda = (float)(1.0 / (double)n_per_lambda);
+  for (int l = 0; l < c->n_lambda; ++l) {
+    double tot = 0.0;
+    for (auto& src : c->sources) tot += src.lum[l];
+    p.L0[l] = tot / (double)p.n_norm;
+    p.L_cut[l] = o.w_min * p.L0[l];
+  }
+  p.profile = reinterpret_cast<unsigned long long*>(o.profile);
   p.flags = c->d_flags;
   cudaError_t e = launch_forward(p, c->grid_kind, 0, c->num_sms, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "forward launch");

@@ -32,8 +32,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 // Random block for (packet, wavelength, event, block): counter =
 // (pid low, pid high, event, (lambda << 8) | block), key = (seed, model).
-__device__ __forceinline__ uint4 draw_block(unsigned long long pid, int lam, int event, int block,
-                                            uint32_t seed, uint32_t model) {
+static __device__ __noinline__ uint4 draw_block(unsigned long long pid, int lam, int event, int block,
+                                        uint32_t seed, uint32_t model) {
   return philox4x32_10(make_uint4((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)event,
                                   ((uint32_t)lam << 8) | (uint32_t)block),
                        seed, model);

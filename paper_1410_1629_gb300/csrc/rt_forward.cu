@@ -32,6 +32,10 @@ namespace rtk {
 namespace {
 
 constexpr int kBlock = 256;
+// Resident blocks per SM the register allocation aims at (3 x 256 threads).
+#ifndef RT_FWD_MIN_BLOCKS
+#define RT_FWD_MIN_BLOCKS 3
+#endif
 
 enum Phase : int {
   kFetch = 0,      // needs a new packet
@@ -51,6 +55,50 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 __device__ __forceinline__ float inv_or_zero(float d) { return d != 0.0f ? 1.0f / d : 0.0f; }
+
+// Exact widening of a positive normal FP32 value to FP64 with integer
+// operations (rebias the exponent by 1023 - 127 and shift the significand),
+// keeping the per-crossing path off GB300's low-rate FP64 pipe.  Zero,
+// subnormal and non-finite inputs take the ordinary conversion.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = u & 0x7f800000u;
+  if (e == 0u || e == 0x7f800000u) return (double)f;
+  const unsigned hi = ((u & 0x7fffffffu) >> 3) + 0x38000000u;
+  return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(u << 29));
+}
+
+// Uniform (r + 1/2) 2^-32 rounded to FP32 (= the FP64 value rounded), from
+// the exact 33-bit integer 2r + 1.
+__device__ __forceinline__ float u01f(uint32_t r) { return __ull2float_rn(2ull * r + 1ull) * 0x1p-33f; }
+
+// 2u - 1 rounded to FP32, exactly: (2r + 1 - 2^32) 2^-32.
+__device__ __forceinline__ float u01f_signed(uint32_t r) {
+  return __ll2float_rn((long long)(2ull * r + 1ull) - (1ll << 32)) * 0x1p-32f;
+}
+
+// L2 residency: the density grid is read at every crossing and should stay in
+// L2; absorption tallies are written once per forced-path crossing and
+// should be the first lines evicted.
+__device__ __forceinline__ float load_density(const float* p) {
+  float v;
+  asm volatile(
+      "{\n\t.reg .b64 pol;\n\t"
+      "createpolicy.fractional.L2::evict_last.b64 pol, 1.0;\n\t"
+      "ld.global.nc.L2::cache_hint.f32 %0, [%1], pol;\n\t}"
+      : "=f"(v)
+      : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void add_absorption(double* p, double v) {
+  asm volatile(
+      "{\n\t.reg .b64 pol;\n\t"
+      "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+      "red.global.add.L2::cache_hint.f64 [%0], %1, pol;\n\t}" ::"l"(p),
+      "d"(v)
+      : "memory");
+}
 
 // ---------------------------------------------------------------- walk state
 // Cartesian walk: current cell indices, entry parameter t of the current
@@ -124,7 +172,7 @@ __device__ __forceinline__ bool walk_advance(const FwdParams& P, float3 x, float
 struct Lane {
   unsigned long long pid;
   int lam, event, phase, q;
-  double L, L_cut;      // weight, termination threshold w_min * L0
+  double L;             // weight
   float kappa;          // extinction per unit density at this wavelength
   float u_mu, u_phi;    // the event's Henyey-Greenstein uniforms
   float3 x, k;          // position, direction of travel
@@ -132,14 +180,23 @@ struct Lane {
   bool has_cell;
   bool walking;
   float3 id;            // inverse direction of the current walk
-  WalkCart w;
+  WalkCart w;           // current cell of the walk and its exit parameters
+  float rho;            // density of the walk's current cell (loaded one crossing ahead)
   float th, tl;         // optical depth of the current walk (pair on forced paths)
-  float aux0, aux1;     // path 1: deposit weight; path 2: tau* as a float pair
+  float aux0, aux1;     // path 1: deposit weight; path 2: tau* as a float pair, then s*
+  int hit;              // path 2: interaction cell
 };
 
-struct BlockTally {
+// Small per-launch tables (instruments, per-wavelength optics) copied to
+// shared memory at kernel start.
+__shared__ DevInstr S_INSTR[kMaxInstruments];
+__shared__ DevLambda S_LAM[kMaxLambda];
+
+// Per-lane tallies, one slot per thread in shared memory (no atomics).
+struct LaneTally {
   double escaped, absorbed, truncated;
-  unsigned long long events, peeloffs, packets, crossings, path_crossings;
+  unsigned long long crossings, path_crossings;
+  unsigned events, peeloffs, packets, pad;
 };
 
 __device__ __forceinline__ void trace_row(const FwdParams& P, const Lane& s, int event, int cell, double L,
@@ -153,22 +210,24 @@ __device__ __forceinline__ void trace_row(const FwdParams& P, const Lane& s, int
   P.trace[event] = r;
 }
 
-// Start a walk from the lane's position along d.
+// Start a walk from the lane's position along d; the first cell's density
+// load is issued here.
 __device__ __forceinline__ void start_walk(const FwdParams& P, Lane& s, float3 d) {
   s.id = make_float3(inv_or_zero(d.x), inv_or_zero(d.y), inv_or_zero(d.z));
   s.th = 0.0f;
   s.tl = 0.0f;
   s.walking = walk_init(P, s.x, d, s.id, s.has_cell, s.ci, s.cj, s.ck, s.w);
+  if (s.walking) s.rho = load_density(&P.density[s.w.cell]);
 }
 
 __device__ __forceinline__ float3 instr_dir(const DevInstr& I) { return make_float3(I.kobs[0], I.kobs[1], I.kobs[2]); }
 
 // Deposit a finished peel-off into instrument q's image(s).
 __device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane& s, bool scattered) {
-  const DevInstr& I = P.instr[s.q];
+  const DevInstr& I = S_INSTR[s.q];
   float phase = 1.0f;
   if (scattered) {
-    const float g = P.lam[s.lam].g;
+    const float g = S_LAM[s.lam].g;
     phase = hg_phase(g, s.k.x * I.kobs[0] + s.k.y * I.kobs[1] + s.k.z * I.kobs[2]);
   }
   const float tau = s.th;
@@ -212,57 +271,62 @@ __device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane& s, 
   }
 }
 
-// Emission (Sect. 3.4): source component by luminosity, position from its
-// geometry (FP64, rounded to FP32), isotropic direction.
+// Emission (Sect. 3.4): source component by luminosity (FP64 comparison of
+// the uniform with the cumulative fractions), position from its geometry and
+// an isotropic direction (FP32).
 __device__ __forceinline__ void emit(const FwdParams& P, Lane& s) {
   const uint4 r0 = draw_block(s.pid, s.lam, 0, 0, P.seed, P.model);
   const uint4 r1 = draw_block(s.pid, s.lam, 0, 1, P.seed, P.model);
-  const double u0 = u01(r0.x), u1 = u01(r0.y), u2 = u01(r0.z), u3 = u01(r0.w);
-  const double u4 = u01(r1.x), u5 = u01(r1.y), u6 = u01(r1.z), u7 = u01(r1.w);
   int src = P.n_sources - 1;
-  for (int i = 0; i < P.n_sources; ++i) {
-    if (u0 < P.src_cum[s.lam * P.n_sources + i]) { src = i; break; }
+  if (P.n_sources > 1) {
+    const double u0 = u01(r0.x);
+    for (int i = 0; i < P.n_sources; ++i) {
+      if (u0 < P.src_cum[s.lam * P.n_sources + i]) { src = i; break; }
+    }
   }
-  const DevSource S = P.src[src];
-  double px = S.center[0], py = S.center[1], pz = S.center[2];
+  const DevSource& S = P.src[src];
+  float3 x = make_float3((float)S.center[0], (float)S.center[1], (float)S.center[2]);
   if (S.kind == RT_SOURCE_EXPDISK) {
-    const double R = -S.scale_r * log(u1 * u2);
-    double sp, cp;
-    sincospi(2.0 * u3, &sp, &cp);
-    double z = -S.scale_z * log(u4);
-    if (u5 < 0.5) z = -z;
-    px += R * cp; py += R * sp; pz += z;
+    // R has density R exp(-R/hR): minus hR times the log of two uniforms
+    const float R = -(float)S.scale_r * (logf(u01f(r0.y)) + logf(u01f(r0.z)));
+    float sp, cp;
+    sincospif(2.0f * u01f(r0.w), &sp, &cp);
+    float z = -(float)S.scale_z * logf(u01f(r1.x));
+    if (r1.y < 0x80000000u) z = -z;  // u5 < 1/2
+    x.x += R * cp; x.y += R * sp; x.z += z;
   } else if (S.kind == RT_SOURCE_PLUMMER) {
-    const double r = S.scale_r / sqrt(pow(u1, -2.0 / 3.0) - 1.0);
-    const double ct = 2.0 * u2 - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
-    double sp, cp;
-    sincospi(2.0 * u3, &sp, &cp);
-    px += r * st * cp; py += r * st * sp; pz += r * ct;
+    // enclosed mass fraction m = r^3 / (r^2 + a^2)^(3/2): r = a / sqrt(m^(-2/3) - 1)
+    const float m = u01f(r0.y);
+    const float r = (float)S.scale_r / sqrtf(expm1f(-(2.0f / 3.0f) * logf(m)));
+    const float ct = u01f_signed(r0.z), st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+    float sp, cp;
+    sincospif(2.0f * u01f(r0.w), &sp, &cp);
+    x.x += r * st * cp; x.y += r * st * sp; x.z += r * ct;
   }
-  s.x = make_float3((float)px, (float)py, (float)pz);
-  const float mu = (float)(2.0 * u6 - 1.0);
+  s.x = x;
+  const float mu = u01f_signed(r1.z);
   const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
   float sp, cp;
-  sincospif((float)(2.0 * u7), &sp, &cp);
+  sincospif(2.0f * u01f(r1.w), &sp, &cp);
   s.k = make_float3(st * cp, st * sp, mu);
 }
 
 __device__ __forceinline__ void start_path(const FwdParams& P, Lane& s) {
   s.phase = kPath1;
   start_walk(P, s, s.k);
-  s.aux0 = (float)((1.0 - P.lam[s.lam].albedo) * s.L);
+  s.aux0 = (float)((1.0 - S_LAM[s.lam].albedo) * s.L);
 }
 
 // After the scattering peel-offs: new direction, then terminate or start the
 // next forced path.
-__device__ __forceinline__ void after_scattering(const FwdParams& P, Lane& s, BlockTally* bt) {
-  const float g = P.lam[s.lam].g;
+__device__ __forceinline__ void after_scattering(const FwdParams& P, Lane& s, LaneTally* bt) {
+  const float g = S_LAM[s.lam].g;
   const float mu = hg_sample(g, s.u_mu);
   float sp, cp;
   sincospif(2.0f * s.u_phi, &sp, &cp);
   s.k = rotate_dir(s.k, mu, sp, cp);
-  if ((P.weight_cut && s.L < s.L_cut) || s.event >= P.max_events) {
-    atomicAdd(&bt->truncated, s.L);
+  if ((P.weight_cut && s.L < P.L_cut[s.lam]) || s.event >= P.max_events) {
+    bt->truncated += s.L;
     s.phase = kFetch;
     return;
   }
@@ -273,28 +337,29 @@ __device__ __forceinline__ void after_scattering(const FwdParams& P, Lane& s, Bl
 // Per-event work for a lane whose walk has finished, or that needs a packet
 // (then `w` is its packet index).  Loops until the lane walks again, waits
 // for a packet, or has no work left.
-__device__ void control(const FwdParams& P, Lane& s, unsigned long long w, BlockTally* bt) {
+__device__ void control(const FwdParams& P, Lane& s, unsigned long long w, LaneTally* bt) {
   while (true) {
     switch (s.phase) {
       case kFetch: {
         if (w >= P.n_total) { s.phase = kExit; return; }
-        s.lam = (int)(w / P.n_per_lambda);
-        s.pid = P.first_id + (w - (unsigned long long)s.lam * P.n_per_lambda);
+        int lam = min((int)(__ull2float_rz(w) * P.inv_n_per_lambda), P.n_lambda - 1);
+        while (lam > 0 && (unsigned long long)lam * P.n_per_lambda > w) --lam;
+        while (lam + 1 < P.n_lambda && (unsigned long long)(lam + 1) * P.n_per_lambda <= w) ++lam;
+        s.lam = lam;
+        s.pid = P.first_id + (w - (unsigned long long)lam * P.n_per_lambda);
         w = ~0ull;
-        const DevLambda LP = P.lam[s.lam];
-        const double L0 = LP.lum_total / (double)P.n_norm;
-        s.kappa = LP.kappa;
+        const double L0 = P.L0[lam];
+        s.kappa = S_LAM[lam].kappa;
         s.L = L0;
-        s.L_cut = P.w_min * L0;
         s.event = 0;
         s.has_cell = false;
         emit(P, s);
-        atomicAdd(&bt->packets, 1ull);
+        bt->packets += 1u;
         trace_row(P, s, 0, -1, L0, 0.0, 0.0);
         if (P.peel_emission && P.n_instr > 0) {
           s.phase = kPeelEmit;
           s.q = 0;
-          start_walk(P, s, instr_dir(P.instr[0]));
+          start_walk(P, s, instr_dir(S_INSTR[0]));
         } else {
           s.event = 1;
           start_path(P, s);
@@ -305,10 +370,10 @@ __device__ void control(const FwdParams& P, Lane& s, unsigned long long w, Block
       case kPeelScat: {
         const bool scattered = s.phase == kPeelScat;
         peel_deposit(P, s, scattered);
-        atomicAdd(&bt->peeloffs, 1ull);
+        bt->peeloffs += 1u;
         s.q += 1;
         if (s.q < P.n_instr) {
-          start_walk(P, s, instr_dir(P.instr[s.q]));
+          start_walk(P, s, instr_dir(S_INSTR[s.q]));
         } else if (!scattered) {
           s.event = 1;
           start_path(P, s);
@@ -321,19 +386,19 @@ __device__ void control(const FwdParams& P, Lane& s, unsigned long long w, Block
         const double tau = (double)s.th + (double)s.tl;
         if (!(tau > 0.0)) {
           trace_row(P, s, s.event, -1, s.L, 0.0, 0.0);
-          atomicAdd(&bt->escaped, s.L);
+          bt->escaped += s.L;
           s.phase = kFetch;
           return;
         }
-        const double albedo = P.lam[s.lam].albedo;
-        const double E = exp(-tau);
+        const double albedo = S_LAM[s.lam].albedo;
         const double one_minus_E = -expm1(-tau);
-        atomicAdd(&bt->escaped, s.L * E);
-        atomicAdd(&bt->absorbed, (1.0 - albedo) * s.L * one_minus_E);
+        const double E = 1.0 - one_minus_E;
+        bt->escaped += s.L * E;
+        bt->absorbed += (1.0 - albedo) * s.L * one_minus_E;
         const uint4 r = draw_block(s.pid, s.lam, s.event, 0, P.seed, P.model);
         const double tau_star = -log1p(-u01(r.x) * one_minus_E);
-        s.u_mu = (float)u01(r.y);
-        s.u_phi = (float)u01(r.z);
+        s.u_mu = u01f(r.y);
+        s.u_phi = u01f(r.z);
         s.aux0 = (float)tau_star;
         s.aux1 = (float)(tau_star - (double)s.aux0);
         s.L = albedo * s.L * one_minus_E;  // weight after the scattering
@@ -342,24 +407,25 @@ __device__ void control(const FwdParams& P, Lane& s, unsigned long long w, Block
         break;
       }
       case kPath2: {
-        // the walk stopped in the interaction cell; w.t holds s*
-        const float s_star = s.w.t;
+        // the walk stopped in the interaction cell `hit`; aux0 holds s*
+        const float s_star = s.aux0;
+        const int ix = s.hit % P.nx, iy = (s.hit / P.nx) % P.ny, iz = s.hit / (P.nx * P.ny);
         float3 x = make_float3(fmaf(s_star, s.k.x, s.x.x), fmaf(s_star, s.k.y, s.x.y), fmaf(s_star, s.k.z, s.x.z));
-        const float lo0 = fmaf((float)s.w.ix, P.d[0], P.lo[0]), hi0 = fmaf((float)(s.w.ix + 1), P.d[0], P.lo[0]);
-        const float lo1 = fmaf((float)s.w.iy, P.d[1], P.lo[1]), hi1 = fmaf((float)(s.w.iy + 1), P.d[1], P.lo[1]);
-        const float lo2 = fmaf((float)s.w.iz, P.d[2], P.lo[2]), hi2 = fmaf((float)(s.w.iz + 1), P.d[2], P.lo[2]);
+        const float lo0 = fmaf((float)ix, P.d[0], P.lo[0]), hi0 = fmaf((float)(ix + 1), P.d[0], P.lo[0]);
+        const float lo1 = fmaf((float)iy, P.d[1], P.lo[1]), hi1 = fmaf((float)(iy + 1), P.d[1], P.lo[1]);
+        const float lo2 = fmaf((float)iz, P.d[2], P.lo[2]), hi2 = fmaf((float)(iz + 1), P.d[2], P.lo[2]);
         x.x = fminf(fmaxf(x.x, lo0), hi0);
         x.y = fminf(fmaxf(x.y, lo1), hi1);
         x.z = fminf(fmaxf(x.z, lo2), hi2);
         s.x = x;
-        s.ci = s.w.ix; s.cj = s.w.iy; s.ck = s.w.iz;
+        s.ci = ix; s.cj = iy; s.ck = iz;
         s.has_cell = true;
-        atomicAdd(&bt->events, 1ull);
-        trace_row(P, s, s.event, s.w.cell, s.L, 0.0, (double)s.aux0 + (double)s.aux1);
+        bt->events += 1u;
+        trace_row(P, s, s.event, s.hit, s.L, 0.0, 0.0);
         if (P.peel_scatter && P.n_instr > 0) {
           s.phase = kPeelScat;
           s.q = 0;
-          start_walk(P, s, instr_dir(P.instr[0]));
+          start_walk(P, s, instr_dir(S_INSTR[0]));
         } else {
           after_scattering(P, s, bt);
         }
@@ -382,16 +448,18 @@ __device__ __forceinline__ void walk_step(const FwdParams& P, Lane& s, unsigned&
   if (w.tz < te) { te = w.tz; axis = 2; }
   const float texit = fmaxf(te, w.t);
   const float ds = texit - w.t;
-  const float kr = s.kappa * __ldg(&P.density[w.cell]);
+  const float kr = s.kappa * s.rho;
   const float dt = kr * ds;
   if (s.phase == kPath2) {
     float nh, e;
     two_sum(s.th, dt, nh, e);
     const float nl = s.tl + e;
     if ((nh - s.aux0) + (nl - s.aux1) > 0.0f) {
-      // interaction in this cell: s* = t_in + (tau* - tau_before) / (kappa rho)
-      const double rem = (((double)s.aux0 - (double)s.th) + (double)s.aux1) - (double)s.tl;
-      w.t = w.t + (float)rem / kr;
+      // interaction in this cell: s* = t_in + (tau* - tau_before) / (kappa rho);
+      // tau* - tau_before from the two pairs (aux0 - th is exact where it matters)
+      const float rem = ((s.aux0 - s.th) + s.aux1) - s.tl;
+      s.aux0 = w.t + rem / kr;
+      s.hit = w.cell;
       s.walking = false;
       return;
     }
@@ -401,7 +469,7 @@ __device__ __forceinline__ void walk_step(const FwdParams& P, Lane& s, unsigned&
     ++n_path;
     if (dt > 0.0f) {
       const float dep = s.aux0 * __expf(-s.th) * -expm1f(-dt);
-      atomicAdd(&P.absorption[(size_t)s.lam * P.n_cells + w.cell], (double)dep);
+      add_absorption(&P.absorption[(size_t)s.lam * P.n_cells + w.cell], widen(dep));
     }
     float nh, e;
     two_sum(s.th, dt, nh, e);
@@ -412,39 +480,47 @@ __device__ __forceinline__ void walk_step(const FwdParams& P, Lane& s, unsigned&
     s.th += dt;
   }
   w.t = texit;
-  if (!walk_advance(P, s.x, s.id, axis, w)) {
+  if (walk_advance(P, s.x, s.id, axis, w)) {
+    s.rho = load_density(&P.density[w.cell]);  // consumed by the next crossing
+  } else {
     s.walking = false;
     if (s.phase == kPath2) {
       // not reachable: the pair sums of both walks are identical and tau* is
       // below the path's optical depth; keep the packet at the path's end
       atomicOr(P.flags, kFlagNoInteraction);
-      w.ix = min(max(w.ix, 0), P.nx - 1);
-      w.iy = min(max(w.iy, 0), P.ny - 1);
-      w.iz = min(max(w.iz, 0), P.nz - 1);
-      w.cell = w.ix + P.nx * (w.iy + P.ny * w.iz);
+      s.aux0 = texit;
+      s.hit = w.cell;  // the advance leaves the cell unchanged when the ray exits
     }
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_forward_cartesian(const FwdParams P) {
-  __shared__ BlockTally bt;
-  if (threadIdx.x == 0) {
-    bt.escaped = bt.absorbed = bt.truncated = 0.0;
-    bt.events = bt.peeloffs = bt.packets = bt.crossings = bt.path_crossings = 0ull;
-  }
+__global__ void __launch_bounds__(kBlock, RT_FWD_MIN_BLOCKS) k_forward_cartesian(const FwdParams P) {
+  __shared__ LaneTally tally[kBlock];
+  for (int i = threadIdx.x; i < P.n_instr; i += kBlock) S_INSTR[i] = P.instr[i];
+  for (int i = threadIdx.x; i < P.n_lambda; i += kBlock) S_LAM[i] = P.lam[i];
   __syncthreads();
+  LaneTally* bt = &tally[threadIdx.x];
+  bt->escaped = bt->absorbed = bt->truncated = 0.0;
+  bt->crossings = bt->path_crossings = 0ull;
+  bt->events = bt->peeloffs = bt->packets = 0u;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
   Lane s;
   s.phase = kFetch;
   s.walking = false;
   unsigned n_path = 0, n_peel = 0;
+  // optional execution counters (warp leader only)
+  const bool prof = P.profile != nullptr && lane == 0;
+  unsigned long long c_iter = 0, c_walk_lanes = 0, c_rounds = 0, c_round_lanes = 0, cyc_ctl = 0, cyc_walk = 0;
   while (true) {
     const bool idle = !s.walking && s.phase != kExit;
     const unsigned need = __ballot_sync(0xffffffffu, idle);
     const unsigned walkers = __ballot_sync(0xffffffffu, s.walking);
     if (need == 0u && walkers == 0u) break;
+    long long t0 = 0;
+    if (prof) { ++c_iter; t0 = clock64(); }
     if (walkers == 0u || __popc(need) >= P.control_min) {
+      if (prof) { ++c_rounds; c_round_lanes += __popc(need); }
       // packets for every lane that needs one: one atomic per warp
       const unsigned fetch = __ballot_sync(0xffffffffu, idle && s.phase == kFetch);
       unsigned long long w = ~0ull;
@@ -455,27 +531,58 @@ __global__ void __launch_bounds__(kBlock) k_forward_cartesian(const FwdParams P)
         base = __shfl_sync(0xffffffffu, base, leader);
         if (idle && s.phase == kFetch) w = base + __popc(fetch & lt_mask);
       }
-      if (idle) control(P, s, w, &bt);
+      if (idle) control(P, s, w, bt);
       if ((n_path | n_peel) & 0xC0000000u) {  // keep the 32-bit lane counters far from overflow
-        atomicAdd(&bt.crossings, (unsigned long long)n_path + n_peel);
-        atomicAdd(&bt.path_crossings, (unsigned long long)n_path);
+        bt->crossings += (unsigned long long)n_path + n_peel;
+        bt->path_crossings += n_path;
         n_path = n_peel = 0;
       }
     }
+    long long t1 = 0;
+    if (prof) { t1 = clock64(); cyc_ctl += t1 - t0; }
+    const unsigned stepping = __ballot_sync(0xffffffffu, s.walking);
     if (s.walking) walk_step(P, s, n_path, n_peel);
+    if (prof) { c_walk_lanes += __popc(stepping); cyc_walk += clock64() - t1; }
   }
-  atomicAdd(&bt.crossings, (unsigned long long)n_path + n_peel);
-  atomicAdd(&bt.path_crossings, (unsigned long long)n_path);
+  if (prof) {
+    atomicAdd(&P.profile[0], c_iter);
+    atomicAdd(&P.profile[1], c_walk_lanes);
+    atomicAdd(&P.profile[2], c_rounds);
+    atomicAdd(&P.profile[3], c_round_lanes);
+    atomicAdd(&P.profile[4], cyc_ctl);
+    atomicAdd(&P.profile[5], cyc_walk);
+  }
+  bt->crossings += (unsigned long long)n_path + n_peel;
+  bt->path_crossings += n_path;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    atomicAdd(&P.stats[1], bt.escaped);
-    atomicAdd(&P.stats[2], bt.absorbed);
-    atomicAdd(&P.stats[3], bt.truncated);
-    atomicAdd(&P.counters[0], bt.crossings);
-    atomicAdd(&P.counters[1], bt.events);
-    atomicAdd(&P.counters[2], bt.peeloffs);
-    atomicAdd(&P.counters[3], bt.packets);
-    atomicAdd(&P.counters[5], bt.path_crossings);
+  if (threadIdx.x < 32) {
+    double esc = 0.0, ab = 0.0, tr = 0.0;
+    unsigned long long cr = 0, pc = 0, ev = 0, pe = 0, pk = 0;
+    for (int t = threadIdx.x; t < kBlock; t += 32) {
+      esc += tally[t].escaped; ab += tally[t].absorbed; tr += tally[t].truncated;
+      cr += tally[t].crossings; pc += tally[t].path_crossings;
+      ev += tally[t].events; pe += tally[t].peeloffs; pk += tally[t].packets;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      esc += __shfl_down_sync(0xffffffffu, esc, o);
+      ab += __shfl_down_sync(0xffffffffu, ab, o);
+      tr += __shfl_down_sync(0xffffffffu, tr, o);
+      cr += __shfl_down_sync(0xffffffffu, cr, o);
+      pc += __shfl_down_sync(0xffffffffu, pc, o);
+      ev += __shfl_down_sync(0xffffffffu, ev, o);
+      pe += __shfl_down_sync(0xffffffffu, pe, o);
+      pk += __shfl_down_sync(0xffffffffu, pk, o);
+    }
+    if (threadIdx.x == 0) {
+      atomicAdd(&P.stats[1], esc);
+      atomicAdd(&P.stats[2], ab);
+      atomicAdd(&P.stats[3], tr);
+      atomicAdd(&P.counters[0], cr);
+      atomicAdd(&P.counters[1], ev);
+      atomicAdd(&P.counters[2], pe);
+      atomicAdd(&P.counters[3], pk);
+      atomicAdd(&P.counters[5], pc);
+    }
   }
 }
 

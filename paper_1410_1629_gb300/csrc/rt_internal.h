@@ -26,7 +26,7 @@ struct DevLambda {
   double lum_total;   // sum of the sources' luminosities at this wavelength
 };
 
-// Emission component (Sect. 3.4); positions are sampled in FP64.
+// Emission component (Sect. 3.4).
 struct DevSource {
   int kind;
   int pad;
@@ -77,6 +77,10 @@ struct FwdParams {
   unsigned long long trace_packet;
   int trace_lambda;
   int control_min;  // lanes that must wait for per-event work before a warp runs it
+  float inv_n_per_lambda;          // 1 / n_per_lambda (estimate of a packet's wavelength index)
+  double L0[kMaxLambda];           // packet weight at emission, L_tot / n_norm, per wavelength
+  double L_cut[kMaxLambda];        // w_min * L0 per wavelength
+  unsigned long long* profile;  // optional execution counters (see rt_launch_opts.profile)
   int* flags;
 };
 

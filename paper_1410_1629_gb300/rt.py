@@ -79,7 +79,8 @@ class rt_launch_opts(ctypes.Structure):
                 ("model_id", ctypes.c_uint32), ("block_size", ctypes.c_int32), ("records", ctypes.c_void_p),
                 ("records_capacity", ctypes.c_int64), ("record_stride", ctypes.c_uint64),
                 ("trace", ctypes.c_void_p), ("trace_capacity", ctypes.c_int64), ("trace_packet", ctypes.c_uint64),
-                ("trace_lambda", ctypes.c_int32), ("control_lanes", ctypes.c_int32)]
+                ("trace_lambda", ctypes.c_int32), ("control_lanes", ctypes.c_int32),
+                ("profile", ctypes.c_void_p)]
 
 
 class rt_stats(ctypes.Structure):
@@ -333,7 +334,7 @@ class Simulation:
         o.max_events = run.max_events
         o.weight_cut = int(run.weight_cut)
         for k, v in kw.items():
-            if k in ("records", "trace"):
+            if k in ("records", "trace", "profile"):
                 setattr(o, k, v)
             elif not hasattr(o, k):
                 raise TypeError(f"unknown launch option {k}")
