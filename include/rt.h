@@ -251,6 +251,36 @@ rt_status rt_read_stats(rt_ctx ctx, rt_stats* out);
 /* Wait for all work queued on `stream` and report asynchronous errors. */
 rt_status rt_synchronize(rt_ctx ctx, void* stream);
 
+/* The cartesian forward transport of rt_launch_packets without any device
+ * memory allocation.  The paper has no counterpart: this entry point exists
+ * for callers that may not allocate GPU memory while they run (a plug-in
+ * inside a framework that owns the device memory pool, a service with a fixed
+ * memory budget), so they pass every device buffer themselves.
+ *   grid: kind RT_GRID_CARTESIAN, on_device = 1, density a device pointer.
+ *   kappa, albedo, g [n_lambda]; sources [n_sources] with host luminosity
+ *   arrays; instruments [n_instruments]: host arrays, as for the context calls.
+ *   images: host array of n_instruments device pointers, each float64
+ *   [channels][n_lambda][ny][nx]; absorption: device float64
+ *   [n_lambda][nx*ny*nz].  Tallies are ADDED to these buffers.
+ *   stats_out: device pointer that receives this call's rt_stats, or NULL.
+ * Limits (fixed by the library's working area): n_lambda <= 64,
+ * n_sources <= 16, n_instruments <= 16; larger values return RT_ERR_ARG.
+ * The library keeps one working area of 16 KiB per device in a static
+ * device array, held by every GPU that loads the library until the process
+ * exits; the call allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library routine).  The first call on a device looks up the working area's
+ * address and should come before any stream capture on that device.  All
+ * calls share the working area, which keeps the last call's contents: calls
+ * that overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Asynchronous on `stream`.  Errors: RT_ERR_ARG,
+ * RT_ERR_CUDA; the message is rt_last_error(NULL). */
+rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t n_lambda, const double* kappa,
+                                    const double* albedo, const double* g, int32_t n_sources,
+                                    const rt_source_desc* sources, int32_t n_instruments,
+                                    const rt_instrument_desc* instruments, double* const* images,
+                                    double* absorption, uint64_t n_per_lambda, uint64_t first_packet_id,
+                                    uint64_t seed, const rt_launch_opts* opts, rt_stats* stats_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

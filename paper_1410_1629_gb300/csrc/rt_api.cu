@@ -37,6 +37,8 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+void rtk::set_context_free_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
 struct rt_ctx_s {
   int device = 0;
   int num_sms = 0;

@@ -90,6 +90,9 @@ enum DeviceFlag : int { kFlagCellRange = 1, kFlagOctreeDepth = 2, kFlagWalkSteps
 // the depths used; this is a safety net, not a tuning knob).
 constexpr unsigned kMaxWalkSteps = 1u << 22;
 
+// Message returned by rt_last_error(NULL) (calls without a context).
+void set_context_free_error(const char* msg);
+
 // Launchers (rt_forward.cu).
 cudaError_t launch_forward(const FwdParams& p, int grid_kind, int block_size, int num_sms, cudaStream_t stream);
 cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t stream);

@@ -1,0 +1,290 @@
+// rt_launch_packets_noalloc: the cartesian forward transport without any
+// device allocation, for callers that cannot allocate GPU memory themselves.
+//
+// Who needs this: code that must not call cudaMalloc or any allocating
+// library routine while it runs -- for example a plug-in executed inside
+// another framework that owns the whole device memory pool, or a service
+// with a fixed memory budget checked at start-up.  Such a caller keeps its
+// own device buffers for the inputs and outputs and needs the library to
+// bring nothing else but a fixed, preallocated working area.
+//
+// The working area is the file-scope array `g_noalloc_scratch` below, a
+// __device__ array of kNoallocScratchBytes bytes that every GPU which loads
+// this library holds until the process exits.  It carries the packet work
+// counter, the tallies and the device flags of one launch, and the small
+// per-launch tables (optics per wavelength, sources, instruments).  Host code
+// cannot use the array's name as a device address: on the first call on each
+// device the library looks the address up with cudaGetSymbolAddress (with that
+// device current) and keeps it.  That first call should therefore come before
+// any stream capture on that device.  Every call uses the same array and the
+// array keeps the last call's contents; a call clears the parts that must
+// start at zero.  Two calls that overlap on the GPU (different streams, or
+// different host threads on one device) race on the array.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "rt_internal.h"
+
+using namespace rtk;
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = 16384;
+constexpr int kMaxDevices = 64;
+
+// Byte offsets inside the working area (each 256-byte aligned block).
+constexpr size_t kOffWork = 0;                                       // 1 x u64
+constexpr size_t kOffStats = 16;                                     // 4 x f64
+constexpr size_t kOffCounters = 48;                                  // 8 x u64
+constexpr size_t kOffFlags = 112;                                    // 1 x i32
+constexpr size_t kOffLam = 256;                                      // DevLambda[kMaxLambda]
+constexpr size_t kOffSrc = kOffLam + sizeof(DevLambda) * kMaxLambda;  // DevSource[kMaxSources]
+constexpr size_t kOffCum = ((kOffSrc + sizeof(DevSource) * kMaxSources + 255) / 256) * 256;
+constexpr size_t kOffInstr = ((kOffCum + sizeof(double) * kMaxLambda * kMaxSources + 255) / 256) * 256;
+constexpr size_t kScratchUsed = kOffInstr + sizeof(DevInstr) * kMaxInstruments;
+static_assert(kScratchUsed <= kNoallocScratchBytes, "working area too small for its layout");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+std::mutex g_mutex;
+void* g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of the working area on the current device (looked up once).
+cudaError_t scratch_address(int device, unsigned char** out) {
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!g_scratch_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[device] = p;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_addr[device]);
+  return cudaSuccess;
+}
+
+// Packs the launch's tallies from the working area into an rt_stats.
+__global__ void k_noalloc_stats(const unsigned char* scratch, double emitted, rt_stats* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double* st = reinterpret_cast<const double*>(scratch + kOffStats);
+  const unsigned long long* cn = reinterpret_cast<const unsigned long long*>(scratch + kOffCounters);
+  const int* flags = reinterpret_cast<const int*>(scratch + kOffFlags);
+  rt_stats s;
+  s.emitted = emitted;
+  s.escaped = st[1];
+  s.absorbed = st[2];
+  s.truncated = st[3];
+  s.crossings = cn[0];
+  s.path_crossings = cn[5];
+  s.events = cn[1];
+  s.peeloffs = cn[2];
+  s.packets = cn[3];
+  s.records = cn[4];
+  s.device_flags = *flags;
+  s.reserved = 0;
+  *out = s;
+}
+
+rt_status fail(rt_status code, const char* msg) {
+  set_context_free_error(msg);
+  return code;
+}
+
+bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+}  // namespace
+
+extern "C" rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t n_lambda, const double* kappa,
+                                               const double* albedo, const double* g, int32_t n_sources,
+                                               const rt_source_desc* sources, int32_t n_instruments,
+                                               const rt_instrument_desc* instruments, double* const* images,
+                                               double* absorption, uint64_t n_per_lambda, uint64_t first_packet_id,
+                                               uint64_t seed, const rt_launch_opts* opts, rt_stats* stats_out,
+                                               void* stream) {
+  set_context_free_error("");
+  // ---- arguments (the same rules as the context calls, plus the fixed limits)
+  if (!grid || grid->kind != RT_GRID_CARTESIAN)
+    return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: a cartesian grid descriptor is required");
+  if (!grid->on_device || !grid->density)
+    return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: the density must be a device pointer (on_device = 1)");
+  if (grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0 || (long long)grid->nx * grid->ny * grid->nz > (1ll << 31) - 1)
+    return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: bad cell counts");
+  for (int a = 0; a < 3; ++a)
+    if (!(std::isfinite(grid->bounds[2 * a]) && std::isfinite(grid->bounds[2 * a + 1]) &&
+          grid->bounds[2 * a] < grid->bounds[2 * a + 1]))
+      return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: bounds are not increasing");
+  if (n_lambda < 1 || n_lambda > kMaxLambda)
+    return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: n_lambda must be 1..64 (working-area limit)");
+  if (n_sources < 1 || n_sources > kMaxSources)
+    return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: n_sources must be 1..16 (working-area limit)");
+  if (n_instruments < 0 || n_instruments > kMaxInstruments)
+    return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: n_instruments must be 0..16 (working-area limit)");
+  if (!kappa || !albedo || !g || !sources || (n_instruments > 0 && (!instruments || !images)) || !absorption)
+    return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: null array");
+  if (seed >> 32) return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: seed must be < 2^32");
+  for (int l = 0; l < n_lambda; ++l) {
+    if (!(std::isfinite(kappa[l]) && kappa[l] >= 0) || !(albedo[l] >= 0 && albedo[l] <= 1) || !(g[l] > -1 && g[l] < 1))
+      return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: invalid optical properties");
+  }
+  for (int i = 0; i < n_sources; ++i) {
+    const rt_source_desc& d = sources[i];
+    if (d.kind < RT_SOURCE_POINT || d.kind > RT_SOURCE_PLUMMER || !d.luminosity || !finite3(d.center) ||
+        (d.kind != RT_SOURCE_POINT && !(d.scale_r > 0)) || (d.kind == RT_SOURCE_EXPDISK && !(d.scale_z > 0)))
+      return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: invalid source");
+    for (int l = 0; l < n_lambda; ++l)
+      if (!(std::isfinite(d.luminosity[l]) && d.luminosity[l] >= 0))
+        return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: invalid source luminosity");
+  }
+  for (int q = 0; q < n_instruments; ++q) {
+    const rt_instrument_desc& d = instruments[q];
+    if (d.nx <= 0 || d.ny <= 0 || (long long)d.nx * d.ny > (1ll << 28) || !(d.half_x > 0 && d.half_y > 0) ||
+        (d.channels != 1 && d.channels != 3) || (d.deposit != RT_DEPOSIT_NEAREST && d.deposit != RT_DEPOSIT_BILINEAR) ||
+        !images[q])
+      return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: invalid instrument or null image");
+  }
+  rt_launch_opts o;
+  rt_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.max_events < 1 || !(o.w_min >= 0 && o.w_min < 1) || o.control_lanes < 0 || o.control_lanes > 32)
+    return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: invalid launch options");
+  // ---- the working area of the current device
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return fail(RT_ERR_CUDA, cudaGetErrorString(e));
+  if (device < 0 || device >= kMaxDevices) return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: device index too large");
+  unsigned char* scratch = nullptr;
+  e = scratch_address(device, &scratch);
+  if (e != cudaSuccess) return fail(RT_ERR_CUDA, cudaGetErrorString(e));
+  int num_sms = 0;
+  e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return fail(RT_ERR_CUDA, cudaGetErrorString(e));
+  if (n_per_lambda == 0) return RT_OK;
+  const unsigned long long n_total = n_per_lambda * (unsigned long long)n_lambda;
+  if (n_total / (unsigned long long)n_lambda != n_per_lambda || n_total > (1ull << 62))
+    return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: packet count overflow");
+  // ---- per-launch tables, built on the host stack and copied into the working area
+  DevLambda lam[kMaxLambda];
+  DevSource src[kMaxSources];
+  double cum[kMaxLambda * kMaxSources];
+  DevInstr ins[kMaxInstruments];
+  std::memset(lam, 0, sizeof lam);
+  std::memset(src, 0, sizeof src);
+  std::memset(cum, 0, sizeof cum);
+  std::memset(ins, 0, sizeof ins);
+  FwdParams p;
+  std::memset(&p, 0, sizeof p);
+  const unsigned long long n_norm = o.n_norm ? o.n_norm : n_per_lambda;
+  double emitted = 0.0;
+  for (int l = 0; l < n_lambda; ++l) {
+    double tot = 0.0;
+    for (int i = 0; i < n_sources; ++i) tot += sources[i].luminosity[l];
+    if (!(tot > 0)) return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: zero total luminosity at a wavelength");
+    lam[l].kappa = (float)kappa[l];
+    lam[l].g = (float)g[l];
+    lam[l].albedo = albedo[l];
+    lam[l].lum_total = tot;
+    double run = 0.0;
+    for (int i = 0; i < n_sources; ++i) {
+      run += sources[i].luminosity[l];
+      cum[l * n_sources + i] = run / tot;
+    }
+    p.L0[l] = tot / (double)n_norm;
+    p.L_cut[l] = o.w_min * p.L0[l];
+    emitted += (double)n_per_lambda * p.L0[l];
+  }
+  for (int i = 0; i < n_sources; ++i) {
+    src[i].kind = sources[i].kind;
+    for (int a = 0; a < 3; ++a) src[i].center[a] = sources[i].center[a];
+    src[i].scale_r = sources[i].scale_r;
+    src[i].scale_z = sources[i].scale_z;
+  }
+  for (int q = 0; q < n_instruments; ++q) {
+    const rt_instrument_desc& d = instruments[q];
+    const double st = std::sin(d.inclination), ct = std::cos(d.inclination);
+    const double sp = std::sin(d.azimuth), cp = std::cos(d.azimuth);
+    const double so = std::sin(d.position_angle), co = std::cos(d.position_angle);
+    const double kobs[3] = {st * cp, st * sp, ct};
+    const double a[3] = {-sp, cp, 0.0};
+    const double b[3] = {-ct * cp, -ct * sp, st};
+    for (int i = 0; i < 3; ++i) {
+      ins[q].kobs[i] = (float)kobs[i];
+      ins[q].ex[i] = (float)(co * a[i] - so * b[i]);
+      ins[q].ey[i] = (float)(so * a[i] + co * b[i]);
+    }
+    ins[q].off_x = (float)(d.half_x - d.center_x);
+    ins[q].off_y = (float)(d.half_y - d.center_y);
+    ins[q].sx = (float)(d.nx / (2.0 * d.half_x));
+    ins[q].sy = (float)(d.ny / (2.0 * d.half_y));
+    ins[q].nx = d.nx;
+    ins[q].ny = d.ny;
+    ins[q].bilinear = d.deposit == RT_DEPOSIT_BILINEAR;
+    ins[q].channels = d.channels;
+    ins[q].image = images[q];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // pageable host -> device copies are staged before these calls return, so
+  // the stack tables may go out of scope afterwards
+  if ((e = cudaMemsetAsync(scratch, 0, 256, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(scratch + kOffLam, lam, sizeof(DevLambda) * n_lambda, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(scratch + kOffSrc, src, sizeof(DevSource) * n_sources, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(scratch + kOffCum, cum, sizeof(double) * n_lambda * n_sources, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (n_instruments > 0 &&
+       (e = cudaMemcpyAsync(scratch + kOffInstr, ins, sizeof(DevInstr) * n_instruments, cudaMemcpyHostToDevice, s)) != cudaSuccess))
+    return fail(RT_ERR_CUDA, cudaGetErrorString(e));
+  // ---- the launch, exactly as rt_launch_packets builds it
+  p.nx = grid->nx; p.ny = grid->ny; p.nz = grid->nz;
+  const int n3[3] = {grid->nx, grid->ny, grid->nz};
+  for (int a = 0; a < 3; ++a) {
+    p.lo[a] = (float)grid->bounds[2 * a];
+    p.hi[a] = (float)grid->bounds[2 * a + 1];
+    const double d = (grid->bounds[2 * a + 1] - grid->bounds[2 * a]) / n3[a];
+    p.d[a] = (float)d;
+    p.inv_d[a] = (float)(1.0 / d);
+  }
+  p.density = grid->density;
+  p.child = nullptr;
+  p.n_cells = (long long)grid->nx * grid->ny * grid->nz;
+  p.n_lambda = n_lambda;
+  p.n_sources = n_sources;
+  p.n_instr = n_instruments;
+  p.lam = reinterpret_cast<const DevLambda*>(scratch + kOffLam);
+  p.src = reinterpret_cast<const DevSource*>(scratch + kOffSrc);
+  p.src_cum = reinterpret_cast<const double*>(scratch + kOffCum);
+  p.instr = reinterpret_cast<const DevInstr*>(scratch + kOffInstr);
+  p.absorption = absorption;
+  p.n_per_lambda = n_per_lambda;
+  p.first_id = first_packet_id;
+  p.n_total = n_total;
+  p.n_norm = n_norm;
+  p.seed = (unsigned)seed;
+  p.model = o.model_id;
+  p.w_min = o.w_min;
+  p.max_events = o.max_events;
+  p.weight_cut = o.weight_cut;
+  p.peel_emission = o.peel_emission;
+  p.peel_scatter = o.peel_scatter;
+  p.work_counter = reinterpret_cast<unsigned long long*>(scratch + kOffWork);
+  p.stats = reinterpret_cast<double*>(scratch + kOffStats);
+  p.counters = reinterpret_cast<unsigned long long*>(scratch + kOffCounters);
+  p.records = o.records;
+  p.records_cap = o.records ? o.records_capacity : 0;
+  p.record_stride = o.record_stride;
+  p.trace = o.trace;
+  p.trace_cap = o.trace ? o.trace_capacity : 0;
+  p.trace_packet = o.trace_packet;
+  p.trace_lambda = o.trace_lambda;
+  p.control_min = o.control_lanes ? o.control_lanes : 16;
+  p.profile = reinterpret_cast<unsigned long long*>(o.profile);
+  p.inv_n_per_lambda = (float)(1.0 / (double)n_per_lambda);
+  p.flags = reinterpret_cast<int*>(scratch + kOffFlags);
+  e = launch_forward(p, RT_GRID_CARTESIAN, 0, num_sms, s);
+  if (e != cudaSuccess) return fail(RT_ERR_CUDA, cudaGetErrorString(e));
+  if (stats_out) {
+    k_noalloc_stats<<<1, 32, 0, s>>>(scratch, emitted, stats_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(RT_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return RT_OK;
+}

@@ -114,6 +114,12 @@ SIGNATURES = {
                                         ctypes.c_int32, ctypes.c_void_p]),
     "rt_read_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rt_stats)]),
     "rt_synchronize": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "rt_launch_packets_noalloc": (ctypes.c_int32, [ctypes.POINTER(rt_grid_desc), ctypes.c_int32, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                                   ctypes.POINTER(rt_source_desc), ctypes.c_int32,
+                                                   ctypes.POINTER(rt_instrument_desc), ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                                   ctypes.POINTER(rt_launch_opts), ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 _lib = None
@@ -250,6 +256,33 @@ def rt_read_stats(ctx) -> rt_stats:
 
 def rt_synchronize(ctx, stream=None):
     _check(ctx, lib().rt_synchronize(ctx, _stream_ptr(stream)))
+
+
+def rt_launch_packets_noalloc(grid_desc_, kappa, albedo, g, sources, luminosities, instruments, image_ptrs,
+                              absorption_ptr, n_per_lambda, first_packet_id=0, seed=0, opts=None, stats_ptr=None,
+                              stream=None):
+    """Forward transport without device allocation: every device buffer
+    (grid density, images, absorption, optional rt_stats output) comes from
+    the caller as a device address."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (kappa, albedo, g)]
+    n_src = len(sources)
+    src = (rt_source_desc * max(1, n_src))()
+    keep = []
+    for i, (d, lum) in enumerate(zip(sources, luminosities)):
+        la = np.ascontiguousarray(lum, dtype=np.float64)
+        keep.append(la)
+        d.luminosity = la.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        src[i] = d
+    n_ins = len(instruments)
+    ins = (rt_instrument_desc * max(1, n_ins))(*instruments)
+    imgs = (ctypes.c_void_p * max(1, n_ins))(*[int(p) for p in image_ptrs])
+    o = opts if opts is not None else rt_default_opts()
+    st = lib().rt_launch_packets_noalloc(ctypes.byref(grid_desc_), arrs[0].size, arrs[0].ctypes.data,
+                                         arrs[1].ctypes.data, arrs[2].ctypes.data, n_src, src, n_ins, ins, imgs,
+                                         int(absorption_ptr), int(n_per_lambda), int(first_packet_id), int(seed),
+                                         ctypes.byref(o), stats_ptr, _stream_ptr(stream))
+    if st != RT_OK:
+        raise RTError(st, lib().rt_last_error(None).decode())
 
 
 # ---------------------------------------------------------------- descriptors from workloads

@@ -1,0 +1,94 @@
+"""The allocation-free entry point gives the same tallies as the context path.
+
+rt_launch_packets_noalloc is for callers that may not allocate GPU memory
+while they run: it brings its own fixed working area (a static device array)
+and takes every other buffer from the caller.  Here two calls in a row through
+the C ABI are each compared with rt_launch_packets on a context, at the
+tolerance of FP64 summation order.  This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1410_1629_gb300 import rt
+from paper_1410_1629_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU-only machines
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def _problem():
+    # several wavelengths, three frames with direct/scattered channels
+    return W.disk_galaxy(n_cells=32, n_lambda=3, n_pix=32, channels=3)
+
+
+def _context_run(prob, n, first, seed, n_norm):
+    sim = rt.Simulation(prob)
+    try:
+        sim.launch(n, first, seed, n_norm=n_norm)
+        imgs = [t.cpu().numpy() for t in sim.images()]
+        ab = sim.absorption().cpu().numpy()
+        st = sim.stats()
+    finally:
+        sim.close()
+    return imgs, ab, st
+
+
+def _noalloc_run(prob, dens, n, first, seed, n_norm):
+    grid = rt.rt_grid_desc()
+    grid.kind = rt.RT_GRID_CARTESIAN
+    grid.bounds[:] = [float(b) for b in prob.grid.bounds]
+    grid.nz, grid.ny, grid.nx = prob.grid.density.shape
+    grid.density = dens.data_ptr()
+    grid.on_device = 1
+    imgs = [torch.zeros((q.channels, prob.n_lambda, q.ny, q.nx), dtype=torch.float64, device="cuda")
+            for q in prob.instruments]
+    ab = torch.zeros((prob.n_lambda, prob.grid.n_cells), dtype=torch.float64, device="cuda")
+    stats = torch.zeros(ctypes.sizeof(rt.rt_stats), dtype=torch.uint8, device="cuda")
+    opts = rt.rt_default_opts()
+    opts.n_norm = n_norm
+    rt.rt_launch_packets_noalloc(grid, prob.kappa, prob.albedo, prob.g, [rt.source_desc(s) for s in prob.sources],
+                                 [s.lum for s in prob.sources], [rt.instrument_desc(q) for q in prob.instruments],
+                                 [t.data_ptr() for t in imgs], ab.data_ptr(), n, first, seed, opts,
+                                 stats.data_ptr())
+    torch.cuda.synchronize()
+    st = rt.rt_stats.from_buffer_copy(bytes(stats.cpu().numpy())).as_dict()
+    return [t.cpu().numpy() for t in imgs], ab.cpu().numpy(), st
+
+
+def test_noalloc_matches_context_path_on_two_calls():
+    prob = _problem()
+    dens = torch.from_numpy(np.ascontiguousarray(prob.grid.density)).cuda()
+    n = 4000
+    for first, seed in [(0, 11), (n, 11)]:
+        gi, ga, gs = _noalloc_run(prob, dens, n, first, seed, 2 * n)
+        ri, ra, rs = _context_run(prob, n, first, seed, 2 * n)
+        for a, b in zip(gi, ri):
+            np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-20)
+        np.testing.assert_allclose(ga, ra, rtol=1e-12, atol=1e-20)
+        for key in ("crossings", "path_crossings", "events", "peeloffs", "packets"):
+            assert gs[key] == rs[key], key
+        for key in ("emitted", "escaped", "absorbed", "truncated"):
+            assert abs(gs[key] - rs[key]) <= 1e-12 * abs(rs[key]) + 1e-300, key
+        assert gs["device_flags"] == 0
+
+
+def test_noalloc_rejects_sizes_beyond_its_working_area():
+    prob = _problem()
+    dens = torch.from_numpy(np.ascontiguousarray(prob.grid.density)).cuda()
+    grid = rt.rt_grid_desc()
+    grid.kind = rt.RT_GRID_CARTESIAN
+    grid.bounds[:] = [float(b) for b in prob.grid.bounds]
+    grid.nz, grid.ny, grid.nx = prob.grid.density.shape
+    grid.density = dens.data_ptr()
+    grid.on_device = 1
+    ab = torch.zeros(1, dtype=torch.float64, device="cuda")
+    many = np.full(65, 0.5)
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_launch_packets_noalloc(grid, many, many, many * 0, [rt.source_desc(prob.sources[0])], [np.ones(65)],
+                                     [], [], ab.data_ptr(), 10)
+    assert e.value.status == rt.RT_ERR_ARG and "64" in str(e.value)
