@@ -34,6 +34,29 @@ L2_FLUSH_BYTES = 256 << 20
 # algorithmic bytes: forced-path crossing = 4 B density + 16 B FP64 absorption RMW;
 # peel-off crossing = 4 B density; peel-off deposit = 16 B FP64 pixel RMW
 BYTES_PATH_CROSSING, BYTES_PEEL_CROSSING, BYTES_DEPOSIT = 20, 4, 16
+# DRAM bytes (read + write) per packet of the forward kernel, from an ncu
+# capture of one 2e6-packet launch of this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum = 69.505 GB), valid only for the kernel sources whose
+# hash is given; the per-launch traffic is this figure times the packets.
+TRAFFIC_CAPTURE = {"sources_sha256_16": "6a5417c8209c9bfd", "bytes_per_packet": 69505258496 / 2e6}
+KERNEL_SOURCES = ["paper_1410_1629_gb300/csrc/rt_forward.cu", "paper_1410_1629_gb300/csrc/rt_device.cuh",
+                  "paper_1410_1629_gb300/csrc/rt_internal.h"]
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(packets):
+    """Per-launch DRAM traffic from the stored capture, or None if the kernel changed since."""
+    if kernel_sources_hash() != TRAFFIC_CAPTURE["sources_sha256_16"]:
+        return None
+    return TRAFFIC_CAPTURE["bytes_per_packet"] * packets
 
 
 def workload(packets=None):
@@ -112,18 +135,19 @@ class ClockSampler:
 
 
 def oracle_sample(prob, seconds, threads):
-    """Time the oracle (as it stands) on a bounded sample of the workload."""
+    """Time the oracle (as it stands) on a bounded sample of the workload: the
+    sample grows until one run takes about `seconds` (runs include the
+    oracle's fixed set-up, so the rate is measured on the final run only)."""
     from oracle import oracle as O
     O.build()
-    probe = 50
-    t0 = time.perf_counter()
-    O.run(prob, probe, n_threads=threads, n_norm=prob.run.n_per_lambda)
-    dt = time.perf_counter() - t0
-    per_packet = dt / (probe * prob.n_lambda)
-    n = int(max(probe, min(prob.run.n_per_lambda, seconds / max(per_packet, 1e-9) / prob.n_lambda)))
-    t0 = time.perf_counter()
-    r = O.run(prob, n, n_threads=threads, n_norm=prob.run.n_per_lambda)
-    dt = time.perf_counter() - t0
+    n = 50
+    while True:
+        t0 = time.perf_counter()
+        r = O.run(prob, n, n_threads=threads, n_norm=prob.run.n_per_lambda)
+        dt = time.perf_counter() - t0
+        if dt >= 0.6 * seconds or n >= prob.run.n_per_lambda:
+            break
+        n = int(min(prob.run.n_per_lambda, max(2 * n, n * 0.9 * seconds / max(dt, 1e-3))))
     packets = n * prob.n_lambda
     return packets / dt, packets, dt, int(r["counters"][0])
 
@@ -162,9 +186,8 @@ def run_gpu(args, prob, world, rank, local_rank):
     device = local_rank
     torch.cuda.set_device(device)
     stream = torch.cuda.Stream(device)
-    n = prob.run.n_per_lambda
-    first = rank * n
-    n_norm = world * n
+    from paper_1410_1629_gb300.sharding import shard
+    first, n, n_norm = shard(rank, world, prob.run.n_per_lambda)
     sim = rt.Simulation(prob, device=device)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{device}")
 
@@ -278,7 +301,8 @@ def run_gpu(args, prob, world, rank, local_rank):
                 "config": workload_config(prob, world),
                 "crossings_per_s": world * crossings_step * args.steps / t_total,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": args.traffic,
+                             "frac": achieved / peak,
+                             "traffic": args.traffic if args.traffic is not None else captured_traffic(packets_step),
                              "peak_source": f"{peak_kind} hbm_gbs",
                              "algorithmic_bytes_per_launch": int(bytes_launch),
                              "kernel": "k_forward<cartesian>", "launch_ms": 1e3 * mean_launch},
