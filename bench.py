@@ -40,7 +40,7 @@ BYTES_PATH_CROSSING, BYTES_PEEL_CROSSING, BYTES_DEPOSIT = 20, 4, 16
 # hash is given; the per-launch traffic is this figure times the packets.
 TRAFFIC_CAPTURE = {"sources_sha256_16": "6a5417c8209c9bfd", "bytes_per_packet": 69505258496 / 2e6}
 KERNEL_SOURCES = ["paper_1410_1629_gb300/csrc/rt_forward.cu", "paper_1410_1629_gb300/csrc/rt_device.cuh",
-                  "paper_1410_1629_gb300/csrc/rt_internal.h"]
+                  "paper_1410_1629_gb300/csrc/rt_internal.h", "paper_1410_1629_gb300/csrc/rt_transport.cuh"]
 
 
 def kernel_sources_hash():
@@ -52,22 +52,33 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def captured_traffic(packets):
-    """Per-launch DRAM traffic from the stored capture, or None if the kernel changed since."""
-    if kernel_sources_hash() != TRAFFIC_CAPTURE["sources_sha256_16"]:
+def captured_traffic(packets, workload_name="disk_galaxy"):
+    """Per-launch DRAM traffic from the stored capture (disk-galaxy workload),
+    or None if the kernel changed since or another workload runs."""
+    if workload_name != "disk_galaxy" or kernel_sources_hash() != TRAFFIC_CAPTURE["sources_sha256_16"]:
         return None
     return TRAFFIC_CAPTURE["bytes_per_packet"] * packets
 
 
-def workload(packets=None):
+def workload(packets=None, name="disk_galaxy"):
     from paper_1410_1629_gb300 import workloads as W
-    if packets:
-        return W.disk_galaxy(n_packets_total=int(packets))
-    return W.disk_galaxy()
+    kw = {"n_packets_total": int(packets)} if packets else {}
+    if name == "clumpy_octree":
+        return W.clumpy_octree(**kw)
+    return W.disk_galaxy(**kw)
 
 
 def workload_config(prob, world):
     packets = prob.run.n_per_lambda * prob.n_lambda
+    if prob.grid.kind == "octree":
+        return {"workload": f"clumpy medium on an adaptive octree: {prob.grid.n_cells} leaves "
+                            f"({prob.meta['nodes']} nodes, max level 10, delta {prob.meta['delta']:.2e}), "
+                            f"Plummer bulge + exponential disk, {prob.n_lambda} wavelengths, {packets:.0e} "
+                            f"packets/step per GPU, 2 frames 1024^2 at i=0/90 deg",
+                "grid": "octree float32 leaves", "n_lambda": prob.n_lambda,
+                "packets_per_step_per_gpu": int(packets),
+                "l2": "flushed between timed steps (256 MiB write)",
+                "parallelism": f"packet-id ranges sharded over {world} GPU(s), no collective on the data path"}
     return {"workload": f"edge-on disk galaxy: 256^3 cartesian grid, 10 wavelengths 0.15-2.2 um, {packets:.0e} "
                         f"packets/step ({prob.run.n_per_lambda:.0e} per wavelength) per GPU, 3 frames 512^2 at "
                         f"i=0/60/90 deg",
@@ -253,10 +264,7 @@ def run_gpu(args, prob, world, rank, local_rank):
             for i in range(e2e_steps + 1):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                d = rt.rt_grid_desc()
-                d.kind = rt.RT_GRID_CARTESIAN
-                d.bounds[:] = [float(b) for b in prob.grid.bounds]
-                d.nz, d.ny, d.nx = prob.grid.density.shape
+                d, keep = rt.grid_desc(prob.grid)
                 d.density = dens_host.data_ptr()
                 rt.rt_create_grid(ctx, d)
                 rt.rt_set_optics(ctx, 0, prob.kappa, prob.albedo, prob.g, prob.wavelengths)
@@ -302,10 +310,11 @@ def run_gpu(args, prob, world, rank, local_rank):
                 "crossings_per_s": world * crossings_step * args.steps / t_total,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak,
-                             "traffic": args.traffic if args.traffic is not None else captured_traffic(packets_step),
+                             "traffic": args.traffic if args.traffic is not None else captured_traffic(packets_step, args.workload),
                              "peak_source": f"{peak_kind} hbm_gbs",
                              "algorithmic_bytes_per_launch": int(bytes_launch),
-                             "kernel": "k_forward<cartesian>", "launch_ms": 1e3 * mean_launch},
+                             "kernel": "k_forward_" + ("octree" if prob.grid.kind == "octree" else "cartesian"),
+                             "launch_ms": 1e3 * mean_launch},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
                 "clocks": clk,
                 "checks": {"conservation_rel": conservation, "path_crossings": int(path_cross),
@@ -325,6 +334,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-step-seconds", type=float, default=8.0)
+    ap.add_argument("--workload", default="disk_galaxy", choices=["disk_galaxy", "clumpy_octree"],
+                    help="disk_galaxy (the headline workload) or clumpy_octree")
     ap.add_argument("--packets", type=float, default=None,
                     help="packets per step (default 1e8, the workload's size); smaller values are for profiling")
     ap.add_argument("--traffic", type=float, default=None,
@@ -335,7 +346,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    prob = workload(args.packets)
+    prob = workload(args.packets, args.workload)
     if args.impl == "reference":
         run_reference(args, prob, world, rank)
         return

@@ -73,7 +73,7 @@ enum { RT_DEPOSIT_NEAREST = 0, RT_DEPOSIT_BILINEAR = 1 };
  *       the index of the first of n's eight contiguous children (octant
  *       o = bit0 x-upper | bit1 y-upper | bit2 z-upper), child[n] < 0 marks a
  *       leaf with leaf id -(child[n] + 1); density float32 [n_leaves];
- *       cell id = leaf id.  Depth at most 24.
+ *       cell id = leaf id.  Depth at most 21.
  *   bounds: xmin, xmax, ymin, ymax, zmin, zmax (FP64; the kernels use FP32).
  *   Pointers are host pointers unless on_device = 1.  Data is copied. */
 typedef struct {

@@ -464,6 +464,7 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   }
   p.density = c->d_density;
   p.child = c->d_child;
+  p.n_nodes = c->n_nodes;
   p.n_cells = c->n_cells;
   p.n_lambda = c->n_lambda;
   p.n_sources = (int)c->sources.size();

@@ -1,622 +1,13 @@
-// Forward transport kernel for cartesian grids: emission, peel-off, forced
-// scattering with continuous absorption, Henyey-Greenstein scattering and
-// termination for a stream of photon packets (SKIRT paper, Sect. 1 and
-// Sect. 2.2-2.4).
-//
-// Execution model.  A persistent grid of warps; every lane carries one packet
-// through a small state machine.  The expensive part of the method is the
-// straight cell walk: per packet a peel-off walk per instrument at emission and
-// at every scattering, and two walks of the forced path per scattering (the
-// first accumulates the optical depth to the boundary and deposits absorption,
-// the second stops at the interaction).  The main loop advances every walking
-// lane by exactly one cell crossing per iteration, whichever of these walks it
-// is in, so the warp stays converged on the hot path.  The per-event work
-// (emission, forced-scattering inversion, weight update, deposits, the
-// Henyey-Greenstein draw, fetching the next packet) is deferred until enough
-// lanes of the warp need it and is then done for those lanes together;
-// packets are fetched with one atomic per warp.
-//
-// Precision.  Geometry, the walk and the phase function are FP32.  The
-// cumulative optical depth of the forced path is held as an unevaluated sum
-// of two FP32 numbers updated by an error-free two-sum (about 2^-46 relative),
-// bit-identical in both walks, so the interaction cell is always found; the
-// inversion remainder, E = exp(-tau), tau*, packet weights and every
-// accumulator are FP64.
-#include <cuda_runtime.h>
-
-#include "rt_device.cuh"
-#include "rt_internal.h"
+// Forward transport on cartesian grids: the state-machine kernel of
+// rt_transport.cuh instantiated with the cartesian cell walk.
+#include "rt_transport.cuh"
 
 namespace rtk {
 
 namespace {
-
-constexpr int kBlock = 256;
-// Resident blocks per SM the register allocation aims at (3 x 256 threads).
-#ifndef RT_FWD_MIN_BLOCKS
-#define RT_FWD_MIN_BLOCKS 3
-#endif
-
-enum Phase : int {
-  kFetch = 0,      // needs a new packet
-  kPeelEmit = 1,   // peel-off walk at emission (instrument q)
-  kPath1 = 2,      // forced path, first walk
-  kPath2 = 3,      // forced path, second walk (stops at the interaction)
-  kPeelScat = 4,   // peel-off walk at a scattering (instrument q)
-  kExit = 5        // no packets left
-};
-
-// Error-free transformation: a + b = s + e exactly (Knuth's two-sum).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bp = __fsub_rn(s, a);
-  const float ap = __fsub_rn(s, bp);
-  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+__global__ void __launch_bounds__(tr::kBlock, RT_FWD_MIN_BLOCKS) k_forward_cartesian(const FwdParams P) {
+  tr::forward_body<tr::CartGrid>(P);
 }
-
-__device__ __forceinline__ float inv_or_zero(float d) { return d != 0.0f ? 1.0f / d : 0.0f; }
-
-// Exact widening of a positive normal FP32 value to FP64 with integer
-// operations (rebias the exponent by 1023 - 127 and shift the significand),
-// keeping the per-crossing path off GB300's low-rate FP64 pipe.  Zero,
-// subnormal and non-finite inputs take the ordinary conversion.
-__device__ __forceinline__ double widen(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = u & 0x7f800000u;
-  if (e == 0u || e == 0x7f800000u) return (double)f;
-  const unsigned hi = ((u & 0x7fffffffu) >> 3) + 0x38000000u;
-  return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(u << 29));
-}
-
-// Uniform (r + 1/2) 2^-32 rounded to FP32 (= the FP64 value rounded), from
-// the exact 33-bit integer 2r + 1.
-__device__ __forceinline__ float u01f(uint32_t r) { return __ull2float_rn(2ull * r + 1ull) * 0x1p-33f; }
-
-// 2u - 1 rounded to FP32, exactly: (2r + 1 - 2^32) 2^-32.
-__device__ __forceinline__ float u01f_signed(uint32_t r) {
-  return __ll2float_rn((long long)(2ull * r + 1ull) - (1ll << 32)) * 0x1p-32f;
-}
-
-// L2 residency: the density grid is read at every crossing and should stay in
-// L2; absorption tallies are written once per forced-path crossing and
-// should be the first lines evicted.
-__device__ __forceinline__ float load_density(const float* p) {
-  float v;
-  asm volatile(
-      "{\n\t.reg .b64 pol;\n\t"
-      "createpolicy.fractional.L2::evict_last.b64 pol, 1.0;\n\t"
-      "ld.global.nc.L2::cache_hint.f32 %0, [%1], pol;\n\t}"
-      : "=f"(v)
-      : "l"(p));
-  return v;
-}
-
-__device__ __forceinline__ void add_absorption(double* p, double v) {
-  asm volatile(
-      "{\n\t.reg .b64 pol;\n\t"
-      "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
-      "red.global.add.L2::cache_hint.f64 [%0], %1, pol;\n\t}" ::"l"(p),
-      "d"(v)
-      : "memory");
-}
-
-// ---------------------------------------------------------------- walk state
-// Cartesian walk: current cell indices, entry parameter t of the current
-// segment and the parameters of the next plane on each axis.  The ray is
-// (origin x of the lane, inverse direction id; id_a = 0 marks d_a = 0).
-struct WalkCart {
-  int ix, iy, iz, cell;
-  float t, tx, ty, tz;
-};
-
-__device__ __forceinline__ float plane_t(const FwdParams& P, int a, int i, float xa, float ida) {
-  return (fmaf((float)i, P.d[a], P.lo[a]) - xa) * ida;
-}
-
-// Start a cartesian walk from x along d.  known: x lies in cell (ci, cj, ck);
-// otherwise locate x or find the entry point.  Returns false if the ray
-// misses the grid.
-__device__ __forceinline__ bool walk_init(const FwdParams& P, float3 x, float3 d, float3 id, bool known, int ci,
-                                          int cj, int ck, WalkCart& w) {
-  w.t = 0.0f;
-  if (known) {
-    w.ix = ci; w.iy = cj; w.iz = ck;
-  } else {
-    int entry = -1;
-    float3 p = x;
-    if (!inside_box(P, x)) {
-      const float3 ik = make_float3(id.x != 0.0f ? id.x : RT_INF, id.y != 0.0f ? id.y : RT_INF,
-                                    id.z != 0.0f ? id.z : RT_INF);
-      if (!ray_box_entry(P, x, d, ik, w.t, entry)) return false;
-      p = make_float3(fmaf(w.t, d.x, x.x), fmaf(w.t, d.y, x.y), fmaf(w.t, d.z, x.z));
-    }
-    w.ix = min(max(__float2int_rd((p.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
-    w.iy = min(max(__float2int_rd((p.y - P.lo[1]) * P.inv_d[1]), 0), P.ny - 1);
-    w.iz = min(max(__float2int_rd((p.z - P.lo[2]) * P.inv_d[2]), 0), P.nz - 1);
-    if (entry == 0) w.ix = d.x > 0.0f ? 0 : P.nx - 1;
-    if (entry == 1) w.iy = d.y > 0.0f ? 0 : P.ny - 1;
-    if (entry == 2) w.iz = d.z > 0.0f ? 0 : P.nz - 1;
-  }
-  w.tx = id.x != 0.0f ? plane_t(P, 0, w.ix + (id.x > 0.0f), x.x, id.x) : RT_INF;
-  w.ty = id.y != 0.0f ? plane_t(P, 1, w.iy + (id.y > 0.0f), x.y, id.y) : RT_INF;
-  w.tz = id.z != 0.0f ? plane_t(P, 2, w.iz + (id.z > 0.0f), x.z, id.z) : RT_INF;
-  w.cell = w.ix + P.nx * (w.iy + P.ny * w.iz);
-  return true;
-}
-
-// Move to the next cell through face `axis`; false when the ray leaves the grid.
-__device__ __forceinline__ bool walk_advance(const FwdParams& P, float3 x, float3 id, int axis, WalkCart& w) {
-  if (axis == 0) {
-    const int s = id.x > 0.0f ? 1 : -1;
-    w.ix += s;
-    if ((unsigned)w.ix >= (unsigned)P.nx) return false;
-    w.cell += s;
-    w.tx = plane_t(P, 0, w.ix + (s > 0), x.x, id.x);
-  } else if (axis == 1) {
-    const int s = id.y > 0.0f ? 1 : -1;
-    w.iy += s;
-    if ((unsigned)w.iy >= (unsigned)P.ny) return false;
-    w.cell += s * P.nx;
-    w.ty = plane_t(P, 1, w.iy + (s > 0), x.y, id.y);
-  } else {
-    const int s = id.z > 0.0f ? 1 : -1;
-    w.iz += s;
-    if ((unsigned)w.iz >= (unsigned)P.nz) return false;
-    w.cell += s * P.nx * P.ny;
-    w.tz = plane_t(P, 2, w.iz + (s > 0), x.z, id.z);
-  }
-  return true;
-}
-
-// ---------------------------------------------------------------- lane state
-struct Lane {
-  unsigned long long pid;
-  int lam, event, phase, q;
-  double L;             // weight
-  float kappa;          // extinction per unit density at this wavelength
-  float u_mu, u_phi;    // the event's Henyey-Greenstein uniforms
-  float3 x, k;          // position, direction of travel
-  int ci, cj, ck;       // cell of x (valid when has_cell)
-  bool has_cell;
-  bool walking;
-  float3 id;            // inverse direction of the current walk
-  WalkCart w;           // current cell of the walk and its exit parameters
-  float rho;            // density of the walk's current cell (loaded one crossing ahead)
-  float th, tl;         // optical depth of the current walk (pair on forced paths)
-  float aux0, aux1;     // path 1: deposit weight; path 2: tau* as a float pair, then s*
-  int hit;              // path 2: interaction cell
-};
-
-// Small per-launch tables (instruments, per-wavelength optics) copied to
-// shared memory at kernel start.
-__shared__ DevInstr S_INSTR[kMaxInstruments];
-__shared__ DevLambda S_LAM[kMaxLambda];
-
-// Per-lane tallies, one slot per thread in shared memory (no atomics).
-struct LaneTally {
-  double escaped, absorbed, truncated;
-  unsigned long long crossings, path_crossings;
-  unsigned events, peeloffs, packets, pad;
-};
-
-__device__ __forceinline__ void trace_row(const FwdParams& P, const Lane& s, int event, int cell, double L,
-                                          double tau_path, double tau_star) {
-  if (!P.trace || s.pid != P.trace_packet || s.lam != P.trace_lambda || event >= P.trace_cap) return;
-  rt_trace_row r;
-  r.event = event; r.reserved = 0; r.cell = cell;
-  r.x[0] = s.x.x; r.x[1] = s.x.y; r.x[2] = s.x.z;
-  r.k[0] = s.k.x; r.k[1] = s.k.y; r.k[2] = s.k.z;
-  r.L = L; r.tau_path = tau_path; r.tau_star = tau_star;
-  P.trace[event] = r;
-}
-
-// Start a walk from the lane's position along d; the first cell's density
-// load is issued here.
-__device__ __forceinline__ void start_walk(const FwdParams& P, Lane& s, float3 d) {
-  s.id = make_float3(inv_or_zero(d.x), inv_or_zero(d.y), inv_or_zero(d.z));
-  s.th = 0.0f;
-  s.tl = 0.0f;
-  s.walking = walk_init(P, s.x, d, s.id, s.has_cell, s.ci, s.cj, s.ck, s.w);
-  if (s.walking) s.rho = load_density(&P.density[s.w.cell]);
-}
-
-__device__ __forceinline__ float3 instr_dir(const DevInstr& I) { return make_float3(I.kobs[0], I.kobs[1], I.kobs[2]); }
-
-// Deposit a finished peel-off into instrument q's image(s).
-__device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane& s, bool scattered) {
-  const DevInstr& I = S_INSTR[s.q];
-  float phase = 1.0f;
-  if (scattered) {
-    const float g = S_LAM[s.lam].g;
-    phase = hg_phase(g, s.k.x * I.kobs[0] + s.k.y * I.kobs[1] + s.k.z * I.kobs[2]);
-  }
-  const float tau = s.th;
-  const double value = tau < 80.0f ? s.L * kInv4PiD * (double)(phase * expf(-tau))
-                                   : s.L * kInv4PiD * (double)phase * exp(-(double)tau);
-  const float fx = (s.x.x * I.ex[0] + s.x.y * I.ex[1] + s.x.z * I.ex[2] + I.off_x) * I.sx;
-  const float fy = (s.x.x * I.ey[0] + s.x.y * I.ey[1] + s.x.z * I.ey[2] + I.off_y) * I.sy;
-  const size_t plane = (size_t)I.ny * I.nx;
-  const int ch = scattered ? 2 : 1;
-  if (!I.bilinear) {
-    const float fix = floorf(fx), fiy = floorf(fy);
-    if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) return;
-    const size_t pix = (size_t)(int)fiy * I.nx + (int)fix;
-    atomicAdd(&I.image[(size_t)s.lam * plane + pix], value);
-    if (I.channels == 3) atomicAdd(&I.image[((size_t)ch * P.n_lambda + s.lam) * plane + pix], value);
-    if (P.records && (P.record_stride <= 1 || s.pid % P.record_stride == 0)) {
-      const unsigned long long slot = atomicAdd(&P.counters[4], 1ull);
-      if ((long long)slot < P.records_cap) {
-        rt_record r;
-        r.packet = s.pid; r.lambda = s.lam; r.event = scattered ? s.event : 0; r.instrument = s.q;
-        r.reserved = 0; r.pixel = (int64_t)pix; r.value = value;
-        P.records[slot] = r;
-      }
-    }
-  } else {
-    const float gx = fx - 0.5f, gy = fy - 0.5f;
-    const float x0 = floorf(gx), y0 = floorf(gy);
-    const float tx = gx - x0, ty = gy - y0;
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        const float fix = x0 + dx, fiy = y0 + dy;
-        if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) continue;
-        const double v = value * (double)((dx ? tx : 1.0f - tx) * (dy ? ty : 1.0f - ty));
-        const size_t pix = (size_t)(int)fiy * I.nx + (int)fix;
-        atomicAdd(&I.image[(size_t)s.lam * plane + pix], v);
-        if (I.channels == 3) atomicAdd(&I.image[((size_t)ch * P.n_lambda + s.lam) * plane + pix], v);
-      }
-    }
-  }
-}
-
-// Emission (Sect. 3.4): source component by luminosity (FP64 comparison of
-// the uniform with the cumulative fractions), position from its geometry and
-// an isotropic direction (FP32).
-__device__ __forceinline__ void emit(const FwdParams& P, Lane& s) {
-  const uint4 r0 = draw_block(s.pid, s.lam, 0, 0, P.seed, P.model);
-  const uint4 r1 = draw_block(s.pid, s.lam, 0, 1, P.seed, P.model);
-  int src = P.n_sources - 1;
-  if (P.n_sources > 1) {
-    const double u0 = u01(r0.x);
-    for (int i = 0; i < P.n_sources; ++i) {
-      if (u0 < P.src_cum[s.lam * P.n_sources + i]) { src = i; break; }
-    }
-  }
-  const DevSource& S = P.src[src];
-  float3 x = make_float3((float)S.center[0], (float)S.center[1], (float)S.center[2]);
-  if (S.kind == RT_SOURCE_EXPDISK) {
-    // R has density R exp(-R/hR): minus hR times the log of two uniforms
-    const float R = -(float)S.scale_r * (logf(u01f(r0.y)) + logf(u01f(r0.z)));
-    float sp, cp;
-    sincospif(2.0f * u01f(r0.w), &sp, &cp);
-    float z = -(float)S.scale_z * logf(u01f(r1.x));
-    if (r1.y < 0x80000000u) z = -z;  // u5 < 1/2
-    x.x += R * cp; x.y += R * sp; x.z += z;
-  } else if (S.kind == RT_SOURCE_PLUMMER) {
-    // enclosed mass fraction m = r^3 / (r^2 + a^2)^(3/2): r = a / sqrt(m^(-2/3) - 1)
-    const float m = u01f(r0.y);
-    const float r = (float)S.scale_r / sqrtf(expm1f(-(2.0f / 3.0f) * logf(m)));
-    const float ct = u01f_signed(r0.z), st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
-    float sp, cp;
-    sincospif(2.0f * u01f(r0.w), &sp, &cp);
-    x.x += r * st * cp; x.y += r * st * sp; x.z += r * ct;
-  }
-  s.x = x;
-  const float mu = u01f_signed(r1.z);
-  const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
-  float sp, cp;
-  sincospif(2.0f * u01f(r1.w), &sp, &cp);
-  s.k = make_float3(st * cp, st * sp, mu);
-}
-
-__device__ __forceinline__ void start_path(const FwdParams& P, Lane& s) {
-  s.phase = kPath1;
-  start_walk(P, s, s.k);
-  s.aux0 = (float)((1.0 - S_LAM[s.lam].albedo) * s.L);
-}
-
-// After the scattering peel-offs: new direction, then terminate or start the
-// next forced path.
-__device__ __forceinline__ void after_scattering(const FwdParams& P, Lane& s, LaneTally* bt) {
-  const float g = S_LAM[s.lam].g;
-  const float mu = hg_sample(g, s.u_mu);
-  float sp, cp;
-  sincospif(2.0f * s.u_phi, &sp, &cp);
-  s.k = rotate_dir(s.k, mu, sp, cp);
-  if ((P.weight_cut && s.L < P.L_cut[s.lam]) || s.event >= P.max_events) {
-    bt->truncated += s.L;
-    s.phase = kFetch;
-    return;
-  }
-  s.event += 1;
-  start_path(P, s);
-}
-
-// Per-event work for a lane whose walk has finished, or that needs a packet
-// (then `w` is its packet index).  Loops until the lane walks again, waits
-// for a packet, or has no work left.
-__device__ void control(const FwdParams& P, Lane& s, unsigned long long w, LaneTally* bt) {
-  while (true) {
-    switch (s.phase) {
-      case kFetch: {
-        if (w >= P.n_total) { s.phase = kExit; return; }
-        int lam = min((int)(__ull2float_rz(w) * P.inv_n_per_lambda), P.n_lambda - 1);
-        while (lam > 0 && (unsigned long long)lam * P.n_per_lambda > w) --lam;
-        while (lam + 1 < P.n_lambda && (unsigned long long)(lam + 1) * P.n_per_lambda <= w) ++lam;
-        s.lam = lam;
-        s.pid = P.first_id + (w - (unsigned long long)lam * P.n_per_lambda);
-        w = ~0ull;
-        const double L0 = P.L0[lam];
-        s.kappa = S_LAM[lam].kappa;
-        s.L = L0;
-        s.event = 0;
-        s.has_cell = false;
-        emit(P, s);
-        bt->packets += 1u;
-        trace_row(P, s, 0, -1, L0, 0.0, 0.0);
-        if (P.peel_emission && P.n_instr > 0) {
-          s.phase = kPeelEmit;
-          s.q = 0;
-          start_walk(P, s, instr_dir(S_INSTR[0]));
-        } else {
-          s.event = 1;
-          start_path(P, s);
-        }
-        break;
-      }
-      case kPeelEmit:
-      case kPeelScat: {
-        const bool scattered = s.phase == kPeelScat;
-        peel_deposit(P, s, scattered);
-        bt->peeloffs += 1u;
-        s.q += 1;
-        if (s.q < P.n_instr) {
-          start_walk(P, s, instr_dir(S_INSTR[s.q]));
-        } else if (!scattered) {
-          s.event = 1;
-          start_path(P, s);
-        } else {
-          after_scattering(P, s, bt);
-        }
-        break;
-      }
-      case kPath1: {
-        const double tau = (double)s.th + (double)s.tl;
-        if (!(tau > 0.0)) {
-          trace_row(P, s, s.event, -1, s.L, 0.0, 0.0);
-          bt->escaped += s.L;
-          s.phase = kFetch;
-          return;
-        }
-        const double albedo = S_LAM[s.lam].albedo;
-        const double one_minus_E = -expm1(-tau);
-        const double E = 1.0 - one_minus_E;
-        bt->escaped += s.L * E;
-        bt->absorbed += (1.0 - albedo) * s.L * one_minus_E;
-        const uint4 r = draw_block(s.pid, s.lam, s.event, 0, P.seed, P.model);
-        const double tau_star = -log1p(-u01(r.x) * one_minus_E);
-        s.u_mu = u01f(r.y);
-        s.u_phi = u01f(r.z);
-        s.aux0 = (float)tau_star;
-        s.aux1 = (float)(tau_star - (double)s.aux0);
-        s.L = albedo * s.L * one_minus_E;  // weight after the scattering
-        s.phase = kPath2;
-        start_walk(P, s, s.k);
-        break;
-      }
-      case kPath2: {
-        // the walk stopped in the interaction cell `hit`; aux0 holds s*
-        const float s_star = s.aux0;
-        const int ix = s.hit % P.nx, iy = (s.hit / P.nx) % P.ny, iz = s.hit / (P.nx * P.ny);
-        float3 x = make_float3(fmaf(s_star, s.k.x, s.x.x), fmaf(s_star, s.k.y, s.x.y), fmaf(s_star, s.k.z, s.x.z));
-        const float lo0 = fmaf((float)ix, P.d[0], P.lo[0]), hi0 = fmaf((float)(ix + 1), P.d[0], P.lo[0]);
-        const float lo1 = fmaf((float)iy, P.d[1], P.lo[1]), hi1 = fmaf((float)(iy + 1), P.d[1], P.lo[1]);
-        const float lo2 = fmaf((float)iz, P.d[2], P.lo[2]), hi2 = fmaf((float)(iz + 1), P.d[2], P.lo[2]);
-        x.x = fminf(fmaxf(x.x, lo0), hi0);
-        x.y = fminf(fmaxf(x.y, lo1), hi1);
-        x.z = fminf(fmaxf(x.z, lo2), hi2);
-        s.x = x;
-        s.ci = ix; s.cj = iy; s.ck = iz;
-        s.has_cell = true;
-        bt->events += 1u;
-        trace_row(P, s, s.event, s.hit, s.L, 0.0, 0.0);
-        if (P.peel_scatter && P.n_instr > 0) {
-          s.phase = kPeelScat;
-          s.q = 0;
-          start_walk(P, s, instr_dir(S_INSTR[0]));
-        } else {
-          after_scattering(P, s, bt);
-        }
-        break;
-      }
-      default:
-        return;
-    }
-    if (s.phase == kFetch || s.phase == kExit) return;
-    if (s.walking) return;
-  }
-}
-
-// 1 - exp(-x) for x >= 0 with a relative error below 5e-7: the alternating
-// series through x^8 for x < 1/4 (truncation below 1e-10), 1 - exp(-x) above.
-__device__ __forceinline__ float one_minus_exp_neg(float x) {
-  if (x < 0.25f) {
-    float p = fmaf(x, -1.0f / 40320.0f, 1.0f / 5040.0f);
-    p = fmaf(x, p, -1.0f / 720.0f);
-    p = fmaf(x, p, 1.0f / 120.0f);
-    p = fmaf(x, p, -1.0f / 24.0f);
-    p = fmaf(x, p, 1.0f / 6.0f);
-    p = fmaf(x, p, -0.5f);
-    p = fmaf(x, p, 1.0f);
-    return x * p;
-  }
-  return 1.0f - expf(-x);
-}
-
-// One cell crossing of the lane's current walk.  Written with selects rather
-// than branches where lanes in different walks (peel-off, forced path 1 or 2)
-// share the step, so the warp issues it once.
-__device__ __forceinline__ void walk_step(const FwdParams& P, Lane& s, unsigned& n_path, unsigned& n_peel) {
-  WalkCart& w = s.w;
-  // exit face: the first axis with the smallest exit parameter
-  const bool by = w.ty < w.tx;
-  const float txy = by ? w.ty : w.tx;
-  const bool bz = w.tz < txy;
-  const float te = bz ? w.tz : txy;
-  const int axis = bz ? 2 : (by ? 1 : 0);
-  const float texit = fmaxf(te, w.t);
-  const float ds = texit - w.t;
-  const float kr = s.kappa * s.rho;
-  const float dt = kr * ds;
-  // optical depth of the walk as an exact pair sum (all walks)
-  float nh, e;
-  two_sum(s.th, dt, nh, e);
-  const float nl = s.tl + e;
-  const bool path1 = s.phase == kPath1;
-  const bool path2 = s.phase == kPath2;
-  if (path2 && (nh - s.aux0) + (nl - s.aux1) > 0.0f) {
-    // interaction in this cell: s* = t_in + (tau* - tau_before) / (kappa rho);
-    // tau* - tau_before from the two pairs (aux0 - th is exact where it matters)
-    const float rem = ((s.aux0 - s.th) + s.aux1) - s.tl;
-    s.aux0 = w.t + rem / kr;
-    s.hit = w.cell;
-    s.walking = false;
-    return;
-  }
-  if (path1 && dt > 0.0f) {
-    // continuous absorption: (1 - albedo) L exp(-tau_before) (1 - exp(-dtau))
-    const float dep = s.aux0 * __expf(-s.th) * one_minus_exp_neg(dt);
-    add_absorption(&P.absorption[(size_t)s.lam * P.n_cells + w.cell], widen(dep));
-  }
-  s.th = nh;
-  s.tl = nl;
-  n_path += path1 ? 1u : 0u;
-  n_peel += (path1 || path2) ? 0u : 1u;
-  // advance through the exit face
-  w.t = texit;
-  const float ida = bz ? s.id.z : (by ? s.id.y : s.id.x);
-  const int step = ida > 0.0f ? 1 : -1;
-  const int ia = (bz ? w.iz : (by ? w.iy : w.ix)) + step;
-  const int na = bz ? P.nz : (by ? P.ny : P.nx);
-  if ((unsigned)ia >= (unsigned)na) {
-    s.walking = false;
-    if (path2) {
-      // not reachable: the pair sums of both walks are identical and tau* is
-      // below the path's optical depth; keep the packet at the path's end
-      atomicOr(P.flags, kFlagNoInteraction);
-      s.aux0 = texit;
-      s.hit = w.cell;
-    }
-    return;
-  }
-  w.cell += step * (bz ? P.nx * P.ny : (by ? P.nx : 1));
-  const float xa = bz ? s.x.z : (by ? s.x.y : s.x.x);
-  const float da = bz ? P.d[2] : (by ? P.d[1] : P.d[0]);
-  const float loa = bz ? P.lo[2] : (by ? P.lo[1] : P.lo[0]);
-  const float t_new = (fmaf((float)(ia + (step > 0)), da, loa) - xa) * ida;
-  w.ix = (axis == 0) ? ia : w.ix;
-  w.iy = (axis == 1) ? ia : w.iy;
-  w.iz = (axis == 2) ? ia : w.iz;
-  w.tx = (axis == 0) ? t_new : w.tx;
-  w.ty = (axis == 1) ? t_new : w.ty;
-  w.tz = (axis == 2) ? t_new : w.tz;
-  s.rho = load_density(&P.density[w.cell]);  // consumed by the next crossing
-}
-
-__global__ void __launch_bounds__(kBlock, RT_FWD_MIN_BLOCKS) k_forward_cartesian(const FwdParams P) {
-  __shared__ LaneTally tally[kBlock];
-  for (int i = threadIdx.x; i < P.n_instr; i += kBlock) S_INSTR[i] = P.instr[i];
-  for (int i = threadIdx.x; i < P.n_lambda; i += kBlock) S_LAM[i] = P.lam[i];
-  __syncthreads();
-  LaneTally* bt = &tally[threadIdx.x];
-  bt->escaped = bt->absorbed = bt->truncated = 0.0;
-  bt->crossings = bt->path_crossings = 0ull;
-  bt->events = bt->peeloffs = bt->packets = 0u;
-  const unsigned lane = threadIdx.x & 31u;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  Lane s;
-  s.phase = kFetch;
-  s.walking = false;
-  unsigned n_path = 0, n_peel = 0;
-  // optional execution counters (warp leader only)
-  const bool prof = P.profile != nullptr && lane == 0;
-  unsigned long long c_iter = 0, c_walk_lanes = 0, c_rounds = 0, c_round_lanes = 0, cyc_ctl = 0, cyc_walk = 0;
-  while (true) {
-    const bool idle = !s.walking && s.phase != kExit;
-    const unsigned need = __ballot_sync(0xffffffffu, idle);
-    const unsigned walkers = __ballot_sync(0xffffffffu, s.walking);
-    if (need == 0u && walkers == 0u) break;
-    long long t0 = 0;
-    if (prof) { ++c_iter; t0 = clock64(); }
-    if (walkers == 0u || __popc(need) >= P.control_min) {
-      if (prof) { ++c_rounds; c_round_lanes += __popc(need); }
-      // packets for every lane that needs one: one atomic per warp
-      const unsigned fetch = __ballot_sync(0xffffffffu, idle && s.phase == kFetch);
-      unsigned long long w = ~0ull;
-      if (fetch) {
-        unsigned long long base = 0;
-        const int leader = __ffs(fetch) - 1;
-        if ((int)lane == leader) base = atomicAdd(P.work_counter, (unsigned long long)__popc(fetch));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (idle && s.phase == kFetch) w = base + __popc(fetch & lt_mask);
-      }
-      if (idle) control(P, s, w, bt);
-      if ((n_path | n_peel) & 0xC0000000u) {  // keep the 32-bit lane counters far from overflow
-        bt->crossings += (unsigned long long)n_path + n_peel;
-        bt->path_crossings += n_path;
-        n_path = n_peel = 0;
-      }
-    }
-    long long t1 = 0;
-    if (prof) { t1 = clock64(); cyc_ctl += t1 - t0; }
-    const unsigned stepping = __ballot_sync(0xffffffffu, s.walking);
-    if (s.walking) walk_step(P, s, n_path, n_peel);
-    if (prof) { c_walk_lanes += __popc(stepping); cyc_walk += clock64() - t1; }
-  }
-  if (prof) {
-    atomicAdd(&P.profile[0], c_iter);
-    atomicAdd(&P.profile[1], c_walk_lanes);
-    atomicAdd(&P.profile[2], c_rounds);
-    atomicAdd(&P.profile[3], c_round_lanes);
-    atomicAdd(&P.profile[4], cyc_ctl);
-    atomicAdd(&P.profile[5], cyc_walk);
-  }
-  bt->crossings += (unsigned long long)n_path + n_peel;
-  bt->path_crossings += n_path;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double esc = 0.0, ab = 0.0, tr = 0.0;
-    unsigned long long cr = 0, pc = 0, ev = 0, pe = 0, pk = 0;
-    for (int t = threadIdx.x; t < kBlock; t += 32) {
-      esc += tally[t].escaped; ab += tally[t].absorbed; tr += tally[t].truncated;
-      cr += tally[t].crossings; pc += tally[t].path_crossings;
-      ev += tally[t].events; pe += tally[t].peeloffs; pk += tally[t].packets;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      esc += __shfl_down_sync(0xffffffffu, esc, o);
-      ab += __shfl_down_sync(0xffffffffu, ab, o);
-      tr += __shfl_down_sync(0xffffffffu, tr, o);
-      cr += __shfl_down_sync(0xffffffffu, cr, o);
-      pc += __shfl_down_sync(0xffffffffu, pc, o);
-      ev += __shfl_down_sync(0xffffffffu, ev, o);
-      pe += __shfl_down_sync(0xffffffffu, pe, o);
-      pk += __shfl_down_sync(0xffffffffu, pk, o);
-    }
-    if (threadIdx.x == 0) {
-      atomicAdd(&P.stats[1], esc);
-      atomicAdd(&P.stats[2], ab);
-      atomicAdd(&P.stats[3], tr);
-      atomicAdd(&P.counters[0], cr);
-      atomicAdd(&P.counters[1], ev);
-      atomicAdd(&P.counters[2], pe);
-      atomicAdd(&P.counters[3], pk);
-      atomicAdd(&P.counters[5], pc);
-    }
-  }
-}
-
 }  // namespace
 
 cudaError_t launch_forward(const FwdParams& p, int grid_kind, int block_size, int num_sms, cudaStream_t stream) {
@@ -625,14 +16,14 @@ cudaError_t launch_forward(const FwdParams& p, int grid_kind, int block_size, in
   cudaError_t e = cudaMemsetAsync(p.work_counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward_cartesian, kBlock, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward_cartesian, tr::kBlock, 0);
   if (e != cudaSuccess) return e;
   per_sm = per_sm < 1 ? 1 : per_sm;
   unsigned long long blocks = (unsigned long long)num_sms * per_sm;
-  const unsigned long long useful = (p.n_total + kBlock - 1) / kBlock;
+  const unsigned long long useful = (p.n_total + tr::kBlock - 1) / tr::kBlock;
   if (blocks > useful) blocks = useful;
   if (blocks < 1) blocks = 1;
-  k_forward_cartesian<<<(unsigned)blocks, kBlock, 0, stream>>>(p);
+  k_forward_cartesian<<<(unsigned)blocks, tr::kBlock, 0, stream>>>(p);
   return cudaGetLastError();
 }
 

@@ -15,7 +15,7 @@ namespace rtk {
 constexpr int kMaxLambda = 64;
 constexpr int kMaxSources = 16;
 constexpr int kMaxInstruments = 16;
-constexpr int kMaxOctreeDepth = 24;
+constexpr int kMaxOctreeDepth = 21;
 
 // Per-wavelength optical properties (Sect. 2.3) and source luminosity total.
 struct DevLambda {
@@ -52,6 +52,7 @@ struct FwdParams {
   float lo[3], hi[3], d[3], inv_d[3];
   const float* density;
   const int32_t* child;  // octree only
+  long long n_nodes;     // octree only
   long long n_cells;
   // problem
   int n_lambda, n_sources, n_instr;

@@ -276,3 +276,116 @@ def build_octree(bounds, refine, leaf_value, max_level):
 
 def octree_problem_like(problem: Problem, grid: Grid) -> Problem:
     return replace(problem, grid=grid)
+
+
+def _spread3(v):
+    """Interleave the low 10 bits of v with two zero bits each (Morton order)."""
+    v = v.astype(np.uint64) & np.uint64(0x3FF)
+    v = (v | (v << np.uint64(16))) & np.uint64(0x30000FF)
+    v = (v | (v << np.uint64(8))) & np.uint64(0x300F00F)
+    v = (v | (v << np.uint64(4))) & np.uint64(0x30C30C3)
+    v = (v | (v << np.uint64(2))) & np.uint64(0x9249249)
+    return v
+
+
+def clumpy_octree(n_particles=1_000_000, n_samples=100_000_000, target_leaves=5_000_000, max_level=10, seed=3,
+                  n_lambda=20, n_pix=1024, n_packets_total=200_000_000, half=20.0, chunk=10_000_000):
+    """Clumpy dust on an adaptive octree (Sect. 2.4).
+
+    ``n_particles`` Gaussian clumps: centres drawn from a double-exponential
+    dust disk (h_R = 6 kpc, h_z = 0.2 kpc), widths log-uniform in 20-200 pc,
+    masses log-normal (sigma_ln = 1.5), total mass 1.  The mixture is binned
+    by drawing ``n_samples`` points from it (Morton keys at ``max_level``); a
+    node is refined while its mass exceeds delta * M_tot, with delta chosen by
+    bisection so that the tree has about ``target_leaves`` leaves.  Leaf
+    density = binned mass / leaf volume.  kappa_V makes the equivalent smooth
+    disk's face-on central optical depth 0.5.  Sources: Plummer bulge
+    (a = 1 kpc, 30 %) and exponential disk (h_R = 4, h_z = 0.35 kpc, 70 %).
+    Two ``n_pix``^2 frames at inclinations 0 and 90 degrees."""
+    if max_level > 10:
+        raise ValueError("max_level <= 10 (30-bit Morton keys)")
+    rng = np.random.default_rng(seed)
+    R = rng.gamma(2.0, 6.0, n_particles)
+    ph = rng.uniform(0.0, 2 * math.pi, n_particles)
+    cx, cy = R * np.cos(ph), R * np.sin(ph)
+    cz = rng.laplace(0.0, 0.2, n_particles)
+    sig = np.exp(rng.uniform(math.log(0.02), math.log(0.2), n_particles))
+    mass = rng.lognormal(0.0, 1.5, n_particles)
+    mass /= mass.sum()
+    cum = np.cumsum(mass)
+    n_side = 1 << max_level
+    keys = []
+    kept = 0
+    for start in range(0, n_samples, chunk):
+        m = min(chunk, n_samples - start)
+        idx = np.minimum(np.searchsorted(cum, rng.uniform(0.0, cum[-1], m)), n_particles - 1)
+        s = sig[idx]
+        px = cx[idx] + s * rng.standard_normal(m)
+        py = cy[idx] + s * rng.standard_normal(m)
+        pz = cz[idx] + s * rng.standard_normal(m)
+        inside = (np.abs(px) < half) & (np.abs(py) < half) & (np.abs(pz) < half)
+        ix = ((px[inside] + half) * (n_side / (2 * half))).astype(np.int64).clip(0, n_side - 1)
+        iy = ((py[inside] + half) * (n_side / (2 * half))).astype(np.int64).clip(0, n_side - 1)
+        iz = ((pz[inside] + half) * (n_side / (2 * half))).astype(np.int64).clip(0, n_side - 1)
+        keys.append((_spread3(ix) | (_spread3(iy) << np.uint64(1)) | (_spread3(iz) << np.uint64(2))).astype(np.uint32))
+        kept += int(inside.sum())
+    keys = np.sort(np.concatenate(keys))
+    weight = 1.0 / n_samples  # mass per sample (M_tot = 1, outside samples dropped)
+    # sample counts per node at every level
+    level_keys, level_counts = [], []
+    for L in range(max_level + 1):
+        k = keys >> np.uint32(3 * (max_level - L))
+        u, c = np.unique(k, return_counts=True)
+        level_keys.append(u)
+        level_counts.append(c)
+    # threshold in samples: leaves = 1 + 7 * (#nodes above threshold at levels < max_level)
+    def n_leaves(thr):
+        return 1 + 7 * sum(int((level_counts[L] > thr).sum()) for L in range(max_level))
+    lo_t, hi_t = 0.0, float(level_counts[0].max())
+    for _ in range(60):
+        mid = 0.5 * (lo_t + hi_t)
+        if n_leaves(mid) > target_leaves:
+            lo_t = mid
+        else:
+            hi_t = mid
+    thr = hi_t
+
+    def key_of(lo, level):
+        cell = np.rint((lo + half) / (2 * half) * (1 << level)).astype(np.int64)
+        return (_spread3(cell[:, 0]) | (_spread3(cell[:, 1]) << np.uint64(1)) | (_spread3(cell[:, 2]) << np.uint64(2)))
+
+    def count_of(lo, level):
+        k = key_of(lo, level)
+        u, c = level_keys[level], level_counts[level]
+        pos = np.searchsorted(u, k)
+        pos_c = np.minimum(pos, len(u) - 1)
+        return np.where((pos < len(u)) & (u[pos_c] == k), c[pos_c], 0)
+
+    level_of = {}
+
+    def refine(lo, hi, level):
+        return count_of(lo, level) > thr
+
+    def leaf_value(lo, hi):
+        size = hi[:, 0] - lo[:, 0]
+        level = np.rint(np.log2(2 * half / size)).astype(np.int64)
+        out = np.zeros(len(lo))
+        for L in np.unique(level):
+            sel = level == L
+            out[sel] = count_of(lo[sel], int(L)) * weight / (size[sel] ** 3)
+        return out
+
+    grid, llo, lhi = build_octree([-half, half] * 3, refine, leaf_value, max_level)
+    wl = np.geomspace(0.15, 2.2, n_lambda)
+    kappa, albedo, g = synthetic_optics(wl, 0.5 * 2 * math.pi * 6.0 ** 2)
+    instr = [Instrument(math.radians(inc), -math.pi / 2, 0.0, n_pix, n_pix, half, half) for inc in (0.0, 90.0)]
+    return Problem(
+        name=f"clumpy_octree_{grid.n_cells}",
+        grid=grid, wavelengths=wl, kappa=kappa, albedo=albedo, g=g,
+        sources=[Source("plummer", (0.0, 0.0, 0.0), np.full(n_lambda, 0.3), scale_r=1.0),
+                 Source("expdisk", (0.0, 0.0, 0.0), np.full(n_lambda, 0.7), scale_r=4.0, scale_z=0.35)],
+        instruments=instr,
+        run=Run(n_per_lambda=max(1, int(n_packets_total) // n_lambda)),
+        meta={"delta": thr * weight, "leaves": grid.n_cells, "nodes": int(grid.child.size),
+              "samples_inside": kept, "seed": seed},
+    )
