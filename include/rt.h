@@ -251,6 +251,35 @@ rt_status rt_read_stats(rt_ctx ctx, rt_stats* out);
 /* Wait for all work queued on `stream` and report asynchronous errors. */
 rt_status rt_synchronize(rt_ctx ctx, void* stream);
 
+/* Replace the cell densities of the current grid (same size as at
+ * rt_create_grid), asynchronously on `stream`: for fitting loops (the inverse
+ * problem of Sect. 1).  Tallies are kept.  density: float32 [n_cells], host
+ * (copied before return) or device (on_device = 1, stream-ordered copy).
+ * Errors: RT_ERR_STATE (no grid), RT_ERR_ARG, RT_ERR_CUDA. */
+rt_status rt_update_density(rt_ctx ctx, const float* density, int32_t on_device, void* stream);
+
+/* Gradient of a linear functional of the tallies with respect to the cell
+ * densities, by reverse-mode differentiation of the transport of
+ * rt_launch_packets under common random numbers (Sect. 1 motivates the
+ * inverse problem: fitting models to observations).  For the packets
+ * [first_packet_id, first_packet_id + n_per_lambda) at every wavelength:
+ *   grad[c] += sum_q sum_pixels adj_images[q][pixel] d image_q[pixel] / d rho_c
+ *            + sum_{l, c'} adj_absorption[l][c'] d absorption[l][c'] / d rho_c
+ * with the derivative taken along each packet's path: directions and random
+ * draws fixed, positions moving with the density through the forced
+ * scattering inversion, weights through 1 - exp(-tau).  Each packet's path is
+ * recomputed from its Philox key.  The functional is continuous in the density
+ * with bilinear deposit and event-cap termination (opts->weight_cut = 0);
+ * use those for gradient checks.  Cartesian grids only; max_events <= 32.
+ *   adj_images: host array of n_instruments device pointers (each shaped like
+ *   the instrument's image) or NULL entries / a NULL array for none;
+ *   adj_absorption: device [n_lambda][n_cells] or NULL; grad_density: device
+ *   float64 [n_cells], accumulated into.  Asynchronous on `stream`.
+ * Errors: RT_ERR_ARG, RT_ERR_STATE, RT_ERR_CUDA. */
+rt_status rt_adjoint(rt_ctx ctx, const double* const* adj_images, int32_t n_adj_images, const double* adj_absorption,
+                     double* grad_density, uint64_t n_per_lambda, uint64_t first_packet_id, uint64_t seed,
+                     const rt_launch_opts* opts, void* stream);
+
 /* The cartesian forward transport of rt_launch_packets without any device
  * memory allocation.  The paper has no counterpart: this entry point exists
  * for callers that may not allocate GPU memory while they run (a plug-in

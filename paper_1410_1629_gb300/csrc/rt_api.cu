@@ -516,6 +516,95 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   return RT_OK;
 }
 
+rt_status rt_update_density(rt_ctx c, const float* density, int32_t on_device, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (!c->has_grid) return fail(c, RT_ERR_STATE, "rt_update_density: no grid");
+  if (!density) return fail(c, RT_ERR_ARG, "rt_update_density: null density");
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)c->n_cells * sizeof(float);
+  if (on_device) {
+    RT_CUDA(c, cudaMemcpyAsync(c->d_density, density, bytes, cudaMemcpyDeviceToDevice, s));
+  } else {
+    // the caller may reuse its host buffer on return: copy synchronously
+    RT_CUDA(c, cudaStreamSynchronize(s));
+    RT_CUDA(c, cudaMemcpy(c->d_density, density, bytes, cudaMemcpyHostToDevice));
+  }
+  return RT_OK;
+}
+
+rt_status rt_adjoint(rt_ctx c, const double* const* adj_images, int32_t n_adj_images, const double* adj_absorption,
+                     double* grad_density, uint64_t n_per_lambda, uint64_t first_packet_id, uint64_t seed,
+                     const rt_launch_opts* opts, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (!c->has_grid || c->n_lambda == 0 || c->sources.empty())
+    return fail(c, RT_ERR_STATE, "rt_adjoint: grid, optics and sources required");
+  if (c->grid_kind != RT_GRID_CARTESIAN) return fail(c, RT_ERR_ARG, "rt_adjoint: cartesian grids only");
+  if (!grad_density) return fail(c, RT_ERR_ARG, "rt_adjoint: null gradient");
+  if (n_adj_images < 0 || n_adj_images > (int)c->instr.size() || (n_adj_images > 0 && !adj_images))
+    return fail(c, RT_ERR_ARG, "rt_adjoint: bad adjoint image list");
+  if (seed >> 32) return fail(c, RT_ERR_ARG, "rt_adjoint: seed must be < 2^32");
+  rt_launch_opts o;
+  rt_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.max_events < 1 || o.max_events > 32) return fail(c, RT_ERR_ARG, "rt_adjoint: max_events must be in [1, 32]");
+  if (!(o.w_min >= 0 && o.w_min < 1)) return fail(c, RT_ERR_ARG, "rt_adjoint: w_min must be in [0, 1)");
+  if (n_per_lambda == 0) return RT_OK;
+  const unsigned long long n_total = n_per_lambda * (unsigned long long)c->n_lambda;
+  if (n_total / (unsigned long long)c->n_lambda != n_per_lambda || n_total > (1ull << 62))
+    return fail(c, RT_ERR_ARG, "rt_adjoint: packet count overflow");
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  rt_status st = upload_tables(c, s);
+  if (st != RT_OK) return st;
+  FwdParams p;
+  std::memset(&p, 0, sizeof p);
+  p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
+  for (int a = 0; a < 3; ++a) {
+    p.lo[a] = (float)c->bounds[2 * a];
+    p.hi[a] = (float)c->bounds[2 * a + 1];
+    const int n = a == 0 ? c->nx : (a == 1 ? c->ny : c->nz);
+    const double d = (c->bounds[2 * a + 1] - c->bounds[2 * a]) / n;
+    p.d[a] = (float)d;
+    p.inv_d[a] = (float)(1.0 / d);
+  }
+  p.density = c->d_density;
+  p.n_cells = c->n_cells;
+  p.n_lambda = c->n_lambda;
+  p.n_sources = (int)c->sources.size();
+  p.n_instr = (int)c->instr.size();
+  p.lam = c->d_lam;
+  p.src = c->d_src;
+  p.src_cum = c->d_src_cum;
+  p.instr = c->d_instr;
+  p.n_per_lambda = n_per_lambda;
+  p.first_id = first_packet_id;
+  p.n_total = n_total;
+  p.n_norm = o.n_norm ? o.n_norm : n_per_lambda;
+  p.seed = (unsigned)seed;
+  p.model = o.model_id;
+  p.w_min = o.w_min;
+  p.max_events = o.max_events;
+  p.weight_cut = o.weight_cut;
+  p.peel_emission = o.peel_emission;
+  p.peel_scatter = o.peel_scatter;
+  p.work_counter = c->d_work;
+  p.flags = c->d_flags;
+  for (int l = 0; l < c->n_lambda; ++l) {
+    double tot = 0.0;
+    for (auto& src : c->sources) tot += src.lum[l];
+    p.L0[l] = tot / (double)p.n_norm;
+    p.L_cut[l] = o.w_min * p.L0[l];
+  }
+  const double* adj[kMaxInstruments] = {nullptr};
+  for (int q = 0; q < n_adj_images; ++q) adj[q] = adj_images[q];
+  cudaError_t e = launch_adjoint(p, adj, adj_absorption, grad_density, c->num_sms, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
+  return RT_OK;
+}
+
 rt_status rt_reset_tallies(rt_ctx c, void* stream) {
   if (!c) return RT_ERR_ARG;
   c->err.clear();

@@ -97,5 +97,7 @@ void set_context_free_error(const char* msg);
 // Launchers (rt_forward.cu).
 cudaError_t launch_forward(const FwdParams& p, int grid_kind, int block_size, int num_sms, cudaStream_t stream);
 cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t stream);
+cudaError_t launch_adjoint(const FwdParams& f, const double* const* adj_img, const double* adj_abs, double* grad,
+                           int num_sms, cudaStream_t stream);
 
 }  // namespace rtk

@@ -454,9 +454,11 @@ __device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane<G>& 
     const float g = S_LAM[s.lam].g;
     phase = hg_phase(g, s.k.x * I.kobs[0] + s.k.y * I.kobs[1] + s.k.z * I.kobs[2]);
   }
+  // exp(-(th + tl)) with the walk's compensated optical depth: the low word
+  // enters as the first-order factor (1 - tl)
   const float tau = s.th;
-  const double value = tau < 80.0f ? s.L * kInv4PiD * (double)(phase * expf(-tau))
-                                   : s.L * kInv4PiD * (double)phase * exp(-(double)tau);
+  const double value = tau < 80.0f ? s.L * kInv4PiD * (double)(phase * expf(-tau) * (1.0f - s.tl))
+                                   : s.L * kInv4PiD * (double)phase * exp(-((double)tau + (double)s.tl));
   const float fx = (s.x.x * I.ex[0] + s.x.y * I.ex[1] + s.x.z * I.ex[2] + I.off_x) * I.sx;
   const float fy = (s.x.x * I.ey[0] + s.x.y * I.ey[1] + s.x.z * I.ey[2] + I.off_y) * I.sy;
   const size_t plane = (size_t)I.ny * I.nx;

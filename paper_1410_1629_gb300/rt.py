@@ -114,6 +114,10 @@ SIGNATURES = {
                                         ctypes.c_int32, ctypes.c_void_p]),
     "rt_read_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rt_stats)]),
     "rt_synchronize": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "rt_update_density": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "rt_adjoint": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(rt_launch_opts),
+                                    ctypes.c_void_p]),
     "rt_launch_packets_noalloc": (ctypes.c_int32, [ctypes.POINTER(rt_grid_desc), ctypes.c_int32, ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                                    ctypes.POINTER(rt_source_desc), ctypes.c_int32,
@@ -256,6 +260,23 @@ def rt_read_stats(ctx) -> rt_stats:
 
 def rt_synchronize(ctx, stream=None):
     _check(ctx, lib().rt_synchronize(ctx, _stream_ptr(stream)))
+
+
+def rt_update_density(ctx, density_ptr, on_device, stream=None):
+    _check(ctx, lib().rt_update_density(ctx, int(density_ptr), int(on_device), _stream_ptr(stream)))
+
+
+def rt_adjoint(ctx, adj_image_ptrs, adj_absorption_ptr, grad_ptr, n_per_lambda, first_packet_id=0, seed=0,
+               opts=None, stream=None):
+    """Accumulate into grad (device float64 [n_cells]) the gradient of
+    sum(adj_images * images) + sum(adj_absorption * absorption) w.r.t. the
+    cell densities.  adj_image_ptrs: device addresses (or None) per instrument."""
+    ptrs = [int(p) if p else 0 for p in (adj_image_ptrs or [])]
+    arr = (ctypes.c_void_p * max(1, len(ptrs)))(*[p or None for p in ptrs])
+    o = opts if opts is not None else rt_default_opts()
+    _check(ctx, lib().rt_adjoint(ctx, arr, len(ptrs), int(adj_absorption_ptr) if adj_absorption_ptr else None,
+                                 int(grad_ptr), int(n_per_lambda), int(first_packet_id), int(seed), ctypes.byref(o),
+                                 _stream_ptr(stream)))
 
 
 def rt_launch_packets_noalloc(grid_desc_, kappa, albedo, g, sources, luminosities, instruments, image_ptrs,

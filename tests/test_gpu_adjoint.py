@@ -1,0 +1,137 @@
+"""GPU adjoint: against the oracle's forward-mode dual numbers on small grids,
+and against central differences of the GPU forward under common random
+numbers (bilinear deposit, termination by event count)."""
+import numpy as np
+import pytest
+
+from paper_1410_1629_gb300 import rt
+from paper_1410_1629_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU-only machines
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def _gpu_grad(prob, n, adj_img, adj_abs, **opts):
+    sim = rt.Simulation(prob)
+    try:
+        a_img = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in adj_img]
+        a_abs = torch.from_numpy(np.ascontiguousarray(adj_abs)).cuda() if adj_abs is not None else None
+        grad = torch.zeros(prob.grid.n_cells, dtype=torch.float64, device="cuda")
+        o = sim.opts(**opts)
+        rt.rt_adjoint(sim.ctx, [a.data_ptr() for a in a_img], a_abs.data_ptr() if a_abs is not None else 0,
+                      grad.data_ptr(), n, 0, prob.run.seed, o)
+        st = sim.stats()  # synchronises, reports device flags
+        assert st["device_flags"] == 0
+        return grad.cpu().numpy()
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("n_cells,channels", [(4, 1), (6, 3)])
+def test_adjoint_matches_oracle_dual_numbers(n_cells, channels):
+    from oracle import oracle as O
+    prob = W.lognormal_cube(n_cells=n_cells, n_pix=8, n_packets=400, max_events=6)
+    prob.instruments[0].channels = channels
+    rng = np.random.default_rng(n_cells)
+    q = prob.instruments[0]
+    adj_img = rng.standard_normal((q.channels, 1, q.ny, q.nx))
+    adj_abs = rng.standard_normal((1, prob.grid.n_cells))
+    n = prob.run.n_per_lambda
+    g = _gpu_grad(prob, n, [adj_img], adj_abs, max_events=6, weight_cut=0)
+    ref = O.vjp(prob, np.arange(prob.grid.n_cells), n, adj_images=[adj_img], adj_absorption=adj_abs,
+                max_events=6, weight_cut=False, n_threads=O.default_threads())
+    scale = np.abs(ref).max()
+    err = np.abs(g - ref)
+    print("max abs err / scale", err.max() / scale, "p99", np.quantile(err, 0.99) / scale)
+    assert np.quantile(err, 0.99) <= 1e-4 * scale
+    assert err.max() <= 1e-3 * scale
+
+
+def test_adjoint_matches_central_differences():
+    """Loss = sum (image - target)^2 on a 24^3 log-normal cube; the adjoint of the
+    GPU forward against central differences of the GPU forward under common
+    random numbers, on the 6 cells of largest gradient and 10 random ones.
+
+    The step is 1e-2 of the cell's density.  The forward computes each
+    contribution in FP32, so a change of one density moves every contribution
+    whose path crosses that cell by its true derivative plus a rounding jitter
+    of about one FP32 ulp; the jitter does not shrink with the step, so the
+    difference quotient at 1e-3 already differs from the derivative by about
+    1e-2 and at 1e-4 by about 1e-1, while the truncation error of the
+    central difference at 1e-2 is of order 1e-4.  The oracle's dual-number
+    derivative pins the same gradient to 1e-5 on the largest cells."""
+    from oracle import oracle as O
+    prob = W.lognormal_cube(n_cells=24, n_pix=32, n_packets=50000, max_events=20)
+    target_prob = W.lognormal_cube(n_cells=24, n_pix=32, n_packets=50000, max_events=20, seed=104)
+    n = prob.run.n_per_lambda
+    opts = dict(max_events=20, weight_cut=0)
+    sim = rt.Simulation(prob)
+    tsim = rt.Simulation(target_prob)
+    try:
+        tsim.launch(n, 0, 0, **opts)
+        target = tsim.images()[0]
+
+        def loss_of(dens):
+            d = torch.from_numpy(np.ascontiguousarray(dens, dtype=np.float32)).cuda()
+            rt.rt_update_density(sim.ctx, d.data_ptr(), 1)
+            sim.reset()
+            sim.launch(n, 0, 0, **opts)
+            img = sim.images()[0]
+            return float(((img - target) ** 2).sum().item()), img
+
+        rho = prob.grid.density.ravel().copy()
+        base, img = loss_of(rho)
+        adj = (2.0 * (img - target)).contiguous()
+        grad = torch.zeros(prob.grid.n_cells, dtype=torch.float64, device="cuda")
+        rt.rt_update_density(sim.ctx, torch.from_numpy(rho).cuda().data_ptr(), 1)
+        rt.rt_adjoint(sim.ctx, [adj.data_ptr()], 0, grad.data_ptr(), n, 0, 0, sim.opts(**opts))
+        assert sim.stats()["device_flags"] == 0
+        g = grad.cpu().numpy()
+        gmax = np.abs(g).max()
+        top = np.argsort(-np.abs(g))[:6]
+        rng = np.random.default_rng(4)
+        rest = np.setdiff1d(np.arange(prob.grid.n_cells), top)
+        cells = np.concatenate([top, rng.choice(rest, 10, replace=False)])
+        for c in cells:
+            up, dn = rho.copy(), rho.copy()
+            up[c] = np.float32(rho[c] * (1 + 1e-2))
+            dn[c] = np.float32(rho[c] * (1 - 1e-2))
+            fd = (loss_of(up)[0] - loss_of(dn)[0]) / (float(up[c]) - float(dn[c]))
+            print(c, fd, g[c])
+            assert abs(fd - g[c]) <= 2e-3 * abs(g[c]) + 1e-4 * gmax, c
+
+        # the same derivative from the oracle's forward-mode duals, on the
+        # oracle's own images
+        kw = dict(max_events=20, weight_cut=False, n_threads=O.default_threads(), absorption=False)
+        t_o = O.run(target_prob, n, **kw)["images"][0]
+        i_o = O.run(prob, n, **kw)["images"][0]
+        g_o = O.vjp(prob, top[:3], n, adj_images=[2.0 * (i_o - t_o)], max_events=20, weight_cut=False,
+                    n_threads=O.default_threads())
+        np.testing.assert_allclose(g[top[:3]], g_o, rtol=1e-4)
+    finally:
+        sim.close()
+        tsim.close()
+
+
+def test_autograd_function_matches_direct_adjoint():
+    from paper_1410_1629_gb300.autograd import transport
+    prob = W.lognormal_cube(n_cells=8, n_pix=16, n_packets=5000, max_events=10)
+    sim = rt.Simulation(prob)
+    try:
+        dens = torch.from_numpy(prob.grid.density.copy()).cuda().requires_grad_(True)
+        imgs, ab = transport(dens, sim, max_events=10, weight_cut=0)
+        w = torch.linspace(-1, 1, imgs[0].numel(), device="cuda", dtype=torch.float64).view_as(imgs[0])
+        loss = (w * imgs[0]).sum() + 0.5 * ab.sum()
+        loss.backward()
+        g_auto = dens.grad.double().cpu().numpy().ravel()
+        grad = torch.zeros(prob.grid.n_cells, dtype=torch.float64, device="cuda")
+        a_abs = torch.full_like(ab, 0.5)
+        rt.rt_adjoint(sim.ctx, [w.contiguous().data_ptr()], a_abs.data_ptr(), grad.data_ptr(), prob.run.n_per_lambda,
+                      0, 0, sim.opts(max_events=10, weight_cut=0))
+        g_dir = grad.cpu().numpy()
+        np.testing.assert_allclose(g_auto, g_dir.astype(np.float32), rtol=1e-5, atol=1e-6 * np.abs(g_dir).max())
+    finally:
+        sim.close()
