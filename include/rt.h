@@ -270,7 +270,13 @@ rt_status rt_update_density(rt_ctx ctx, const float* density, int32_t on_device,
  * scattering inversion, weights through 1 - exp(-tau).  Each packet's path is
  * recomputed from its Philox key.  The functional is continuous in the density
  * with bilinear deposit and event-cap termination (opts->weight_cut = 0);
- * use those for gradient checks.  Cartesian grids only; max_events <= 32.
+ * use those for gradient checks.  Cartesian grids only; max_events <= 256.
+ * The context keeps a device buffer of per-event records, about
+ * 200 B x (max_events + 1) per resident thread (77,824 threads on a 152-SM
+ * GPU: 0.33 GB at max_events = 20), allocated on the first call that needs
+ * more (RT_ERR_OOM if it cannot be had).  opts->profile, if not NULL, is a
+ * device uint64 array: [0] += cell crossings of all walks, [1] += crossings
+ * that deposited into grad_density.
  *   adj_images: host array of n_instruments device pointers (each shaped like
  *   the instrument's image) or NULL entries / a NULL array for none;
  *   adj_absorption: device [n_lambda][n_cells] or NULL; grad_density: device

@@ -4,22 +4,42 @@
 // directions and random draws fixed, positions moving with the density
 // through the forced-scattering inversion, weights through 1 - exp(-tau)).
 //
-// One thread per packet.  The packet's path is first replayed from its Philox
-// key (the forced path of every event, no peel-offs), storing one checkpoint
-// per event: position, carried cell, direction, weight, tau_path, tau*.  The
-// events are then swept backwards with the adjoints of the position and the
-// weight:
+// Structure.  Under common random numbers a packet's adjoint is linear in the
+// adjoints (Lb, xb) of its weight and position that flow backwards from later
+// events, so almost all of the work runs in the forward order:
 //   * peel-off at event j towards instrument q, value l = L_j P e^{-tau(x_j)} W(x_j)
-//     (W: the adjoint image interpolated like the deposit):
-//       walk 1: tau and d tau / d x (the density jumps across the crossed planes),
-//       walk 2: grad[c] -= l kappa ds_c;
-//   * forced path of event j from x_{j-1}:
-//       walk 1: optical depths, deposit adjoints, the interaction cell h,
-//       walk 2: grad[c_m] += kappa ds_m S_m with S_m the suffix sum of the
-//       adjoints of tau_i, and the plane terms of d/dx.
-// Geometry is FP32 as in the forward kernel; adjoints of position and weight
-// and every accumulator are FP64.
+//     (W: the adjoint image interpolated like the deposit): a measuring walk
+//     gives tau and d tau / d x, a depositing walk adds -l kappa ds to the
+//     crossed cells; its share of (Lb_j, xb_j) is stored with the event;
+//   * forced path j from x_{j-1}: the replay's two walks (to the boundary, to
+//     the interaction) also give the per-axis plane sums G1, GH (and, with an
+//     absorption adjoint, the deposit adjoints and G0) that the position
+//     adjoint needs, and the interaction data;
+// and then, per packet,
+//   * the backward sweep over the stored events (no walks): the total T_j of
+//     the optical-depth adjoints, the adjoint tbh_j of tau_{h-1}, the
+//     interaction-cell term and the new (Lb, xb);
+//   * one depositing walk per forced path: grad[c_m] += kappa ds_m
+//     (T_j - tbh_j [m >= h_j]) (the suffix sums of the optical-depth adjoints).
+// With n instruments a scattering costs 1 + 1/2 + 1 + 2n walks against the
+// forward's 1 + 1/2 + n.
+//
+// Execution model as in the forward kernel: persistent warps, one packet per
+// lane, every walking lane advancing one crossing per iteration whatever its
+// walk, the per-event work deferred until enough lanes need it and then done
+// in a fixed order of stages, so that lanes at the same stage run together.
+// The events of a packet are stored in the lane's slot of a device buffer.
+//
+// Precision.  The replay repeats the forward kernel's arithmetic (FP32
+// geometry and pair sums, FP64 inversion and weights), so it follows the same
+// paths.  Adjoint quantities are FP32 in exact power-of-two units (the record
+// type states them), which keeps the per-event work off GB300's low-rate FP64
+// pipe; each deposit into the FP64 gradient is an FP32 product widened and
+// rescaled exactly with integer operations.
 #include "rt_transport.cuh"
+
+#include <climits>
+#include <cmath>
 
 namespace rtk {
 
@@ -27,343 +47,606 @@ namespace {
 
 using tr::CartGrid;
 
-constexpr int kAdjBlock = 128;
-constexpr int kMaxAdjEvents = 32;
+constexpr int kAdjBlock = 256;
+constexpr float kInv4PiF = 0.0795774715459476679f;
+
+enum AdjPhase : int {
+  aFetch = 0,  // needs a new packet
+  aPeelM = 1,  // peel-off measuring walk (instrument q)
+  aPeelD = 2,  // peel-off depositing walk
+  aPath1 = 3,  // forced path, first walk (to the boundary)
+  aPath2 = 4,  // forced path, second walk (to the interaction)
+  aSweep = 5,  // the packet's events are complete: backward sweep
+  aDep = 6,    // depositing walk of forced path `event`, after the sweep
+  aExit = 7
+};
 
 struct AdjParams {
   FwdParams f;
-  const double* adj_img[kMaxInstruments];  // adjoint images, shaped like the images (or null)
-  const double* adj_abs;                   // [n_lambda][n_cells] or null
-  double* grad;                            // [n_cells]
+  const float* adj_img[kMaxInstruments];  // adjoint images in units 2^ea (or null)
+  const double* adj_abs;                  // [n_lambda][n_cells] or null (FP64, as given)
+  const unsigned long long* maxbits;      // largest |adjoint input| (FP64 bits): gives ea
+  int e0[kMaxLambda];                     // exponent of the initial weight per wavelength
+  double* grad;                           // [n_cells]
+  AdjRecord* recs;                        // [lanes][max_events + 1]
+  int rec_stride;                         // records per lane
+  unsigned long long* counters;           // optional: [0] crossings, [1] depositing crossings
 };
 
-struct Checkpoint {
-  float3 x, k;        // position after event j, direction of the forced path that follows
-  int ci, cj, ck;     // carried cell (ci < 0: locate)
-  double L;           // weight after event j
-  double tau_path;    // optical depth of the forced path that led to event j
-  double tau_star;    // its drawn tau*
-};
-
-__device__ __forceinline__ void grad_add(double* g, int cell, double v) { atomicAdd(&g[cell], v); }
-
-// Walk from x along d (known cell or located) calling f(cell, t_in, ds, kr, exit_axis, is_last).
-template <class F>
-__device__ __forceinline__ void walk(const FwdParams& P, float3 x, float3 d, bool known, const CartGrid::Cell& c,
-                                     float kappa, F&& f) {
+// The lane: one packet.
+struct ALane {
+  unsigned long long pid;
+  int lam, event, phase, q, J;
+  int eL, eLA;          // 2^eL: unit of weights; 2^eLA: unit of position and tau adjoints
+  double L;             // weight (as in the forward kernel)
+  float kappa;
+  float u_mu, u_phi;    // the event's Henyey-Greenstein uniforms
+  float3 x, k;          // position, direction of travel
+  CartGrid::Cell cell;  // cell of x (valid when has_cell)
+  bool has_cell, walking;
+  float3 d, id;         // the walk's direction and its inverse (0 for a zero component)
   CartGrid::Walk w;
-  CartGrid::Scratch sc;
-  const float3 id = make_float3(tr::inv_or_zero(d.x), tr::inv_or_zero(d.y), tr::inv_or_zero(d.z));
-  if (!CartGrid::init(P, x, d, id, known, c, w, sc)) return;
-  while (true) {
-    int axis;
-    const float te = CartGrid::exit(w, x, id, axis);
-    const float texit = fmaxf(te, w.t);
-    const float kr = kappa * __ldg(&P.density[w.cell]);
-    const int cell = w.cell;
-    const float t_in = w.t;
-    w.t = texit;
-    const bool more = CartGrid::advance(P, x, d, id, axis, w, sc);
-    if (!f(cell, t_in, texit - t_in, kr, axis, !more) || !more) return;
-  }
+  float rho;            // density of the walk's current cell
+  float th, tl;         // optical depth of the walk (pair sum)
+  float a0, a1;         // path 2: tau* as a pair, then s*; path 2 hit: a1 = tau* - tau_{h-1}
+  float3 g;             // plane sums of the walk: sum over segments of kr (e_exit - e_entry)
+  int axis_in;          // axis of the plane the current segment was entered by (-1: none)
+  int n_cross;          // crossings of the walk so far
+  int h;                // path 2: crossing index of the interaction (-1: none); deposits: split index
+  float kr_h;           // path 2: kappa rho of the interaction cell
+  float c0, c1;         // depositing walks: coefficient before / from crossing h (units 2^eLA)
+  // absorption adjoint, path 1 (FP64, true units)
+  double P, D, a_prev, e_prev;
+  double3 g0;
+  AdjRecord* rec;
+};
+
+__device__ __forceinline__ void grad_add(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 
-__device__ __forceinline__ double3 plane_dt_dx(int axis, float3 d) {
-  // d t / d x for the crossing of a plane normal to `axis` (t = (plane - x_a) / d_a)
-  const double da = axis == 0 ? d.x : (axis == 1 ? d.y : d.z);
-  const double v = -1.0 / da;
-  return make_double3(axis == 0 ? v : 0.0, axis == 1 ? v : 0.0, axis == 2 ? v : 0.0);
+// v 2^e as FP64 for FP32 v: integer operations when v is a normal number and
+// the result stays normal, the FP64 pipe otherwise.
+__device__ __forceinline__ double scaled(float v, int e) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned ex = u & 0x7f800000u;
+  const int be = (int)(ex >> 23) + 896 + e;  // biased FP64 exponent of the result
+  if (ex == 0u || ex == 0x7f800000u || be <= 0 || be >= 2047) return ldexp((double)v, e);
+  const int hi = (int)((u & 0x7fffffffu) >> 3) + (896 + e) * (1 << 20);
+  return __hiloint2double(hi | (int)(u & 0x80000000u), (int)(u << 29));
 }
 
-// The adjoint image interpolated at x like a deposit, and its gradient in x.
-__device__ __forceinline__ double adj_weight(const AdjParams& A, int q, int lam, bool scattered, float3 x,
-                                             double3& dW) {
+// v 2^-e as FP32 for FP64 v, truncating the significand, with integer
+// operations; zero below the FP32 normal range.
+__device__ __forceinline__ float narrow(double v, int e) {
+  const int hi = __double2hiint(v);
+  const unsigned lo = (unsigned)__double2loint(v);
+  const int be = (hi >> 20) & 0x7ff;
+  const int fe = be - 896 - e;  // biased FP32 exponent
+  if (be == 0x7ff || fe >= 255) return (float)ldexp(v, -e);
+  if (be == 0 || fe <= 0) return 0.0f;
+  const unsigned bits = ((unsigned)hi & 0x80000000u) | ((unsigned)fe << 23) | (((unsigned)hi & 0xfffffu) << 3) |
+                        (lo >> 29);
+  return __uint_as_float(bits);
+}
+
+// Exponent ea of the adjoint inputs (their largest magnitude is below 2^ea).
+__device__ __forceinline__ int adjoint_exponent(unsigned long long bits) {
+  const int be = (int)((bits >> 52) & 0x7ffull);
+  return be == 0 ? 0 : be - 1022;
+}
+
+// The adjoint image interpolated at x like a deposit, and its gradient in x
+// (units 2^ea).
+__device__ __forceinline__ float adj_weight(const AdjParams& A, int q, int lam, bool scattered, float3 x,
+                                            float3& dW) {
   const DevInstr& I = tr::S_INSTR[q];
-  dW = make_double3(0.0, 0.0, 0.0);
-  const double* img = A.adj_img[q];
-  if (!img) return 0.0;
+  dW = make_float3(0.0f, 0.0f, 0.0f);
+  const float* img = A.adj_img[q];
+  if (!img) return 0.0f;
   const size_t plane = (size_t)I.ny * I.nx;
-  const double* a0 = img + (size_t)lam * plane;
-  const double* a1 = I.channels == 3 ? img + ((size_t)(scattered ? 2 : 1) * A.f.n_lambda + lam) * plane : nullptr;
+  const float* a0 = img + (size_t)lam * plane;
+  const float* a1 = I.channels == 3 ? img + ((size_t)(scattered ? 2 : 1) * A.f.n_lambda + lam) * plane : nullptr;
   const float fx = (x.x * I.ex[0] + x.y * I.ex[1] + x.z * I.ex[2] + I.off_x) * I.sx;
   const float fy = (x.x * I.ey[0] + x.y * I.ey[1] + x.z * I.ey[2] + I.off_y) * I.sy;
-  auto at = [&](float fix, float fiy) -> double {
-    if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) return 0.0;
+  auto at = [&](float fix, float fiy) -> float {
+    if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) return 0.0f;
     const size_t pix = (size_t)(int)fiy * I.nx + (int)fix;
-    return a0[pix] + (a1 ? a1[pix] : 0.0);
+    return a0[pix] + (a1 ? a1[pix] : 0.0f);
   };
-  if (!I.bilinear) {
-    return at(floorf(fx), floorf(fy));  // piecewise constant in x
-  }
+  if (!I.bilinear) return at(floorf(fx), floorf(fy));  // piecewise constant in x
   const float gx = fx - 0.5f, gy = fy - 0.5f;
   const float x0 = floorf(gx), y0 = floorf(gy);
-  const double tx = gx - x0, ty = gy - y0;
-  const double a00 = at(x0, y0), a10 = at(x0 + 1, y0), a01 = at(x0, y0 + 1), a11 = at(x0 + 1, y0 + 1);
-  const double W = a00 * (1 - tx) * (1 - ty) + a10 * tx * (1 - ty) + a01 * (1 - tx) * ty + a11 * tx * ty;
-  const double dWdfx = (a10 - a00) * (1 - ty) + (a11 - a01) * ty;
-  const double dWdfy = (a01 - a00) * (1 - tx) + (a11 - a10) * tx;
-  dW.x = dWdfx * I.sx * I.ex[0] + dWdfy * I.sy * I.ey[0];
-  dW.y = dWdfx * I.sx * I.ex[1] + dWdfy * I.sy * I.ey[1];
-  dW.z = dWdfx * I.sx * I.ex[2] + dWdfy * I.sy * I.ey[2];
+  const float tx = gx - x0, ty = gy - y0;
+  const float a00 = at(x0, y0), a10 = at(x0 + 1, y0), a01 = at(x0, y0 + 1), a11 = at(x0 + 1, y0 + 1);
+  const float W = a00 * (1 - tx) * (1 - ty) + a10 * tx * (1 - ty) + a01 * (1 - tx) * ty + a11 * tx * ty;
+  const float dWdfx = ((a10 - a00) * (1 - ty) + (a11 - a01) * ty) * I.sx;
+  const float dWdfy = ((a01 - a00) * (1 - tx) + (a11 - a10) * tx) * I.sy;
+  dW.x = dWdfx * I.ex[0] + dWdfy * I.ey[0];
+  dW.y = dWdfx * I.ex[1] + dWdfy * I.ey[1];
+  dW.z = dWdfx * I.ex[2] + dWdfy * I.ey[2];
   return W;
 }
 
-__global__ void __launch_bounds__(kAdjBlock) k_adjoint(const AdjParams A) {
+__device__ __forceinline__ void start_walk(const FwdParams& P, ALane& s, float3 d) {
+  s.d = d;
+  s.id = make_float3(tr::inv_or_zero(d.x), tr::inv_or_zero(d.y), tr::inv_or_zero(d.z));
+  s.th = s.tl = 0.0f;
+  s.g = make_float3(0.0f, 0.0f, 0.0f);
+  s.axis_in = -1;
+  s.n_cross = 0;
+  CartGrid::Scratch sc;
+  s.walking = CartGrid::init(P, s.x, d, s.id, s.has_cell, s.cell, s.w, sc);
+  if (s.walking) s.rho = tr::load_density(&P.density[s.w.cell]);
+}
+
+__device__ __forceinline__ int linear_cell(const FwdParams& P, const CartGrid::Cell& c) {
+  return c.ix + P.nx * (c.iy + P.ny * c.iz);
+}
+
+// Start the peel-off walk of instrument s.q (or of a later one) from the
+// lane's position; false when no instrument is left.
+__device__ __forceinline__ bool next_peel(const AdjParams& A, ALane& s) {
+  const FwdParams& P = A.f;
+  const bool on = s.event == 0 ? P.peel_emission : P.peel_scatter;
+  for (; on && s.q < P.n_instr; ++s.q) {
+    float3 dW;
+    const float W = adj_weight(A, s.q, s.lam, s.event > 0, s.x, dW);
+    if (W == 0.0f && dW.x == 0.0f && dW.y == 0.0f && dW.z == 0.0f) continue;  // contributes nothing
+    s.phase = aPeelM;
+    start_walk(P, s, tr::instr_dir(tr::S_INSTR[s.q]));
+    return true;
+  }
+  return false;
+}
+
+template <bool kAbs>
+__device__ __forceinline__ void start_path(const AdjParams& A, ALane& s) {
+  s.phase = aPath1;
+  start_walk(A.f, s, s.k);
+  if (kAbs) {
+    s.P = s.D = s.a_prev = 0.0;
+    s.e_prev = 1.0;
+    s.g0 = make_double3(0.0, 0.0, 0.0);
+  }
+}
+
+// After the peel-offs of event s.event: the first forced path, or the new
+// direction and then termination (the sweep) or the next forced path.
+template <bool kAbs>
+__device__ __forceinline__ void after_peels(const AdjParams& A, ALane& s) {
+  const FwdParams& P = A.f;
+  if (s.event == 0) {
+    s.event = 1;
+    start_path<kAbs>(A, s);
+    return;
+  }
+  const float mu = hg_sample(tr::S_LAM[s.lam].g, s.u_mu);
+  float sp, cp;
+  sincospif(2.0f * s.u_phi, &sp, &cp);
+  s.k = rotate_dir(s.k, mu, sp, cp);
+  if ((P.weight_cut && s.L < P.L_cut[s.lam]) || s.event >= P.max_events) {
+    s.J = s.event;
+    s.phase = aSweep;
+    return;
+  }
+  s.event += 1;
+  start_path<kAbs>(A, s);
+}
+
+// ---- the stages of a control round (each for the lanes in that phase)
+
+__device__ __forceinline__ void fetch(const AdjParams& A, ALane& s, unsigned long long w) {
+  const FwdParams& P = A.f;
+  if (w >= P.n_total) { s.phase = aExit; return; }
+  int lam = min((int)(__ull2float_rz(w) * P.inv_n_per_lambda), P.n_lambda - 1);
+  while (lam > 0 && (unsigned long long)lam * P.n_per_lambda > w) --lam;
+  while (lam + 1 < P.n_lambda && (unsigned long long)(lam + 1) * P.n_per_lambda <= w) ++lam;
+  s.lam = lam;
+  s.pid = P.first_id + (w - (unsigned long long)lam * P.n_per_lambda);
+  s.kappa = tr::S_LAM[lam].kappa;
+  s.L = P.L0[lam];
+  s.eL = A.e0[lam];
+  s.eLA = s.eL + adjoint_exponent(*A.maxbits);
+  s.event = 0;
+  s.J = 0;
+  s.has_cell = false;
+  tr::emit(P, s);
+  s.q = 0;
+}
+
+// Path 1 ended: escape, or the inversion (the forward kernel's FP64 steps)
+// and the record of the path; then the second walk.
+template <bool kAbs>
+__device__ __forceinline__ void finish_path1(const AdjParams& A, ALane& s) {
+  const FwdParams& P = A.f;
+  const double tau = (double)s.th + (double)s.tl;
+  if (!(tau > 0.0)) {  // escapes: there is no event s.event
+    s.J = s.event - 1;
+    s.phase = aSweep;
+    return;
+  }
+  const double albedo = tr::S_LAM[s.lam].albedo;
+  const double omE = -expm1(-tau);
+  const uint4 rn = draw_block(s.pid, s.lam, s.event, 0, P.seed, P.model);
+  const double u = u01(rn.x);
+  const double tau_star = -log1p(-u * omE);
+  s.u_mu = tr::u01f(rn.y);
+  s.u_phi = tr::u01f(rn.z);
+  AdjRecord& r = s.rec[s.event];
+  r.x[0] = s.x.x; r.x[1] = s.x.y; r.x[2] = s.x.z;
+  r.k[0] = s.k.x; r.k[1] = s.k.y; r.k[2] = s.k.z;
+  r.cell = s.has_cell ? linear_cell(P, s.cell) : -1;
+  r.L = narrow(s.L, s.eL);
+  r.omE = (float)omE;
+  r.E = (float)(1.0 - omE);
+  r.u = tr::u01f(rn.x);
+  r.g1[0] = s.g.x; r.g1[1] = s.g.y; r.g1[2] = s.g.z;
+  if (kAbs) {
+    const double wd = (1.0 - albedo) * s.L;
+    const int ea = s.eLA - s.eL;
+    r.Tdep = narrow(s.P + wd * s.e_prev * s.a_prev, s.eLA);  // the last index: a_n = 0
+    r.D = narrow(s.D, ea);
+    r.g0[0] = narrow(s.g0.x, s.eLA); r.g0[1] = narrow(s.g0.y, s.eLA); r.g0[2] = narrow(s.g0.z, s.eLA);
+  } else {
+    r.Tdep = 0.0f;
+    r.D = 0.0f;
+    r.g0[0] = r.g0[1] = r.g0[2] = 0.0f;
+  }
+  s.L = albedo * s.L * omE;  // weight after the scattering
+  s.a0 = (float)tau_star;
+  s.a1 = (float)(tau_star - (double)s.a0);
+  s.phase = aPath2;
+  start_walk(P, s, s.k);
+  s.h = -1;
+}
+
+// Path 2 ended at the interaction: record it, move the packet, start the
+// scattering peel-offs.
+template <bool kAbs>
+__device__ __forceinline__ void finish_path2(const AdjParams& A, ALane& s) {
+  const FwdParams& P = A.f;
+  if (s.h < 0) {  // not reachable: identical pair sums in both walks and tau* < tau_path
+    atomicOr(P.flags, kFlagNoInteraction);
+    s.J = s.event - 1;
+    s.phase = aSweep;
+    return;
+  }
+  AdjRecord& r = s.rec[s.event];
+  r.h = s.h;
+  r.hit_axis = s.axis_in;
+  r.hit_cell = s.w.cell;
+  r.kr_h = s.kr_h;
+  r.rem = s.a1;
+  // segments h.. with the entry of h counted: all segments minus those before h
+  r.gh[0] = r.g1[0] - s.g.x; r.gh[1] = r.g1[1] - s.g.y; r.gh[2] = r.g1[2] - s.g.z;
+  r.dLb = 0.0f;
+  r.dxb[0] = r.dxb[1] = r.dxb[2] = 0.0f;
+  const float s_star = s.a0;
+  float3 x = make_float3(fmaf(s_star, s.k.x, s.x.x), fmaf(s_star, s.k.y, s.x.y), fmaf(s_star, s.k.z, s.x.z));
+  s.cell = CartGrid::carried(s.w);
+  CartGrid::clamp(P, s.cell, x);
+  s.x = x;
+  s.has_cell = true;
+  s.q = 0;
+  if (!next_peel(A, s)) after_peels<kAbs>(A, s);
+}
+
+// A peel-off measuring walk ended: value l = L phase e^{-tau} W / (4 pi) and
+// d tau / d x_a = -g_a / d_a; the event's share of (Lb, xb); then the
+// depositing walk, or the next peel-off.
+template <bool kAbs>
+__device__ __forceinline__ void finish_peel_measure(const AdjParams& A, ALane& s) {
+  const DevInstr& I = tr::S_INSTR[s.q];
+  float3 dW;
+  const float W = adj_weight(A, s.q, s.lam, s.event > 0, s.x, dW);
+  float phase = 1.0f;
+  if (s.event > 0) phase = hg_phase(tr::S_LAM[s.lam].g, s.k.x * I.kobs[0] + s.k.y * I.kobs[1] + s.k.z * I.kobs[2]);
+  const float pe = kInv4PiF * phase * expf(-s.th) * (1.0f - s.tl);
+  const float V = narrow(s.L, s.eL) * pe;  // units 2^eL
+  const float l = V * W;                   // units 2^eLA
+  if (s.event > 0) {
+    AdjRecord& r = s.rec[s.event];
+    r.dLb += pe * W;
+    r.dxb[0] += V * dW.x + l * s.g.x * s.id.x;
+    r.dxb[1] += V * dW.y + l * s.g.y * s.id.y;
+    r.dxb[2] += V * dW.z + l * s.g.z * s.id.z;
+  }
+  if (l != 0.0f && s.n_cross > 0) {
+    s.c0 = s.c1 = -l * s.kappa;
+    s.phase = aPeelD;
+    start_walk(A.f, s, tr::instr_dir(I));
+    s.h = INT_MAX;
+    return;
+  }
+  s.q += 1;
+  if (!next_peel(A, s)) after_peels<kAbs>(A, s);
+}
+
+template <bool kAbs>
+__device__ __forceinline__ void finish_peel_deposit(const AdjParams& A, ALane& s) {
+  s.q += 1;
+  if (!next_peel(A, s)) after_peels<kAbs>(A, s);
+}
+
+// Start the depositing walk of forced path s.event (or of a later one); the
+// lane needs a new packet when none is left.
+__device__ __forceinline__ void next_deposit(const AdjParams& A, ALane& s) {
+  const FwdParams& P = A.f;
+  for (; s.event <= s.J; ++s.event) {
+    const AdjRecord& r = s.rec[s.event];
+    s.c0 = s.kappa * r.T;
+    s.c1 = s.kappa * (r.T - r.tbh);
+    if (s.c0 == 0.0f && s.c1 == 0.0f) continue;
+    s.h = r.h;
+    s.x = make_float3(r.x[0], r.x[1], r.x[2]);
+    s.has_cell = r.cell >= 0;
+    if (s.has_cell) {
+      s.cell.ix = r.cell % P.nx;
+      s.cell.iy = (r.cell / P.nx) % P.ny;
+      s.cell.iz = r.cell / (P.nx * P.ny);
+    }
+    s.phase = aDep;
+    start_walk(P, s, make_float3(r.k[0], r.k[1], r.k[2]));
+    if (s.walking) return;
+  }
+  s.phase = aFetch;
+}
+
+// Backward sweep over the packet's events J..1 (no walks): per forced path
+// the total T of its optical-depth adjoints and the adjoint of tau_{h-1} for
+// the depositing walk, the interaction-cell term of the gradient, and the
+// adjoints of the path's start weight and position.  Then the depositing walks.
+__device__ __forceinline__ void sweep(const AdjParams& A, ALane& s) {
+  const float albedo = (float)tr::S_LAM[s.lam].albedo;
+  float Lb = 0.0f, xb0 = 0.0f, xb1 = 0.0f, xb2 = 0.0f;
+  for (int j = s.J; j >= 1; --j) {
+    AdjRecord& r = s.rec[j];
+    Lb += r.dLb;
+    xb0 += r.dxb[0]; xb1 += r.dxb[1]; xb2 += r.dxb[2];
+    const float k0 = r.k[0], k1 = r.k[1], k2 = r.k[2];
+    // x_j = x_{j-1} + s* k with s* = t_in(h) + (tau* - tau_{h-1}) / kr_h
+    const float sb = xb0 * k0 + xb1 * k1 + xb2 * k2;
+    const float krh = r.kr_h;
+    const float tsb = sb / krh;  // adjoint of tau*
+    grad_add(&A.grad[r.hit_cell], scaled(-tsb * r.rem * s.kappa / krh, s.eLA));
+    float tbh = 0.0f;
+    if (r.hit_axis >= 0) {  // t_in(h): the plane entering h, d t / d x_a = -1 / k_a
+      tbh = -tsb;
+      if (r.hit_axis == 0) xb0 -= sb / k0;
+      else if (r.hit_axis == 1) xb1 -= sb / k1;
+      else xb2 -= sb / k2;
+    }
+    // L_j = albedo L (1 - E), tau* = -ln(1 - u (1 - E)), E = exp(-tau_path)
+    const float Eb = -Lb * albedo * r.L - tsb * r.u / (1.0f - r.u * r.omE);
+    const float T = r.Tdep + tbh - r.E * Eb;
+    // the planes of the path move with x: d ds_m / d x through their parameters
+    if (k0 != 0.0f) xb0 -= (T * r.g1[0] - r.g0[0] - tbh * r.gh[0]) / k0;
+    if (k1 != 0.0f) xb1 -= (T * r.g1[1] - r.g0[1] - tbh * r.gh[1]) / k1;
+    if (k2 != 0.0f) xb2 -= (T * r.g1[2] - r.g0[2] - tbh * r.gh[2]) / k2;
+    Lb = Lb * albedo * r.omE + (1.0f - albedo) * r.D;
+    r.T = T;
+    r.tbh = tbh;
+  }
+  s.event = 1;
+  next_deposit(A, s);
+}
+
+// Per-event work of an idle lane, one stage per phase in walk order.
+template <bool kAbs>
+__device__ __forceinline__ void control(const AdjParams& A, ALane& s) {
+  if (!s.walking && s.phase == aPath1) finish_path1<kAbs>(A, s);
+  if (!s.walking && s.phase == aPath2) finish_path2<kAbs>(A, s);
+  if (!s.walking && s.phase == aPeelM) finish_peel_measure<kAbs>(A, s);
+  if (!s.walking && s.phase == aPeelD) finish_peel_deposit<kAbs>(A, s);
+  if (!s.walking && s.phase == aSweep) {
+    if (s.J >= 1) sweep(A, s); else s.phase = aFetch;
+  }
+  if (!s.walking && s.phase == aDep) {
+    s.event += 1;
+    next_deposit(A, s);
+  }
+}
+
+// One cell crossing of the lane's current walk.
+template <bool kAbs>
+__device__ __forceinline__ void step(const AdjParams& A, ALane& s, unsigned& n_cross, unsigned& n_dep) {
+  const FwdParams& P = A.f;
+  CartGrid::Walk& w = s.w;
+  int axis;
+  const float te = CartGrid::exit(w, s.x, s.id, axis);
+  const float texit = fmaxf(te, w.t);
+  const float ds = texit - w.t;
+  const float kr = s.kappa * s.rho;
+  const float dt = kr * ds;
+  float nh, e;
+  tr::two_sum(s.th, dt, nh, e);
+  const float nl = s.tl + e;
+  ++n_cross;
+  if (s.phase == aPath2 && (nh - s.a0) + (nl - s.a1) > 0.0f) {
+    // the interaction is in this segment (the forward kernel's test and remainder)
+    const float rem = ((s.a0 - s.th) + s.a1) - s.tl;
+    s.a0 = w.t + rem / kr;
+    s.a1 = rem;
+    s.kr_h = kr;
+    s.h = s.n_cross;
+    s.walking = false;
+    return;
+  }
+  // plane sums: +kr at the exit plane, -kr at the entry plane
+  s.g.x += (axis == 0 ? kr : 0.0f) - (s.axis_in == 0 ? kr : 0.0f);
+  s.g.y += (axis == 1 ? kr : 0.0f) - (s.axis_in == 1 ? kr : 0.0f);
+  s.g.z += (axis == 2 ? kr : 0.0f) - (s.axis_in == 2 ? kr : 0.0f);
+  const int cell = w.cell;
+  if (s.phase == aPeelD || s.phase == aDep) {
+    grad_add(&A.grad[cell], scaled((s.n_cross >= s.h ? s.c1 : s.c0) * ds, s.eLA));
+    ++n_dep;
+  }
+  if (kAbs && s.phase == aPath1) {
+    // deposits (1 - albedo) L (e_{m-1} - e_m) with adjoints a_m: P is the
+    // prefix of the optical-depth adjoints wd e_i (a_i - a_{i+1}), i < m
+    const double a = dt > 0.0f ? A.adj_abs[(size_t)s.lam * P.n_cells + cell] : 0.0;
+    const double e_cur = (double)(expf(-nh) * (1.0f - nl));
+    const double wd = (1.0 - tr::S_LAM[s.lam].albedo) * s.L;
+    if (s.n_cross > 0) s.P += wd * s.e_prev * (s.a_prev - a);
+    if (s.P != 0.0) grad_add(&A.grad[cell], -(double)(s.kappa * ds) * s.P);
+    const double c = (double)kr * s.P;
+    s.g0.x += (axis == 0 ? c : 0.0) - (s.axis_in == 0 ? c : 0.0);
+    s.g0.y += (axis == 1 ? c : 0.0) - (s.axis_in == 1 ? c : 0.0);
+    s.g0.z += (axis == 2 ? c : 0.0) - (s.axis_in == 2 ? c : 0.0);
+    s.D += a * (s.e_prev - e_cur);
+    s.e_prev = e_cur;
+    s.a_prev = a;
+  }
+  s.th = nh;
+  s.tl = nl;
+  s.axis_in = axis;
+  ++s.n_cross;
+  w.t = texit;
+  CartGrid::Scratch sc;
+  if (CartGrid::advance(P, s.x, s.d, s.id, axis, w, sc)) {
+    s.rho = tr::load_density(&P.density[w.cell]);
+  } else {
+    s.walking = false;
+  }
+}
+
+template <bool kAbs>
+__global__ void __launch_bounds__(kAdjBlock, 2) k_adjoint(const AdjParams A) {
   const FwdParams& P = A.f;
   for (int i = threadIdx.x; i < P.n_instr; i += kAdjBlock) tr::S_INSTR[i] = P.instr[i];
   for (int i = threadIdx.x; i < P.n_lambda; i += kAdjBlock) tr::S_LAM[i] = P.lam[i];
   __syncthreads();
-  Checkpoint ev[kMaxAdjEvents + 1];
   const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  ALane s;
+  s.phase = aFetch;
+  s.walking = false;
+  s.rec = A.recs + ((size_t)blockIdx.x * kAdjBlock + threadIdx.x) * (size_t)A.rec_stride;
+  unsigned n_cross = 0, n_dep = 0;
+  unsigned long long tot_cross = 0, tot_dep = 0;
   while (true) {
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(P.work_counter, 32ull);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= P.n_total) break;
-    const unsigned long long w = base + lane;
-    if (w < P.n_total) {
-      const int lam = (int)(w / P.n_per_lambda);
-      const unsigned long long pid = P.first_id + (w - (unsigned long long)lam * P.n_per_lambda);
-      const DevLambda LP = tr::S_LAM[lam];
-      const float kappa = LP.kappa;
-      const double albedo = LP.albedo;
-      // ---- forward replay: checkpoints of every event
-      tr::Lane<CartGrid> s;
-      s.pid = pid;
-      s.lam = lam;
-      tr::emit(P, s);
-      ev[0].x = s.x; ev[0].k = s.k; ev[0].ci = -1; ev[0].cj = ev[0].ck = 0;
-      ev[0].L = P.L0[lam]; ev[0].tau_path = 0.0; ev[0].tau_star = 0.0;
-      int J = 0;
-      for (int j = 1; j <= P.max_events && j <= kMaxAdjEvents; ++j) {
-        const Checkpoint& e0 = ev[j - 1];
-        const CartGrid::Cell c0{e0.ci, e0.cj, e0.ck};
-        float th = 0.0f, tl = 0.0f;
-        walk(P, e0.x, e0.k, e0.ci >= 0, c0, kappa, [&](int, float, float ds, float kr, int, bool) {
-          float nh, e;
-          tr::two_sum(th, kr * ds, nh, e);
-          th = nh;
-          tl += e;
-          return true;
-        });
-        const double tau = (double)th + (double)tl;
-        if (!(tau > 0.0)) break;  // escapes: no event j
-        const double omE = -expm1(-tau);
-        const uint4 r = draw_block(pid, lam, j, 0, P.seed, P.model);
-        const double tau_star = -log1p(-u01(r.x) * omE);
-        const float a0 = (float)tau_star, a1 = (float)(tau_star - (double)a0);
-        float h2 = 0.0f, l2 = 0.0f, s_star = 0.0f;
-        int hx = -1, hy = 0, hz = 0;
-        walk(P, e0.x, e0.k, e0.ci >= 0, c0, kappa, [&](int cell, float t_in, float ds, float kr, int, bool last) {
-          float nh, e;
-          tr::two_sum(h2, kr * ds, nh, e);
-          const float nl = l2 + e;
-          if ((nh - a0) + (nl - a1) > 0.0f || last) {
-            const float rem = ((a0 - h2) + a1) - l2;
-            s_star = ((nh - a0) + (nl - a1) > 0.0f) ? t_in + rem / kr : t_in + ds;
-            hx = cell % P.nx; hy = (cell / P.nx) % P.ny; hz = cell / (P.nx * P.ny);
-            return false;
-          }
-          h2 = nh;
-          l2 = nl;
-          return true;
-        });
-        float3 x = make_float3(fmaf(s_star, e0.k.x, e0.x.x), fmaf(s_star, e0.k.y, e0.x.y), fmaf(s_star, e0.k.z, e0.x.z));
-        const CartGrid::Cell hc{hx, hy, hz};
-        CartGrid::clamp(P, hc, x);
-        const float mu = hg_sample(LP.g, tr::u01f(r.y));
-        float sp, cp;
-        sincospif(2.0f * tr::u01f(r.z), &sp, &cp);
-        Checkpoint& e1 = ev[j];
-        e1.x = x;
-        e1.k = rotate_dir(e0.k, mu, sp, cp);
-        e1.ci = hx; e1.cj = hy; e1.ck = hz;
-        e1.L = albedo * e0.L * omE;
-        e1.tau_path = tau;
-        e1.tau_star = tau_star;
-        J = j;
-        if (P.weight_cut && e1.L < P.L_cut[lam]) break;
+    const bool idle = !s.walking && s.phase != aExit;
+    const unsigned need = __ballot_sync(0xffffffffu, idle);
+    const unsigned walkers = __ballot_sync(0xffffffffu, s.walking);
+    if (need == 0u && walkers == 0u) break;
+    if (walkers == 0u || __popc(need) >= P.control_min) {
+      if (idle && s.phase != aFetch) control<kAbs>(A, s);
+      // packets for every lane that needs one: one atomic per warp
+      const bool wants = !s.walking && s.phase == aFetch;
+      const unsigned fetchers = __ballot_sync(0xffffffffu, wants);
+      if (fetchers) {
+        unsigned long long base = 0;
+        const int leader = __ffs(fetchers) - 1;
+        if ((int)lane == leader) base = atomicAdd(P.work_counter, (unsigned long long)__popc(fetchers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (wants) {
+          fetch(A, s, base + __popc(fetchers & lt_mask));
+          if (s.phase != aExit && !next_peel(A, s)) after_peels<kAbs>(A, s);
+        }
       }
-      // ---- backward sweep
-      double3 xb = make_double3(0.0, 0.0, 0.0);
-      double Lb = 0.0;
-      const double* adjA = A.adj_abs ? A.adj_abs + (size_t)lam * P.n_cells : nullptr;
-      for (int j = J; j >= 0; --j) {
-        const Checkpoint& ej = ev[j];
-        const CartGrid::Cell cj{ej.ci, ej.cj, ej.ck};
-        // peel-offs from x_j
-        const bool do_peel = j == 0 ? P.peel_emission : P.peel_scatter;
-        for (int q = 0; do_peel && q < P.n_instr; ++q) {
-          const DevInstr& I = tr::S_INSTR[q];
-          const float3 kobs = make_float3(I.kobs[0], I.kobs[1], I.kobs[2]);
-          double3 dW;
-          const double W = adj_weight(A, q, lam, j > 0, ej.x, dW);
-          if (W == 0.0 && dW.x == 0.0 && dW.y == 0.0 && dW.z == 0.0) continue;
-          const float3 kin = j > 0 ? ev[j - 1].k : ej.k;
-          const double phase = j > 0 ? (double)hg_phase(LP.g, kin.x * kobs.x + kin.y * kobs.y + kin.z * kobs.z) : 1.0;
-          float tau = 0.0f;
-          double3 gx = make_double3(0.0, 0.0, 0.0);
-          float kr_prev = 0.0f;
-          int axis_prev = -1;
-          walk(P, ej.x, kobs, ej.ci >= 0, cj, kappa, [&](int, float, float ds, float kr, int axis, bool last) {
-            tau += kr * ds;
-            if (axis_prev >= 0) {  // plane between the previous and this segment
-              const double3 dt = plane_dt_dx(axis_prev, kobs);
-              const double jump = (double)kr_prev - (double)kr;
-              gx.x += dt.x * jump; gx.y += dt.y * jump; gx.z += dt.z * jump;
-            }
-            kr_prev = kr;
-            axis_prev = axis;
-            if (last) {
-              const double3 dt = plane_dt_dx(axis, kobs);
-              gx.x += dt.x * kr; gx.y += dt.y * kr; gx.z += dt.z * kr;
-            }
-            return true;
-          });
-          const double pe = kInv4PiD * phase * exp(-(double)tau);
-          const double V = ej.L * pe;
-          const double l = V * W;
-          Lb += pe * W;
-          xb.x += V * dW.x - l * gx.x;
-          xb.y += V * dW.y - l * gx.y;
-          xb.z += V * dW.z - l * gx.z;
-          walk(P, ej.x, kobs, ej.ci >= 0, cj, kappa, [&](int cell, float, float ds, float, int, bool) {
-            grad_add(A.grad, cell, -l * (double)kappa * (double)ds);
-            return true;
-          });
-        }
-        if (j == 0) break;
-        // forced path of event j from x_{j-1}
-        const Checkpoint& ep = ev[j - 1];
-        const CartGrid::Cell cp{ep.ci, ep.cj, ep.ck};
-        const double L = ep.L;
-        const double tau_path = ej.tau_path, tau_star = ej.tau_star;
-        const double omE = -expm1(-tau_path);
-        const double E = 1.0 - omE;
-        const uint4 r = draw_block(pid, lam, j, 0, P.seed, P.model);
-        const double u = u01(r.x);
-        const float a0 = (float)tau_star, a1 = (float)(tau_star - (double)a0);
-        const double wd = (1.0 - albedo) * L;
-        // walk 1: deposit adjoints, interaction cell
-        float th = 0.0f, tl = 0.0f;
-        double dL_dep = 0.0, T_dep = 0.0;
-        double e_prev = 1.0, a_prev = 0.0;
-        bool found = false;
-        int hit_cell = -1, hit_axis = -1;
-        double tau_hm1 = 0.0, kr_h = 0.0;
-        int axis_before = -1;
-        walk(P, ep.x, ep.k, ep.ci >= 0, cp, kappa, [&](int cell, float, float ds, float kr, int axis, bool) {
-          const float dt = kr * ds;
-          float nh, e;
-          tr::two_sum(th, dt, nh, e);
-          const float nl = tl + e;
-          const double a = (adjA && dt > 0.0f) ? adjA[cell] : 0.0;
-          const double e_cur = exp(-((double)nh + (double)nl));
-          // tau-adjoint of the previous index from the deposits, wd e_{m-1} (a_{m-1} - a_m)
-          // (none before the first segment: tau_0 = 0 is not a variable)
-          if (axis_before >= 0) T_dep += wd * e_prev * (a_prev - a);
-          dL_dep += a * (e_prev - e_cur);
-          if (!found && (nh - a0) + (nl - a1) > 0.0f) {
-            found = true;
-            hit_cell = cell;
-            hit_axis = axis_before;  // plane crossed at the hit cell's entry
-            tau_hm1 = (double)th + (double)tl;
-            kr_h = kr;
-          }
-          th = nh;
-          tl = nl;
-          e_prev = e_cur;
-          a_prev = a;
-          axis_before = axis;
-          return true;
-        });
-        T_dep += wd * e_prev * a_prev;  // last index: a_{n+1} = 0
-        if (!found) {  // not reachable with identical pair sums; keep the packet's derivative finite
-          atomicOr(P.flags, kFlagNoInteraction);
-          continue;
-        }
-        const double Lb_prev = Lb * albedo * omE + (1.0 - albedo) * dL_dep;
-        double Eb = -Lb * albedo * L;
-        const double sb = xb.x * ep.k.x + xb.y * ep.k.y + xb.z * ep.k.z;
-        const double tsb = sb / kr_h;  // adjoint of tau*
-        Eb += tsb * (-u / (1.0 - u * omE));
-        const double tb_path = -E * Eb;
-        const double tb_hm1 = hit_axis >= 0 ? -tsb : 0.0;
-        grad_add(A.grad, hit_cell, -sb * (tau_star - tau_hm1) * (double)kappa / (kr_h * kr_h));
-        if (hit_axis >= 0) {
-          const double3 dt = plane_dt_dx(hit_axis, ep.k);
-          xb.x += sb * dt.x; xb.y += sb * dt.y; xb.z += sb * dt.z;
-        }
-        const double T = T_dep + tb_hm1 + tb_path;
-        // walk 2: grad[c_m] += kappa ds_m S_m, plane terms of d/dx
-        th = 0.0f; tl = 0.0f;
-        double prefix = 0.0;
-        e_prev = 1.0; a_prev = 0.0;
-        double kr_prev = 0.0, S_prev = 0.0;
-        int axis_prev = -1, m = 0;
-        bool past_hit = false;
-        walk(P, ep.x, ep.k, ep.ci >= 0, cp, kappa, [&](int cell, float, float ds, float kr, int axis, bool last) {
-          const float dt = kr * ds;
-          float nh, e;
-          tr::two_sum(th, dt, nh, e);
-          const float nl = tl + e;
-          const double a = (adjA && dt > 0.0f) ? adjA[cell] : 0.0;
-          const double e_cur = exp(-((double)nh + (double)nl));
-          if (m > 0) {
-            // close index m-1: its tau-adjoint enters the prefix
-            prefix += wd * e_prev * (a_prev - a);
-            if (!past_hit && cell == hit_cell) prefix += tb_hm1;  // index m-1 is h-1
-          }
-          if (cell == hit_cell) past_hit = true;
-          const double S = T - prefix;
-          grad_add(A.grad, cell, (double)kappa * (double)ds * S);
-          if (axis_prev >= 0) {
-            const double3 dtp = plane_dt_dx(axis_prev, ep.k);
-            const double v = kr_prev * S_prev - (double)kr * S;
-            xb.x += dtp.x * v; xb.y += dtp.y * v; xb.z += dtp.z * v;
-          }
-          if (last) {
-            const double3 dte = plane_dt_dx(axis, ep.k);
-            const double v = (double)kr * S;
-            xb.x += dte.x * v; xb.y += dte.y * v; xb.z += dte.z * v;
-          }
-          kr_prev = kr;
-          S_prev = S;
-          axis_prev = axis;
-          th = nh;
-          tl = nl;
-          e_prev = e_cur;
-          a_prev = a;
-          ++m;
-          return true;
-        });
-        Lb = Lb_prev;
+      if ((n_cross | n_dep) & 0xC0000000u) {  // keep the 32-bit lane counters far from overflow
+        tot_cross += n_cross;
+        tot_dep += n_dep;
+        n_cross = n_dep = 0;
       }
     }
-    __syncwarp();
+    if (s.walking) step<kAbs>(A, s, n_cross, n_dep);
   }
+  if (A.counters) {
+    tot_cross += n_cross;
+    tot_dep += n_dep;
+    for (int o = 16; o > 0; o >>= 1) {
+      tot_cross += __shfl_down_sync(0xffffffffu, tot_cross, o);
+      tot_dep += __shfl_down_sync(0xffffffffu, tot_dep, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&A.counters[0], tot_cross);
+      atomicAdd(&A.counters[1], tot_dep);
+    }
+  }
+}
+
+// Largest magnitude of an FP64 array (as FP64 bits: non-negative doubles
+// order like their bit patterns).
+__global__ void k_absmax(const double* a, size_t n, unsigned long long* out) {
+  unsigned long long m = 0ull;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a[i]) & 0x7fffffffffffffffull;
+    m = b > m ? b : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_down_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31u) == 0u && m) atomicMax(out, m);
+}
+
+// FP32 copy of an adjoint image in units 2^ea.
+__global__ void k_to_units(const double* a, size_t n, const unsigned long long* maxbits, float* out) {
+  const int ea = adjoint_exponent(*maxbits);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)ldexp(a[i], -ea);
 }
 
 }  // namespace
 
-cudaError_t launch_adjoint(const FwdParams& f, const double* const* adj_img, const double* adj_abs, double* grad,
-                           int num_sms, cudaStream_t stream) {
-  AdjParams a;
-  a.f = f;
-  for (int q = 0; q < kMaxInstruments; ++q) a.adj_img[q] = q < f.n_instr ? adj_img[q] : nullptr;
-  a.adj_abs = adj_abs;
-  a.grad = grad;
-  cudaError_t e = cudaMemsetAsync(f.work_counter, 0, sizeof(unsigned long long), stream);
+cudaError_t adjoint_lanes(int num_sms, unsigned long long n_total, unsigned long long* lanes) {
+  int per_sm = 0, per_sm_abs = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<false>, kAdjBlock, 0);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint, kAdjBlock, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_abs, k_adjoint<true>, kAdjBlock, 0);
   if (e != cudaSuccess) return e;
+  per_sm = per_sm_abs > per_sm ? per_sm_abs : per_sm;
   per_sm = per_sm < 1 ? 1 : per_sm;
   unsigned long long blocks = (unsigned long long)num_sms * per_sm;
-  const unsigned long long useful = (f.n_total + kAdjBlock - 1) / kAdjBlock;
+  const unsigned long long useful = (n_total + kAdjBlock - 1) / kAdjBlock;
   if (blocks > useful) blocks = useful;
   if (blocks < 1) blocks = 1;
-  k_adjoint<<<(unsigned)blocks, kAdjBlock, 0, stream>>>(a);
+  *lanes = blocks * kAdjBlock;
+  return cudaSuccess;
+}
+
+cudaError_t launch_adjoint(const FwdParams& f, const double* const* adj_img, const size_t* img_elems,
+                           const double* adj_abs, double* grad, AdjRecord* recs, unsigned long long lanes,
+                           unsigned long long* counters, float* img_f, unsigned long long* maxbits,
+                           cudaStream_t stream) {
+  AdjParams a;
+  a.f = f;
+  a.adj_abs = adj_abs;
+  a.maxbits = maxbits;
+  a.grad = grad;
+  a.recs = recs;
+  a.rec_stride = f.max_events + 1;
+  a.counters = counters;
+  for (int l = 0; l < kMaxLambda; ++l) {
+    int e0 = 0;
+    if (l < f.n_lambda && f.L0[l] > 0.0) std::frexp(f.L0[l], &e0);
+    a.e0[l] = e0;
+  }
+  cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  const int rb = 256, rg = 304;
+  for (int q = 0; q < f.n_instr; ++q)
+    if (adj_img[q]) k_absmax<<<rg, rb, 0, stream>>>(adj_img[q], img_elems[q], maxbits);
+  if (adj_abs) k_absmax<<<rg, rb, 0, stream>>>(adj_abs, (size_t)f.n_lambda * (size_t)f.n_cells, maxbits);
+  size_t off = 0;
+  for (int q = 0; q < kMaxInstruments; ++q) {
+    a.adj_img[q] = nullptr;
+    if (q < f.n_instr && adj_img[q]) {
+      k_to_units<<<rg, rb, 0, stream>>>(adj_img[q], img_elems[q], maxbits, img_f + off);
+      a.adj_img[q] = img_f + off;
+      off += img_elems[q];
+    }
+  }
+  e = cudaMemsetAsync(f.work_counter, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)(lanes / kAdjBlock);
+  if (adj_abs) {
+    k_adjoint<true><<<blocks, kAdjBlock, 0, stream>>>(a);
+  } else {
+    k_adjoint<false><<<blocks, kAdjBlock, 0, stream>>>(a);
+  }
   return cudaGetLastError();
 }
 

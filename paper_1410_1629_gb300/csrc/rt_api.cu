@@ -69,6 +69,11 @@ struct rt_ctx_s {
   unsigned long long* d_work = nullptr;
   int* d_flags = nullptr;
   bool tables_dirty = true;
+  AdjRecord* d_adj = nullptr;  // adjoint event records, grown on demand
+  size_t adj_bytes = 0;
+  float* d_adj_img = nullptr;  // FP32 copies of the adjoint images, grown on demand
+  size_t adj_img_elems = 0;
+  unsigned long long* d_adj_max = nullptr;
   double emitted = 0.0;  // luminosity emitted since the last reset (host-side sum)
 };
 
@@ -254,6 +259,7 @@ rt_status rt_context_destroy(rt_ctx c) {
   free_grid(c);
   dfree(c->d_lam); dfree(c->d_src); dfree(c->d_src_cum); dfree(c->d_instr);
   dfree(c->d_stats); dfree(c->d_counters); dfree(c->d_work); dfree(c->d_flags);
+  dfree(c->d_adj); dfree(c->d_adj_img); dfree(c->d_adj_max);
   delete c;
   return RT_OK;
 }
@@ -549,7 +555,8 @@ rt_status rt_adjoint(rt_ctx c, const double* const* adj_images, int32_t n_adj_im
   rt_launch_opts o;
   rt_default_opts(&o);
   if (opts) o = *opts;
-  if (o.max_events < 1 || o.max_events > 32) return fail(c, RT_ERR_ARG, "rt_adjoint: max_events must be in [1, 32]");
+  if (o.max_events < 1 || o.max_events > kMaxAdjointEvents)
+    return fail(c, RT_ERR_ARG, "rt_adjoint: max_events must be in [1, %d]", kMaxAdjointEvents);
   if (!(o.w_min >= 0 && o.w_min < 1)) return fail(c, RT_ERR_ARG, "rt_adjoint: w_min must be in [0, 1)");
   if (n_per_lambda == 0) return RT_OK;
   const unsigned long long n_total = n_per_lambda * (unsigned long long)c->n_lambda;
@@ -592,6 +599,9 @@ rt_status rt_adjoint(rt_ctx c, const double* const* adj_images, int32_t n_adj_im
   p.peel_scatter = o.peel_scatter;
   p.work_counter = c->d_work;
   p.flags = c->d_flags;
+  if (o.control_lanes < 0 || o.control_lanes > 32) return fail(c, RT_ERR_ARG, "rt_adjoint: control_lanes in [0, 32]");
+  p.control_min = o.control_lanes ? o.control_lanes : 16;
+  p.inv_n_per_lambda = (float)(1.0 / (double)n_per_lambda);
   for (int l = 0; l < c->n_lambda; ++l) {
     double tot = 0.0;
     for (auto& src : c->sources) tot += src.lum[l];
@@ -600,7 +610,41 @@ rt_status rt_adjoint(rt_ctx c, const double* const* adj_images, int32_t n_adj_im
   }
   const double* adj[kMaxInstruments] = {nullptr};
   for (int q = 0; q < n_adj_images; ++q) adj[q] = adj_images[q];
-  cudaError_t e = launch_adjoint(p, adj, adj_absorption, grad_density, c->num_sms, s);
+  unsigned long long lanes = 0;
+  cudaError_t e = adjoint_lanes(c->num_sms, n_total, &lanes);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint occupancy");
+  const size_t need = (size_t)lanes * (size_t)(o.max_events + 1) * sizeof(AdjRecord);
+  if (need > c->adj_bytes) {
+    dfree(c->d_adj);
+    c->adj_bytes = 0;
+    e = cudaMalloc(&c->d_adj, need);
+    if (e != cudaSuccess) {
+      c->d_adj = nullptr;
+      cudaGetLastError();
+      return fail(c, RT_ERR_OOM, "rt_adjoint: %zu bytes of event records", need);
+    }
+    c->adj_bytes = need;
+  }
+  size_t elems[kMaxInstruments] = {0};
+  size_t img_total = 0;
+  for (int q = 0; q < n_adj_images; ++q) {
+    elems[q] = c->instr[q].n_elems;
+    if (adj[q]) img_total += elems[q];
+  }
+  if (img_total > c->adj_img_elems || !c->d_adj_img) {
+    dfree(c->d_adj_img);
+    c->adj_img_elems = 0;
+    e = cudaMalloc(&c->d_adj_img, (img_total ? img_total : 1) * sizeof(float));
+    if (e != cudaSuccess) {
+      c->d_adj_img = nullptr;
+      cudaGetLastError();
+      return fail(c, RT_ERR_OOM, "rt_adjoint: %zu floats of adjoint images", img_total);
+    }
+    c->adj_img_elems = img_total ? img_total : 1;
+  }
+  if (!c->d_adj_max) RT_CUDA(c, cudaMalloc(&c->d_adj_max, sizeof(unsigned long long)));
+  e = launch_adjoint(p, adj, elems, adj_absorption, grad_density, c->d_adj, lanes,
+                     reinterpret_cast<unsigned long long*>(o.profile), c->d_adj_img, c->d_adj_max, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
   return RT_OK;
 }

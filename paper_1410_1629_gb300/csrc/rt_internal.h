@@ -97,7 +97,39 @@ void set_context_free_error(const char* msg);
 // Launchers (rt_forward.cu).
 cudaError_t launch_forward(const FwdParams& p, int grid_kind, int block_size, int num_sms, cudaStream_t stream);
 cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t stream);
-cudaError_t launch_adjoint(const FwdParams& f, const double* const* adj_img, const double* adj_abs, double* grad,
-                           int num_sms, cudaStream_t stream);
+// One forced path of a packet in the adjoint (rt_adjoint.cu): what the
+// backward sweep and the path's depositing walk need.  Adjoint quantities are
+// FP32 in exact power-of-two units: weights in 2^e0 (e0 the exponent of the
+// packet's initial weight), adjoints of weights in 2^ea (ea the exponent of
+// the largest adjoint input), adjoints of positions and optical depths in
+// 2^(e0 + ea).
+struct AdjRecord {
+  float x[3], k[3];    // start of the path (the previous event's position) and its direction
+  int cell;            // linear cell of the start (-1: located by the walk)
+  int hit_cell;        // cell of the interaction
+  int h;               // crossing index of the interaction segment
+  int hit_axis;        // axis of the plane entering segment h (-1 when h = 0)
+  float kr_h;          // kappa rho of the interaction cell
+  float rem;           // tau* - tau_{h-1}
+  float L, omE, E, u;  // weight at the start, 1 - exp(-tau_path), exp(-tau_path), inversion uniform
+  float g1[3];         // plane sums of the whole path: sum over segments of kr (e_exit - e_entry)
+  float gh[3];         // the same over segments h..
+  float g0[3];         // the same weighted by the deposit-adjoint prefix (absorption adjoint)
+  float D, Tdep;       // absorption adjoint: sum a_m (e_{m-1} - e_m); sum of the deposit tau-adjoints
+  float dLb, dxb[3];   // peel-offs at the interaction: adjoints of its weight and position
+  float T, tbh;        // from the sweep: total tau-adjoint of the path, adjoint of tau_{h-1}
+};
+static_assert(sizeof(AdjRecord) == 132, "AdjRecord layout");
+constexpr int kMaxAdjointEvents = 256;
+
+// Lanes (threads) of the adjoint launch for n_total packets; the record
+// buffer holds lanes * (max_events + 1) records.
+cudaError_t adjoint_lanes(int num_sms, unsigned long long n_total, unsigned long long* lanes);
+// adj_img[q]: FP64 adjoint images of img_elems[q] elements (or null);
+// img_f: FP32 scratch of sum img_elems elements; maxbits: one device word.
+cudaError_t launch_adjoint(const FwdParams& f, const double* const* adj_img, const size_t* img_elems,
+                           const double* adj_abs, double* grad, AdjRecord* recs, unsigned long long lanes,
+                           unsigned long long* counters, float* img_f, unsigned long long* maxbits,
+                           cudaStream_t stream);
 
 }  // namespace rtk

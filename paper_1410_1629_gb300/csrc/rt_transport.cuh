@@ -500,8 +500,8 @@ __device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane<G>& 
 // Emission (Sect. 3.4): source component by luminosity (FP64 comparison of
 // the uniform with the cumulative fractions), position from its geometry and
 // an isotropic direction (FP32).
-template <class G>
-__device__ __forceinline__ void emit(const FwdParams& P, Lane<G>& s) {
+template <class LaneT>
+__device__ __forceinline__ void emit(const FwdParams& P, LaneT& s) {
   const uint4 r0 = draw_block(s.pid, s.lam, 0, 0, P.seed, P.model);
   const uint4 r1 = draw_block(s.pid, s.lam, 0, 1, P.seed, P.model);
   int src = P.n_sources - 1;
