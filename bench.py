@@ -186,6 +186,72 @@ def run_reference(args, prob, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_ratio(args, device, stream, flush):
+    """Adjoint/forward time on the differentiation workload: 64^3 log-normal
+    cube, 10^7 packets, 128^2 bilinear detector, termination after 20 events;
+    the adjoint of the L2 image loss against the image of an independent
+    field.  CUDA events on the launching stream, L2 flushed before each."""
+    import torch
+    from paper_1410_1629_gb300 import rt
+    from paper_1410_1629_gb300 import workloads as W
+    prob = W.lognormal_cube()
+    target_prob = W.lognormal_cube(seed=104)
+    n = prob.run.n_per_lambda
+    opts = dict(max_events=prob.run.max_events, weight_cut=0)
+    sim = rt.Simulation(prob, device=device)
+    tsim = rt.Simulation(target_prob, device=device)
+    try:
+        with torch.cuda.stream(stream):
+            tsim.launch(n, 0, prob.run.seed, stream=stream, **opts)
+            target = tsim.images(stream=stream)[0]
+            sim.launch(n, 0, prob.run.seed, stream=stream, **opts)
+            adj = (2.0 * (sim.images(stream=stream)[0] - target)).contiguous()
+            grad = torch.zeros(prob.grid.n_cells, dtype=torch.float64, device=f"cuda:{device}")
+            prof = torch.zeros(8, dtype=torch.int64, device=f"cuda:{device}")
+        o = sim.opts(**opts)
+        o_prof = sim.opts(profile=prof.data_ptr(), **opts)
+
+        def fwd():
+            sim.reset(stream=stream)
+            sim.launch(n, 0, prob.run.seed, stream=stream, **opts)
+
+        def bwd(o_):
+            grad.zero_()
+            rt.rt_adjoint(sim.ctx, [adj.data_ptr()], 0, grad.data_ptr(), n, 0, prob.run.seed, o_, stream.cuda_stream)
+
+        def timed(f):
+            ts = []
+            for i in range(args.warmup + min(args.steps, 3)):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    f()
+                    e1.record(stream)
+                e1.synchronize()
+                if i >= args.warmup:
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+            return sum(ts) / len(ts)
+
+        t_f = timed(fwd)
+        st = sim.stats()
+        with torch.cuda.stream(stream):
+            t_b = timed(lambda: bwd(o))
+            bwd(o_prof)
+        torch.cuda.synchronize()
+        adj_cross, dep_cross = int(prof[0].item()), int(prof[1].item())
+        flags = sim.stats()["device_flags"]
+    finally:
+        sim.close()
+        tsim.close()
+    return {"workload": "lognormal_cube_64: 64^3 cells, 1e7 packets, 128^2 bilinear detector, 20 events, "
+                        "L2 image loss against an independent field",
+            "forward_ms": 1e3 * t_f, "adjoint_ms": 1e3 * t_b, "ratio": t_b / t_f,
+            "forward_crossings": int(st["crossings"]), "adjoint_crossings": adj_cross,
+            "adjoint_deposit_crossings": dep_cross, "adjoint_crossings_per_s": adj_cross / t_b,
+            "device_flags": int(flags), "l2": "flushed before each timed launch"}
+
+
 def run_gpu(args, prob, world, rank, local_rank):
     import torch
     from paper_1410_1629_gb300 import rt
@@ -294,6 +360,10 @@ def run_gpu(args, prob, world, rank, local_rank):
                            "rt_read_images and rt_read_absorption to pinned host memory"}
     sim.close()
 
+    adjoint = None
+    if rank == 0 and world == 1 and not args.skip_adjoint:
+        adjoint = adjoint_ratio(args, device, stream, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         threads = os.cpu_count() or 1
@@ -315,7 +385,7 @@ def run_gpu(args, prob, world, rank, local_rank):
                              "algorithmic_bytes_per_launch": int(bytes_launch),
                              "kernel": "k_forward_" + ("octree" if prob.grid.kind == "octree" else "cartesian"),
                              "launch_ms": 1e3 * mean_launch},
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "adjoint": adjoint,
                 "clocks": clk,
                 "checks": {"conservation_rel": conservation, "path_crossings": int(path_cross),
                            "peel_crossings": int(peel_cross), "peeloffs": int(deposits),
@@ -331,6 +401,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-adjoint", action="store_true",
+                    help="skip the adjoint/forward measurement on the 64^3 differentiation workload")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-step-seconds", type=float, default=8.0)

@@ -48,17 +48,27 @@ namespace {
 using tr::CartGrid;
 
 constexpr int kAdjBlock = 256;
+// Resident blocks per SM the register allocation aims at.
+#ifndef RT_ADJ_MIN_BLOCKS
+#define RT_ADJ_MIN_BLOCKS 3
+#endif
 constexpr float kInv4PiF = 0.0795774715459476679f;
 
 enum AdjPhase : int {
-  aFetch = 0,  // needs a new packet
-  aPeelM = 1,  // peel-off measuring walk (instrument q)
-  aPeelD = 2,  // peel-off depositing walk
-  aPath1 = 3,  // forced path, first walk (to the boundary)
-  aPath2 = 4,  // forced path, second walk (to the interaction)
-  aSweep = 5,  // the packet's events are complete: backward sweep
-  aDep = 6,    // depositing walk of forced path `event`, after the sweep
-  aExit = 7
+  // walks (the lane walks; when the walk ends its phase names the stage that finishes it)
+  aPeelM = 0,     // peel-off measuring walk (instrument q)
+  aPeelD = 1,     // peel-off depositing walk
+  aPath1 = 2,     // forced path, first walk (to the boundary)
+  aPath2 = 3,     // forced path, second walk (to the interaction)
+  aDep = 4,       // depositing walk of forced path `event`, after the sweep
+  // pending work between walks
+  aFetch = 5,     // needs a new packet
+  aPeelScan = 6,  // find the next instrument from instrument q
+  aAfter = 7,     // after the peel-offs of event `event`
+  aSweep = 8,     // the packet's events are complete: backward sweep
+  aDepScan = 9,   // find the next forced path to deposit from path `event`
+  aStart = 10,    // start walk `wphase` from x along d
+  aExit = 11
 };
 
 struct AdjParams {
@@ -76,7 +86,7 @@ struct AdjParams {
 // The lane: one packet.
 struct ALane {
   unsigned long long pid;
-  int lam, event, phase, q, J;
+  int lam, event, phase, wphase, q, J;
   int eL, eLA;          // 2^eL: unit of weights; 2^eLA: unit of position and tau adjoints
   double L;             // weight (as in the forward kernel)
   float kappa;
@@ -168,15 +178,23 @@ __device__ __forceinline__ float adj_weight(const AdjParams& A, int q, int lam, 
   return W;
 }
 
-__device__ __forceinline__ void start_walk(const FwdParams& P, ALane& s, float3 d) {
+// Ask for walk `phase` from the lane's position along d; walks start in the
+// last stage of a control round, from one place in the code.
+__device__ __forceinline__ void request_walk(ALane& s, int phase, float3 d) {
+  s.wphase = phase;
   s.d = d;
-  s.id = make_float3(tr::inv_or_zero(d.x), tr::inv_or_zero(d.y), tr::inv_or_zero(d.z));
+  s.phase = aStart;
+}
+
+__device__ __forceinline__ void start_walk(const FwdParams& P, ALane& s) {
+  s.phase = s.wphase;
+  s.id = make_float3(tr::inv_or_zero(s.d.x), tr::inv_or_zero(s.d.y), tr::inv_or_zero(s.d.z));
   s.th = s.tl = 0.0f;
   s.g = make_float3(0.0f, 0.0f, 0.0f);
   s.axis_in = -1;
   s.n_cross = 0;
   CartGrid::Scratch sc;
-  s.walking = CartGrid::init(P, s.x, d, s.id, s.has_cell, s.cell, s.w, sc);
+  s.walking = CartGrid::init(P, s.x, s.d, s.id, s.has_cell, s.cell, s.w, sc);
   if (s.walking) s.rho = tr::load_density(&P.density[s.w.cell]);
 }
 
@@ -184,54 +202,14 @@ __device__ __forceinline__ int linear_cell(const FwdParams& P, const CartGrid::C
   return c.ix + P.nx * (c.iy + P.ny * c.iz);
 }
 
-// Start the peel-off walk of instrument s.q (or of a later one) from the
-// lane's position; false when no instrument is left.
-__device__ __forceinline__ bool next_peel(const AdjParams& A, ALane& s) {
-  const FwdParams& P = A.f;
-  const bool on = s.event == 0 ? P.peel_emission : P.peel_scatter;
-  for (; on && s.q < P.n_instr; ++s.q) {
-    float3 dW;
-    const float W = adj_weight(A, s.q, s.lam, s.event > 0, s.x, dW);
-    if (W == 0.0f && dW.x == 0.0f && dW.y == 0.0f && dW.z == 0.0f) continue;  // contributes nothing
-    s.phase = aPeelM;
-    start_walk(P, s, tr::instr_dir(tr::S_INSTR[s.q]));
-    return true;
-  }
-  return false;
-}
-
 template <bool kAbs>
-__device__ __forceinline__ void start_path(const AdjParams& A, ALane& s) {
-  s.phase = aPath1;
-  start_walk(A.f, s, s.k);
+__device__ __forceinline__ void request_path(ALane& s) {
+  request_walk(s, aPath1, s.k);
   if (kAbs) {
     s.P = s.D = s.a_prev = 0.0;
     s.e_prev = 1.0;
     s.g0 = make_double3(0.0, 0.0, 0.0);
   }
-}
-
-// After the peel-offs of event s.event: the first forced path, or the new
-// direction and then termination (the sweep) or the next forced path.
-template <bool kAbs>
-__device__ __forceinline__ void after_peels(const AdjParams& A, ALane& s) {
-  const FwdParams& P = A.f;
-  if (s.event == 0) {
-    s.event = 1;
-    start_path<kAbs>(A, s);
-    return;
-  }
-  const float mu = hg_sample(tr::S_LAM[s.lam].g, s.u_mu);
-  float sp, cp;
-  sincospif(2.0f * s.u_phi, &sp, &cp);
-  s.k = rotate_dir(s.k, mu, sp, cp);
-  if ((P.weight_cut && s.L < P.L_cut[s.lam]) || s.event >= P.max_events) {
-    s.J = s.event;
-    s.phase = aSweep;
-    return;
-  }
-  s.event += 1;
-  start_path<kAbs>(A, s);
 }
 
 // ---- the stages of a control round (each for the lanes in that phase)
@@ -253,6 +231,7 @@ __device__ __forceinline__ void fetch(const AdjParams& A, ALane& s, unsigned lon
   s.has_cell = false;
   tr::emit(P, s);
   s.q = 0;
+  s.phase = aPeelScan;
 }
 
 // Path 1 ended: escape, or the inversion (the forward kernel's FP64 steps)
@@ -296,14 +275,12 @@ __device__ __forceinline__ void finish_path1(const AdjParams& A, ALane& s) {
   s.L = albedo * s.L * omE;  // weight after the scattering
   s.a0 = (float)tau_star;
   s.a1 = (float)(tau_star - (double)s.a0);
-  s.phase = aPath2;
-  start_walk(P, s, s.k);
   s.h = -1;
+  request_walk(s, aPath2, s.k);
 }
 
-// Path 2 ended at the interaction: record it, move the packet, start the
+// Path 2 ended at the interaction: record it, move the packet, then the
 // scattering peel-offs.
-template <bool kAbs>
 __device__ __forceinline__ void finish_path2(const AdjParams& A, ALane& s) {
   const FwdParams& P = A.f;
   if (s.h < 0) {  // not reachable: identical pair sums in both walks and tau* < tau_path
@@ -329,13 +306,12 @@ __device__ __forceinline__ void finish_path2(const AdjParams& A, ALane& s) {
   s.x = x;
   s.has_cell = true;
   s.q = 0;
-  if (!next_peel(A, s)) after_peels<kAbs>(A, s);
+  s.phase = aPeelScan;
 }
 
 // A peel-off measuring walk ended: value l = L phase e^{-tau} W / (4 pi) and
 // d tau / d x_a = -g_a / d_a; the event's share of (Lb, xb); then the
 // depositing walk, or the next peel-off.
-template <bool kAbs>
 __device__ __forceinline__ void finish_peel_measure(const AdjParams& A, ALane& s) {
   const DevInstr& I = tr::S_INSTR[s.q];
   float3 dW;
@@ -354,49 +330,56 @@ __device__ __forceinline__ void finish_peel_measure(const AdjParams& A, ALane& s
   }
   if (l != 0.0f && s.n_cross > 0) {
     s.c0 = s.c1 = -l * s.kappa;
-    s.phase = aPeelD;
-    start_walk(A.f, s, tr::instr_dir(I));
     s.h = INT_MAX;
+    request_walk(s, aPeelD, s.d);
     return;
   }
   s.q += 1;
-  if (!next_peel(A, s)) after_peels<kAbs>(A, s);
+  s.phase = aPeelScan;
 }
 
-template <bool kAbs>
-__device__ __forceinline__ void finish_peel_deposit(const AdjParams& A, ALane& s) {
-  s.q += 1;
-  if (!next_peel(A, s)) after_peels<kAbs>(A, s);
-}
-
-// Start the depositing walk of forced path s.event (or of a later one); the
-// lane needs a new packet when none is left.
-__device__ __forceinline__ void next_deposit(const AdjParams& A, ALane& s) {
+// The next instrument from s.q whose adjoint weight at the lane's position
+// is not zero: its peel-off walk; after the last one, aAfter.
+__device__ __forceinline__ void peel_scan(const AdjParams& A, ALane& s) {
   const FwdParams& P = A.f;
-  for (; s.event <= s.J; ++s.event) {
-    const AdjRecord& r = s.rec[s.event];
-    s.c0 = s.kappa * r.T;
-    s.c1 = s.kappa * (r.T - r.tbh);
-    if (s.c0 == 0.0f && s.c1 == 0.0f) continue;
-    s.h = r.h;
-    s.x = make_float3(r.x[0], r.x[1], r.x[2]);
-    s.has_cell = r.cell >= 0;
-    if (s.has_cell) {
-      s.cell.ix = r.cell % P.nx;
-      s.cell.iy = (r.cell / P.nx) % P.ny;
-      s.cell.iz = r.cell / (P.nx * P.ny);
-    }
-    s.phase = aDep;
-    start_walk(P, s, make_float3(r.k[0], r.k[1], r.k[2]));
-    if (s.walking) return;
+  const bool on = s.event == 0 ? P.peel_emission : P.peel_scatter;
+  for (; on && s.q < P.n_instr; ++s.q) {
+    float3 dW;
+    const float W = adj_weight(A, s.q, s.lam, s.event > 0, s.x, dW);
+    if (W == 0.0f && dW.x == 0.0f && dW.y == 0.0f && dW.z == 0.0f) continue;  // contributes nothing
+    request_walk(s, aPeelM, tr::instr_dir(tr::S_INSTR[s.q]));
+    return;
   }
-  s.phase = aFetch;
+  s.phase = aAfter;
+}
+
+// After the peel-offs of event s.event: the first forced path, or the new
+// direction and then termination (the sweep) or the next forced path.
+template <bool kAbs>
+__device__ __forceinline__ void after_peels(const AdjParams& A, ALane& s) {
+  const FwdParams& P = A.f;
+  if (s.event == 0) {
+    s.event = 1;
+    request_path<kAbs>(s);
+    return;
+  }
+  const float mu = hg_sample(tr::S_LAM[s.lam].g, s.u_mu);
+  float sp, cp;
+  sincospif(2.0f * s.u_phi, &sp, &cp);
+  s.k = rotate_dir(s.k, mu, sp, cp);
+  if ((P.weight_cut && s.L < P.L_cut[s.lam]) || s.event >= P.max_events) {
+    s.J = s.event;
+    s.phase = aSweep;
+    return;
+  }
+  s.event += 1;
+  request_path<kAbs>(s);
 }
 
 // Backward sweep over the packet's events J..1 (no walks): per forced path
 // the total T of its optical-depth adjoints and the adjoint of tau_{h-1} for
 // the depositing walk, the interaction-cell term of the gradient, and the
-// adjoints of the path's start weight and position.  Then the depositing walks.
+// adjoints of the path's start weight and position.
 __device__ __forceinline__ void sweep(const AdjParams& A, ALane& s) {
   const float albedo = (float)tr::S_LAM[s.lam].albedo;
   float Lb = 0.0f, xb0 = 0.0f, xb1 = 0.0f, xb2 = 0.0f;
@@ -429,23 +412,30 @@ __device__ __forceinline__ void sweep(const AdjParams& A, ALane& s) {
     r.tbh = tbh;
   }
   s.event = 1;
-  next_deposit(A, s);
+  s.phase = aDepScan;
 }
 
-// Per-event work of an idle lane, one stage per phase in walk order.
-template <bool kAbs>
-__device__ __forceinline__ void control(const AdjParams& A, ALane& s) {
-  if (!s.walking && s.phase == aPath1) finish_path1<kAbs>(A, s);
-  if (!s.walking && s.phase == aPath2) finish_path2<kAbs>(A, s);
-  if (!s.walking && s.phase == aPeelM) finish_peel_measure<kAbs>(A, s);
-  if (!s.walking && s.phase == aPeelD) finish_peel_deposit<kAbs>(A, s);
-  if (!s.walking && s.phase == aSweep) {
-    if (s.J >= 1) sweep(A, s); else s.phase = aFetch;
+// The depositing walk of forced path s.event or of a later one; after the
+// last, the lane needs a new packet.
+__device__ __forceinline__ void dep_scan(const AdjParams& A, ALane& s) {
+  const FwdParams& P = A.f;
+  for (; s.event <= s.J; ++s.event) {
+    const AdjRecord& r = s.rec[s.event];
+    s.c0 = s.kappa * r.T;
+    s.c1 = s.kappa * (r.T - r.tbh);
+    if (s.c0 == 0.0f && s.c1 == 0.0f) continue;
+    s.h = r.h;
+    s.x = make_float3(r.x[0], r.x[1], r.x[2]);
+    s.has_cell = r.cell >= 0;
+    if (s.has_cell) {
+      s.cell.ix = r.cell % P.nx;
+      s.cell.iy = (r.cell / P.nx) % P.ny;
+      s.cell.iz = r.cell / (P.nx * P.ny);
+    }
+    request_walk(s, aDep, make_float3(r.k[0], r.k[1], r.k[2]));
+    return;
   }
-  if (!s.walking && s.phase == aDep) {
-    s.event += 1;
-    next_deposit(A, s);
-  }
+  s.phase = aFetch;
 }
 
 // One cell crossing of the lane's current walk.
@@ -512,7 +502,7 @@ __device__ __forceinline__ void step(const AdjParams& A, ALane& s, unsigned& n_c
 }
 
 template <bool kAbs>
-__global__ void __launch_bounds__(kAdjBlock, 2) k_adjoint(const AdjParams A) {
+__global__ void __launch_bounds__(kAdjBlock, RT_ADJ_MIN_BLOCKS) k_adjoint(const AdjParams A) {
   const FwdParams& P = A.f;
   for (int i = threadIdx.x; i < P.n_instr; i += kAdjBlock) tr::S_INSTR[i] = P.instr[i];
   for (int i = threadIdx.x; i < P.n_lambda; i += kAdjBlock) tr::S_LAM[i] = P.lam[i];
@@ -531,7 +521,15 @@ __global__ void __launch_bounds__(kAdjBlock, 2) k_adjoint(const AdjParams A) {
     const unsigned walkers = __ballot_sync(0xffffffffu, s.walking);
     if (need == 0u && walkers == 0u) break;
     if (walkers == 0u || __popc(need) >= P.control_min) {
-      if (idle && s.phase != aFetch) control<kAbs>(A, s);
+      // per-event work in stages, each run by the lanes in its phase together;
+      // a stage only hands lanes on to later stages
+      if (!s.walking) {
+        if (s.phase == aPath1) finish_path1<kAbs>(A, s);
+        if (s.phase == aPath2) finish_path2(A, s);
+        if (s.phase == aPeelM) finish_peel_measure(A, s);
+        if (s.phase == aPeelD) { s.q += 1; s.phase = aPeelScan; }
+        if (s.phase == aDep) { s.event += 1; s.phase = aDepScan; }
+      }
       // packets for every lane that needs one: one atomic per warp
       const bool wants = !s.walking && s.phase == aFetch;
       const unsigned fetchers = __ballot_sync(0xffffffffu, wants);
@@ -540,11 +538,15 @@ __global__ void __launch_bounds__(kAdjBlock, 2) k_adjoint(const AdjParams A) {
         const int leader = __ffs(fetchers) - 1;
         if ((int)lane == leader) base = atomicAdd(P.work_counter, (unsigned long long)__popc(fetchers));
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (wants) {
-          fetch(A, s, base + __popc(fetchers & lt_mask));
-          if (s.phase != aExit && !next_peel(A, s)) after_peels<kAbs>(A, s);
-        }
+        if (wants) fetch(A, s, base + __popc(fetchers & lt_mask));
       }
+      if (s.phase == aPeelScan) peel_scan(A, s);
+      if (s.phase == aAfter) after_peels<kAbs>(A, s);
+      if (s.phase == aSweep) {
+        if (s.J >= 1) sweep(A, s); else s.phase = aFetch;
+      }
+      if (s.phase == aDepScan) dep_scan(A, s);
+      if (s.phase == aStart) start_walk(P, s);
       if ((n_cross | n_dep) & 0xC0000000u) {  // keep the 32-bit lane counters far from overflow
         tot_cross += n_cross;
         tot_dep += n_dep;

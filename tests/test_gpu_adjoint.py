@@ -50,22 +50,28 @@ def test_adjoint_matches_oracle_dual_numbers(n_cells, channels):
     assert err.max() <= 1e-3 * scale
 
 
-def test_adjoint_matches_central_differences():
-    """Loss = sum (image - target)^2 on a 24^3 log-normal cube; the adjoint of the
-    GPU forward against central differences of the GPU forward under common
-    random numbers, on the 6 cells of largest gradient and 10 random ones.
+def _loss_problem(n_cells, n_pix, n_packets):
+    prob = W.lognormal_cube(n_cells=n_cells, n_pix=n_pix, n_packets=n_packets, max_events=20)
+    target = W.lognormal_cube(n_cells=n_cells, n_pix=n_pix, n_packets=n_packets, max_events=20, seed=104)
+    return prob, target
 
-    The step is 1e-2 of the cell's density.  The forward computes each
-    contribution in FP32, so a change of one density moves every contribution
-    whose path crosses that cell by its true derivative plus a rounding jitter
-    of about one FP32 ulp; the jitter does not shrink with the step, so the
-    difference quotient at 1e-3 already differs from the derivative by about
-    1e-2 and at 1e-4 by about 1e-1, while the truncation error of the
-    central difference at 1e-2 is of order 1e-4.  The oracle's dual-number
-    derivative pins the same gradient to 1e-5 on the largest cells."""
+
+def test_adjoint_matches_central_differences_and_duals():
+    """Loss = sum (image - target)^2 on a 24^3 log-normal cube.
+
+    The estimator is piecewise smooth in the densities: the optical depth
+    along a ray is piecewise linear in the ray's start (kinks where the ray
+    meets cell edges) and the bilinear deposit has kinks at pixel centres, so
+    a central difference straddles kinks and converges only as fast as they
+    allow.  Even the FP64 oracle's own central differences at steps 1e-2 to
+    1e-3 of a density differ from its exact (dual-number) derivative by up to
+    a few per cent on cells whose gradient is small.  The pin is therefore
+    the oracle's dual-number derivative on every sampled cell; central
+    differences of the GPU forward (step 1e-2, common random numbers) are
+    held to the same derivative on the cells of largest gradient, where the
+    kinks are negligible."""
     from oracle import oracle as O
-    prob = W.lognormal_cube(n_cells=24, n_pix=32, n_packets=50000, max_events=20)
-    target_prob = W.lognormal_cube(n_cells=24, n_pix=32, n_packets=50000, max_events=20, seed=104)
+    prob, target_prob = _loss_problem(24, 32, 50000)
     n = prob.run.n_per_lambda
     opts = dict(max_events=20, weight_cut=0)
     sim = rt.Simulation(prob)
@@ -95,25 +101,51 @@ def test_adjoint_matches_central_differences():
         rng = np.random.default_rng(4)
         rest = np.setdiff1d(np.arange(prob.grid.n_cells), top)
         cells = np.concatenate([top, rng.choice(rest, 10, replace=False)])
-        for c in cells:
+        for c in top:
             up, dn = rho.copy(), rho.copy()
             up[c] = np.float32(rho[c] * (1 + 1e-2))
             dn[c] = np.float32(rho[c] * (1 - 1e-2))
             fd = (loss_of(up)[0] - loss_of(dn)[0]) / (float(up[c]) - float(dn[c]))
-            print(c, fd, g[c])
-            assert abs(fd - g[c]) <= 2e-3 * abs(g[c]) + 1e-4 * gmax, c
+            print("fd", c, fd, g[c])
+            assert abs(fd - g[c]) <= 2e-3 * abs(g[c]) + 1e-5 * gmax, c
 
-        # the same derivative from the oracle's forward-mode duals, on the
-        # oracle's own images
+        # the exact derivative of the same estimator: the oracle's forward-mode
+        # duals, with the oracle's own images in the adjoint
         kw = dict(max_events=20, weight_cut=False, n_threads=O.default_threads(), absorption=False)
         t_o = O.run(target_prob, n, **kw)["images"][0]
         i_o = O.run(prob, n, **kw)["images"][0]
-        g_o = O.vjp(prob, top[:3], n, adj_images=[2.0 * (i_o - t_o)], max_events=20, weight_cut=False,
+        g_o = O.vjp(prob, cells, n, adj_images=[2.0 * (i_o - t_o)], max_events=20, weight_cut=False,
                     n_threads=O.default_threads())
-        np.testing.assert_allclose(g[top[:3]], g_o, rtol=1e-4)
+        for c, go in zip(cells, g_o):
+            print("dual", c, go, g[c])
+        np.testing.assert_allclose(g[cells], g_o, rtol=5e-4, atol=1e-9 * gmax)
     finally:
         sim.close()
         tsim.close()
+
+
+def test_adjoint_matches_duals_at_full_grid_size():
+    """The 64^3 log-normal cube with its 128^2 bilinear detector (the
+    differentiation workload at full grid and detector size; packets are
+    independent, so 10^5 of them exercise the same per-packet arithmetic):
+    the GPU adjoint against the oracle's dual-number derivative on the 4
+    cells of largest gradient and 4 random cells, each to 5e-4 relative."""
+    from oracle import oracle as O
+    prob, target_prob = _loss_problem(64, 128, 100000)
+    n = prob.run.n_per_lambda
+    kw = dict(max_events=20, weight_cut=False, n_threads=O.default_threads(), absorption=False)
+    t_o = O.run(target_prob, n, **kw)["images"][0]
+    i_o = O.run(prob, n, **kw)["images"][0]
+    adj_o = 2.0 * (i_o - t_o)
+    g = _gpu_grad(prob, n, [adj_o], None, max_events=20, weight_cut=0)
+    gmax = np.abs(g).max()
+    top = np.argsort(-np.abs(g))[:4]
+    rng = np.random.default_rng(4)
+    cells = np.concatenate([top, rng.choice(np.setdiff1d(np.arange(prob.grid.n_cells), top), 4, replace=False)])
+    g_o = O.vjp(prob, cells, n, adj_images=[adj_o], max_events=20, weight_cut=False, n_threads=O.default_threads())
+    for c, go in zip(cells, g_o):
+        print(c, go, g[c])
+    np.testing.assert_allclose(g[cells], g_o, rtol=5e-4, atol=1e-12 * gmax)
 
 
 def test_autograd_function_matches_direct_adjoint():
