@@ -252,6 +252,42 @@ def adjoint_ratio(args, device, stream, flush):
             "device_flags": int(flags), "l2": "flushed before each timed launch"}
 
 
+def batch_rate(args, device, stream):
+    """Packets/s of one batched launch of the 4096-model workload (8^3-48^3
+    cubes, 1e4-1e6 packets each, 64^2 frame each): tuned once, then warm-up
+    and timed graph launches with CUDA events on the launching stream.  The
+    batch's densities (0.55 GB) and images (0.13 GB) exceed L2."""
+    import torch
+    from paper_1410_1629_gb300 import rt
+    from paper_1410_1629_gb300 import workloads as W
+    models = W.batch_models()
+    b = rt.Batch(models, device=device)
+    try:
+        lanes, run = b.tune(seed=0, fraction=0.02, stream=stream.cuda_stream)
+        ts = []
+        for i in range(args.warmup + 2):
+            b.reset(stream=stream.cuda_stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                b.launch(seed=0, stream=stream.cuda_stream)
+                e1.record(stream)
+            e1.synchronize()
+            if i >= args.warmup:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        st = b.stats()
+    finally:
+        b.close()
+    t = sum(ts) / len(ts)
+    return {"workload": "4096 models: 8^3-48^3 cells, half uniform / half exponential slab, axis tau 0.1-20, "
+                        "g 0-0.9, albedo 0.3-0.8, 1e4-1e6 packets, one 64^2 frame each",
+            "models": len(models), "packets": int(st["packets"]), "seconds_per_launch": t,
+            "packets_per_s": st["packets"] / t, "crossings_per_s": st["crossings"] / t,
+            "tuned": {"control_lanes": lanes, "run_packets": run}, "launch": "CUDA graph",
+            "timed_launches": len(ts), "device_flags": int(st["device_flags"]),
+            "l2": "inputs larger than L2"}
+
+
 def run_gpu(args, prob, world, rank, local_rank):
     import torch
     from paper_1410_1629_gb300 import rt
@@ -363,6 +399,9 @@ def run_gpu(args, prob, world, rank, local_rank):
     adjoint = None
     if rank == 0 and world == 1 and not args.skip_adjoint:
         adjoint = adjoint_ratio(args, device, stream, flush)
+    batch = None
+    if rank == 0 and world == 1 and not args.skip_batch:
+        batch = batch_rate(args, device, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -386,6 +425,7 @@ def run_gpu(args, prob, world, rank, local_rank):
                              "kernel": "k_forward_" + ("octree" if prob.grid.kind == "octree" else "cartesian"),
                              "launch_ms": 1e3 * mean_launch},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "adjoint": adjoint,
+                "batch": batch,
                 "clocks": clk,
                 "checks": {"conservation_rel": conservation, "path_crossings": int(path_cross),
                            "peel_crossings": int(peel_cross), "peeloffs": int(deposits),
@@ -401,6 +441,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true",
+                    help="skip the batched 4096-model measurement")
     ap.add_argument("--skip-adjoint", action="store_true",
                     help="skip the adjoint/forward measurement on the 64^3 differentiation workload")
     ap.add_argument("--e2e-steps", type=int, default=2)

@@ -316,6 +316,77 @@ rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t n_lambda, 
                                     double* absorption, uint64_t n_per_lambda, uint64_t first_packet_id,
                                     uint64_t seed, const rt_launch_opts* opts, rt_stats* stats_out, void* stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many small independent models in one persistent launch, for the parameter
+ * searches of model fitting that Sect. 1 motivates: thousands of small grids,
+ * each too small to fill the GPU alone.  A model is a cartesian grid with one
+ * wavelength, one point source and one single-channel frame.  Its packets are
+ * the packets rt_launch_packets runs for the same problem with
+ * model_id = the model's index in the batch and n_norm = n_packets, with the
+ * same arithmetic, so its image and tallies equal that launch's up to the
+ * order of FP64 additions.  No absorption field is kept (its total is). */
+typedef struct {
+  int32_t nx, ny, nz;            /* cells per axis, 1 .. 65536 */
+  int32_t reserved;
+  double bounds[6];              /* xmin, xmax, ymin, ymax, zmin, zmax */
+  const float* density;          /* host, float32 [nz][ny][nx], finite and >= 0; copied */
+  double kappa;                  /* extinction per unit density and length, >= 0 */
+  double albedo;                 /* 0 .. 1 */
+  double g;                      /* Henyey-Greenstein asymmetry, -1 < g < 1 */
+  double luminosity;             /* of the point source, > 0 */
+  double source[3];              /* point source position */
+  rt_instrument_desc instrument; /* the frame; channels must be 1 */
+  uint64_t n_packets;            /* packets per launch, 1 .. 2^32 - 1 */
+} rt_model_desc;
+
+/* Copy n_models (1 .. 2^20) models to the device: densities in one buffer,
+ * one table row per model, FP64 images and tallies zeroed, the work list of
+ * packet runs sorted by estimated cost.  *batch_id receives the handle.
+ * Errors: RT_ERR_ARG (the model index is in the message), RT_ERR_OOM,
+ * RT_ERR_CUDA. */
+rt_status rt_batch_create(rt_ctx ctx, int32_t n_models, const rt_model_desc* models, int32_t* batch_id);
+
+/* Free a batch (after its work has finished). */
+rt_status rt_batch_destroy(rt_ctx ctx, int32_t batch_id);
+
+/* Run every model's n_packets packets, accumulating into the batch's images
+ * and tallies, asynchronously on `stream`, as one CUDA graph (reset the work
+ * counter, add each model's luminosity to its emitted tally, the persistent
+ * kernel) whose kernel parameters are updated per call.  opts: w_min,
+ * max_events, weight_cut, peel_emission, peel_scatter and control_lanes are
+ * used (control_lanes 0: the value rt_batch_tune chose, else 16); seed < 2^32.
+ * Errors: RT_ERR_ARG, RT_ERR_CUDA. */
+rt_status rt_batch_launch(rt_ctx ctx, int32_t batch_id, uint64_t seed, const rt_launch_opts* opts, void* stream);
+
+/* Zero the batch's images, tallies and counters (stream-ordered). */
+rt_status rt_batch_reset(rt_ctx ctx, int32_t batch_id, void* stream);
+
+/* The models' images, concatenated in model order, each [ny][nx] float64;
+ * n_elems must be the sum of nx * ny.  dst on the host (the call waits) or
+ * on the device (on_device = 1, stream-ordered). */
+rt_status rt_batch_read_images(rt_ctx ctx, int32_t batch_id, double* dst, size_t n_elems, int32_t on_device,
+                               void* stream);
+
+/* Per-model tallies [n_models][4] float64: emitted, escaped, absorbed,
+ * truncated luminosity; n_elems must be 4 * n_models. */
+rt_status rt_batch_read_tallies(rt_ctx ctx, int32_t batch_id, double* dst, size_t n_elems, int32_t on_device,
+                                void* stream);
+
+/* Synchronise and sum: the totals over the models and the counters
+ * (crossings, events, peeloffs, packets); records, path_crossings 0.
+ * Errors: RT_ERR_CUDA, RT_ERR_DEVICE_FLAG. */
+rt_status rt_batch_read_stats(rt_ctx ctx, int32_t batch_id, rt_stats* out);
+
+/* Choose control_lanes and the packets per work-list run by timing launches
+ * of a fraction (0 < fraction <= 1) of every model's packets for each
+ * candidate (control_lanes 8, 12, ..., 32; runs of 64, 256, 1024, 4096
+ * packets); the choice is kept for later launches with control_lanes 0 and
+ * written to *control_lanes and *run_packets if not NULL.  The images and
+ * tallies are zeroed afterwards.  Synchronous.  Errors: RT_ERR_ARG,
+ * RT_ERR_CUDA. */
+rt_status rt_batch_tune(rt_ctx ctx, int32_t batch_id, uint64_t seed, double fraction, int32_t* control_lanes,
+                        uint32_t* run_packets, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

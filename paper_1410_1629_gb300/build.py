@@ -21,7 +21,11 @@ OUT_DIR = os.environ.get("RT_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB_NAME = "librt_gb300.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+# -fmad=false: no implicit contraction of a*b + c (the kernels call fmaf
+# where they mean it), so the per-packet arithmetic that the forward, adjoint,
+# batched and allocation-free kernels share rounds the same way in each and a
+# packet follows the same path in all of them.
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-Xptxas", "-O3"]
 
 

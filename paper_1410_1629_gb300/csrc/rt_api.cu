@@ -39,6 +39,32 @@ thread_local std::string g_create_error;
 
 void rtk::set_context_free_error(const char* msg) { g_create_error = msg ? msg : ""; }
 
+// A batch of small models (rt_batch_*).
+struct Batch {
+  int n_models = 0;
+  std::vector<double> lum;                    // per model
+  std::vector<unsigned long long> n_packets;  // per model
+  std::vector<double> cost;                   // estimated work per packet, per model
+  std::vector<size_t> img_off, img_elems;     // per model, in doubles
+  size_t img_total = 0;
+  float* d_density = nullptr;
+  DevModel* d_models = nullptr;
+  BatchChunk* d_chunks = nullptr;
+  int n_chunks = 0;
+  unsigned run_packets = 0;                   // packets per work-list run
+  int control_lanes = 0;                      // chosen by rt_batch_tune (0: none)
+  double* d_images = nullptr;
+  double* d_tallies = nullptr;                // [n][4]
+  double* d_lum = nullptr;
+  unsigned long long* d_chunk_counter = nullptr;
+  unsigned long long* d_counters = nullptr;   // [4]
+  int* d_flags = nullptr;
+  unsigned blocks = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t kernel_node = nullptr;
+};
+
 struct rt_ctx_s {
   int device = 0;
   int num_sms = 0;
@@ -74,6 +100,7 @@ struct rt_ctx_s {
   float* d_adj_img = nullptr;  // FP32 copies of the adjoint images, grown on demand
   size_t adj_img_elems = 0;
   unsigned long long* d_adj_max = nullptr;
+  std::vector<Batch*> batches;  // by id; null after rt_batch_destroy
   double emitted = 0.0;  // luminosity emitted since the last reset (host-side sum)
 };
 
@@ -219,6 +246,125 @@ rt_status upload_tables(rt_ctx c, cudaStream_t s) {
 
 bool is_finite(double v) { return std::isfinite(v); }
 
+void free_batch(Batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  dfree(b->d_density); dfree(b->d_models); dfree(b->d_chunks); dfree(b->d_images); dfree(b->d_tallies);
+  dfree(b->d_lum); dfree(b->d_chunk_counter); dfree(b->d_counters); dfree(b->d_flags);
+  delete b;
+}
+
+Batch* get_batch(rt_ctx c, int32_t id) {
+  if (id < 0 || (size_t)id >= c->batches.size()) return nullptr;
+  return c->batches[(size_t)id];
+}
+
+// Work list: every model's packets in runs of at most run_packets (models
+// with fewer packets in one run), sorted by estimated cost, largest first.
+std::vector<BatchChunk> batch_chunks(const Batch& b, unsigned run_packets, double fraction) {
+  std::vector<BatchChunk> out;
+  std::vector<double> cost;
+  for (int m = 0; m < b.n_models; ++m) {
+    unsigned long long n = b.n_packets[(size_t)m];
+    if (fraction < 1.0) n = std::max<unsigned long long>(1, (unsigned long long)std::ceil((double)n * fraction));
+    for (unsigned long long f = 0; f < n; f += run_packets) {
+      BatchChunk ch;
+      ch.first = f;
+      ch.model = m;
+      ch.count = (unsigned)std::min<unsigned long long>(run_packets, n - f);
+      out.push_back(ch);
+      cost.push_back(b.cost[(size_t)m] * ch.count);
+    }
+  }
+  std::vector<size_t> order(out.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return cost[a] > cost[c]; });
+  std::vector<BatchChunk> sorted(out.size());
+  for (size_t i = 0; i < order.size(); ++i) sorted[i] = out[order[i]];
+  return sorted;
+}
+
+rt_status upload_chunks(rt_ctx c, Batch* b, unsigned run_packets) {
+  const std::vector<BatchChunk> ch = batch_chunks(*b, run_packets, 1.0);
+  dfree(b->d_chunks);
+  RT_CUDA(c, cudaMalloc(&b->d_chunks, std::max<size_t>(1, ch.size()) * sizeof(BatchChunk)));
+  RT_CUDA(c, cudaMemcpy(b->d_chunks, ch.data(), ch.size() * sizeof(BatchChunk), cudaMemcpyHostToDevice));
+  b->n_chunks = (int)ch.size();
+  b->run_packets = run_packets;
+  return RT_OK;
+}
+
+rt_status batch_opts(rt_ctx c, const rt_launch_opts* opts, uint64_t seed, rt_launch_opts& o) {
+  rt_default_opts(&o);
+  if (opts) o = *opts;
+  if (seed >> 32) return fail(c, RT_ERR_ARG, "rt_batch: seed must be < 2^32");
+  if (o.max_events < 1) return fail(c, RT_ERR_ARG, "rt_batch: max_events must be >= 1");
+  if (!(o.w_min >= 0 && o.w_min < 1)) return fail(c, RT_ERR_ARG, "rt_batch: w_min must be in [0, 1)");
+  if (o.control_lanes < 0 || o.control_lanes > 32) return fail(c, RT_ERR_ARG, "rt_batch: control_lanes in [0, 32]");
+  return RT_OK;
+}
+
+BatchParams batch_params(const Batch* b, const rt_launch_opts& o, uint64_t seed, const BatchChunk* chunks,
+                         int n_chunks) {
+  BatchParams p;
+  std::memset(&p, 0, sizeof p);
+  p.models = b->d_models;
+  p.chunks = chunks;
+  p.n_models = b->n_models;
+  p.n_chunks = n_chunks;
+  p.density = b->d_density;
+  p.tallies = b->d_tallies;
+  p.chunk_counter = b->d_chunk_counter;
+  p.counters = b->d_counters;
+  p.flags = b->d_flags;
+  p.w_min = o.w_min;
+  p.seed = (unsigned)seed;
+  p.max_events = o.max_events;
+  p.weight_cut = o.weight_cut;
+  p.peel_emission = o.peel_emission;
+  p.peel_scatter = o.peel_scatter;
+  p.control_min = o.control_lanes ? o.control_lanes : (b->control_lanes ? b->control_lanes : 16);
+  return p;
+}
+
+// The launch graph: zero the work counter and add the emitted luminosity,
+// then the persistent kernel.
+rt_status build_graph(rt_ctx c, Batch* b, const BatchParams& p) {
+  RT_CUDA(c, cudaGraphCreate(&b->graph, 0));
+  cudaMemsetParams mp;
+  std::memset(&mp, 0, sizeof mp);
+  mp.dst = b->d_chunk_counter;
+  mp.value = 0;
+  mp.elementSize = 4;
+  mp.width = 2;
+  mp.height = 1;
+  cudaGraphNode_t n_zero, n_emit;
+  RT_CUDA(c, cudaGraphAddMemsetNode(&n_zero, b->graph, nullptr, 0, &mp));
+  double* tallies = b->d_tallies;
+  const double* lum = b->d_lum;
+  int n = b->n_models;
+  void* eargs[] = {&tallies, &lum, &n};
+  cudaKernelNodeParams ep;
+  std::memset(&ep, 0, sizeof ep);
+  ep.func = const_cast<void*>(batch_emitted_kernel());
+  ep.gridDim = dim3((unsigned)((n + 255) / 256));
+  ep.blockDim = dim3(256);
+  ep.kernelParams = eargs;
+  RT_CUDA(c, cudaGraphAddKernelNode(&n_emit, b->graph, nullptr, 0, &ep));
+  BatchParams pc = p;
+  void* kargs[] = {&pc};
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof kp);
+  kp.func = const_cast<void*>(batch_kernel());
+  kp.gridDim = dim3(b->blocks);
+  kp.blockDim = dim3(kBatchBlock);
+  kp.kernelParams = kargs;
+  cudaGraphNode_t deps[2] = {n_zero, n_emit};
+  RT_CUDA(c, cudaGraphAddKernelNode(&b->kernel_node, b->graph, deps, 2, &kp));
+  RT_CUDA(c, cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return RT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -255,6 +401,7 @@ rt_status rt_context_create(int32_t device, rt_ctx* out) {
 rt_status rt_context_destroy(rt_ctx c) {
   if (!c) return RT_OK;
   cudaSetDevice(c->device);
+  for (size_t i = 0; i < c->batches.size(); ++i) rt_batch_destroy(c, (int32_t)i);
   free_problem(c);
   free_grid(c);
   dfree(c->d_lam); dfree(c->d_src); dfree(c->d_src_cum); dfree(c->d_instr);
@@ -716,6 +863,292 @@ rt_status rt_synchronize(rt_ctx c, void* stream) {
   RT_CUDA(c, cudaStreamSynchronize((cudaStream_t)stream));
   RT_CUDA(c, cudaGetLastError());
   return RT_OK;
+}
+
+rt_status rt_batch_create(rt_ctx c, int32_t n_models, const rt_model_desc* models, int32_t* batch_id) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (!batch_id) return fail(c, RT_ERR_ARG, "rt_batch_create: null batch_id");
+  if (n_models < 1 || n_models > (1 << 20) || !models) return fail(c, RT_ERR_ARG, "rt_batch_create: 1 .. 2^20 models");
+  size_t n_cells_total = 0;
+  for (int m = 0; m < n_models; ++m) {
+    const rt_model_desc& d = models[m];
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nx > 65536 || d.ny > 65536 || d.nz > 65536)
+      return fail(c, RT_ERR_ARG, "rt_batch_create: model %d: cells per axis in 1 .. 65536", m);
+    for (int a = 0; a < 3; ++a)
+      if (!(d.bounds[2 * a + 1] > d.bounds[2 * a]) || !is_finite(d.bounds[2 * a]) || !is_finite(d.bounds[2 * a + 1]))
+        return fail(c, RT_ERR_ARG, "rt_batch_create: model %d: empty or non-finite bounds", m);
+    if (!d.density) return fail(c, RT_ERR_ARG, "rt_batch_create: model %d: null density", m);
+    if (!(d.kappa >= 0) || !is_finite(d.kappa) || !(d.albedo >= 0 && d.albedo <= 1) || !(d.g > -1 && d.g < 1))
+      return fail(c, RT_ERR_ARG, "rt_batch_create: model %d: bad optics", m);
+    if (!(d.luminosity > 0) || !is_finite(d.luminosity)) return fail(c, RT_ERR_ARG, "rt_batch_create: model %d: luminosity", m);
+    for (int a = 0; a < 3; ++a)
+      if (!is_finite(d.source[a])) return fail(c, RT_ERR_ARG, "rt_batch_create: model %d: source position", m);
+    const rt_instrument_desc& q = d.instrument;
+    if (q.nx < 1 || q.ny < 1 || !(q.half_x > 0) || !(q.half_y > 0) || q.channels != 1 ||
+        (q.deposit != RT_DEPOSIT_NEAREST && q.deposit != RT_DEPOSIT_BILINEAR))
+      return fail(c, RT_ERR_ARG, "rt_batch_create: model %d: bad frame (channels must be 1)", m);
+    if (d.n_packets < 1 || d.n_packets > 0xffffffffull)
+      return fail(c, RT_ERR_ARG, "rt_batch_create: model %d: packets in 1 .. 2^32 - 1", m);
+    const size_t nc = (size_t)d.nx * d.ny * d.nz;
+    for (size_t i = 0; i < nc; ++i)
+      if (!(d.density[i] >= 0.0f) || !std::isfinite(d.density[i]))
+        return fail(c, RT_ERR_ARG, "rt_batch_create: model %d: density must be finite and >= 0", m);
+    n_cells_total += nc;
+  }
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  Batch* b = new (std::nothrow) Batch();
+  if (!b) return fail(c, RT_ERR_OOM, "rt_batch_create: host allocation");
+  b->n_models = n_models;
+  std::vector<DevModel> rows((size_t)n_models);
+  std::vector<float> dens(n_cells_total);
+  size_t off = 0;
+  for (int m = 0; m < n_models; ++m) {
+    const rt_model_desc& d = models[m];
+    DevModel& M = rows[(size_t)m];
+    std::memset(&M, 0, sizeof M);
+    M.nx = d.nx; M.ny = d.ny; M.nz = d.nz;
+    double mass = 0.0;
+    const size_t nc = (size_t)d.nx * d.ny * d.nz;
+    for (size_t i = 0; i < nc; ++i) mass += d.density[i];
+    for (int a = 0; a < 3; ++a) {
+      const int n = a == 0 ? d.nx : (a == 1 ? d.ny : d.nz);
+      const double dd = (d.bounds[2 * a + 1] - d.bounds[2 * a]) / n;  // as rt_launch_packets
+      M.lo[a] = (float)d.bounds[2 * a];
+      M.hi[a] = (float)d.bounds[2 * a + 1];
+      M.d[a] = (float)dd;
+      M.inv_d[a] = (float)(1.0 / dd);
+      M.src[a] = (float)d.source[a];
+    }
+    M.kappa = (float)d.kappa;
+    M.g = (float)d.g;
+    M.albedo = d.albedo;
+    M.L0 = d.luminosity / (double)d.n_packets;
+    M.density = (long long)off;
+    std::memcpy(&dens[off], d.density, nc * sizeof(float));
+    off += nc;
+    double kobs[3], ex[3], ey[3];
+    frame_axes(d.instrument, kobs, ex, ey);
+    DevInstr& I = M.instr;
+    for (int a = 0; a < 3; ++a) { I.kobs[a] = (float)kobs[a]; I.ex[a] = (float)ex[a]; I.ey[a] = (float)ey[a]; }
+    I.off_x = (float)(d.instrument.half_x - d.instrument.center_x);
+    I.off_y = (float)(d.instrument.half_y - d.instrument.center_y);
+    I.sx = (float)(d.instrument.nx / (2.0 * d.instrument.half_x));
+    I.sy = (float)(d.instrument.ny / (2.0 * d.instrument.half_y));
+    I.nx = d.instrument.nx; I.ny = d.instrument.ny;
+    I.bilinear = d.instrument.deposit == RT_DEPOSIT_BILINEAR;
+    I.channels = 1;
+    b->lum.push_back(d.luminosity);
+    b->n_packets.push_back(d.n_packets);
+    b->img_off.push_back(b->img_total);
+    b->img_elems.push_back((size_t)d.instrument.nx * d.instrument.ny);
+    b->img_total += (size_t)d.instrument.nx * d.instrument.ny;
+    // work per packet ~ cells along a path x (1 + expected events), the
+    // events from the mean optical depth across the model and the albedo
+    const double side = (d.nx + d.ny + d.nz) / 3.0;
+    const double tau = d.kappa * mass / (double)nc * (d.bounds[1] - d.bounds[0]);
+    const double keep = std::max(1e-3, d.albedo * -std::expm1(-0.5 * tau));
+    const double events = std::min(1000.0, std::log(1e-4) / std::log(std::min(keep, 0.999)));
+    b->cost.push_back(side * (1.0 + events));
+  }
+  auto bail = [&](rt_status st) { free_batch(b); return st; };
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](auto** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(1, bytes));
+  };
+  alloc(&b->d_density, dens.size() * sizeof(float));
+  alloc(&b->d_models, rows.size() * sizeof(DevModel));
+  alloc(&b->d_images, b->img_total * sizeof(double));
+  alloc(&b->d_tallies, (size_t)n_models * 4 * sizeof(double));
+  alloc(&b->d_lum, (size_t)n_models * sizeof(double));
+  alloc(&b->d_chunk_counter, sizeof(unsigned long long));
+  alloc(&b->d_counters, 4 * sizeof(unsigned long long));
+  alloc(&b->d_flags, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(c, RT_ERR_OOM, "rt_batch_create: device allocation: %s", cudaGetErrorString(e)));
+  }
+  for (int m = 0; m < n_models; ++m) rows[(size_t)m].instr.image = b->d_images + b->img_off[(size_t)m];
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_density, dens.data(), dens.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_models, rows.data(), rows.size() * sizeof(DevModel), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_lum, b->lum.data(), b->lum.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->d_images, 0, b->img_total * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(b->d_tallies, 0, (size_t)n_models * 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(b->d_flags, 0, sizeof(int));
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "rt_batch_create: upload"));
+  int per_sm = 0;
+  e = batch_blocks_per_sm(&per_sm);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "rt_batch_create: occupancy"));
+  b->blocks = (unsigned)(c->num_sms * std::max(1, per_sm));
+  rt_status st = upload_chunks(c, b, 1024);
+  if (st != RT_OK) return bail(st);
+  c->batches.push_back(b);
+  *batch_id = (int32_t)(c->batches.size() - 1);
+  return RT_OK;
+}
+
+rt_status rt_batch_destroy(rt_ctx c, int32_t id) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  Batch* b = get_batch(c, id);
+  if (!b) return fail(c, RT_ERR_ARG, "rt_batch_destroy: unknown batch %d", id);
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  cudaDeviceSynchronize();
+  free_batch(b);
+  c->batches[(size_t)id] = nullptr;
+  return RT_OK;
+}
+
+rt_status rt_batch_launch(rt_ctx c, int32_t id, uint64_t seed, const rt_launch_opts* opts, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  Batch* b = get_batch(c, id);
+  if (!b) return fail(c, RT_ERR_ARG, "rt_batch_launch: unknown batch %d", id);
+  rt_launch_opts o;
+  rt_status st = batch_opts(c, opts, seed, o);
+  if (st != RT_OK) return st;
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  const BatchParams p = batch_params(b, o, seed, b->d_chunks, b->n_chunks);
+  if (!b->exec) {
+    st = build_graph(c, b, p);
+    if (st != RT_OK) return st;
+  } else {
+    BatchParams pc = p;
+    void* kargs[] = {&pc};
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    kp.func = const_cast<void*>(batch_kernel());
+    kp.gridDim = dim3(b->blocks);
+    kp.blockDim = dim3(kBatchBlock);
+    kp.kernelParams = kargs;
+    RT_CUDA(c, cudaGraphExecKernelNodeSetParams(b->exec, b->kernel_node, &kp));
+  }
+  RT_CUDA(c, cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+  return RT_OK;
+}
+
+rt_status rt_batch_reset(rt_ctx c, int32_t id, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  Batch* b = get_batch(c, id);
+  if (!b) return fail(c, RT_ERR_ARG, "rt_batch_reset: unknown batch %d", id);
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  RT_CUDA(c, cudaMemsetAsync(b->d_images, 0, b->img_total * sizeof(double), s));
+  RT_CUDA(c, cudaMemsetAsync(b->d_tallies, 0, (size_t)b->n_models * 4 * sizeof(double), s));
+  RT_CUDA(c, cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(unsigned long long), s));
+  RT_CUDA(c, cudaMemsetAsync(b->d_flags, 0, sizeof(int), s));
+  return RT_OK;
+}
+
+rt_status rt_batch_read_images(rt_ctx c, int32_t id, double* dst, size_t n_elems, int32_t on_device, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  Batch* b = get_batch(c, id);
+  if (!b) return fail(c, RT_ERR_ARG, "rt_batch_read_images: unknown batch %d", id);
+  if (!dst) return fail(c, RT_ERR_ARG, "rt_batch_read_images: null destination");
+  if (n_elems != b->img_total) return fail(c, RT_ERR_ARG, "rt_batch_read_images: n_elems %zu != %zu", n_elems, b->img_total);
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  return copy_out(c, dst, b->d_images, n_elems, on_device, stream);
+}
+
+rt_status rt_batch_read_tallies(rt_ctx c, int32_t id, double* dst, size_t n_elems, int32_t on_device, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  Batch* b = get_batch(c, id);
+  if (!b) return fail(c, RT_ERR_ARG, "rt_batch_read_tallies: unknown batch %d", id);
+  if (!dst) return fail(c, RT_ERR_ARG, "rt_batch_read_tallies: null destination");
+  const size_t n = (size_t)b->n_models * 4;
+  if (n_elems != n) return fail(c, RT_ERR_ARG, "rt_batch_read_tallies: n_elems %zu != %zu", n_elems, n);
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  return copy_out(c, dst, b->d_tallies, n, on_device, stream);
+}
+
+rt_status rt_batch_read_stats(rt_ctx c, int32_t id, rt_stats* out) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  Batch* b = get_batch(c, id);
+  if (!b) return fail(c, RT_ERR_ARG, "rt_batch_read_stats: unknown batch %d", id);
+  if (!out) return fail(c, RT_ERR_ARG, "rt_batch_read_stats: null output");
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  RT_CUDA(c, cudaDeviceSynchronize());
+  std::vector<double> t((size_t)b->n_models * 4);
+  unsigned long long cn[4];
+  int flags = 0;
+  RT_CUDA(c, cudaMemcpy(t.data(), b->d_tallies, t.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  RT_CUDA(c, cudaMemcpy(cn, b->d_counters, sizeof cn, cudaMemcpyDeviceToHost));
+  RT_CUDA(c, cudaMemcpy(&flags, b->d_flags, sizeof flags, cudaMemcpyDeviceToHost));
+  std::memset(out, 0, sizeof *out);
+  for (int m = 0; m < b->n_models; ++m) {
+    out->emitted += t[(size_t)m * 4];
+    out->escaped += t[(size_t)m * 4 + 1];
+    out->absorbed += t[(size_t)m * 4 + 2];
+    out->truncated += t[(size_t)m * 4 + 3];
+  }
+  out->crossings = cn[0]; out->events = cn[1]; out->peeloffs = cn[2]; out->packets = cn[3];
+  out->device_flags = flags;
+  if (flags) return fail(c, RT_ERR_DEVICE_FLAG, "a kernel bounds check fired (flags 0x%x)", flags);
+  return RT_OK;
+}
+
+rt_status rt_batch_tune(rt_ctx c, int32_t id, uint64_t seed, double fraction, int32_t* control_lanes,
+                        uint32_t* run_packets, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  Batch* b = get_batch(c, id);
+  if (!b) return fail(c, RT_ERR_ARG, "rt_batch_tune: unknown batch %d", id);
+  if (!(fraction > 0 && fraction <= 1)) return fail(c, RT_ERR_ARG, "rt_batch_tune: fraction in (0, 1]");
+  rt_launch_opts o;
+  rt_status st = batch_opts(c, nullptr, seed, o);
+  if (st != RT_OK) return st;
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int lanes_c[] = {8, 12, 16, 20, 24, 28, 32};
+  const unsigned runs_c[] = {64, 256, 1024, 4096};
+  cudaEvent_t e0, e1;
+  RT_CUDA(c, cudaEventCreate(&e0));
+  RT_CUDA(c, cudaEventCreate(&e1));
+  float best = -1.0f;
+  int best_lanes = 16;
+  unsigned best_run = 1024;
+  BatchChunk* d_ch = nullptr;
+  cudaError_t e = cudaSuccess;
+  for (unsigned run : runs_c) {
+    const std::vector<BatchChunk> ch = batch_chunks(*b, run, fraction);
+    dfree(d_ch);
+    e = cudaMalloc(&d_ch, std::max<size_t>(1, ch.size()) * sizeof(BatchChunk));
+    if (e == cudaSuccess) e = cudaMemcpy(d_ch, ch.data(), ch.size() * sizeof(BatchChunk), cudaMemcpyHostToDevice);
+    for (int lanes : lanes_c) {
+      if (e != cudaSuccess) break;
+      o.control_lanes = lanes;
+      const BatchParams p = batch_params(b, o, seed, d_ch, (int)ch.size());
+      e = cudaMemsetAsync(b->d_chunk_counter, 0, sizeof(unsigned long long), s);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = launch_batch(p, b->blocks, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && (best < 0 || ms < best)) {
+        best = ms;
+        best_lanes = lanes;
+        best_run = run;
+      }
+    }
+  }
+  dfree(d_ch);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rt_batch_tune");
+  b->control_lanes = best_lanes;
+  if (best_run != b->run_packets) {
+    st = upload_chunks(c, b, best_run);
+    if (st != RT_OK) return st;
+  }
+  if (control_lanes) *control_lanes = best_lanes;
+  if (run_packets) *run_packets = best_run;
+  return rt_batch_reset(c, id, stream);
 }
 
 }  // extern "C"

@@ -1,0 +1,381 @@
+// Many small independent models in one persistent launch: parameter
+// searches run the same transport on thousands of small grids (the model
+// fitting of Sect. 1), each too small to fill a GB300 alone.
+//
+// Every model is a cartesian grid with one wavelength, one point source and
+// one single-channel frame; its packets are the forward kernel's packets with
+// Philox key (seed, model index), computed with the same arithmetic, so a
+// model of a batch gives the tallies of rt_launch_packets on that model
+// with model_id = its index.
+//
+// Work list: runs of packets of one model (chunks), sorted by estimated cost,
+// largest first, so that the long runs start early and the short ones fill
+// the tail.  A warp takes a chunk with one atomic and hands its packets to
+// its lanes as they need them; lanes of a warp may hold packets of different
+// models.  A lane keeps its model's grid geometry in its own shared-memory
+// slot (the cell walk reads it there), and the model's escaped / absorbed /
+// truncated luminosity in another, flushed to the model's FP64 tallies when
+// the lane moves to another model.
+#include "rt_transport.cuh"
+
+namespace rtk {
+
+namespace {
+
+using tr::CartGrid;
+
+// Grid geometry of a lane's model, in the shape CartGrid reads.
+struct Geo {
+  int nx, ny, nz, pad;
+  float lo[3], hi[3], d[3], inv_d[3];
+};
+
+struct Tally {
+  double escaped, absorbed, truncated;
+  int model, pad;
+};
+
+__shared__ Geo S_GEO[kBatchBlock];
+__shared__ Tally S_TALLY[kBatchBlock];
+
+struct BLane {
+  unsigned long long pid;
+  int m, event, phase;
+  double L;
+  float kappa;
+  float u_mu, u_phi;
+  float3 x, k;
+  CartGrid::Cell cell;
+  bool has_cell, walking;
+  float3 d, id;
+  CartGrid::Walk w;
+  float rho;
+  float th, tl;
+  float aux0, aux1;   // path 1: deposit weight (unused here); path 2: tau* pair, then s*
+  const float* dens;  // the model's densities
+};
+
+__device__ __forceinline__ void flush(const BatchParams& P, Tally& t) {
+  if (t.model >= 0) {
+    double* q = &P.tallies[(size_t)t.model * 4];
+    if (t.escaped != 0.0) atomicAdd(&q[1], t.escaped);
+    if (t.absorbed != 0.0) atomicAdd(&q[2], t.absorbed);
+    if (t.truncated != 0.0) atomicAdd(&q[3], t.truncated);
+  }
+  t.escaped = t.absorbed = t.truncated = 0.0;
+}
+
+__device__ __forceinline__ void start_walk(BLane& s, const Geo& G, float3 d) {
+  s.d = d;
+  s.id = make_float3(tr::inv_or_zero(d.x), tr::inv_or_zero(d.y), tr::inv_or_zero(d.z));
+  s.th = 0.0f;
+  s.tl = 0.0f;
+  CartGrid::Scratch sc;
+  s.walking = CartGrid::init(G, s.x, d, s.id, s.has_cell, s.cell, s.w, sc);
+  if (s.walking) s.rho = tr::load_density(&s.dens[s.w.cell]);
+}
+
+__device__ __forceinline__ float3 kobs(const DevInstr& I) { return make_float3(I.kobs[0], I.kobs[1], I.kobs[2]); }
+
+// The forward kernel's peel-off deposit for a single-channel frame.
+__device__ __forceinline__ void deposit(const DevModel& M, const BLane& s, bool scattered) {
+  const DevInstr& I = M.instr;
+  float phase = 1.0f;
+  if (scattered) phase = hg_phase(M.g, s.k.x * I.kobs[0] + s.k.y * I.kobs[1] + s.k.z * I.kobs[2]);
+  const float tau = s.th;
+  const double value = tau < 80.0f ? s.L * kInv4PiD * (double)(phase * expf(-tau) * (1.0f - s.tl))
+                                   : s.L * kInv4PiD * (double)phase * exp(-((double)tau + (double)s.tl));
+  const float fx = (s.x.x * I.ex[0] + s.x.y * I.ex[1] + s.x.z * I.ex[2] + I.off_x) * I.sx;
+  const float fy = (s.x.x * I.ey[0] + s.x.y * I.ey[1] + s.x.z * I.ey[2] + I.off_y) * I.sy;
+  if (!I.bilinear) {
+    const float fix = floorf(fx), fiy = floorf(fy);
+    if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) return;
+    atomicAdd(&I.image[(size_t)(int)fiy * I.nx + (int)fix], value);
+    return;
+  }
+  const float gx = fx - 0.5f, gy = fy - 0.5f;
+  const float x0 = floorf(gx), y0 = floorf(gy);
+  const float tx = gx - x0, ty = gy - y0;
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy) {
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const float fix = x0 + dx, fiy = y0 + dy;
+      if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) continue;
+      const double v = value * (double)((dx ? tx : 1.0f - tx) * (dy ? ty : 1.0f - ty));
+      atomicAdd(&I.image[(size_t)(int)fiy * I.nx + (int)fix], v);
+    }
+  }
+}
+
+__device__ __forceinline__ void start_path(BLane& s, const Geo& G) {
+  s.phase = tr::kPath1;
+  start_walk(s, G, s.k);
+}
+
+// A new packet (model m, packet id pid): the model's geometry, emission from
+// its point source (the forward kernel's event-0 draws), the emission peel-off.
+__device__ __forceinline__ void begin(const BatchParams& P, BLane& s, Geo& G, Tally& T, int m,
+                                      unsigned long long pid) {
+  const DevModel& M = P.models[m];
+  if (T.model != m) {
+    flush(P, T);
+    T.model = m;
+  }
+  G.nx = M.nx; G.ny = M.ny; G.nz = M.nz;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    G.lo[a] = M.lo[a]; G.hi[a] = M.hi[a]; G.d[a] = M.d[a]; G.inv_d[a] = M.inv_d[a];
+  }
+  s.m = m;
+  s.pid = pid;
+  s.dens = P.density + M.density;
+  s.kappa = M.kappa;
+  s.L = M.L0;
+  s.event = 0;
+  s.has_cell = false;
+  // one point source: the position draws of block 0 are not needed
+  const uint4 r1 = draw_block(pid, 0, 0, 1, P.seed, (unsigned)m);
+  s.x = make_float3(M.src[0], M.src[1], M.src[2]);
+  const float mu = tr::u01f_signed(r1.z);
+  const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+  float sp, cp;
+  sincospif(2.0f * tr::u01f(r1.w), &sp, &cp);
+  s.k = make_float3(st * cp, st * sp, mu);
+  if (P.peel_emission) {
+    s.phase = tr::kPeelEmit;
+    start_walk(s, G, kobs(M.instr));
+  } else {
+    s.event = 1;
+    start_path(s, G);
+  }
+}
+
+__device__ __forceinline__ void after_scattering(const BatchParams& P, const DevModel& M, BLane& s, const Geo& G,
+                                                 Tally& T) {
+  const float mu = hg_sample(M.g, s.u_mu);
+  float sp, cp;
+  sincospif(2.0f * s.u_phi, &sp, &cp);
+  s.k = rotate_dir(s.k, mu, sp, cp);
+  if ((P.weight_cut && s.L < P.w_min * M.L0) || s.event >= P.max_events) {
+    T.truncated += s.L;
+    s.phase = tr::kFetch;
+    return;
+  }
+  s.event += 1;
+  start_path(s, G);
+}
+
+// Per-event work of a lane whose walk has ended (the forward kernel's, for a
+// single-channel frame and no absorption field).
+__device__ void control(const BatchParams& P, BLane& s, const Geo& G, Tally& T, unsigned& n_events,
+                        unsigned& n_peel) {
+  const DevModel& M = P.models[s.m];
+  while (true) {
+    switch (s.phase) {
+      case tr::kPeelEmit:
+      case tr::kPeelScat: {
+        const bool scattered = s.phase == tr::kPeelScat;
+        deposit(M, s, scattered);
+        n_peel += 1u;
+        if (!scattered) {
+          s.event = 1;
+          start_path(s, G);
+        } else {
+          after_scattering(P, M, s, G, T);
+        }
+        break;
+      }
+      case tr::kPath1: {
+        const double tau = (double)s.th + (double)s.tl;
+        if (!(tau > 0.0)) {
+          T.escaped += s.L;
+          s.phase = tr::kFetch;
+          return;
+        }
+        const double albedo = M.albedo;
+        const double one_minus_E = -expm1(-tau);
+        const double E = 1.0 - one_minus_E;
+        T.escaped += s.L * E;
+        T.absorbed += (1.0 - albedo) * s.L * one_minus_E;
+        const uint4 r = draw_block(s.pid, 0, s.event, 0, P.seed, (unsigned)s.m);
+        const double tau_star = -log1p(-u01(r.x) * one_minus_E);
+        s.u_mu = tr::u01f(r.y);
+        s.u_phi = tr::u01f(r.z);
+        s.aux0 = (float)tau_star;
+        s.aux1 = (float)(tau_star - (double)s.aux0);
+        s.L = albedo * s.L * one_minus_E;
+        s.phase = tr::kPath2;
+        start_walk(s, G, s.k);
+        break;
+      }
+      case tr::kPath2: {
+        const float s_star = s.aux0;
+        float3 x = make_float3(fmaf(s_star, s.k.x, s.x.x), fmaf(s_star, s.k.y, s.x.y), fmaf(s_star, s.k.z, s.x.z));
+        s.cell = CartGrid::carried(s.w);
+        CartGrid::clamp(G, s.cell, x);
+        s.x = x;
+        s.has_cell = true;
+        n_events += 1u;
+        if (P.peel_scatter) {
+          s.phase = tr::kPeelScat;
+          start_walk(s, G, kobs(M.instr));
+        } else {
+          after_scattering(P, M, s, G, T);
+        }
+        break;
+      }
+      default:
+        return;
+    }
+    if (s.phase == tr::kFetch || s.phase == tr::kExit) return;
+    if (s.walking) return;
+  }
+}
+
+// One cell crossing (the forward kernel's step without the absorption field).
+__device__ __forceinline__ void step(const BatchParams& P, BLane& s, const Geo& G, unsigned& n_cross) {
+  CartGrid::Walk& w = s.w;
+  int axis;
+  const float te = CartGrid::exit(w, s.x, s.id, axis);
+  const float texit = fmaxf(te, w.t);
+  const float ds = texit - w.t;
+  const float kr = s.kappa * s.rho;
+  const float dt = kr * ds;
+  float nh, e;
+  tr::two_sum(s.th, dt, nh, e);
+  const float nl = s.tl + e;
+  const bool path2 = s.phase == tr::kPath2;
+  if (path2 && (nh - s.aux0) + (nl - s.aux1) > 0.0f) {
+    const float rem = ((s.aux0 - s.th) + s.aux1) - s.tl;
+    s.aux0 = w.t + rem / kr;
+    s.walking = false;
+    return;
+  }
+  s.th = nh;
+  s.tl = nl;
+  n_cross += path2 ? 0u : 1u;
+  w.t = texit;
+  CartGrid::Scratch sc;
+  if (CartGrid::advance(G, s.x, s.d, s.id, axis, w, sc)) {
+    s.rho = tr::load_density(&s.dens[w.cell]);
+  } else {
+    s.walking = false;
+    if (path2) {  // not reachable (see the forward kernel)
+      atomicOr(P.flags, kFlagNoInteraction);
+      s.aux0 = texit;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBatchBlock, 3) k_batch(const BatchParams P) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  Geo& G = S_GEO[threadIdx.x];
+  Tally& T = S_TALLY[threadIdx.x];
+  T.escaped = T.absorbed = T.truncated = 0.0;
+  T.model = -1;
+  BLane s;
+  s.phase = tr::kFetch;
+  s.walking = false;
+  s.m = 0;
+  unsigned n_cross = 0, n_events = 0, n_peel = 0, n_packets = 0;
+  unsigned long long tot_cross = 0;
+  // the warp's current chunk (the same in every lane)
+  unsigned long long c_next = 0, c_end = 0;
+  int c_model = 0;
+  bool drained = false;
+  while (true) {
+    const bool idle = !s.walking && s.phase != tr::kExit;
+    const unsigned need = __ballot_sync(0xffffffffu, idle);
+    const unsigned walkers = __ballot_sync(0xffffffffu, s.walking);
+    if (need == 0u && walkers == 0u) break;
+    if (walkers == 0u || __popc(need) >= P.control_min) {
+      if (idle && s.phase != tr::kFetch) control(P, s, G, T, n_events, n_peel);
+      const bool wants = !s.walking && s.phase == tr::kFetch;
+      const unsigned fetchers = __ballot_sync(0xffffffffu, wants);
+      if (fetchers) {
+        // hand out packets of the warp's chunk, taking new chunks as needed
+        const int rank = __popc(fetchers & lt_mask);
+        int remaining = __popc(fetchers), done = 0;
+        int my_model = -1;
+        unsigned long long my_pid = 0;
+        while (remaining > 0 && !drained) {
+          if (c_next >= c_end) {
+            unsigned long long ci = 0;
+            if (lane == 0) ci = atomicAdd(P.chunk_counter, 1ull);
+            ci = __shfl_sync(0xffffffffu, ci, 0);
+            if (ci >= (unsigned long long)P.n_chunks) {
+              drained = true;
+              break;
+            }
+            const BatchChunk ch = P.chunks[ci];
+            c_model = ch.model;
+            c_next = ch.first;
+            c_end = ch.first + ch.count;
+          }
+          const unsigned long long avail = c_end - c_next;
+          const int take = avail < (unsigned long long)remaining ? (int)avail : remaining;
+          if (wants && rank >= done && rank < done + take) {
+            my_model = c_model;
+            my_pid = c_next + (unsigned long long)(rank - done);
+          }
+          c_next += (unsigned long long)take;
+          done += take;
+          remaining -= take;
+        }
+        if (wants) {
+          if (my_model >= 0) {
+            begin(P, s, G, T, my_model, my_pid);
+            n_packets += 1u;
+            if (!s.walking) control(P, s, G, T, n_events, n_peel);
+          } else {
+            s.phase = tr::kExit;
+          }
+        }
+      }
+      if (n_cross & 0xC0000000u) {
+        tot_cross += n_cross;
+        n_cross = 0;
+      }
+    }
+    if (s.walking) step(P, s, G, n_cross);
+  }
+  flush(P, T);
+  tot_cross += n_cross;
+  unsigned long long ev = n_events, pe = n_peel, pk = n_packets;
+  for (int o = 16; o > 0; o >>= 1) {
+    tot_cross += __shfl_down_sync(0xffffffffu, tot_cross, o);
+    ev += __shfl_down_sync(0xffffffffu, ev, o);
+    pe += __shfl_down_sync(0xffffffffu, pe, o);
+    pk += __shfl_down_sync(0xffffffffu, pk, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&P.counters[0], tot_cross);
+    atomicAdd(&P.counters[1], ev);
+    atomicAdd(&P.counters[2], pe);
+    atomicAdd(&P.counters[3], pk);
+  }
+}
+
+// Every model emits its luminosity per launch.
+__global__ void k_batch_emitted(double* tallies, const double* lum, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) tallies[(size_t)i * 4] += lum[i];
+}
+
+}  // namespace
+
+const void* batch_kernel() { return reinterpret_cast<const void*>(&k_batch); }
+const void* batch_emitted_kernel() { return reinterpret_cast<const void*>(&k_batch_emitted); }
+
+cudaError_t launch_batch(const BatchParams& p, unsigned blocks, cudaStream_t stream) {
+  k_batch<<<blocks, kBatchBlock, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_blocks_per_sm(int* blocks) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_batch, kBatchBlock, 0);
+}
+
+}  // namespace rtk

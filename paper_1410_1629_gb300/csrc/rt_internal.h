@@ -122,6 +122,48 @@ struct AdjRecord {
 static_assert(sizeof(AdjRecord) == 132, "AdjRecord layout");
 constexpr int kMaxAdjointEvents = 256;
 
+// One model of a batch (rt_batch.cu): cartesian grid, one wavelength, one
+// point source, one single-channel frame.
+struct DevModel {
+  int nx, ny, nz, pad0;
+  float lo[3], hi[3], d[3], inv_d[3];  // as FwdParams
+  float kappa, g;
+  float src[3];                        // point source position
+  int pad1;
+  double albedo;
+  double L0;                           // packet weight: luminosity / packets
+  long long density;                   // offset of the model's densities in the batch buffer
+  DevInstr instr;                      // its frame; image = the model's image [ny][nx]
+};
+// A run of packets [first, first + count) of one model; the work list is
+// sorted by estimated cost, largest first.
+struct BatchChunk {
+  unsigned long long first;
+  int model;
+  unsigned count;
+};
+struct BatchParams {
+  const DevModel* models;
+  const BatchChunk* chunks;
+  int n_models, n_chunks;
+  const float* density;
+  double* tallies;                     // [n_models][4]: emitted (host side), escaped, absorbed, truncated
+  unsigned long long* chunk_counter;
+  unsigned long long* counters;        // [4]: crossings, events, peel-offs, packets
+  int* flags;
+  double w_min;
+  unsigned seed;
+  int max_events, weight_cut, peel_emission, peel_scatter, control_min;
+};
+constexpr int kBatchBlock = 256;
+// The batch kernel and the per-launch emitted-tally kernel (graph nodes:
+// k_batch(BatchParams), k_batch_emitted(double* tallies, const double* lum,
+// int n)), the batch kernel's resident blocks per SM, and a plain launch.
+const void* batch_kernel();
+const void* batch_emitted_kernel();
+cudaError_t batch_blocks_per_sm(int* blocks);
+cudaError_t launch_batch(const BatchParams& p, unsigned blocks, cudaStream_t stream);
+
 // Lanes (threads) of the adjoint launch for n_total packets; the record
 // buffer holds lanes * (max_events + 1) records.
 cudaError_t adjoint_lanes(int num_sms, unsigned long long n_total, unsigned long long* lanes);

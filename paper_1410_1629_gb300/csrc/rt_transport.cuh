@@ -143,15 +143,19 @@ struct CartGrid {
   };
   struct Scratch {};
 
-  __device__ static __forceinline__ float plane_t(const FwdParams& P, int a, int i, float xa, float ida) {
+  // Geo: the grid geometry, nx, ny, nz, lo[3], hi[3], d[3], inv_d[3] (the
+  // launch parameters, or one model of a batch).
+  template <class Geo>
+  __device__ static __forceinline__ float plane_t(const Geo& P, int a, int i, float xa, float ida) {
     return (fmaf((float)i, P.d[a], P.lo[a]) - xa) * ida;
   }
 
   // Start a walk from x along d (inverse id; id_a = 0 marks d_a = 0).  With a
   // known cell x lies in it; otherwise x is located or the entry point found.
   // False if the ray misses the grid.
-  __device__ static __forceinline__ bool init(const FwdParams& P, float3 x, float3 d, float3 id, bool known,
-                                              const Cell& c, Walk& w, Scratch&) {
+  template <class Geo>
+  __device__ static __forceinline__ bool init(const Geo& P, float3 x, float3 d, float3 id, bool known, const Cell& c,
+                                              Walk& w, Scratch&) {
     w.t = 0.0f;
     if (known) {
       w.ix = c.ix; w.iy = c.iy; w.iz = c.iz;
@@ -185,8 +189,9 @@ struct CartGrid {
   // Move through face `axis` (w.t already at the exit); false when the ray
   // leaves the grid, in which case the walk still describes the last cell.
   // Selects rather than branches: the warp issues the advance once.
-  __device__ static __forceinline__ bool advance(const FwdParams& P, float3 x, float3, float3 id, int axis,
-                                                 Walk& w, Scratch&) {
+  template <class Geo>
+  __device__ static __forceinline__ bool advance(const Geo& P, float3 x, float3, float3 id, int axis, Walk& w,
+                                                 Scratch&) {
     const bool bz = axis == 2, by = axis == 1;
     const float ida = bz ? id.z : (by ? id.y : id.x);
     const int step = ida > 0.0f ? 1 : -1;
@@ -212,7 +217,8 @@ struct CartGrid {
   __device__ static __forceinline__ Cell carried(const Walk& w) { return Cell{w.ix, w.iy, w.iz}; }
 
   // Keep x inside cell c.
-  __device__ static __forceinline__ void clamp(const FwdParams& P, const Cell& c, float3& x) {
+  template <class Geo>
+  __device__ static __forceinline__ void clamp(const Geo& P, const Cell& c, float3& x) {
     x.x = fminf(fmaxf(x.x, fmaf((float)c.ix, P.d[0], P.lo[0])), fmaf((float)(c.ix + 1), P.d[0], P.lo[0]));
     x.y = fminf(fmaxf(x.y, fmaf((float)c.iy, P.d[1], P.lo[1])), fmaf((float)(c.iy + 1), P.d[1], P.lo[1]));
     x.z = fminf(fmaxf(x.z, fmaf((float)c.iz, P.d[2], P.lo[2])), fmaf((float)(c.iz + 1), P.d[2], P.lo[2]));

@@ -93,6 +93,13 @@ class rt_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class rt_model_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("bounds", ctypes.c_double * 6), ("density", ctypes.c_void_p), ("kappa", ctypes.c_double),
+                ("albedo", ctypes.c_double), ("g", ctypes.c_double), ("luminosity", ctypes.c_double),
+                ("source", ctypes.c_double * 3), ("instrument", rt_instrument_desc), ("n_packets", ctypes.c_uint64)]
+
+
 # name -> (restype, argtypes): the exported symbols of include/rt.h
 SIGNATURES = {
     "rt_version": (ctypes.c_char_p, []),
@@ -124,6 +131,19 @@ SIGNATURES = {
                                                    ctypes.POINTER(rt_instrument_desc), ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                                    ctypes.POINTER(rt_launch_opts), ctypes.c_void_p, ctypes.c_void_p]),
+    "rt_batch_create": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(rt_model_desc),
+                                         ctypes.POINTER(ctypes.c_int32)]),
+    "rt_batch_destroy": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "rt_batch_launch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(rt_launch_opts),
+                                         ctypes.c_void_p]),
+    "rt_batch_reset": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "rt_batch_read_images": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                              ctypes.c_int32, ctypes.c_void_p]),
+    "rt_batch_read_tallies": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                               ctypes.c_int32, ctypes.c_void_p]),
+    "rt_batch_read_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(rt_stats)]),
+    "rt_batch_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p]),
 }
 
 _lib = None
@@ -306,6 +326,50 @@ def rt_launch_packets_noalloc(grid_desc_, kappa, albedo, g, sources, luminositie
         raise RTError(st, lib().rt_last_error(None).decode())
 
 
+def rt_batch_create(ctx, descs) -> int:
+    arr = (rt_model_desc * len(descs))(*descs)
+    b = ctypes.c_int32()
+    _check(ctx, lib().rt_batch_create(ctx, len(descs), arr, ctypes.byref(b)))
+    return b.value
+
+
+def rt_batch_destroy(ctx, batch_id):
+    _check(ctx, lib().rt_batch_destroy(ctx, int(batch_id)))
+
+
+def rt_batch_launch(ctx, batch_id, seed=0, opts=None, stream=None):
+    o = opts if opts is not None else rt_default_opts()
+    _check(ctx, lib().rt_batch_launch(ctx, int(batch_id), int(seed), ctypes.byref(o), _stream_ptr(stream)))
+
+
+def rt_batch_reset(ctx, batch_id, stream=None):
+    _check(ctx, lib().rt_batch_reset(ctx, int(batch_id), _stream_ptr(stream)))
+
+
+def rt_batch_read_images(ctx, batch_id, dst_ptr, n_elems, on_device, stream=None):
+    _check(ctx, lib().rt_batch_read_images(ctx, int(batch_id), dst_ptr, int(n_elems), int(on_device),
+                                           _stream_ptr(stream)))
+
+
+def rt_batch_read_tallies(ctx, batch_id, dst_ptr, n_elems, on_device, stream=None):
+    _check(ctx, lib().rt_batch_read_tallies(ctx, int(batch_id), dst_ptr, int(n_elems), int(on_device),
+                                            _stream_ptr(stream)))
+
+
+def rt_batch_read_stats(ctx, batch_id) -> rt_stats:
+    s = rt_stats()
+    _check(ctx, lib().rt_batch_read_stats(ctx, int(batch_id), ctypes.byref(s)))
+    return s
+
+
+def rt_batch_tune(ctx, batch_id, seed=0, fraction=0.05, stream=None):
+    lanes = ctypes.c_int32()
+    run = ctypes.c_uint32()
+    _check(ctx, lib().rt_batch_tune(ctx, int(batch_id), int(seed), float(fraction), ctypes.byref(lanes),
+                                    ctypes.byref(run), _stream_ptr(stream)))
+    return lanes.value, run.value
+
+
 # ---------------------------------------------------------------- descriptors from workloads
 def grid_desc(grid, on_device_arrays=None):
     """rt_grid_desc for a workloads.Grid (host arrays; kept alive by the returned tuple)."""
@@ -346,6 +410,106 @@ def instrument_desc(q):
     d.deposit = RT_DEPOSIT_BILINEAR if q.bilinear else RT_DEPOSIT_NEAREST
     d.channels = int(q.channels)
     return d
+
+
+def model_desc(problem, n_packets=None):
+    """rt_model_desc for a one-wavelength cartesian Problem with one point
+    source and one single-channel frame (host density kept alive by the
+    returned tuple)."""
+    if problem.grid.kind != "cartesian" or problem.n_lambda != 1 or len(problem.sources) != 1 \
+            or problem.sources[0].kind != "point" or len(problem.instruments) != 1 or problem.instruments[0].channels != 1:
+        raise ValueError("a batch model has a cartesian grid, one wavelength, one point source and one frame")
+    d = rt_model_desc()
+    dens = np.ascontiguousarray(problem.grid.density, dtype=np.float32)
+    d.nz, d.ny, d.nx = dens.shape
+    d.bounds[:] = [float(b) for b in np.asarray(problem.grid.bounds, dtype=np.float64)]
+    d.density = dens.ctypes.data
+    d.kappa, d.albedo, d.g = float(problem.kappa[0]), float(problem.albedo[0]), float(problem.g[0])
+    d.luminosity = float(problem.sources[0].lum[0])
+    d.source[:] = [float(c) for c in problem.sources[0].center]
+    d.instrument = instrument_desc(problem.instruments[0])
+    d.n_packets = int(problem.run.n_per_lambda if n_packets is None else n_packets)
+    return d, dens
+
+
+class Batch:
+    """A batch of one-wavelength models (workloads.Problem each) in one
+    context: uploaded once, launched any number of times as one persistent
+    kernel; images and per-model tallies read back."""
+
+    def __init__(self, problems, device: int = 0, n_packets=None):
+        self.problems = list(problems)
+        self.device = int(device)
+        self.ctx = rt_context_create(self.device)
+        try:
+            descs, keep = [], []
+            for i, p in enumerate(self.problems):
+                d, dens = model_desc(p, None if n_packets is None else n_packets[i])
+                descs.append(d)
+                keep.append(dens)
+            self.id = rt_batch_create(self.ctx, descs)
+            del keep
+        except Exception:
+            self.close()
+            raise
+        self.shapes = [(p.instruments[0].ny, p.instruments[0].nx) for p in self.problems]
+        self.n_image = int(sum(a * b for a, b in self.shapes))
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            rt_context_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def opts(self, **kw) -> rt_launch_opts:
+        o = rt_default_opts()
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown launch option {k}")
+            setattr(o, k, v)
+        return o
+
+    def launch(self, seed=0, stream=None, **opts):
+        rt_batch_launch(self.ctx, self.id, seed, self.opts(**opts), stream)
+
+    def reset(self, stream=None):
+        rt_batch_reset(self.ctx, self.id, stream)
+
+    def tune(self, seed=0, fraction=0.05, stream=None):
+        return rt_batch_tune(self.ctx, self.id, seed, fraction, stream)
+
+    def images_flat(self, device=True, stream=None):
+        if device:
+            import torch
+            t = torch.empty(self.n_image, dtype=torch.float64, device=f"cuda:{self.device}")
+            rt_batch_read_images(self.ctx, self.id, t.data_ptr(), self.n_image, 1, stream)
+        else:
+            t = np.empty(self.n_image, dtype=np.float64)
+            rt_batch_read_images(self.ctx, self.id, t.ctypes.data, self.n_image, 0, stream)
+        return t
+
+    def images(self):
+        """Per-model images as numpy arrays [ny][nx]."""
+        flat = self.images_flat(device=False)
+        out, o = [], 0
+        for ny, nx in self.shapes:
+            out.append(flat[o:o + ny * nx].reshape(ny, nx))
+            o += ny * nx
+        return out
+
+    def tallies(self):
+        """[n_models][4]: emitted, escaped, absorbed, truncated."""
+        t = np.empty((len(self.problems), 4), dtype=np.float64)
+        rt_batch_read_tallies(self.ctx, self.id, t.ctypes.data, t.size, 0, None)
+        return t
+
+    def stats(self) -> dict:
+        return rt_batch_read_stats(self.ctx, self.id).as_dict()
 
 
 class Simulation:

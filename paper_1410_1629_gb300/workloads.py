@@ -215,6 +215,48 @@ def lognormal_cube(n_cells=64, sigma_ln=1.0, mean_axis_tau=2.0, smooth_cells=2.0
     )
 
 
+def batch_models(n_models=4096, seed=5, n_pix=64, packets=(1e4, 1e6), sides=(8, 48), axis_tau=(0.1, 20.0),
+                 g=(0.0, 0.9), albedo=(0.3, 0.8)) -> list:
+    """Many small one-wavelength models for a batched launch (the parameter
+    searches of model fitting, Sect. 1).  Per model, drawn with
+    ``default_rng(seed)``: cells per side uniform in ``sides`` (inclusive) on
+    [-1, 1]^3; half the models (a random half) uniform, the others an
+    exponential slab rho ~ exp(-|z| / (0.2 side)) with side = 2 the cube's
+    side length, at cell centres; the optical depth along the full x axis
+    through the centre (the central row of cells, kappa = 1) log-uniform in
+    ``axis_tau``; g and the albedo uniform in their ranges; a central point
+    source of unit luminosity; one ``n_pix``^2 face-on frame covering the
+    cube; packets log-uniform in ``packets``."""
+    rng = np.random.default_rng(seed)
+    n_side = rng.integers(sides[0], sides[1] + 1, n_models)
+    slab = rng.permutation(np.arange(n_models) < n_models // 2)
+    taus = np.exp(rng.uniform(np.log(axis_tau[0]), np.log(axis_tau[1]), n_models))
+    gs = rng.uniform(g[0], g[1], n_models)
+    albs = rng.uniform(albedo[0], albedo[1], n_models)
+    pk = np.rint(np.exp(rng.uniform(np.log(packets[0]), np.log(packets[1]), n_models))).astype(np.int64)
+    bounds = [-1.0, 1.0] * 3
+    out = []
+    for m in range(n_models):
+        side = int(n_side[m])
+        if slab[m]:
+            _, _, zs = cell_centres(bounds, (side, side, side))
+            dens = np.broadcast_to(np.exp(-np.abs(zs) / (0.2 * 2.0))[:, None, None], (side, side, side))
+        else:
+            dens = np.ones((side, side, side))
+        column = dens[side // 2, side // 2, :].sum() * (2.0 / side)
+        dens = np.ascontiguousarray(dens * (taus[m] / column), dtype=np.float32)
+        out.append(Problem(
+            name=f"batch_model_{m}",
+            grid=cartesian_grid(bounds, dens),
+            wavelengths=_f64([0.55]), kappa=_f64([1.0]), albedo=_f64([albs[m]]), g=_f64([gs[m]]),
+            sources=[Source("point", (0.0, 0.0, 0.0), _f64([1.0]))],
+            instruments=[face_on(n_pix, 1.0)],
+            run=Run(n_per_lambda=int(pk[m])),
+            meta={"model": m, "slab": bool(slab[m]), "axis_tau": float(taus[m])},
+        ))
+    return out
+
+
 def with_density(problem: Problem, density) -> Problem:
     """Copy of ``problem`` with a different density array (same grid shape)."""
     grid = replace(problem.grid, density=np.ascontiguousarray(density, dtype=np.float32))

@@ -60,6 +60,37 @@ def test_struct_sizes_match_the_header():
     assert ctypes.sizeof(rt.rt_stats) == 32 + 48 + 8
 
 
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets the
+    C compiler gives the header's struct."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"rt_grid_desc": rt.rt_grid_desc, "rt_source_desc": rt.rt_source_desc,
+               "rt_instrument_desc": rt.rt_instrument_desc, "rt_record": rt.rt_record,
+               "rt_trace_row": rt.rt_trace_row, "rt_launch_opts": rt.rt_launch_opts, "rt_stats": rt.rt_stats,
+               "rt_model_desc": rt.rt_model_desc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rt.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            # a trailing underscore marks a C member named like a Python keyword
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f.rstrip("_")}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+
+
 def test_no_gpu_context_creation_reports_an_error():
     import torch
     if torch.cuda.is_available():
