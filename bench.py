@@ -35,12 +35,14 @@ L2_FLUSH_BYTES = 256 << 20
 # peel-off crossing = 4 B density; peel-off deposit = 16 B FP64 pixel RMW
 BYTES_PATH_CROSSING, BYTES_PEEL_CROSSING, BYTES_DEPOSIT = 20, 4, 16
 # DRAM bytes (read + write) per packet of the forward kernel, from an ncu
-# capture of one 2e6-packet launch of this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum = 69.505 GB), valid only for the kernel sources whose
-# hash is given; the per-launch traffic is this figure times the packets.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "6a5417c8209c9bfd", "bytes_per_packet": 69505258496 / 2e6}
+# capture of one 2e6-packet launch of this workload (dram__bytes_read.sum
+# 50.396 GB + dram__bytes_write.sum 18.633 GB), valid only for the kernel
+# sources whose hash is given; the per-launch traffic is this figure times
+# the packets.
+TRAFFIC_CAPTURE = {"sources_sha256_16": "fc916bb89d1c1211", "bytes_per_packet": (50396154624 + 18632865280) / 2e6}
 KERNEL_SOURCES = ["paper_1410_1629_gb300/csrc/rt_forward.cu", "paper_1410_1629_gb300/csrc/rt_device.cuh",
-                  "paper_1410_1629_gb300/csrc/rt_internal.h", "paper_1410_1629_gb300/csrc/rt_transport.cuh"]
+                  "paper_1410_1629_gb300/csrc/rt_internal.h", "paper_1410_1629_gb300/csrc/rt_transport.cuh",
+                  "paper_1410_1629_gb300/build.py"]
 
 
 def kernel_sources_hash():
@@ -194,8 +196,8 @@ def adjoint_ratio(args, device, stream, flush):
     import torch
     from paper_1410_1629_gb300 import rt
     from paper_1410_1629_gb300 import workloads as W
-    prob = W.lognormal_cube()
-    target_prob = W.lognormal_cube(seed=104)
+    prob = W.lognormal_cube(n_packets=int(args.adjoint_packets))
+    target_prob = W.lognormal_cube(seed=104, n_packets=int(args.adjoint_packets))
     n = prob.run.n_per_lambda
     opts = dict(max_events=prob.run.max_events, weight_cut=0)
     sim = rt.Simulation(prob, device=device)
@@ -244,7 +246,7 @@ def adjoint_ratio(args, device, stream, flush):
     finally:
         sim.close()
         tsim.close()
-    return {"workload": "lognormal_cube_64: 64^3 cells, 1e7 packets, 128^2 bilinear detector, 20 events, "
+    return {"workload": f"lognormal_cube_64: 64^3 cells, {n:.3g} packets, 128^2 bilinear detector, 20 events, "
                         "L2 image loss against an independent field",
             "forward_ms": 1e3 * t_f, "adjoint_ms": 1e3 * t_b, "ratio": t_b / t_f,
             "forward_crossings": int(st["crossings"]), "adjoint_crossings": adj_cross,
@@ -260,8 +262,10 @@ def batch_rate(args, device, stream):
     import torch
     from paper_1410_1629_gb300 import rt
     from paper_1410_1629_gb300 import workloads as W
-    models = W.batch_models()
-    b = rt.Batch(models, device=device)
+    models = W.batch_models(n_models=args.batch_models)
+    scale = args.batch_packet_scale
+    counts = None if scale == 1.0 else [max(1, int(round(m.run.n_per_lambda * scale))) for m in models]
+    b = rt.Batch(models, device=device, n_packets=counts)
     try:
         lanes, run = b.tune(seed=0, fraction=0.02, stream=stream.cuda_stream)
         ts = []
@@ -279,8 +283,8 @@ def batch_rate(args, device, stream):
     finally:
         b.close()
     t = sum(ts) / len(ts)
-    return {"workload": "4096 models: 8^3-48^3 cells, half uniform / half exponential slab, axis tau 0.1-20, "
-                        "g 0-0.9, albedo 0.3-0.8, 1e4-1e6 packets, one 64^2 frame each",
+    return {"workload": f"{len(models)} models: 8^3-48^3 cells, half uniform / half exponential slab, axis tau 0.1-20, "
+                        f"g 0-0.9, albedo 0.3-0.8, {scale:g} x (1e4-1e6) packets, one 64^2 frame each",
             "models": len(models), "packets": int(st["packets"]), "seconds_per_launch": t,
             "packets_per_s": st["packets"] / t, "crossings_per_s": st["crossings"] / t,
             "tuned": {"control_lanes": lanes, "run_packets": run}, "launch": "CUDA graph",
@@ -441,6 +445,13 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--only", choices=["adjoint", "batch"], default=None,
+                    help="run one sub-measurement alone and print its object (profiling)")
+    ap.add_argument("--adjoint-packets", type=float, default=1e7,
+                    help="packets of the adjoint/forward measurement (default 1e7, the workload's size)")
+    ap.add_argument("--batch-models", type=int, default=4096, help="models of the batch measurement (default 4096)")
+    ap.add_argument("--batch-packet-scale", type=float, default=1.0,
+                    help="scale of every batch model's packet count (default 1, the workload's size)")
     ap.add_argument("--skip-batch", action="store_true",
                     help="skip the batched 4096-model measurement")
     ap.add_argument("--skip-adjoint", action="store_true",
@@ -460,6 +471,18 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.only:
+        # one sub-measurement alone (for profiling): its JSON object only
+        import torch
+        torch.cuda.set_device(0)
+        stream = torch.cuda.Stream(0)
+        if args.only == "adjoint":
+            flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda:0")
+            out = adjoint_ratio(args, 0, stream, flush)
+        else:
+            out = batch_rate(args, 0, stream)
+        print(json.dumps({"only": args.only, args.only: out}), flush=True)
+        return
     prob = workload(args.packets, args.workload)
     if args.impl == "reference":
         run_reference(args, prob, world, rank)
