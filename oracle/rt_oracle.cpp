@@ -255,11 +255,21 @@ struct Frame {
   int channels;
 };
 
+// Sines and cosines of the frame angles within 1e-15 of 0 or +-1 are taken
+// as exact: the angles of the usual face-on and edge-on frames are multiples
+// of pi/2, whose rounded values would otherwise leave components of order
+// 1e-17 in directions meant to lie along the axes.
+double snap_unit(double v) {
+  if (std::fabs(v) < 1e-15) return 0.0;
+  if (std::fabs(std::fabs(v) - 1.0) < 1e-15) return v > 0 ? 1.0 : -1.0;
+  return v;
+}
+
 Frame make_frame(const or_instrument& in) {
   Frame f;
-  double st = std::sin(in.inclination), ct = std::cos(in.inclination);
-  double sp = std::sin(in.azimuth), cp = std::cos(in.azimuth);
-  double so = std::sin(in.position_angle), co = std::cos(in.position_angle);
+  double st = snap_unit(std::sin(in.inclination)), ct = snap_unit(std::cos(in.inclination));
+  double sp = snap_unit(std::sin(in.azimuth)), cp = snap_unit(std::cos(in.azimuth));
+  double so = snap_unit(std::sin(in.position_angle)), co = snap_unit(std::cos(in.position_angle));
   f.kobs = {st * cp, st * sp, ct};
   V3d a = {-sp, cp, 0.0};            // image x axis before the position angle
   V3d b = {-ct * cp, -ct * sp, st};  // image y axis before the position angle

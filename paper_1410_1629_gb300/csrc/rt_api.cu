@@ -165,18 +165,8 @@ rt_status zero_tallies(rt_ctx c, cudaStream_t s) {
   return RT_OK;
 }
 
-// Frame axes from inclination, azimuth and position angle (FP64 on the host).
 void frame_axes(const rt_instrument_desc& d, double kobs[3], double ex[3], double ey[3]) {
-  const double st = std::sin(d.inclination), ct = std::cos(d.inclination);
-  const double sp = std::sin(d.azimuth), cp = std::cos(d.azimuth);
-  const double so = std::sin(d.position_angle), co = std::cos(d.position_angle);
-  kobs[0] = st * cp; kobs[1] = st * sp; kobs[2] = ct;
-  const double a[3] = {-sp, cp, 0.0};
-  const double b[3] = {-ct * cp, -ct * sp, st};
-  for (int i = 0; i < 3; ++i) {
-    ex[i] = co * a[i] - so * b[i];
-    ey[i] = so * a[i] + co * b[i];
-  }
+  rtk::frame_axes(d.inclination, d.azimuth, d.position_angle, kobs, ex, ey);
 }
 
 // Rebuild the small device tables (per-wavelength optics, sources, instruments).

@@ -2,6 +2,7 @@
 // kernels.  Not part of the public interface (include/rt.h).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -90,6 +91,29 @@ enum DeviceFlag : int { kFlagCellRange = 1, kFlagOctreeDepth = 2, kFlagWalkSteps
 // kernel flags an error and stops the walk (3 * 2^depth covers any ray for
 // the depths used; this is a safety net, not a tuning knob).
 constexpr unsigned kMaxWalkSteps = 1u << 22;
+
+// Frame axes from inclination, azimuth and position angle (Sect. 2.2; FP64
+// on the host).  Sines and cosines within 1e-15 of 0 or +-1 are taken as
+// exact, so that the face-on and edge-on frames (angles at multiples of pi/2)
+// look exactly along the grid axes.
+inline double snap_unit(double v) {
+  if (std::fabs(v) < 1e-15) return 0.0;
+  if (std::fabs(std::fabs(v) - 1.0) < 1e-15) return v > 0 ? 1.0 : -1.0;
+  return v;
+}
+inline void frame_axes(double inclination, double azimuth, double position_angle, double kobs[3], double ex[3],
+                       double ey[3]) {
+  const double st = snap_unit(std::sin(inclination)), ct = snap_unit(std::cos(inclination));
+  const double sp = snap_unit(std::sin(azimuth)), cp = snap_unit(std::cos(azimuth));
+  const double so = snap_unit(std::sin(position_angle)), co = snap_unit(std::cos(position_angle));
+  kobs[0] = st * cp; kobs[1] = st * sp; kobs[2] = ct;
+  const double a[3] = {-sp, cp, 0.0};
+  const double b[3] = {-ct * cp, -ct * sp, st};
+  for (int i = 0; i < 3; ++i) {
+    ex[i] = co * a[i] - so * b[i];
+    ey[i] = so * a[i] + co * b[i];
+  }
+}
 
 // Message returned by rt_last_error(NULL) (calls without a context).
 void set_context_free_error(const char* msg);

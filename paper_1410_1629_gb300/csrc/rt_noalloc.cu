@@ -202,16 +202,12 @@ extern "C" rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t
   }
   for (int q = 0; q < n_instruments; ++q) {
     const rt_instrument_desc& d = instruments[q];
-    const double st = std::sin(d.inclination), ct = std::cos(d.inclination);
-    const double sp = std::sin(d.azimuth), cp = std::cos(d.azimuth);
-    const double so = std::sin(d.position_angle), co = std::cos(d.position_angle);
-    const double kobs[3] = {st * cp, st * sp, ct};
-    const double a[3] = {-sp, cp, 0.0};
-    const double b[3] = {-ct * cp, -ct * sp, st};
+    double kobs[3], ex[3], ey[3];
+    frame_axes(d.inclination, d.azimuth, d.position_angle, kobs, ex, ey);
     for (int i = 0; i < 3; ++i) {
       ins[q].kobs[i] = (float)kobs[i];
-      ins[q].ex[i] = (float)(co * a[i] - so * b[i]);
-      ins[q].ey[i] = (float)(so * a[i] + co * b[i]);
+      ins[q].ex[i] = (float)ex[i];
+      ins[q].ey[i] = (float)ey[i];
     }
     ins[q].off_x = (float)(d.half_x - d.center_x);
     ins[q].off_y = (float)(d.half_y - d.center_y);
