@@ -34,6 +34,8 @@ L2_FLUSH_BYTES = 256 << 20
 # algorithmic bytes: forced-path crossing = 4 B density + 16 B FP64 absorption RMW;
 # peel-off crossing = 4 B density; peel-off deposit = 16 B FP64 pixel RMW
 BYTES_PATH_CROSSING, BYTES_PEEL_CROSSING, BYTES_DEPOSIT = 20, 4, 16
+# a peel-off along a grid axis reads 4 B of density and 4 B of column sum
+BYTES_COLUMN_PEEL = 8
 # DRAM bytes (read + write) per packet of the forward kernel, from an ncu
 # capture of one 2e6-packet launch of this workload (dram__bytes_read.sum
 # 50.396 GB + dram__bytes_write.sum 18.633 GB), valid only for the kernel
@@ -347,9 +349,13 @@ def run_gpu(args, prob, world, rank, local_rank):
     st = counts[-1]
     crossings_step = st["crossings"]
     path_cross = st["path_crossings"]
-    peel_cross = crossings_step - path_cross
+    # peel-off rays along grid axes read two numbers (the cell's density and
+    # its column sum) instead of walking; their crossings count as the walk's
+    column_cross, column_peels = st["column_crossings"], st["column_peels"]
+    peel_cross = crossings_step - path_cross - column_cross
     deposits = st["peeloffs"]
-    bytes_launch = BYTES_PATH_CROSSING * path_cross + BYTES_PEEL_CROSSING * peel_cross + BYTES_DEPOSIT * deposits
+    bytes_launch = (BYTES_PATH_CROSSING * path_cross + BYTES_PEEL_CROSSING * peel_cross
+                    + BYTES_COLUMN_PEEL * column_peels + BYTES_DEPOSIT * deposits)
     mean_launch = t_total / args.steps
     peak, peak_kind = peaks()
     achieved = bytes_launch / mean_launch / 1e9
@@ -432,7 +438,8 @@ def run_gpu(args, prob, world, rank, local_rank):
                 "batch": batch,
                 "clocks": clk,
                 "checks": {"conservation_rel": conservation, "path_crossings": int(path_cross),
-                           "peel_crossings": int(peel_cross), "peeloffs": int(deposits),
+                           "walked_peel_crossings": int(peel_cross), "column_peels": int(column_peels),
+                           "column_crossings": int(column_cross), "peeloffs": int(deposits),
                            "events": int(st["events"])}}
         print(json.dumps(line), flush=True)
 

@@ -150,7 +150,10 @@ typedef struct {
   int32_t peel_scatter;
   uint64_t n_norm;      /* packets per wavelength for the weight L_tot/n_norm; 0 = n_per_lambda */
   uint32_t model_id;    /* second Philox key word                                          */
-  int32_t block_size;   /* reserved; set to 0                                               */
+  int32_t walk_peels;   /* 0 (default): a peel-off towards a frame that looks exactly along a
+                           grid axis takes its optical depth from per-line suffix sums of the
+                           density (cartesian grids; rebuilt at every launch); 1: every
+                           peel-off walks its ray.  The two agree to FP32 rounding.       */
   rt_record* records;   /* device buffer for debug records, or NULL                        */
   int64_t records_capacity;
   uint64_t record_stride; /* record only packets whose id is a multiple of this (0, 1: all)  */
@@ -175,6 +178,8 @@ typedef struct {
   uint64_t peeloffs;    /* peel-off paths (one per instrument per emission / scattering)   */
   uint64_t packets;
   uint64_t records;     /* debug records produced (may exceed the capacity)                */
+  uint64_t column_peels;     /* peel-offs whose optical depth came from column sums        */
+  uint64_t column_crossings; /* the crossings of their rays (included in crossings)        */
   int32_t device_flags; /* non-zero if a kernel bounds check fired                         */
   int32_t reserved;
 } rt_stats;
@@ -287,7 +292,9 @@ rt_status rt_adjoint(rt_ctx ctx, const double* const* adj_images, int32_t n_adj_
                      const rt_launch_opts* opts, void* stream);
 
 /* The cartesian forward transport of rt_launch_packets without any device
- * memory allocation.  The paper has no counterpart: this entry point exists
+ * memory allocation (every peel-off walks its ray: there is no room for
+ * column sums, so it equals rt_launch_packets with opts->walk_peels = 1 to
+ * FP64 summation order).  The paper has no counterpart: this entry point exists
  * for callers that may not allocate GPU memory while they run (a plug-in
  * inside a framework that owns the device memory pool, a service with a fixed
  * memory budget), so they pass every device buffer themselves.
@@ -373,7 +380,8 @@ rt_status rt_batch_read_tallies(rt_ctx ctx, int32_t batch_id, double* dst, size_
                                 void* stream);
 
 /* Synchronise and sum: the totals over the models and the counters
- * (crossings, events, peeloffs, packets); records, path_crossings 0.
+ * (crossings, events, peeloffs, packets, column_peels, column_crossings);
+ * records, path_crossings 0.
  * Errors: RT_ERR_CUDA, RT_ERR_DEVICE_FLAG. */
 rt_status rt_batch_read_stats(rt_ctx ctx, int32_t batch_id, rt_stats* out);
 

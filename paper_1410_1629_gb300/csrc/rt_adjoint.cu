@@ -38,6 +38,7 @@
 // rescaled exactly with integer operations.
 #include "rt_transport.cuh"
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 
@@ -79,6 +80,9 @@ struct AdjParams {
   int e0[kMaxLambda];                     // exponent of the initial weight per wavelength
   double* grad;                           // [n_cells]
   AdjRecord* recs;                        // [lanes][max_events + 1]
+  double* line_dep[6];                    // frames along grid axes: per-line deposit differences, index
+                                          // 2 axis + (direction > 0); cell c holds what every cell
+                                          // beyond c on its line (in the ray's direction) receives
   int rec_stride;                         // records per lane
   unsigned long long* counters;           // optional: [0] crossings, [1] depositing crossings
 };
@@ -309,13 +313,10 @@ __device__ __forceinline__ void finish_path2(const AdjParams& A, ALane& s) {
   s.phase = aPeelScan;
 }
 
-// A peel-off measuring walk ended: value l = L phase e^{-tau} W / (4 pi) and
-// d tau / d x_a = -g_a / d_a; the event's share of (Lb, xb); then the
-// depositing walk, or the next peel-off.
-__device__ __forceinline__ void finish_peel_measure(const AdjParams& A, ALane& s) {
-  const DevInstr& I = tr::S_INSTR[s.q];
-  float3 dW;
-  const float W = adj_weight(A, s.q, s.lam, s.event > 0, s.x, dW);
+// A peel-off's value l = L phase e^{-tau} W / (4 pi) once its optical depth
+// (and d tau / d x_a = -g_a / d_a) is known, and the event's share of (Lb,
+// xb); returns l (units 2^eLA).
+__device__ __forceinline__ float peel_values(const AdjParams& A, ALane& s, const DevInstr& I, float W, float3 dW) {
   float phase = 1.0f;
   if (s.event > 0) phase = hg_phase(tr::S_LAM[s.lam].g, s.k.x * I.kobs[0] + s.k.y * I.kobs[1] + s.k.z * I.kobs[2]);
   const float pe = kInv4PiF * phase * expf(-s.th) * (1.0f - s.tl);
@@ -328,6 +329,16 @@ __device__ __forceinline__ void finish_peel_measure(const AdjParams& A, ALane& s
     r.dxb[1] += V * dW.y + l * s.g.y * s.id.y;
     r.dxb[2] += V * dW.z + l * s.g.z * s.id.z;
   }
+  return l;
+}
+
+// A peel-off measuring walk ended: its values, then the depositing walk or
+// the next peel-off.
+__device__ __forceinline__ void finish_peel_measure(const AdjParams& A, ALane& s) {
+  const DevInstr& I = tr::S_INSTR[s.q];
+  float3 dW;
+  const float W = adj_weight(A, s.q, s.lam, s.event > 0, s.x, dW);
+  const float l = peel_values(A, s, I, W, dW);
   if (l != 0.0f && s.n_cross > 0) {
     s.c0 = s.c1 = -l * s.kappa;
     s.h = INT_MAX;
@@ -338,16 +349,64 @@ __device__ __forceinline__ void finish_peel_measure(const AdjParams& A, ALane& s
   s.phase = aPeelScan;
 }
 
+// A peel-off along a frame that looks exactly along a grid axis, without
+// walks: the forward kernel's column sums give tau = kappa (rho_c ds_0 +
+// column[c]); the only plane the ray's optical depth depends on is the exit
+// face of the first cell, g_axis = kappa rho_c; the deposit -l kappa ds goes
+// to cell c directly and, for the cells beyond it, into the line's
+// difference array.  False when the position is outside the grid.
+__device__ __forceinline__ bool column_peel(const AdjParams& A, ALane& s, const DevInstr& I, float W, float3 dW,
+                                            unsigned& n_cross, unsigned& n_dep) {
+  const FwdParams& P = A.f;
+  CartGrid::Cell c;
+  if (s.has_cell) {
+    c = s.cell;
+  } else {
+    if (!inside_box(P, s.x)) return false;
+    c.ix = min(max(__float2int_rd((s.x.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
+    c.iy = min(max(__float2int_rd((s.x.y - P.lo[1]) * P.inv_d[1]), 0), P.ny - 1);
+    c.iz = min(max(__float2int_rd((s.x.z - P.lo[2]) * P.inv_d[2]), 0), P.nz - 1);
+  }
+  const int a = I.axis;
+  const bool up = I.dir > 0;
+  const int i = a == 0 ? c.ix : (a == 1 ? c.iy : c.iz);
+  const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
+  const float xa = a == 0 ? s.x.x : (a == 1 ? s.x.y : s.x.z);
+  const float plane = fmaf((float)(i + (up ? 1 : 0)), P.d[a], P.lo[a]);
+  const float ds0 = fmaxf(up ? plane - xa : xa - plane, 0.0f);
+  const int cell = c.ix + P.nx * (c.iy + P.ny * c.iz);
+  const float rho = tr::load_density(&P.density[cell]);
+  s.th = s.kappa * fmaf(rho, ds0, __ldg(&I.column[cell]));
+  s.tl = 0.0f;
+  const float kr0 = s.kappa * rho;
+  const float sgn = up ? 1.0f : -1.0f;
+  s.g = make_float3(a == 0 ? kr0 : 0.0f, a == 1 ? kr0 : 0.0f, a == 2 ? kr0 : 0.0f);
+  s.id = make_float3(a == 0 ? sgn : 0.0f, a == 1 ? sgn : 0.0f, a == 2 ? sgn : 0.0f);
+  const unsigned cells = (unsigned)(up ? n - i : i + 1);
+  n_cross += 2u * cells;  // the measuring and the depositing walk it stands for
+  const float l = peel_values(A, s, I, W, dW);
+  if (l != 0.0f) {
+    const float coef = -l * s.kappa;
+    grad_add(&A.grad[cell], scaled(coef * ds0, s.eLA));
+    if (cells > 1u) grad_add(&A.line_dep[2 * a + (up ? 1 : 0)][cell], scaled(coef * P.d[a], s.eLA));
+    n_dep += cells;
+  }
+  return true;
+}
+
 // The next instrument from s.q whose adjoint weight at the lane's position
-// is not zero: its peel-off walk; after the last one, aAfter.
-__device__ __forceinline__ void peel_scan(const AdjParams& A, ALane& s) {
+// is not zero: its peel-off walk (frames along grid axes are done here
+// without walks); after the last one, aAfter.
+__device__ __forceinline__ void peel_scan(const AdjParams& A, ALane& s, unsigned& n_cross, unsigned& n_dep) {
   const FwdParams& P = A.f;
   const bool on = s.event == 0 ? P.peel_emission : P.peel_scatter;
   for (; on && s.q < P.n_instr; ++s.q) {
     float3 dW;
     const float W = adj_weight(A, s.q, s.lam, s.event > 0, s.x, dW);
     if (W == 0.0f && dW.x == 0.0f && dW.y == 0.0f && dW.z == 0.0f) continue;  // contributes nothing
-    request_walk(s, aPeelM, tr::instr_dir(tr::S_INSTR[s.q]));
+    const DevInstr& I = tr::S_INSTR[s.q];
+    if (P.use_columns && I.column && column_peel(A, s, I, W, dW, n_cross, n_dep)) continue;
+    request_walk(s, aPeelM, tr::instr_dir(I));
     return;
   }
   s.phase = aAfter;
@@ -540,7 +599,7 @@ __global__ void __launch_bounds__(kAdjBlock, RT_ADJ_MIN_BLOCKS) k_adjoint(const 
         base = __shfl_sync(0xffffffffu, base, leader);
         if (wants) fetch(A, s, base + __popc(fetchers & lt_mask));
       }
-      if (s.phase == aPeelScan) peel_scan(A, s);
+      if (s.phase == aPeelScan) peel_scan(A, s, n_cross, n_dep);
       if (s.phase == aAfter) after_peels<kAbs>(A, s);
       if (s.phase == aSweep) {
         if (s.J >= 1) sweep(A, s); else s.phase = aFetch;
@@ -584,6 +643,33 @@ __global__ void k_absmax(const double* a, size_t n, unsigned long long* out) {
   if ((threadIdx.x & 31u) == 0u && m) atomicMax(out, m);
 }
 
+// The per-line deposit differences into the gradient: along each grid line,
+// in the ray's direction, every cell receives the sum of the entries of the
+// cells before it.
+__global__ void k_line_scatter(const double* __restrict__ dep, double* __restrict__ grad, int nx, int ny, int nz,
+                               int axis, int dir) {
+  const long long n_lines = axis == 0 ? (long long)ny * nz : (axis == 1 ? (long long)nx * nz : (long long)nx * ny);
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < n_lines;
+       L += (long long)gridDim.x * blockDim.x) {
+    long long base, stride;
+    int n;
+    if (axis == 0) {
+      base = L * nx; stride = 1; n = nx;
+    } else if (axis == 1) {
+      base = (L % nx) + (L / nx) * (long long)nx * ny; stride = nx; n = ny;
+    } else {
+      base = L; stride = (long long)nx * ny; n = nz;
+    }
+    double run = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const int j = dir > 0 ? k : n - 1 - k;
+      const long long c = base + (long long)j * stride;
+      if (run != 0.0) grad[c] += run;
+      run += dep[c];
+    }
+  }
+}
+
 // FP32 copy of an adjoint image in units 2^ea.
 __global__ void k_to_units(const double* a, size_t n, const unsigned long long* maxbits, float* out) {
   const int ea = adjoint_exponent(*maxbits);
@@ -612,9 +698,16 @@ cudaError_t adjoint_lanes(int num_sms, unsigned long long n_total, unsigned long
 cudaError_t launch_adjoint(const FwdParams& f, const double* const* adj_img, const size_t* img_elems,
                            const double* adj_abs, double* grad, AdjRecord* recs, unsigned long long lanes,
                            unsigned long long* counters, float* img_f, unsigned long long* maxbits,
-                           cudaStream_t stream) {
+                           double* const* line_dep, cudaStream_t stream) {
   AdjParams a;
   a.f = f;
+  for (int k = 0; k < 6; ++k) {
+    a.line_dep[k] = f.use_columns ? line_dep[k] : nullptr;
+    if (a.line_dep[k]) {
+      cudaError_t e = cudaMemsetAsync(a.line_dep[k], 0, (size_t)f.n_cells * sizeof(double), stream);
+      if (e != cudaSuccess) return e;
+    }
+  }
   a.adj_abs = adj_abs;
   a.maxbits = maxbits;
   a.grad = grad;
@@ -649,7 +742,16 @@ cudaError_t launch_adjoint(const FwdParams& f, const double* const* adj_img, con
   } else {
     k_adjoint<false><<<blocks, kAdjBlock, 0, stream>>>(a);
   }
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+    if (!a.line_dep[k]) continue;
+    const int axis = k / 2;
+    const long long n_lines = (long long)f.n_cells / (axis == 0 ? f.nx : (axis == 1 ? f.ny : f.nz));
+    const long long nb = std::min<long long>((n_lines + 255) / 256, 65535);
+    k_line_scatter<<<(unsigned)nb, 256, 0, stream>>>(a.line_dep[k], grad, f.nx, f.ny, f.nz, axis, (k & 1) ? 1 : -1);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace rtk

@@ -48,6 +48,7 @@ struct Batch {
   std::vector<size_t> img_off, img_elems;     // per model, in doubles
   size_t img_total = 0;
   float* d_density = nullptr;
+  float* d_columns = nullptr;                 // column sums, parallel to d_density (or null)
   DevModel* d_models = nullptr;
   BatchChunk* d_chunks = nullptr;
   int n_chunks = 0;
@@ -95,9 +96,14 @@ struct rt_ctx_s {
   unsigned long long* d_work = nullptr;
   int* d_flags = nullptr;
   bool tables_dirty = true;
+  // per-line suffix sums of the density for frames along the grid axes,
+  // index 2 * axis + (direction > 0); rebuilt at every launch that uses them
+  float* d_columns[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool columns_used[6] = {false, false, false, false, false, false};
   AdjRecord* d_adj = nullptr;  // adjoint event records, grown on demand
   size_t adj_bytes = 0;
   float* d_adj_img = nullptr;  // FP32 copies of the adjoint images, grown on demand
+  double* d_line_dep[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // adjoint, per column table
   size_t adj_img_elems = 0;
   unsigned long long* d_adj_max = nullptr;
   std::vector<Batch*> batches;  // by id; null after rt_batch_destroy
@@ -142,7 +148,24 @@ void free_grid(rt_ctx c) {
   dfree(c->d_density);
   dfree(c->d_child);
   dfree(c->d_absorption);
+  for (auto& p : c->d_columns) dfree(p);
+  for (auto& p : c->d_line_dep) dfree(p);
+  c->tables_dirty = true;
   c->has_grid = false;
+}
+
+// The grid axis (and direction) a frame looks along exactly, or false.
+bool frame_axis(const DevInstr& I, int& axis, int& dir) {
+  int n = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (I.kobs[a] != 0.0f) {
+      ++n;
+      axis = a;
+    }
+  }
+  if (n != 1 || std::fabs(I.kobs[axis]) != 1.0f) return false;
+  dir = I.kobs[axis] > 0.0f ? 1 : -1;
+  return true;
 }
 
 void free_problem(rt_ctx c) {
@@ -218,7 +241,18 @@ rt_status upload_tables(rt_ctx c, cudaStream_t s) {
     I.bilinear = d.deposit == RT_DEPOSIT_BILINEAR;
     I.channels = d.channels;
     I.image = c->instr[q].d_image;
+    int axis = 0, dir = 0;
+    if (c->grid_kind == RT_GRID_CARTESIAN && frame_axis(I, axis, dir)) {
+      const int k = 2 * axis + (dir > 0 ? 1 : 0);
+      if (!c->d_columns[k]) RT_CUDA(c, cudaMalloc(&c->d_columns[k], (size_t)c->n_cells * sizeof(float)));
+      I.column = c->d_columns[k];
+      I.axis = axis;
+      I.dir = dir;
+    }
   }
+  for (int k = 0; k < 6; ++k) c->columns_used[k] = false;
+  for (const DevInstr& I : ins)
+    if (I.column) c->columns_used[2 * I.axis + (I.dir > 0 ? 1 : 0)] = true;
   dfree(c->d_lam); dfree(c->d_src); dfree(c->d_src_cum); dfree(c->d_instr);
   RT_CUDA(c, cudaMalloc(&c->d_lam, std::max<size_t>(1, lam.size()) * sizeof(DevLambda)));
   RT_CUDA(c, cudaMalloc(&c->d_src, std::max<size_t>(1, src.size()) * sizeof(DevSource)));
@@ -239,7 +273,7 @@ bool is_finite(double v) { return std::isfinite(v); }
 void free_batch(Batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  dfree(b->d_density); dfree(b->d_models); dfree(b->d_chunks); dfree(b->d_images); dfree(b->d_tallies);
+  dfree(b->d_density); dfree(b->d_columns); dfree(b->d_models); dfree(b->d_chunks); dfree(b->d_images); dfree(b->d_tallies);
   dfree(b->d_lum); dfree(b->d_chunk_counter); dfree(b->d_counters); dfree(b->d_flags);
   delete b;
 }
@@ -314,11 +348,12 @@ BatchParams batch_params(const Batch* b, const rt_launch_opts& o, uint64_t seed,
   p.peel_emission = o.peel_emission;
   p.peel_scatter = o.peel_scatter;
   p.control_min = o.control_lanes ? o.control_lanes : (b->control_lanes ? b->control_lanes : 16);
+  p.use_columns = !o.walk_peels;
   return p;
 }
 
-// The launch graph: zero the work counter and add the emitted luminosity,
-// then the persistent kernel.
+// The launch graph: zero the work counter, add the emitted luminosity and
+// rebuild the column sums, then the persistent kernel.
 rt_status build_graph(rt_ctx c, Batch* b, const BatchParams& p) {
   RT_CUDA(c, cudaGraphCreate(&b->graph, 0));
   cudaMemsetParams mp;
@@ -341,6 +376,17 @@ rt_status build_graph(rt_ctx c, Batch* b, const BatchParams& p) {
   ep.blockDim = dim3(256);
   ep.kernelParams = eargs;
   RT_CUDA(c, cudaGraphAddKernelNode(&n_emit, b->graph, nullptr, 0, &ep));
+  const DevModel* models = b->d_models;
+  const float* dens = b->d_density;
+  void* cargs[] = {&models, &n, &dens};
+  cudaKernelNodeParams cp;
+  std::memset(&cp, 0, sizeof cp);
+  cp.func = const_cast<void*>(batch_columns_kernel());
+  cp.gridDim = dim3((unsigned)n);
+  cp.blockDim = dim3(128);
+  cp.kernelParams = cargs;
+  cudaGraphNode_t n_cols;
+  RT_CUDA(c, cudaGraphAddKernelNode(&n_cols, b->graph, nullptr, 0, &cp));
   BatchParams pc = p;
   void* kargs[] = {&pc};
   cudaKernelNodeParams kp;
@@ -349,8 +395,8 @@ rt_status build_graph(rt_ctx c, Batch* b, const BatchParams& p) {
   kp.gridDim = dim3(b->blocks);
   kp.blockDim = dim3(kBatchBlock);
   kp.kernelParams = kargs;
-  cudaGraphNode_t deps[2] = {n_zero, n_emit};
-  RT_CUDA(c, cudaGraphAddKernelNode(&b->kernel_node, b->graph, deps, 2, &kp));
+  cudaGraphNode_t deps[3] = {n_zero, n_emit, n_cols};
+  RT_CUDA(c, cudaGraphAddKernelNode(&b->kernel_node, b->graph, deps, 3, &kp));
   RT_CUDA(c, cudaGraphInstantiate(&b->exec, b->graph, 0));
   return RT_OK;
 }
@@ -397,6 +443,7 @@ rt_status rt_context_destroy(rt_ctx c) {
   dfree(c->d_lam); dfree(c->d_src); dfree(c->d_src_cum); dfree(c->d_instr);
   dfree(c->d_stats); dfree(c->d_counters); dfree(c->d_work); dfree(c->d_flags);
   dfree(c->d_adj); dfree(c->d_adj_img); dfree(c->d_adj_max);
+  for (auto& p : c->d_line_dep) dfree(p);
   delete c;
   return RT_OK;
 }
@@ -648,7 +695,17 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   }
   p.profile = reinterpret_cast<unsigned long long*>(o.profile);
   p.flags = c->d_flags;
-  cudaError_t e = launch_forward(p, c->grid_kind, 0, c->num_sms, s);
+  p.use_columns = c->grid_kind == RT_GRID_CARTESIAN && !o.walk_peels;
+  if (p.use_columns) {
+    for (int k = 0; k < 6; ++k) {
+      if (!c->columns_used[k]) continue;
+      const int axis = k / 2;
+      cudaError_t ec = launch_columns(c->d_density, c->nx, c->ny, c->nz, axis, (k & 1) ? 1 : -1, p.d[axis],
+                                      c->d_columns[k], s);
+      if (ec != cudaSuccess) return cuda_fail(c, ec, "column sums");
+    }
+  }
+  cudaError_t e = launch_forward(p, c->grid_kind, c->num_sms, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "forward launch");
   // every packet starts with L0 = L_tot / n_norm
   for (int l = 0; l < c->n_lambda; ++l) {
@@ -780,8 +837,22 @@ rt_status rt_adjoint(rt_ctx c, const double* const* adj_images, int32_t n_adj_im
     c->adj_img_elems = img_total ? img_total : 1;
   }
   if (!c->d_adj_max) RT_CUDA(c, cudaMalloc(&c->d_adj_max, sizeof(unsigned long long)));
+  // frames along grid axes: the forward kernel's column sums, and a deposit
+  // difference array per column table
+  p.use_columns = !o.walk_peels;
+  double* line_dep[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (p.use_columns) {
+    for (int k = 0; k < 6; ++k) {
+      if (!c->columns_used[k]) continue;
+      const int axis = k / 2;
+      if (!c->d_line_dep[k]) RT_CUDA(c, cudaMalloc(&c->d_line_dep[k], (size_t)c->n_cells * sizeof(double)));
+      line_dep[k] = c->d_line_dep[k];
+      e = launch_columns(c->d_density, c->nx, c->ny, c->nz, axis, (k & 1) ? 1 : -1, p.d[axis], c->d_columns[k], s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "column sums");
+    }
+  }
   e = launch_adjoint(p, adj, elems, adj_absorption, grad_density, c->d_adj, lanes,
-                     reinterpret_cast<unsigned long long*>(o.profile), c->d_adj_img, c->d_adj_max, s);
+                     reinterpret_cast<unsigned long long*>(o.profile), c->d_adj_img, c->d_adj_max, line_dep, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
   return RT_OK;
 }
@@ -841,6 +912,7 @@ rt_status rt_read_stats(rt_ctx c, rt_stats* out) {
   std::memset(out, 0, sizeof *out);
   out->emitted = c->emitted; out->escaped = st[1]; out->absorbed = st[2]; out->truncated = st[3];
   out->crossings = cn[0]; out->path_crossings = cn[5]; out->events = cn[1]; out->peeloffs = cn[2]; out->packets = cn[3]; out->records = cn[4];
+  out->column_peels = cn[6]; out->column_crossings = cn[7];
   out->device_flags = flags;
   if (flags) return fail(c, RT_ERR_DEVICE_FLAG, "a kernel bounds check fired (flags 0x%x)", flags);
   return RT_OK;
@@ -928,6 +1000,12 @@ rt_status rt_batch_create(rt_ctx c, int32_t n_models, const rt_model_desc* model
     I.nx = d.instrument.nx; I.ny = d.instrument.ny;
     I.bilinear = d.instrument.deposit == RT_DEPOSIT_BILINEAR;
     I.channels = 1;
+    int axis = 0, dir = 0;
+    if (frame_axis(I, axis, dir)) {
+      I.axis = axis;
+      I.dir = dir;
+      I.column = reinterpret_cast<const float*>(1);  // marks "has column sums"; set after allocation
+    }
     b->lum.push_back(d.luminosity);
     b->n_packets.push_back(d.n_packets);
     b->img_off.push_back(b->img_total);
@@ -947,24 +1025,31 @@ rt_status rt_batch_create(rt_ctx c, int32_t n_models, const rt_model_desc* model
     if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(1, bytes));
   };
   alloc(&b->d_density, dens.size() * sizeof(float));
+  bool any_columns = false;
+  for (const DevModel& M : rows) any_columns = any_columns || M.instr.column != nullptr;
+  if (any_columns) alloc(&b->d_columns, dens.size() * sizeof(float));
   alloc(&b->d_models, rows.size() * sizeof(DevModel));
   alloc(&b->d_images, b->img_total * sizeof(double));
   alloc(&b->d_tallies, (size_t)n_models * 4 * sizeof(double));
   alloc(&b->d_lum, (size_t)n_models * sizeof(double));
   alloc(&b->d_chunk_counter, sizeof(unsigned long long));
-  alloc(&b->d_counters, 4 * sizeof(unsigned long long));
+  alloc(&b->d_counters, 6 * sizeof(unsigned long long));
   alloc(&b->d_flags, sizeof(int));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return bail(fail(c, RT_ERR_OOM, "rt_batch_create: device allocation: %s", cudaGetErrorString(e)));
   }
-  for (int m = 0; m < n_models; ++m) rows[(size_t)m].instr.image = b->d_images + b->img_off[(size_t)m];
+  for (int m = 0; m < n_models; ++m) {
+    DevModel& M = rows[(size_t)m];
+    M.instr.image = b->d_images + b->img_off[(size_t)m];
+    if (M.instr.column) M.instr.column = b->d_columns + M.density;
+  }
   if (e == cudaSuccess) e = cudaMemcpy(b->d_density, dens.data(), dens.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_models, rows.data(), rows.size() * sizeof(DevModel), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_lum, b->lum.data(), b->lum.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->d_images, 0, b->img_total * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(b->d_tallies, 0, (size_t)n_models * 4 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, 6 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(b->d_flags, 0, sizeof(int));
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "rt_batch_create: upload"));
   int per_sm = 0;
@@ -1027,7 +1112,7 @@ rt_status rt_batch_reset(rt_ctx c, int32_t id, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   RT_CUDA(c, cudaMemsetAsync(b->d_images, 0, b->img_total * sizeof(double), s));
   RT_CUDA(c, cudaMemsetAsync(b->d_tallies, 0, (size_t)b->n_models * 4 * sizeof(double), s));
-  RT_CUDA(c, cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(unsigned long long), s));
+  RT_CUDA(c, cudaMemsetAsync(b->d_counters, 0, 6 * sizeof(unsigned long long), s));
   RT_CUDA(c, cudaMemsetAsync(b->d_flags, 0, sizeof(int), s));
   return RT_OK;
 }
@@ -1064,7 +1149,7 @@ rt_status rt_batch_read_stats(rt_ctx c, int32_t id, rt_stats* out) {
   if (set_device(c) != RT_OK) return RT_ERR_CUDA;
   RT_CUDA(c, cudaDeviceSynchronize());
   std::vector<double> t((size_t)b->n_models * 4);
-  unsigned long long cn[4];
+  unsigned long long cn[6];
   int flags = 0;
   RT_CUDA(c, cudaMemcpy(t.data(), b->d_tallies, t.size() * sizeof(double), cudaMemcpyDeviceToHost));
   RT_CUDA(c, cudaMemcpy(cn, b->d_counters, sizeof cn, cudaMemcpyDeviceToHost));
@@ -1077,6 +1162,7 @@ rt_status rt_batch_read_stats(rt_ctx c, int32_t id, rt_stats* out) {
     out->truncated += t[(size_t)m * 4 + 3];
   }
   out->crossings = cn[0]; out->events = cn[1]; out->peeloffs = cn[2]; out->packets = cn[3];
+  out->column_peels = cn[4]; out->column_crossings = cn[5];
   out->device_flags = flags;
   if (flags) return fail(c, RT_ERR_DEVICE_FLAG, "a kernel bounds check fired (flags 0x%x)", flags);
   return RT_OK;
@@ -1096,6 +1182,7 @@ rt_status rt_batch_tune(rt_ctx c, int32_t id, uint64_t seed, double fraction, in
   cudaStream_t s = (cudaStream_t)stream;
   const int lanes_c[] = {8, 12, 16, 20, 24, 28, 32};
   const unsigned runs_c[] = {64, 256, 1024, 4096};
+  RT_CUDA(c, launch_batch_columns(b->d_models, b->n_models, b->d_density, s));
   cudaEvent_t e0, e1;
   RT_CUDA(c, cudaEventCreate(&e0));
   RT_CUDA(c, cudaEventCreate(&e1));

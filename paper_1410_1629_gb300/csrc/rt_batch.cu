@@ -33,6 +33,7 @@ struct Geo {
 struct Tally {
   double escaped, absorbed, truncated;
   int model, pad;
+  unsigned long long column_peels, column_crossings;  // the lane's, over the launch
 };
 
 __shared__ Geo S_GEO[kBatchBlock];
@@ -108,6 +109,43 @@ __device__ __forceinline__ void deposit(const DevModel& M, const BLane& s, bool 
   }
 }
 
+// The forward kernel's column shortcut for a frame along a grid axis (see
+// column_peel there); false when the position is outside the grid.
+__device__ __forceinline__ bool column_peel(const DevInstr& I, BLane& s, const Geo& G, Tally& T,
+                                            unsigned& n_cross) {
+  CartGrid::Cell c;
+  if (s.has_cell) {
+    c = s.cell;
+  } else {
+    if (!inside_box(G, s.x)) return false;
+    c.ix = min(max(__float2int_rd((s.x.x - G.lo[0]) * G.inv_d[0]), 0), G.nx - 1);
+    c.iy = min(max(__float2int_rd((s.x.y - G.lo[1]) * G.inv_d[1]), 0), G.ny - 1);
+    c.iz = min(max(__float2int_rd((s.x.z - G.lo[2]) * G.inv_d[2]), 0), G.nz - 1);
+  }
+  const int a = I.axis;
+  const bool up = I.dir > 0;
+  const int i = a == 0 ? c.ix : (a == 1 ? c.iy : c.iz);
+  const int n = a == 0 ? G.nx : (a == 1 ? G.ny : G.nz);
+  const float xa = a == 0 ? s.x.x : (a == 1 ? s.x.y : s.x.z);
+  const float plane = fmaf((float)(i + (up ? 1 : 0)), G.d[a], G.lo[a]);
+  const float ds0 = fmaxf(up ? plane - xa : xa - plane, 0.0f);
+  const int cell = c.ix + G.nx * (c.iy + G.ny * c.iz);
+  s.th = s.kappa * fmaf(tr::load_density(&s.dens[cell]), ds0, __ldg(&I.column[cell]));
+  s.tl = 0.0f;
+  s.walking = false;
+  const unsigned nc = (unsigned)(up ? n - i : i + 1);
+  n_cross += nc;
+  T.column_peels += 1ull;
+  T.column_crossings += nc;
+  return true;
+}
+
+__device__ __forceinline__ void start_peel(const BatchParams& P, const DevInstr& I, BLane& s, const Geo& G,
+                                           Tally& T, unsigned& n_cross) {
+  if (P.use_columns && I.column && column_peel(I, s, G, T, n_cross)) return;
+  start_walk(s, G, kobs(I));
+}
+
 __device__ __forceinline__ void start_path(BLane& s, const Geo& G) {
   s.phase = tr::kPath1;
   start_walk(s, G, s.k);
@@ -116,7 +154,7 @@ __device__ __forceinline__ void start_path(BLane& s, const Geo& G) {
 // A new packet (model m, packet id pid): the model's geometry, emission from
 // its point source (the forward kernel's event-0 draws), the emission peel-off.
 __device__ __forceinline__ void begin(const BatchParams& P, BLane& s, Geo& G, Tally& T, int m,
-                                      unsigned long long pid) {
+                                      unsigned long long pid, unsigned& n_cross) {
   const DevModel& M = P.models[m];
   if (T.model != m) {
     flush(P, T);
@@ -144,7 +182,7 @@ __device__ __forceinline__ void begin(const BatchParams& P, BLane& s, Geo& G, Ta
   s.k = make_float3(st * cp, st * sp, mu);
   if (P.peel_emission) {
     s.phase = tr::kPeelEmit;
-    start_walk(s, G, kobs(M.instr));
+    start_peel(P, M.instr, s, G, T, n_cross);
   } else {
     s.event = 1;
     start_path(s, G);
@@ -169,7 +207,7 @@ __device__ __forceinline__ void after_scattering(const BatchParams& P, const Dev
 // Per-event work of a lane whose walk has ended (the forward kernel's, for a
 // single-channel frame and no absorption field).
 __device__ void control(const BatchParams& P, BLane& s, const Geo& G, Tally& T, unsigned& n_events,
-                        unsigned& n_peel) {
+                        unsigned& n_peel, unsigned& n_cross) {
   const DevModel& M = P.models[s.m];
   while (true) {
     switch (s.phase) {
@@ -219,7 +257,7 @@ __device__ void control(const BatchParams& P, BLane& s, const Geo& G, Tally& T, 
         n_events += 1u;
         if (P.peel_scatter) {
           s.phase = tr::kPeelScat;
-          start_walk(s, G, kobs(M.instr));
+          start_peel(P, M.instr, s, G, T, n_cross);
         } else {
           after_scattering(P, M, s, G, T);
         }
@@ -275,6 +313,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch(const BatchParams P) {
   Tally& T = S_TALLY[threadIdx.x];
   T.escaped = T.absorbed = T.truncated = 0.0;
   T.model = -1;
+  T.column_peels = T.column_crossings = 0ull;
   BLane s;
   s.phase = tr::kFetch;
   s.walking = false;
@@ -291,7 +330,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch(const BatchParams P) {
     const unsigned walkers = __ballot_sync(0xffffffffu, s.walking);
     if (need == 0u && walkers == 0u) break;
     if (walkers == 0u || __popc(need) >= P.control_min) {
-      if (idle && s.phase != tr::kFetch) control(P, s, G, T, n_events, n_peel);
+      if (idle && s.phase != tr::kFetch) control(P, s, G, T, n_events, n_peel, n_cross);
       const bool wants = !s.walking && s.phase == tr::kFetch;
       const unsigned fetchers = __ballot_sync(0xffffffffu, wants);
       if (fetchers) {
@@ -326,9 +365,9 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch(const BatchParams P) {
         }
         if (wants) {
           if (my_model >= 0) {
-            begin(P, s, G, T, my_model, my_pid);
+            begin(P, s, G, T, my_model, my_pid, n_cross);
             n_packets += 1u;
-            if (!s.walking) control(P, s, G, T, n_events, n_peel);
+            if (!s.walking) control(P, s, G, T, n_events, n_peel, n_cross);
           } else {
             s.phase = tr::kExit;
           }
@@ -343,8 +382,10 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch(const BatchParams P) {
   }
   flush(P, T);
   tot_cross += n_cross;
-  unsigned long long ev = n_events, pe = n_peel, pk = n_packets;
+  unsigned long long ev = n_events, pe = n_peel, pk = n_packets, cp = T.column_peels, cc = T.column_crossings;
   for (int o = 16; o > 0; o >>= 1) {
+    cp += __shfl_down_sync(0xffffffffu, cp, o);
+    cc += __shfl_down_sync(0xffffffffu, cc, o);
     tot_cross += __shfl_down_sync(0xffffffffu, tot_cross, o);
     ev += __shfl_down_sync(0xffffffffu, ev, o);
     pe += __shfl_down_sync(0xffffffffu, pe, o);
@@ -355,6 +396,42 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch(const BatchParams P) {
     atomicAdd(&P.counters[1], ev);
     atomicAdd(&P.counters[2], pe);
     atomicAdd(&P.counters[3], pk);
+    if (cp) {
+      atomicAdd(&P.counters[4], cp);
+      atomicAdd(&P.counters[5], cc);
+    }
+  }
+}
+
+// Column sums of each model whose frame looks along a grid axis: one block
+// per model, one thread per grid line (the forward path's k_columns).
+__global__ void k_batch_columns(const DevModel* models, int n_models, const float* density) {
+  const int m = blockIdx.x;
+  if (m >= n_models) return;
+  const DevModel& M = models[m];
+  float* out = const_cast<float*>(M.instr.column);
+  if (!out) return;
+  const float* dens = density + M.density;
+  const int nx = M.nx, ny = M.ny, axis = M.instr.axis, dir = M.instr.dir;
+  const int n = axis == 0 ? M.nx : (axis == 1 ? M.ny : M.nz);
+  const long long n_lines = (long long)M.nx * M.ny * M.nz / n;
+  const double d = (double)M.d[axis];
+  for (long long L = threadIdx.x; L < n_lines; L += blockDim.x) {
+    long long base, stride;
+    if (axis == 0) {
+      base = L * nx; stride = 1;
+    } else if (axis == 1) {
+      base = (L % nx) + (L / nx) * (long long)nx * ny; stride = nx;
+    } else {
+      base = L; stride = (long long)nx * ny;
+    }
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const int j = dir > 0 ? n - 1 - k : k;
+      const long long c = base + (long long)j * stride;
+      out[c] = (float)acc;
+      acc += (double)dens[c] * d;
+    }
   }
 }
 
@@ -368,6 +445,12 @@ __global__ void k_batch_emitted(double* tallies, const double* lum, int n) {
 
 const void* batch_kernel() { return reinterpret_cast<const void*>(&k_batch); }
 const void* batch_emitted_kernel() { return reinterpret_cast<const void*>(&k_batch_emitted); }
+const void* batch_columns_kernel() { return reinterpret_cast<const void*>(&k_batch_columns); }
+
+cudaError_t launch_batch_columns(const DevModel* models, int n_models, const float* density, cudaStream_t stream) {
+  k_batch_columns<<<(unsigned)n_models, 128, 0, stream>>>(models, n_models, density);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_batch(const BatchParams& p, unsigned blocks, cudaStream_t stream) {
   k_batch<<<blocks, kBatchBlock, 0, stream>>>(p);

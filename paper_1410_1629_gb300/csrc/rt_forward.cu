@@ -10,8 +10,7 @@ __global__ void __launch_bounds__(tr::kBlock, RT_FWD_MIN_BLOCKS) k_forward_carte
 }
 }  // namespace
 
-cudaError_t launch_forward(const FwdParams& p, int grid_kind, int block_size, int num_sms, cudaStream_t stream) {
-  (void)block_size;
+cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaStream_t stream) {
   if (grid_kind != RT_GRID_CARTESIAN) return launch_forward_octree(p, num_sms, stream);
   cudaError_t e = cudaMemsetAsync(p.work_counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
@@ -24,6 +23,47 @@ cudaError_t launch_forward(const FwdParams& p, int grid_kind, int block_size, in
   if (blocks > useful) blocks = useful;
   if (blocks < 1) blocks = 1;
   k_forward_cartesian<<<(unsigned)blocks, tr::kBlock, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// One thread per grid line along `axis`: the density integral from the far
+// face of each cell to the boundary the ray meets (direction dir), summed in
+// FP64 from that boundary inwards.
+__global__ void k_columns(const float* __restrict__ density, int nx, int ny, int nz, int axis, int dir, double d,
+                          float* __restrict__ out) {
+  const long long n_lines = axis == 0 ? (long long)ny * nz : (axis == 1 ? (long long)nx * nz : (long long)nx * ny);
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < n_lines;
+       L += (long long)gridDim.x * blockDim.x) {
+    long long base, stride;
+    int n;
+    if (axis == 0) {
+      base = L * nx; stride = 1; n = nx;
+    } else if (axis == 1) {
+      base = (L % nx) + (L / nx) * (long long)nx * ny; stride = nx; n = ny;
+    } else {
+      base = L; stride = (long long)nx * ny; n = nz;
+    }
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const int j = dir > 0 ? n - 1 - k : k;
+      const long long c = base + (long long)j * stride;
+      out[c] = (float)acc;
+      acc += (double)density[c] * d;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_columns(const float* density, int nx, int ny, int nz, int axis, int dir, float d, float* out,
+                           cudaStream_t stream) {
+  const long long n_lines = axis == 0 ? (long long)ny * nz : (axis == 1 ? (long long)nx * nz : (long long)nx * ny);
+  const int block = 256;
+  long long blocks = (n_lines + block - 1) / block;
+  if (blocks > 65535) blocks = 65535;
+  k_columns<<<(unsigned)blocks, block, 0, stream>>>(density, nx, ny, nz, axis, dir, (double)d, out);
   return cudaGetLastError();
 }
 

@@ -43,6 +43,11 @@ struct DevInstr {
   int nx, ny;
   int bilinear, channels;
   double* image;       // [channels][n_lambda][ny][nx]
+  // a frame looking exactly along grid axis `axis` (dir +-1): column[c] is the
+  // density integral from the face of cell c that the ray leaves to the grid
+  // boundary, sum of rho d_axis over the cells beyond c (or null: walk)
+  const float* column;
+  int axis, dir;
 };
 
 // Everything a forward launch needs, passed by value.
@@ -84,6 +89,7 @@ struct FwdParams {
   double L_cut[kMaxLambda];        // w_min * L0 per wavelength
   unsigned long long* profile;  // optional execution counters (see rt_launch_opts.profile)
   int* flags;
+  int use_columns;              // peel-offs along grid axes use the instruments' column sums
 };
 
 enum DeviceFlag : int { kFlagCellRange = 1, kFlagOctreeDepth = 2, kFlagWalkSteps = 4, kFlagNoInteraction = 8 };
@@ -119,7 +125,12 @@ inline void frame_axes(double inclination, double azimuth, double position_angle
 void set_context_free_error(const char* msg);
 
 // Launchers (rt_forward.cu).
-cudaError_t launch_forward(const FwdParams& p, int grid_kind, int block_size, int num_sms, cudaStream_t stream);
+cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaStream_t stream);
+// Per-line suffix sums for peel-offs along axis `axis` in direction dir
+// (+1 / -1): out[c] = sum over the cells j beyond c on c's grid line of
+// rho_j d, accumulated in FP64 from the boundary (rt_forward.cu).
+cudaError_t launch_columns(const float* density, int nx, int ny, int nz, int axis, int dir, float d, float* out,
+                           cudaStream_t stream);
 cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t stream);
 // One forced path of a packet in the adjoint (rt_adjoint.cu): what the
 // backward sweep and the path's depositing walk need.  Adjoint quantities are
@@ -173,11 +184,13 @@ struct BatchParams {
   const float* density;
   double* tallies;                     // [n_models][4]: emitted (host side), escaped, absorbed, truncated
   unsigned long long* chunk_counter;
-  unsigned long long* counters;        // [4]: crossings, events, peel-offs, packets
+  unsigned long long* counters;        // [6]: crossings, events, peel-offs, packets, column peel-offs,
+                                       //      their crossings
   int* flags;
   double w_min;
   unsigned seed;
   int max_events, weight_cut, peel_emission, peel_scatter, control_min;
+  int use_columns;                     // frames along grid axes use the models' column sums
 };
 constexpr int kBatchBlock = 256;
 // The batch kernel and the per-launch emitted-tally kernel (graph nodes:
@@ -185,8 +198,12 @@ constexpr int kBatchBlock = 256;
 // int n)), the batch kernel's resident blocks per SM, and a plain launch.
 const void* batch_kernel();
 const void* batch_emitted_kernel();
+// k_batch_columns(const DevModel* models, int n_models, const float* density):
+// the column sums of every model whose frame looks along a grid axis.
+const void* batch_columns_kernel();
 cudaError_t batch_blocks_per_sm(int* blocks);
 cudaError_t launch_batch(const BatchParams& p, unsigned blocks, cudaStream_t stream);
+cudaError_t launch_batch_columns(const DevModel* models, int n_models, const float* density, cudaStream_t stream);
 
 // Lanes (threads) of the adjoint launch for n_total packets; the record
 // buffer holds lanes * (max_events + 1) records.
@@ -196,6 +213,6 @@ cudaError_t adjoint_lanes(int num_sms, unsigned long long n_total, unsigned long
 cudaError_t launch_adjoint(const FwdParams& f, const double* const* adj_img, const size_t* img_elems,
                            const double* adj_abs, double* grad, AdjRecord* recs, unsigned long long lanes,
                            unsigned long long* counters, float* img_f, unsigned long long* maxbits,
-                           cudaStream_t stream);
+                           double* const* line_dep, cudaStream_t stream);
 
 }  // namespace rtk

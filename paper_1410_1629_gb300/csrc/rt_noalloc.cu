@@ -82,6 +82,8 @@ __global__ void k_noalloc_stats(const unsigned char* scratch, double emitted, rt
   s.peeloffs = cn[2];
   s.packets = cn[3];
   s.records = cn[4];
+  s.column_peels = cn[6];
+  s.column_crossings = cn[7];
   s.device_flags = *flags;
   s.reserved = 0;
   *out = s;
@@ -275,7 +277,7 @@ extern "C" rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t
   p.profile = reinterpret_cast<unsigned long long*>(o.profile);
   p.inv_n_per_lambda = (float)(1.0 / (double)n_per_lambda);
   p.flags = reinterpret_cast<int*>(scratch + kOffFlags);
-  e = launch_forward(p, RT_GRID_CARTESIAN, 0, num_sms, s);
+  e = launch_forward(p, RT_GRID_CARTESIAN, num_sms, s);
   if (e != cudaSuccess) return fail(RT_ERR_CUDA, cudaGetErrorString(e));
   if (stats_out) {
     k_noalloc_stats<<<1, 32, 0, s>>>(scratch, emitted, stats_out);

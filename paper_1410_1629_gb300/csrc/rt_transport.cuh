@@ -133,6 +133,7 @@ __device__ __forceinline__ float pick(int a, float3 v) { return a == 2 ? v.z : (
 
 // ---------------------------------------------------------------- cartesian grid
 struct CartGrid {
+  static constexpr bool kColumns = true;  // peel-offs along grid axes may use column sums
   struct Cell {
     int ix, iy, iz;
   };
@@ -235,6 +236,7 @@ __shared__ int S_CHILD[kChildCache];
 __shared__ int S_STACK[kBlock * kOctStack];
 
 struct OctGrid {
+  static constexpr bool kColumns = false;
   struct Cell {
     int leaf;
     float lo[3], hi[3];
@@ -421,8 +423,8 @@ __shared__ DevLambda S_LAM[kMaxLambda];
 // Per-lane tallies, one slot per thread in shared memory (no atomics).
 struct LaneTally {
   double escaped, absorbed, truncated;
-  unsigned long long crossings, path_crossings;
-  unsigned events, peeloffs, packets, pad;
+  unsigned long long crossings, path_crossings, column_crossings;
+  unsigned events, peeloffs, packets, column_peels;
 };
 
 template <class G>
@@ -450,6 +452,52 @@ __device__ __forceinline__ void start_walk(const FwdParams& P, Lane<G>& s, float
 }
 
 __device__ __forceinline__ float3 instr_dir(const DevInstr& I) { return make_float3(I.kobs[0], I.kobs[1], I.kobs[2]); }
+
+// A peel-off along a frame that looks exactly along grid axis I.axis: the
+// optical depth to the boundary is kappa (rho_c ds_0 + column[c]), with ds_0
+// the distance to the face of the current cell that the ray leaves (the first
+// segment of the walk) and column[c] the density integral of the cells beyond
+// it on the same grid line.  The walk's crossings are counted all the same.
+// False when the position is outside the grid (the walk then finds the entry).
+template <class G>
+__device__ __forceinline__ bool column_peel(const FwdParams& P, Lane<G>& s, const DevInstr& I, LaneTally* bt) {
+  CartGrid::Cell c;
+  if (s.has_cell) {
+    c = s.cell;
+  } else {
+    if (!inside_box(P, s.x)) return false;
+    c.ix = min(max(__float2int_rd((s.x.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
+    c.iy = min(max(__float2int_rd((s.x.y - P.lo[1]) * P.inv_d[1]), 0), P.ny - 1);
+    c.iz = min(max(__float2int_rd((s.x.z - P.lo[2]) * P.inv_d[2]), 0), P.nz - 1);
+  }
+  const int a = I.axis;
+  const bool up = I.dir > 0;
+  const int i = a == 0 ? c.ix : (a == 1 ? c.iy : c.iz);
+  const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
+  const float xa = a == 0 ? s.x.x : (a == 1 ? s.x.y : s.x.z);
+  const float plane = fmaf((float)(i + (up ? 1 : 0)), P.d[a], P.lo[a]);
+  const float ds0 = fmaxf(up ? plane - xa : xa - plane, 0.0f);
+  const int cell = c.ix + P.nx * (c.iy + P.ny * c.iz);
+  s.th = s.kappa * fmaf(load_density(&P.density[cell]), ds0, __ldg(&I.column[cell]));
+  s.tl = 0.0f;
+  s.walking = false;
+  const unsigned long long nc = (unsigned long long)(up ? n - i : i + 1);
+  bt->crossings += nc;
+  bt->column_crossings += nc;
+  bt->column_peels += 1u;
+  return true;
+}
+
+// Start the peel-off towards instrument s.q: the column sums when the frame
+// looks along a grid axis, else the walk.
+template <class G>
+__device__ __forceinline__ void start_peel(const FwdParams& P, Lane<G>& s, typename G::Scratch& sc, LaneTally* bt) {
+  const DevInstr& I = S_INSTR[s.q];
+  if constexpr (G::kColumns) {
+    if (P.use_columns && I.column && column_peel(P, s, I, bt)) return;
+  }
+  start_walk(P, s, instr_dir(I), sc);
+}
 
 // Deposit a finished peel-off into instrument q's image(s).
 template <class G>
@@ -597,7 +645,7 @@ __device__ void control(const FwdParams& P, Lane<G>& s, unsigned long long w, La
         if (P.peel_emission && P.n_instr > 0) {
           s.phase = kPeelEmit;
           s.q = 0;
-          start_walk(P, s, instr_dir(S_INSTR[0]), sc);
+          start_peel(P, s, sc, bt);
         } else {
           s.event = 1;
           start_path(P, s, sc);
@@ -611,7 +659,7 @@ __device__ void control(const FwdParams& P, Lane<G>& s, unsigned long long w, La
         bt->peeloffs += 1u;
         s.q += 1;
         if (s.q < P.n_instr) {
-          start_walk(P, s, instr_dir(S_INSTR[s.q]), sc);
+          start_peel(P, s, sc, bt);
         } else if (!scattered) {
           s.event = 1;
           start_path(P, s, sc);
@@ -657,7 +705,7 @@ __device__ void control(const FwdParams& P, Lane<G>& s, unsigned long long w, La
         if (P.peel_scatter && P.n_instr > 0) {
           s.phase = kPeelScat;
           s.q = 0;
-          start_walk(P, s, instr_dir(S_INSTR[0]), sc);
+          start_peel(P, s, sc, bt);
         } else {
           after_scattering(P, s, bt, sc);
         }
@@ -750,8 +798,8 @@ __device__ __forceinline__ void forward_body(const FwdParams& P) {
   typename G::Scratch sc = lane_scratch<G>();
   LaneTally* bt = &tally[threadIdx.x];
   bt->escaped = bt->absorbed = bt->truncated = 0.0;
-  bt->crossings = bt->path_crossings = 0ull;
-  bt->events = bt->peeloffs = bt->packets = 0u;
+  bt->crossings = bt->path_crossings = bt->column_crossings = 0ull;
+  bt->events = bt->peeloffs = bt->packets = bt->column_peels = 0u;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
   Lane<G> s;
@@ -806,11 +854,12 @@ __device__ __forceinline__ void forward_body(const FwdParams& P) {
   __syncthreads();
   if (threadIdx.x < 32) {
     double esc = 0.0, ab = 0.0, trc = 0.0;
-    unsigned long long cr = 0, pc = 0, ev = 0, pe = 0, pk = 0;
+    unsigned long long cr = 0, pc = 0, ev = 0, pe = 0, pk = 0, cc = 0, cp = 0;
     for (int t = threadIdx.x; t < kBlock; t += 32) {
       esc += tally[t].escaped; ab += tally[t].absorbed; trc += tally[t].truncated;
       cr += tally[t].crossings; pc += tally[t].path_crossings;
       ev += tally[t].events; pe += tally[t].peeloffs; pk += tally[t].packets;
+      cc += tally[t].column_crossings; cp += tally[t].column_peels;
     }
     for (int o = 16; o > 0; o >>= 1) {
       esc += __shfl_down_sync(0xffffffffu, esc, o);
@@ -821,6 +870,8 @@ __device__ __forceinline__ void forward_body(const FwdParams& P) {
       ev += __shfl_down_sync(0xffffffffu, ev, o);
       pe += __shfl_down_sync(0xffffffffu, pe, o);
       pk += __shfl_down_sync(0xffffffffu, pk, o);
+      cc += __shfl_down_sync(0xffffffffu, cc, o);
+      cp += __shfl_down_sync(0xffffffffu, cp, o);
     }
     if (threadIdx.x == 0) {
       atomicAdd(&P.stats[1], esc);
@@ -831,6 +882,10 @@ __device__ __forceinline__ void forward_body(const FwdParams& P) {
       atomicAdd(&P.counters[2], pe);
       atomicAdd(&P.counters[3], pk);
       atomicAdd(&P.counters[5], pc);
+      if (cp) {
+        atomicAdd(&P.counters[6], cp);
+        atomicAdd(&P.counters[7], cc);
+      }
     }
   }
 }

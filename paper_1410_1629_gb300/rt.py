@@ -76,7 +76,7 @@ TRACE_DTYPE = np.dtype([("event", "<i4"), ("pad", "<i4"), ("cell", "<i8"), ("x",
 class rt_launch_opts(ctypes.Structure):
     _fields_ = [("w_min", ctypes.c_double), ("max_events", ctypes.c_int32), ("weight_cut", ctypes.c_int32),
                 ("peel_emission", ctypes.c_int32), ("peel_scatter", ctypes.c_int32), ("n_norm", ctypes.c_uint64),
-                ("model_id", ctypes.c_uint32), ("block_size", ctypes.c_int32), ("records", ctypes.c_void_p),
+                ("model_id", ctypes.c_uint32), ("walk_peels", ctypes.c_int32), ("records", ctypes.c_void_p),
                 ("records_capacity", ctypes.c_int64), ("record_stride", ctypes.c_uint64),
                 ("trace", ctypes.c_void_p), ("trace_capacity", ctypes.c_int64), ("trace_packet", ctypes.c_uint64),
                 ("trace_lambda", ctypes.c_int32), ("control_lanes", ctypes.c_int32),
@@ -87,6 +87,7 @@ class rt_stats(ctypes.Structure):
     _fields_ = [("emitted", ctypes.c_double), ("escaped", ctypes.c_double), ("absorbed", ctypes.c_double),
                 ("truncated", ctypes.c_double), ("crossings", ctypes.c_uint64), ("path_crossings", ctypes.c_uint64), ("events", ctypes.c_uint64),
                 ("peeloffs", ctypes.c_uint64), ("packets", ctypes.c_uint64), ("records", ctypes.c_uint64),
+                ("column_peels", ctypes.c_uint64), ("column_crossings", ctypes.c_uint64),
                 ("device_flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):

@@ -29,7 +29,8 @@ def _problem():
 def _context_run(prob, n, first, seed, n_norm):
     sim = rt.Simulation(prob)
     try:
-        sim.launch(n, first, seed, n_norm=n_norm)
+        # the allocation-free path walks every peel-off (it keeps no column sums)
+        sim.launch(n, first, seed, n_norm=n_norm, walk_peels=1)
         imgs = [t.cpu().numpy() for t in sim.images()]
         ab = sim.absorption().cpu().numpy()
         st = sim.stats()
