@@ -243,7 +243,7 @@ __device__ __forceinline__ void fetch(const AdjParams& A, ALane& s, unsigned lon
 template <bool kAbs>
 __device__ __forceinline__ void finish_path1(const AdjParams& A, ALane& s) {
   const FwdParams& P = A.f;
-  const double tau = (double)s.th + (double)s.tl;
+  const double tau = tr::widen(s.th) + tr::widen(s.tl);
   if (!(tau > 0.0)) {  // escapes: there is no event s.event
     s.J = s.event - 1;
     s.phase = aSweep;
@@ -277,8 +277,7 @@ __device__ __forceinline__ void finish_path1(const AdjParams& A, ALane& s) {
     r.g0[0] = r.g0[1] = r.g0[2] = 0.0f;
   }
   s.L = albedo * s.L * omE;  // weight after the scattering
-  s.a0 = (float)tau_star;
-  s.a1 = (float)(tau_star - (double)s.a0);
+  tr::split_pair(tau_star, s.a0, s.a1);  // as the forward kernel
   s.h = -1;
   request_walk(s, aPath2, s.k);
 }

@@ -202,6 +202,7 @@ rt_status upload_tables(rt_ctx c, cudaStream_t s) {
     L.kappa = (float)c->kappa[l];
     L.g = (float)c->g[l];
     L.albedo = c->albedo[l];
+    L.one_minus_albedo = 1.0 - c->albedo[l];
     double tot = 0.0;
     for (auto& src : c->sources) tot += src.lum[l];
     L.lum_total = tot;

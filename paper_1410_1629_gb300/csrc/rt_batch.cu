@@ -84,7 +84,7 @@ __device__ __forceinline__ void deposit(const DevModel& M, const BLane& s, bool 
   float phase = 1.0f;
   if (scattered) phase = hg_phase(M.g, s.k.x * I.kobs[0] + s.k.y * I.kobs[1] + s.k.z * I.kobs[2]);
   const float tau = s.th;
-  const double value = tau < 80.0f ? s.L * kInv4PiD * (double)(phase * expf(-tau) * (1.0f - s.tl))
+  const double value = tau < 80.0f ? s.L * tr::widen(tr::kInv4PiF * phase * expf(-tau) * (1.0f - s.tl))
                                    : s.L * kInv4PiD * (double)phase * exp(-((double)tau + (double)s.tl));
   const float fx = (s.x.x * I.ex[0] + s.x.y * I.ex[1] + s.x.z * I.ex[2] + I.off_x) * I.sx;
   const float fy = (s.x.x * I.ey[0] + s.x.y * I.ey[1] + s.x.z * I.ey[2] + I.off_y) * I.sy;
@@ -103,7 +103,7 @@ __device__ __forceinline__ void deposit(const DevModel& M, const BLane& s, bool 
     for (int dx = 0; dx < 2; ++dx) {
       const float fix = x0 + dx, fiy = y0 + dy;
       if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) continue;
-      const double v = value * (double)((dx ? tx : 1.0f - tx) * (dy ? ty : 1.0f - ty));
+      const double v = value * tr::widen((dx ? tx : 1.0f - tx) * (dy ? ty : 1.0f - ty));
       atomicAdd(&I.image[(size_t)(int)fiy * I.nx + (int)fix], v);
     }
   }
@@ -225,7 +225,7 @@ __device__ void control(const BatchParams& P, BLane& s, const Geo& G, Tally& T, 
         break;
       }
       case tr::kPath1: {
-        const double tau = (double)s.th + (double)s.tl;
+        const double tau = tr::widen(s.th) + tr::widen(s.tl);
         if (!(tau > 0.0)) {
           T.escaped += s.L;
           s.phase = tr::kFetch;
@@ -235,13 +235,12 @@ __device__ void control(const BatchParams& P, BLane& s, const Geo& G, Tally& T, 
         const double one_minus_E = -expm1(-tau);
         const double E = 1.0 - one_minus_E;
         T.escaped += s.L * E;
-        T.absorbed += (1.0 - albedo) * s.L * one_minus_E;
+        T.absorbed += (1.0 - albedo) * s.L * one_minus_E;  // (the forward kernel's one_minus_albedo)
         const uint4 r = draw_block(s.pid, 0, s.event, 0, P.seed, (unsigned)s.m);
         const double tau_star = -log1p(-u01(r.x) * one_minus_E);
         s.u_mu = tr::u01f(r.y);
         s.u_phi = tr::u01f(r.z);
-        s.aux0 = (float)tau_star;
-        s.aux1 = (float)(tau_star - (double)s.aux0);
+        tr::split_pair(tau_star, s.aux0, s.aux1);
         s.L = albedo * s.L * one_minus_E;
         s.phase = tr::kPath2;
         start_walk(s, G, s.k);

@@ -39,8 +39,15 @@ static __device__ __noinline__ uint4 draw_block(unsigned long long pid, int lam,
                        seed, model);
 }
 
-// Uniform in (0, 1): (r + 1/2) 2^-32, exact in FP64.
-__device__ __forceinline__ double u01(uint32_t r) { return ((double)r + 0.5) * 0x1p-32; }
+// Uniform in (0, 1): (r + 1/2) 2^-32 = (2r + 1) 2^-33, exact in FP64, built
+// from the 33-bit odd integer with integer operations (normalise by its
+// leading zeros): the same value as the FP64 arithmetic, off the FP64 pipe.
+__device__ __forceinline__ double u01(uint32_t r) {
+  const unsigned long long m = 2ull * r + 1ull;
+  const int lz = __clzll((long long)m);
+  const unsigned long long bits = ((unsigned long long)(1053 - lz) << 52) | (((m << lz) << 1) >> 12);
+  return __longlong_as_double((long long)bits);
+}
 
 // ---------------------------------------------------------------- scattering
 constexpr double kInv4PiD = 0.0795774715459476679;

@@ -24,6 +24,7 @@ struct DevLambda {
   float g;            // HG asymmetry parameter
   float pad0, pad1;
   double albedo;
+  double one_minus_albedo;
   double lum_total;   // sum of the sources' luminosities at this wavelength
 };
 

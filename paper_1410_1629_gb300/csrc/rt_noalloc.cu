@@ -186,6 +186,7 @@ extern "C" rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t
     lam[l].kappa = (float)kappa[l];
     lam[l].g = (float)g[l];
     lam[l].albedo = albedo[l];
+    lam[l].one_minus_albedo = 1.0 - albedo[l];
     lam[l].lum_total = tot;
     double run = 0.0;
     for (int i = 0; i < n_sources; ++i) {

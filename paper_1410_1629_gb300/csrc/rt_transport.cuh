@@ -36,6 +36,7 @@ namespace rtk {
 namespace tr {
 
 constexpr int kBlock = 256;
+constexpr float kInv4PiF = 0.0795774715459476679f;
 // Resident blocks per SM the register allocation aims at (3 x 256 threads).
 #ifndef RT_FWD_MIN_BLOCKS
 #define RT_FWD_MIN_BLOCKS 3
@@ -47,7 +48,10 @@ enum Phase : int {
   kPath1 = 2,      // forced path, first walk
   kPath2 = 3,      // forced path, second walk (stops at the interaction)
   kPeelScat = 4,   // peel-off walk at a scattering (instrument q)
-  kExit = 5        // no packets left
+  kExit = 5,       // no packets left
+  kPeelScan = 6,   // find the next peel-off of the event from instrument q
+  kAfter = 7,      // after the scattering peel-offs
+  kStart = 8       // start walk `wphase` from x along d
 };
 
 // Error-free transformation: a + b = s + e exactly (Knuth's two-sum).
@@ -70,6 +74,24 @@ __device__ __forceinline__ double widen(float f) {
   if (e == 0u || e == 0x7f800000u) return (double)f;
   const unsigned hi = ((u & 0x7fffffffu) >> 3) + 0x38000000u;
   return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(u << 29));
+}
+
+// FP64 to FP32 by cutting the significand to 24 bits, with integer
+// operations; zero and values outside the normal FP32 range take the
+// ordinary conversion.
+__device__ __forceinline__ float cut(double v) {
+  const long long b = __double_as_longlong(v);
+  const int be = (int)((b >> 52) & 0x7ff);
+  if (be < 1023 - 126 || be > 1023 + 127) return (float)v;
+  const unsigned top = (unsigned)((unsigned long long)b >> 32);
+  return __uint_as_float((top & 0x80000000u) | ((unsigned)(be - 896) << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
+}
+
+// v as the unevaluated FP32 pair hi + lo: hi = v cut to 24 bits, lo = the
+// remainder (exact in FP64) cut likewise: |v - hi - lo| < 2^-46 |v|.
+__device__ __forceinline__ void split_pair(double v, float& hi, float& lo) {
+  hi = cut(v);
+  lo = cut(v - widen(hi));
 }
 
 // Uniform (r + 1/2) 2^-32 rounded to FP32 (= the FP64 value rounded), from
@@ -401,6 +423,7 @@ template <class G>
 struct Lane {
   unsigned long long pid;
   int lam, event, phase, q;
+  int wphase;           // the walk a kStart lane begins
   double L;             // weight
   float kappa;          // extinction per unit density at this wavelength
   float u_mu, u_phi;    // the event's Henyey-Greenstein uniforms
@@ -488,17 +511,6 @@ __device__ __forceinline__ bool column_peel(const FwdParams& P, Lane<G>& s, cons
   return true;
 }
 
-// Start the peel-off towards instrument s.q: the column sums when the frame
-// looks along a grid axis, else the walk.
-template <class G>
-__device__ __forceinline__ void start_peel(const FwdParams& P, Lane<G>& s, typename G::Scratch& sc, LaneTally* bt) {
-  const DevInstr& I = S_INSTR[s.q];
-  if constexpr (G::kColumns) {
-    if (P.use_columns && I.column && column_peel(P, s, I, bt)) return;
-  }
-  start_walk(P, s, instr_dir(I), sc);
-}
-
 // Deposit a finished peel-off into instrument q's image(s).
 template <class G>
 __device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane<G>& s, bool scattered) {
@@ -511,7 +523,7 @@ __device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane<G>& 
   // exp(-(th + tl)) with the walk's compensated optical depth: the low word
   // enters as the first-order factor (1 - tl)
   const float tau = s.th;
-  const double value = tau < 80.0f ? s.L * kInv4PiD * (double)(phase * expf(-tau) * (1.0f - s.tl))
+  const double value = tau < 80.0f ? s.L * widen(kInv4PiF * phase * expf(-tau) * (1.0f - s.tl))
                                    : s.L * kInv4PiD * (double)phase * exp(-((double)tau + (double)s.tl));
   const float fx = (s.x.x * I.ex[0] + s.x.y * I.ex[1] + s.x.z * I.ex[2] + I.off_x) * I.sx;
   const float fy = (s.x.x * I.ey[0] + s.x.y * I.ey[1] + s.x.z * I.ey[2] + I.off_y) * I.sy;
@@ -542,7 +554,7 @@ __device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane<G>& 
       for (int dx = 0; dx < 2; ++dx) {
         const float fix = x0 + dx, fiy = y0 + dy;
         if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) continue;
-        const double v = value * (double)((dx ? tx : 1.0f - tx) * (dy ? ty : 1.0f - ty));
+        const double v = value * widen((dx ? tx : 1.0f - tx) * (dy ? ty : 1.0f - ty));
         const size_t pix = (size_t)(int)fiy * I.nx + (int)fix;
         atomicAdd(&I.image[(size_t)s.lam * plane + pix], v);
         if (I.channels == 3) atomicAdd(&I.image[((size_t)ch * P.n_lambda + s.lam) * plane + pix], v);
@@ -592,20 +604,119 @@ __device__ __forceinline__ void emit(const FwdParams& P, LaneT& s) {
   s.k = make_float3(st * cp, st * sp, mu);
 }
 
+// Ask for walk `phase` from the lane's position along d; walks start in the
+// last stage of a control round, from one place in the code.
 template <class G>
-__device__ __forceinline__ void start_path(const FwdParams& P, Lane<G>& s, typename G::Scratch& sc) {
-  s.phase = kPath1;
-  start_walk(P, s, s.k, sc);
-  s.aux0 = (float)((1.0 - S_LAM[s.lam].albedo) * s.L);
+__device__ __forceinline__ void request_walk(Lane<G>& s, int phase, float3 d) {
+  s.wphase = phase;
+  s.d = d;
+  s.phase = kStart;
 }
 
-// After the scattering peel-offs: new direction, then terminate or start the
+// The forced path of event s.event: its first walk carries the deposit
+// weight (1 - albedo) L.
+template <class G>
+__device__ __forceinline__ void request_path(Lane<G>& s) {
+  s.aux0 = cut(S_LAM[s.lam].one_minus_albedo * s.L);
+  request_walk(s, kPath1, s.k);
+}
+
+// ---- the stages of a control round (each for the lanes in that phase)
+
+// A new packet (index w of the launch): wavelength, weight, emission.
+template <class G>
+__device__ __forceinline__ void fetch(const FwdParams& P, Lane<G>& s, unsigned long long w, LaneTally* bt) {
+  if (w >= P.n_total) { s.phase = kExit; return; }
+  int lam = min((int)(__ull2float_rz(w) * P.inv_n_per_lambda), P.n_lambda - 1);
+  while (lam > 0 && (unsigned long long)lam * P.n_per_lambda > w) --lam;
+  while (lam + 1 < P.n_lambda && (unsigned long long)(lam + 1) * P.n_per_lambda <= w) ++lam;
+  s.lam = lam;
+  s.pid = P.first_id + (w - (unsigned long long)lam * P.n_per_lambda);
+  const double L0 = P.L0[lam];
+  s.kappa = S_LAM[lam].kappa;
+  s.L = L0;
+  s.event = 0;
+  s.has_cell = false;
+  emit(P, s);
+  bt->packets += 1u;
+  trace_row(P, s, 0, -1, L0, 0.0, 0.0);
+  s.q = 0;
+  s.phase = kPeelScan;
+}
+
+// Path 1 ended: escape, or the deposit bookkeeping and the forced-scattering
+// inversion (FP64); then the second walk.
+template <class G>
+__device__ __forceinline__ void finish_path1(const FwdParams& P, Lane<G>& s, LaneTally* bt) {
+  const double tau = widen(s.th) + widen(s.tl);
+  if (!(tau > 0.0)) {
+    trace_row(P, s, s.event, -1, s.L, 0.0, 0.0);
+    bt->escaped += s.L;
+    s.phase = kFetch;
+    return;
+  }
+  const double one_minus_E = -expm1(-tau);
+  const double E = 1.0 - one_minus_E;
+  bt->escaped += s.L * E;
+  bt->absorbed += S_LAM[s.lam].one_minus_albedo * s.L * one_minus_E;
+  const uint4 r = draw_block(s.pid, s.lam, s.event, 0, P.seed, P.model);
+  const double tau_star = -log1p(-u01(r.x) * one_minus_E);
+  s.u_mu = u01f(r.y);
+  s.u_phi = u01f(r.z);
+  split_pair(tau_star, s.aux0, s.aux1);
+  s.L = S_LAM[s.lam].albedo * s.L * one_minus_E;  // weight after the scattering
+  request_walk(s, kPath2, s.k);
+}
+
+// Path 2 ended in the interaction cell (aux0 holds s*): move the packet,
+// then the scattering peel-offs.
+template <class G>
+__device__ __forceinline__ void finish_path2(const FwdParams& P, Lane<G>& s, LaneTally* bt) {
+  const float s_star = s.aux0;
+  float3 x = make_float3(fmaf(s_star, s.k.x, s.x.x), fmaf(s_star, s.k.y, s.x.y), fmaf(s_star, s.k.z, s.x.z));
+  s.cell = G::carried(s.w);
+  G::clamp(P, s.cell, x);
+  s.x = x;
+  s.has_cell = true;
+  bt->events += 1u;
+  trace_row(P, s, s.event, G::cell(s.w), s.L, 0.0, 0.0);
+  s.q = 0;
+  s.phase = kPeelScan;
+}
+
+// The peel-off towards instrument s.q, or the end of the event's peel-offs:
+// along a frame that looks along a grid axis the optical depth comes from
+// the column sums at once (the lane then waits for the deposit stage);
+// otherwise its walk.  After the last instrument: the first forced path
+// (emission) or the scattering (aAfter).
+template <class G>
+__device__ __forceinline__ void peel_scan(const FwdParams& P, Lane<G>& s, LaneTally* bt) {
+  const bool emission = s.event == 0;
+  if ((emission ? P.peel_emission : P.peel_scatter) && s.q < P.n_instr) {
+    const DevInstr& I = S_INSTR[s.q];
+    const int phase = emission ? kPeelEmit : kPeelScat;
+    if constexpr (G::kColumns) {
+      if (P.use_columns && I.column && column_peel(P, s, I, bt)) {
+        s.phase = phase;
+        return;
+      }
+    }
+    request_walk(s, phase, instr_dir(I));
+    return;
+  }
+  if (emission) {
+    s.event = 1;
+    request_path(s);
+  } else {
+    s.phase = kAfter;
+  }
+}
+
+// After the scattering peel-offs: new direction, then termination or the
 // next forced path.
 template <class G>
-__device__ __forceinline__ void after_scattering(const FwdParams& P, Lane<G>& s, LaneTally* bt,
-                                                 typename G::Scratch& sc) {
-  const float g = S_LAM[s.lam].g;
-  const float mu = hg_sample(g, s.u_mu);
+__device__ __forceinline__ void after_scattering(const FwdParams& P, Lane<G>& s, LaneTally* bt) {
+  const float mu = hg_sample(S_LAM[s.lam].g, s.u_mu);
   float sp, cp;
   sincospif(2.0f * s.u_phi, &sp, &cp);
   s.k = rotate_dir(s.k, mu, sp, cp);
@@ -615,107 +726,45 @@ __device__ __forceinline__ void after_scattering(const FwdParams& P, Lane<G>& s,
     return;
   }
   s.event += 1;
-  start_path(P, s, sc);
+  request_path(s);
 }
 
-// Per-event work for a lane whose walk has finished, or that needs a packet
-// (then `w` is its packet index).  Loops until the lane walks again, waits
-// for a packet, or has no work left.
+// One control round for the warp: every stage runs for the lanes in its
+// phase together, and a stage only hands lanes on to later stages (the
+// peel-off loop repeats deposit and scan while any lane has a peel-off
+// ready, which column sums complete without a walk).
 template <class G>
-__device__ void control(const FwdParams& P, Lane<G>& s, unsigned long long w, LaneTally* bt,
-                        typename G::Scratch& sc) {
+__device__ __forceinline__ void control_round(const FwdParams& P, Lane<G>& s, LaneTally* bt,
+                                              typename G::Scratch& sc, unsigned lane, unsigned lt_mask) {
+  if (!s.walking) {
+    if (s.phase == kPath1) finish_path1(P, s, bt);
+    if (s.phase == kPath2) finish_path2(P, s, bt);
+  }
+  // packets for every lane that needs one: one atomic per warp
+  const bool wants = !s.walking && s.phase == kFetch;
+  const unsigned fetchers = __ballot_sync(0xffffffffu, wants);
+  if (fetchers) {
+    unsigned long long base = 0;
+    const int leader = __ffs(fetchers) - 1;
+    if ((int)lane == leader) base = atomicAdd(P.work_counter, (unsigned long long)__popc(fetchers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (wants) fetch(P, s, base + __popc(fetchers & lt_mask), bt);
+  }
   while (true) {
-    switch (s.phase) {
-      case kFetch: {
-        if (w >= P.n_total) { s.phase = kExit; return; }
-        int lam = min((int)(__ull2float_rz(w) * P.inv_n_per_lambda), P.n_lambda - 1);
-        while (lam > 0 && (unsigned long long)lam * P.n_per_lambda > w) --lam;
-        while (lam + 1 < P.n_lambda && (unsigned long long)(lam + 1) * P.n_per_lambda <= w) ++lam;
-        s.lam = lam;
-        s.pid = P.first_id + (w - (unsigned long long)lam * P.n_per_lambda);
-        w = ~0ull;
-        const double L0 = P.L0[lam];
-        s.kappa = S_LAM[lam].kappa;
-        s.L = L0;
-        s.event = 0;
-        s.has_cell = false;
-        emit(P, s);
-        bt->packets += 1u;
-        trace_row(P, s, 0, -1, L0, 0.0, 0.0);
-        if (P.peel_emission && P.n_instr > 0) {
-          s.phase = kPeelEmit;
-          s.q = 0;
-          start_peel(P, s, sc, bt);
-        } else {
-          s.event = 1;
-          start_path(P, s, sc);
-        }
-        break;
-      }
-      case kPeelEmit:
-      case kPeelScat: {
-        const bool scattered = s.phase == kPeelScat;
-        peel_deposit(P, s, scattered);
-        bt->peeloffs += 1u;
-        s.q += 1;
-        if (s.q < P.n_instr) {
-          start_peel(P, s, sc, bt);
-        } else if (!scattered) {
-          s.event = 1;
-          start_path(P, s, sc);
-        } else {
-          after_scattering(P, s, bt, sc);
-        }
-        break;
-      }
-      case kPath1: {
-        const double tau = (double)s.th + (double)s.tl;
-        if (!(tau > 0.0)) {
-          trace_row(P, s, s.event, -1, s.L, 0.0, 0.0);
-          bt->escaped += s.L;
-          s.phase = kFetch;
-          return;
-        }
-        const double albedo = S_LAM[s.lam].albedo;
-        const double one_minus_E = -expm1(-tau);
-        const double E = 1.0 - one_minus_E;
-        bt->escaped += s.L * E;
-        bt->absorbed += (1.0 - albedo) * s.L * one_minus_E;
-        const uint4 r = draw_block(s.pid, s.lam, s.event, 0, P.seed, P.model);
-        const double tau_star = -log1p(-u01(r.x) * one_minus_E);
-        s.u_mu = u01f(r.y);
-        s.u_phi = u01f(r.z);
-        s.aux0 = (float)tau_star;
-        s.aux1 = (float)(tau_star - (double)s.aux0);
-        s.L = albedo * s.L * one_minus_E;  // weight after the scattering
-        s.phase = kPath2;
-        start_walk(P, s, s.k, sc);
-        break;
-      }
-      case kPath2: {
-        // the walk stopped in the interaction cell; aux0 holds s*
-        const float s_star = s.aux0;
-        float3 x = make_float3(fmaf(s_star, s.k.x, s.x.x), fmaf(s_star, s.k.y, s.x.y), fmaf(s_star, s.k.z, s.x.z));
-        s.cell = G::carried(s.w);
-        G::clamp(P, s.cell, x);
-        s.x = x;
-        s.has_cell = true;
-        bt->events += 1u;
-        trace_row(P, s, s.event, G::cell(s.w), s.L, 0.0, 0.0);
-        if (P.peel_scatter && P.n_instr > 0) {
-          s.phase = kPeelScat;
-          s.q = 0;
-          start_peel(P, s, sc, bt);
-        } else {
-          after_scattering(P, s, bt, sc);
-        }
-        break;
-      }
-      default:
-        return;
+    const bool ready = !s.walking && (s.phase == kPeelEmit || s.phase == kPeelScat);
+    if (!__any_sync(0xffffffffu, ready || s.phase == kPeelScan)) break;
+    if (ready) {
+      peel_deposit(P, s, s.phase == kPeelScat);
+      bt->peeloffs += 1u;
+      s.q += 1;
+      s.phase = kPeelScan;
     }
-    if (s.phase == kFetch || s.phase == kExit) return;
-    if (s.walking) return;
+    if (s.phase == kPeelScan) peel_scan(P, s, bt);
+  }
+  if (s.phase == kAfter) after_scattering(P, s, bt);
+  if (s.phase == kStart) {
+    s.phase = s.wphase;
+    start_walk(P, s, s.d, sc);
   }
 }
 
@@ -818,17 +867,7 @@ __device__ __forceinline__ void forward_body(const FwdParams& P) {
     if (prof) { ++c_iter; t0 = clock64(); }
     if (walkers == 0u || __popc(need) >= P.control_min) {
       if (prof) { ++c_rounds; c_round_lanes += __popc(need); }
-      // packets for every lane that needs one: one atomic per warp
-      const unsigned fetch = __ballot_sync(0xffffffffu, idle && s.phase == kFetch);
-      unsigned long long w = ~0ull;
-      if (fetch) {
-        unsigned long long base = 0;
-        const int leader = __ffs(fetch) - 1;
-        if ((int)lane == leader) base = atomicAdd(P.work_counter, (unsigned long long)__popc(fetch));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (idle && s.phase == kFetch) w = base + __popc(fetch & lt_mask);
-      }
-      if (idle) control(P, s, w, bt, sc);
+      control_round(P, s, bt, sc, lane, lt_mask);
       if ((n_path | n_peel) & 0xC0000000u) {  // keep the 32-bit lane counters far from overflow
         bt->crossings += (unsigned long long)n_path + n_peel;
         bt->path_crossings += n_path;
