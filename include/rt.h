@@ -235,6 +235,16 @@ rt_status rt_add_instruments(rt_ctx ctx, int32_t n, const rt_instrument_desc* in
 rt_status rt_launch_packets(rt_ctx ctx, uint64_t n_per_lambda, uint64_t first_packet_id, uint64_t seed,
                             const rt_launch_opts* opts, void* stream);
 
+/* Choose the per-event deferral threshold (opts->control_lanes) for this
+ * context's problem: times a launch of n_per_lambda packets per wavelength
+ * for each of 8, 12, 16, 20, 24, 28 lanes (other options from opts or the
+ * defaults) and keeps the fastest for later launches with control_lanes 0;
+ * written to *control_lanes if not NULL.  The threshold only reorders work:
+ * results are the same to FP64 summation order.  The tallies are zeroed
+ * afterwards.  Synchronous.  Errors: as rt_launch_packets. */
+rt_status rt_tune(rt_ctx ctx, uint64_t n_per_lambda, uint64_t seed, const rt_launch_opts* opts,
+                  int32_t* control_lanes, void* stream);
+
 /* Zero images, absorption and statistics (asynchronous on stream). */
 rt_status rt_reset_tallies(rt_ctx ctx, void* stream);
 

@@ -588,22 +588,27 @@ __global__ void __launch_bounds__(kAdjBlock, RT_ADJ_MIN_BLOCKS) k_adjoint(const 
         if (s.phase == aPeelD) { s.q += 1; s.phase = aPeelScan; }
         if (s.phase == aDep) { s.event += 1; s.phase = aDepScan; }
       }
-      // packets for every lane that needs one: one atomic per warp
-      const bool wants = !s.walking && s.phase == aFetch;
-      const unsigned fetchers = __ballot_sync(0xffffffffu, wants);
-      if (fetchers) {
-        unsigned long long base = 0;
-        const int leader = __ffs(fetchers) - 1;
-        if ((int)lane == leader) base = atomicAdd(P.work_counter, (unsigned long long)__popc(fetchers));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (wants) fetch(A, s, base + __popc(fetchers & lt_mask));
+      // new packets, their peel-offs, scatterings, sweeps and deposit scans,
+      // repeated while a lane has just finished its packet (at most two passes)
+      while (true) {
+        const bool wants = !s.walking && s.phase == aFetch;
+        const unsigned fetchers = __ballot_sync(0xffffffffu, wants);
+        if (fetchers) {
+          unsigned long long base = 0;
+          const int leader = __ffs(fetchers) - 1;
+          if ((int)lane == leader) base = atomicAdd(P.work_counter, (unsigned long long)__popc(fetchers));
+          base = __shfl_sync(0xffffffffu, base, leader);
+          if (wants) fetch(A, s, base + __popc(fetchers & lt_mask));
+        }
+        if (s.phase == aPeelScan) peel_scan(A, s, n_cross, n_dep);
+        if (s.phase == aAfter) after_peels<kAbs>(A, s);
+        if (s.phase == aSweep) {
+          if (s.J >= 1) sweep(A, s); else s.phase = aFetch;
+        }
+        if (s.phase == aDepScan) dep_scan(A, s);
+        // a fetched lane never returns to aFetch within the round
+        if (!__any_sync(0xffffffffu, !s.walking && s.phase == aFetch)) break;
       }
-      if (s.phase == aPeelScan) peel_scan(A, s, n_cross, n_dep);
-      if (s.phase == aAfter) after_peels<kAbs>(A, s);
-      if (s.phase == aSweep) {
-        if (s.J >= 1) sweep(A, s); else s.phase = aFetch;
-      }
-      if (s.phase == aDepScan) dep_scan(A, s);
       if (s.phase == aStart) start_walk(P, s);
       if ((n_cross | n_dep) & 0xC0000000u) {  // keep the 32-bit lane counters far from overflow
         tot_cross += n_cross;

@@ -107,6 +107,7 @@ struct rt_ctx_s {
   size_t adj_img_elems = 0;
   unsigned long long* d_adj_max = nullptr;
   std::vector<Batch*> batches;  // by id; null after rt_batch_destroy
+  int control_lanes = 0;        // chosen by rt_tune for launches with control_lanes 0 (0: none)
   double emitted = 0.0;  // luminosity emitted since the last reset (host-side sum)
 };
 
@@ -686,7 +687,7 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   p.trace_cap = o.trace ? o.trace_capacity : 0;
   p.trace_packet = o.trace_packet;
   p.trace_lambda = o.trace_lambda;
-  p.control_min = o.control_lanes ? o.control_lanes : 16;
+  p.control_min = o.control_lanes ? o.control_lanes : (c->control_lanes ? c->control_lanes : 16);
   p.inv_n_per_lambda = (float)(1.0 / (double)n_per_lambda);
   for (int l = 0; l < c->n_lambda; ++l) {
     double tot = 0.0;
@@ -856,6 +857,52 @@ rt_status rt_adjoint(rt_ctx c, const double* const* adj_images, int32_t n_adj_im
                      reinterpret_cast<unsigned long long*>(o.profile), c->d_adj_img, c->d_adj_max, line_dep, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
   return RT_OK;
+}
+
+rt_status rt_tune(rt_ctx c, uint64_t n_per_lambda, uint64_t seed, const rt_launch_opts* opts, int32_t* control_lanes,
+                  void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (n_per_lambda == 0) return fail(c, RT_ERR_ARG, "rt_tune: n_per_lambda must be >= 1");
+  rt_launch_opts o;
+  rt_default_opts(&o);
+  if (opts) o = *opts;
+  o.records = nullptr;
+  o.trace = nullptr;
+  o.profile = nullptr;
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cand[] = {8, 12, 16, 20, 24, 28};
+  cudaEvent_t e0, e1;
+  RT_CUDA(c, cudaEventCreate(&e0));
+  RT_CUDA(c, cudaEventCreate(&e1));
+  float best = -1.0f;
+  int best_lanes = 16;
+  rt_status st = RT_OK;
+  for (int lanes : cand) {
+    o.control_lanes = lanes;
+    cudaError_t e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) st = rt_launch_packets(c, n_per_lambda, 0, seed, &o, stream);
+    if (st != RT_OK) break;
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(c, e, "rt_tune");
+      break;
+    }
+    if (best < 0 || ms < best) {
+      best = ms;
+      best_lanes = lanes;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != RT_OK) return st;
+  c->control_lanes = best_lanes;
+  if (control_lanes) *control_lanes = best_lanes;
+  return rt_reset_tallies(c, stream);
 }
 
 rt_status rt_reset_tallies(rt_ctx c, void* stream) {

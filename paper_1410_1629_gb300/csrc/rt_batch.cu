@@ -42,6 +42,7 @@ __shared__ Tally S_TALLY[kBatchBlock];
 struct BLane {
   unsigned long long pid;
   int m, event, phase;
+  int q, wphase;      // peel-off done (1) or not (0) for this event; the walk a kStart lane begins
   double L;
   float kappa;
   float u_mu, u_phi;
@@ -140,21 +141,21 @@ __device__ __forceinline__ bool column_peel(const DevInstr& I, BLane& s, const G
   return true;
 }
 
-__device__ __forceinline__ void start_peel(const BatchParams& P, const DevInstr& I, BLane& s, const Geo& G,
-                                           Tally& T, unsigned& n_cross) {
-  if (P.use_columns && I.column && column_peel(I, s, G, T, n_cross)) return;
-  start_walk(s, G, kobs(I));
+// Ask for walk `phase` from the lane's position along d (started in the last
+// stage of a control round, from one place in the code).
+__device__ __forceinline__ void request_walk(BLane& s, int phase, float3 d) {
+  s.wphase = phase;
+  s.d = d;
+  s.phase = tr::kStart;
 }
 
-__device__ __forceinline__ void start_path(BLane& s, const Geo& G) {
-  s.phase = tr::kPath1;
-  start_walk(s, G, s.k);
-}
+// ---- the stages of a control round (the forward kernel's, for one frame
+// per model and no absorption field)
 
 // A new packet (model m, packet id pid): the model's geometry, emission from
-// its point source (the forward kernel's event-0 draws), the emission peel-off.
+// its point source (the forward kernel's event-0 draws).
 __device__ __forceinline__ void begin(const BatchParams& P, BLane& s, Geo& G, Tally& T, int m,
-                                      unsigned long long pid, unsigned& n_cross) {
+                                      unsigned long long pid) {
   const DevModel& M = P.models[m];
   if (T.model != m) {
     flush(P, T);
@@ -180,17 +181,68 @@ __device__ __forceinline__ void begin(const BatchParams& P, BLane& s, Geo& G, Ta
   float sp, cp;
   sincospif(2.0f * tr::u01f(r1.w), &sp, &cp);
   s.k = make_float3(st * cp, st * sp, mu);
-  if (P.peel_emission) {
-    s.phase = tr::kPeelEmit;
-    start_peel(P, M.instr, s, G, T, n_cross);
-  } else {
+  s.q = 0;
+  s.phase = tr::kPeelScan;
+}
+
+__device__ __forceinline__ void finish_path1(const BatchParams& P, BLane& s, Tally& T) {
+  const DevModel& M = P.models[s.m];
+  const double tau = tr::widen(s.th) + tr::widen(s.tl);
+  if (!(tau > 0.0)) {
+    T.escaped += s.L;
+    s.phase = tr::kFetch;
+    return;
+  }
+  const double albedo = M.albedo;
+  const double one_minus_E = -expm1(-tau);
+  const double E = 1.0 - one_minus_E;
+  T.escaped += s.L * E;
+  T.absorbed += (1.0 - albedo) * s.L * one_minus_E;
+  const uint4 r = draw_block(s.pid, 0, s.event, 0, P.seed, (unsigned)s.m);
+  const double tau_star = -log1p(-u01(r.x) * one_minus_E);
+  s.u_mu = tr::u01f(r.y);
+  s.u_phi = tr::u01f(r.z);
+  tr::split_pair(tau_star, s.aux0, s.aux1);
+  s.L = albedo * s.L * one_minus_E;
+  request_walk(s, tr::kPath2, s.k);
+}
+
+__device__ __forceinline__ void finish_path2(const Geo& G, BLane& s, unsigned& n_events) {
+  const float s_star = s.aux0;
+  float3 x = make_float3(fmaf(s_star, s.k.x, s.x.x), fmaf(s_star, s.k.y, s.x.y), fmaf(s_star, s.k.z, s.x.z));
+  s.cell = CartGrid::carried(s.w);
+  CartGrid::clamp(G, s.cell, x);
+  s.x = x;
+  s.has_cell = true;
+  n_events += 1u;
+  s.q = 0;
+  s.phase = tr::kPeelScan;
+}
+
+// The model's one peel-off of this event, or what follows it.
+__device__ __forceinline__ void peel_scan(const BatchParams& P, BLane& s, const Geo& G, Tally& T,
+                                          unsigned& n_cross) {
+  const bool emission = s.event == 0;
+  if ((emission ? P.peel_emission : P.peel_scatter) && s.q == 0) {
+    const DevInstr& I = P.models[s.m].instr;
+    const int phase = emission ? tr::kPeelEmit : tr::kPeelScat;
+    if (P.use_columns && I.column && column_peel(I, s, G, T, n_cross)) {
+      s.phase = phase;
+      return;
+    }
+    request_walk(s, phase, kobs(I));
+    return;
+  }
+  if (emission) {
     s.event = 1;
-    start_path(s, G);
+    request_walk(s, tr::kPath1, s.k);
+  } else {
+    s.phase = tr::kAfter;
   }
 }
 
-__device__ __forceinline__ void after_scattering(const BatchParams& P, const DevModel& M, BLane& s, const Geo& G,
-                                                 Tally& T) {
+__device__ __forceinline__ void after_scattering(const BatchParams& P, BLane& s, Tally& T) {
+  const DevModel& M = P.models[s.m];
   const float mu = hg_sample(M.g, s.u_mu);
   float sp, cp;
   sincospif(2.0f * s.u_phi, &sp, &cp);
@@ -201,73 +253,7 @@ __device__ __forceinline__ void after_scattering(const BatchParams& P, const Dev
     return;
   }
   s.event += 1;
-  start_path(s, G);
-}
-
-// Per-event work of a lane whose walk has ended (the forward kernel's, for a
-// single-channel frame and no absorption field).
-__device__ void control(const BatchParams& P, BLane& s, const Geo& G, Tally& T, unsigned& n_events,
-                        unsigned& n_peel, unsigned& n_cross) {
-  const DevModel& M = P.models[s.m];
-  while (true) {
-    switch (s.phase) {
-      case tr::kPeelEmit:
-      case tr::kPeelScat: {
-        const bool scattered = s.phase == tr::kPeelScat;
-        deposit(M, s, scattered);
-        n_peel += 1u;
-        if (!scattered) {
-          s.event = 1;
-          start_path(s, G);
-        } else {
-          after_scattering(P, M, s, G, T);
-        }
-        break;
-      }
-      case tr::kPath1: {
-        const double tau = tr::widen(s.th) + tr::widen(s.tl);
-        if (!(tau > 0.0)) {
-          T.escaped += s.L;
-          s.phase = tr::kFetch;
-          return;
-        }
-        const double albedo = M.albedo;
-        const double one_minus_E = -expm1(-tau);
-        const double E = 1.0 - one_minus_E;
-        T.escaped += s.L * E;
-        T.absorbed += (1.0 - albedo) * s.L * one_minus_E;  // (the forward kernel's one_minus_albedo)
-        const uint4 r = draw_block(s.pid, 0, s.event, 0, P.seed, (unsigned)s.m);
-        const double tau_star = -log1p(-u01(r.x) * one_minus_E);
-        s.u_mu = tr::u01f(r.y);
-        s.u_phi = tr::u01f(r.z);
-        tr::split_pair(tau_star, s.aux0, s.aux1);
-        s.L = albedo * s.L * one_minus_E;
-        s.phase = tr::kPath2;
-        start_walk(s, G, s.k);
-        break;
-      }
-      case tr::kPath2: {
-        const float s_star = s.aux0;
-        float3 x = make_float3(fmaf(s_star, s.k.x, s.x.x), fmaf(s_star, s.k.y, s.x.y), fmaf(s_star, s.k.z, s.x.z));
-        s.cell = CartGrid::carried(s.w);
-        CartGrid::clamp(G, s.cell, x);
-        s.x = x;
-        s.has_cell = true;
-        n_events += 1u;
-        if (P.peel_scatter) {
-          s.phase = tr::kPeelScat;
-          start_peel(P, M.instr, s, G, T, n_cross);
-        } else {
-          after_scattering(P, M, s, G, T);
-        }
-        break;
-      }
-      default:
-        return;
-    }
-    if (s.phase == tr::kFetch || s.phase == tr::kExit) return;
-    if (s.walking) return;
-  }
+  request_walk(s, tr::kPath1, s.k);
 }
 
 // One cell crossing (the forward kernel's step without the absorption field).
@@ -329,10 +315,29 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch(const BatchParams P) {
     const unsigned walkers = __ballot_sync(0xffffffffu, s.walking);
     if (need == 0u && walkers == 0u) break;
     if (walkers == 0u || __popc(need) >= P.control_min) {
-      if (idle && s.phase != tr::kFetch) control(P, s, G, T, n_events, n_peel, n_cross);
-      const bool wants = !s.walking && s.phase == tr::kFetch;
-      const unsigned fetchers = __ballot_sync(0xffffffffu, wants);
-      if (fetchers) {
+      // per-event work in stages, each run by the lanes in its phase together
+      if (!s.walking) {
+        if (s.phase == tr::kPath1) finish_path1(P, s, T);
+        if (s.phase == tr::kPath2) finish_path2(G, s, n_events);
+      }
+      // peel-offs, the scattering and new packets, repeated while a lane has
+      // just finished its packet (at most two passes)
+      while (true) {
+        while (true) {
+          const bool ready = !s.walking && (s.phase == tr::kPeelEmit || s.phase == tr::kPeelScat);
+          if (!__any_sync(0xffffffffu, ready || s.phase == tr::kPeelScan)) break;
+          if (ready) {
+            deposit(P.models[s.m], s, s.phase == tr::kPeelScat);
+            n_peel += 1u;
+            s.q = 1;
+            s.phase = tr::kPeelScan;
+          }
+          if (s.phase == tr::kPeelScan) peel_scan(P, s, G, T, n_cross);
+        }
+        if (s.phase == tr::kAfter) after_scattering(P, s, T);
+        const bool wants = !s.walking && s.phase == tr::kFetch;
+        const unsigned fetchers = __ballot_sync(0xffffffffu, wants);
+        if (!fetchers) break;
         // hand out packets of the warp's chunk, taking new chunks as needed
         const int rank = __popc(fetchers & lt_mask);
         int remaining = __popc(fetchers), done = 0;
@@ -364,13 +369,16 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch(const BatchParams P) {
         }
         if (wants) {
           if (my_model >= 0) {
-            begin(P, s, G, T, my_model, my_pid, n_cross);
+            begin(P, s, G, T, my_model, my_pid);
             n_packets += 1u;
-            if (!s.walking) control(P, s, G, T, n_events, n_peel, n_cross);
           } else {
             s.phase = tr::kExit;
           }
         }
+      }
+      if (s.phase == tr::kStart) {
+        s.phase = s.wphase;
+        start_walk(s, G, s.d);
       }
       if (n_cross & 0xC0000000u) {
         tot_cross += n_cross;

@@ -730,9 +730,10 @@ __device__ __forceinline__ void after_scattering(const FwdParams& P, Lane<G>& s,
 }
 
 // One control round for the warp: every stage runs for the lanes in its
-// phase together, and a stage only hands lanes on to later stages (the
-// peel-off loop repeats deposit and scan while any lane has a peel-off
-// ready, which column sums complete without a walk).
+// phase together, and a stage hands lanes on to later stages (the peel-off
+// loop repeats deposit and scan while any lane has a peel-off ready, which
+// column sums complete without a walk; lanes whose packet ended fetch the
+// next one and go round once more).
 template <class G>
 __device__ __forceinline__ void control_round(const FwdParams& P, Lane<G>& s, LaneTally* bt,
                                               typename G::Scratch& sc, unsigned lane, unsigned lt_mask) {
@@ -740,28 +741,32 @@ __device__ __forceinline__ void control_round(const FwdParams& P, Lane<G>& s, La
     if (s.phase == kPath1) finish_path1(P, s, bt);
     if (s.phase == kPath2) finish_path2(P, s, bt);
   }
-  // packets for every lane that needs one: one atomic per warp
-  const bool wants = !s.walking && s.phase == kFetch;
-  const unsigned fetchers = __ballot_sync(0xffffffffu, wants);
-  if (fetchers) {
+  // Peel-offs, the scattering and new packets, repeated while a lane has
+  // just finished its packet: such a lane starts its next packet in the same
+  // round (at most two passes: a new packet never ends before its first walk).
+  while (true) {
+    while (true) {
+      const bool ready = !s.walking && (s.phase == kPeelEmit || s.phase == kPeelScat);
+      if (!__any_sync(0xffffffffu, ready || s.phase == kPeelScan)) break;
+      if (ready) {
+        peel_deposit(P, s, s.phase == kPeelScat);
+        bt->peeloffs += 1u;
+        s.q += 1;
+        s.phase = kPeelScan;
+      }
+      if (s.phase == kPeelScan) peel_scan(P, s, bt);
+    }
+    if (s.phase == kAfter) after_scattering(P, s, bt);
+    // packets for every lane that needs one: one atomic per warp
+    const bool wants = !s.walking && s.phase == kFetch;
+    const unsigned fetchers = __ballot_sync(0xffffffffu, wants);
+    if (!fetchers) break;
     unsigned long long base = 0;
     const int leader = __ffs(fetchers) - 1;
     if ((int)lane == leader) base = atomicAdd(P.work_counter, (unsigned long long)__popc(fetchers));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (wants) fetch(P, s, base + __popc(fetchers & lt_mask), bt);
   }
-  while (true) {
-    const bool ready = !s.walking && (s.phase == kPeelEmit || s.phase == kPeelScat);
-    if (!__any_sync(0xffffffffu, ready || s.phase == kPeelScan)) break;
-    if (ready) {
-      peel_deposit(P, s, s.phase == kPeelScat);
-      bt->peeloffs += 1u;
-      s.q += 1;
-      s.phase = kPeelScan;
-    }
-    if (s.phase == kPeelScan) peel_scan(P, s, bt);
-  }
-  if (s.phase == kAfter) after_scattering(P, s, bt);
   if (s.phase == kStart) {
     s.phase = s.wphase;
     start_walk(P, s, s.d, sc);

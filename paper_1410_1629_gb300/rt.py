@@ -116,6 +116,8 @@ SIGNATURES = {
     "rt_launch_packets": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                            ctypes.POINTER(rt_launch_opts), ctypes.c_void_p]),
     "rt_reset_tallies": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "rt_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(rt_launch_opts),
+                                 ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "rt_read_absorption": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
                                             ctypes.c_void_p]),
     "rt_read_images": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
@@ -258,6 +260,14 @@ def rt_launch_packets(ctx, n_per_lambda, first_packet_id=0, seed=0, opts=None, s
     o = opts if opts is not None else rt_default_opts()
     _check(ctx, lib().rt_launch_packets(ctx, int(n_per_lambda), int(first_packet_id), int(seed), ctypes.byref(o),
                                         _stream_ptr(stream)))
+
+
+def rt_tune(ctx, n_per_lambda, seed=0, opts=None, stream=None) -> int:
+    o = opts if opts is not None else rt_default_opts()
+    lanes = ctypes.c_int32()
+    _check(ctx, lib().rt_tune(ctx, int(n_per_lambda), int(seed), ctypes.byref(o), ctypes.byref(lanes),
+                              _stream_ptr(stream)))
+    return lanes.value
 
 
 def rt_reset_tallies(ctx, stream=None):
@@ -568,6 +578,10 @@ class Simulation:
 
     def reset(self, stream=None):
         rt_reset_tallies(self.ctx, stream)
+
+    def tune(self, n_per_lambda, seed=0, stream=None, **opts) -> int:
+        """Choose the per-event deferral threshold on a sample launch (tallies zeroed after)."""
+        return rt_tune(self.ctx, n_per_lambda, seed, self.opts(**opts), stream)
 
     def image_shape(self, q):
         ins = self.problem.instruments[q]

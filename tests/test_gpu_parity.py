@@ -192,6 +192,24 @@ def test_column_sums_equal_walked_peel_offs(problem):
     np.testing.assert_allclose(summed["stats"], walked["stats"], rtol=1e-12)
 
 
+def test_tuner_keeps_results():
+    """rt_tune picks a deferral threshold on a sample and zeroes the tallies;
+    a launch afterwards equals an untuned launch to FP64 summation order."""
+    prob = W.disk_galaxy(n_cells=32, n_lambda=2, n_pix=32)
+    ref = PAR.gpu_run(prob, 5000)
+    sim = rt.Simulation(prob)
+    try:
+        lanes = sim.tune(2000, seed=3)
+        assert lanes in (8, 12, 16, 20, 24, 28)
+        assert sim.stats()["packets"] == 0
+        got = PAR.gpu_run(prob, 5000, sim=sim)
+    finally:
+        sim.close()
+    for a, b in zip(got["images"], ref["images"]):
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-20)
+    assert np.array_equal(got["counters"], ref["counters"])
+
+
 def test_clumpy_octree_small():
     """Clumpy medium on an adaptive octree (7 levels, ~2e4 leaves), Plummer
     bulge + exponential disk, four wavelengths, two frames."""
