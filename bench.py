@@ -220,6 +220,8 @@ def adjoint_ratio(args, device, stream, flush):
             sim.reset(stream=stream)
             sim.launch(n, 0, prob.run.seed, stream=stream, **opts)
 
+        rt.rt_adjoint_tune(sim.ctx, [adj.data_ptr()], 0, max(1, n // 10), prob.run.seed + 1, o, stream.cuda_stream)
+
         def bwd(o_):
             grad.zero_()
             rt.rt_adjoint(sim.ctx, [adj.data_ptr()], 0, grad.data_ptr(), n, 0, prob.run.seed, o_, stream.cuda_stream)

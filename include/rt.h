@@ -245,6 +245,14 @@ rt_status rt_launch_packets(rt_ctx ctx, uint64_t n_per_lambda, uint64_t first_pa
 rt_status rt_tune(rt_ctx ctx, uint64_t n_per_lambda, uint64_t seed, const rt_launch_opts* opts,
                   int32_t* control_lanes, void* stream);
 
+/* The same for rt_adjoint: times rt_adjoint with these adjoint inputs (into
+ * a scratch gradient the context owns) for 12, 16, ..., 32 lanes and keeps
+ * the fastest for rt_adjoint calls with control_lanes 0.  Synchronous.
+ * Errors: as rt_adjoint, RT_ERR_OOM. */
+rt_status rt_adjoint_tune(rt_ctx ctx, const double* const* adj_images, int32_t n_adj_images,
+                          const double* adj_absorption, uint64_t n_per_lambda, uint64_t seed,
+                          const rt_launch_opts* opts, int32_t* control_lanes, void* stream);
+
 /* Zero images, absorption and statistics (asynchronous on stream). */
 rt_status rt_reset_tallies(rt_ctx ctx, void* stream);
 

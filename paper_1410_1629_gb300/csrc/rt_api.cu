@@ -108,6 +108,9 @@ struct rt_ctx_s {
   unsigned long long* d_adj_max = nullptr;
   std::vector<Batch*> batches;  // by id; null after rt_batch_destroy
   int control_lanes = 0;        // chosen by rt_tune for launches with control_lanes 0 (0: none)
+  int adjoint_lanes = 0;        // chosen by rt_adjoint_tune for rt_adjoint (0: none)
+  double* d_tune_grad = nullptr;  // rt_adjoint_tune's scratch gradient
+  size_t tune_grad_cells = 0;
   double emitted = 0.0;  // luminosity emitted since the last reset (host-side sum)
 };
 
@@ -444,7 +447,7 @@ rt_status rt_context_destroy(rt_ctx c) {
   free_grid(c);
   dfree(c->d_lam); dfree(c->d_src); dfree(c->d_src_cum); dfree(c->d_instr);
   dfree(c->d_stats); dfree(c->d_counters); dfree(c->d_work); dfree(c->d_flags);
-  dfree(c->d_adj); dfree(c->d_adj_img); dfree(c->d_adj_max);
+  dfree(c->d_adj); dfree(c->d_adj_img); dfree(c->d_adj_max); dfree(c->d_tune_grad);
   for (auto& p : c->d_line_dep) dfree(p);
   delete c;
   return RT_OK;
@@ -796,7 +799,7 @@ rt_status rt_adjoint(rt_ctx c, const double* const* adj_images, int32_t n_adj_im
   p.work_counter = c->d_work;
   p.flags = c->d_flags;
   if (o.control_lanes < 0 || o.control_lanes > 32) return fail(c, RT_ERR_ARG, "rt_adjoint: control_lanes in [0, 32]");
-  p.control_min = o.control_lanes ? o.control_lanes : 16;
+  p.control_min = o.control_lanes ? o.control_lanes : (c->adjoint_lanes ? c->adjoint_lanes : 16);
   p.inv_n_per_lambda = (float)(1.0 / (double)n_per_lambda);
   for (int l = 0; l < c->n_lambda; ++l) {
     double tot = 0.0;
@@ -903,6 +906,59 @@ rt_status rt_tune(rt_ctx c, uint64_t n_per_lambda, uint64_t seed, const rt_launc
   c->control_lanes = best_lanes;
   if (control_lanes) *control_lanes = best_lanes;
   return rt_reset_tallies(c, stream);
+}
+
+rt_status rt_adjoint_tune(rt_ctx c, const double* const* adj_images, int32_t n_adj_images,
+                          const double* adj_absorption, uint64_t n_per_lambda, uint64_t seed,
+                          const rt_launch_opts* opts, int32_t* control_lanes, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (!c->has_grid) return fail(c, RT_ERR_STATE, "rt_adjoint_tune: no grid");
+  if (n_per_lambda == 0) return fail(c, RT_ERR_ARG, "rt_adjoint_tune: n_per_lambda must be >= 1");
+  rt_launch_opts o;
+  rt_default_opts(&o);
+  if (opts) o = *opts;
+  o.profile = nullptr;
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  if ((size_t)c->n_cells > c->tune_grad_cells) {
+    dfree(c->d_tune_grad);
+    c->tune_grad_cells = 0;
+    RT_CUDA(c, cudaMalloc(&c->d_tune_grad, (size_t)c->n_cells * sizeof(double)));
+    c->tune_grad_cells = (size_t)c->n_cells;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cand[] = {12, 16, 20, 24, 28, 32};
+  cudaEvent_t e0, e1;
+  RT_CUDA(c, cudaEventCreate(&e0));
+  RT_CUDA(c, cudaEventCreate(&e1));
+  float best = -1.0f;
+  int best_lanes = 16;
+  rt_status st = RT_OK;
+  for (int lanes : cand) {
+    o.control_lanes = lanes;
+    cudaError_t e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess)
+      st = rt_adjoint(c, adj_images, n_adj_images, adj_absorption, c->d_tune_grad, n_per_lambda, 0, seed, &o, stream);
+    if (st != RT_OK) break;
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(c, e, "rt_adjoint_tune");
+      break;
+    }
+    if (best < 0 || ms < best) {
+      best = ms;
+      best_lanes = lanes;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != RT_OK) return st;
+  c->adjoint_lanes = best_lanes;
+  if (control_lanes) *control_lanes = best_lanes;
+  return RT_OK;
 }
 
 rt_status rt_reset_tallies(rt_ctx c, void* stream) {

@@ -116,6 +116,9 @@ SIGNATURES = {
     "rt_launch_packets": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                            ctypes.POINTER(rt_launch_opts), ctypes.c_void_p]),
     "rt_reset_tallies": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "rt_adjoint_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(rt_launch_opts),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "rt_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(rt_launch_opts),
                                  ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "rt_read_absorption": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
@@ -308,6 +311,17 @@ def rt_adjoint(ctx, adj_image_ptrs, adj_absorption_ptr, grad_ptr, n_per_lambda, 
     _check(ctx, lib().rt_adjoint(ctx, arr, len(ptrs), int(adj_absorption_ptr) if adj_absorption_ptr else None,
                                  int(grad_ptr), int(n_per_lambda), int(first_packet_id), int(seed), ctypes.byref(o),
                                  _stream_ptr(stream)))
+
+
+def rt_adjoint_tune(ctx, adj_image_ptrs, adj_absorption_ptr, n_per_lambda, seed=0, opts=None, stream=None) -> int:
+    ptrs = [int(p) if p else 0 for p in (adj_image_ptrs or [])]
+    arr = (ctypes.c_void_p * max(1, len(ptrs)))(*[p or None for p in ptrs])
+    o = opts if opts is not None else rt_default_opts()
+    lanes = ctypes.c_int32()
+    _check(ctx, lib().rt_adjoint_tune(ctx, arr, len(ptrs), int(adj_absorption_ptr) if adj_absorption_ptr else None,
+                                      int(n_per_lambda), int(seed), ctypes.byref(o), ctypes.byref(lanes),
+                                      _stream_ptr(stream)))
+    return lanes.value
 
 
 def rt_launch_packets_noalloc(grid_desc_, kappa, albedo, g, sources, luminosities, instruments, image_ptrs,

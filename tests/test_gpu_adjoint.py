@@ -165,6 +165,29 @@ def test_column_sums_equal_walked_peel_offs_in_the_adjoint():
         np.testing.assert_allclose(summed, walked, rtol=0, atol=2e-5 * scale)
 
 
+def test_adjoint_tuner_keeps_gradients():
+    """rt_adjoint_tune only chooses the deferral threshold: the gradient
+    afterwards equals the untuned one to FP64 summation order."""
+    prob = W.lognormal_cube(n_cells=16, n_pix=24, n_packets=8000, max_events=10)
+    rng = np.random.default_rng(9)
+    q = prob.instruments[0]
+    adj_img = rng.standard_normal((q.channels, 1, q.ny, q.nx))
+    n = prob.run.n_per_lambda
+    ref = _gpu_grad(prob, n, [adj_img], None, max_events=10, weight_cut=0)
+    sim = rt.Simulation(prob)
+    try:
+        a = torch.from_numpy(adj_img).cuda()
+        lanes = rt.rt_adjoint_tune(sim.ctx, [a.data_ptr()], 0, 2000, 1, sim.opts(max_events=10, weight_cut=0))
+        assert lanes in (12, 16, 20, 24, 28, 32)
+        grad = torch.zeros(prob.grid.n_cells, dtype=torch.float64, device="cuda")
+        rt.rt_adjoint(sim.ctx, [a.data_ptr()], 0, grad.data_ptr(), n, 0, prob.run.seed,
+                      sim.opts(max_events=10, weight_cut=0))
+        g = grad.cpu().numpy()
+    finally:
+        sim.close()
+    np.testing.assert_allclose(g, ref, rtol=1e-11, atol=1e-12 * np.abs(ref).max())
+
+
 def test_autograd_function_matches_direct_adjoint():
     from paper_1410_1629_gb300.autograd import transport
     prob = W.lognormal_cube(n_cells=8, n_pix=16, n_packets=5000, max_events=10)
