@@ -377,11 +377,37 @@ struct OctGrid {
                            fminf(fmaxf(fmaf(w.t, d.y, x.y), w.lo[1]), w.hi[1]),
                            fminf(fmaxf(fmaf(w.t, d.z, x.z), w.lo[2]), w.hi[2]));
     if (axis == 0) p.x = plane; else if (axis == 1) p.y = plane; else p.z = plane;
-    // replay from the root along the old path
     const int old_depth = w.depth;
     const unsigned long long old_path = w.path;
     float lo[3] = {P.lo[0], P.lo[1], P.lo[2]}, hi[3] = {P.hi[0], P.hi[1], P.hi[2]};
     int depth = 0;
+    // When the exit point lies strictly inside the leaf's box in the two other
+    // axes, the old path and the new one part at the level where the face
+    // plane splits an ancestor: with i the leaf's integer coordinate along
+    // `axis` at its depth D, level D - 1 - (trailing ones of i) going up,
+    // D - 1 - (trailing zeros of i) going down.  The ancestor's box there is
+    // rebuilt by halving along the old path (the same arithmetic as the
+    // descent).  Otherwise (a coordinate on a face of the leaf: the tie rule
+    // may part the paths earlier) the path is replayed from the root.
+    const bool in_x = axis == 0 || (p.x > w.lo[0] && p.x < w.hi[0]);
+    const bool in_y = axis == 1 || (p.y > w.lo[1] && p.y < w.hi[1]);
+    const bool in_z = axis == 2 || (p.z > w.lo[2] && p.z < w.hi[2]);
+    const bool inside = in_x && in_y && in_z;
+    if (inside) {
+      unsigned ia = 0;
+      for (int l = 0; l < old_depth; ++l) ia = (ia << 1) | (unsigned)((old_path >> (3 * l + axis)) & 1ull);
+      const int tb = da > 0.0f ? __ffs(~ia) - 1 : __ffs(ia) - 1;
+      const int part = old_depth - 1 - tb;
+      for (; depth < part; ++depth) {
+        const int oct = (int)((old_path >> (3 * depth)) & 7ull);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float mid = 0.5f * (lo[a] + hi[a]);
+          if ((oct >> a) & 1) lo[a] = mid; else hi[a] = mid;
+        }
+      }
+    }
+    // replay from the root along the old path (or confirm the level found)
     while (depth < old_depth) {
       float l2[3] = {lo[0], lo[1], lo[2]}, h2[3] = {hi[0], hi[1], hi[2]};
       const int oct = octant(p, d, l2, h2, true);
