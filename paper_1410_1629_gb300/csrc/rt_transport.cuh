@@ -394,9 +394,17 @@ struct OctGrid {
     const bool in_z = axis == 2 || (p.z > w.lo[2] && p.z < w.hi[2]);
     const bool inside = in_x && in_y && in_z;
     if (inside) {
-      unsigned ia = 0;
-      for (int l = 0; l < old_depth; ++l) ia = (ia << 1) | (unsigned)((old_path >> (3 * l + axis)) & 1ull);
-      const int tb = da > 0.0f ? __ffs(~ia) - 1 : __ffs(ia) - 1;
+      // the path's bits on `axis`, level l at bit l (Morton compaction of
+      // every third bit), then moved so that the leaf's level is bit 31
+      unsigned long long m = (old_path >> axis) & 0x1249249249249249ull;
+      m = (m ^ (m >> 2)) & 0x10c30c30c30c30c3ull;
+      m = (m ^ (m >> 4)) & 0x100f00f00f00f00full;
+      m = (m ^ (m >> 8)) & 0x1f0000ff0000ffull;
+      m = (m ^ (m >> 16)) & 0x1f00000000ffffull;
+      m = (m ^ (m >> 32)) & 0x1fffffull;
+      const unsigned top = (unsigned)m << (32 - old_depth);
+      // trailing ones (up) / zeros (down) of the leaf's coordinate
+      const int tb = da > 0.0f ? __clz(~top) : __clz(top);
       const int part = old_depth - 1 - tb;
       for (; depth < part; ++depth) {
         const int oct = (int)((old_path >> (3 * depth)) & 7ull);
@@ -406,8 +414,13 @@ struct OctGrid {
           if ((oct >> a) & 1) lo[a] = mid; else hi[a] = mid;
         }
       }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { w.lo[a] = lo[a]; w.hi[a] = hi[a]; }
+      w.depth = depth;
+      w.path = depth > 0 ? (old_path & ((1ull << (3 * depth)) - 1ull)) : 0ull;
+      return descend(P, p, d, w, sc);
     }
-    // replay from the root along the old path (or confirm the level found)
+    // replay from the root along the old path
     while (depth < old_depth) {
       float l2[3] = {lo[0], lo[1], lo[2]}, h2[3] = {hi[0], hi[1], hi[2]};
       const int oct = octant(p, d, l2, h2, true);
