@@ -167,6 +167,12 @@ typedef struct {
                            NULL: loop iterations, walking lanes summed over iterations,
                            per-event rounds, lanes served summed over rounds, clock cycles in
                            per-event work, clock cycles in the walk, packets, reserved      */
+  int32_t tape;         /* 1: record the adjoint tape of this launch in the context (cartesian
+                           grids; 160 B x (max_events + 1) per packet), so that an rt_adjoint
+                           of the same packets (same n_per_lambda, first_packet_id, seed and
+                           options, density unchanged, no absorption adjoint) needs no
+                           replay of the forced paths                                       */
+  int32_t reserved;
 } rt_launch_opts;
 
 /* Tallies since the last rt_reset_tallies. */

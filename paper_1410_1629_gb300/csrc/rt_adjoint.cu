@@ -85,6 +85,7 @@ struct AdjParams {
                                           // beyond c on its line (in the ray's direction) receives
   int rec_stride;                         // records per lane
   unsigned long long* counters;           // optional: [0] crossings, [1] depositing crossings
+  AdjRecord* tape;                        // the forward launch's tape ([packets][rec_stride]) or null: replay
 };
 
 // The lane: one packet.
@@ -113,6 +114,7 @@ struct ALane {
   double P, D, a_prev, e_prev;
   double3 g0;
   AdjRecord* rec;
+  float Lf;             // tape: the weight at the current event, units 2^eL
 };
 
 __device__ __forceinline__ void grad_add(double* p, double v) {
@@ -218,6 +220,29 @@ __device__ __forceinline__ void request_path(ALane& s) {
 
 // ---- the stages of a control round (each for the lanes in that phase)
 
+// Tape: the lane's position, cell and weight at event s.event (records
+// event+1 for events before the last, record 0 for the last), and the
+// direction of travel into it (that of path s.event, for the phase function).
+__device__ __forceinline__ void tape_event(const AdjParams& A, ALane& s) {
+  const AdjRecord& r = s.rec[s.event < s.J ? s.event + 1 : 0];
+  s.x = make_float3(r.x[0], r.x[1], r.x[2]);
+  s.Lf = r.L;
+  s.has_cell = r.cell >= 0;
+  if (s.has_cell) {
+    const FwdParams& P = A.f;
+    s.cell.ix = r.cell % P.nx;
+    s.cell.iy = (r.cell / P.nx) % P.ny;
+    s.cell.iz = r.cell / (P.nx * P.ny);
+  }
+  if (s.event > 0) {
+    AdjRecord& pj = s.rec[s.event];
+    s.k = make_float3(pj.k[0], pj.k[1], pj.k[2]);
+    pj.dLb = 0.0f;  // the peel-offs at this event accumulate here
+    pj.dxb[0] = pj.dxb[1] = pj.dxb[2] = 0.0f;
+  }
+}
+
+template <bool kTape>
 __device__ __forceinline__ void fetch(const AdjParams& A, ALane& s, unsigned long long w) {
   const FwdParams& P = A.f;
   if (w >= P.n_total) { s.phase = aExit; return; }
@@ -233,9 +258,16 @@ __device__ __forceinline__ void fetch(const AdjParams& A, ALane& s, unsigned lon
   s.event = 0;
   s.J = 0;
   s.has_cell = false;
-  tr::emit(P, s);
   s.q = 0;
   s.phase = aPeelScan;
+  if constexpr (kTape) {
+    // the forward launch recorded this packet's events: no replay
+    s.rec = A.tape + (size_t)w * (size_t)A.rec_stride;
+    s.J = s.rec[0].h;
+    tape_event(A, s);
+  } else {
+    tr::emit(P, s);
+  }
 }
 
 // Path 1 ended: escape, or the inversion (the forward kernel's FP64 steps)
@@ -271,10 +303,6 @@ __device__ __forceinline__ void finish_path1(const AdjParams& A, ALane& s) {
     r.Tdep = narrow(s.P + wd * s.e_prev * s.a_prev, s.eLA);  // the last index: a_n = 0
     r.D = narrow(s.D, ea);
     r.g0[0] = narrow(s.g0.x, s.eLA); r.g0[1] = narrow(s.g0.y, s.eLA); r.g0[2] = narrow(s.g0.z, s.eLA);
-  } else {
-    r.Tdep = 0.0f;
-    r.D = 0.0f;
-    r.g0[0] = r.g0[1] = r.g0[2] = 0.0f;
   }
   s.L = albedo * s.L * omE;  // weight after the scattering
   tr::split_pair(tau_star, s.a0, s.a1);  // as the forward kernel
@@ -299,7 +327,7 @@ __device__ __forceinline__ void finish_path2(const AdjParams& A, ALane& s) {
   r.kr_h = s.kr_h;
   r.rem = s.a1;
   // segments h.. with the entry of h counted: all segments minus those before h
-  r.gh[0] = r.g1[0] - s.g.x; r.gh[1] = r.g1[1] - s.g.y; r.gh[2] = r.g1[2] - s.g.z;
+  r.gp[0] = s.g.x; r.gp[1] = s.g.y; r.gp[2] = s.g.z;
   r.dLb = 0.0f;
   r.dxb[0] = r.dxb[1] = r.dxb[2] = 0.0f;
   const float s_star = s.a0;
@@ -319,7 +347,7 @@ __device__ __forceinline__ float peel_values(const AdjParams& A, ALane& s, const
   float phase = 1.0f;
   if (s.event > 0) phase = hg_phase(tr::S_LAM[s.lam].g, s.k.x * I.kobs[0] + s.k.y * I.kobs[1] + s.k.z * I.kobs[2]);
   const float pe = kInv4PiF * phase * expf(-s.th) * (1.0f - s.tl);
-  const float V = narrow(s.L, s.eL) * pe;  // units 2^eL
+  const float V = (A.tape ? s.Lf : narrow(s.L, s.eL)) * pe;  // units 2^eL
   const float l = V * W;                   // units 2^eLA
   if (s.event > 0) {
     AdjRecord& r = s.rec[s.event];
@@ -413,9 +441,20 @@ __device__ __forceinline__ void peel_scan(const AdjParams& A, ALane& s, unsigned
 
 // After the peel-offs of event s.event: the first forced path, or the new
 // direction and then termination (the sweep) or the next forced path.
-template <bool kAbs>
+template <bool kAbs, bool kTape>
 __device__ __forceinline__ void after_peels(const AdjParams& A, ALane& s) {
   const FwdParams& P = A.f;
+  if constexpr (kTape) {  // the next recorded event, or the sweep
+    if (s.event < s.J) {
+      s.event += 1;
+      s.q = 0;
+      tape_event(A, s);
+      s.phase = aPeelScan;
+    } else {
+      s.phase = aSweep;
+    }
+    return;
+  }
   if (s.event == 0) {
     s.event = 1;
     request_path<kAbs>(s);
@@ -438,6 +477,7 @@ __device__ __forceinline__ void after_peels(const AdjParams& A, ALane& s) {
 // the total T of its optical-depth adjoints and the adjoint of tau_{h-1} for
 // the depositing walk, the interaction-cell term of the gradient, and the
 // adjoints of the path's start weight and position.
+template <bool kAbs>
 __device__ __forceinline__ void sweep(const AdjParams& A, ALane& s) {
   const float albedo = (float)tr::S_LAM[s.lam].albedo;
   float Lb = 0.0f, xb0 = 0.0f, xb1 = 0.0f, xb2 = 0.0f;
@@ -460,12 +500,16 @@ __device__ __forceinline__ void sweep(const AdjParams& A, ALane& s) {
     }
     // L_j = albedo L (1 - E), tau* = -ln(1 - u (1 - E)), E = exp(-tau_path)
     const float Eb = -Lb * albedo * r.L - tsb * r.u / (1.0f - r.u * r.omE);
-    const float T = r.Tdep + tbh - r.E * Eb;
+    // deposit adjoints (with an absorption adjoint only)
+    const float Tdep = kAbs ? r.Tdep : 0.0f, Dd = kAbs ? r.D : 0.0f;
+    const float g00 = kAbs ? r.g0[0] : 0.0f, g01 = kAbs ? r.g0[1] : 0.0f, g02 = kAbs ? r.g0[2] : 0.0f;
+    const float T = Tdep + tbh - r.E * Eb;
     // the planes of the path move with x: d ds_m / d x through their parameters
-    if (k0 != 0.0f) xb0 -= (T * r.g1[0] - r.g0[0] - tbh * r.gh[0]) / k0;
-    if (k1 != 0.0f) xb1 -= (T * r.g1[1] - r.g0[1] - tbh * r.gh[1]) / k1;
-    if (k2 != 0.0f) xb2 -= (T * r.g1[2] - r.g0[2] - tbh * r.gh[2]) / k2;
-    Lb = Lb * albedo * r.omE + (1.0f - albedo) * r.D;
+    // (segments from h on: all minus those before h)
+    if (k0 != 0.0f) xb0 -= (T * r.g1[0] - g00 - tbh * (r.g1[0] - r.gp[0])) / k0;
+    if (k1 != 0.0f) xb1 -= (T * r.g1[1] - g01 - tbh * (r.g1[1] - r.gp[1])) / k1;
+    if (k2 != 0.0f) xb2 -= (T * r.g1[2] - g02 - tbh * (r.g1[2] - r.gp[2])) / k2;
+    Lb = Lb * albedo * r.omE + (1.0f - albedo) * Dd;
     r.T = T;
     r.tbh = tbh;
   }
@@ -559,7 +603,7 @@ __device__ __forceinline__ void step(const AdjParams& A, ALane& s, unsigned& n_c
   }
 }
 
-template <bool kAbs>
+template <bool kAbs, bool kTape>
 __global__ void __launch_bounds__(kAdjBlock, RT_ADJ_MIN_BLOCKS) k_adjoint(const AdjParams A) {
   const FwdParams& P = A.f;
   for (int i = threadIdx.x; i < P.n_instr; i += kAdjBlock) tr::S_INSTR[i] = P.instr[i];
@@ -582,8 +626,10 @@ __global__ void __launch_bounds__(kAdjBlock, RT_ADJ_MIN_BLOCKS) k_adjoint(const 
       // per-event work in stages, each run by the lanes in its phase together;
       // a stage only hands lanes on to later stages
       if (!s.walking) {
-        if (s.phase == aPath1) finish_path1<kAbs>(A, s);
-        if (s.phase == aPath2) finish_path2(A, s);
+        if constexpr (!kTape) {
+          if (s.phase == aPath1) finish_path1<kAbs>(A, s);
+          if (s.phase == aPath2) finish_path2(A, s);
+        }
         if (s.phase == aPeelM) finish_peel_measure(A, s);
         if (s.phase == aPeelD) { s.q += 1; s.phase = aPeelScan; }
         if (s.phase == aDep) { s.event += 1; s.phase = aDepScan; }
@@ -598,12 +644,12 @@ __global__ void __launch_bounds__(kAdjBlock, RT_ADJ_MIN_BLOCKS) k_adjoint(const 
           const int leader = __ffs(fetchers) - 1;
           if ((int)lane == leader) base = atomicAdd(P.work_counter, (unsigned long long)__popc(fetchers));
           base = __shfl_sync(0xffffffffu, base, leader);
-          if (wants) fetch(A, s, base + __popc(fetchers & lt_mask));
+          if (wants) fetch<kTape>(A, s, base + __popc(fetchers & lt_mask));
         }
         if (s.phase == aPeelScan) peel_scan(A, s, n_cross, n_dep);
-        if (s.phase == aAfter) after_peels<kAbs>(A, s);
+        if (s.phase == aAfter) after_peels<kAbs, kTape>(A, s);
         if (s.phase == aSweep) {
-          if (s.J >= 1) sweep(A, s); else s.phase = aFetch;
+          if (s.J >= 1) sweep<kAbs>(A, s); else s.phase = aFetch;
         }
         if (s.phase == aDepScan) dep_scan(A, s);
         // a fetched lane never returns to aFetch within the round
@@ -685,9 +731,9 @@ __global__ void k_to_units(const double* a, size_t n, const unsigned long long* 
 
 cudaError_t adjoint_lanes(int num_sms, unsigned long long n_total, unsigned long long* lanes) {
   int per_sm = 0, per_sm_abs = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<false>, kAdjBlock, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<false, false>, kAdjBlock, 0);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_abs, k_adjoint<true>, kAdjBlock, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_abs, k_adjoint<true, false>, kAdjBlock, 0);
   if (e != cudaSuccess) return e;
   per_sm = per_sm_abs > per_sm ? per_sm_abs : per_sm;
   per_sm = per_sm < 1 ? 1 : per_sm;
@@ -702,9 +748,10 @@ cudaError_t adjoint_lanes(int num_sms, unsigned long long n_total, unsigned long
 cudaError_t launch_adjoint(const FwdParams& f, const double* const* adj_img, const size_t* img_elems,
                            const double* adj_abs, double* grad, AdjRecord* recs, unsigned long long lanes,
                            unsigned long long* counters, float* img_f, unsigned long long* maxbits,
-                           double* const* line_dep, cudaStream_t stream) {
+                           double* const* line_dep, AdjRecord* tape, cudaStream_t stream) {
   AdjParams a;
   a.f = f;
+  a.tape = adj_abs ? nullptr : tape;  // the tape holds no absorption-adjoint quantities
   for (int k = 0; k < 6; ++k) {
     a.line_dep[k] = f.use_columns ? line_dep[k] : nullptr;
     if (a.line_dep[k]) {
@@ -742,9 +789,11 @@ cudaError_t launch_adjoint(const FwdParams& f, const double* const* adj_img, con
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)(lanes / kAdjBlock);
   if (adj_abs) {
-    k_adjoint<true><<<blocks, kAdjBlock, 0, stream>>>(a);
+    k_adjoint<true, false><<<blocks, kAdjBlock, 0, stream>>>(a);
+  } else if (a.tape) {
+    k_adjoint<false, true><<<blocks, kAdjBlock, 0, stream>>>(a);
   } else {
-    k_adjoint<false><<<blocks, kAdjBlock, 0, stream>>>(a);
+    k_adjoint<false, false><<<blocks, kAdjBlock, 0, stream>>>(a);
   }
   e = cudaGetLastError();
   for (int k = 0; k < 6 && e == cudaSuccess; ++k) {

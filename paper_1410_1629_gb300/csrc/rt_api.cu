@@ -111,6 +111,13 @@ struct rt_ctx_s {
   int adjoint_lanes = 0;        // chosen by rt_adjoint_tune for rt_adjoint (0: none)
   double* d_tune_grad = nullptr;  // rt_adjoint_tune's scratch gradient
   size_t tune_grad_cells = 0;
+  // the adjoint tape of the last launch that recorded one, and what it holds
+  AdjRecord* d_tape = nullptr;
+  size_t tape_bytes = 0;
+  bool tape_valid = false;
+  unsigned long long tape_n = 0, tape_first = 0, tape_seed = 0, tape_norm = 0;
+  int tape_max_events = 0, tape_weight_cut = 0, tape_peel_e = 0, tape_peel_s = 0, tape_model = 0, tape_columns = 0;
+  double tape_w_min = 0.0;
   double emitted = 0.0;  // luminosity emitted since the last reset (host-side sum)
 };
 
@@ -149,12 +156,14 @@ rt_status set_device(rt_ctx ctx) {
 }
 
 void free_grid(rt_ctx c) {
+  c->tape_valid = false;
   dfree(c->d_density);
   dfree(c->d_child);
   dfree(c->d_absorption);
   for (auto& p : c->d_columns) dfree(p);
   for (auto& p : c->d_line_dep) dfree(p);
   c->tables_dirty = true;
+  c->tape_valid = false;
   c->has_grid = false;
 }
 
@@ -173,12 +182,14 @@ bool frame_axis(const DevInstr& I, int& axis, int& dir) {
 }
 
 void free_problem(rt_ctx c) {
+  c->tape_valid = false;
   for (auto& q : c->instr) dfree(q.d_image);
   c->instr.clear();
   c->sources.clear();
   c->n_lambda = 0;
   dfree(c->d_absorption);
   c->tables_dirty = true;
+  c->tape_valid = false;
 }
 
 rt_status zero_tallies(rt_ctx c, cudaStream_t s) {
@@ -447,7 +458,7 @@ rt_status rt_context_destroy(rt_ctx c) {
   free_grid(c);
   dfree(c->d_lam); dfree(c->d_src); dfree(c->d_src_cum); dfree(c->d_instr);
   dfree(c->d_stats); dfree(c->d_counters); dfree(c->d_work); dfree(c->d_flags);
-  dfree(c->d_adj); dfree(c->d_adj_img); dfree(c->d_adj_max); dfree(c->d_tune_grad);
+  dfree(c->d_adj); dfree(c->d_adj_img); dfree(c->d_adj_max); dfree(c->d_tune_grad); dfree(c->d_tape);
   for (auto& p : c->d_line_dep) dfree(p);
   delete c;
   return RT_OK;
@@ -522,6 +533,7 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
   c->n_nodes = n_nodes;
   c->has_grid = true;
   c->tables_dirty = true;
+  c->tape_valid = false;
   if (grid_id) *grid_id = 0;
   return RT_OK;
 }
@@ -553,6 +565,7 @@ rt_status rt_set_optics(rt_ctx c, int32_t grid_id, int32_t n_lambda, const doubl
   RT_CUDA(c, cudaMemset(c->d_counters, 0, 8 * sizeof(unsigned long long)));
   c->emitted = 0.0;
   c->tables_dirty = true;
+  c->tape_valid = false;
   return RT_OK;
 }
 
@@ -580,6 +593,7 @@ rt_status rt_add_sources(rt_ctx c, int32_t n, const rt_source_desc* s) {
     c->sources.push_back(h);
   }
   c->tables_dirty = true;
+  c->tape_valid = false;
   return RT_OK;
 }
 
@@ -613,6 +627,7 @@ rt_status rt_add_instruments(rt_ctx c, int32_t n, const rt_instrument_desc* q, i
     c->instr.push_back(h);
   }
   c->tables_dirty = true;
+  c->tape_valid = false;
   return RT_OK;
 }
 
@@ -701,6 +716,27 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   p.profile = reinterpret_cast<unsigned long long*>(o.profile);
   p.flags = c->d_flags;
   p.use_columns = c->grid_kind == RT_GRID_CARTESIAN && !o.walk_peels;
+  if (o.tape) {
+    if (c->grid_kind != RT_GRID_CARTESIAN) return fail(c, RT_ERR_ARG, "rt_launch_packets: the tape needs a cartesian grid");
+    if (o.max_events > kMaxAdjointEvents)
+      return fail(c, RT_ERR_ARG, "rt_launch_packets: the tape needs max_events <= %d", kMaxAdjointEvents);
+    const size_t need = (size_t)n_total * (size_t)(o.max_events + 1) * sizeof(AdjRecord);
+    if (need / sizeof(AdjRecord) / (size_t)(o.max_events + 1) != (size_t)n_total)
+      return fail(c, RT_ERR_ARG, "rt_launch_packets: tape size overflow");
+    if (need > c->tape_bytes) {
+      dfree(c->d_tape);
+      c->tape_bytes = 0;
+      cudaError_t ea = cudaMalloc(&c->d_tape, need);
+      if (ea != cudaSuccess) {
+        c->d_tape = nullptr;
+        cudaGetLastError();
+        return fail(c, RT_ERR_OOM, "rt_launch_packets: %zu bytes of adjoint tape", need);
+      }
+      c->tape_bytes = need;
+    }
+    p.tape = c->d_tape;
+    p.tape_stride = o.max_events + 1;
+  }
   if (p.use_columns) {
     for (int k = 0; k < 6; ++k) {
       if (!c->columns_used[k]) continue;
@@ -712,6 +748,12 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   }
   cudaError_t e = launch_forward(p, c->grid_kind, c->num_sms, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "forward launch");
+  if (o.tape) {
+    c->tape_valid = true;
+    c->tape_n = n_per_lambda; c->tape_first = first_packet_id; c->tape_seed = seed; c->tape_norm = p.n_norm;
+    c->tape_max_events = o.max_events; c->tape_weight_cut = o.weight_cut; c->tape_w_min = o.w_min;
+    c->tape_peel_e = o.peel_emission; c->tape_peel_s = o.peel_scatter; c->tape_model = (int)o.model_id;
+  }
   // every packet starts with L0 = L_tot / n_norm
   for (int l = 0; l < c->n_lambda; ++l) {
     double tot = 0.0;
@@ -728,6 +770,7 @@ rt_status rt_update_density(rt_ctx c, const float* density, int32_t on_device, v
   if (!density) return fail(c, RT_ERR_ARG, "rt_update_density: null density");
   if (set_device(c) != RT_OK) return RT_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
+  c->tape_valid = false;
   const size_t bytes = (size_t)c->n_cells * sizeof(float);
   if (on_device) {
     RT_CUDA(c, cudaMemcpyAsync(c->d_density, density, bytes, cudaMemcpyDeviceToDevice, s));
@@ -809,10 +852,16 @@ rt_status rt_adjoint(rt_ctx c, const double* const* adj_images, int32_t n_adj_im
   }
   const double* adj[kMaxInstruments] = {nullptr};
   for (int q = 0; q < n_adj_images; ++q) adj[q] = adj_images[q];
+  // the forward launch's tape, when it recorded exactly these packets
+  const bool use_tape = c->tape_valid && !adj_absorption && c->tape_n == n_per_lambda &&
+                        c->tape_first == first_packet_id && c->tape_seed == seed && c->tape_norm == p.n_norm &&
+                        c->tape_max_events == o.max_events && c->tape_weight_cut == o.weight_cut &&
+                        c->tape_w_min == o.w_min && c->tape_peel_e == o.peel_emission &&
+                        c->tape_peel_s == o.peel_scatter && c->tape_model == (int)o.model_id;
   unsigned long long lanes = 0;
   cudaError_t e = adjoint_lanes(c->num_sms, n_total, &lanes);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint occupancy");
-  const size_t need = (size_t)lanes * (size_t)(o.max_events + 1) * sizeof(AdjRecord);
+  const size_t need = use_tape ? 0 : (size_t)lanes * (size_t)(o.max_events + 1) * sizeof(AdjRecord);
   if (need > c->adj_bytes) {
     dfree(c->d_adj);
     c->adj_bytes = 0;
@@ -857,7 +906,8 @@ rt_status rt_adjoint(rt_ctx c, const double* const* adj_images, int32_t n_adj_im
     }
   }
   e = launch_adjoint(p, adj, elems, adj_absorption, grad_density, c->d_adj, lanes,
-                     reinterpret_cast<unsigned long long*>(o.profile), c->d_adj_img, c->d_adj_max, line_dep, s);
+                     reinterpret_cast<unsigned long long*>(o.profile), c->d_adj_img, c->d_adj_max, line_dep,
+                     use_tape ? c->d_tape : nullptr, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
   return RT_OK;
 }

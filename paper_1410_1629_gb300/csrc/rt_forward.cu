@@ -8,6 +8,11 @@ namespace {
 __global__ void __launch_bounds__(tr::kBlock, RT_FWD_MIN_BLOCKS) k_forward_cartesian(const FwdParams P) {
   tr::forward_body<tr::CartGrid>(P);
 }
+// The same launch recording the adjoint tape (P.tape): the tape's lane state
+// needs the registers of two resident blocks per SM.
+__global__ void __launch_bounds__(tr::kBlock, 2) k_forward_cartesian_tape(const FwdParams P) {
+  tr::forward_body<tr::CartGrid, true>(P);
+}
 }  // namespace
 
 cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaStream_t stream) {
@@ -15,14 +20,19 @@ cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaS
   cudaError_t e = cudaMemsetAsync(p.work_counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward_cartesian, tr::kBlock, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p.tape ? k_forward_cartesian_tape : k_forward_cartesian,
+                                                    tr::kBlock, 0);
   if (e != cudaSuccess) return e;
   per_sm = per_sm < 1 ? 1 : per_sm;
   unsigned long long blocks = (unsigned long long)num_sms * per_sm;
   const unsigned long long useful = (p.n_total + tr::kBlock - 1) / tr::kBlock;
   if (blocks > useful) blocks = useful;
   if (blocks < 1) blocks = 1;
-  k_forward_cartesian<<<(unsigned)blocks, tr::kBlock, 0, stream>>>(p);
+  if (p.tape) {
+    k_forward_cartesian_tape<<<(unsigned)blocks, tr::kBlock, 0, stream>>>(p);
+  } else {
+    k_forward_cartesian<<<(unsigned)blocks, tr::kBlock, 0, stream>>>(p);
+  }
   return cudaGetLastError();
 }
 

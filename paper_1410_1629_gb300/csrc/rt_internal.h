@@ -51,6 +51,8 @@ struct DevInstr {
   int axis, dir;
 };
 
+struct AdjRecord;
+
 // Everything a forward launch needs, passed by value.
 struct FwdParams {
   // dust grid
@@ -91,6 +93,8 @@ struct FwdParams {
   unsigned long long* profile;  // optional execution counters (see rt_launch_opts.profile)
   int* flags;
   int use_columns;              // peel-offs along grid axes use the instruments' column sums
+  AdjRecord* tape;              // adjoint tape: [packets][tape_stride] event records, or null
+  int tape_stride;              // records per packet (max_events + 1)
 };
 
 enum DeviceFlag : int { kFlagCellRange = 1, kFlagOctreeDepth = 2, kFlagWalkSteps = 4, kFlagNoInteraction = 8 };
@@ -139,23 +143,36 @@ cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t 
 // packet's initial weight), adjoints of weights in 2^ea (ea the exponent of
 // the largest adjoint input), adjoints of positions and optical depths in
 // 2^(e0 + ea).
-struct AdjRecord {
+struct alignas(32) AdjRecord {
+  // sectors 0-1: written when the path's first walk ends
   float x[3], k[3];    // start of the path (the previous event's position) and its direction
   int cell;            // linear cell of the start (-1: located by the walk)
-  int hit_cell;        // cell of the interaction
+  float L;             // weight at the start
+  float omE, E, u;     // 1 - exp(-tau_path), exp(-tau_path), the inversion uniform
+  float g1[3];         // plane sums of the whole path: sum over segments of kr (e_exit - e_entry)
+  float pad0, pad1;
+  // sector 2: written at the interaction
   int h;               // crossing index of the interaction segment
   int hit_axis;        // axis of the plane entering segment h (-1 when h = 0)
+  int hit_cell;        // cell of the interaction
   float kr_h;          // kappa rho of the interaction cell
   float rem;           // tau* - tau_{h-1}
-  float L, omE, E, u;  // weight at the start, 1 - exp(-tau_path), exp(-tau_path), inversion uniform
-  float g1[3];         // plane sums of the whole path: sum over segments of kr (e_exit - e_entry)
-  float gh[3];         // the same over segments h..
-  float g0[3];         // the same weighted by the deposit-adjoint prefix (absorption adjoint)
-  float D, Tdep;       // absorption adjoint: sum a_m (e_{m-1} - e_m); sum of the deposit tau-adjoints
+  float gp[3];         // the plane sums of the segments before h (those from h on: g1 - gp)
+  // sector 3: the adjoint's
   float dLb, dxb[3];   // peel-offs at the interaction: adjoints of its weight and position
   float T, tbh;        // from the sweep: total tau-adjoint of the path, adjoint of tau_{h-1}
+  float pad2, pad3;
+  // sector 4: with an absorption adjoint
+  float g0[3];         // plane sums weighted by the deposit-adjoint prefix
+  float D, Tdep;       // sum a_m (e_{m-1} - e_m); sum of the deposit tau-adjoints
+  float pad4[3];
 };
-static_assert(sizeof(AdjRecord) == 132, "AdjRecord layout");
+static_assert(sizeof(AdjRecord) == 160, "AdjRecord layout: five 32-byte sectors");
+// The fields are grouped by writer in whole 32-byte sectors, so that the
+// forward launch recording the tape writes full sectors and never reads one.
+// Record 0 of a packet on the tape: h = the packet's last event J, x / cell
+// / L = its position, cell and weight after event J (records 1..J are its
+// forced paths, as in the adjoint's own replay).
 constexpr int kMaxAdjointEvents = 256;
 
 // One model of a batch (rt_batch.cu): cartesian grid, one wavelength, one
@@ -214,6 +231,6 @@ cudaError_t adjoint_lanes(int num_sms, unsigned long long n_total, unsigned long
 cudaError_t launch_adjoint(const FwdParams& f, const double* const* adj_img, const size_t* img_elems,
                            const double* adj_abs, double* grad, AdjRecord* recs, unsigned long long lanes,
                            unsigned long long* counters, float* img_f, unsigned long long* maxbits,
-                           double* const* line_dep, cudaStream_t stream);
+                           double* const* line_dep, AdjRecord* tape, cudaStream_t stream);
 
 }  // namespace rtk

@@ -475,6 +475,13 @@ struct Lane {
   float rho;            // density of the walk's current cell (loaded one crossing ahead)
   float th, tl;         // optical depth of the current walk (pair sum)
   float aux0, aux1;     // path 1: deposit weight; path 2: tau* as a float pair, then s*
+  // adjoint tape (launches that record one): plane sums of the current path
+  // walk, entry axis of its segment, crossings so far, the interaction's
+  // crossing index, kappa rho and remainder, the unit exponent of weights
+  float3 g;
+  int axis_in, n_cross, h, eL;
+  float kr_h, rem;
+  AdjRecord* rec;
 };
 
 // Small per-launch tables (instruments, per-wavelength optics) copied to
@@ -662,8 +669,40 @@ __device__ __forceinline__ void request_path(Lane<G>& s) {
 
 // ---- the stages of a control round (each for the lanes in that phase)
 
-// A new packet (index w of the launch): wavelength, weight, emission.
+// ---- the adjoint tape (cartesian grids; records as the adjoint's replay writes them)
+
+// v 2^-e as FP32 (e: the unit exponent), by cutting the significand.
+__device__ __forceinline__ float tape_units(double v, int e) {
+  const long long b = __double_as_longlong(v);
+  const int be = (int)((b >> 52) & 0x7ff);
+  const int fe = be - 896 - e;
+  if (be == 0x7ff || fe >= 255) return (float)ldexp(v, -e);
+  if (be == 0 || fe <= 0) return 0.0f;
+  const unsigned top = (unsigned)((unsigned long long)b >> 32);
+  return __uint_as_float((top & 0x80000000u) | ((unsigned)fe << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
+}
+
 template <class G>
+__device__ __forceinline__ int tape_cell(const FwdParams& P, const Lane<G>& s) {
+  if constexpr (G::kColumns) {
+    return s.has_cell ? s.cell.ix + P.nx * (s.cell.iy + P.ny * s.cell.iz) : -1;
+  } else {
+    return -1;
+  }
+}
+
+// The packet ends after event J: record 0 holds J and the last position.
+template <class G>
+__device__ __forceinline__ void tape_end(const FwdParams& P, const Lane<G>& s, int J) {
+  AdjRecord& r = s.rec[0];
+  r.h = J;
+  r.x[0] = s.x.x; r.x[1] = s.x.y; r.x[2] = s.x.z;
+  r.cell = tape_cell(P, s);
+  r.L = tape_units(s.L, s.eL);
+}
+
+// A new packet (index w of the launch): wavelength, weight, emission.
+template <class G, bool kTape>
 __device__ __forceinline__ void fetch(const FwdParams& P, Lane<G>& s, unsigned long long w, LaneTally* bt) {
   if (w >= P.n_total) { s.phase = kExit; return; }
   int lam = min((int)(__ull2float_rz(w) * P.inv_n_per_lambda), P.n_lambda - 1);
@@ -679,18 +718,24 @@ __device__ __forceinline__ void fetch(const FwdParams& P, Lane<G>& s, unsigned l
   emit(P, s);
   bt->packets += 1u;
   trace_row(P, s, 0, -1, L0, 0.0, 0.0);
+  if (kTape) {
+    s.rec = P.tape + (size_t)w * (size_t)P.tape_stride;
+    const int be = (int)((__double_as_longlong(L0) >> 52) & 0x7ff);
+    s.eL = be == 0 ? 0 : be - 1022;  // L0 = m 2^eL, m in [1/2, 1)
+  }
   s.q = 0;
   s.phase = kPeelScan;
 }
 
 // Path 1 ended: escape, or the deposit bookkeeping and the forced-scattering
 // inversion (FP64); then the second walk.
-template <class G>
+template <class G, bool kTape>
 __device__ __forceinline__ void finish_path1(const FwdParams& P, Lane<G>& s, LaneTally* bt) {
   const double tau = widen(s.th) + widen(s.tl);
   if (!(tau > 0.0)) {
     trace_row(P, s, s.event, -1, s.L, 0.0, 0.0);
     bt->escaped += s.L;
+    if (kTape) tape_end(P, s, s.event - 1);
     s.phase = kFetch;
     return;
   }
@@ -703,14 +748,29 @@ __device__ __forceinline__ void finish_path1(const FwdParams& P, Lane<G>& s, Lan
   s.u_mu = u01f(r.y);
   s.u_phi = u01f(r.z);
   split_pair(tau_star, s.aux0, s.aux1);
+  if (kTape) {
+    // the record's first two sectors, whole, with 16-byte stores
+    float4* t = reinterpret_cast<float4*>(&s.rec[s.event]);
+    t[0] = make_float4(s.x.x, s.x.y, s.x.z, s.k.x);
+    t[1] = make_float4(s.k.y, s.k.z, __int_as_float(tape_cell(P, s)), tape_units(s.L, s.eL));
+    t[2] = make_float4((float)one_minus_E, (float)E, u01f(r.x), s.g.x);
+    t[3] = make_float4(s.g.y, s.g.z, 0.0f, 0.0f);
+    s.h = -1;
+  }
   s.L = S_LAM[s.lam].albedo * s.L * one_minus_E;  // weight after the scattering
   request_walk(s, kPath2, s.k);
 }
 
 // Path 2 ended in the interaction cell (aux0 holds s*): move the packet,
 // then the scattering peel-offs.
-template <class G>
+template <class G, bool kTape>
 __device__ __forceinline__ void finish_path2(const FwdParams& P, Lane<G>& s, LaneTally* bt) {
+  if (kTape) {
+    // the record's third sector, whole
+    float4* t = reinterpret_cast<float4*>(&s.rec[s.event]);
+    t[4] = make_float4(__int_as_float(s.h), __int_as_float(s.axis_in), __int_as_float(G::cell(s.w)), s.kr_h);
+    t[5] = make_float4(s.rem, s.g.x, s.g.y, s.g.z);
+  }
   const float s_star = s.aux0;
   float3 x = make_float3(fmaf(s_star, s.k.x, s.x.x), fmaf(s_star, s.k.y, s.x.y), fmaf(s_star, s.k.z, s.x.z));
   s.cell = G::carried(s.w);
@@ -753,7 +813,7 @@ __device__ __forceinline__ void peel_scan(const FwdParams& P, Lane<G>& s, LaneTa
 
 // After the scattering peel-offs: new direction, then termination or the
 // next forced path.
-template <class G>
+template <class G, bool kTape>
 __device__ __forceinline__ void after_scattering(const FwdParams& P, Lane<G>& s, LaneTally* bt) {
   const float mu = hg_sample(S_LAM[s.lam].g, s.u_mu);
   float sp, cp;
@@ -761,6 +821,7 @@ __device__ __forceinline__ void after_scattering(const FwdParams& P, Lane<G>& s,
   s.k = rotate_dir(s.k, mu, sp, cp);
   if ((P.weight_cut && s.L < P.L_cut[s.lam]) || s.event >= P.max_events) {
     bt->truncated += s.L;
+    if (kTape) tape_end(P, s, s.event);
     s.phase = kFetch;
     return;
   }
@@ -773,12 +834,12 @@ __device__ __forceinline__ void after_scattering(const FwdParams& P, Lane<G>& s,
 // loop repeats deposit and scan while any lane has a peel-off ready, which
 // column sums complete without a walk; lanes whose packet ended fetch the
 // next one and go round once more).
-template <class G>
+template <class G, bool kTape>
 __device__ __forceinline__ void control_round(const FwdParams& P, Lane<G>& s, LaneTally* bt,
                                               typename G::Scratch& sc, unsigned lane, unsigned lt_mask) {
   if (!s.walking) {
-    if (s.phase == kPath1) finish_path1(P, s, bt);
-    if (s.phase == kPath2) finish_path2(P, s, bt);
+    if (s.phase == kPath1) finish_path1<G, kTape>(P, s, bt);
+    if (s.phase == kPath2) finish_path2<G, kTape>(P, s, bt);
   }
   // Peel-offs, the scattering and new packets, repeated while a lane has
   // just finished its packet: such a lane starts its next packet in the same
@@ -795,7 +856,7 @@ __device__ __forceinline__ void control_round(const FwdParams& P, Lane<G>& s, La
       }
       if (s.phase == kPeelScan) peel_scan(P, s, bt);
     }
-    if (s.phase == kAfter) after_scattering(P, s, bt);
+    if (s.phase == kAfter) after_scattering<G, kTape>(P, s, bt);
     // packets for every lane that needs one: one atomic per warp
     const bool wants = !s.walking && s.phase == kFetch;
     const unsigned fetchers = __ballot_sync(0xffffffffu, wants);
@@ -804,10 +865,15 @@ __device__ __forceinline__ void control_round(const FwdParams& P, Lane<G>& s, La
     const int leader = __ffs(fetchers) - 1;
     if ((int)lane == leader) base = atomicAdd(P.work_counter, (unsigned long long)__popc(fetchers));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (wants) fetch(P, s, base + __popc(fetchers & lt_mask), bt);
+    if (wants) fetch<G, kTape>(P, s, base + __popc(fetchers & lt_mask), bt);
   }
   if (s.phase == kStart) {
     s.phase = s.wphase;
+    if (kTape) {
+      s.g = make_float3(0.0f, 0.0f, 0.0f);
+      s.axis_in = -1;
+      s.n_cross = 0;
+    }
     start_walk(P, s, s.d, sc);
   }
 }
@@ -815,7 +881,7 @@ __device__ __forceinline__ void control_round(const FwdParams& P, Lane<G>& s, La
 // One cell crossing of the lane's current walk.  Written with selects rather
 // than branches where lanes in different walks (peel-off, forced path 1 or 2)
 // share the step, so the warp issues it once.
-template <class G>
+template <class G, bool kTape>
 __device__ __forceinline__ void walk_step(const FwdParams& P, Lane<G>& s, unsigned& n_path, unsigned& n_peel,
                                           typename G::Scratch& sc) {
   typename G::Walk& w = s.w;
@@ -837,7 +903,20 @@ __device__ __forceinline__ void walk_step(const FwdParams& P, Lane<G>& s, unsign
     const float rem = ((s.aux0 - s.th) + s.aux1) - s.tl;
     s.aux0 = w.t + rem / kr;
     s.walking = false;
+    if (kTape) {
+      s.kr_h = kr;
+      s.rem = rem;
+      s.h = s.n_cross;
+    }
     return;
+  }
+  if (kTape && (path1 || path2)) {
+    // plane sums of the path for the adjoint: +kr at the exit plane, -kr at the entry plane
+    s.g.x += (axis == 0 ? kr : 0.0f) - (s.axis_in == 0 ? kr : 0.0f);
+    s.g.y += (axis == 1 ? kr : 0.0f) - (s.axis_in == 1 ? kr : 0.0f);
+    s.g.z += (axis == 2 ? kr : 0.0f) - (s.axis_in == 2 ? kr : 0.0f);
+    s.axis_in = axis;
+    ++s.n_cross;
   }
   if (path1 && dt > 0.0f) {
     // continuous absorption: (1 - albedo) L exp(-tau_before) (1 - exp(-dtau))
@@ -881,7 +960,7 @@ __device__ __forceinline__ void load_grid_cache<OctGrid>(const FwdParams& P) {
   for (int i = threadIdx.x; i < n; i += kBlock) S_CHILD[i] = P.child[i];
 }
 
-template <class G>
+template <class G, bool kTape = false>
 __device__ __forceinline__ void forward_body(const FwdParams& P) {
   __shared__ LaneTally tally[kBlock];
   for (int i = threadIdx.x; i < P.n_instr; i += kBlock) S_INSTR[i] = P.instr[i];
@@ -911,7 +990,7 @@ __device__ __forceinline__ void forward_body(const FwdParams& P) {
     if (prof) { ++c_iter; t0 = clock64(); }
     if (walkers == 0u || __popc(need) >= P.control_min) {
       if (prof) { ++c_rounds; c_round_lanes += __popc(need); }
-      control_round(P, s, bt, sc, lane, lt_mask);
+      control_round<G, kTape>(P, s, bt, sc, lane, lt_mask);
       if ((n_path | n_peel) & 0xC0000000u) {  // keep the 32-bit lane counters far from overflow
         bt->crossings += (unsigned long long)n_path + n_peel;
         bt->path_crossings += n_path;
@@ -921,7 +1000,7 @@ __device__ __forceinline__ void forward_body(const FwdParams& P) {
     long long t1 = 0;
     if (prof) { t1 = clock64(); cyc_ctl += t1 - t0; }
     const unsigned stepping = __ballot_sync(0xffffffffu, s.walking);
-    if (s.walking) walk_step(P, s, n_path, n_peel, sc);
+    if (s.walking) walk_step<G, kTape>(P, s, n_path, n_peel, sc);
     if (prof) { c_walk_lanes += __popc(stepping); cyc_walk += clock64() - t1; }
   }
   if (prof) {

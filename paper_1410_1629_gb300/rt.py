@@ -80,7 +80,7 @@ class rt_launch_opts(ctypes.Structure):
                 ("records_capacity", ctypes.c_int64), ("record_stride", ctypes.c_uint64),
                 ("trace", ctypes.c_void_p), ("trace_capacity", ctypes.c_int64), ("trace_packet", ctypes.c_uint64),
                 ("trace_lambda", ctypes.c_int32), ("control_lanes", ctypes.c_int32),
-                ("profile", ctypes.c_void_p)]
+                ("profile", ctypes.c_void_p), ("tape", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class rt_stats(ctypes.Structure):

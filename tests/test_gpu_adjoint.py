@@ -165,6 +165,44 @@ def test_column_sums_equal_walked_peel_offs_in_the_adjoint():
         np.testing.assert_allclose(summed, walked, rtol=0, atol=2e-5 * scale)
 
 
+@pytest.mark.parametrize("n_cells,max_events", [(16, 10), (24, 20)])
+def test_tape_equals_replay(n_cells, max_events):
+    """A forward launch that records the adjoint tape lets rt_adjoint skip
+    the replay of the forced paths; the gradient equals the replayed one to
+    FP64 summation order (the forward writes every record field with the
+    replay's own arithmetic).  A changed density invalidates the tape."""
+    prob = W.lognormal_cube(n_cells=n_cells, n_pix=24, n_packets=6000, max_events=max_events)
+    rng = np.random.default_rng(11)
+    q = prob.instruments[0]
+    a = torch.from_numpy(rng.standard_normal((q.channels, 1, q.ny, q.nx))).cuda()
+    n = prob.run.n_per_lambda
+    o = dict(max_events=max_events, weight_cut=0)
+    sim = rt.Simulation(prob)
+    try:
+        grads = []
+        for tape in (0, 1):
+            sim.reset()
+            sim.launch(n, 0, 5, tape=tape, **o)
+            grad = torch.zeros(prob.grid.n_cells, dtype=torch.float64, device="cuda")
+            prof = torch.zeros(8, dtype=torch.int64, device="cuda")
+            rt.rt_adjoint(sim.ctx, [a.data_ptr()], 0, grad.data_ptr(), n, 0, 5, sim.opts(profile=prof.data_ptr(), **o))
+            grads.append((grad.cpu().numpy(), int(prof[0])))
+            assert sim.stats()["device_flags"] == 0
+        (g0, c0), (g1, c1) = grads
+        np.testing.assert_allclose(g1, g0, rtol=1e-10, atol=1e-12 * np.abs(g0).max())
+        assert c1 < c0  # the tape run walked fewer cells (no replay)
+        # a new density invalidates the tape: the next adjoint replays
+        d = torch.from_numpy(prob.grid.density.ravel().copy()).cuda()
+        rt.rt_update_density(sim.ctx, d.data_ptr(), 1)
+        prof = torch.zeros(8, dtype=torch.int64, device="cuda")
+        grad = torch.zeros(prob.grid.n_cells, dtype=torch.float64, device="cuda")
+        rt.rt_adjoint(sim.ctx, [a.data_ptr()], 0, grad.data_ptr(), n, 0, 5, sim.opts(profile=prof.data_ptr(), **o))
+        assert int(prof[0]) == c0
+        np.testing.assert_allclose(grad.cpu().numpy(), g0, rtol=1e-10, atol=1e-12 * np.abs(g0).max())
+    finally:
+        sim.close()
+
+
 def test_adjoint_tuner_keeps_gradients():
     """rt_adjoint_tune only chooses the deferral threshold: the gradient
     afterwards equals the untuned one to FP64 summation order."""
