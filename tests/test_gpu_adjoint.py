@@ -203,6 +203,30 @@ def test_tape_equals_replay(n_cells, max_events):
         sim.close()
 
 
+def test_autograd_image_loss_uses_the_tape():
+    """An image-only loss through the autograd Function: the forward records
+    the tape and the backward uses it; the gradient equals a direct replayed
+    adjoint of the same adjoint image."""
+    from paper_1410_1629_gb300.autograd import transport
+    prob = W.lognormal_cube(n_cells=12, n_pix=16, n_packets=5000, max_events=10)
+    sim = rt.Simulation(prob)
+    try:
+        dens = torch.from_numpy(prob.grid.density.copy()).cuda().requires_grad_(True)
+        imgs, _ = transport(dens, sim, max_events=10, weight_cut=0)
+        w = torch.linspace(-1, 1, imgs[0].numel(), device="cuda", dtype=torch.float64).view_as(imgs[0])
+        (w * imgs[0]).sum().backward()
+        g_auto = dens.grad.double().cpu().numpy().ravel()
+        sim.reset()
+        sim.launch(prob.run.n_per_lambda, 0, prob.run.seed, max_events=10, weight_cut=0)  # no tape: replay
+        grad = torch.zeros(prob.grid.n_cells, dtype=torch.float64, device="cuda")
+        rt.rt_adjoint(sim.ctx, [w.contiguous().data_ptr()], 0, grad.data_ptr(), prob.run.n_per_lambda, 0,
+                      prob.run.seed, sim.opts(max_events=10, weight_cut=0))
+        g_dir = grad.cpu().numpy()
+        np.testing.assert_allclose(g_auto, g_dir.astype(np.float32), rtol=1e-5, atol=1e-6 * np.abs(g_dir).max())
+    finally:
+        sim.close()
+
+
 def test_adjoint_tuner_keeps_gradients():
     """rt_adjoint_tune only chooses the deferral threshold: the gradient
     afterwards equals the untuned one to FP64 summation order."""
