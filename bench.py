@@ -38,10 +38,10 @@ BYTES_PATH_CROSSING, BYTES_PEEL_CROSSING, BYTES_DEPOSIT = 20, 4, 16
 BYTES_COLUMN_PEEL = 8
 # DRAM bytes (read + write) per packet of the forward kernel, from an ncu
 # capture of one 2e6-packet launch of this workload (dram__bytes_read.sum
-# 50.396 GB + dram__bytes_write.sum 18.633 GB), valid only for the kernel
+# 50.474 GB + dram__bytes_write.sum 18.314 GB), valid only for the kernel
 # sources whose hash is given; the per-launch traffic is this figure times
 # the packets.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "fc916bb89d1c1211", "bytes_per_packet": (50396154624 + 18632865280) / 2e6}
+TRAFFIC_CAPTURE = {"sources_sha256_16": "51edaf64edb17c52", "bytes_per_packet": (50473811968 + 18314334208) / 2e6}
 KERNEL_SOURCES = ["paper_1410_1629_gb300/csrc/rt_forward.cu", "paper_1410_1629_gb300/csrc/rt_device.cuh",
                   "paper_1410_1629_gb300/csrc/rt_internal.h", "paper_1410_1629_gb300/csrc/rt_transport.cuh",
                   "paper_1410_1629_gb300/build.py"]
