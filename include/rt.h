@@ -172,7 +172,14 @@ typedef struct {
                            of the same packets (same n_per_lambda, first_packet_id, seed and
                            options, density unchanged, no absorption adjoint) needs no
                            replay of the forced paths                                       */
-  int32_t reserved;
+  int32_t inline_peels; /* 0 (default): on cartesian grids, the peel-offs that walk (frames not
+                           along a grid axis, or all with walk_peels) run in a second pass after
+                           the transport kernel, ordered by instrument and start cell so that
+                           the walks of a warp share cache lines (skipped with the tape, and
+                           while its buffer, sized from the last launch's count within 40 % of
+                           free device memory, cannot be had); 1: each walks inside the
+                           transport kernel.  The two give the same optical depths, crossings
+                           and deposits; only the order of the FP64 image additions differs.   */
 } rt_launch_opts;
 
 /* Tallies since the last rt_reset_tallies. */
@@ -186,6 +193,7 @@ typedef struct {
   uint64_t records;     /* debug records produced (may exceed the capacity)                */
   uint64_t column_peels;     /* peel-offs whose optical depth came from column sums        */
   uint64_t column_crossings; /* the crossings of their rays (included in crossings)        */
+  uint64_t sorted_peels;     /* peel-offs walked in the sorted pass (rt_launch_opts.inline_peels) */
   int32_t device_flags; /* non-zero if a kernel bounds check fired                         */
   int32_t reserved;
 } rt_stats;

@@ -118,6 +118,25 @@ struct rt_ctx_s {
   unsigned long long tape_n = 0, tape_first = 0, tape_seed = 0, tape_norm = 0;
   int tape_max_events = 0, tape_weight_cut = 0, tape_peel_e = 0, tape_peel_s = 0, tape_model = 0, tape_columns = 0;
   double tape_w_min = 0.0;
+  // the sorted peel-off pass (cartesian launches): records, their order,
+  // counts per sort key and per scan tile, the record counter; the count of
+  // the last launch comes back through pinned memory without a wait and sizes
+  // the buffer of later launches
+  int n_walked_frames = 0;         // instruments without column sums
+  PeelRecord* d_peel = nullptr;
+  unsigned* d_peel_perm = nullptr;
+  unsigned long long peel_cap = 0;
+  ulonglong2* d_peel_tag = nullptr;  // packet ids and events, for launches with debug records
+  unsigned long long peel_tag_cap = 0;
+  unsigned* d_peel_hist = nullptr;
+  unsigned* d_peel_tiles = nullptr;
+  unsigned long long peel_keys = 0;
+  unsigned long long* d_peel_count = nullptr;
+  unsigned long long* h_peel_count = nullptr;  // pinned
+  cudaEvent_t peel_event = nullptr;
+  bool peel_pending = false;
+  unsigned long long peel_last_packets = 0;
+  double peel_per_packet = 0.0;    // records per packet seen (0: none yet)
   double emitted = 0.0;  // luminosity emitted since the last reset (host-side sum)
 };
 
@@ -197,7 +216,7 @@ rt_status zero_tallies(rt_ctx c, cudaStream_t s) {
   if (c->d_absorption)
     RT_CUDA(c, cudaMemsetAsync(c->d_absorption, 0, (size_t)c->n_lambda * c->n_cells * sizeof(double), s));
   RT_CUDA(c, cudaMemsetAsync(c->d_stats, 0, 4 * sizeof(double), s));
-  RT_CUDA(c, cudaMemsetAsync(c->d_counters, 0, 8 * sizeof(unsigned long long), s));
+  RT_CUDA(c, cudaMemsetAsync(c->d_counters, 0, 9 * sizeof(unsigned long long), s));
   RT_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), s));
   c->emitted = 0.0;
   return RT_OK;
@@ -267,8 +286,11 @@ rt_status upload_tables(rt_ctx c, cudaStream_t s) {
     }
   }
   for (int k = 0; k < 6; ++k) c->columns_used[k] = false;
-  for (const DevInstr& I : ins)
+  c->n_walked_frames = 0;
+  for (const DevInstr& I : ins) {
     if (I.column) c->columns_used[2 * I.axis + (I.dir > 0 ? 1 : 0)] = true;
+    else c->n_walked_frames += 1;
+  }
   dfree(c->d_lam); dfree(c->d_src); dfree(c->d_src_cum); dfree(c->d_instr);
   RT_CUDA(c, cudaMalloc(&c->d_lam, std::max<size_t>(1, lam.size()) * sizeof(DevLambda)));
   RT_CUDA(c, cudaMalloc(&c->d_src, std::max<size_t>(1, src.size()) * sizeof(DevSource)));
@@ -436,11 +458,11 @@ rt_status rt_context_create(int32_t device, rt_ctx* out) {
   e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, 4 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 9 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_work, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_flags, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, 4 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, 9 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(c->d_flags, 0, sizeof(int));
   if (e != cudaSuccess) {
     rt_context_destroy(c);
@@ -460,6 +482,10 @@ rt_status rt_context_destroy(rt_ctx c) {
   dfree(c->d_stats); dfree(c->d_counters); dfree(c->d_work); dfree(c->d_flags);
   dfree(c->d_adj); dfree(c->d_adj_img); dfree(c->d_adj_max); dfree(c->d_tune_grad); dfree(c->d_tape);
   for (auto& p : c->d_line_dep) dfree(p);
+  dfree(c->d_peel); dfree(c->d_peel_perm); dfree(c->d_peel_hist); dfree(c->d_peel_tiles); dfree(c->d_peel_count);
+  dfree(c->d_peel_tag);
+  if (c->h_peel_count) cudaFreeHost(c->h_peel_count);
+  if (c->peel_event) cudaEventDestroy(c->peel_event);
   delete c;
   return RT_OK;
 }
@@ -562,7 +588,7 @@ rt_status rt_set_optics(rt_ctx c, int32_t grid_id, int32_t n_lambda, const doubl
   RT_CUDA(c, cudaMalloc(&c->d_absorption, n_abs * sizeof(double)));
   RT_CUDA(c, cudaMemset(c->d_absorption, 0, n_abs * sizeof(double)));
   RT_CUDA(c, cudaMemset(c->d_stats, 0, 4 * sizeof(double)));
-  RT_CUDA(c, cudaMemset(c->d_counters, 0, 8 * sizeof(unsigned long long)));
+  RT_CUDA(c, cudaMemset(c->d_counters, 0, 9 * sizeof(unsigned long long)));
   c->emitted = 0.0;
   c->tables_dirty = true;
   c->tape_valid = false;
@@ -630,6 +656,86 @@ rt_status rt_add_instruments(rt_ctx c, int32_t n, const rt_instrument_desc* q, i
   c->tape_valid = false;
   return RT_OK;
 }
+
+namespace {
+
+// Buffers of the sorted peel-off pass for a launch of n_total packets with
+// `walked` instruments whose peel-offs walk; on success p.peel is set (left
+// null when the pass does not fit: the kernel then walks every peel-off).
+rt_status prepare_peel_pass(rt_ctx c, FwdParams& p, unsigned long long n_total, int walked, bool tags,
+                            cudaStream_t s) {
+  const unsigned long long keys = (unsigned long long)c->instr.size() * (unsigned long long)(c->n_cells + 1);
+  if (keys >= 0xffffffffull) return RT_OK;
+  if (!c->peel_event) {
+    RT_CUDA(c, cudaEventCreateWithFlags(&c->peel_event, cudaEventDisableTiming));
+    RT_CUDA(c, cudaMallocHost(&c->h_peel_count, sizeof(unsigned long long)));
+    RT_CUDA(c, cudaMalloc(&c->d_peel_count, sizeof(unsigned long long)));
+  }
+  if (c->peel_pending) {
+    const cudaError_t q = cudaEventQuery(c->peel_event);
+    if (q == cudaSuccess) {
+      c->peel_pending = false;
+      if (c->peel_last_packets)
+        c->peel_per_packet = (double)*c->h_peel_count / (double)c->peel_last_packets;
+    } else if (q == cudaErrorNotReady) {
+      cudaGetLastError();  // not an error: the last launch is still running
+    } else {
+      return cuda_fail(c, q, "peel-off pass");
+    }
+  }
+  // records per packet: what the last launch asked for plus a quarter, else
+  // eight per walked instrument (a packet peels off once per event)
+  const double per = c->peel_per_packet > 0.0 ? 1.25 * c->peel_per_packet + 0.05 : 8.0 * walked;
+  unsigned long long want = (unsigned long long)std::min(per * (double)n_total, 4.0e9);
+  want = std::max(want, 4096ull);
+  if (want > c->peel_cap) {
+    dfree(c->d_peel);
+    dfree(c->d_peel_perm);
+    c->peel_cap = 0;
+    size_t free_b = 0, total_b = 0;
+    RT_CUDA(c, cudaMemGetInfo(&free_b, &total_b));
+    // at most 40 % of the free device memory
+    const unsigned long long fit = (unsigned long long)(0.4 * (double)free_b) / (sizeof(PeelRecord) + sizeof(unsigned));
+    want = std::min(want, fit);
+    if (want < 4096) return RT_OK;
+    if (cudaMalloc(&c->d_peel, want * sizeof(PeelRecord)) != cudaSuccess ||
+        cudaMalloc(&c->d_peel_perm, want * sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      dfree(c->d_peel);
+      dfree(c->d_peel_perm);
+      return RT_OK;
+    }
+    c->peel_cap = want;
+  }
+  if (tags && c->peel_tag_cap < c->peel_cap) {
+    dfree(c->d_peel_tag);
+    c->peel_tag_cap = 0;
+    if (cudaMalloc(&c->d_peel_tag, c->peel_cap * sizeof(ulonglong2)) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_peel_tag = nullptr;
+      return RT_OK;
+    }
+    c->peel_tag_cap = c->peel_cap;
+  }
+  if (keys > c->peel_keys) {
+    dfree(c->d_peel_hist);
+    dfree(c->d_peel_tiles);
+    c->peel_keys = 0;
+    RT_CUDA(c, cudaMalloc(&c->d_peel_hist, keys * sizeof(unsigned)));
+    RT_CUDA(c, cudaMalloc(&c->d_peel_tiles, ((keys + 4095) / 4096) * sizeof(unsigned)));
+    c->peel_keys = keys;
+  }
+  RT_CUDA(c, cudaMemsetAsync(c->d_peel_hist, 0, keys * sizeof(unsigned), s));
+  RT_CUDA(c, cudaMemsetAsync(c->d_peel_count, 0, sizeof(unsigned long long), s));
+  p.peel = c->d_peel;
+  p.peel_cap = c->peel_cap;
+  p.peel_count = c->d_peel_count;
+  p.peel_hist = c->d_peel_hist;
+  p.peel_tag = tags ? c->d_peel_tag : nullptr;
+  return RT_OK;
+}
+
+}  // namespace
 
 rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_packet_id, uint64_t seed,
                             const rt_launch_opts* opts, void* stream) {
@@ -746,8 +852,26 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
       if (ec != cudaSuccess) return cuda_fail(c, ec, "column sums");
     }
   }
+  const int walked = o.walk_peels ? (int)c->instr.size() : c->n_walked_frames;
+  if (c->grid_kind == RT_GRID_CARTESIAN && !o.tape && !o.inline_peels && walked > 0 &&
+      (o.peel_emission || o.peel_scatter)) {
+    st = prepare_peel_pass(c, p, n_total, walked, o.records != nullptr, s);
+    if (st != RT_OK) return st;
+  }
   cudaError_t e = launch_forward(p, c->grid_kind, c->num_sms, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "forward launch");
+  if (p.peel) {
+    e = launch_peel_pass(p, (unsigned long long)c->instr.size() * (unsigned long long)(c->n_cells + 1),
+                         c->d_peel_tiles, c->d_peel_perm, c->num_sms, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "peel-off pass");
+    if (!c->peel_pending) {
+      RT_CUDA(c, cudaMemcpyAsync(c->h_peel_count, c->d_peel_count, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
+      RT_CUDA(c, cudaEventRecord(c->peel_event, s));
+      c->peel_pending = true;
+      c->peel_last_packets = n_total;
+    }
+  }
   if (o.tape) {
     c->tape_valid = true;
     c->tape_n = n_per_lambda; c->tape_first = first_packet_id; c->tape_seed = seed; c->tape_norm = p.n_norm;
@@ -1058,7 +1182,7 @@ rt_status rt_read_stats(rt_ctx c, rt_stats* out) {
   if (set_device(c) != RT_OK) return RT_ERR_CUDA;
   RT_CUDA(c, cudaDeviceSynchronize());
   double st[4];
-  unsigned long long cn[8];
+  unsigned long long cn[9];
   int flags = 0;
   RT_CUDA(c, cudaMemcpy(st, c->d_stats, sizeof st, cudaMemcpyDeviceToHost));
   RT_CUDA(c, cudaMemcpy(cn, c->d_counters, sizeof cn, cudaMemcpyDeviceToHost));
@@ -1066,7 +1190,7 @@ rt_status rt_read_stats(rt_ctx c, rt_stats* out) {
   std::memset(out, 0, sizeof *out);
   out->emitted = c->emitted; out->escaped = st[1]; out->absorbed = st[2]; out->truncated = st[3];
   out->crossings = cn[0]; out->path_crossings = cn[5]; out->events = cn[1]; out->peeloffs = cn[2]; out->packets = cn[3]; out->records = cn[4];
-  out->column_peels = cn[6]; out->column_crossings = cn[7];
+  out->column_peels = cn[6]; out->column_crossings = cn[7]; out->sorted_peels = cn[8];
   out->device_flags = flags;
   if (flags) return fail(c, RT_ERR_DEVICE_FLAG, "a kernel bounds check fired (flags 0x%x)", flags);
   return RT_OK;

@@ -53,6 +53,21 @@ struct DevInstr {
 
 struct AdjRecord;
 
+// A peel-off whose walk runs in the sorted pass after the transport kernel
+// (one 32-byte sector): the position it starts from; its sort key, the
+// instrument q times (n_cells + 1) plus the cell of the position (n_cells
+// when it lies outside the grid); the packet weight; the phase-function value
+// towards the instrument (1 at emission); the wavelength in the low 16 bits
+// of meta, bit 30 set for a scattering, bit 31 when the walk starts from the
+// packet's known cell.
+struct alignas(32) PeelRecord {
+  float x, y, z;
+  unsigned key;
+  double L;
+  float phase;
+  unsigned meta;
+};
+
 // Everything a forward launch needs, passed by value.
 struct FwdParams {
   // dust grid
@@ -78,7 +93,8 @@ struct FwdParams {
   int max_events, weight_cut, peel_emission, peel_scatter;
   unsigned long long* work_counter;
   double* stats;                  // emitted, escaped, absorbed, truncated
-  unsigned long long* counters;   // crossings, events, peeloffs, packets, records, path crossings
+  unsigned long long* counters;   // crossings, events, peeloffs, packets, records, path crossings,
+                                  // column peel-offs, column crossings, sorted-pass peel-offs
   rt_record* records;
   long long records_cap;
   unsigned long long record_stride;
@@ -95,6 +111,12 @@ struct FwdParams {
   int use_columns;              // peel-offs along grid axes use the instruments' column sums
   AdjRecord* tape;              // adjoint tape: [packets][tape_stride] event records, or null
   int tape_stride;              // records per packet (max_events + 1)
+  // peel-off walks deferred to the sorted pass (cartesian grids), or peel null
+  PeelRecord* peel;
+  unsigned long long peel_cap;     // records peel holds
+  unsigned long long* peel_count;  // records asked for (beyond peel_cap the kernel walks them itself)
+  unsigned* peel_hist;             // [n_instr][n_cells + 1]: records per sort key
+  ulonglong2* peel_tag;            // [peel_cap] packet id and event of each record (debug records on), or null
 };
 
 enum DeviceFlag : int { kFlagCellRange = 1, kFlagOctreeDepth = 2, kFlagWalkSteps = 4, kFlagNoInteraction = 8 };
@@ -137,6 +159,12 @@ cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaS
 cudaError_t launch_columns(const float* density, int nx, int ny, int nz, int axis, int dir, float d, float* out,
                            cudaStream_t stream);
 cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t stream);
+// The sorted peel-off pass after a forward launch with p.peel set
+// (rt_forward.cu): scan of p.peel_hist (n_keys entries, tile totals in
+// tile_sum: (n_keys + 4095) / 4096 entries), the permutation that orders the
+// records by key (perm: p.peel_cap entries), and the walks and deposits.
+cudaError_t launch_peel_pass(const FwdParams& p, unsigned long long n_keys, unsigned* tile_sum, unsigned* perm,
+                             int num_sms, cudaStream_t stream);
 // One forced path of a packet in the adjoint (rt_adjoint.cu): what the
 // backward sweep and the path's depositing walk need.  Adjoint quantities are
 // FP32 in exact power-of-two units: weights in 2^e0 (e0 the exponent of the

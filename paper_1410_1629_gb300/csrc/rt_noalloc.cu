@@ -84,6 +84,7 @@ __global__ void k_noalloc_stats(const unsigned char* scratch, double emitted, rt
   s.records = cn[4];
   s.column_peels = cn[6];
   s.column_crossings = cn[7];
+  s.sorted_peels = 0;
   s.device_flags = *flags;
   s.reserved = 0;
   *out = s;

@@ -557,35 +557,37 @@ __device__ __forceinline__ bool column_peel(const FwdParams& P, Lane<G>& s, cons
   return true;
 }
 
-// Deposit a finished peel-off into instrument q's image(s).
-template <class G>
-__device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane<G>& s, bool scattered) {
-  const DevInstr& I = S_INSTR[s.q];
-  float phase = 1.0f;
-  if (scattered) {
-    const float g = S_LAM[s.lam].g;
-    phase = hg_phase(g, s.k.x * I.kobs[0] + s.k.y * I.kobs[1] + s.k.z * I.kobs[2]);
-  }
+// Phase-function value of a scattering peel-off towards instrument I.
+__device__ __forceinline__ float peel_phase(int lam, float3 k, const DevInstr& I) {
+  return hg_phase(S_LAM[lam].g, k.x * I.kobs[0] + k.y * I.kobs[1] + k.z * I.kobs[2]);
+}
+
+// Deposit a finished peel-off from x (weight L, phase-function value phase,
+// optical depth th + tl) into instrument q's image(s); pid and event only
+// label debug records.
+__device__ __forceinline__ void deposit_peel(const FwdParams& P, int q, int lam, float3 x, double L, float phase,
+                                             float th, float tl, bool scattered, unsigned long long pid, int event) {
+  const DevInstr& I = S_INSTR[q];
   // exp(-(th + tl)) with the walk's compensated optical depth: the low word
   // enters as the first-order factor (1 - tl)
-  const float tau = s.th;
-  const double value = tau < 80.0f ? s.L * widen(kInv4PiF * phase * expf(-tau) * (1.0f - s.tl))
-                                   : s.L * kInv4PiD * (double)phase * exp(-((double)tau + (double)s.tl));
-  const float fx = (s.x.x * I.ex[0] + s.x.y * I.ex[1] + s.x.z * I.ex[2] + I.off_x) * I.sx;
-  const float fy = (s.x.x * I.ey[0] + s.x.y * I.ey[1] + s.x.z * I.ey[2] + I.off_y) * I.sy;
+  const float tau = th;
+  const double value = tau < 80.0f ? L * widen(kInv4PiF * phase * expf(-tau) * (1.0f - tl))
+                                   : L * kInv4PiD * (double)phase * exp(-((double)tau + (double)tl));
+  const float fx = (x.x * I.ex[0] + x.y * I.ex[1] + x.z * I.ex[2] + I.off_x) * I.sx;
+  const float fy = (x.x * I.ey[0] + x.y * I.ey[1] + x.z * I.ey[2] + I.off_y) * I.sy;
   const size_t plane = (size_t)I.ny * I.nx;
   const int ch = scattered ? 2 : 1;
   if (!I.bilinear) {
     const float fix = floorf(fx), fiy = floorf(fy);
     if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) return;
     const size_t pix = (size_t)(int)fiy * I.nx + (int)fix;
-    atomicAdd(&I.image[(size_t)s.lam * plane + pix], value);
-    if (I.channels == 3) atomicAdd(&I.image[((size_t)ch * P.n_lambda + s.lam) * plane + pix], value);
-    if (P.records && (P.record_stride <= 1 || s.pid % P.record_stride == 0)) {
+    atomicAdd(&I.image[(size_t)lam * plane + pix], value);
+    if (I.channels == 3) atomicAdd(&I.image[((size_t)ch * P.n_lambda + lam) * plane + pix], value);
+    if (P.records && (P.record_stride <= 1 || pid % P.record_stride == 0)) {
       const unsigned long long slot = atomicAdd(&P.counters[4], 1ull);
       if ((long long)slot < P.records_cap) {
         rt_record r;
-        r.packet = s.pid; r.lambda = s.lam; r.event = scattered ? s.event : 0; r.instrument = s.q;
+        r.packet = pid; r.lambda = lam; r.event = scattered ? event : 0; r.instrument = q;
         r.reserved = 0; r.pixel = (int64_t)pix; r.value = value;
         P.records[slot] = r;
       }
@@ -602,11 +604,52 @@ __device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane<G>& 
         if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) continue;
         const double v = value * widen((dx ? tx : 1.0f - tx) * (dy ? ty : 1.0f - ty));
         const size_t pix = (size_t)(int)fiy * I.nx + (int)fix;
-        atomicAdd(&I.image[(size_t)s.lam * plane + pix], v);
-        if (I.channels == 3) atomicAdd(&I.image[((size_t)ch * P.n_lambda + s.lam) * plane + pix], v);
+        atomicAdd(&I.image[(size_t)lam * plane + pix], v);
+        if (I.channels == 3) atomicAdd(&I.image[((size_t)ch * P.n_lambda + lam) * plane + pix], v);
       }
     }
   }
+}
+
+template <class G>
+__device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane<G>& s, bool scattered) {
+  const float phase = scattered ? peel_phase(s.lam, s.k, S_INSTR[s.q]) : 1.0f;
+  deposit_peel(P, s.q, s.lam, s.x, s.L, phase, s.th, s.tl, scattered, s.pid, s.event);
+}
+
+// Hand the peel-off towards instrument q to the sorted pass: a record in
+// the next free slot (one atomic per group of lanes), counted under its sort
+// key.  False when the buffer is full (the lane then walks it itself).
+template <class G>
+__device__ __forceinline__ bool defer_peel(const FwdParams& P, const Lane<G>& s, const DevInstr& I, bool emission) {
+  const unsigned m = __activemask();
+  const unsigned lane = threadIdx.x & 31u;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if ((int)lane == leader) base = atomicAdd(P.peel_count, (unsigned long long)__popc(m));
+  base = __shfl_sync(m, base, leader);
+  const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+  if (slot >= P.peel_cap) return false;
+  unsigned c = (unsigned)P.n_cells;
+  if (s.has_cell) {
+    c = (unsigned)(s.cell.ix + P.nx * (s.cell.iy + P.ny * s.cell.iz));
+  } else if (inside_box(P, s.x)) {
+    // the cell the walk will locate x in
+    const int ix = min(max(__float2int_rd((s.x.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
+    const int iy = min(max(__float2int_rd((s.x.y - P.lo[1]) * P.inv_d[1]), 0), P.ny - 1);
+    const int iz = min(max(__float2int_rd((s.x.z - P.lo[2]) * P.inv_d[2]), 0), P.nz - 1);
+    c = (unsigned)(ix + P.nx * (iy + P.ny * iz));
+  }
+  const unsigned key = (unsigned)s.q * (unsigned)(P.n_cells + 1) + c;
+  const float phase = emission ? 1.0f : peel_phase(s.lam, s.k, I);
+  const unsigned meta = (unsigned)s.lam | (emission ? 0u : 1u << 30) | (s.has_cell ? 1u << 31 : 0u);
+  const long long Lb = __double_as_longlong(s.L);
+  float4* r = reinterpret_cast<float4*>(&P.peel[slot]);
+  r[0] = make_float4(s.x.x, s.x.y, s.x.z, __uint_as_float(key));
+  r[1] = make_float4(__int_as_float((int)(unsigned)Lb), __int_as_float((int)(Lb >> 32)), phase, __uint_as_float(meta));
+  if (P.peel_tag) P.peel_tag[slot] = make_ulonglong2(s.pid, (unsigned long long)s.event);
+  atomicAdd(&P.peel_hist[key], 1u);
+  return true;
 }
 
 // Emission (Sect. 3.4): source component by luminosity (FP64 comparison of
@@ -786,8 +829,9 @@ __device__ __forceinline__ void finish_path2(const FwdParams& P, Lane<G>& s, Lan
 // The peel-off towards instrument s.q, or the end of the event's peel-offs:
 // along a frame that looks along a grid axis the optical depth comes from
 // the column sums at once (the lane then waits for the deposit stage);
-// otherwise its walk.  After the last instrument: the first forced path
-// (emission) or the scattering (aAfter).
+// otherwise a record for the sorted pass, or (no pass, or its buffer full)
+// its walk.  After the last instrument: the first forced path (emission) or
+// the scattering (kAfter).
 template <class G>
 __device__ __forceinline__ void peel_scan(const FwdParams& P, Lane<G>& s, LaneTally* bt) {
   const bool emission = s.event == 0;
@@ -797,6 +841,12 @@ __device__ __forceinline__ void peel_scan(const FwdParams& P, Lane<G>& s, LaneTa
     if constexpr (G::kColumns) {
       if (P.use_columns && I.column && column_peel(P, s, I, bt)) {
         s.phase = phase;
+        return;
+      }
+      if (P.peel && defer_peel(P, s, I, emission)) {
+        // walked and deposited by the sorted pass; on to the next instrument
+        bt->peeloffs += 1u;
+        s.q += 1;
         return;
       }
     }

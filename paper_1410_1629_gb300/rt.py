@@ -80,7 +80,7 @@ class rt_launch_opts(ctypes.Structure):
                 ("records_capacity", ctypes.c_int64), ("record_stride", ctypes.c_uint64),
                 ("trace", ctypes.c_void_p), ("trace_capacity", ctypes.c_int64), ("trace_packet", ctypes.c_uint64),
                 ("trace_lambda", ctypes.c_int32), ("control_lanes", ctypes.c_int32),
-                ("profile", ctypes.c_void_p), ("tape", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("profile", ctypes.c_void_p), ("tape", ctypes.c_int32), ("inline_peels", ctypes.c_int32)]
 
 
 class rt_stats(ctypes.Structure):
@@ -88,7 +88,7 @@ class rt_stats(ctypes.Structure):
                 ("truncated", ctypes.c_double), ("crossings", ctypes.c_uint64), ("path_crossings", ctypes.c_uint64), ("events", ctypes.c_uint64),
                 ("peeloffs", ctypes.c_uint64), ("packets", ctypes.c_uint64), ("records", ctypes.c_uint64),
                 ("column_peels", ctypes.c_uint64), ("column_crossings", ctypes.c_uint64),
-                ("device_flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("sorted_peels", ctypes.c_uint64), ("device_flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -57,7 +57,7 @@ def test_struct_sizes_match_the_header():
     assert ctypes.sizeof(rt.rt_grid_desc) == 16 + 48 + 8 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(rt.rt_record) == 40 == rt.RECORD_DTYPE.itemsize
     assert ctypes.sizeof(rt.rt_instrument_desc) == 24 + 8 + 32 + 8
-    assert ctypes.sizeof(rt.rt_stats) == 32 + 64 + 8
+    assert ctypes.sizeof(rt.rt_stats) == 32 + 72 + 8
 
 
 def test_struct_layouts_match_the_c_compiler(tmp_path):

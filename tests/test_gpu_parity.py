@@ -192,6 +192,62 @@ def test_column_sums_equal_walked_peel_offs(problem):
     np.testing.assert_allclose(summed["stats"], walked["stats"], rtol=1e-12)
 
 
+@pytest.mark.parametrize("case", ["disk", "walk_all", "overflow"])
+def test_sorted_peel_pass_equals_inline_walks(case):
+    """Walked peel-offs run in a second pass over records ordered by
+    instrument and start cell (the default on cartesian grids) or inside the
+    transport kernel (inline_peels=1): the same optical depths, crossings and
+    deposits, so tallies agree to the order of the FP64 additions.  In
+    'overflow' a packet makes up to 41 peel-offs, more than the first launch's
+    buffer holds: the kernel walks the rest itself, and the next launch's
+    buffer is sized from the first launch's count."""
+    if case == "overflow":
+        prob = W.uniform_cube(n_cells=24, axis_tau=6.0, albedo=0.9, n_pix=32, channels=3)
+        n, opts = 20000, {"walk_peels": 1, "max_events": 40, "weight_cut": 0}
+    else:
+        prob = W.disk_galaxy(n_cells=48, n_lambda=2, n_pix=48, channels=3)
+        n, opts = 20000, ({"walk_peels": 1} if case == "walk_all" else {})
+    ref = PAR.gpu_run(prob, n, inline_peels=1, **opts)
+    assert ref["raw_stats"]["sorted_peels"] == 0
+    sim = rt.Simulation(prob)
+    try:
+        runs = []
+        for _ in range(2):
+            sim.reset()
+            runs.append(PAR.gpu_run(prob, n, sim=sim, **opts))
+    finally:
+        sim.close()
+    for got in runs:
+        assert np.array_equal(got["counters"], ref["counters"])
+        for k in ("path_crossings", "column_peels", "column_crossings"):
+            assert got["raw_stats"][k] == ref["raw_stats"][k], k
+        np.testing.assert_allclose(got["absorption"], ref["absorption"], rtol=1e-12, atol=1e-30)
+        for a, b in zip(got["images"], ref["images"]):
+            np.testing.assert_allclose(a, b, rtol=1e-11, atol=1e-14 * b.max())
+        np.testing.assert_allclose(got["stats"], ref["stats"], rtol=1e-12)
+    walked = ref["raw_stats"]["peeloffs"] - ref["raw_stats"]["column_peels"]
+    first, second = (r["raw_stats"]["sorted_peels"] for r in runs)
+    if case == "overflow":
+        assert walked > 30 * n and 0 < first < walked
+    else:
+        assert first == walked
+    assert second == walked
+
+
+def test_sorted_peel_pass_records_match_inline():
+    """Debug records of peel-offs from the sorted pass carry the packet id,
+    event, instrument, pixel and value of the in-kernel walk (as a set)."""
+    prob = W.disk_galaxy(n_cells=48, n_lambda=2, n_pix=48)
+    n = 5000
+    a = PAR.gpu_run(prob, n, records_cap=400_000, inline_peels=1)
+    b = PAR.gpu_run(prob, n, records_cap=400_000)
+    assert b["raw_stats"]["sorted_peels"] > 0
+    assert a["records_total"] == b["records_total"] <= 400_000
+    ra, rb = np.sort(a["records"], order=["pid", "lam", "event", "instr"]), \
+        np.sort(b["records"], order=["pid", "lam", "event", "instr"])
+    assert np.array_equal(ra, rb)
+
+
 def test_tuner_keeps_results():
     """rt_tune picks a deferral threshold on a sample and zeroes the tallies;
     a launch afterwards equals an untuned launch to FP64 summation order."""
