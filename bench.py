@@ -41,10 +41,37 @@ BYTES_COLUMN_PEEL = 8
 # 50.474 GB + dram__bytes_write.sum 18.314 GB), valid only for the kernel
 # sources whose hash is given; the per-launch traffic is this figure times
 # the packets.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "51edaf64edb17c52", "bytes_per_packet": (50473811968 + 18314334208) / 2e6}
+TRAFFIC_CAPTURE = {"sources_sha256_16": "51edaf64edb17c52", "kernel": "k_forward_cartesian",
+                   "bytes_per_packet": (50473811968 + 18314334208) / 2e6}
 KERNEL_SOURCES = ["paper_1410_1629_gb300/csrc/rt_forward.cu", "paper_1410_1629_gb300/csrc/rt_device.cuh",
                   "paper_1410_1629_gb300/csrc/rt_internal.h", "paper_1410_1629_gb300/csrc/rt_transport.cuh",
                   "paper_1410_1629_gb300/build.py"]
+
+
+def column_tables(prob):
+    """Column-sum tables a cartesian launch builds: one per distinct grid axis
+    and direction among the frames that look exactly along an axis (sines
+    and cosines within 1e-15 of 0 or 1 taken as exact, as the library does)."""
+    import math
+    if prob.grid.kind != "cartesian":
+        return 0
+
+    def snap(v):
+        if abs(v) < 1e-15:
+            return 0.0
+        if abs(abs(v) - 1.0) < 1e-15:
+            return math.copysign(1.0, v)
+        return v
+
+    seen = set()
+    for q in prob.instruments:
+        st, ct = snap(math.sin(q.inclination)), snap(math.cos(q.inclination))
+        sp, cp = snap(math.sin(q.azimuth)), snap(math.cos(q.azimuth))
+        k = (st * cp, st * sp, ct)
+        nz = [a for a in range(3) if k[a] != 0.0]
+        if len(nz) == 1:
+            seen.add((nz[0], k[nz[0]] > 0))
+    return len(seen)
 
 
 def kernel_sources_hash():
@@ -56,10 +83,12 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def captured_traffic(packets, workload_name="disk_galaxy"):
-    """Per-launch DRAM traffic from the stored capture (disk-galaxy workload),
-    or None if the kernel changed since or another workload runs."""
-    if workload_name != "disk_galaxy" or kernel_sources_hash() != TRAFFIC_CAPTURE["sources_sha256_16"]:
+def captured_traffic(packets, workload_name="disk_galaxy", kernel="k_forward_cartesian"):
+    """Per-launch DRAM traffic of `kernel` from the stored capture
+    (disk-galaxy workload), or None if the kernel changed since, another
+    kernel is asked for or another workload runs."""
+    if (workload_name != "disk_galaxy" or kernel != TRAFFIC_CAPTURE["kernel"]
+            or kernel_sources_hash() != TRAFFIC_CAPTURE["sources_sha256_16"]):
         return None
     return TRAFFIC_CAPTURE["bytes_per_packet"] * packets
 
@@ -344,7 +373,7 @@ def run_gpu(args, prob, world, rank, local_rank):
             flush.zero_()
             sim.reset(stream=stream)
             ev0.record(stream)
-            sim.launch(n, first, prob.run.seed, stream=stream, n_norm=n_norm)
+            sim.launch(n, first, prob.run.seed, stream=stream, n_norm=n_norm, time_parts=1)
             ev1.record(stream)
 
     for _ in range(args.warmup):
@@ -356,13 +385,14 @@ def run_gpu(args, prob, world, rank, local_rank):
     torch.cuda.synchronize()
     clocks = ClockSampler(device)
     clocks.start()
-    times, counts = [], []
+    times, counts, parts = [], [], []
     for _ in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         step(e0, e1)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
         counts.append(sim.stats())
+        parts.append(sim.launch_times())
     torch.cuda.synchronize()
     clk = clocks.stop()
     if dist:
@@ -387,7 +417,22 @@ def run_gpu(args, prob, world, rank, local_rank):
                     + BYTES_COLUMN_PEEL * column_peels + BYTES_DEPOSIT * deposits)
     mean_launch = t_total / args.steps
     peak, peak_kind = peaks()
-    achieved = bytes_launch / mean_launch / 1e9
+    # per kernel: the transport kernel's share of the bytes and the sorted
+    # peel-off walks' share (walked peel-offs it could not hold stay in the
+    # transport kernel; their crossings are apportioned by count)
+    sorted_peels = st["sorted_peels"]
+    walked_peels = deposits - column_peels
+    sorted_cross = peel_cross * sorted_peels / walked_peels if walked_peels else 0
+    bytes_walks = BYTES_PEEL_CROSSING * sorted_cross + BYTES_DEPOSIT * sorted_peels
+    bytes_transport = bytes_launch - bytes_walks
+    part_ms = {k: statistics.mean(p[k] for p in parts) for k in parts[0]}
+    part_bytes = {"column_sums": 0, "transport": bytes_transport, "peel_order": 0, "peel_walks": bytes_walks}
+    names = {"column_sums": "k_columns", "transport": "k_forward_" + ("octree" if prob.grid.kind == "octree"
+                                                                         else "cartesian"),
+             "peel_order": "k_peel_scan_tiles + k_peel_scan_sums + k_peel_scatter", "peel_walks": "k_peel_sorted"}
+    top = max(part_ms, key=part_ms.get)
+    achieved = part_bytes[top] / (part_ms[top] / 1e3) / 1e9
+    launches_step = column_tables(prob) + 1 + (4 if sorted_peels else 0)
     conservation = abs(st["emitted"] - st["escaped"] - st["absorbed"] - st["truncated"]) / st["emitted"]
 
     # end to end through the C ABI with host buffers: upload the grid, set up,
@@ -459,19 +504,25 @@ def run_gpu(args, prob, world, rank, local_rank):
                 "crossings_per_s": world * crossings_step * args.steps / t_total,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak,
-                             "traffic": args.traffic if args.traffic is not None else captured_traffic(packets_step, args.workload),
+                             "traffic": (args.traffic if args.traffic is not None
+                                         else captured_traffic(packets_step, args.workload, names[top])),
                              "peak_source": f"{peak_kind} hbm_gbs",
-                             "algorithmic_bytes_per_launch": int(bytes_launch),
-                             "kernel": "k_forward_" + ("octree" if prob.grid.kind == "octree" else "cartesian"),
-                             "launch_ms": 1e3 * mean_launch},
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "adjoint": adjoint,
+                             "kernel": names[top], "kernel_ms": part_ms[top],
+                             "algorithmic_bytes_per_launch": int(part_bytes[top]),
+                             "parts": {k: {"kernel": names[k], "ms": part_ms[k],
+                                           "algorithmic_bytes": int(part_bytes[k]),
+                                           "GB_per_s": part_bytes[k] / (part_ms[k] / 1e3) / 1e9 if part_ms[k] else 0.0}
+                                       for k in part_ms},
+                             "whole_launch": {"ms": 1e3 * mean_launch, "algorithmic_bytes": int(bytes_launch),
+                                              "GB_per_s": bytes_launch / mean_launch / 1e9}},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_step * args.steps, "adjoint": adjoint,
                 "tuned": {"control_lanes": lanes, "sample": "5 % of the packets, another seed, before the warm-up"},
                 "batch": batch,
                 "clocks": clk,
                 "checks": {"conservation_rel": conservation, "path_crossings": int(path_cross),
                            "walked_peel_crossings": int(peel_cross), "column_peels": int(column_peels),
                            "column_crossings": int(column_cross), "peeloffs": int(deposits),
-                           "events": int(st["events"])}}
+                           "events": int(st["events"]), "sorted_peels": int(sorted_peels)}}
         print(json.dumps(line), flush=True)
 
 

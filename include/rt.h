@@ -180,6 +180,9 @@ typedef struct {
                            free device memory, cannot be had); 1: each walks inside the
                            transport kernel.  The two give the same optical depths, crossings
                            and deposits; only the order of the FP64 image additions differs.   */
+  int32_t time_parts;   /* 1: record CUDA events around the parts of this launch on its stream,
+                           read back by rt_read_launch_times                               */
+  int32_t reserved;
 } rt_launch_opts;
 
 /* Tallies since the last rt_reset_tallies. */
@@ -284,6 +287,15 @@ rt_status rt_read_images(rt_ctx ctx, int32_t instrument_id, double* dst, size_t 
 /* Synchronise the context's work and read the statistics.
  * Errors: RT_ERR_CUDA, RT_ERR_DEVICE_FLAG (stats are still written). */
 rt_status rt_read_stats(rt_ctx ctx, rt_stats* out);
+
+/* Device time in milliseconds of the parts of the last rt_launch_packets made
+ * with opts->time_parts = 1 (CUDA events on its stream; waits for them):
+ * ms[0] column sums, ms[1] the transport kernel, ms[2] the ordering of the
+ * sorted peel-off pass (scan and scatter), ms[3] its walks; parts that did not
+ * run read 0.  n (1..4) is the number of entries written.
+ * Errors: RT_ERR_ARG (null ms, n out of range), RT_ERR_STATE (no timed
+ * launch since the context was created), RT_ERR_CUDA. */
+rt_status rt_read_launch_times(rt_ctx ctx, float* ms, int32_t n);
 
 /* Wait for all work queued on `stream` and report asynchronous errors. */
 rt_status rt_synchronize(rt_ctx ctx, void* stream);

@@ -266,7 +266,7 @@ __device__ __forceinline__ void fetch(const AdjParams& A, ALane& s, unsigned lon
     s.J = s.rec[0].h;
     tape_event(A, s);
   } else {
-    tr::emit(P, s);
+    tr::emit(P, s.pid, s.lam, s.x, s.k);
   }
 }
 

@@ -137,6 +137,11 @@ struct rt_ctx_s {
   bool peel_pending = false;
   unsigned long long peel_last_packets = 0;
   double peel_per_packet = 0.0;    // records per packet seen (0: none yet)
+  // events around the parts of the last launch made with opts.time_parts:
+  // start, after the column sums, after the transport kernel, after the
+  // ordering, after the sorted walks
+  cudaEvent_t part_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool parts_timed = false;
   double emitted = 0.0;  // luminosity emitted since the last reset (host-side sum)
 };
 
@@ -486,6 +491,8 @@ rt_status rt_context_destroy(rt_ctx c) {
   dfree(c->d_peel_tag);
   if (c->h_peel_count) cudaFreeHost(c->h_peel_count);
   if (c->peel_event) cudaEventDestroy(c->peel_event);
+  for (auto& e : c->part_ev)
+    if (e) cudaEventDestroy(e);
   delete c;
   return RT_OK;
 }
@@ -822,6 +829,13 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   p.profile = reinterpret_cast<unsigned long long*>(o.profile);
   p.flags = c->d_flags;
   p.use_columns = c->grid_kind == RT_GRID_CARTESIAN && !o.walk_peels;
+  cudaEvent_t* ev = nullptr;
+  if (o.time_parts) {
+    for (auto& e : c->part_ev)
+      if (!e) RT_CUDA(c, cudaEventCreate(&e));
+    ev = c->part_ev;
+    c->parts_timed = false;
+  }
   if (o.tape) {
     if (c->grid_kind != RT_GRID_CARTESIAN) return fail(c, RT_ERR_ARG, "rt_launch_packets: the tape needs a cartesian grid");
     if (o.max_events > kMaxAdjointEvents)
@@ -843,6 +857,7 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
     p.tape = c->d_tape;
     p.tape_stride = o.max_events + 1;
   }
+  if (ev) RT_CUDA(c, cudaEventRecord(ev[0], s));
   if (p.use_columns) {
     for (int k = 0; k < 6; ++k) {
       if (!c->columns_used[k]) continue;
@@ -852,6 +867,7 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
       if (ec != cudaSuccess) return cuda_fail(c, ec, "column sums");
     }
   }
+  if (ev) RT_CUDA(c, cudaEventRecord(ev[1], s));
   const int walked = o.walk_peels ? (int)c->instr.size() : c->n_walked_frames;
   if (c->grid_kind == RT_GRID_CARTESIAN && !o.tape && !o.inline_peels && walked > 0 &&
       (o.peel_emission || o.peel_scatter)) {
@@ -860,9 +876,10 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   }
   cudaError_t e = launch_forward(p, c->grid_kind, c->num_sms, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "forward launch");
+  if (ev) RT_CUDA(c, cudaEventRecord(ev[2], s));
   if (p.peel) {
     e = launch_peel_pass(p, (unsigned long long)c->instr.size() * (unsigned long long)(c->n_cells + 1),
-                         c->d_peel_tiles, c->d_peel_perm, c->num_sms, s);
+                         c->d_peel_tiles, c->d_peel_perm, c->num_sms, s, ev ? ev[3] : nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "peel-off pass");
     if (!c->peel_pending) {
       RT_CUDA(c, cudaMemcpyAsync(c->h_peel_count, c->d_peel_count, sizeof(unsigned long long),
@@ -871,6 +888,12 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
       c->peel_pending = true;
       c->peel_last_packets = n_total;
     }
+  } else if (ev) {
+    RT_CUDA(c, cudaEventRecord(ev[3], s));
+  }
+  if (ev) {
+    RT_CUDA(c, cudaEventRecord(ev[4], s));
+    c->parts_timed = true;
   }
   if (o.tape) {
     c->tape_valid = true;
@@ -1193,6 +1216,17 @@ rt_status rt_read_stats(rt_ctx c, rt_stats* out) {
   out->column_peels = cn[6]; out->column_crossings = cn[7]; out->sorted_peels = cn[8];
   out->device_flags = flags;
   if (flags) return fail(c, RT_ERR_DEVICE_FLAG, "a kernel bounds check fired (flags 0x%x)", flags);
+  return RT_OK;
+}
+
+rt_status rt_read_launch_times(rt_ctx c, float* ms, int32_t n) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (!ms || n < 1 || n > 4) return fail(c, RT_ERR_ARG, "rt_read_launch_times: need 1..4 entries");
+  if (!c->parts_timed) return fail(c, RT_ERR_STATE, "rt_read_launch_times: no launch with time_parts");
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  RT_CUDA(c, cudaEventSynchronize(c->part_ev[4]));
+  for (int i = 0; i < n; ++i) RT_CUDA(c, cudaEventElapsedTime(&ms[i], c->part_ev[i], c->part_ev[i + 1]));
   return RT_OK;
 }
 

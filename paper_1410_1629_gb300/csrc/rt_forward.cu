@@ -252,12 +252,16 @@ __global__ void __launch_bounds__(256) k_peel_sorted(const FwdParams P, const un
 }  // namespace
 
 cudaError_t launch_peel_pass(const FwdParams& p, unsigned long long n_keys, unsigned* tile_sum, unsigned* perm,
-                             int num_sms, cudaStream_t stream) {
+                             int num_sms, cudaStream_t stream, cudaEvent_t mid) {
   const unsigned long long n_tiles = (n_keys + kScanTile - 1) / kScanTile;
   k_peel_scan_tiles<<<(unsigned)n_tiles, 256, 0, stream>>>(p.peel_hist, n_keys, tile_sum);
   k_peel_scan_sums<<<1, 1024, 0, stream>>>(tile_sum, n_tiles);
   k_peel_scatter<<<(unsigned)num_sms * 8u, 256, 0, stream>>>(p.peel, p.peel_count, p.peel_cap, p.peel_hist, tile_sum,
                                                             perm);
+  if (mid) {
+    const cudaError_t em = cudaEventRecord(mid, stream);
+    if (em != cudaSuccess) return em;
+  }
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel_sorted, 256, 0);
   if (e != cudaSuccess) return e;

@@ -163,8 +163,10 @@ cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t 
 // (rt_forward.cu): scan of p.peel_hist (n_keys entries, tile totals in
 // tile_sum: (n_keys + 4095) / 4096 entries), the permutation that orders the
 // records by key (perm: p.peel_cap entries), and the walks and deposits.
+// `mid`, if not null, is recorded on the stream between the ordering and the
+// walks.
 cudaError_t launch_peel_pass(const FwdParams& p, unsigned long long n_keys, unsigned* tile_sum, unsigned* perm,
-                             int num_sms, cudaStream_t stream);
+                             int num_sms, cudaStream_t stream, cudaEvent_t mid);
 // One forced path of a packet in the adjoint (rt_adjoint.cu): what the
 // backward sweep and the path's depositing walk need.  Adjoint quantities are
 // FP32 in exact power-of-two units: weights in 2^e0 (e0 the exponent of the

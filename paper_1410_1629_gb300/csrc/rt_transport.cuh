@@ -37,9 +37,10 @@ namespace tr {
 
 constexpr int kBlock = 256;
 constexpr float kInv4PiF = 0.0795774715459476679f;
-// Resident blocks per SM the register allocation aims at (3 x 256 threads).
+// Resident blocks per SM the register allocation aims at (4 x 256 threads,
+// 64 registers: the per-event lane state lives in shared memory).
 #ifndef RT_FWD_MIN_BLOCKS
-#define RT_FWD_MIN_BLOCKS 3
+#define RT_FWD_MIN_BLOCKS 4
 #endif
 
 enum Phase : int {
@@ -458,18 +459,46 @@ struct OctGrid {
 };
 
 // ---------------------------------------------------------------- lane state
+// The lane state that only the per-event work touches lives in per-thread
+// slots of shared memory (structure of arrays: the lanes of a warp hit
+// distinct banks), so that the walk's own state fits the registers of four
+// resident blocks per SM.
+__shared__ unsigned long long S_PID[kBlock];
+__shared__ double S_WEIGHT[kBlock];
+__shared__ float3 S_DIR[kBlock];
+__shared__ float2 S_HG[kBlock];
+__shared__ int S_EVENT[kBlock], S_INSTR_Q[kBlock], S_WPHASE[kBlock];
+__shared__ bool S_HAS_CELL[kBlock];
+__shared__ CartGrid::Cell S_CELL_CART[kBlock];
+__shared__ OctGrid::Cell S_CELL_OCT[kBlock];
+
+template <class G>
+__device__ __forceinline__ typename G::Cell& cell_slot();
+template <>
+__device__ __forceinline__ CartGrid::Cell& cell_slot<CartGrid>() { return S_CELL_CART[threadIdx.x]; }
+template <>
+__device__ __forceinline__ OctGrid::Cell& cell_slot<OctGrid>() { return S_CELL_OCT[threadIdx.x]; }
+
 template <class G>
 struct Lane {
-  unsigned long long pid;
-  int lam, event, phase, q;
-  int wphase;           // the walk a kStart lane begins
-  double L;             // weight
+  int lam, phase;
   float kappa;          // extinction per unit density at this wavelength
-  float u_mu, u_phi;    // the event's Henyey-Greenstein uniforms
-  float3 x, k;          // position, direction of travel
-  typename G::Cell cell;  // cell of x (valid when has_cell)
-  bool has_cell;
+  float3 x;             // position
   bool walking;
+  // in shared memory: packet id, event index, instrument of the next
+  // peel-off, the walk a kStart lane begins, weight, direction of travel,
+  // the event's Henyey-Greenstein uniforms, the cell of x (valid when
+  // has_cell)
+  __device__ __forceinline__ unsigned long long& pid() const { return S_PID[threadIdx.x]; }
+  __device__ __forceinline__ int& event() const { return S_EVENT[threadIdx.x]; }
+  __device__ __forceinline__ int& q() const { return S_INSTR_Q[threadIdx.x]; }
+  __device__ __forceinline__ int& wphase() const { return S_WPHASE[threadIdx.x]; }
+  __device__ __forceinline__ double& L() const { return S_WEIGHT[threadIdx.x]; }
+  __device__ __forceinline__ float3& k() const { return S_DIR[threadIdx.x]; }
+  __device__ __forceinline__ float& u_mu() const { return S_HG[threadIdx.x].x; }
+  __device__ __forceinline__ float& u_phi() const { return S_HG[threadIdx.x].y; }
+  __device__ __forceinline__ typename G::Cell& cell() const { return cell_slot<G>(); }
+  __device__ __forceinline__ bool& has_cell() const { return S_HAS_CELL[threadIdx.x]; }
   float3 d, id;         // direction of the current walk and its inverse
   typename G::Walk w;   // the walk: its current cell and exit data
   float rho;            // density of the walk's current cell (loaded one crossing ahead)
@@ -499,11 +528,11 @@ struct LaneTally {
 template <class G>
 __device__ __forceinline__ void trace_row(const FwdParams& P, const Lane<G>& s, int event, int cell, double L,
                                           double tau_path, double tau_star) {
-  if (!P.trace || s.pid != P.trace_packet || s.lam != P.trace_lambda || event >= P.trace_cap) return;
+  if (!P.trace || s.pid() != P.trace_packet || s.lam != P.trace_lambda || event >= P.trace_cap) return;
   rt_trace_row r;
   r.event = event; r.reserved = 0; r.cell = cell;
   r.x[0] = s.x.x; r.x[1] = s.x.y; r.x[2] = s.x.z;
-  r.k[0] = s.k.x; r.k[1] = s.k.y; r.k[2] = s.k.z;
+  r.k[0] = s.k().x; r.k[1] = s.k().y; r.k[2] = s.k().z;
   r.L = L; r.tau_path = tau_path; r.tau_star = tau_star;
   P.trace[event] = r;
 }
@@ -516,7 +545,7 @@ __device__ __forceinline__ void start_walk(const FwdParams& P, Lane<G>& s, float
   s.id = make_float3(inv_or_zero(d.x), inv_or_zero(d.y), inv_or_zero(d.z));
   s.th = 0.0f;
   s.tl = 0.0f;
-  s.walking = G::init(P, s.x, d, s.id, s.has_cell, s.cell, s.w, sc);
+  s.walking = G::init(P, s.x, d, s.id, s.has_cell(), s.cell(), s.w, sc);
   if (s.walking) s.rho = load_density(&P.density[G::cell(s.w)]);
 }
 
@@ -531,8 +560,8 @@ __device__ __forceinline__ float3 instr_dir(const DevInstr& I) { return make_flo
 template <class G>
 __device__ __forceinline__ bool column_peel(const FwdParams& P, Lane<G>& s, const DevInstr& I, LaneTally* bt) {
   CartGrid::Cell c;
-  if (s.has_cell) {
-    c = s.cell;
+  if (s.has_cell()) {
+    c = s.cell();
   } else {
     if (!inside_box(P, s.x)) return false;
     c.ix = min(max(__float2int_rd((s.x.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
@@ -613,8 +642,8 @@ __device__ __forceinline__ void deposit_peel(const FwdParams& P, int q, int lam,
 
 template <class G>
 __device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane<G>& s, bool scattered) {
-  const float phase = scattered ? peel_phase(s.lam, s.k, S_INSTR[s.q]) : 1.0f;
-  deposit_peel(P, s.q, s.lam, s.x, s.L, phase, s.th, s.tl, scattered, s.pid, s.event);
+  const float phase = scattered ? peel_phase(s.lam, s.k(), S_INSTR[s.q()]) : 1.0f;
+  deposit_peel(P, s.q(), s.lam, s.x, s.L(), phase, s.th, s.tl, scattered, s.pid(), s.event());
 }
 
 // Hand the peel-off towards instrument q to the sorted pass: a record in
@@ -631,8 +660,8 @@ __device__ __forceinline__ bool defer_peel(const FwdParams& P, const Lane<G>& s,
   const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
   if (slot >= P.peel_cap) return false;
   unsigned c = (unsigned)P.n_cells;
-  if (s.has_cell) {
-    c = (unsigned)(s.cell.ix + P.nx * (s.cell.iy + P.ny * s.cell.iz));
+  if (s.has_cell()) {
+    c = (unsigned)(s.cell().ix + P.nx * (s.cell().iy + P.ny * s.cell().iz));
   } else if (inside_box(P, s.x)) {
     // the cell the walk will locate x in
     const int ix = min(max(__float2int_rd((s.x.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
@@ -640,14 +669,14 @@ __device__ __forceinline__ bool defer_peel(const FwdParams& P, const Lane<G>& s,
     const int iz = min(max(__float2int_rd((s.x.z - P.lo[2]) * P.inv_d[2]), 0), P.nz - 1);
     c = (unsigned)(ix + P.nx * (iy + P.ny * iz));
   }
-  const unsigned key = (unsigned)s.q * (unsigned)(P.n_cells + 1) + c;
-  const float phase = emission ? 1.0f : peel_phase(s.lam, s.k, I);
-  const unsigned meta = (unsigned)s.lam | (emission ? 0u : 1u << 30) | (s.has_cell ? 1u << 31 : 0u);
-  const long long Lb = __double_as_longlong(s.L);
+  const unsigned key = (unsigned)s.q() * (unsigned)(P.n_cells + 1) + c;
+  const float phase = emission ? 1.0f : peel_phase(s.lam, s.k(), I);
+  const unsigned meta = (unsigned)s.lam | (emission ? 0u : 1u << 30) | (s.has_cell() ? 1u << 31 : 0u);
+  const long long Lb = __double_as_longlong(s.L());
   float4* r = reinterpret_cast<float4*>(&P.peel[slot]);
   r[0] = make_float4(s.x.x, s.x.y, s.x.z, __uint_as_float(key));
   r[1] = make_float4(__int_as_float((int)(unsigned)Lb), __int_as_float((int)(Lb >> 32)), phase, __uint_as_float(meta));
-  if (P.peel_tag) P.peel_tag[slot] = make_ulonglong2(s.pid, (unsigned long long)s.event);
+  if (P.peel_tag) P.peel_tag[slot] = make_ulonglong2(s.pid(), (unsigned long long)s.event());
   atomicAdd(&P.peel_hist[key], 1u);
   return true;
 }
@@ -655,15 +684,14 @@ __device__ __forceinline__ bool defer_peel(const FwdParams& P, const Lane<G>& s,
 // Emission (Sect. 3.4): source component by luminosity (FP64 comparison of
 // the uniform with the cumulative fractions), position from its geometry and
 // an isotropic direction (FP32).
-template <class LaneT>
-__device__ __forceinline__ void emit(const FwdParams& P, LaneT& s) {
-  const uint4 r0 = draw_block(s.pid, s.lam, 0, 0, P.seed, P.model);
-  const uint4 r1 = draw_block(s.pid, s.lam, 0, 1, P.seed, P.model);
+__device__ __forceinline__ void emit(const FwdParams& P, unsigned long long pid, int lam, float3& x_out, float3& k_out) {
+  const uint4 r0 = draw_block(pid, lam, 0, 0, P.seed, P.model);
+  const uint4 r1 = draw_block(pid, lam, 0, 1, P.seed, P.model);
   int src = P.n_sources - 1;
   if (P.n_sources > 1) {
     const double u0 = u01(r0.x);
     for (int i = 0; i < P.n_sources; ++i) {
-      if (u0 < P.src_cum[s.lam * P.n_sources + i]) { src = i; break; }
+      if (u0 < P.src_cum[lam * P.n_sources + i]) { src = i; break; }
     }
   }
   const DevSource& S = P.src[src];
@@ -685,29 +713,29 @@ __device__ __forceinline__ void emit(const FwdParams& P, LaneT& s) {
     sincospif(2.0f * u01f(r0.w), &sp, &cp);
     x.x += r * st * cp; x.y += r * st * sp; x.z += r * ct;
   }
-  s.x = x;
+  x_out = x;
   const float mu = u01f_signed(r1.z);
   const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
   float sp, cp;
   sincospif(2.0f * u01f(r1.w), &sp, &cp);
-  s.k = make_float3(st * cp, st * sp, mu);
+  k_out = make_float3(st * cp, st * sp, mu);
 }
 
 // Ask for walk `phase` from the lane's position along d; walks start in the
 // last stage of a control round, from one place in the code.
 template <class G>
 __device__ __forceinline__ void request_walk(Lane<G>& s, int phase, float3 d) {
-  s.wphase = phase;
+  s.wphase() = phase;
   s.d = d;
   s.phase = kStart;
 }
 
-// The forced path of event s.event: its first walk carries the deposit
+// The forced path of event s.event(): its first walk carries the deposit
 // weight (1 - albedo) L.
 template <class G>
 __device__ __forceinline__ void request_path(Lane<G>& s) {
-  s.aux0 = cut(S_LAM[s.lam].one_minus_albedo * s.L);
-  request_walk(s, kPath1, s.k);
+  s.aux0 = cut(S_LAM[s.lam].one_minus_albedo * s.L());
+  request_walk(s, kPath1, s.k());
 }
 
 // ---- the stages of a control round (each for the lanes in that phase)
@@ -728,7 +756,7 @@ __device__ __forceinline__ float tape_units(double v, int e) {
 template <class G>
 __device__ __forceinline__ int tape_cell(const FwdParams& P, const Lane<G>& s) {
   if constexpr (G::kColumns) {
-    return s.has_cell ? s.cell.ix + P.nx * (s.cell.iy + P.ny * s.cell.iz) : -1;
+    return s.has_cell() ? s.cell().ix + P.nx * (s.cell().iy + P.ny * s.cell().iz) : -1;
   } else {
     return -1;
   }
@@ -741,7 +769,7 @@ __device__ __forceinline__ void tape_end(const FwdParams& P, const Lane<G>& s, i
   r.h = J;
   r.x[0] = s.x.x; r.x[1] = s.x.y; r.x[2] = s.x.z;
   r.cell = tape_cell(P, s);
-  r.L = tape_units(s.L, s.eL);
+  r.L = tape_units(s.L(), s.eL);
 }
 
 // A new packet (index w of the launch): wavelength, weight, emission.
@@ -752,13 +780,13 @@ __device__ __forceinline__ void fetch(const FwdParams& P, Lane<G>& s, unsigned l
   while (lam > 0 && (unsigned long long)lam * P.n_per_lambda > w) --lam;
   while (lam + 1 < P.n_lambda && (unsigned long long)(lam + 1) * P.n_per_lambda <= w) ++lam;
   s.lam = lam;
-  s.pid = P.first_id + (w - (unsigned long long)lam * P.n_per_lambda);
+  s.pid() = P.first_id + (w - (unsigned long long)lam * P.n_per_lambda);
   const double L0 = P.L0[lam];
   s.kappa = S_LAM[lam].kappa;
-  s.L = L0;
-  s.event = 0;
-  s.has_cell = false;
-  emit(P, s);
+  s.L() = L0;
+  s.event() = 0;
+  s.has_cell() = false;
+  emit(P, s.pid(), s.lam, s.x, s.k());
   bt->packets += 1u;
   trace_row(P, s, 0, -1, L0, 0.0, 0.0);
   if (kTape) {
@@ -766,7 +794,7 @@ __device__ __forceinline__ void fetch(const FwdParams& P, Lane<G>& s, unsigned l
     const int be = (int)((__double_as_longlong(L0) >> 52) & 0x7ff);
     s.eL = be == 0 ? 0 : be - 1022;  // L0 = m 2^eL, m in [1/2, 1)
   }
-  s.q = 0;
+  s.q() = 0;
   s.phase = kPeelScan;
 }
 
@@ -776,32 +804,32 @@ template <class G, bool kTape>
 __device__ __forceinline__ void finish_path1(const FwdParams& P, Lane<G>& s, LaneTally* bt) {
   const double tau = widen(s.th) + widen(s.tl);
   if (!(tau > 0.0)) {
-    trace_row(P, s, s.event, -1, s.L, 0.0, 0.0);
-    bt->escaped += s.L;
-    if (kTape) tape_end(P, s, s.event - 1);
+    trace_row(P, s, s.event(), -1, s.L(), 0.0, 0.0);
+    bt->escaped += s.L();
+    if (kTape) tape_end(P, s, s.event() - 1);
     s.phase = kFetch;
     return;
   }
   const double one_minus_E = -expm1(-tau);
   const double E = 1.0 - one_minus_E;
-  bt->escaped += s.L * E;
-  bt->absorbed += S_LAM[s.lam].one_minus_albedo * s.L * one_minus_E;
-  const uint4 r = draw_block(s.pid, s.lam, s.event, 0, P.seed, P.model);
+  bt->escaped += s.L() * E;
+  bt->absorbed += S_LAM[s.lam].one_minus_albedo * s.L() * one_minus_E;
+  const uint4 r = draw_block(s.pid(), s.lam, s.event(), 0, P.seed, P.model);
   const double tau_star = -log1p(-u01(r.x) * one_minus_E);
-  s.u_mu = u01f(r.y);
-  s.u_phi = u01f(r.z);
+  s.u_mu() = u01f(r.y);
+  s.u_phi() = u01f(r.z);
   split_pair(tau_star, s.aux0, s.aux1);
   if (kTape) {
     // the record's first two sectors, whole, with 16-byte stores
-    float4* t = reinterpret_cast<float4*>(&s.rec[s.event]);
-    t[0] = make_float4(s.x.x, s.x.y, s.x.z, s.k.x);
-    t[1] = make_float4(s.k.y, s.k.z, __int_as_float(tape_cell(P, s)), tape_units(s.L, s.eL));
+    float4* t = reinterpret_cast<float4*>(&s.rec[s.event()]);
+    t[0] = make_float4(s.x.x, s.x.y, s.x.z, s.k().x);
+    t[1] = make_float4(s.k().y, s.k().z, __int_as_float(tape_cell(P, s)), tape_units(s.L(), s.eL));
     t[2] = make_float4((float)one_minus_E, (float)E, u01f(r.x), s.g.x);
     t[3] = make_float4(s.g.y, s.g.z, 0.0f, 0.0f);
     s.h = -1;
   }
-  s.L = S_LAM[s.lam].albedo * s.L * one_minus_E;  // weight after the scattering
-  request_walk(s, kPath2, s.k);
+  s.L() = S_LAM[s.lam].albedo * s.L() * one_minus_E;  // weight after the scattering
+  request_walk(s, kPath2, s.k());
 }
 
 // Path 2 ended in the interaction cell (aux0 holds s*): move the packet,
@@ -810,23 +838,23 @@ template <class G, bool kTape>
 __device__ __forceinline__ void finish_path2(const FwdParams& P, Lane<G>& s, LaneTally* bt) {
   if (kTape) {
     // the record's third sector, whole
-    float4* t = reinterpret_cast<float4*>(&s.rec[s.event]);
+    float4* t = reinterpret_cast<float4*>(&s.rec[s.event()]);
     t[4] = make_float4(__int_as_float(s.h), __int_as_float(s.axis_in), __int_as_float(G::cell(s.w)), s.kr_h);
     t[5] = make_float4(s.rem, s.g.x, s.g.y, s.g.z);
   }
   const float s_star = s.aux0;
-  float3 x = make_float3(fmaf(s_star, s.k.x, s.x.x), fmaf(s_star, s.k.y, s.x.y), fmaf(s_star, s.k.z, s.x.z));
-  s.cell = G::carried(s.w);
-  G::clamp(P, s.cell, x);
+  float3 x = make_float3(fmaf(s_star, s.k().x, s.x.x), fmaf(s_star, s.k().y, s.x.y), fmaf(s_star, s.k().z, s.x.z));
+  s.cell() = G::carried(s.w);
+  G::clamp(P, s.cell(), x);
   s.x = x;
-  s.has_cell = true;
+  s.has_cell() = true;
   bt->events += 1u;
-  trace_row(P, s, s.event, G::cell(s.w), s.L, 0.0, 0.0);
-  s.q = 0;
+  trace_row(P, s, s.event(), G::cell(s.w), s.L(), 0.0, 0.0);
+  s.q() = 0;
   s.phase = kPeelScan;
 }
 
-// The peel-off towards instrument s.q, or the end of the event's peel-offs:
+// The peel-off towards instrument s.q(), or the end of the event's peel-offs:
 // along a frame that looks along a grid axis the optical depth comes from
 // the column sums at once (the lane then waits for the deposit stage);
 // otherwise a record for the sorted pass, or (no pass, or its buffer full)
@@ -834,9 +862,9 @@ __device__ __forceinline__ void finish_path2(const FwdParams& P, Lane<G>& s, Lan
 // the scattering (kAfter).
 template <class G>
 __device__ __forceinline__ void peel_scan(const FwdParams& P, Lane<G>& s, LaneTally* bt) {
-  const bool emission = s.event == 0;
-  if ((emission ? P.peel_emission : P.peel_scatter) && s.q < P.n_instr) {
-    const DevInstr& I = S_INSTR[s.q];
+  const bool emission = s.event() == 0;
+  if ((emission ? P.peel_emission : P.peel_scatter) && s.q() < P.n_instr) {
+    const DevInstr& I = S_INSTR[s.q()];
     const int phase = emission ? kPeelEmit : kPeelScat;
     if constexpr (G::kColumns) {
       if (P.use_columns && I.column && column_peel(P, s, I, bt)) {
@@ -846,7 +874,7 @@ __device__ __forceinline__ void peel_scan(const FwdParams& P, Lane<G>& s, LaneTa
       if (P.peel && defer_peel(P, s, I, emission)) {
         // walked and deposited by the sorted pass; on to the next instrument
         bt->peeloffs += 1u;
-        s.q += 1;
+        s.q() += 1;
         return;
       }
     }
@@ -854,7 +882,7 @@ __device__ __forceinline__ void peel_scan(const FwdParams& P, Lane<G>& s, LaneTa
     return;
   }
   if (emission) {
-    s.event = 1;
+    s.event() = 1;
     request_path(s);
   } else {
     s.phase = kAfter;
@@ -865,17 +893,17 @@ __device__ __forceinline__ void peel_scan(const FwdParams& P, Lane<G>& s, LaneTa
 // next forced path.
 template <class G, bool kTape>
 __device__ __forceinline__ void after_scattering(const FwdParams& P, Lane<G>& s, LaneTally* bt) {
-  const float mu = hg_sample(S_LAM[s.lam].g, s.u_mu);
+  const float mu = hg_sample(S_LAM[s.lam].g, s.u_mu());
   float sp, cp;
-  sincospif(2.0f * s.u_phi, &sp, &cp);
-  s.k = rotate_dir(s.k, mu, sp, cp);
-  if ((P.weight_cut && s.L < P.L_cut[s.lam]) || s.event >= P.max_events) {
-    bt->truncated += s.L;
-    if (kTape) tape_end(P, s, s.event);
+  sincospif(2.0f * s.u_phi(), &sp, &cp);
+  s.k() = rotate_dir(s.k(), mu, sp, cp);
+  if ((P.weight_cut && s.L() < P.L_cut[s.lam]) || s.event() >= P.max_events) {
+    bt->truncated += s.L();
+    if (kTape) tape_end(P, s, s.event());
     s.phase = kFetch;
     return;
   }
-  s.event += 1;
+  s.event() += 1;
   request_path(s);
 }
 
@@ -901,7 +929,7 @@ __device__ __forceinline__ void control_round(const FwdParams& P, Lane<G>& s, La
       if (ready) {
         peel_deposit(P, s, s.phase == kPeelScat);
         bt->peeloffs += 1u;
-        s.q += 1;
+        s.q() += 1;
         s.phase = kPeelScan;
       }
       if (s.phase == kPeelScan) peel_scan(P, s, bt);
@@ -918,7 +946,7 @@ __device__ __forceinline__ void control_round(const FwdParams& P, Lane<G>& s, La
     if (wants) fetch<G, kTape>(P, s, base + __popc(fetchers & lt_mask), bt);
   }
   if (s.phase == kStart) {
-    s.phase = s.wphase;
+    s.phase = s.wphase();
     if (kTape) {
       s.g = make_float3(0.0f, 0.0f, 0.0f);
       s.axis_in = -1;
@@ -1030,16 +1058,21 @@ __device__ __forceinline__ void forward_body(const FwdParams& P) {
   unsigned n_path = 0, n_peel = 0;
   // optional execution counters (warp leader only)
   const bool prof = P.profile != nullptr && lane == 0;
-  unsigned long long c_iter = 0, c_walk_lanes = 0, c_rounds = 0, c_round_lanes = 0, cyc_ctl = 0, cyc_walk = 0;
+  // iterations, walking lanes, rounds, lanes served, cycles in control, in
+  // the walk: per warp in shared memory (no registers held across the loop)
+  __shared__ unsigned long long prof_c[kBlock / 32][6];
+  unsigned long long* pc = prof_c[threadIdx.x >> 5];
+  if (prof)
+    for (int i = 0; i < 6; ++i) pc[i] = 0ull;
   while (true) {
     const bool idle = !s.walking && s.phase != kExit;
     const unsigned need = __ballot_sync(0xffffffffu, idle);
     const unsigned walkers = __ballot_sync(0xffffffffu, s.walking);
     if (need == 0u && walkers == 0u) break;
     long long t0 = 0;
-    if (prof) { ++c_iter; t0 = clock64(); }
+    if (prof) { pc[0] += 1ull; t0 = clock64(); }
     if (walkers == 0u || __popc(need) >= P.control_min) {
-      if (prof) { ++c_rounds; c_round_lanes += __popc(need); }
+      if (prof) { pc[2] += 1ull; pc[3] += __popc(need); }
       control_round<G, kTape>(P, s, bt, sc, lane, lt_mask);
       if ((n_path | n_peel) & 0xC0000000u) {  // keep the 32-bit lane counters far from overflow
         bt->crossings += (unsigned long long)n_path + n_peel;
@@ -1048,18 +1081,13 @@ __device__ __forceinline__ void forward_body(const FwdParams& P) {
       }
     }
     long long t1 = 0;
-    if (prof) { t1 = clock64(); cyc_ctl += t1 - t0; }
+    if (prof) { t1 = clock64(); pc[4] += t1 - t0; }
     const unsigned stepping = __ballot_sync(0xffffffffu, s.walking);
     if (s.walking) walk_step<G, kTape>(P, s, n_path, n_peel, sc);
-    if (prof) { c_walk_lanes += __popc(stepping); cyc_walk += clock64() - t1; }
+    if (prof) { pc[1] += __popc(stepping); pc[5] += clock64() - t1; }
   }
   if (prof) {
-    atomicAdd(&P.profile[0], c_iter);
-    atomicAdd(&P.profile[1], c_walk_lanes);
-    atomicAdd(&P.profile[2], c_rounds);
-    atomicAdd(&P.profile[3], c_round_lanes);
-    atomicAdd(&P.profile[4], cyc_ctl);
-    atomicAdd(&P.profile[5], cyc_walk);
+    for (int i = 0; i < 6; ++i) atomicAdd(&P.profile[i], pc[i]);
   }
   bt->crossings += (unsigned long long)n_path + n_peel;
   bt->path_crossings += n_path;

@@ -80,7 +80,8 @@ class rt_launch_opts(ctypes.Structure):
                 ("records_capacity", ctypes.c_int64), ("record_stride", ctypes.c_uint64),
                 ("trace", ctypes.c_void_p), ("trace_capacity", ctypes.c_int64), ("trace_packet", ctypes.c_uint64),
                 ("trace_lambda", ctypes.c_int32), ("control_lanes", ctypes.c_int32),
-                ("profile", ctypes.c_void_p), ("tape", ctypes.c_int32), ("inline_peels", ctypes.c_int32)]
+                ("profile", ctypes.c_void_p), ("tape", ctypes.c_int32), ("inline_peels", ctypes.c_int32),
+                ("time_parts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class rt_stats(ctypes.Structure):
@@ -127,6 +128,7 @@ SIGNATURES = {
                                         ctypes.c_int32, ctypes.c_void_p]),
     "rt_read_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rt_stats)]),
     "rt_synchronize": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "rt_read_launch_times": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "rt_update_density": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "rt_adjoint": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(rt_launch_opts),
@@ -290,6 +292,16 @@ def rt_read_stats(ctx) -> rt_stats:
     s = rt_stats()
     _check(ctx, lib().rt_read_stats(ctx, ctypes.byref(s)))
     return s
+
+
+LAUNCH_PARTS = ("column_sums", "transport", "peel_order", "peel_walks")
+
+
+def rt_read_launch_times(ctx) -> dict:
+    """Milliseconds per part of the last launch made with time_parts=1."""
+    ms = (ctypes.c_float * 4)()
+    _check(ctx, lib().rt_read_launch_times(ctx, ms, 4))
+    return dict(zip(LAUNCH_PARTS, (float(v) for v in ms)))
 
 
 def rt_synchronize(ctx, stream=None):
@@ -631,3 +643,7 @@ class Simulation:
 
     def stats(self) -> dict:
         return rt_read_stats(self.ctx).as_dict()
+
+    def launch_times(self) -> dict:
+        """Device milliseconds of the parts of the last launch with time_parts=1."""
+        return rt_read_launch_times(self.ctx)
