@@ -9,8 +9,11 @@ __global__ void __launch_bounds__(tr::kBlock, RT_FWD_MIN_BLOCKS) k_forward_carte
   tr::forward_body<tr::CartGrid>(P);
 }
 // The same launch recording the adjoint tape (P.tape): the tape's lane state
-// needs the registers of two resident blocks per SM.
-__global__ void __launch_bounds__(tr::kBlock, 2) k_forward_cartesian_tape(const FwdParams P) {
+// needs more registers (RT_TAPE_MIN_BLOCKS resident blocks per SM).
+#ifndef RT_TAPE_MIN_BLOCKS
+#define RT_TAPE_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(tr::kBlock, RT_TAPE_MIN_BLOCKS) k_forward_cartesian_tape(const FwdParams P) {
   tr::forward_body<tr::CartGrid, true>(P);
 }
 }  // namespace

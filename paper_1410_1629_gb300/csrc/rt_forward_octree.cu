@@ -4,10 +4,16 @@
 // shared memory).
 #include "rt_transport.cuh"
 
+// Resident blocks per SM the register allocation aims at (the per-lane
+// ancestor stacks take 67 KB of shared memory per block).
+#ifndef RT_OCT_MIN_BLOCKS
+#define RT_OCT_MIN_BLOCKS 3
+#endif
+
 namespace rtk {
 
 namespace {
-__global__ void __launch_bounds__(tr::kBlock, 2) k_forward_octree(const FwdParams P) {
+__global__ void __launch_bounds__(tr::kBlock, RT_OCT_MIN_BLOCKS) k_forward_octree(const FwdParams P) {
   tr::forward_body<tr::OctGrid>(P);
 }
 }  // namespace
