@@ -39,16 +39,33 @@ struct Tally {
 __shared__ Geo S_GEO[kBatchBlock];
 __shared__ Tally S_TALLY[kBatchBlock];
 
+// The lane state that only the per-event work touches sits in the transport
+// kernels' per-thread shared-memory slots, so that the walk's state fits the
+// registers of four resident blocks per SM.
+#ifndef RT_BATCH_MIN_BLOCKS
+#define RT_BATCH_MIN_BLOCKS 4
+#endif
+static_assert(kBatchBlock == tr::kBlock, "per-thread slots are sized for the transport block");
+
 struct BLane {
-  unsigned long long pid;
-  int m, event, phase;
-  int q, wphase;      // peel-off done (1) or not (0) for this event; the walk a kStart lane begins
-  double L;
+  int m, phase;
   float kappa;
-  float u_mu, u_phi;
-  float3 x, k;
-  CartGrid::Cell cell;
-  bool has_cell, walking;
+  float3 x;
+  bool walking;
+  // in shared memory: packet id, event index, peel-off done (1) or not (0)
+  // for this event, the walk a kStart lane begins, weight, direction of
+  // travel, the event's Henyey-Greenstein uniforms, the cell of x (valid when
+  // has_cell)
+  __device__ __forceinline__ unsigned long long& pid() const { return tr::S_PID[threadIdx.x]; }
+  __device__ __forceinline__ int& event() const { return tr::S_EVENT[threadIdx.x]; }
+  __device__ __forceinline__ int& q() const { return tr::S_INSTR_Q[threadIdx.x]; }
+  __device__ __forceinline__ int& wphase() const { return tr::S_WPHASE[threadIdx.x]; }
+  __device__ __forceinline__ double& L() const { return tr::S_WEIGHT[threadIdx.x]; }
+  __device__ __forceinline__ float3& k() const { return tr::S_DIR[threadIdx.x]; }
+  __device__ __forceinline__ float& u_mu() const { return tr::S_HG[threadIdx.x].x; }
+  __device__ __forceinline__ float& u_phi() const { return tr::S_HG[threadIdx.x].y; }
+  __device__ __forceinline__ CartGrid::Cell& cell() const { return tr::S_CELL_CART[threadIdx.x]; }
+  __device__ __forceinline__ bool& has_cell() const { return tr::S_HAS_CELL[threadIdx.x]; }
   float3 d, id;
   CartGrid::Walk w;
   float rho;
@@ -73,7 +90,7 @@ __device__ __forceinline__ void start_walk(BLane& s, const Geo& G, float3 d) {
   s.th = 0.0f;
   s.tl = 0.0f;
   CartGrid::Scratch sc;
-  s.walking = CartGrid::init(G, s.x, d, s.id, s.has_cell, s.cell, s.w, sc);
+  s.walking = CartGrid::init(G, s.x, d, s.id, s.has_cell(), s.cell(), s.w, sc);
   if (s.walking) s.rho = tr::load_density(&s.dens[s.w.cell]);
 }
 
@@ -83,10 +100,10 @@ __device__ __forceinline__ float3 kobs(const DevInstr& I) { return make_float3(I
 __device__ __forceinline__ void deposit(const DevModel& M, const BLane& s, bool scattered) {
   const DevInstr& I = M.instr;
   float phase = 1.0f;
-  if (scattered) phase = hg_phase(M.g, s.k.x * I.kobs[0] + s.k.y * I.kobs[1] + s.k.z * I.kobs[2]);
+  if (scattered) phase = hg_phase(M.g, s.k().x * I.kobs[0] + s.k().y * I.kobs[1] + s.k().z * I.kobs[2]);
   const float tau = s.th;
-  const double value = tau < 80.0f ? s.L * tr::widen(tr::kInv4PiF * phase * expf(-tau) * (1.0f - s.tl))
-                                   : s.L * kInv4PiD * (double)phase * exp(-((double)tau + (double)s.tl));
+  const double value = tau < 80.0f ? s.L() * tr::widen(tr::kInv4PiF * phase * expf(-tau) * (1.0f - s.tl))
+                                   : s.L() * kInv4PiD * (double)phase * exp(-((double)tau + (double)s.tl));
   const float fx = (s.x.x * I.ex[0] + s.x.y * I.ex[1] + s.x.z * I.ex[2] + I.off_x) * I.sx;
   const float fy = (s.x.x * I.ey[0] + s.x.y * I.ey[1] + s.x.z * I.ey[2] + I.off_y) * I.sy;
   if (!I.bilinear) {
@@ -115,8 +132,8 @@ __device__ __forceinline__ void deposit(const DevModel& M, const BLane& s, bool 
 __device__ __forceinline__ bool column_peel(const DevInstr& I, BLane& s, const Geo& G, Tally& T,
                                             unsigned& n_cross) {
   CartGrid::Cell c;
-  if (s.has_cell) {
-    c = s.cell;
+  if (s.has_cell()) {
+    c = s.cell();
   } else {
     if (!inside_box(G, s.x)) return false;
     c.ix = min(max(__float2int_rd((s.x.x - G.lo[0]) * G.inv_d[0]), 0), G.nx - 1);
@@ -144,7 +161,7 @@ __device__ __forceinline__ bool column_peel(const DevInstr& I, BLane& s, const G
 // Ask for walk `phase` from the lane's position along d (started in the last
 // stage of a control round, from one place in the code).
 __device__ __forceinline__ void request_walk(BLane& s, int phase, float3 d) {
-  s.wphase = phase;
+  s.wphase() = phase;
   s.d = d;
   s.phase = tr::kStart;
 }
@@ -167,12 +184,12 @@ __device__ __forceinline__ void begin(const BatchParams& P, BLane& s, Geo& G, Ta
     G.lo[a] = M.lo[a]; G.hi[a] = M.hi[a]; G.d[a] = M.d[a]; G.inv_d[a] = M.inv_d[a];
   }
   s.m = m;
-  s.pid = pid;
+  s.pid() = pid;
   s.dens = P.density + M.density;
   s.kappa = M.kappa;
-  s.L = M.L0;
-  s.event = 0;
-  s.has_cell = false;
+  s.L() = M.L0;
+  s.event() = 0;
+  s.has_cell() = false;
   // one point source: the position draws of block 0 are not needed
   const uint4 r1 = draw_block(pid, 0, 0, 1, P.seed, (unsigned)m);
   s.x = make_float3(M.src[0], M.src[1], M.src[2]);
@@ -180,8 +197,8 @@ __device__ __forceinline__ void begin(const BatchParams& P, BLane& s, Geo& G, Ta
   const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
   float sp, cp;
   sincospif(2.0f * tr::u01f(r1.w), &sp, &cp);
-  s.k = make_float3(st * cp, st * sp, mu);
-  s.q = 0;
+  s.k() = make_float3(st * cp, st * sp, mu);
+  s.q() = 0;
   s.phase = tr::kPeelScan;
 }
 
@@ -189,41 +206,41 @@ __device__ __forceinline__ void finish_path1(const BatchParams& P, BLane& s, Tal
   const DevModel& M = P.models[s.m];
   const double tau = tr::widen(s.th) + tr::widen(s.tl);
   if (!(tau > 0.0)) {
-    T.escaped += s.L;
+    T.escaped += s.L();
     s.phase = tr::kFetch;
     return;
   }
   const double albedo = M.albedo;
   const double one_minus_E = -expm1(-tau);
   const double E = 1.0 - one_minus_E;
-  T.escaped += s.L * E;
-  T.absorbed += (1.0 - albedo) * s.L * one_minus_E;
-  const uint4 r = draw_block(s.pid, 0, s.event, 0, P.seed, (unsigned)s.m);
+  T.escaped += s.L() * E;
+  T.absorbed += (1.0 - albedo) * s.L() * one_minus_E;
+  const uint4 r = draw_block(s.pid(), 0, s.event(), 0, P.seed, (unsigned)s.m);
   const double tau_star = -log1p(-u01(r.x) * one_minus_E);
-  s.u_mu = tr::u01f(r.y);
-  s.u_phi = tr::u01f(r.z);
+  s.u_mu() = tr::u01f(r.y);
+  s.u_phi() = tr::u01f(r.z);
   tr::split_pair(tau_star, s.aux0, s.aux1);
-  s.L = albedo * s.L * one_minus_E;
-  request_walk(s, tr::kPath2, s.k);
+  s.L() = albedo * s.L() * one_minus_E;
+  request_walk(s, tr::kPath2, s.k());
 }
 
 __device__ __forceinline__ void finish_path2(const Geo& G, BLane& s, unsigned& n_events) {
   const float s_star = s.aux0;
-  float3 x = make_float3(fmaf(s_star, s.k.x, s.x.x), fmaf(s_star, s.k.y, s.x.y), fmaf(s_star, s.k.z, s.x.z));
-  s.cell = CartGrid::carried(s.w);
-  CartGrid::clamp(G, s.cell, x);
+  float3 x = make_float3(fmaf(s_star, s.k().x, s.x.x), fmaf(s_star, s.k().y, s.x.y), fmaf(s_star, s.k().z, s.x.z));
+  s.cell() = CartGrid::carried(s.w);
+  CartGrid::clamp(G, s.cell(), x);
   s.x = x;
-  s.has_cell = true;
+  s.has_cell() = true;
   n_events += 1u;
-  s.q = 0;
+  s.q() = 0;
   s.phase = tr::kPeelScan;
 }
 
 // The model's one peel-off of this event, or what follows it.
 __device__ __forceinline__ void peel_scan(const BatchParams& P, BLane& s, const Geo& G, Tally& T,
                                           unsigned& n_cross) {
-  const bool emission = s.event == 0;
-  if ((emission ? P.peel_emission : P.peel_scatter) && s.q == 0) {
+  const bool emission = s.event() == 0;
+  if ((emission ? P.peel_emission : P.peel_scatter) && s.q() == 0) {
     const DevInstr& I = P.models[s.m].instr;
     const int phase = emission ? tr::kPeelEmit : tr::kPeelScat;
     if (P.use_columns && I.column && column_peel(I, s, G, T, n_cross)) {
@@ -234,8 +251,8 @@ __device__ __forceinline__ void peel_scan(const BatchParams& P, BLane& s, const 
     return;
   }
   if (emission) {
-    s.event = 1;
-    request_walk(s, tr::kPath1, s.k);
+    s.event() = 1;
+    request_walk(s, tr::kPath1, s.k());
   } else {
     s.phase = tr::kAfter;
   }
@@ -243,17 +260,17 @@ __device__ __forceinline__ void peel_scan(const BatchParams& P, BLane& s, const 
 
 __device__ __forceinline__ void after_scattering(const BatchParams& P, BLane& s, Tally& T) {
   const DevModel& M = P.models[s.m];
-  const float mu = hg_sample(M.g, s.u_mu);
+  const float mu = hg_sample(M.g, s.u_mu());
   float sp, cp;
-  sincospif(2.0f * s.u_phi, &sp, &cp);
-  s.k = rotate_dir(s.k, mu, sp, cp);
-  if ((P.weight_cut && s.L < P.w_min * M.L0) || s.event >= P.max_events) {
-    T.truncated += s.L;
+  sincospif(2.0f * s.u_phi(), &sp, &cp);
+  s.k() = rotate_dir(s.k(), mu, sp, cp);
+  if ((P.weight_cut && s.L() < P.w_min * M.L0) || s.event() >= P.max_events) {
+    T.truncated += s.L();
     s.phase = tr::kFetch;
     return;
   }
-  s.event += 1;
-  request_walk(s, tr::kPath1, s.k);
+  s.event() += 1;
+  request_walk(s, tr::kPath1, s.k());
 }
 
 // One cell crossing (the forward kernel's step without the absorption field).
@@ -291,7 +308,7 @@ __device__ __forceinline__ void step(const BatchParams& P, BLane& s, const Geo& 
   }
 }
 
-__global__ void __launch_bounds__(kBatchBlock, 3) k_batch(const BatchParams P) {
+__global__ void __launch_bounds__(kBatchBlock, RT_BATCH_MIN_BLOCKS) k_batch(const BatchParams P) {
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
   Geo& G = S_GEO[threadIdx.x];
@@ -329,7 +346,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch(const BatchParams P) {
           if (ready) {
             deposit(P.models[s.m], s, s.phase == tr::kPeelScat);
             n_peel += 1u;
-            s.q = 1;
+            s.q() = 1;
             s.phase = tr::kPeelScan;
           }
           if (s.phase == tr::kPeelScan) peel_scan(P, s, G, T, n_cross);
@@ -377,7 +394,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch(const BatchParams P) {
         }
       }
       if (s.phase == tr::kStart) {
-        s.phase = s.wphase;
+        s.phase = s.wphase();
         start_walk(s, G, s.d);
       }
       if (n_cross & 0xC0000000u) {
