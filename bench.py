@@ -36,13 +36,13 @@ L2_FLUSH_BYTES = 256 << 20
 BYTES_PATH_CROSSING, BYTES_PEEL_CROSSING, BYTES_DEPOSIT = 20, 4, 16
 # a peel-off along a grid axis reads 4 B of density and 4 B of column sum
 BYTES_COLUMN_PEEL = 8
-# DRAM bytes (read + write) per packet of the forward kernel, from an ncu
+# DRAM bytes (read + write) per packet of the transport kernel, from an ncu
 # capture of one 2e6-packet launch of this workload (dram__bytes_read.sum
-# 50.474 GB + dram__bytes_write.sum 18.314 GB), valid only for the kernel
+# 50.829 GB + dram__bytes_write.sum 21.036 GB), valid only for the kernel
 # sources whose hash is given; the per-launch traffic is this figure times
 # the packets.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "51edaf64edb17c52", "kernel": "k_forward_cartesian",
-                   "bytes_per_packet": (50473811968 + 18314334208) / 2e6}
+TRAFFIC_CAPTURE = {"sources_sha256_16": "66f6cb07abf451a4", "kernel": "k_forward_cartesian",
+                   "bytes_per_packet": (50828612352 + 21036353792) / 2e6}
 KERNEL_SOURCES = ["paper_1410_1629_gb300/csrc/rt_forward.cu", "paper_1410_1629_gb300/csrc/rt_device.cuh",
                   "paper_1410_1629_gb300/csrc/rt_internal.h", "paper_1410_1629_gb300/csrc/rt_transport.cuh",
                   "paper_1410_1629_gb300/build.py"]

@@ -141,35 +141,12 @@ __global__ void __launch_bounds__(256) k_peel_sorted(const FwdParams P, const un
     const double L = __hiloint2double(__float_as_int(b.y), __float_as_int(b.x));
     const float3 x = make_float3(a.x, a.y, a.z);
     const DevInstr& I = tr::S_INSTR[q];
-    const float3 d = tr::instr_dir(I);
-    const float3 id = make_float3(tr::inv_or_zero(d.x), tr::inv_or_zero(d.y), tr::inv_or_zero(d.z));
     tr::CartGrid::Cell cell;
     cell.ix = (int)(c % (unsigned)P.nx);
     cell.iy = (int)((c / (unsigned)P.nx) % (unsigned)P.ny);
     cell.iz = (int)(c / ((unsigned)P.nx * (unsigned)P.ny));
-    tr::CartGrid::Walk w;
-    tr::CartGrid::Scratch sc;
-    float th = 0.0f, tl = 0.0f;
-    if (tr::CartGrid::init(P, x, d, id, known, cell, w, sc)) {
-      const float kappa = tr::S_LAM[lam].kappa;
-      float rho = tr::load_density(&P.density[w.cell]);
-      while (true) {
-        int axis;
-        const float te = tr::CartGrid::exit(w, x, id, axis);
-        const float texit = fmaxf(te, w.t);
-        const float ds = texit - w.t;
-        const float kr = kappa * rho;
-        const float dt = kr * ds;
-        float nh, e;
-        tr::two_sum(th, dt, nh, e);
-        tl = tl + e;
-        th = nh;
-        ++crossings;
-        w.t = texit;
-        if (!tr::CartGrid::advance(P, x, d, id, axis, w, sc)) break;
-        rho = tr::load_density(&P.density[w.cell]);
-      }
-    }
+    float th, tl;
+    crossings += tr::ray_tau(P, x, tr::instr_dir(I), known, cell, tr::S_LAM[lam].kappa, th, tl);
     const ulonglong2 tag = P.peel_tag ? P.peel_tag[i] : make_ulonglong2(0ull, 0ull);
     tr::deposit_peel(P, q, lam, x, L, b.z, th, tl, (meta >> 30) & 1u, tag.x, (int)tag.y);
   }

@@ -555,35 +555,77 @@ __device__ __forceinline__ float3 instr_dir(const DevInstr& I) { return make_flo
 // optical depth to the boundary is kappa (rho_c ds_0 + column[c]), with ds_0
 // the distance to the face of the current cell that the ray leaves (the first
 // segment of the walk) and column[c] the density integral of the cells beyond
-// it on the same grid line.  The walk's crossings are counted all the same.
-// False when the position is outside the grid (the walk then finds the entry).
-template <class G>
-__device__ __forceinline__ bool column_peel(const FwdParams& P, Lane<G>& s, const DevInstr& I, LaneTally* bt) {
+// it on the same grid line.  The walk's crossings (n_cross) are counted all
+// the same.  known: x lies in cell cc.  False when the position is outside the
+// grid (the walk then finds the entry).
+__device__ __forceinline__ bool column_tau(const FwdParams& P, float3 x, bool known, const CartGrid::Cell& cc,
+                                           const DevInstr& I, float kappa, float& th,
+                                           unsigned long long& n_cross) {
   CartGrid::Cell c;
-  if (s.has_cell()) {
-    c = s.cell();
+  if (known) {
+    c = cc;
   } else {
-    if (!inside_box(P, s.x)) return false;
-    c.ix = min(max(__float2int_rd((s.x.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
-    c.iy = min(max(__float2int_rd((s.x.y - P.lo[1]) * P.inv_d[1]), 0), P.ny - 1);
-    c.iz = min(max(__float2int_rd((s.x.z - P.lo[2]) * P.inv_d[2]), 0), P.nz - 1);
+    if (!inside_box(P, x)) return false;
+    c.ix = min(max(__float2int_rd((x.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
+    c.iy = min(max(__float2int_rd((x.y - P.lo[1]) * P.inv_d[1]), 0), P.ny - 1);
+    c.iz = min(max(__float2int_rd((x.z - P.lo[2]) * P.inv_d[2]), 0), P.nz - 1);
   }
   const int a = I.axis;
   const bool up = I.dir > 0;
   const int i = a == 0 ? c.ix : (a == 1 ? c.iy : c.iz);
   const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
-  const float xa = a == 0 ? s.x.x : (a == 1 ? s.x.y : s.x.z);
+  const float xa = a == 0 ? x.x : (a == 1 ? x.y : x.z);
   const float plane = fmaf((float)(i + (up ? 1 : 0)), P.d[a], P.lo[a]);
   const float ds0 = fmaxf(up ? plane - xa : xa - plane, 0.0f);
   const int cell = c.ix + P.nx * (c.iy + P.ny * c.iz);
-  s.th = s.kappa * fmaf(load_density(&P.density[cell]), ds0, __ldg(&I.column[cell]));
+  th = kappa * fmaf(load_density(&P.density[cell]), ds0, __ldg(&I.column[cell]));
+  n_cross = (unsigned long long)(up ? n - i : i + 1);
+  return true;
+}
+
+template <class G>
+__device__ __forceinline__ bool column_peel(const FwdParams& P, Lane<G>& s, const DevInstr& I, LaneTally* bt) {
+  unsigned long long nc;
+  if (!column_tau(P, s.x, s.has_cell(), s.cell(), I, s.kappa, s.th, nc)) return false;
   s.tl = 0.0f;
   s.walking = false;
-  const unsigned long long nc = (unsigned long long)(up ? n - i : i + 1);
   bt->crossings += nc;
   bt->column_crossings += nc;
   bt->column_peels += 1u;
   return true;
+}
+
+// The optical depth th + tl from x along d to the grid boundary (FP32 pair
+// sum, the transport kernel's walk arithmetic); known: x lies in cell cc.
+// Returns the crossings.
+__device__ __forceinline__ unsigned ray_tau(const FwdParams& P, float3 x, float3 d, bool known,
+                                            const CartGrid::Cell& cc, float kappa, float& th, float& tl) {
+  const float3 id = make_float3(inv_or_zero(d.x), inv_or_zero(d.y), inv_or_zero(d.z));
+  CartGrid::Walk w;
+  CartGrid::Scratch sc;
+  th = 0.0f;
+  tl = 0.0f;
+  unsigned n = 0;
+  if (CartGrid::init(P, x, d, id, known, cc, w, sc)) {
+    float rho = load_density(&P.density[w.cell]);
+    while (true) {
+      int axis;
+      const float te = CartGrid::exit(w, x, id, axis);
+      const float texit = fmaxf(te, w.t);
+      const float ds = texit - w.t;
+      const float kr = kappa * rho;
+      const float dt = kr * ds;
+      float nh, e;
+      two_sum(th, dt, nh, e);
+      tl = tl + e;
+      th = nh;
+      ++n;
+      w.t = texit;
+      if (!CartGrid::advance(P, x, d, id, axis, w, sc)) break;
+      rho = load_density(&P.density[w.cell]);
+    }
+  }
+  return n;
 }
 
 // Phase-function value of a scattering peel-off towards instrument I.
@@ -646,11 +688,13 @@ __device__ __forceinline__ void peel_deposit(const FwdParams& P, const Lane<G>& 
   deposit_peel(P, s.q(), s.lam, s.x, s.L(), phase, s.th, s.tl, scattered, s.pid(), s.event());
 }
 
-// Hand the peel-off towards instrument q to the sorted pass: a record in
-// the next free slot (one atomic per group of lanes), counted under its sort
-// key.  False when the buffer is full (the lane then walks it itself).
-template <class G>
-__device__ __forceinline__ bool defer_peel(const FwdParams& P, const Lane<G>& s, const DevInstr& I, bool emission) {
+// Hand the peel-off towards instrument q from x to the sorted pass: a
+// record in the next free slot (one atomic per group of lanes), counted under
+// its sort key.  known: x lies in cell c (else it is located by the walk).
+// False when the buffer is full (the caller then walks it itself).
+__device__ __forceinline__ bool defer_record(const FwdParams& P, int q, int lam, float3 x, double L, float phase,
+                                             bool known, const CartGrid::Cell& cc, bool emission,
+                                             unsigned long long pid, int event) {
   const unsigned m = __activemask();
   const unsigned lane = threadIdx.x & 31u;
   const int leader = __ffs(m) - 1;
@@ -660,25 +704,30 @@ __device__ __forceinline__ bool defer_peel(const FwdParams& P, const Lane<G>& s,
   const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
   if (slot >= P.peel_cap) return false;
   unsigned c = (unsigned)P.n_cells;
-  if (s.has_cell()) {
-    c = (unsigned)(s.cell().ix + P.nx * (s.cell().iy + P.ny * s.cell().iz));
-  } else if (inside_box(P, s.x)) {
+  if (known) {
+    c = (unsigned)(cc.ix + P.nx * (cc.iy + P.ny * cc.iz));
+  } else if (inside_box(P, x)) {
     // the cell the walk will locate x in
-    const int ix = min(max(__float2int_rd((s.x.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
-    const int iy = min(max(__float2int_rd((s.x.y - P.lo[1]) * P.inv_d[1]), 0), P.ny - 1);
-    const int iz = min(max(__float2int_rd((s.x.z - P.lo[2]) * P.inv_d[2]), 0), P.nz - 1);
+    const int ix = min(max(__float2int_rd((x.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
+    const int iy = min(max(__float2int_rd((x.y - P.lo[1]) * P.inv_d[1]), 0), P.ny - 1);
+    const int iz = min(max(__float2int_rd((x.z - P.lo[2]) * P.inv_d[2]), 0), P.nz - 1);
     c = (unsigned)(ix + P.nx * (iy + P.ny * iz));
   }
-  const unsigned key = (unsigned)s.q() * (unsigned)(P.n_cells + 1) + c;
-  const float phase = emission ? 1.0f : peel_phase(s.lam, s.k(), I);
-  const unsigned meta = (unsigned)s.lam | (emission ? 0u : 1u << 30) | (s.has_cell() ? 1u << 31 : 0u);
-  const long long Lb = __double_as_longlong(s.L());
+  const unsigned key = (unsigned)q * (unsigned)(P.n_cells + 1) + c;
+  const unsigned meta = (unsigned)lam | (emission ? 0u : 1u << 30) | (known ? 1u << 31 : 0u);
+  const long long Lb = __double_as_longlong(L);
   float4* r = reinterpret_cast<float4*>(&P.peel[slot]);
-  r[0] = make_float4(s.x.x, s.x.y, s.x.z, __uint_as_float(key));
+  r[0] = make_float4(x.x, x.y, x.z, __uint_as_float(key));
   r[1] = make_float4(__int_as_float((int)(unsigned)Lb), __int_as_float((int)(Lb >> 32)), phase, __uint_as_float(meta));
-  if (P.peel_tag) P.peel_tag[slot] = make_ulonglong2(s.pid(), (unsigned long long)s.event());
+  if (P.peel_tag) P.peel_tag[slot] = make_ulonglong2(pid, (unsigned long long)event);
   atomicAdd(&P.peel_hist[key], 1u);
   return true;
+}
+
+template <class G>
+__device__ __forceinline__ bool defer_peel(const FwdParams& P, const Lane<G>& s, const DevInstr& I, bool emission) {
+  const float phase = emission ? 1.0f : peel_phase(s.lam, s.k(), I);
+  return defer_record(P, s.q(), s.lam, s.x, s.L(), phase, s.has_cell(), s.cell(), emission, s.pid(), s.event());
 }
 
 // Emission (Sect. 3.4): source component by luminosity (FP64 comparison of
