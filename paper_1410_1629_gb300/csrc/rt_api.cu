@@ -12,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -143,6 +144,9 @@ struct rt_ctx_s {
   cudaEvent_t part_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   bool parts_timed = false;
   double emitted = 0.0;  // luminosity emitted since the last reset (host-side sum)
+  // device buffers released by the problem's set-up calls, for reuse
+  std::vector<std::pair<void*, size_t>> pool;
+  size_t pool_bytes = 0;
 };
 
 namespace {
@@ -174,6 +178,50 @@ void dfree(T*& p) {
   p = nullptr;
 }
 
+// Device buffers of the problem (density, absorption, images, column sums)
+// that a set-up call releases are kept for the next allocation of the same
+// size, so that a problem rebuilt with the same grid, wavelengths and
+// instruments (a fitting loop, an end-to-end run) allocates nothing.  At most
+// kPoolLimit bytes are kept; an allocation that fails empties the pool and
+// tries again.
+constexpr size_t kPoolLimit = size_t(16) << 30;
+
+void pool_flush(rt_ctx c) {
+  for (auto& b : c->pool) cudaFree(b.first);
+  c->pool.clear();
+  c->pool_bytes = 0;
+}
+
+template <class T>
+void pool_release(rt_ctx c, T*& p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0 || c->pool_bytes + bytes > kPoolLimit) {
+    cudaFree(p);
+  } else {
+    c->pool.emplace_back(static_cast<void*>(p), bytes);
+    c->pool_bytes += bytes;
+  }
+  p = nullptr;
+}
+
+template <class T>
+cudaError_t pool_alloc(rt_ctx c, T** p, size_t bytes) {
+  for (size_t i = 0; i < c->pool.size(); ++i) {
+    if (c->pool[i].second != bytes) continue;
+    *p = static_cast<T*>(c->pool[i].first);
+    c->pool_bytes -= bytes;
+    c->pool.erase(c->pool.begin() + (long)i);
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation && !c->pool.empty()) {
+    cudaGetLastError();
+    pool_flush(c);
+    e = cudaMalloc(p, bytes);
+  }
+  return e;
+}
+
 rt_status set_device(rt_ctx ctx) {
   RT_CUDA(ctx, cudaSetDevice(ctx->device));
   return RT_OK;
@@ -181,11 +229,12 @@ rt_status set_device(rt_ctx ctx) {
 
 void free_grid(rt_ctx c) {
   c->tape_valid = false;
-  dfree(c->d_density);
-  dfree(c->d_child);
-  dfree(c->d_absorption);
-  for (auto& p : c->d_columns) dfree(p);
-  for (auto& p : c->d_line_dep) dfree(p);
+  cudaDeviceSynchronize();  // no kernel may still read the released buffers
+  pool_release(c, c->d_density, (size_t)c->n_cells * sizeof(float));
+  pool_release(c, c->d_child, (size_t)c->n_nodes * sizeof(int32_t));
+  pool_release(c, c->d_absorption, (size_t)c->n_lambda * c->n_cells * sizeof(double));
+  for (auto& p : c->d_columns) pool_release(c, p, (size_t)c->n_cells * sizeof(float));
+  for (auto& p : c->d_line_dep) pool_release(c, p, (size_t)c->n_cells * sizeof(double));
   c->tables_dirty = true;
   c->tape_valid = false;
   c->has_grid = false;
@@ -207,11 +256,12 @@ bool frame_axis(const DevInstr& I, int& axis, int& dir) {
 
 void free_problem(rt_ctx c) {
   c->tape_valid = false;
-  for (auto& q : c->instr) dfree(q.d_image);
+  cudaDeviceSynchronize();  // no kernel may still write the released buffers
+  for (auto& q : c->instr) pool_release(c, q.d_image, q.n_elems * sizeof(double));
   c->instr.clear();
   c->sources.clear();
+  pool_release(c, c->d_absorption, (size_t)c->n_lambda * c->n_cells * sizeof(double));
   c->n_lambda = 0;
-  dfree(c->d_absorption);
   c->tables_dirty = true;
   c->tape_valid = false;
 }
@@ -284,7 +334,7 @@ rt_status upload_tables(rt_ctx c, cudaStream_t s) {
     int axis = 0, dir = 0;
     if (c->grid_kind == RT_GRID_CARTESIAN && frame_axis(I, axis, dir)) {
       const int k = 2 * axis + (dir > 0 ? 1 : 0);
-      if (!c->d_columns[k]) RT_CUDA(c, cudaMalloc(&c->d_columns[k], (size_t)c->n_cells * sizeof(float)));
+      if (!c->d_columns[k]) RT_CUDA(c, pool_alloc(c, &c->d_columns[k], (size_t)c->n_cells * sizeof(float)));
       I.column = c->d_columns[k];
       I.axis = axis;
       I.dir = dir;
@@ -483,6 +533,7 @@ rt_status rt_context_destroy(rt_ctx c) {
   for (size_t i = 0; i < c->batches.size(); ++i) rt_batch_destroy(c, (int32_t)i);
   free_problem(c);
   free_grid(c);
+  pool_flush(c);
   dfree(c->d_lam); dfree(c->d_src); dfree(c->d_src_cum); dfree(c->d_instr);
   dfree(c->d_stats); dfree(c->d_counters); dfree(c->d_work); dfree(c->d_flags);
   dfree(c->d_adj); dfree(c->d_adj_img); dfree(c->d_adj_max); dfree(c->d_tune_grad); dfree(c->d_tape);
@@ -553,10 +604,10 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
   free_problem(c);
   free_grid(c);
   const cudaMemcpyKind kind = d->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  RT_CUDA(c, cudaMalloc(&c->d_density, (size_t)n_cells * sizeof(float)));
+  RT_CUDA(c, pool_alloc(c, &c->d_density, (size_t)n_cells * sizeof(float)));
   RT_CUDA(c, cudaMemcpy(c->d_density, d->density, (size_t)n_cells * sizeof(float), kind));
   if (d->kind == RT_GRID_OCTREE) {
-    RT_CUDA(c, cudaMalloc(&c->d_child, (size_t)n_nodes * sizeof(int32_t)));
+    RT_CUDA(c, pool_alloc(c, &c->d_child, (size_t)n_nodes * sizeof(int32_t)));
     RT_CUDA(c, cudaMemcpy(c->d_child, child_host.data(), (size_t)n_nodes * sizeof(int32_t), cudaMemcpyHostToDevice));
   }
   c->grid_kind = d->kind;
@@ -592,7 +643,7 @@ rt_status rt_set_optics(rt_ctx c, int32_t grid_id, int32_t n_lambda, const doubl
   c->albedo.assign(albedo, albedo + n_lambda);
   c->g.assign(g, g + n_lambda);
   const size_t n_abs = (size_t)n_lambda * c->n_cells;
-  RT_CUDA(c, cudaMalloc(&c->d_absorption, n_abs * sizeof(double)));
+  RT_CUDA(c, pool_alloc(c, &c->d_absorption, n_abs * sizeof(double)));
   RT_CUDA(c, cudaMemset(c->d_absorption, 0, n_abs * sizeof(double)));
   RT_CUDA(c, cudaMemset(c->d_stats, 0, 4 * sizeof(double)));
   RT_CUDA(c, cudaMemset(c->d_counters, 0, 9 * sizeof(unsigned long long)));
@@ -654,7 +705,7 @@ rt_status rt_add_instruments(rt_ctx c, int32_t n, const rt_instrument_desc* q, i
     HostInstr h;
     h.desc = q[i];
     h.n_elems = (size_t)q[i].channels * c->n_lambda * q[i].ny * q[i].nx;
-    RT_CUDA(c, cudaMalloc(&h.d_image, h.n_elems * sizeof(double)));
+    RT_CUDA(c, pool_alloc(c, &h.d_image, h.n_elems * sizeof(double)));
     RT_CUDA(c, cudaMemset(h.d_image, 0, h.n_elems * sizeof(double)));
     if (ids) ids[i] = (int32_t)c->instr.size();
     c->instr.push_back(h);
@@ -1046,7 +1097,7 @@ rt_status rt_adjoint(rt_ctx c, const double* const* adj_images, int32_t n_adj_im
     for (int k = 0; k < 6; ++k) {
       if (!c->columns_used[k]) continue;
       const int axis = k / 2;
-      if (!c->d_line_dep[k]) RT_CUDA(c, cudaMalloc(&c->d_line_dep[k], (size_t)c->n_cells * sizeof(double)));
+      if (!c->d_line_dep[k]) RT_CUDA(c, pool_alloc(c, &c->d_line_dep[k], (size_t)c->n_cells * sizeof(double)));
       line_dep[k] = c->d_line_dep[k];
       e = launch_columns(c->d_density, c->nx, c->ny, c->nz, axis, (k & 1) ? 1 : -1, p.d[axis], c->d_columns[k], s);
       if (e != cudaSuccess) return cuda_fail(c, e, "column sums");
