@@ -122,6 +122,53 @@ def test_split_launches_equal_one_launch():
     assert sa["crossings"] == sb["crossings"] and sa["events"] == sb["events"]
 
 
+def _raw_run(ctx, prob, n):
+    """Set the problem up on an existing context and run n packets per wavelength."""
+    d, keep = rt.grid_desc(prob.grid)
+    rt.rt_create_grid(ctx, d)
+    rt.rt_set_optics(ctx, 0, prob.kappa, prob.albedo, prob.g, prob.wavelengths)
+    rt.rt_add_sources(ctx, [rt.source_desc(s) for s in prob.sources], [s.lum for s in prob.sources])
+    rt.rt_add_instruments(ctx, [rt.instrument_desc(q) for q in prob.instruments])
+    del keep
+    o = rt.rt_default_opts()
+    o.w_min, o.max_events, o.weight_cut = prob.run.w_min, prob.run.max_events, int(prob.run.weight_cut)
+    rt.rt_launch_packets(ctx, n, 0, 0, o, None)
+    imgs = []
+    for q, inst in enumerate(prob.instruments):
+        a = np.empty((inst.channels, prob.n_lambda, inst.ny, inst.nx), dtype=np.float64)
+        rt.rt_read_images(ctx, q, a.ctypes.data, a.size, 0, None)
+        imgs.append(a)
+    ab = np.empty((prob.n_lambda, prob.grid.n_cells), dtype=np.float64)
+    rt.rt_read_absorption(ctx, ab.ctypes.data, ab.size, 0, None)
+    return imgs, ab, rt.rt_read_stats(ctx).as_dict()
+
+
+def test_problem_rebuilt_on_one_context():
+    """Set-up calls release the problem's device buffers to a pool of the
+    context and later set-ups of the same sizes reuse them: a problem rebuilt
+    on one context gives a fresh context's tallies, with the same sizes and
+    after the sizes change."""
+    a = W.disk_galaxy(n_cells=32, n_lambda=2, n_pix=32)
+    b = W.uniform_cube(n_cells=24, channels=3)
+    n = 5000
+    ref = {}
+    for name, prob in (("a", a), ("b", b)):
+        g = PAR.gpu_run(prob, n)
+        ref[name] = (g["images"], g["absorption"], g["raw_stats"])
+    ctx = rt.rt_context_create(0)
+    try:
+        for name, prob in (("a", a), ("a", a), ("b", b), ("a", a)):
+            imgs, ab, st = _raw_run(ctx, prob, n)
+            r_imgs, r_ab, r_st = ref[name]
+            for x, y in zip(imgs, r_imgs):
+                np.testing.assert_allclose(x, y, rtol=1e-12, atol=1e-300)
+            np.testing.assert_allclose(ab, r_ab, rtol=1e-12, atol=1e-300)
+            assert st["crossings"] == r_st["crossings"] and st["events"] == r_st["events"]
+            assert st["device_flags"] == 0
+    finally:
+        rt.rt_context_destroy(ctx)
+
+
 def test_state_and_argument_errors():
     ctx = rt.rt_context_create(0)
     try:
