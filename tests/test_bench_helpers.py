@@ -1,0 +1,46 @@
+"""Host-side helpers of bench.py: the count of column-sum tables a launch
+builds (part of the reported launch count), the kernel-source hash that keys
+the stored DRAM traffic capture, and when that capture applies."""
+import math
+
+import numpy as np
+
+import bench
+from paper_1410_1629_gb300 import workloads as W
+
+
+def test_column_tables_follow_the_frames():
+    # frames at 0, 60 and 90 degrees: face-on (+z) and edge-on look along axes
+    assert bench.column_tables(W.disk_galaxy(n_cells=8, n_lambda=1, n_pix=8)) == 2
+    assert bench.column_tables(W.uniform_cube(n_cells=4, n_pix=8)) == 1
+    prob = W.uniform_cube(n_cells=4, n_pix=8)
+    prob.instruments[0].inclination = 0.3
+    assert bench.column_tables(prob) == 0
+    # two frames along the same axis and direction share one table
+    prob = W.uniform_cube(n_cells=4, n_pix=8)
+    prob.instruments.append(W.Instrument(0.0, 0.5 * math.pi, 0.0, 8, 8, 1.0, 1.0))
+    assert bench.column_tables(prob) == 1
+    # the opposite direction is a table of its own
+    prob.instruments.append(W.Instrument(math.pi, 0.0, 0.0, 8, 8, 1.0, 1.0))
+    assert bench.column_tables(prob) == 2
+
+
+def test_octree_has_no_column_tables():
+    grid, _, _ = W.build_octree([-1, 1] * 3, lambda lo, hi, l: np.full(len(lo), l < 1),
+                                lambda lo, hi: np.ones(len(lo)), 3)
+    prob = W.uniform_cube(n_cells=4, n_pix=8)
+    prob.grid = grid
+    assert bench.column_tables(prob) == 0
+
+
+def test_traffic_capture_applies_to_its_kernel_and_workload_only():
+    h = bench.kernel_sources_hash()
+    assert len(h) == 16 and int(h, 16) >= 0
+    cap = bench.TRAFFIC_CAPTURE
+    got = bench.captured_traffic(1e8)
+    if h == cap["sources_sha256_16"]:
+        assert got == cap["bytes_per_packet"] * 1e8
+    else:
+        assert got is None
+    assert bench.captured_traffic(1e8, "clumpy_octree") is None
+    assert bench.captured_traffic(1e8, "disk_galaxy", "k_peel_sorted") is None
