@@ -60,6 +60,17 @@
 // (common random numbers: directions and draws are fixed; positions move with
 // the density through the forced-scattering inversion).
 //
+// Pins (the tests under tests/test_oracle_*.py): Philox against a library
+// generator, the phase function and emission distributions, the grid walks
+// by brute force, closed-form path lengths and direct images, quadratures of
+// the first-step escape, absorption field and single-scattering flux,
+// special cases, symmetry, scale invariance, conservation, dual gradients
+// against central differences, multiple scattering (escaped and absorbed
+// fractions, intensity towards a frame) against an analog simulation, and
+// mutations of this file that the pins must catch.  Parity unpinned: the
+// spatial distribution of multiply scattered light in an image, beyond those
+// totals and the invariants (no closed form exists).
+//
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared -pthread
 
 #include <cmath>
