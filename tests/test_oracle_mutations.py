@@ -37,6 +37,10 @@ MUTATIONS = {
     # azimuth drawn over half a turn
     "half_azimuth": ("return rotate_dir(k, hg_sample(g, u1), 2.0 * M_PI * u2);",
                      "return rotate_dir(k, hg_sample(g, u1), M_PI * u2);", "test_oracle_optics.py"),
+    # scattering directions drawn with the opposite asymmetry (forward and
+    # backward scattering swapped after the first event)
+    "scatter_g_sign": ("return rotate_dir(k, hg_sample(g, u1), 2.0 * M_PI * u2);",
+                       "return rotate_dir(k, hg_sample(-g, u1), 2.0 * M_PI * u2);", "test_oracle_analog.py"),
     # derivative of exp with the wrong sign
     "dual_exp_sign": ("inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, e * a.d}; }",
                       "inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, -e * a.d}; }",
