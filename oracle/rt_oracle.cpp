@@ -65,11 +65,12 @@
 // by brute force, closed-form path lengths and direct images, quadratures of
 // the first-step escape, absorption field and single-scattering flux,
 // special cases, symmetry, scale invariance, conservation, dual gradients
-// against central differences, multiple scattering (escaped and absorbed
-// fractions, intensity towards a frame) against an analog simulation, and
-// mutations of this file that the pins must catch.  Parity unpinned: the
-// spatial distribution of multiply scattered light in an image, beyond those
-// totals and the invariants (no closed form exists).
+// against central differences, multiple scattering against an analog
+// simulation (escaped and absorbed fractions, intensity towards a frame, the
+// frame's inner 2 x 2 blocks of 4 x 4, the absorption field in 4 x 4 x 4
+// blocks), and mutations of this file that the pins must catch.  Parity
+// unpinned: multiply scattered light below that block resolution, beyond the
+// invariants (no closed form exists).
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared -pthread
 
