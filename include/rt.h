@@ -31,7 +31,11 @@
  *     default stream).  Launches are asynchronous.  Errors raised by
  *     asynchronous work surface at the next synchronising call (rt_read_* to
  *     host memory, rt_read_stats, rt_synchronize).
- *   - A context is bound to one CUDA device and is not thread-safe.
+ *   - A context is bound to one CUDA device and is not thread-safe.  Its
+ *     launches share working buffers (the packet counter, the sorted
+ *     peel-off pass's records, the adjoint tape), so two launches of one
+ *     context must not overlap on the GPU: queue them on one stream or
+ *     synchronise between them (separate contexts may run concurrently).
  *
  * Units: lengths in any consistent unit; kappa is the extinction cross
  * section per unit density per unit length; images hold luminosity per
