@@ -39,9 +39,9 @@ BYTES_COLUMN_PEEL = 8
 # DRAM bytes (read + write) per packet of the transport kernel, from an ncu
 # capture of one 2e6-packet launch of this workload (dram__bytes_read.sum
 # 50.829 GB + dram__bytes_write.sum 21.036 GB), valid only for the kernel
-# sources whose hash is given; the per-launch traffic is this figure times
-# the packets.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "66f6cb07abf451a4", "kernel": "k_forward_cartesian",
+# code whose hash is given (kernel_sources_hash: the sources without their
+# comments); the per-launch traffic is this figure times the packets.
+TRAFFIC_CAPTURE = {"sources_sha256_16": "3db4f7fad838f02c", "kernel": "k_forward_cartesian",
                    "bytes_per_packet": (50828612352 + 21036353792) / 2e6}
 KERNEL_SOURCES = ["paper_1410_1629_gb300/csrc/rt_forward.cu", "paper_1410_1629_gb300/csrc/rt_device.cuh",
                   "paper_1410_1629_gb300/csrc/rt_internal.h", "paper_1410_1629_gb300/csrc/rt_transport.cuh",
@@ -74,12 +74,33 @@ def column_tables(prob):
     return len(seen)
 
 
-def kernel_sources_hash():
+def source_code(text, name):
+    """The code of a CUDA source without its // comments and blank lines (a
+    comment edit leaves the kernel, and so its traffic, unchanged); other
+    files whole."""
+    if not name.endswith((".cu", ".cuh", ".h")):
+        return text
+    out = []
+    for line in text.splitlines():
+        i = line.find("//")
+        line = (line if i < 0 else line[:i]).rstrip()
+        if line:
+            out.append(line)
+    return "\n".join(out)
+
+
+def kernel_sources_hash(read=None):
+    """Hash of the code of the transport kernel's sources; read(name) -> text
+    reads another version of them (default: the working tree)."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        if read is None:
+            with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+                text = fh.read()
+        else:
+            text = read(f)
+        h.update(source_code(text, f).encode("utf-8"))
     return h.hexdigest()[:16]
 
 

@@ -8,9 +8,12 @@
 // straight cell walk: per packet a peel-off walk per instrument at emission and
 // at every scattering, and two walks of the forced path per scattering (the
 // first accumulates the optical depth to the boundary and deposits absorption,
-// the second stops at the interaction).  The main loop advances every walking
-// lane by exactly one cell crossing per iteration, whichever of these walks it
-// is in, so the warp stays converged on the hot path.  The per-event work
+// the second stops at the interaction).  Peel-offs towards a frame along a grid
+// axis take their optical depth from per-line column sums; on cartesian grids
+// the other peel-offs become records for the sorted pass (rt_peel.cu), which
+// walks them after this kernel, ordered by start cell.  The main loop advances
+// every walking lane by exactly one cell crossing per iteration, whichever of
+// the remaining walks it is in, so the warp stays converged on the hot path.  The per-event work
 // (emission, forced-scattering inversion, weight update, deposits, the
 // Henyey-Greenstein draw, fetching the next packet) is deferred until enough
 // lanes of the warp need it and is then done for those lanes together;
