@@ -44,3 +44,12 @@ def test_traffic_capture_applies_to_its_kernel_and_workload_only():
         assert got is None
     assert bench.captured_traffic(1e8, "clumpy_octree") is None
     assert bench.captured_traffic(1e8, "disk_galaxy", "k_peel_sorted") is None
+
+
+def test_kernel_hash_ignores_comments_only():
+    a = "int x;  // one\n\n// a whole line\nint y;\n"
+    b = "int x;\nint y;  // two\n"
+    assert bench.source_code(a, "k.cu") == bench.source_code(b, "k.cu")
+    assert bench.source_code("int x;\nint z;\n", "k.cu") != bench.source_code(a, "k.cu")
+    # other files are hashed whole
+    assert bench.source_code("x = 1  # c\n", "build.py") == "x = 1  # c\n"
