@@ -324,10 +324,11 @@ rt_status rt_update_density(rt_ctx ctx, const float* density, int32_t on_device,
  * recomputed from its Philox key.  The functional is continuous in the density
  * with bilinear deposit and event-cap termination (opts->weight_cut = 0);
  * use those for gradient checks.  Cartesian grids only; max_events <= 256.
- * The context keeps a device buffer of per-event records, about
- * 200 B x (max_events + 1) per resident thread (77,824 threads on a 152-SM
- * GPU: 0.33 GB at max_events = 20), allocated on the first call that needs
- * more (RT_ERR_OOM if it cannot be had).  opts->profile, if not NULL, is a
+ * The context keeps a device buffer of per-event records, 160 B x
+ * (max_events + 1) per resident thread (116,736 threads on a 152-SM GPU:
+ * 0.39 GB at max_events = 20), allocated on the first call that needs more
+ * (RT_ERR_OOM if it cannot be had); a call that can use the forward launch's
+ * tape (rt_launch_opts.tape) needs none.  opts->profile, if not NULL, is a
  * device uint64 array: [0] += cell crossings of all walks, [1] += crossings
  * that deposited into grad_density.
  *   adj_images: host array of n_instruments device pointers (each shaped like
@@ -353,17 +354,23 @@ rt_status rt_adjoint(rt_ctx ctx, const double* const* adj_images, int32_t n_adj_
  *   [channels][n_lambda][ny][nx]; absorption: device float64
  *   [n_lambda][nx*ny*nz].  Tallies are ADDED to these buffers.
  *   stats_out: device pointer that receives this call's rt_stats, or NULL.
+ * Options: as for rt_launch_packets; every peel-off walks its ray inside the
+ * transport kernel (walk_peels and inline_peels are implied), and tape or
+ * time_parts set returns RT_ERR_ARG (both need a context).
  * Limits (fixed by the library's working area): n_lambda <= 64,
  * n_sources <= 16, n_instruments <= 16; larger values return RT_ERR_ARG.
  * The library keeps one working area of 16 KiB per device in a static
  * device array, held by every GPU that loads the library until the process
  * exits; the call allocates nothing (no cudaMalloc, cudaFree or allocating
- * library routine).  The first call on a device looks up the working area's
- * address and should come before any stream capture on that device.  All
- * calls share the working area, which keeps the last call's contents: calls
- * that overlap on the GPU (other streams, other threads) race and must be
- * serialised by the caller.  Asynchronous on `stream`.  Errors: RT_ERR_ARG,
- * RT_ERR_CUDA; the message is rt_last_error(NULL). */
+ * library routine).  Every call looks the working area's address up on the
+ * current device; the first call on a device also loads the library's device
+ * code there and should come before any stream capture on that device.  The
+ * call's tables reach the working area as a kernel parameter, so the caller's
+ * host arrays may be reused when the call returns.  All calls share the
+ * working area, which keeps the last call's contents: calls that overlap on
+ * the GPU (other streams, other threads) race and must be serialised by the
+ * caller.  Asynchronous on `stream`.  Errors: RT_ERR_ARG, RT_ERR_CUDA; the
+ * message is rt_last_error(NULL). */
 rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t n_lambda, const double* kappa,
                                     const double* albedo, const double* g, int32_t n_sources,
                                     const rt_source_desc* sources, int32_t n_instruments,

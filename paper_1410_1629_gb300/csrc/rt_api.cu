@@ -117,7 +117,7 @@ struct rt_ctx_s {
   size_t tape_bytes = 0;
   bool tape_valid = false;
   unsigned long long tape_n = 0, tape_first = 0, tape_seed = 0, tape_norm = 0;
-  int tape_max_events = 0, tape_weight_cut = 0, tape_peel_e = 0, tape_peel_s = 0, tape_model = 0, tape_columns = 0;
+  int tape_max_events = 0, tape_weight_cut = 0, tape_peel_e = 0, tape_peel_s = 0, tape_model = 0;
   double tape_w_min = 0.0;
   // the sorted peel-off pass (cartesian launches): records, their order,
   // counts per sort key and per scan tile, the record counter; the count of
@@ -809,7 +809,8 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   if (!(o.w_min >= 0 && o.w_min < 1)) return fail(c, RT_ERR_ARG, "rt_launch_packets: w_min must be in [0, 1)");
   if (o.control_lanes < 0 || o.control_lanes > 32)
     return fail(c, RT_ERR_ARG, "rt_launch_packets: control_lanes must be in [0, 32]");
-  if (o.records && o.records_capacity < 0) return fail(c, RT_ERR_ARG, "rt_launch_packets: negative record capacity");
+  if ((o.records && o.records_capacity < 0) || (o.trace && o.trace_capacity < 0))
+    return fail(c, RT_ERR_ARG, "rt_launch_packets: negative record or trace capacity");
   for (int l = 0; l < c->n_lambda; ++l) {
     double tot = 0;
     for (auto& s : c->sources) tot += s.lum[l];

@@ -13,16 +13,20 @@
 // this library holds until the process exits.  It carries the packet work
 // counter, the tallies and the device flags of one launch, and the small
 // per-launch tables (optics per wavelength, sources, instruments).  Host code
-// cannot use the array's name as a device address: on the first call on each
-// device the library looks the address up with cudaGetSymbolAddress (with that
-// device current) and keeps it.  That first call should therefore come before
-// any stream capture on that device.  Every call uses the same array and the
-// array keeps the last call's contents; a call clears the parts that must
-// start at zero.  Two calls that overlap on the GPU (different streams, or
-// different host threads on one device) race on the array.
+// cannot use the array's name as a device address: every call looks the
+// address up with cudaGetSymbolAddress on the current device (a lookup that
+// allocates nothing, repeated per call so that a reset device never leaves a
+// stale address behind).  The first call on a device also loads the library's
+// device code there, so it should come before any stream capture on that
+// device.  The per-launch tables travel to the working area as the parameter
+// of a small set-up kernel (by value), never as a copy from host memory, so
+// no queued work refers to the caller's stack.  Every call uses the same array
+// and the array keeps the last call's contents; a call clears the parts that
+// must start at zero.  Two calls that overlap on the GPU (different streams,
+// or different host threads on one device) race on the array.
 #include <cmath>
 #include <cstring>
-#include <mutex>
+#include <cstddef>
 
 #include <cuda_runtime.h>
 
@@ -33,36 +37,49 @@ using namespace rtk;
 namespace {
 
 constexpr size_t kNoallocScratchBytes = 16384;
-constexpr int kMaxDevices = 64;
 
-// Byte offsets inside the working area (each 256-byte aligned block).
-constexpr size_t kOffWork = 0;                                       // 1 x u64
-constexpr size_t kOffStats = 16;                                     // 4 x f64
-constexpr size_t kOffCounters = 48;                                  // 8 x u64
-constexpr size_t kOffFlags = 112;                                    // 1 x i32
-constexpr size_t kOffLam = 256;                                      // DevLambda[kMaxLambda]
-constexpr size_t kOffSrc = kOffLam + sizeof(DevLambda) * kMaxLambda;  // DevSource[kMaxSources]
-constexpr size_t kOffCum = ((kOffSrc + sizeof(DevSource) * kMaxSources + 255) / 256) * 256;
-constexpr size_t kOffInstr = ((kOffCum + sizeof(double) * kMaxLambda * kMaxSources + 255) / 256) * 256;
-constexpr size_t kScratchUsed = kOffInstr + sizeof(DevInstr) * kMaxInstruments;
-static_assert(kScratchUsed <= kNoallocScratchBytes, "working area too small for its layout");
+// The per-launch tables, passed by value to the set-up kernel and kept in the
+// working area after its first 256 bytes.
+struct NoallocTables {
+  DevLambda lam[kMaxLambda];
+  DevSource src[kMaxSources];
+  double cum[kMaxLambda * kMaxSources];  // [n_lambda][n_sources] cumulative luminosity fractions
+  DevInstr ins[kMaxInstruments];
+};
+
+// Byte offsets inside the working area.
+constexpr size_t kOffWork = 0;       // 1 x u64
+constexpr size_t kOffStats = 16;     // 4 x f64
+constexpr size_t kOffCounters = 48;  // 8 x u64
+constexpr size_t kOffFlags = 112;    // 1 x i32
+constexpr size_t kOffTables = 256;   // NoallocTables
+constexpr size_t kOffLam = kOffTables + offsetof(NoallocTables, lam);
+constexpr size_t kOffSrc = kOffTables + offsetof(NoallocTables, src);
+constexpr size_t kOffCum = kOffTables + offsetof(NoallocTables, cum);
+constexpr size_t kOffInstr = kOffTables + offsetof(NoallocTables, ins);
+static_assert(kOffTables + sizeof(NoallocTables) <= kNoallocScratchBytes, "working area too small for its layout");
+// a kernel parameter may hold up to 32764 bytes (CUDA 12.1 and later)
+static_assert(sizeof(NoallocTables) <= 32000, "tables too large for a kernel parameter");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of the working area on the current device (looked up once).
-cudaError_t scratch_address(int device, unsigned char** out) {
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[device] = p;
-  }
-  *out = static_cast<unsigned char*>(g_scratch_addr[device]);
+// Device address of the working area on the current device.
+cudaError_t scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
+}
+
+// Clears the counters, tallies and flags and writes the launch's tables into
+// the working area.
+__global__ void k_noalloc_setup(const NoallocTables t, unsigned char* scratch) {
+  const unsigned* src = reinterpret_cast<const unsigned*>(&t);
+  unsigned* dst = reinterpret_cast<unsigned*>(scratch + kOffTables);
+  for (unsigned i = threadIdx.x; i < sizeof(NoallocTables) / 4; i += blockDim.x) dst[i] = src[i];
+  unsigned* head = reinterpret_cast<unsigned*>(scratch);
+  if (threadIdx.x < kOffTables / 4) head[threadIdx.x] = 0u;
 }
 
 // Packs the launch's tallies from the working area into an rt_stats.
@@ -152,13 +169,16 @@ extern "C" rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t
   if (opts) o = *opts;
   if (o.max_events < 1 || !(o.w_min >= 0 && o.w_min < 1) || o.control_lanes < 0 || o.control_lanes > 32)
     return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: invalid launch options");
+  if ((o.records && o.records_capacity < 0) || (o.trace && o.trace_capacity < 0))
+    return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: negative record or trace capacity");
+  if (o.tape || o.time_parts)
+    return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: the adjoint tape and part timings need a context");
   // ---- the working area of the current device
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);
   if (e != cudaSuccess) return fail(RT_ERR_CUDA, cudaGetErrorString(e));
-  if (device < 0 || device >= kMaxDevices) return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: device index too large");
   unsigned char* scratch = nullptr;
-  e = scratch_address(device, &scratch);
+  e = scratch_address(&scratch);
   if (e != cudaSuccess) return fail(RT_ERR_CUDA, cudaGetErrorString(e));
   int num_sms = 0;
   e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -167,15 +187,13 @@ extern "C" rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t
   const unsigned long long n_total = n_per_lambda * (unsigned long long)n_lambda;
   if (n_total / (unsigned long long)n_lambda != n_per_lambda || n_total > (1ull << 62))
     return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: packet count overflow");
-  // ---- per-launch tables, built on the host stack and copied into the working area
-  DevLambda lam[kMaxLambda];
-  DevSource src[kMaxSources];
-  double cum[kMaxLambda * kMaxSources];
-  DevInstr ins[kMaxInstruments];
-  std::memset(lam, 0, sizeof lam);
-  std::memset(src, 0, sizeof src);
-  std::memset(cum, 0, sizeof cum);
-  std::memset(ins, 0, sizeof ins);
+  // ---- per-launch tables, handed to the set-up kernel by value
+  NoallocTables t;
+  std::memset(&t, 0, sizeof t);
+  DevLambda* lam = t.lam;
+  DevSource* src = t.src;
+  double* cum = t.cum;
+  DevInstr* ins = t.ins;
   FwdParams p;
   std::memset(&p, 0, sizeof p);
   const unsigned long long n_norm = o.n_norm ? o.n_norm : n_per_lambda;
@@ -224,15 +242,8 @@ extern "C" rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t
     ins[q].image = images[q];
   }
   cudaStream_t s = (cudaStream_t)stream;
-  // pageable host -> device copies are staged before these calls return, so
-  // the stack tables may go out of scope afterwards
-  if ((e = cudaMemsetAsync(scratch, 0, 256, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(scratch + kOffLam, lam, sizeof(DevLambda) * n_lambda, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(scratch + kOffSrc, src, sizeof(DevSource) * n_sources, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(scratch + kOffCum, cum, sizeof(double) * n_lambda * n_sources, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (n_instruments > 0 &&
-       (e = cudaMemcpyAsync(scratch + kOffInstr, ins, sizeof(DevInstr) * n_instruments, cudaMemcpyHostToDevice, s)) != cudaSuccess))
-    return fail(RT_ERR_CUDA, cudaGetErrorString(e));
+  k_noalloc_setup<<<1, 256, 0, s>>>(t, scratch);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(RT_ERR_CUDA, cudaGetErrorString(e));
   // ---- the launch, exactly as rt_launch_packets builds it
   p.nx = grid->nx; p.ny = grid->ny; p.nz = grid->nz;
   const int n3[3] = {grid->nx, grid->ny, grid->nz};

@@ -7,6 +7,7 @@ the C ABI are each compared with rt_launch_packets on a context, at the
 tolerance of FP64 summation order.  This file is collected last on purpose.
 """
 import ctypes
+from dataclasses import replace
 
 import numpy as np
 import pytest
@@ -39,13 +40,18 @@ def _context_run(prob, n, first, seed, n_norm):
     return imgs, ab, st
 
 
-def _noalloc_run(prob, dens, n, first, seed, n_norm):
+def _grid(prob, dens):
     grid = rt.rt_grid_desc()
     grid.kind = rt.RT_GRID_CARTESIAN
     grid.bounds[:] = [float(b) for b in prob.grid.bounds]
     grid.nz, grid.ny, grid.nx = prob.grid.density.shape
     grid.density = dens.data_ptr()
     grid.on_device = 1
+    return grid
+
+
+def _noalloc_run(prob, dens, n, first, seed, n_norm):
+    grid = _grid(prob, dens)
     imgs = [torch.zeros((q.channels, prob.n_lambda, q.ny, q.nx), dtype=torch.float64, device="cuda")
             for q in prob.instruments]
     ab = torch.zeros((prob.n_lambda, prob.grid.n_cells), dtype=torch.float64, device="cuda")
@@ -78,18 +84,52 @@ def test_noalloc_matches_context_path_on_two_calls():
         assert gs["device_flags"] == 0
 
 
+def test_noalloc_without_instruments_or_stats_allocates_nothing():
+    """No frames and no statistics output: the absorption field still equals
+    the context path's.  The calls allocate no device memory: after a first
+    call (which loads the library's device code), the free device memory is
+    the same before and after several more calls."""
+    prob = _problem()
+    dens = torch.from_numpy(np.ascontiguousarray(prob.grid.density)).cuda()
+    grid = _grid(prob, dens)
+    n = 4000
+    ab = torch.zeros((prob.n_lambda, prob.grid.n_cells), dtype=torch.float64, device="cuda")
+    srcs = [rt.source_desc(s) for s in prob.sources]
+    lums = [s.lum for s in prob.sources]
+    rt.rt_launch_packets_noalloc(grid, prob.kappa, prob.albedo, prob.g, srcs, lums, [], [], ab.data_ptr(), n, 0, 3)
+    torch.cuda.synchronize()
+    got = ab.cpu().numpy()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in range(4):
+        rt.rt_launch_packets_noalloc(grid, prob.kappa, prob.albedo, prob.g, srcs, lums, [], [], ab.data_ptr(), n,
+                                     0, 3)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
+    np.testing.assert_allclose(ab.cpu().numpy(), 5 * got, rtol=1e-11, atol=1e-300)
+    noframes = replace(prob, instruments=[])
+    sim = rt.Simulation(noframes)
+    try:
+        sim.launch(n, 0, 3, walk_peels=1)
+        ref = sim.absorption().cpu().numpy()
+    finally:
+        sim.close()
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-20)
+
+
 def test_noalloc_rejects_sizes_beyond_its_working_area():
     prob = _problem()
     dens = torch.from_numpy(np.ascontiguousarray(prob.grid.density)).cuda()
-    grid = rt.rt_grid_desc()
-    grid.kind = rt.RT_GRID_CARTESIAN
-    grid.bounds[:] = [float(b) for b in prob.grid.bounds]
-    grid.nz, grid.ny, grid.nx = prob.grid.density.shape
-    grid.density = dens.data_ptr()
-    grid.on_device = 1
+    grid = _grid(prob, dens)
     ab = torch.zeros(1, dtype=torch.float64, device="cuda")
     many = np.full(65, 0.5)
     with pytest.raises(rt.RTError) as e:
         rt.rt_launch_packets_noalloc(grid, many, many, many * 0, [rt.source_desc(prob.sources[0])], [np.ones(65)],
                                      [], [], ab.data_ptr(), 10)
     assert e.value.status == rt.RT_ERR_ARG and "64" in str(e.value)
+    opts = rt.rt_default_opts()
+    opts.tape = 1
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_launch_packets_noalloc(grid, prob.kappa, prob.albedo, prob.g, [rt.source_desc(prob.sources[0])],
+                                     [prob.sources[0].lum], [], [], ab.data_ptr(), 10, opts=opts)
+    assert e.value.status == rt.RT_ERR_ARG
