@@ -135,6 +135,11 @@ def lib():
             L.or_trace.restype = ctypes.c_int64
             L.or_trace.argtypes = [ctypes.POINTER(OrProblem), ctypes.POINTER(OrOpts), ctypes.c_uint64,
                                    ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64]
+            L.or_interaction.restype = ctypes.c_int32
+            L.or_interaction.argtypes = [ctypes.POINTER(OrProblem), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
             L.or_vjp.restype = ctypes.c_int32
             L.or_vjp.argtypes = [ctypes.POINTER(OrProblem), ctypes.POINTER(OrOpts),
                                  ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
@@ -396,3 +401,19 @@ def locate(problem, p, k=(1.0, 1.0, 1.0)):
 
 def default_threads() -> int:
     return os.cpu_count() or 1
+
+
+def interaction(problem, x, k, u, lam=0, start_cell=-1):
+    """One forced path from x along k and its interaction for the uniform u
+    (steps a and c): returns (x_interaction, cell, tau_path, tau_star, flags),
+    flags bit 0 = the inversion's rounding fallback acted, bit 1 = the point
+    was moved into the interaction cell, bit 2 = no dust on the path."""
+    m = _Marshalled(problem)
+    xx = (ctypes.c_double * 3)(*[float(v) for v in x])
+    kk = (ctypes.c_double * 3)(*[float(v) for v in k])
+    ox = (ctypes.c_double * 3)()
+    oc = ctypes.c_int64(-1)
+    ot = (ctypes.c_double * 2)()
+    f = lib().or_interaction(ctypes.byref(m.problem), xx, kk, int(start_cell), int(lam), float(u), ox,
+                             ctypes.byref(oc), ot)
+    return np.array(ox[:]), int(oc.value), float(ot[0]), float(ot[1]), int(f)

@@ -575,7 +575,8 @@ inline void shared_add(double* p, double v) {
 }
 
 // Accumulates into plain arrays (double runs).  With `shared_abs` set, the
-// absorption tallies of all threads go to one array (large grids).
+// absorption tallies of all threads go to one array (large grids); with
+// `shared_img` set, the images likewise (large frames).
 struct ArrayTally {
   const Problem* P;
   std::vector<std::vector<double>> images;
@@ -585,6 +586,8 @@ struct ArrayTally {
   bool want_abs = false, want_counts = false;
   double* shared_abs = nullptr;
   int64_t* shared_abs_counts = nullptr;
+  double* const* shared_img = nullptr;       // per instrument, the output images
+  int64_t* const* shared_img_counts = nullptr;
   NSum emitted, escaped, absorbed, truncated;
   uint64_t crossings = 0, events = 0, peeloffs = 0, packets = 0;
   std::vector<or_record>* records = nullptr;
@@ -594,7 +597,7 @@ struct ArrayTally {
     want_abs = abs;
     want_counts = counts;
     for (const Frame& f : prob.frames) {
-      size_t n = (size_t)f.channels * prob.n_lambda * f.ny * f.nx;
+      size_t n = shared_img ? 0 : (size_t)f.channels * prob.n_lambda * f.ny * f.nx;
       images.emplace_back(n, 0.0);
       image_counts.emplace_back(counts ? n : 0, 0);
     }
@@ -606,9 +609,15 @@ struct ArrayTally {
   void pixel(int q, int ch, int lam, int64_t pix, double value, uint64_t pid, int event) {
     const Frame& f = P->frames[q];
     size_t base = ((size_t)ch * P->n_lambda + lam) * f.ny * f.nx;
+    if (records && ch == 0) records->push_back({pid, lam, event, q, 0, pix, value});
+    if (shared_img) {
+      if (shared_img[q]) shared_add(&shared_img[q][base + pix], value);
+      if (shared_img_counts && shared_img_counts[q])
+        __atomic_fetch_add(&shared_img_counts[q][base + pix], 1, __ATOMIC_RELAXED);
+      return;
+    }
     images[q][base + pix] += value;
     if (want_counts) image_counts[q][base + pix] += 1;
-    if (records && ch == 0) records->push_back({pid, lam, event, q, 0, pix, value});
   }
   void absorb(int lam, int64_t cell, double value) {
     absorbed.add(value);
@@ -762,6 +771,54 @@ struct Transport {
   }
   T t_emitted = T(0.0), t_escaped = T(0.0), t_truncated = T(0.0);
 
+  // Step (a): the forced path from x along k to the grid boundary, its
+  // segments (segs) and cumulative optical depths tau[0..n]; returns tau_path.
+  T forced_path(const V3<T>& x, const V3d& k, int64_t cell, int lam) {
+    grid_path(P.grid, x, k, cell, segs);
+    tally_crossings += segs.size();
+    tau.assign(segs.size() + 1, T(0.0));
+    for (size_t i = 0; i < segs.size(); ++i)
+      tau[i + 1] = tau[i] + T(P.kappa[lam]) * rho(segs[i].cell) * (segs[i].s_out - segs[i].s_in);
+    return tau[segs.size()];
+  }
+
+  // Step (c): the segment of the forced path in which the cumulative optical
+  // depth first exceeds tau_star, and the path length s_star of the
+  // interaction, s_in + (tau_star - tau_before) / (kappa rho).  When rounding
+  // leaves tau_star at or above the path's optical depth (u at its upper end),
+  // the interaction is the end of the last segment that holds dust (the limit
+  // of the inversion as tau_star tends to tau_path); *fallback reports it.
+  size_t interaction(const T& tau_star, double kap, T& s_star, bool* fallback) {
+    size_t hit = segs.size();
+    for (size_t i = 0; i < segs.size(); ++i)
+      if (val(tau[i + 1]) > val(tau_star)) { hit = i; break; }
+    if (fallback) *fallback = hit == segs.size();
+    if (hit == segs.size()) {
+      hit = 0;
+      for (size_t i = 0; i < segs.size(); ++i) if (val(tau[i + 1]) > val(tau[i])) hit = i;
+      s_star = segs[hit].s_out;
+    } else {
+      s_star = segs[hit].s_in + (tau_star - tau[hit]) / (T(kap) * rho(segs[hit].cell));
+    }
+    return hit;
+  }
+
+  // Move x along k by s_star and keep it inside the interaction cell (the
+  // point lies in that cell's segment; rounding of x + s_star k may put it a
+  // few ulps outside).  *clamped reports whether a coordinate was moved.
+  void move_to(V3<T>& x, const V3d& k, const T& s_star, int64_t cell, bool* clamped) {
+    x = {x.x + s_star * T(k.x), x.y + s_star * T(k.y), x.z + s_star * T(k.z)};
+    Box b = P.grid.cell_box(cell);
+    bool moved = false;
+    for (int a = 0; a < 3; ++a) {
+      T xa = comp(x, a);
+      if (val(xa) < b.lo[a]) { xa = T(b.lo[a]); moved = true; }
+      if (val(xa) > b.hi[a]) { xa = T(b.hi[a]); moved = true; }
+      set_comp(x, a, xa);
+    }
+    if (clamped) *clamped = moved;
+  }
+
   void run_packet(uint64_t pid, int lam) {
     double Ltot = 0.0;
     for (size_t s = 0; s < P.sources.size(); ++s) Ltot += P.lum[s * P.n_lambda + lam];
@@ -777,12 +834,7 @@ struct Transport {
     if (O.peel_emission) peel(x, cell, lam, L, false, k, pid, 0);
     for (int j = 1;; ++j) {
       // (a) the forced path to the boundary
-      grid_path(P.grid, x, k, cell, segs);
-      tally_crossings += segs.size();
-      tau.assign(segs.size() + 1, T(0.0));
-      for (size_t i = 0; i < segs.size(); ++i)
-        tau[i + 1] = tau[i] + T(kap) * rho(segs[i].cell) * (segs[i].s_out - segs[i].s_in);
-      const T tau_path = tau[segs.size()];
+      const T tau_path = forced_path(x, k, cell, lam);
       if (val(tau_path) <= 0.0) {
         trace_row(j, -1, x, k, L, 0.0, 0.0);
         t_escaped = t_escaped + L;
@@ -801,27 +853,10 @@ struct Transport {
       double u[4];
       draw4(pid, lam, j, 0, O.seed, O.model_id, u);
       const T tau_star = -log1p(-T(u[0]) * one_minus_E);
-      size_t hit = segs.size();
-      for (size_t i = 0; i < segs.size(); ++i)
-        if (val(tau[i + 1]) > val(tau_star)) { hit = i; break; }
       T s_star;
-      if (hit == segs.size()) {  // rounding fallback: end of the last dusty segment
-        hit = 0;
-        for (size_t i = 0; i < segs.size(); ++i) if (val(tau[i + 1]) > val(tau[i])) hit = i;
-        s_star = segs[hit].s_out;
-      } else {
-        s_star = segs[hit].s_in + (tau_star - tau[hit]) / (T(kap) * rho(segs[hit].cell));
-      }
-      x = {x.x + s_star * T(k.x), x.y + s_star * T(k.y), x.z + s_star * T(k.z)};
+      const size_t hit = interaction(tau_star, kap, s_star, nullptr);
       cell = segs[hit].cell;
-      // keep the position inside the interaction cell
-      Box b = P.grid.cell_box(cell);
-      for (int a = 0; a < 3; ++a) {
-        T xa = comp(x, a);
-        if (val(xa) < b.lo[a]) xa = T(b.lo[a]);
-        if (val(xa) > b.hi[a]) xa = T(b.hi[a]);
-        set_comp(x, a, xa);
-      }
+      move_to(x, k, s_star, cell, nullptr);
       // (d) scattered weight and peel-off
       L = T(alb) * L * one_minus_E;
       trace_row(j, cell, x, k, L, val(tau_path), val(tau_star));
@@ -921,23 +956,33 @@ int32_t or_run(const or_problem* prob, const or_opts* opts, or_output* out) {
   Problem P = make_problem(*prob);
   const or_opts& O = *opts;
   const int64_t n_total = total_packets(P, O);
-  int n_threads = std::max(1, O.n_threads);
-  if (out->records) n_threads = 1;  // records keep packet order
+  const int n_threads = std::max(1, O.n_threads);
   const bool want_abs = out->absorption != nullptr;
   const bool want_counts = out->image_counts != nullptr || out->absorption_counts != nullptr;
   std::vector<ArrayTally> tallies((size_t)n_threads);
-  std::vector<std::vector<or_record>> recs(1);
+  // peel-off records per thread, concatenated in thread order
+  std::vector<std::vector<or_record>> recs((size_t)n_threads);
   // private absorption arrays per thread unless that needs more than 2 GiB
   const double abs_bytes = (double)P.n_lambda * (double)P.grid.n_cells() * (want_counts ? 16.0 : 8.0);
   const bool shared = want_abs && n_threads > 1 && abs_bytes * n_threads > 2.0 * (1 << 30);
+  // likewise one set of images for all threads when private ones would need
+  // more than 2 GiB
+  double img_bytes = 0.0;
+  for (const Frame& f : P.frames) img_bytes += (double)f.channels * P.n_lambda * f.ny * f.nx * (want_counts ? 16.0 : 8.0);
+  const bool shared_images = n_threads > 1 && out->images && img_bytes * n_threads > 2.0 * (1 << 30);
   for (int t = 0; t < n_threads; ++t) {
     if (shared) {
       tallies[t].shared_abs = out->absorption;
       tallies[t].shared_abs_counts = out->absorption_counts;
     }
+    if (shared_images) {
+      tallies[t].shared_img = out->images;
+      tallies[t].shared_img_counts = want_counts ? out->image_counts : nullptr;
+    }
     tallies[t].init(P, want_abs, want_counts);
   }
-  if (out->records) tallies[0].records = &recs[0];
+  if (out->records)
+    for (int t = 0; t < n_threads; ++t) tallies[t].records = &recs[(size_t)t];
   // static interleaved chunks: deterministic for a given thread count
   const int64_t chunk = 64;
   auto worker = [&](int tid) {
@@ -973,7 +1018,7 @@ int32_t or_run(const or_problem* prob, const or_opts* opts, or_output* out) {
     ArrayTally& T = tallies[t];
     em.add(T.emitted.value()); es.add(T.escaped.value()); ab.add(T.absorbed.value()); tr.add(T.truncated.value());
     cr += T.crossings; ev += T.events; pe += T.peeloffs; pk += T.packets;
-    for (size_t q = 0; q < P.frames.size(); ++q) {
+    for (size_t q = 0; q < P.frames.size() && !shared_images; ++q) {
       if (out->images && out->images[q]) {
         double* dst = out->images[q];
         for (size_t i = 0; i < T.images[q].size(); ++i) dst[i] += T.images[q][i];
@@ -992,9 +1037,13 @@ int32_t or_run(const or_problem* prob, const or_opts* opts, or_output* out) {
   out->stats[0] += em.value(); out->stats[1] += es.value(); out->stats[2] += ab.value(); out->stats[3] += tr.value();
   out->counters[0] += cr; out->counters[1] += ev; out->counters[2] += pe; out->counters[3] += pk;
   if (out->records) {
-    int64_t n = std::min<int64_t>((int64_t)recs[0].size(), out->records_cap);
-    std::memcpy(out->records, recs[0].data(), (size_t)n * sizeof(or_record));
-    out->records_n = (int64_t)recs[0].size();
+    int64_t n = 0;
+    for (const auto& r : recs) {
+      const int64_t take = std::min<int64_t>((int64_t)r.size(), std::max<int64_t>(0, out->records_cap - n));
+      if (take > 0) std::memcpy(out->records + n, r.data(), (size_t)take * sizeof(or_record));
+      n += (int64_t)r.size();
+    }
+    out->records_n = n;
   }
   return 0;
 }
@@ -1011,6 +1060,39 @@ int64_t or_trace(const or_problem* prob, const or_opts* opts, uint64_t pid, int3
   t.run_packet(pid, lam);
   for (int64_t i = 0; i < (int64_t)tr.size() && i < cap; ++i) rows[i] = tr[(size_t)i];
   return (int64_t)tr.size();
+}
+
+// One forced path and its interaction (steps a and c of the per-packet
+// algorithm) for a given uniform u, from x along k (start_cell >= 0: x lies in
+// that cell): out_x[3] the interaction point, *out_cell its cell, *out_tau =
+// {tau_path, tau_star}; returns flags: bit 0 the rounding fallback of the
+// inversion acted, bit 1 the position was moved into the interaction cell,
+// bit 2 the path holds no dust (nothing else is written).
+int32_t or_interaction(const or_problem* prob, const double x[3], const double k[3], int64_t start_cell,
+                       int32_t lam, double u, double out_x[3], int64_t* out_cell, double out_tau[2]) {
+  Problem P = make_problem(*prob);
+  or_opts O;
+  std::memset(&O, 0, sizeof O);
+  O.n_per_lambda = 1;
+  O.n_norm = 1;
+  ArrayTally T;
+  T.init(P, false, false);
+  Transport<double, ArrayTally> tr(P, O, DensityOf<double>{&P.grid}, T);
+  V3d xv{x[0], x[1], x[2]}, kv{k[0], k[1], k[2]};
+  const double tau_path = tr.forced_path(xv, kv, start_cell, lam);
+  if (!(tau_path > 0.0)) return 4;
+  const double one_minus_E = -std::expm1(-tau_path);
+  const double tau_star = -std::log1p(-u * one_minus_E);
+  double s_star = 0.0;
+  bool fallback = false, clamped = false;
+  const size_t hit = tr.interaction(tau_star, P.kappa[lam], s_star, &fallback);
+  const int64_t cell = tr.segs[hit].cell;
+  tr.move_to(xv, kv, s_star, cell, &clamped);
+  out_x[0] = xv.x; out_x[1] = xv.y; out_x[2] = xv.z;
+  *out_cell = cell;
+  out_tau[0] = tau_path;
+  out_tau[1] = tau_star;
+  return (fallback ? 1 : 0) | (clamped ? 2 : 0);
 }
 
 // Vector-Jacobian product by forward-mode dual numbers, one seeded cell at a

@@ -331,7 +331,7 @@ def _spread3(v):
 
 
 def clumpy_octree(n_particles=1_000_000, n_samples=100_000_000, target_leaves=5_000_000, max_level=10, seed=3,
-                  n_lambda=20, n_pix=1024, n_packets_total=200_000_000, half=20.0, chunk=10_000_000):
+                  n_lambda=20, n_pix=1024, n_packets_total=200_000_000, half=20.0, chunk=10_000_000, channels=1):
     """Clumpy dust on an adaptive octree (Sect. 2.4).
 
     ``n_particles`` Gaussian clumps: centres drawn from a double-exponential
@@ -420,7 +420,8 @@ def clumpy_octree(n_particles=1_000_000, n_samples=100_000_000, target_leaves=5_
     grid, llo, lhi = build_octree([-half, half] * 3, refine, leaf_value, max_level)
     wl = np.geomspace(0.15, 2.2, n_lambda)
     kappa, albedo, g = synthetic_optics(wl, 0.5 * 2 * math.pi * 6.0 ** 2)
-    instr = [Instrument(math.radians(inc), -math.pi / 2, 0.0, n_pix, n_pix, half, half) for inc in (0.0, 90.0)]
+    instr = [Instrument(math.radians(inc), -math.pi / 2, 0.0, n_pix, n_pix, half, half, channels=channels)
+             for inc in (0.0, 90.0)]
     return Problem(
         name=f"clumpy_octree_{grid.n_cells}",
         grid=grid, wavelengths=wl, kappa=kappa, albedo=albedo, g=g,

@@ -62,9 +62,17 @@ def _keys(rec):
             + rec["event"].astype(np.uint64)) * np.uint64(64) + rec["instr"].astype(np.uint64)
 
 
+def _channel_of(event):
+    """Channel of a peel-off in a 3-channel frame: 1 direct (emission), 2 scattered."""
+    return np.where(np.asarray(event) == 0, 1, 2)
+
+
 def flip_corrected_images(gpu, ora, problem):
-    """GPU total-channel images with every contribution whose pixel differs from
-    the oracle's moved to the oracle's pixel.  Returns (images, report)."""
+    """GPU images (every channel) with every contribution whose pixel differs
+    from the oracle's moved to the oracle's pixel, every GPU-only record
+    removed and every oracle-only record added.  Returns (images, report);
+    report["touched"] lists, per instrument, the flat bins
+    (channel, lambda * ny * nx + pixel) that a correction changed."""
     g, o = gpu["records"], ora["records"]
     assert gpu["records_total"] == len(g) and ora["records_total"] == len(o), "record buffer overflow"
     kg, ko = _keys(g), _keys(o)
@@ -73,17 +81,25 @@ def flip_corrected_images(gpu, ora, problem):
     flip = g["pixel"][ig] != o["pixel"][io]
     only_g = np.setdiff1d(np.arange(len(g)), ig)
     only_o = np.setdiff1d(np.arange(len(o)), io)
-    imgs = [im[0].copy() for im in gpu["images"]]  # total channel [n_lambda, ny, nx]
-    for sel_g, sel_o in ((ig[flip], io[flip]),):
-        for a, b in zip(sel_g, sel_o):
-            q, lam = g["instr"][a], g["lam"][a]
-            im = imgs[q][lam].reshape(-1)
-            im[g["pixel"][a]] -= g["value"][a]
-            im[o["pixel"][b]] += g["value"][a]
+    imgs = [im.copy() for im in gpu["images"]]  # [channels, n_lambda, ny, nx]
+    touched = [set() for _ in imgs]
+
+    def add(q, lam, event, pix, value):
+        im = imgs[q]
+        plane = im.shape[-2] * im.shape[-1]
+        chans = (0, int(_channel_of(event))) if im.shape[0] == 3 else (0,)
+        for ch in chans:
+            im[ch, lam].reshape(-1)[pix] += value
+            touched[q].add((ch, int(lam) * plane + int(pix)))
+
+    for a, b in zip(ig[flip], io[flip]):
+        q, lam, ev = g["instr"][a], g["lam"][a], g["event"][a]
+        add(q, lam, ev, g["pixel"][a], -g["value"][a])
+        add(q, lam, ev, o["pixel"][b], g["value"][a])
     for a in only_g:
-        imgs[g["instr"][a]][g["lam"][a]].reshape(-1)[g["pixel"][a]] -= g["value"][a]
+        add(g["instr"][a], g["lam"][a], g["event"][a], g["pixel"][a], -g["value"][a])
     for b in only_o:
-        imgs[o["instr"][b]][o["lam"][b]].reshape(-1)[o["pixel"][b]] += o["value"][b]
+        add(o["instr"][b], o["lam"][b], o["event"][b], o["pixel"][b], o["value"][b])
     rel = np.abs(g["value"][ig] - o["value"][io]) / np.maximum(np.abs(o["value"][io]), 1e-300)
     worst = np.argsort(rel)[::-1][:3]
     report = {"worst_records": [{"pid": int(o["pid"][io[w]]), "lam": int(o["lam"][io[w]]),
@@ -92,16 +108,21 @@ def flip_corrected_images(gpu, ora, problem):
                                 for w in worst if rel[w] > 1e-3],
               "records": int(len(o)), "flips": int(flip.sum()), "gpu_only": int(len(only_g)),
               "oracle_only": int(len(only_o)), "record_rel_p999": float(np.quantile(rel, 0.999)) if len(rel) else 0.0,
-              "record_rel_max": float(rel.max()) if len(rel) else 0.0}
+              "record_rel_max": float(rel.max()) if len(rel) else 0.0, "touched": touched}
     return imgs, report
 
 
 def bin_check(gpu_vals, ora_vals, counts, min_count=1000, rtol=1e-4):
+    """Bins with at least min_count oracle contributions must agree within rtol
+    (relative); returns the number of such bins, of violations and their flat
+    indices, and the largest relative difference."""
     mask = counts >= min_count
-    diff = np.abs(gpu_vals[mask] - ora_vals[mask])
-    rel = np.where(diff == 0, 0.0, diff / np.maximum(np.abs(ora_vals[mask]), 1e-300))
+    g, o = gpu_vals[mask], ora_vals[mask]
+    diff = np.abs(g - o)
+    rel = np.where(diff == 0, 0.0, diff / np.maximum(np.abs(o), 1e-300))
+    bad = np.flatnonzero(mask.reshape(-1))[rel > rtol]
     return {"bins": int(mask.sum()), "violations": int((rel > rtol).sum()),
-            "max_rel": float(rel.max()) if rel.size else 0.0}
+            "max_rel": float(rel.max()) if rel.size else 0.0, "violating": bad}
 
 
 def block_sum(a, b):
@@ -110,7 +131,39 @@ def block_sum(a, b):
     return a.reshape(a.shape[:-2] + (ny // b, b, nx // b, b)).sum(axis=(-3, -1))
 
 
-def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_records=True, block=8):
+def cell_groups(grid, block=4):
+    """Group id of every cell for coarser absorption bins: cartesian grids in
+    block^3 cubes of cells, octrees by the parent node of the leaf."""
+    if grid.kind == "cartesian":
+        nx, ny, nz = grid.shape
+        iz, iy, ix = np.meshgrid(np.arange(nz) // block, np.arange(ny) // block, np.arange(nx) // block,
+                                 indexing="ij")
+        gx, gy = (nx + block - 1) // block, (ny + block - 1) // block
+        return (ix + gx * (iy + gy * iz)).reshape(-1)
+    child = np.asarray(grid.child, dtype=np.int64)
+    groups = np.zeros(grid.n_cells, dtype=np.int64)
+    parents = np.flatnonzero(child >= 0)
+    for o in range(8):
+        kids = child[parents] + o
+        leaf = child[kids] < 0
+        groups[-child[kids[leaf]] - 1] = parents[leaf]
+    return groups
+
+
+def _grouped(a, groups):
+    n = int(groups.max()) + 1
+    return np.stack([np.bincount(groups, weights=np.asarray(a[l], dtype=np.float64), minlength=n)
+                     for l in range(a.shape[0])])
+
+
+def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_records=True, block=8,
+            groups=None):
+    """The acceptance rule, applied to every channel of every frame and to the
+    absorption field (per cell and wavelength, and per cell summed over the
+    wavelengths).  With records, the flip corrections are bounded: at most
+    1e-4 of the records plus 10 may be flipped, GPU-only or oracle-only, and
+    every bin that violates the rule before the correction must be one the
+    correction changed."""
     rep = {}
     st_g, st_o = gpu["stats"], ora["stats"]
     # emitted, escaped and absorbed relative to themselves; the truncated
@@ -119,32 +172,74 @@ def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_rec
     rep["totals_rel"] = (np.abs(st_g - st_o) / np.abs(scale).clip(1e-300)).tolist()
     img_tot_g = sum(im[0].sum() for im in gpu["images"])
     img_tot_o = sum(im[0].sum() for im in ora["images"])
-    rep["image_total_rel"] = float(abs(img_tot_g - img_tot_o) / img_tot_o)
+    rep["image_total_rel"] = float(abs(img_tot_g - img_tot_o) / img_tot_o) if img_tot_o else float(img_tot_g != 0)
     rep["absorption_total_rel"] = float(abs(gpu["absorption"].sum() - ora["absorption"].sum())
                                         / ora["absorption"].sum()) if ora["absorption"].sum() > 0 else 0.0
     rep["conservation_gpu"] = float(abs(st_g[0] - st_g[1] - st_g[2] - st_g[3]) / st_g[0])
     cg, co = gpu["counters"].astype(np.float64), ora["counters"].astype(np.float64)
     rep["crossings_rel"] = float(abs(cg[0] - co[0]) / co[0])
     rep["events_diff"] = int(cg[1] - co[1])
+    touched = None
     if use_records:
         imgs, rrep = flip_corrected_images(gpu, ora, problem)
+        touched = rrep.pop("touched")
         rep.update(rrep)
+        rep["corrections"] = rep["flips"] + rep["gpu_only"] + rep["oracle_only"]
+        rep["corrections_limit"] = 1e-4 * rep["records"] + 10
     else:
-        imgs = [im[0] for im in gpu["images"]]
+        imgs = gpu["images"]
     rep["pixels"] = []
+    unexplained = 0
     for q, im in enumerate(imgs):
-        raw = bin_check(gpu["images"][q][0], ora["images"][q][0], ora["image_counts"][q][0], min_count, rtol)
-        cor = bin_check(im, ora["images"][q][0], ora["image_counts"][q][0], min_count, rtol)
-        entry = {"raw": raw, "corrected": cor}
-        ny, nx = im.shape[-2:]
-        if block and ny % block == 0 and nx % block == 0:
-            entry["blocks"] = bin_check(block_sum(im, block), block_sum(ora["images"][q][0], block),
-                                        block_sum(ora["image_counts"][q][0], block), min_count, rtol)
-        rep["pixels"].append(entry)
+        for ch in range(im.shape[0]):
+            counts = ora["image_counts"][q][ch]
+            raw = bin_check(gpu["images"][q][ch], ora["images"][q][ch], counts, min_count, rtol)
+            cor = bin_check(im[ch], ora["images"][q][ch], counts, min_count, rtol)
+            entry = {"instrument": q, "channel": ch, "raw": raw, "corrected": cor}
+            if touched is not None:
+                entry["raw_unexplained"] = sum(1 for b in raw["violating"] if (ch, int(b)) not in touched[q])
+                unexplained += entry["raw_unexplained"]
+            for r in (raw, cor):
+                r["violating"] = r["violating"][:16].tolist()
+            ny, nx = im.shape[-2:]
+            if block and ny % block == 0 and nx % block == 0:
+                entry["blocks"] = bin_check(block_sum(im[ch], block), block_sum(ora["images"][q][ch], block),
+                                            block_sum(counts, block), min_count, rtol)
+            rep["pixels"].append(entry)
+    rep["raw_unexplained"] = unexplained
     rep["cells"] = bin_check(gpu["absorption"], ora["absorption"], ora["absorption_counts"], min_count, rtol)
+    rep["cells_all_lambda"] = bin_check(gpu["absorption"].sum(axis=0), ora["absorption"].sum(axis=0),
+                                        ora["absorption_counts"].sum(axis=0), min_count, rtol)
+    if groups is not None:
+        rep["cell_groups"] = bin_check(_grouped(gpu["absorption"], groups), _grouped(ora["absorption"], groups),
+                                       _grouped(ora["absorption_counts"], groups), min_count, rtol)
+    for key in ("cells", "cells_all_lambda", "cell_groups"):
+        if key not in rep:
+            continue
+        rep[key]["violating"] = rep[key]["violating"][:16].tolist()
+    for p in rep["pixels"]:
+        if "blocks" in p:
+            p["blocks"]["violating"] = p["blocks"]["violating"][:16].tolist()
     ok = (max(rep["totals_rel"]) <= tot_rtol and rep["image_total_rel"] <= tot_rtol
           and rep["absorption_total_rel"] <= tot_rtol and rep["cells"]["violations"] == 0
+          and rep["cells_all_lambda"]["violations"] == 0
+          and rep.get("cell_groups", {"violations": 0})["violations"] == 0
           and all(p["corrected"]["violations"] == 0 for p in rep["pixels"])
-          and all(p.get("blocks", {"violations": 0})["violations"] == 0 for p in rep["pixels"]))
+          and all(p.get("blocks", {"violations": 0})["violations"] == 0 for p in rep["pixels"])
+          and unexplained == 0
+          and (not use_records or rep["corrections"] <= rep["corrections_limit"]))
     rep["ok"] = bool(ok)
     return rep
+
+
+def summary(rep):
+    """One line of the counts a parity test checked (for the test log)."""
+    px = rep["pixels"]
+    return (f"bins: pixels {sum(p['corrected']['bins'] for p in px)} "
+            f"(channels {sorted({p['channel'] for p in px})}), blocks {sum(p.get('blocks', {'bins': 0})['bins'] for p in px)}, "
+            f"cells {rep['cells']['bins']}, cells over all wavelengths {rep['cells_all_lambda']['bins']}, "
+            f"cell groups {rep.get('cell_groups', {'bins': 0})['bins']}; "
+            f"records {rep.get('records', 0)}, flips {rep.get('flips', 0)}, gpu-only {rep.get('gpu_only', 0)}, "
+            f"oracle-only {rep.get('oracle_only', 0)} (limit {rep.get('corrections_limit', 0):.0f}); "
+            f"max rel: pixels {max((p['corrected']['max_rel'] for p in px), default=0):.2e}, "
+            f"cells {rep['cells']['max_rel']:.2e}; totals {max(rep['totals_rel']):.2e}")

@@ -1,5 +1,6 @@
 """GPU parity: the CUDA transport library against the FP64 oracle on the same
 seeded inputs and the same Philox streams, called through the C ABI."""
+import functools
 import math
 
 import numpy as np
@@ -18,21 +19,27 @@ import parity as PAR  # noqa: E402
 
 
 def _assert_ok(rep):
+    print(PAR.summary(rep))
     if not rep["ok"]:
         import json
         print("PARITY REPORT", json.dumps(rep, default=float))
     assert rep["ok"]
 
 
+@functools.lru_cache(maxsize=2)
+def _full(workload, channels=1):
+    """The full-size workload (generated once per test session)."""
+    return W.disk_galaxy(channels=channels) if workload == "disk_galaxy" else W.clumpy_octree(channels=channels)
+
+
 @pytest.mark.parametrize("n", [100_000, 1_000_000])
 def test_uniform_cube(n):
     """Plain method: 32^3 uniform cube, axis tau 1, albedo 0.6, g 0.5, 64^2
     face-on frame; 1e5 packets (the workload's size) and 1e6."""
-    prob = W.uniform_cube()
+    prob = W.uniform_cube(channels=3)
     g = PAR.gpu_run(prob, n, records_cap=12 * n)
     o = PAR.oracle_run(prob, n, records_cap=12 * n)
-    rep = PAR.compare(g, o, prob)
-    print(rep)
+    rep = PAR.compare(g, o, prob, groups=PAR.cell_groups(prob.grid))
     _assert_ok(rep)
     assert rep["pixels"][0]["corrected"]["bins"] >= (4 if n < 1_000_000 else 100)
     assert rep["pixels"][0]["blocks"]["bins"] >= 40
@@ -46,12 +53,11 @@ def test_uniform_cube(n):
 
 def test_disk_galaxy_reduced():
     """Several wavelengths and three frames (0, 60, 90 degrees) on a 64^3 disk."""
-    prob = W.disk_galaxy(n_cells=64, n_lambda=3, n_pix=64)
+    prob = W.disk_galaxy(n_cells=64, n_lambda=3, n_pix=64, channels=3)
     n = 20000
     g = PAR.gpu_run(prob, n, records_cap=6_000_000)
     o = PAR.oracle_run(prob, n, records_cap=6_000_000)
-    rep = PAR.compare(g, o, prob)
-    print(rep)
+    rep = PAR.compare(g, o, prob, groups=PAR.cell_groups(prob.grid))
     _assert_ok(rep)
     assert sum(p["corrected"]["bins"] for p in rep["pixels"]) > 100
 
@@ -66,7 +72,6 @@ def test_octree_parity():
     g = PAR.gpu_run(prob, n, records_cap=4_000_000)
     o = PAR.oracle_run(prob, n, records_cap=4_000_000)
     rep = PAR.compare(g, o, prob)
-    print(rep)
     _assert_ok(rep)
 
 
@@ -85,7 +90,7 @@ def test_special_cases(case):
     g = PAR.gpu_run(prob, n, records_cap=2_000_000)
     o = PAR.oracle_run(prob, n, records_cap=2_000_000)
     rep = PAR.compare(g, o, prob)
-    print(case, rep)
+    print(case)
     _assert_ok(rep)
     if case == "no_scattering":
         assert np.all(g["images"][0][2] == 0.0) and g["stats"][3] == 0.0
@@ -100,7 +105,6 @@ def test_bilinear_count_only_termination():
     g = PAR.gpu_run(prob, n)
     o = PAR.oracle_run(prob, n)
     rep = PAR.compare(g, o, prob, use_records=False)
-    print(rep)
     _assert_ok(rep)
 
 
@@ -322,7 +326,6 @@ def test_clumpy_octree_small():
     g = PAR.gpu_run(prob, n, records_cap=8_000_000)
     o = PAR.oracle_run(prob, n, records_cap=8_000_000)
     rep = PAR.compare(g, o, prob)
-    print(rep)
     _assert_ok(rep)
     assert rep["crossings_rel"] < 1e-4
     assert rep["flips"] + rep["gpu_only"] + rep["oracle_only"] <= 1e-4 * rep["records"] + 10
@@ -334,7 +337,7 @@ def test_full_size_sampled_packets(workload):
     transported; the peel-off records of a sample of packet ids (every
     1e6-th) are compared one by one with the oracle run on those ids, and
     luminosity is conserved."""
-    prob = W.disk_galaxy() if workload == "disk_galaxy" else W.clumpy_octree()
+    prob = _full(workload)
     n = prob.run.n_per_lambda
     stride = 1_000_000
     g = PAR.gpu_run(prob, n, records_cap=2_000_000, record_stride=stride)
@@ -364,3 +367,32 @@ def test_full_size_sampled_packets(workload):
           "p99 rel", np.quantile(sel, 0.99))
     assert np.median(sel) < 1e-5
     assert np.quantile(sel, 0.99) < 1e-3
+
+
+@pytest.mark.parametrize("workload,n_ids", [("disk_galaxy", 100_000), ("clumpy_octree", 2_000)])
+def test_full_resolution_on_the_first_packet_ids(workload, n_ids):
+    """The full-size workload (disk galaxy: 256^3 cells, 10 wavelengths, three
+    512^2 frames; clumpy octree: 5e6 leaves, 20 wavelengths, two 1024^2
+    frames), direct and scattered channels on, in the bench's launch
+    configuration, restricted to the first n_ids packet ids of every
+    wavelength with the full workload's packet weights; the oracle runs the
+    same ids.  Every peel-off record is matched, and every bin that holds at
+    least 1e3 of the oracle's contributions -- pixels, 8 x 8 pixel blocks,
+    cells, cells summed over the wavelengths, 4^3-cell blocks (octree: the
+    leaves of one parent) -- agrees within 1e-4."""
+    prob = _full(workload, channels=3)
+    n_norm = prob.run.n_per_lambda
+    cap = 24 * n_ids * prob.n_lambda
+    g = PAR.gpu_run(prob, n_ids, n_norm=n_norm, records_cap=cap)
+    o = PAR.oracle_run(prob, n_ids, n_norm=n_norm, records_cap=cap)
+    assert g["raw_stats"]["device_flags"] == 0
+    if workload == "disk_galaxy":
+        assert g["raw_stats"]["sorted_peels"] > 0 and g["raw_stats"]["column_peels"] > 0
+    rep = PAR.compare(g, o, prob, groups=PAR.cell_groups(prob.grid))
+    _assert_ok(rep)
+    checked = (sum(p["corrected"]["bins"] + p.get("blocks", {"bins": 0})["bins"] for p in rep["pixels"])
+               + rep["cells"]["bins"] + rep["cells_all_lambda"]["bins"] + rep["cell_groups"]["bins"])
+    assert checked >= 100
+    assert all(p.get("blocks", {"bins": 1})["bins"] > 0 for p in rep["pixels"] if p["channel"] == 0)
+    assert rep["cell_groups"]["bins"] > 0
+    assert rep["crossings_rel"] < 1e-4

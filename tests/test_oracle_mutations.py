@@ -41,6 +41,16 @@ MUTATIONS = {
     # backward scattering swapped after the first event)
     "scatter_g_sign": ("return rotate_dir(k, hg_sample(g, u1), 2.0 * M_PI * u2);",
                        "return rotate_dir(k, hg_sample(-g, u1), 2.0 * M_PI * u2);", "test_oracle_analog.py"),
+    # rounding fallback of the inversion placed at the end of the path instead
+    # of the end of the last dusty segment
+    "fallback_last_segment": ("for (size_t i = 0; i < segs.size(); ++i) if (val(tau[i + 1]) > val(tau[i])) hit = i;",
+                              "hit = segs.size() - 1;", "test_oracle_interaction.py"),
+    # interaction point left where rounding put it (no move into its cell)
+    "no_cell_clamp": ("      set_comp(x, a, xa);\n    }\n    if (clamped)", "    }\n    if (clamped)",
+                      "test_oracle_interaction.py"),
+    # inversion remainder measured from the segment's far end
+    "inversion_remainder": ("(tau_star - tau[hit]) / (T(kap)", "(tau_star - tau[hit + 1]) / (T(kap)",
+                            "test_oracle_interaction.py"),
     # derivative of exp with the wrong sign
     "dual_exp_sign": ("inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, e * a.d}; }",
                       "inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, -e * a.d}; }",
