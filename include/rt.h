@@ -67,7 +67,7 @@ enum {
 
 enum { RT_GRID_CARTESIAN = 0, RT_GRID_OCTREE = 1 };
 enum { RT_SOURCE_POINT = 0, RT_SOURCE_EXPDISK = 1, RT_SOURCE_PLUMMER = 2 };
-enum { RT_DEPOSIT_NEAREST = 0, RT_DEPOSIT_BILINEAR = 1 };
+enum { RT_DEPOSIT_NEAREST = 0, RT_DEPOSIT_BILINEAR = 1, RT_DEPOSIT_SED = 2 };
 
 /* Dust grid (Sect. 2.2: constant density per cell; Sect. 2.4: grid kinds).
  *   kind RT_GRID_CARTESIAN: nx*ny*nz equal cells spanning `bounds`;
@@ -106,7 +106,11 @@ typedef struct {
 } rt_source_desc;
 
 /* Frame instrument with parallel projection (Sect. 2.2; the parameters of
- * the FrameInstrument of the Sect. 2.5 example).  Direction to the observer
+ * the FrameInstrument of the Sect. 2.5 example), or SED instrument
+ * (deposit = RT_DEPOSIT_SED; Sect. 2.2: the spectral energy distribution of
+ * the flux received from the viewing direction): every peel-off towards it
+ * is summed per wavelength, wherever it starts; nx = ny = 1, the half widths
+ * and field centre are not used, and the layout is [channels][n_lambda].  Direction to the observer
  * k = (sin i cos a, sin i sin a, cos i); image axes before the position angle
  * w: ex = (-sin a, cos a, 0), ey = (-cos i cos a, -cos i sin a, sin i); the
  * position angle turns them to cos w ex - sin w ey and sin w ex + cos w ey.
@@ -119,7 +123,7 @@ typedef struct {
   int32_t nx, ny;
   double half_x, half_y;
   double center_x, center_y;
-  int32_t deposit;   /* RT_DEPOSIT_NEAREST or RT_DEPOSIT_BILINEAR (pixel centres) */
+  int32_t deposit;   /* RT_DEPOSIT_NEAREST, RT_DEPOSIT_BILINEAR (pixel centres) or RT_DEPOSIT_SED */
   int32_t channels;  /* 1 or 3 */
 } rt_instrument_desc;
 
@@ -243,7 +247,8 @@ rt_status rt_add_sources(rt_ctx ctx, int32_t n, const rt_source_desc* sources);
 
 /* Append n frame instruments (Sect. 2.2); at most 16 in total.  ids (may be
  * NULL) receives their indices.  Allocates and zeroes their images.
- * Errors: RT_ERR_ARG (pixels <= 0, half widths <= 0, channels not 1 or 3),
+ * Errors: RT_ERR_ARG (pixels <= 0, half widths <= 0 for a frame, an SED
+ * instrument with nx or ny other than 1, channels not 1 or 3),
  * RT_ERR_STATE (no optics), RT_ERR_OOM. */
 rt_status rt_add_instruments(rt_ctx ctx, int32_t n, const rt_instrument_desc* instruments, int32_t* ids);
 

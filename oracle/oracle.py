@@ -59,7 +59,8 @@ class OrInstrument(ctypes.Structure):
                 ("position_angle", ctypes.c_double), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("half_x", ctypes.c_double), ("half_y", ctypes.c_double),
                 ("center_x", ctypes.c_double), ("center_y", ctypes.c_double),
-                ("bilinear", ctypes.c_int32), ("channels", ctypes.c_int32)]
+                ("bilinear", ctypes.c_int32), ("channels", ctypes.c_int32), ("sed", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class OrProblem(ctypes.Structure):
@@ -220,6 +221,7 @@ def make_instrument(q) -> OrInstrument:
     oi.center_x, oi.center_y = float(q.center_x), float(q.center_y)
     oi.bilinear = int(bool(q.bilinear))
     oi.channels = int(q.channels)
+    oi.sed = int(bool(getattr(q, "sed", False)))
     return oi
 
 

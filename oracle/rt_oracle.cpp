@@ -188,6 +188,8 @@ typedef struct {
   double center_x, center_y;  // field centre in the image plane
   int32_t bilinear;           // 0 = nearest pixel, 1 = bilinear
   int32_t channels;           // 1 = total; 3 = total, direct, scattered
+  int32_t sed;                // 1 = SED instrument: one bin per wavelength, no projection
+  int32_t pad;
 } or_instrument;
 
 typedef struct {
@@ -265,6 +267,7 @@ struct Frame {
   double half_x, half_y, cx, cy;
   bool bilinear;
   int channels;
+  bool sed;
 };
 
 // Sines and cosines of the frame angles within 1e-15 of 0 or +-1 are taken
@@ -292,6 +295,7 @@ Frame make_frame(const or_instrument& in) {
   f.cx = in.center_x; f.cy = in.center_y;
   f.bilinear = in.bilinear != 0;
   f.channels = in.channels;
+  f.sed = in.sed != 0;
   return f;
 }
 
@@ -731,6 +735,13 @@ struct Transport {
       if (scattered) w = w * T(hg_phase(P.g[lam], k.x * f.kobs.x + k.y * f.kobs.y + k.z * f.kobs.z));
       T value = w * exp(-optical_depth(x, f.kobs, cell, lam, tally_crossings));
       tally_peeloffs += 1;
+      if (f.sed) {
+        // SED instrument (Sect. 2.2): the flux received from direction k_obs
+        // per wavelength, wherever the peel-off starts
+        tally.pixel((int)q, 0, lam, 0, value, pid, event);
+        if (f.channels == 3) tally.pixel((int)q, scattered ? 2 : 1, lam, 0, value, pid, event);
+        continue;
+      }
       T xp = x.x * T(f.ex.x) + x.y * T(f.ex.y) + x.z * T(f.ex.z) - T(f.cx);
       T yp = x.x * T(f.ey.x) + x.y * T(f.ey.y) + x.z * T(f.ey.z) - T(f.cy);
       T fx = (xp + T(f.half_x)) * T(f.nx / (2.0 * f.half_x));

@@ -165,6 +165,7 @@ __device__ __forceinline__ float adj_weight(const AdjParams& A, int q, int lam, 
   const float* a1 = I.channels == 3 ? img + ((size_t)(scattered ? 2 : 1) * A.f.n_lambda + lam) * plane : nullptr;
   const float fx = (x.x * I.ex[0] + x.y * I.ex[1] + x.z * I.ex[2] + I.off_x) * I.sx;
   const float fy = (x.x * I.ey[0] + x.y * I.ey[1] + x.z * I.ey[2] + I.off_y) * I.sy;
+  if (I.sed) return a0[0] + (a1 ? a1[0] : 0.0f);  // one bin, independent of x
   auto at = [&](float fix, float fiy) -> float {
     if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) return 0.0f;
     const size_t pix = (size_t)(int)fiy * I.nx + (int)fix;

@@ -329,6 +329,7 @@ rt_status upload_tables(rt_ctx c, cudaStream_t s) {
     I.sy = (float)(d.ny / (2.0 * d.half_y));
     I.nx = d.nx; I.ny = d.ny;
     I.bilinear = d.deposit == RT_DEPOSIT_BILINEAR;
+    I.sed = d.deposit == RT_DEPOSIT_SED;
     I.channels = d.channels;
     I.image = c->instr[q].d_image;
     int axis = 0, dir = 0;
@@ -692,10 +693,13 @@ rt_status rt_add_instruments(rt_ctx c, int32_t n, const rt_instrument_desc* q, i
     const rt_instrument_desc& d = q[i];
     if (d.nx <= 0 || d.ny <= 0 || (long long)d.nx * d.ny > (1ll << 28))
       return fail(c, RT_ERR_ARG, "instrument %d: bad pixel counts", i);
-    if (!(d.half_x > 0 && d.half_y > 0)) return fail(c, RT_ERR_ARG, "instrument %d: half widths must be > 0", i);
-    if (d.channels != 1 && d.channels != 3) return fail(c, RT_ERR_ARG, "instrument %d: channels must be 1 or 3", i);
-    if (d.deposit != RT_DEPOSIT_NEAREST && d.deposit != RT_DEPOSIT_BILINEAR)
+    if (d.deposit != RT_DEPOSIT_NEAREST && d.deposit != RT_DEPOSIT_BILINEAR && d.deposit != RT_DEPOSIT_SED)
       return fail(c, RT_ERR_ARG, "instrument %d: unknown deposit mode", i);
+    if (d.deposit == RT_DEPOSIT_SED && (d.nx != 1 || d.ny != 1))
+      return fail(c, RT_ERR_ARG, "instrument %d: an SED instrument has nx = ny = 1", i);
+    if (d.deposit != RT_DEPOSIT_SED && !(d.half_x > 0 && d.half_y > 0))
+      return fail(c, RT_ERR_ARG, "instrument %d: half widths must be > 0", i);
+    if (d.channels != 1 && d.channels != 3) return fail(c, RT_ERR_ARG, "instrument %d: channels must be 1 or 3", i);
     if (!(is_finite(d.inclination) && is_finite(d.azimuth) && is_finite(d.position_angle) && is_finite(d.center_x) &&
           is_finite(d.center_y)))
       return fail(c, RT_ERR_ARG, "instrument %d: non-finite angle or centre", i);

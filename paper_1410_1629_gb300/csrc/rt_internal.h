@@ -43,6 +43,7 @@ struct DevInstr {
   float sx, sy;        // pixels per unit length: n / (2 half)
   int nx, ny;
   int bilinear, channels;
+  int sed;             // SED instrument: one bin per wavelength, no projection
   double* image;       // [channels][n_lambda][ny][nx]
   // a frame looking exactly along grid axis `axis` (dir +-1): column[c] is the
   // density integral from the face of cell c that the ray leaves to the grid

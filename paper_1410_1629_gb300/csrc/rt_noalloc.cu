@@ -159,9 +159,10 @@ extern "C" rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t
   }
   for (int q = 0; q < n_instruments; ++q) {
     const rt_instrument_desc& d = instruments[q];
-    if (d.nx <= 0 || d.ny <= 0 || (long long)d.nx * d.ny > (1ll << 28) || !(d.half_x > 0 && d.half_y > 0) ||
-        (d.channels != 1 && d.channels != 3) || (d.deposit != RT_DEPOSIT_NEAREST && d.deposit != RT_DEPOSIT_BILINEAR) ||
-        !images[q])
+    const bool sed = d.deposit == RT_DEPOSIT_SED;
+    if (d.nx <= 0 || d.ny <= 0 || (long long)d.nx * d.ny > (1ll << 28) || (!sed && !(d.half_x > 0 && d.half_y > 0)) ||
+        (sed && (d.nx != 1 || d.ny != 1)) || (d.channels != 1 && d.channels != 3) ||
+        (d.deposit != RT_DEPOSIT_NEAREST && d.deposit != RT_DEPOSIT_BILINEAR && !sed) || !images[q])
       return fail(RT_ERR_ARG, "rt_launch_packets_noalloc: invalid instrument or null image");
   }
   rt_launch_opts o;
@@ -238,6 +239,7 @@ extern "C" rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t
     ins[q].nx = d.nx;
     ins[q].ny = d.ny;
     ins[q].bilinear = d.deposit == RT_DEPOSIT_BILINEAR;
+    ins[q].sed = d.deposit == RT_DEPOSIT_SED;
     ins[q].channels = d.channels;
     ins[q].image = images[q];
   }

@@ -647,10 +647,34 @@ __device__ __forceinline__ void deposit_peel(const FwdParams& P, int q, int lam,
   const float tau = th;
   const double value = tau < 80.0f ? L * widen(kInv4PiF * phase * expf(-tau) * (1.0f - tl))
                                    : L * kInv4PiD * (double)phase * exp(-((double)tau + (double)tl));
+  const int ch = scattered ? 2 : 1;
+  if (I.sed) {
+    // an SED instrument has one bin per wavelength and channel: the lanes of
+    // the warp that deposit into the same bin add their values first (in lane
+    // order) and one of them issues the atomics
+    const unsigned act = __activemask();
+    const unsigned key = ((unsigned)q << 20) | ((unsigned)lam << 1) | (scattered ? 1u : 0u);
+    const unsigned grp = __match_any_sync(act, key);
+    double sum = 0.0;
+    for (unsigned m = grp; m; m &= m - 1u) sum += __shfl_sync(grp, value, __ffs(m) - 1);
+    if ((int)(threadIdx.x & 31u) == __ffs(grp) - 1) {
+      atomicAdd(&I.image[lam], sum);
+      if (I.channels == 3) atomicAdd(&I.image[(size_t)ch * P.n_lambda + lam], sum);
+    }
+    if (P.records && (P.record_stride <= 1 || pid % P.record_stride == 0)) {
+      const unsigned long long slot = atomicAdd(&P.counters[4], 1ull);
+      if ((long long)slot < P.records_cap) {
+        rt_record r;
+        r.packet = pid; r.lambda = lam; r.event = scattered ? event : 0; r.instrument = q;
+        r.reserved = 0; r.pixel = 0; r.value = value;
+        P.records[slot] = r;
+      }
+    }
+    return;
+  }
   const float fx = (x.x * I.ex[0] + x.y * I.ex[1] + x.z * I.ex[2] + I.off_x) * I.sx;
   const float fy = (x.x * I.ey[0] + x.y * I.ey[1] + x.z * I.ey[2] + I.off_y) * I.sy;
   const size_t plane = (size_t)I.ny * I.nx;
-  const int ch = scattered ? 2 : 1;
   if (!I.bilinear) {
     const float fix = floorf(fx), fiy = floorf(fy);
     if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) return;

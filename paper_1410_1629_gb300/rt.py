@@ -22,7 +22,7 @@ from . import build as _build
 RT_OK, RT_ERR_ARG, RT_ERR_STATE, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_DEVICE_FLAG = 0, -1, -2, -3, -4, -5, -6
 RT_GRID_CARTESIAN, RT_GRID_OCTREE = 0, 1
 RT_SOURCE_POINT, RT_SOURCE_EXPDISK, RT_SOURCE_PLUMMER = 0, 1, 2
-RT_DEPOSIT_NEAREST, RT_DEPOSIT_BILINEAR = 0, 1
+RT_DEPOSIT_NEAREST, RT_DEPOSIT_BILINEAR, RT_DEPOSIT_SED = 0, 1, 2
 
 _SOURCE_KIND = {"point": RT_SOURCE_POINT, "expdisk": RT_SOURCE_EXPDISK, "plummer": RT_SOURCE_PLUMMER}
 
@@ -444,7 +444,8 @@ def instrument_desc(q):
     d.nx, d.ny = int(q.nx), int(q.ny)
     d.half_x, d.half_y = float(q.half_x), float(q.half_y)
     d.center_x, d.center_y = float(q.center_x), float(q.center_y)
-    d.deposit = RT_DEPOSIT_BILINEAR if q.bilinear else RT_DEPOSIT_NEAREST
+    d.deposit = (RT_DEPOSIT_SED if getattr(q, "sed", False) else
+                 RT_DEPOSIT_BILINEAR if q.bilinear else RT_DEPOSIT_NEAREST)
     d.channels = int(q.channels)
     return d
 

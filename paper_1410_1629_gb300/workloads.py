@@ -65,7 +65,9 @@ class Source:
 class Instrument:
     """Frame instrument with parallel projection.  Angles in radians;
     ``half_x``/``half_y`` are half-widths of the field; ``channels`` is 1
-    (total) or 3 (total, direct, scattered)."""
+    (total) or 3 (total, direct, scattered).  ``sed``: an SED instrument
+    (one bin per wavelength: the flux received from the viewing direction,
+    wherever it comes from; nx = ny = 1, the field is not used)."""
     inclination: float
     azimuth: float
     position_angle: float
@@ -77,6 +79,7 @@ class Instrument:
     center_y: float = 0.0
     bilinear: bool = False
     channels: int = 1
+    sed: bool = False
 
 
 @dataclass
@@ -134,6 +137,11 @@ def synthetic_optics(wavelengths_um, kappa_v):
     albedo = np.clip(0.6 - 0.1 * x * x, 0.3, 0.8)
     g = np.clip(0.6 - 0.15 * x, 0.0, 0.9)
     return kappa, albedo, g
+
+
+def sed_instrument(inclination_deg, azimuth=-math.pi / 2, channels=3) -> Instrument:
+    """SED instrument viewing from inclination ``inclination_deg`` degrees."""
+    return Instrument(math.radians(inclination_deg), azimuth, 0.0, 1, 1, 1.0, 1.0, channels=channels, sed=True)
 
 
 def face_on(n, half, bilinear=False, channels=1) -> Instrument:

@@ -54,11 +54,19 @@ def test_uniform_cube(n):
 def test_disk_galaxy_reduced():
     """Several wavelengths and three frames (0, 60, 90 degrees) on a 64^3 disk."""
     prob = W.disk_galaxy(n_cells=64, n_lambda=3, n_pix=64, channels=3)
+    # SED instruments (one along a grid axis: column sums; one inclined:
+    # the sorted pass)
+    prob.instruments += [W.sed_instrument(90.0), W.sed_instrument(60.0)]
     n = 20000
-    g = PAR.gpu_run(prob, n, records_cap=6_000_000)
-    o = PAR.oracle_run(prob, n, records_cap=6_000_000)
+    g = PAR.gpu_run(prob, n, records_cap=8_000_000)
+    o = PAR.oracle_run(prob, n, records_cap=8_000_000)
     rep = PAR.compare(g, o, prob, groups=PAR.cell_groups(prob.grid))
     _assert_ok(rep)
+    for q in (3, 4):
+        sed_g, sed_o = g["images"][q][:, :, 0, 0], o["images"][q][:, :, 0, 0]
+        print("SED", q, np.abs(sed_g - sed_o).max() / np.abs(sed_o).max())
+        np.testing.assert_allclose(sed_g, sed_o, rtol=1e-6)
+        np.testing.assert_allclose(sed_g[0], sed_g[1] + sed_g[2], rtol=1e-12)
     assert sum(p["corrected"]["bins"] for p in rep["pixels"]) > 100
 
 

@@ -51,6 +51,9 @@ MUTATIONS = {
     # inversion remainder measured from the segment's far end
     "inversion_remainder": ("(tau_star - tau[hit]) / (T(kap)", "(tau_star - tau[hit + 1]) / (T(kap)",
                             "test_oracle_interaction.py"),
+    # SED instrument recording scattered light as direct
+    "sed_channel": ("if (f.channels == 3) tally.pixel((int)q, scattered ? 2 : 1, lam, 0, value, pid, event);",
+                    "if (f.channels == 3) tally.pixel((int)q, 1, lam, 0, value, pid, event);", "test_oracle_sed.py"),
     # derivative of exp with the wrong sign
     "dual_exp_sign": ("inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, e * a.d}; }",
                       "inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, -e * a.d}; }",
