@@ -65,13 +65,21 @@ enum {
   RT_ERR_DEVICE_FLAG = -6   /* a kernel's own bounds check fired; results are not valid        */
 };
 
-enum { RT_GRID_CARTESIAN = 0, RT_GRID_OCTREE = 1 };
+enum { RT_GRID_CARTESIAN = 0, RT_GRID_OCTREE = 1, RT_GRID_RECTILINEAR = 2 };
 enum { RT_SOURCE_POINT = 0, RT_SOURCE_EXPDISK = 1, RT_SOURCE_PLUMMER = 2 };
 enum { RT_DEPOSIT_NEAREST = 0, RT_DEPOSIT_BILINEAR = 1, RT_DEPOSIT_SED = 2 };
 
-/* Dust grid (Sect. 2.2: constant density per cell; Sect. 2.4: grid kinds).
+/* Dust grid (Sect. 2.2: constant density per cell; Sect. 2.4 and Table 1(d):
+ * grid kinds).
  *   kind RT_GRID_CARTESIAN: nx*ny*nz equal cells spanning `bounds`;
  *       density float32 [nz][ny][nx] (x fastest); cell id = ix + nx*(iy + ny*iz).
+ *   kind RT_GRID_RECTILINEAR: nx*ny*nz cuboidal cells between the strictly
+ *       increasing edges edges[0] [nx + 1], edges[1] [ny + 1], edges[2]
+ *       [nz + 1] (FP64; the first and last edges must equal `bounds`; they
+ *       must stay strictly increasing when rounded to FP32).  The PowCub
+ *       grid of Table 1(d) is the case of power-law spaced edges.  Density
+ *       and cell ids as for RT_GRID_CARTESIAN.  Not supported by rt_adjoint,
+ *       the adjoint tape, batches or rt_launch_packets_noalloc.
  *   kind RT_GRID_OCTREE: recursive 2x2x2 subdivision of `bounds` at box
  *       midpoints; child int32 [n_nodes], node 0 the root: child[n] >= 0 is
  *       the index of the first of n's eight contiguous children (octant
@@ -90,6 +98,7 @@ typedef struct {
   int64_t n_leaves;
   int32_t on_device;
   int32_t reserved;
+  const double* edges[3]; /* RT_GRID_RECTILINEAR: cell edges per axis (host or device, as on_device) */
 } rt_grid_desc;
 
 /* Emission component (Sect. 2.2 stellar system, Sect. 3.4 position sampling,

@@ -46,7 +46,8 @@ class OrGrid(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("nz", ctypes.c_int32), ("bounds", ctypes.c_double * 6),
                 ("density", ctypes.POINTER(ctypes.c_float)), ("n_nodes", ctypes.c_int64),
-                ("child", ctypes.POINTER(ctypes.c_int32)), ("n_leaves", ctypes.c_int64)]
+                ("child", ctypes.POINTER(ctypes.c_int32)), ("n_leaves", ctypes.c_int64),
+                ("edges", ctypes.POINTER(ctypes.c_double) * 3)]
 
 
 class OrSource(ctypes.Structure):
@@ -168,10 +169,15 @@ class _Marshalled:
         dens = np.ascontiguousarray(grid.density, dtype=np.float32).ravel()
         self.keep.append(dens)
         og.density = _ptr(dens, ctypes.c_float)
-        if grid.kind == "cartesian":
-            og.kind = 0
+        if grid.kind in ("cartesian", "rectilinear"):
+            og.kind = 0 if grid.kind == "cartesian" else 2
             nz, ny, nx = np.asarray(grid.density).shape
             og.nx, og.ny, og.nz = nx, ny, nz
+            if grid.kind == "rectilinear":
+                for a in range(3):
+                    e = np.ascontiguousarray(grid.edges[a], dtype=np.float64)
+                    self.keep.append(e)
+                    og.edges[a] = _ptr(e, ctypes.c_double)
         else:
             og.kind = 1
             child = np.ascontiguousarray(grid.child, dtype=np.int32)

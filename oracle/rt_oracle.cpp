@@ -164,13 +164,14 @@ template <class T> void set_comp(V3<T>& a, int axis, T v) {
 extern "C" {
 
 typedef struct {
-  int32_t kind;  // 0 = cartesian, 1 = octree
+  int32_t kind;  // 0 = cartesian, 1 = octree, 2 = rectilinear
   int32_t nx, ny, nz;
   double bounds[6];  // xmin, xmax, ymin, ymax, zmin, zmax
-  const float* density;  // cartesian [nz][ny][nx] (x fastest); octree: per leaf
+  const float* density;  // cartesian, rectilinear [nz][ny][nx] (x fastest); octree: per leaf
   int64_t n_nodes;
   const int32_t* child;  // octree: >= 0 first child index; < 0 leaf -(leaf+1)
   int64_t n_leaves;
+  const double* edges[3];  // rectilinear: cell edges per axis, n + 1 each
 } or_grid;
 
 typedef struct {
@@ -358,11 +359,13 @@ struct Grid {
   const int32_t* child;
   int64_t n_nodes, n_leaves;
   std::vector<Box> leaf_box;  // octree: box of every leaf
+  std::vector<double> edges[3];  // rectilinear: cell edges per axis
 
-  int64_t n_cells() const { return kind == 0 ? (int64_t)n[0] * n[1] * n[2] : n_leaves; }
+  int64_t n_cells() const { return kind == 1 ? n_leaves : (int64_t)n[0] * n[1] * n[2]; }
 
-  // Cartesian plane positions: lo + i * (hi - lo) / n.
-  double plane(int axis, int i) const { return lo[axis] + i * d[axis]; }
+  // Plane positions: cartesian lo + i * (hi - lo) / n; rectilinear the
+  // given edges (Table 1(d): PowCub grids space them by a power law).
+  double plane(int axis, int i) const { return kind == 2 ? edges[axis][(size_t)i] : lo[axis] + i * d[axis]; }
 
   Box cell_box(int64_t cell) const {
     if (kind == 1) return leaf_box[(size_t)cell];
@@ -415,11 +418,17 @@ struct Grid {
     }
   }
 
-  // Cartesian cell containing p (clamped into the grid).
+  // Cartesian or rectilinear cell containing p (clamped into the grid): on
+  // each axis the last cell whose lower plane is at or below p.
   int64_t cart_locate(const double p[3]) const {
     int64_t idx[3];
     for (int a = 0; a < 3; ++a) {
-      int64_t i = (int64_t)std::floor((p[a] - lo[a]) / d[a]);
+      int64_t i;
+      if (kind == 2) {
+        i = (int64_t)(std::upper_bound(edges[a].begin(), edges[a].end(), p[a]) - edges[a].begin()) - 1;
+      } else {
+        i = (int64_t)std::floor((p[a] - lo[a]) / d[a]);
+      }
       idx[a] = std::min<int64_t>(std::max<int64_t>(i, 0), n[a] - 1);
     }
     return idx[0] + n[0] * (idx[1] + (int64_t)n[1] * idx[2]);
@@ -461,8 +470,8 @@ void grid_path(const Grid& G, const V3<T>& x, const V3d& k, int64_t start_cell,
       t = (T(plane) - comp(x, entry_axis)) / T(ka);
     }
   }
-  if (G.kind == 0) {
-    // cartesian: indices of the current cell
+  if (G.kind != 1) {
+    // cartesian and rectilinear: indices of the current cell
     int64_t idx[3];
     if (cell >= 0) {
       idx[0] = cell % G.n[0]; idx[1] = (cell / G.n[0]) % G.n[1]; idx[2] = cell / ((int64_t)G.n[0] * G.n[1]);
@@ -548,6 +557,8 @@ Problem make_problem(const or_problem& in) {
   for (int a = 0; a < 3; ++a) { G.lo[a] = in.grid.bounds[2 * a]; G.hi[a] = in.grid.bounds[2 * a + 1]; }
   G.n[0] = in.grid.nx; G.n[1] = in.grid.ny; G.n[2] = in.grid.nz;
   for (int a = 0; a < 3; ++a) G.d[a] = G.kind == 0 ? (G.hi[a] - G.lo[a]) / G.n[a] : 0.0;
+  if (G.kind == 2)
+    for (int a = 0; a < 3; ++a) G.edges[a].assign(in.grid.edges[a], in.grid.edges[a] + G.n[a] + 1);
   G.density = in.grid.density;
   G.child = in.grid.child;
   G.n_nodes = in.grid.n_nodes;

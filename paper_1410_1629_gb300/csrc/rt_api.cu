@@ -80,6 +80,7 @@ struct rt_ctx_s {
   long long n_nodes = 0;
   float* d_density = nullptr;
   int32_t* d_child = nullptr;
+  float* d_edges = nullptr;  // rectilinear grids: FP32 edges, x then y then z (nx + ny + nz + 3)
   // optics
   int n_lambda = 0;
   std::vector<double> kappa, albedo, g;
@@ -232,6 +233,7 @@ void free_grid(rt_ctx c) {
   cudaDeviceSynchronize();  // no kernel may still read the released buffers
   pool_release(c, c->d_density, (size_t)c->n_cells * sizeof(float));
   pool_release(c, c->d_child, (size_t)c->n_nodes * sizeof(int32_t));
+  pool_release(c, c->d_edges, (size_t)(c->nx + c->ny + c->nz + 3) * sizeof(float));
   pool_release(c, c->d_absorption, (size_t)c->n_lambda * c->n_cells * sizeof(double));
   for (auto& p : c->d_columns) pool_release(c, p, (size_t)c->n_cells * sizeof(float));
   for (auto& p : c->d_line_dep) pool_release(c, p, (size_t)c->n_cells * sizeof(double));
@@ -569,10 +571,33 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
     if (!(is_finite(d->bounds[2 * a]) && is_finite(d->bounds[2 * a + 1]) && d->bounds[2 * a] < d->bounds[2 * a + 1]))
       return fail(c, RT_ERR_ARG, "rt_create_grid: bounds on axis %d are not increasing", a);
   long long n_cells = 0, n_nodes = 0;
-  if (d->kind == RT_GRID_CARTESIAN) {
+  std::vector<float> edges_f;
+  if (d->kind == RT_GRID_CARTESIAN || d->kind == RT_GRID_RECTILINEAR) {
     if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0) return fail(c, RT_ERR_ARG, "rt_create_grid: cell counts must be > 0");
     n_cells = (long long)d->nx * d->ny * d->nz;
     if (n_cells > (1ll << 31) - 1) return fail(c, RT_ERR_ARG, "rt_create_grid: more than 2^31-1 cells");
+  }
+  if (d->kind == RT_GRID_RECTILINEAR) {
+    // the edges: strictly increasing in FP64 and in FP32, ends equal to the bounds
+    const int n3[3] = {d->nx, d->ny, d->nz};
+    for (int a = 0; a < 3; ++a) {
+      if (!d->edges[a]) return fail(c, RT_ERR_ARG, "rt_create_grid: rectilinear grid without edges on axis %d", a);
+      std::vector<double> e((size_t)n3[a] + 1);
+      if (d->on_device) {
+        if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+        RT_CUDA(c, cudaMemcpy(e.data(), d->edges[a], e.size() * sizeof(double), cudaMemcpyDeviceToHost));
+      } else {
+        std::memcpy(e.data(), d->edges[a], e.size() * sizeof(double));
+      }
+      if (e.front() != d->bounds[2 * a] || e.back() != d->bounds[2 * a + 1])
+        return fail(c, RT_ERR_ARG, "rt_create_grid: edges on axis %d do not end at the bounds", a);
+      for (size_t i = 0; i < e.size(); ++i) {
+        if (!is_finite(e[i]) || (i > 0 && !(e[i] > e[i - 1] && (float)e[i] > (float)e[i - 1])))
+          return fail(c, RT_ERR_ARG, "rt_create_grid: edges on axis %d not strictly increasing (in FP32) at %zu", a, i);
+        edges_f.push_back((float)e[i]);
+      }
+    }
+  } else if (d->kind == RT_GRID_CARTESIAN) {
   } else if (d->kind == RT_GRID_OCTREE) {
     if (!d->child || d->n_nodes <= 0 || d->n_leaves <= 0)
       return fail(c, RT_ERR_ARG, "rt_create_grid: octree needs child[] and counts > 0");
@@ -607,6 +632,10 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
   const cudaMemcpyKind kind = d->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   RT_CUDA(c, pool_alloc(c, &c->d_density, (size_t)n_cells * sizeof(float)));
   RT_CUDA(c, cudaMemcpy(c->d_density, d->density, (size_t)n_cells * sizeof(float), kind));
+  if (d->kind == RT_GRID_RECTILINEAR) {
+    RT_CUDA(c, pool_alloc(c, &c->d_edges, edges_f.size() * sizeof(float)));
+    RT_CUDA(c, cudaMemcpy(c->d_edges, edges_f.data(), edges_f.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   if (d->kind == RT_GRID_OCTREE) {
     RT_CUDA(c, pool_alloc(c, &c->d_child, (size_t)n_nodes * sizeof(int32_t)));
     RT_CUDA(c, cudaMemcpy(c->d_child, child_host.data(), (size_t)n_nodes * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -844,6 +873,11 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   p.density = c->d_density;
   p.child = c->d_child;
   p.n_nodes = c->n_nodes;
+  if (c->grid_kind == RT_GRID_RECTILINEAR) {
+    p.edge[0] = c->d_edges;
+    p.edge[1] = c->d_edges + c->nx + 1;
+    p.edge[2] = c->d_edges + c->nx + c->ny + 2;
+  }
   p.n_cells = c->n_cells;
   p.n_lambda = c->n_lambda;
   p.n_sources = (int)c->sources.size();

@@ -1,0 +1,29 @@
+// Forward transport on rectilinear grids (cells between arbitrary edges per
+// axis; the PowCub grid of the SKIRT paper, Table 1(d)): the state-machine
+// kernel of rt_transport.cuh instantiated with the rectilinear cell walk.
+#include "rt_transport.cuh"
+
+namespace rtk {
+
+namespace {
+__global__ void __launch_bounds__(tr::kBlock, RT_FWD_MIN_BLOCKS) k_forward_rect(const FwdParams P) {
+  tr::forward_body<tr::RectGrid>(P);
+}
+}  // namespace
+
+cudaError_t launch_forward_rect(const FwdParams& p, int num_sms, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(p.work_counter, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward_rect, tr::kBlock, 0);
+  if (e != cudaSuccess) return e;
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  unsigned long long blocks = (unsigned long long)num_sms * per_sm;
+  const unsigned long long useful = (p.n_total + tr::kBlock - 1) / tr::kBlock;
+  if (blocks > useful) blocks = useful;
+  if (blocks < 1) blocks = 1;
+  k_forward_rect<<<(unsigned)blocks, tr::kBlock, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace rtk

@@ -78,6 +78,7 @@ struct FwdParams {
   const float* density;
   const int32_t* child;  // octree only
   long long n_nodes;     // octree only
+  const float* edge[3];  // rectilinear only: cell edges per axis, n + 1 each
   long long n_cells;
   // problem
   int n_lambda, n_sources, n_instr;
@@ -160,6 +161,7 @@ cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaS
 cudaError_t launch_columns(const float* density, int nx, int ny, int nz, int axis, int dir, float d, float* out,
                            cudaStream_t stream);
 cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t stream);
+cudaError_t launch_forward_rect(const FwdParams& p, int num_sms, cudaStream_t stream);
 // The sorted peel-off pass after a forward launch with p.peel set
 // (rt_forward.cu): scan of p.peel_hist (n_keys entries, tile totals in
 // tile_sum: (n_keys + 4095) / 4096 entries), the permutation that orders the

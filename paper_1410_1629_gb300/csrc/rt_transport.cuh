@@ -252,6 +252,95 @@ struct CartGrid {
   }
 };
 
+// ---------------------------------------------------------------- rectilinear grid
+// Cuboidal cells between increasing edges given per axis (Table 1(d): the
+// PowCub grid places them by a power law; Sect. 2.2: logarithmic and
+// power-law grids put smaller cells in the central areas).  The walk is the
+// cartesian one with the plane positions read from the edge arrays (FP32
+// copies of the FP64 edges); a position is located by binary search.
+struct RectGrid {
+  static constexpr bool kColumns = false;
+  using Cell = CartGrid::Cell;
+  using Walk = CartGrid::Walk;
+  struct Scratch {};
+
+  __device__ static __forceinline__ float edge(const FwdParams& P, int a, int i) { return __ldg(&P.edge[a][i]); }
+
+  // The cell along axis a that holds coordinate xa: the last i in [0, n) with
+  // edge[i] <= xa (clamped into the grid).
+  __device__ static __forceinline__ int locate(const FwdParams& P, int a, float xa, int n) {
+    const float* e = P.edge[a];
+    int lo = 0, hi = n - 1;  // answer in [lo, hi]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(&e[mid]) <= xa) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  }
+
+  __device__ static __forceinline__ bool init(const FwdParams& P, float3 x, float3 d, float3 id, bool known,
+                                              const Cell& c, Walk& w, Scratch&) {
+    w.t = 0.0f;
+    if (known) {
+      w.ix = c.ix; w.iy = c.iy; w.iz = c.iz;
+    } else {
+      int entry = -1;
+      float3 p = x;
+      if (!inside_box(P, x)) {
+        const float3 ik = make_float3(id.x != 0.0f ? id.x : RT_INF, id.y != 0.0f ? id.y : RT_INF,
+                                      id.z != 0.0f ? id.z : RT_INF);
+        if (!ray_box_entry(P, x, d, ik, w.t, entry)) return false;
+        p = make_float3(fmaf(w.t, d.x, x.x), fmaf(w.t, d.y, x.y), fmaf(w.t, d.z, x.z));
+      }
+      w.ix = locate(P, 0, p.x, P.nx);
+      w.iy = locate(P, 1, p.y, P.ny);
+      w.iz = locate(P, 2, p.z, P.nz);
+      if (entry == 0) w.ix = d.x > 0.0f ? 0 : P.nx - 1;
+      if (entry == 1) w.iy = d.y > 0.0f ? 0 : P.ny - 1;
+      if (entry == 2) w.iz = d.z > 0.0f ? 0 : P.nz - 1;
+    }
+    w.tx = id.x != 0.0f ? (edge(P, 0, w.ix + (id.x > 0.0f)) - x.x) * id.x : RT_INF;
+    w.ty = id.y != 0.0f ? (edge(P, 1, w.iy + (id.y > 0.0f)) - x.y) * id.y : RT_INF;
+    w.tz = id.z != 0.0f ? (edge(P, 2, w.iz + (id.z > 0.0f)) - x.z) * id.z : RT_INF;
+    w.cell = w.ix + P.nx * (w.iy + P.ny * w.iz);
+    return true;
+  }
+
+  __device__ static __forceinline__ float exit(const Walk& w, float3, float3, int& axis) {
+    return first_min(w.tx, w.ty, w.tz, axis);
+  }
+
+  __device__ static __forceinline__ bool advance(const FwdParams& P, float3 x, float3, float3 id, int axis, Walk& w,
+                                                 Scratch&) {
+    const bool bz = axis == 2, by = axis == 1;
+    const float ida = bz ? id.z : (by ? id.y : id.x);
+    const int step = ida > 0.0f ? 1 : -1;
+    const int ia = (bz ? w.iz : (by ? w.iy : w.ix)) + step;
+    const int na = bz ? P.nz : (by ? P.ny : P.nx);
+    if ((unsigned)ia >= (unsigned)na) return false;
+    w.cell += step * (bz ? P.nx * P.ny : (by ? P.nx : 1));
+    const float xa = bz ? x.z : (by ? x.y : x.x);
+    const float t_new = (edge(P, axis, ia + (step > 0)) - xa) * ida;
+    w.ix = (axis == 0) ? ia : w.ix;
+    w.iy = by ? ia : w.iy;
+    w.iz = bz ? ia : w.iz;
+    w.tx = (axis == 0) ? t_new : w.tx;
+    w.ty = by ? t_new : w.ty;
+    w.tz = bz ? t_new : w.tz;
+    return true;
+  }
+
+  __device__ static __forceinline__ int cell(const Walk& w) { return w.cell; }
+
+  __device__ static __forceinline__ Cell carried(const Walk& w) { return Cell{w.ix, w.iy, w.iz}; }
+
+  __device__ static __forceinline__ void clamp(const FwdParams& P, const Cell& c, float3& x) {
+    x.x = fminf(fmaxf(x.x, edge(P, 0, c.ix)), edge(P, 0, c.ix + 1));
+    x.y = fminf(fmaxf(x.y, edge(P, 1, c.iy)), edge(P, 1, c.iy + 1));
+    x.z = fminf(fmaxf(x.z, edge(P, 2, c.iz)), edge(P, 2, c.iz + 1));
+  }
+};
+
 // ---------------------------------------------------------------- octree grid
 // Nodes are split at box midpoints (Sect. 2.4); a point on a splitting plane
 // belongs to the child the ray enters (upper if d_a >= 0, lower if d_a < 0).
@@ -481,6 +570,8 @@ template <>
 __device__ __forceinline__ CartGrid::Cell& cell_slot<CartGrid>() { return S_CELL_CART[threadIdx.x]; }
 template <>
 __device__ __forceinline__ OctGrid::Cell& cell_slot<OctGrid>() { return S_CELL_OCT[threadIdx.x]; }
+template <>
+__device__ __forceinline__ RectGrid::Cell& cell_slot<RectGrid>() { return S_CELL_CART[threadIdx.x]; }
 
 template <class G>
 struct Lane {
@@ -1100,6 +1191,8 @@ __device__ __forceinline__ typename G::Scratch lane_scratch();
 template <>
 __device__ __forceinline__ CartGrid::Scratch lane_scratch<CartGrid>() { return CartGrid::Scratch{}; }
 template <>
+__device__ __forceinline__ RectGrid::Scratch lane_scratch<RectGrid>() { return RectGrid::Scratch{}; }
+template <>
 __device__ __forceinline__ OctGrid::Scratch lane_scratch<OctGrid>() {
   return OctGrid::Scratch{&S_STACK[threadIdx.x * kOctStack]};
 }
@@ -1108,6 +1201,8 @@ template <class G>
 __device__ __forceinline__ void load_grid_cache(const FwdParams& P);
 template <>
 __device__ __forceinline__ void load_grid_cache<CartGrid>(const FwdParams&) {}
+template <>
+__device__ __forceinline__ void load_grid_cache<RectGrid>(const FwdParams&) {}
 template <>
 __device__ __forceinline__ void load_grid_cache<OctGrid>(const FwdParams& P) {
   const int n = P.n_nodes < kChildCache ? (int)P.n_nodes : kChildCache;

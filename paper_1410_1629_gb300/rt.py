@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build
 
 RT_OK, RT_ERR_ARG, RT_ERR_STATE, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_DEVICE_FLAG = 0, -1, -2, -3, -4, -5, -6
-RT_GRID_CARTESIAN, RT_GRID_OCTREE = 0, 1
+RT_GRID_CARTESIAN, RT_GRID_OCTREE, RT_GRID_RECTILINEAR = 0, 1, 2
 RT_SOURCE_POINT, RT_SOURCE_EXPDISK, RT_SOURCE_PLUMMER = 0, 1, 2
 RT_DEPOSIT_NEAREST, RT_DEPOSIT_BILINEAR, RT_DEPOSIT_SED = 0, 1, 2
 
@@ -37,7 +37,7 @@ class rt_grid_desc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("bounds", ctypes.c_double * 6), ("density", ctypes.c_void_p), ("n_nodes", ctypes.c_int64),
                 ("child", ctypes.c_void_p), ("n_leaves", ctypes.c_int64), ("on_device", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("edges", ctypes.c_void_p * 3)]
 
 
 class rt_source_desc(ctypes.Structure):
@@ -415,10 +415,15 @@ def grid_desc(grid, on_device_arrays=None):
     dens = np.ascontiguousarray(grid.density, dtype=np.float32)
     keep = [dens]
     d.density = dens.ctypes.data
-    if grid.kind == "cartesian":
-        d.kind = RT_GRID_CARTESIAN
+    if grid.kind in ("cartesian", "rectilinear"):
+        d.kind = RT_GRID_CARTESIAN if grid.kind == "cartesian" else RT_GRID_RECTILINEAR
         nz, ny, nx = dens.shape
         d.nx, d.ny, d.nz = nx, ny, nz
+        if grid.kind == "rectilinear":
+            for a in range(3):
+                e = np.ascontiguousarray(grid.edges[a], dtype=np.float64)
+                keep.append(e)
+                d.edges[a] = e.ctypes.data
     else:
         d.kind = RT_GRID_OCTREE
         child = np.ascontiguousarray(grid.child, dtype=np.int32)

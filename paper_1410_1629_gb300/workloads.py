@@ -18,6 +18,8 @@ SKIRT paper, Sect. 2.5 and its ski file, and the component table, Table 1):
   (Sect. 2.4), Plummer bulge plus exponential disk.
 * ``lognormal_cube``: log-normal density field for gradient checks.
 * ``batch_models``: many small independent models for the batched launcher.
+* ``spiral_example``: the paper's worked spiral-galaxy example (Sect. 2.5)
+  on a 3D power-law (PowCub) or equal-cell grid.
 """
 from __future__ import annotations
 
@@ -31,12 +33,15 @@ import numpy as np
 @dataclass
 class Grid:
     """Dust grid.  ``kind`` is ``"cartesian"`` (density float32 [nz, ny, nx],
-    x fastest) or ``"octree"`` (``child`` int32 per node: index of the first of
-    eight children, or -(leaf + 1) for a leaf; density float32 per leaf)."""
+    x fastest), ``"rectilinear"`` (the same with cell edges per axis in
+    ``edges``: three float64 arrays of n + 1 increasing values) or
+    ``"octree"`` (``child`` int32 per node: index of the first of eight
+    children, or -(leaf + 1) for a leaf; density float32 per leaf)."""
     kind: str
     bounds: np.ndarray  # float64 [xmin, xmax, ymin, ymax, zmin, zmax]
     density: np.ndarray
     child: Optional[np.ndarray] = None
+    edges: Optional[list] = None
 
     @property
     def n_cells(self) -> int:
@@ -118,6 +123,47 @@ def cartesian_grid(bounds, density) -> Grid:
     return Grid("cartesian", _f64(bounds), np.ascontiguousarray(density, dtype=np.float32))
 
 
+def rectilinear_grid(edges, density) -> Grid:
+    """Grid of cuboidal cells between the given edges (x, y, z)."""
+    e = [np.ascontiguousarray(a, dtype=np.float64) for a in edges]
+    bounds = [e[0][0], e[0][-1], e[1][0], e[1][-1], e[2][0], e[2][-1]]
+    return Grid("rectilinear", _f64(bounds), np.ascontiguousarray(density, dtype=np.float32), edges=e)
+
+
+def powcub_edges(lo, hi, n, ratio):
+    """Cell edges of ``n`` cells on [lo, hi], symmetric about the centre, with
+    widths growing by a constant factor from the centre outwards so that the
+    outermost cell is ``ratio`` times as wide as the innermost (the power-law
+    spacing of the PowCub grid, Table 1(d); ratio 1 gives equal cells).  An
+    odd ``n`` has one central cell."""
+    half = n // 2
+    centre = 0.5 * (lo + hi)
+    length = hi - lo
+    if n % 2 == 0:
+        steps = half - 1
+        q = ratio ** (1.0 / steps) if steps > 0 else 1.0
+        w = q ** np.arange(half)
+        t = np.concatenate([[0.0], np.cumsum(w)])
+        t *= 0.5 * length / t[-1]
+        edges = np.concatenate([centre - t[::-1], centre + t[1:]])
+    else:
+        q = ratio ** (1.0 / half) if half > 0 else 1.0
+        w = q ** np.arange(half + 1)  # w[0]: the central cell
+        t = np.concatenate([[0.5 * w[0]], 0.5 * w[0] + np.cumsum(w[1:])])
+        t *= 0.5 * length / t[-1]
+        edges = np.concatenate([centre - t[::-1], centre + t])
+    edges[0], edges[-1] = lo, hi
+    return edges
+
+
+def cell_centres_of(grid):
+    """Cell-centre coordinates (x [nx], y [ny], z [nz]) of a cartesian or
+    rectilinear grid."""
+    if grid.kind == "rectilinear":
+        return tuple(0.5 * (e[1:] + e[:-1]) for e in grid.edges)
+    return cell_centres(grid.bounds, grid.shape)
+
+
 def cell_centres(bounds, shape):
     """Cell-centre coordinates (x [nx], y [ny], z [nz]) of a cartesian grid."""
     nx, ny, nz = shape
@@ -195,6 +241,84 @@ def disk_galaxy(n_cells=256, n_lambda=10, n_pix=512, n_packets_total=100_000_000
         sources=[Source("expdisk", (0.0, 0.0, 0.0), np.ones(n_lambda), scale_r=4.0, scale_z=0.35)],
         instruments=instr,
         run=Run(n_per_lambda=max(1, n_packets_total // n_lambda)),
+    )
+
+
+# Units of the spiral-galaxy example: lengths in pc, luminosity and dust mass
+# in solar units.  Extinction per unit dust mass at 0.55 um: a synthetic
+# Milky-Way-like 2.6e4 cm^2 / g (the paper's Draine & Li tables are not
+# available), converted to pc^2 / Msun.
+PC_CM = 3.0857e18
+MSUN_G = 1.98892e33
+KAPPA_V_CM2_G = 2.6e4
+KAPPA_V_PC2_MSUN = KAPPA_V_CM2_G * MSUN_G / PC_CM ** 2
+
+
+def _exp_disk_cell_means(edges, h_r, h_z, n_gauss=4, chunk=1 << 20):
+    """Mean of exp(-R/h_r - |z|/h_z) over each cell of a rectilinear grid:
+    an n_gauss^3-point Gauss-Legendre rule per cell (the paper's example
+    averages random density samples per cell; a fixed rule keeps the input
+    deterministic).  Returns float64 [nz, ny, nx]."""
+    gx, gw = np.polynomial.legendre.leggauss(n_gauss)
+    ex, ey, ez = (np.asarray(e, dtype=np.float64) for e in edges)
+    nx, ny, nz = len(ex) - 1, len(ey) - 1, len(ez) - 1
+    # z factor separates: mean of exp(-|z|/h_z) per z cell by the rule
+    zc, zh = 0.5 * (ez[1:] + ez[:-1]), 0.5 * (ez[1:] - ez[:-1])
+    fz = (np.exp(-np.abs(zc[:, None] + zh[:, None] * gx[None, :]) / h_z) * gw[None, :]).sum(axis=1) / 2.0
+    xc, xh = 0.5 * (ex[1:] + ex[:-1]), 0.5 * (ex[1:] - ex[:-1])
+    yc, yh = 0.5 * (ey[1:] + ey[:-1]), 0.5 * (ey[1:] - ey[:-1])
+    xs = (xc[:, None] + xh[:, None] * gx[None, :])  # [nx, g]
+    ys = (yc[:, None] + yh[:, None] * gx[None, :])  # [ny, g]
+    w2 = (gw[:, None] * gw[None, :]) / 4.0          # [g, g]
+    fxy = np.empty((ny, nx))
+    for j0 in range(0, ny, max(1, chunk // (nx * n_gauss * n_gauss))):
+        j1 = min(ny, j0 + max(1, chunk // (nx * n_gauss * n_gauss)))
+        R = np.sqrt(ys[j0:j1, None, :, None] ** 2 + xs[None, :, None, :] ** 2)  # [j, nx, g, g]
+        fxy[j0:j1] = (np.exp(-R / h_r) * w2[None, None]).sum(axis=(2, 3))
+    return fz[:, None, None] * fxy[None, :, :]
+
+
+def spiral_example(grid="powcub", n_xy=256, n_z=128, xy_ratio=20.0, z_ratio=50.0, n_packets=10_000_000,
+                   n_pix=(1200, 300)) -> Problem:
+    """The simple spiral galaxy of the paper's worked example (Sect. 2.5, its
+    ski file): a stellar exponential disk (scale length 4400 pc, height
+    500 pc, 1e11 Lsun at 0.55 um) and a dust exponential disk (6600 pc,
+    250 pc, 4e7 Msun of dust), 1e7 packets at one wavelength, one frame
+    "xz" at inclination 90 deg, azimuth -90 deg, 1200 x 300 pixels with
+    extents 28000 x 7000 pc (taken as half-widths).  The paper's grid is 2D
+    axisymmetric (logarithmic radially from 250 to 25000 pc, power-law
+    vertically up to 7000 pc with ratio 50); here the same domain
+    [-25000, 25000]^2 x [-7000, 7000] pc is a 3D grid: ``grid="powcub"``
+    with power-law spaced edges (``xy_ratio`` horizontally, ``z_ratio``
+    vertically) or ``grid="cartesian"`` with equal cells.  Cell densities are
+    cell means (Gauss-Legendre rule).  Optics at 0.55 um: the synthetic
+    kappa of KAPPA_V_PC2_MSUN, albedo 0.6, g 0.6."""
+    h_r, h_z, mass = 6600.0, 250.0, 4e7
+    rho0 = mass / (4.0 * math.pi * h_r * h_r * h_z)
+    if grid == "powcub":
+        edges = [powcub_edges(-25000.0, 25000.0, n_xy, xy_ratio), powcub_edges(-25000.0, 25000.0, n_xy, xy_ratio),
+                 powcub_edges(-7000.0, 7000.0, n_z, z_ratio)]
+    elif grid == "cartesian":
+        edges = [-25000.0 + np.arange(n_xy + 1) * (50000.0 / n_xy), -25000.0 + np.arange(n_xy + 1) * (50000.0 / n_xy),
+                 -7000.0 + np.arange(n_z + 1) * (14000.0 / n_z)]
+        for e, hi in zip(edges, (25000.0, 25000.0, 7000.0)):
+            e[-1] = hi
+    else:
+        raise ValueError(grid)
+    dens = (rho0 * _exp_disk_cell_means(edges, h_r, h_z)).astype(np.float32)
+    g = rectilinear_grid(edges, dens) if grid == "powcub" else cartesian_grid([-25000.0, 25000.0, -25000.0, 25000.0,
+                                                                                -7000.0, 7000.0], dens)
+    kappa, albedo, gg = synthetic_optics([0.55], KAPPA_V_PC2_MSUN)
+    frame = Instrument(math.radians(90.0), math.radians(-90.0), 0.0, n_pix[0], n_pix[1], 28000.0, 7000.0)
+    return Problem(
+        name=f"spiral_example_{grid}",
+        grid=g, wavelengths=_f64([0.55]), kappa=kappa, albedo=albedo, g=gg,
+        sources=[Source("expdisk", (0.0, 0.0, 0.0), _f64([1e11]), scale_r=4400.0, scale_z=500.0)],
+        instruments=[frame],
+        run=Run(n_per_lambda=int(n_packets)),
+        meta={"dust_mass": mass, "rho0": rho0, "kappa_v_pc2_msun": float(KAPPA_V_PC2_MSUN),
+              "face_on_tau_v": float(KAPPA_V_PC2_MSUN * mass / (2.0 * math.pi * h_r * h_r)),
+              "edge_on_tau_v": float(KAPPA_V_PC2_MSUN * mass / (2.0 * math.pi * h_r * h_z))},
     )
 
 

@@ -67,18 +67,29 @@ def _channel_of(event):
     return np.where(np.asarray(event) == 0, 1, 2)
 
 
-def flip_corrected_images(gpu, ora, problem):
-    """GPU images (every channel) with every contribution whose pixel differs
-    from the oracle's moved to the oracle's pixel, every GPU-only record
-    removed and every oracle-only record added.  Returns (images, report);
-    report["touched"] lists, per instrument, the flat bins
-    (channel, lambda * ny * nx + pixel) that a correction changed."""
+def flip_corrected_images(gpu, ora, problem, value_flip_rtol=1e-2):
+    """GPU images (every channel) with the FP32 flips undone, per record:
+
+    * a pixel flip (the record's pixel differs from the oracle's) has its
+      contribution moved to the oracle's pixel;
+    * a value flip (same pixel, value off by more than value_flip_rtol: the
+      FP32 position fell on the other side of a cell face, so the peel-off
+      ray runs through other cells) has its contribution replaced by the
+      oracle's value;
+    * a GPU-only record is removed and an oracle-only record added.
+
+    Returns (images, report); report["touched"] lists, per instrument, the
+    flat bins (channel, lambda * ny * nx + pixel) a correction changed, and
+    report["far_flips"] counts pixel flips to a pixel that is not a
+    neighbour of the oracle's (Chebyshev distance above 1)."""
     g, o = gpu["records"], ora["records"]
     assert gpu["records_total"] == len(g) and ora["records_total"] == len(o), "record buffer overflow"
     kg, ko = _keys(g), _keys(o)
     assert len(np.unique(kg)) == len(kg) and len(np.unique(ko)) == len(ko)
     common, ig, io = np.intersect1d(kg, ko, return_indices=True)
     flip = g["pixel"][ig] != o["pixel"][io]
+    rel = np.abs(g["value"][ig] - o["value"][io]) / np.maximum(np.abs(o["value"][io]), 1e-300)
+    vflip = ~flip & (rel > value_flip_rtol)
     only_g = np.setdiff1d(np.arange(len(g)), ig)
     only_o = np.setdiff1d(np.arange(len(o)), io)
     imgs = [im.copy() for im in gpu["images"]]  # [channels, n_lambda, ny, nx]
@@ -92,22 +103,28 @@ def flip_corrected_images(gpu, ora, problem):
             im[ch, lam].reshape(-1)[pix] += value
             touched[q].add((ch, int(lam) * plane + int(pix)))
 
+    far = 0
     for a, b in zip(ig[flip], io[flip]):
         q, lam, ev = g["instr"][a], g["lam"][a], g["event"][a]
-        add(q, lam, ev, g["pixel"][a], -g["value"][a])
-        add(q, lam, ev, o["pixel"][b], g["value"][a])
+        nx = imgs[q].shape[-1]
+        pg, po = int(g["pixel"][a]), int(o["pixel"][b])
+        far += max(abs(pg % nx - po % nx), abs(pg // nx - po // nx)) > 1
+        add(q, lam, ev, pg, -g["value"][a])
+        add(q, lam, ev, po, g["value"][a])
+    for a, b in zip(ig[vflip], io[vflip]):
+        add(g["instr"][a], g["lam"][a], g["event"][a], g["pixel"][a], o["value"][b] - g["value"][a])
     for a in only_g:
         add(g["instr"][a], g["lam"][a], g["event"][a], g["pixel"][a], -g["value"][a])
     for b in only_o:
         add(o["instr"][b], o["lam"][b], o["event"][b], o["pixel"][b], o["value"][b])
-    rel = np.abs(g["value"][ig] - o["value"][io]) / np.maximum(np.abs(o["value"][io]), 1e-300)
     worst = np.argsort(rel)[::-1][:3]
     report = {"worst_records": [{"pid": int(o["pid"][io[w]]), "lam": int(o["lam"][io[w]]),
                                  "event": int(o["event"][io[w]]), "instr": int(o["instr"][io[w]]),
                                  "gpu": float(g["value"][ig[w]]), "oracle": float(o["value"][io[w]])}
                                 for w in worst if rel[w] > 1e-3],
-              "records": int(len(o)), "flips": int(flip.sum()), "gpu_only": int(len(only_g)),
-              "oracle_only": int(len(only_o)), "record_rel_p999": float(np.quantile(rel, 0.999)) if len(rel) else 0.0,
+              "records": int(len(o)), "flips": int(flip.sum()), "value_flips": int(vflip.sum()),
+              "far_flips": int(far), "gpu_only": int(len(only_g)), "oracle_only": int(len(only_o)),
+              "record_rel_p999": float(np.quantile(rel, 0.999)) if len(rel) else 0.0,
               "record_rel_max": float(rel.max()) if len(rel) else 0.0, "touched": touched}
     return imgs, report
 
@@ -134,7 +151,7 @@ def block_sum(a, b):
 def cell_groups(grid, block=4):
     """Group id of every cell for coarser absorption bins: cartesian grids in
     block^3 cubes of cells, octrees by the parent node of the leaf."""
-    if grid.kind == "cartesian":
+    if grid.kind in ("cartesian", "rectilinear"):
         nx, ny, nz = grid.shape
         iz, iy, ix = np.meshgrid(np.arange(nz) // block, np.arange(ny) // block, np.arange(nx) // block,
                                  indexing="ij")
@@ -159,9 +176,11 @@ def _grouped(a, groups):
 def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_records=True, block=8,
             groups=None):
     """The acceptance rule, applied to every channel of every frame and to the
-    absorption field (per cell and wavelength, and per cell summed over the
-    wavelengths).  With records, the flip corrections are bounded: at most
-    1e-4 of the records plus 10 may be flipped, GPU-only or oracle-only, and
+    absorption field (per cell and wavelength, per cell summed over the
+    wavelengths, and per group of cells when `groups` is given).  With
+    records, the corrections are bounded: at most 1e-4 of the records plus
+    10 may be GPU-only or oracle-only, at most 1e-3 plus 10 may be FP32 flips
+    (pixel or value), every pixel flip lands in a neighbouring pixel, and
     every bin that violates the rule before the correction must be one the
     correction changed."""
     rep = {}
@@ -184,8 +203,13 @@ def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_rec
         imgs, rrep = flip_corrected_images(gpu, ora, problem)
         touched = rrep.pop("touched")
         rep.update(rrep)
-        rep["corrections"] = rep["flips"] + rep["gpu_only"] + rep["oracle_only"]
+        # records one side lacks: at most 1e-4 of them (plus 10); FP32 flips
+        # (pixel or value): at most 1e-3 (plus 10), every pixel flip to a
+        # neighbouring pixel
+        rep["corrections"] = rep["gpu_only"] + rep["oracle_only"]
         rep["corrections_limit"] = 1e-4 * rep["records"] + 10
+        rep["flip_total"] = rep["flips"] + rep["value_flips"]
+        rep["flip_limit"] = 1e-3 * rep["records"] + 10
     else:
         imgs = gpu["images"]
     rep["pixels"] = []
@@ -227,7 +251,8 @@ def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_rec
           and all(p["corrected"]["violations"] == 0 for p in rep["pixels"])
           and all(p.get("blocks", {"violations": 0})["violations"] == 0 for p in rep["pixels"])
           and unexplained == 0
-          and (not use_records or rep["corrections"] <= rep["corrections_limit"]))
+          and (not use_records or (rep["corrections"] <= rep["corrections_limit"]
+                                   and rep["flip_total"] <= rep["flip_limit"] and rep["far_flips"] == 0)))
     rep["ok"] = bool(ok)
     return rep
 
@@ -239,7 +264,8 @@ def summary(rep):
             f"(channels {sorted({p['channel'] for p in px})}), blocks {sum(p.get('blocks', {'bins': 0})['bins'] for p in px)}, "
             f"cells {rep['cells']['bins']}, cells over all wavelengths {rep['cells_all_lambda']['bins']}, "
             f"cell groups {rep.get('cell_groups', {'bins': 0})['bins']}; "
-            f"records {rep.get('records', 0)}, flips {rep.get('flips', 0)}, gpu-only {rep.get('gpu_only', 0)}, "
+            f"records {rep.get('records', 0)}, flips {rep.get('flips', 0)} + value flips {rep.get('value_flips', 0)} "
+            f"(limit {rep.get('flip_limit', 0):.0f}, far {rep.get('far_flips', 0)}), gpu-only {rep.get('gpu_only', 0)}, "
             f"oracle-only {rep.get('oracle_only', 0)} (limit {rep.get('corrections_limit', 0):.0f}); "
             f"max rel: pixels {max((p['corrected']['max_rel'] for p in px), default=0):.2e}, "
             f"cells {rep['cells']['max_rel']:.2e}; totals {max(rep['totals_rel']):.2e}")

@@ -269,3 +269,81 @@ def test_autograd_function_matches_direct_adjoint():
         np.testing.assert_allclose(g_auto, g_dir.astype(np.float32), rtol=1e-5, atol=1e-6 * np.abs(g_dir).max())
     finally:
         sim.close()
+
+
+def test_finite_differences_of_the_forward_on_64_random_cells():
+    """Central differences at the workload's step (eps = 1e-3 of a cell's
+    density) on 64 random cells of the 64^3 log-normal cube with its 128^2
+    bilinear detector (1e5 packets, common random numbers), of the linear
+    functional sum_pixels a * image with a = 2 (image - target) from the
+    oracle.
+
+    * The oracle's central differences follow its dual-number derivative
+      (the estimator's kinks make a few cells differ; most agree closely).
+    * The GPU adjoint follows the dual-number derivative.
+    * The GPU forward's central differences equal the oracle's at the same
+      step within the GPU forward's own rounding noise: FP32 arithmetic
+      rounds every contribution of a packet that crosses the perturbed cell
+      afresh in each run, and for a functional whose contributions cancel
+      (a changes sign) that noise does not average away.  The noise of each
+      cell is measured from nine GPU differences at steps eps (1 + j/1000),
+      j = 0..8 (the same derivative, other roundings): their mean must lie
+      within 6 standard errors of the oracle's difference (at most one cell
+      beyond that, none beyond 10: a t statistic with 8 degrees of freedom
+      exceeds 6 with probability 3e-4)."""
+    from oracle import oracle as O
+    prob, target_prob = _loss_problem(64, 128, 100000)
+    n = prob.run.n_per_lambda
+    eps = 1e-3
+    kw = dict(max_events=20, weight_cut=False, n_threads=O.default_threads(), absorption=False)
+    i_o = O.run(prob, n, **kw)["images"][0]
+    t_o = O.run(target_prob, n, **kw)["images"][0]
+    a = 2.0 * (i_o - t_o)
+    cells = np.random.default_rng(4).choice(prob.grid.n_cells, 64, replace=False)
+    rho = prob.grid.density.ravel().copy()
+    opts = dict(max_events=20, weight_cut=0)
+    sim = rt.Simulation(prob)
+    try:
+        def functional(dens):
+            d = torch.from_numpy(np.ascontiguousarray(dens, dtype=np.float32)).cuda()
+            rt.rt_update_density(sim.ctx, d.data_ptr(), 1)
+            sim.reset()
+            sim.launch(n, 0, 0, **opts)
+            return float((a * sim.images()[0].cpu().numpy()).sum())
+
+        fd_g = np.zeros((64, 9))
+        fd_o = np.zeros(64)
+        for i, c in enumerate(cells):
+            for j in range(9):
+                e = eps * (1.0 + j / 1000.0)
+                up, dn = rho.copy(), rho.copy()
+                up[c] = np.float32(rho[c] * (1 + e))
+                dn[c] = np.float32(rho[c] * (1 - e))
+                h = float(up[c]) - float(dn[c])
+                fd_g[i, j] = (functional(up) - functional(dn)) / h
+                if j == 0:
+                    iu = O.run(W.with_density(prob, up.reshape(prob.grid.density.shape)), n, **kw)["images"][0]
+                    idn = O.run(W.with_density(prob, dn.reshape(prob.grid.density.shape)), n, **kw)["images"][0]
+                    fd_o[i] = float((a * (iu - idn)).sum() / h)
+        rt.rt_update_density(sim.ctx, torch.from_numpy(rho).cuda().data_ptr(), 1)
+        adj = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        grad = torch.zeros(prob.grid.n_cells, dtype=torch.float64, device="cuda")
+        rt.rt_adjoint(sim.ctx, [adj.data_ptr()], 0, grad.data_ptr(), n, 0, 0, sim.opts(**opts))
+        assert sim.stats()["device_flags"] == 0
+        g = grad.cpu().numpy()[cells]
+    finally:
+        sim.close()
+    dual = O.vjp(prob, cells, n, adj_images=[a], max_events=20, weight_cut=False, n_threads=O.default_threads())
+    mean, se = fd_g.mean(axis=1), fd_g.std(axis=1, ddof=1) / 3.0
+    t = (mean - fd_o) / np.maximum(se, 1e-300)
+    rel = lambda x, y: np.abs(x - y) / np.abs(y)
+    print("t |quantiles|", np.quantile(np.abs(t), [0.5, 0.9, 1.0]))
+    print("GPU FD (one step) vs oracle FD: rel median, p90", np.quantile(rel(fd_g[:, 0], fd_o), [0.5, 0.9]))
+    print("GPU FD (mean of nine) vs GPU adjoint: rel median, p90", np.quantile(rel(mean, g), [0.5, 0.9]))
+    print("oracle FD vs duals: rel median, p90", np.quantile(rel(fd_o, dual), [0.5, 0.9]))
+    print("GPU adjoint vs duals: rel median, p90, max", np.quantile(rel(g, dual), [0.5, 0.9, 1.0]))
+    assert np.sum(np.abs(t) > 6.0) <= 1 and np.all(np.abs(t) <= 10.0)
+    assert np.median(rel(fd_o, dual)) < 1e-3
+    scale = np.abs(dual).max()
+    assert np.median(rel(g, dual)) < 1e-3
+    assert np.all(np.abs(g - dual) <= 2e-3 * np.abs(dual) + 1e-3 * scale)

@@ -1,0 +1,91 @@
+"""GPU parity on rectilinear grids (cells between arbitrary edges per axis;
+the PowCub grid of Table 1(d)) and on the paper's worked spiral-galaxy
+example (Sect. 2.5), through the C ABI against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_1410_1629_gb300 import rt
+from paper_1410_1629_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU-only machines
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import parity as PAR  # noqa: E402
+
+
+def _assert_ok(rep):
+    print(PAR.summary(rep))
+    if not rep["ok"]:
+        import json
+        print("PARITY REPORT", json.dumps(rep, default=float))
+    assert rep["ok"]
+
+
+def _powcub_disk(nx=48, nz=32, n_lambda=3, n_pix=48):
+    """The disk galaxy's dust and stars on a power-law spaced grid (ratio 20
+    in x and y, 50 in z), three frames with direct and scattered channels and
+    an SED instrument."""
+    base = W.disk_galaxy(n_cells=nx, n_lambda=n_lambda, n_pix=n_pix, channels=3)
+    edges = [W.powcub_edges(-25.0, 25.0, nx, 20.0), W.powcub_edges(-25.0, 25.0, nx, 20.0),
+             W.powcub_edges(-3.0, 3.0, nz, 50.0)]
+    xs, ys, zs = (0.5 * (e[1:] + e[:-1]) for e in edges)
+    R = np.sqrt(xs[None, None, :] ** 2 + ys[None, :, None] ** 2)
+    dens = np.exp(-R / 6.0 - np.abs(zs)[:, None, None] / 0.2)
+    prob = W.replace(base, grid=W.rectilinear_grid(edges, dens))
+    prob.instruments = prob.instruments + [W.sed_instrument(60.0)]
+    return prob
+
+
+def test_powcub_grid_parity():
+    prob = _powcub_disk()
+    n = 20000
+    g = PAR.gpu_run(prob, n, records_cap=8_000_000)
+    o = PAR.oracle_run(prob, n, records_cap=8_000_000)
+    assert g["raw_stats"]["device_flags"] == 0
+    rep = PAR.compare(g, o, prob, groups=PAR.cell_groups(prob.grid))
+    _assert_ok(rep)
+    assert rep["crossings_rel"] < 1e-5
+    sed_g, sed_o = g["images"][3][:, :, 0, 0], o["images"][3][:, :, 0, 0]
+    np.testing.assert_allclose(sed_g, sed_o, rtol=1e-6)
+
+
+def test_rectilinear_grid_arguments_are_checked():
+    prob = _powcub_disk(nx=8, nz=4, n_lambda=1, n_pix=8)
+    ctx = rt.rt_context_create(0)
+    try:
+        d, keep = rt.grid_desc(prob.grid)
+        bad = np.array(prob.grid.edges[2])
+        bad[2] = bad[1]  # not strictly increasing
+        keep.append(bad)
+        d.edges[2] = bad.ctypes.data
+        with pytest.raises(rt.RTError) as e:
+            rt.rt_create_grid(ctx, d)
+        assert e.value.status == rt.RT_ERR_ARG
+        d, keep = rt.grid_desc(prob.grid)
+        d.bounds[5] = 4.0  # last z edge is 3
+        with pytest.raises(rt.RTError) as e:
+            rt.rt_create_grid(ctx, d)
+        assert e.value.status == rt.RT_ERR_ARG
+    finally:
+        rt.rt_context_destroy(ctx)
+
+
+@pytest.mark.parametrize("grid", ["powcub", "cartesian"])
+def test_spiral_example_first_packet_ids(grid):
+    """The paper's spiral-galaxy example at full size (256 x 256 x 128
+    power-law cells, or 256 x 256 x 72 equal cells; 1200 x 300 edge-on
+    frame; 1e7-packet weights) on its first 1e5 packet ids: bins of at least
+    1e3 oracle contributions (pixels, 8 x 8 blocks, cells, 4^3-cell blocks)
+    within 1e-4, totals within 1e-6."""
+    prob = W.spiral_example(grid) if grid == "powcub" else W.spiral_example("cartesian", n_z=72)
+    prob.instruments[0].channels = 3
+    n_ids = 100_000
+    g = PAR.gpu_run(prob, n_ids, n_norm=prob.run.n_per_lambda, records_cap=40 * n_ids)
+    o = PAR.oracle_run(prob, n_ids, n_norm=prob.run.n_per_lambda, records_cap=40 * n_ids)
+    assert g["raw_stats"]["device_flags"] == 0
+    rep = PAR.compare(g, o, prob, groups=PAR.cell_groups(prob.grid))
+    _assert_ok(rep)
+    assert rep["pixels"][0]["blocks"]["bins"] > 0 and rep["cell_groups"]["bins"] > 0

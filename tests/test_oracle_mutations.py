@@ -54,6 +54,9 @@ MUTATIONS = {
     # SED instrument recording scattered light as direct
     "sed_channel": ("if (f.channels == 3) tally.pixel((int)q, scattered ? 2 : 1, lam, 0, value, pid, event);",
                     "if (f.channels == 3) tally.pixel((int)q, 1, lam, 0, value, pid, event);", "test_oracle_sed.py"),
+    # rectilinear grid planes read one edge off
+    "rect_plane_index": ("return kind == 2 ? edges[axis][(size_t)i] :",
+                         "return kind == 2 ? edges[axis][(size_t)(i > 0 ? i - 1 : 0)] :", "test_oracle_rectilinear.py"),
     # derivative of exp with the wrong sign
     "dual_exp_sign": ("inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, e * a.d}; }",
                       "inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, -e * a.d}; }",

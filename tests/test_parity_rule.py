@@ -30,7 +30,7 @@ def test_identical_runs_pass(runs):
     prob, r = runs
     rep = PAR.compare(_gpu_like(r), r, prob)
     assert rep["ok"], rep
-    assert rep["corrections"] == 0 and rep["raw_unexplained"] == 0
+    assert rep["corrections"] == 0 and rep["flip_total"] == 0 and rep["raw_unexplained"] == 0
     assert {p["channel"] for p in rep["pixels"]} == {0, 1, 2}
     assert all(p["corrected"]["bins"] > 0 for p in rep["pixels"])
     assert rep["cells"]["bins"] > 0 and rep["cells_all_lambda"]["bins"] > 0
@@ -82,3 +82,36 @@ def test_changed_cell_fails(runs):
     g["absorption"][0, c] *= 1.001
     rep = PAR.compare(g, r, prob)
     assert not rep["ok"] and rep["cells"]["violations"] == 1
+
+
+def test_far_pixel_moves_fail(runs):
+    """A record whose GPU pixel is far from the oracle's is not an FP32 flip."""
+    prob, r = runs
+    g = _gpu_like(r)
+    i = int(np.argmax(g["records"]["value"]))
+    rec = g["records"][i]
+    nx = prob.instruments[0].nx
+    old = int(rec["pixel"])
+    new = (old + 5 * nx + 5) % (nx * nx)
+    for ch in (0, 1 if rec["event"] == 0 else 2):
+        img = g["images"][rec["instr"]][ch, rec["lam"]].reshape(-1)
+        img[old] -= rec["value"]
+        img[new] += rec["value"]
+    g["records"]["pixel"][i] = new
+    rep = PAR.compare(g, r, prob)
+    assert rep["far_flips"] == 1 and not rep["ok"]
+
+
+def test_value_flips_are_bounded(runs):
+    """Records whose values differ by more than 1e-2 are taken as cell flips
+    (repaired per record), but only up to 1e-3 of the records."""
+    prob, r = runs
+    g = _gpu_like(r)
+    sel = np.arange(0, len(g["records"]), 200)
+    for i in sel:
+        rec = g["records"][i]
+        for ch in (0, 1 if rec["event"] == 0 else 2):
+            g["images"][rec["instr"]][ch, rec["lam"]].reshape(-1)[rec["pixel"]] += 0.5 * rec["value"]
+    g["records"]["value"][sel] *= 1.5
+    rep = PAR.compare(g, r, prob)
+    assert rep["value_flips"] == len(sel) and rep["flip_total"] > rep["flip_limit"] and not rep["ok"]
