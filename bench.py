@@ -240,6 +240,129 @@ def run_reference(args, prob, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def launch_bytes(st, with_absorption=True):
+    """Algorithmic bytes of a launch from its counters (the unit costs
+    above); forced-path crossings move no absorption bytes when the launch
+    keeps no absorption field (batches)."""
+    path_cross, column_cross, column_peels = st["path_crossings"], st["column_crossings"], st["column_peels"]
+    peel_cross = st["crossings"] - path_cross - column_cross
+    return ((BYTES_PATH_CROSSING if with_absorption else BYTES_PEEL_CROSSING) * path_cross
+            + BYTES_PEEL_CROSSING * peel_cross + BYTES_COLUMN_PEEL * column_peels + BYTES_DEPOSIT * st["peeloffs"])
+
+
+def workload_rate(prob, device, stream, flush, warmup, timed, tune_fraction=0.05, cpu_seconds=0.0, peak=None,
+                  kernel="k_forward_cartesian"):
+    """Packets/s, crossings/s and the transport kernel's roofline for one
+    workload: tuned on a sample (another seed), `warmup` untimed and `timed`
+    timed launches (CUDA events on the launching stream, L2 flushed before
+    each), optionally the oracle on a bounded sample of the same workload."""
+    import torch
+    from paper_1410_1629_gb300 import rt
+    n = prob.run.n_per_lambda
+    sim = rt.Simulation(prob, device=device)
+    try:
+        lanes = sim.tune(max(1, int(n * tune_fraction)), seed=prob.run.seed + 1, stream=stream.cuda_stream)
+        times, parts = [], []
+        for i in range(warmup + timed):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                sim.reset(stream=stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.launch(n, 0, prob.run.seed, stream=stream, time_parts=1)
+                e1.record(stream)
+            e1.synchronize()
+            if i >= warmup:
+                times.append(e0.elapsed_time(e1) / 1e3)
+                parts.append(sim.launch_times())
+        st = sim.stats()
+    finally:
+        sim.close()
+    t = sum(times) / len(times)
+    packets = n * prob.n_lambda
+    kern_ms = statistics.mean(p["transport"] for p in parts)
+    walks_ms = statistics.mean(p["peel_walks"] for p in parts)
+    sorted_peels = st["sorted_peels"]
+    walked = st["peeloffs"] - st["column_peels"]
+    peel_cross = st["crossings"] - st["path_crossings"] - st["column_crossings"]
+    sorted_cross = peel_cross * sorted_peels / walked if walked else 0
+    bytes_all = launch_bytes(st)
+    bytes_kernel = bytes_all - (BYTES_PEEL_CROSSING * sorted_cross + BYTES_DEPOSIT * sorted_peels)
+    out = {"packets": int(packets), "seconds_per_launch": t, "packets_per_s": packets / t,
+           "crossings_per_s": st["crossings"] / t,
+           "walked_crossings_per_s": (st["crossings"] - st["column_crossings"]) / t,
+           "timed_launches": len(times), "tuned": {"control_lanes": lanes},
+           "kernel_ms": kern_ms, "peel_walks_ms": walks_ms,
+           "conservation_rel": abs(st["emitted"] - st["escaped"] - st["absorbed"] - st["truncated"]) / st["emitted"],
+           "device_flags": int(st["device_flags"]), "l2": "flushed before each timed launch (256 MiB write)"}
+    if peak:
+        ach = bytes_kernel / (kern_ms / 1e3) / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": peak[0], "unit": "GB/s",
+                           "frac": ach / peak[0], "peak_source": f"{peak[1]} hbm_gbs",
+                           "algorithmic_bytes_per_launch": int(bytes_kernel), "traffic": None}
+    if cpu_seconds > 0:
+        threads = os.cpu_count() or 1
+        rate, cpackets, dt, _ = oracle_sample(prob, cpu_seconds, threads)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": f"first {cpackets // prob.n_lambda} packet ids per wavelength "
+                                         f"({cpackets} packets, {dt:.1f} s), FP64 oracle, all host threads"}
+    return out
+
+
+def octree_rate(args, device, stream, flush, peak):
+    """The clumpy medium on the adaptive octree: 1e6 Gaussian clumps binned
+    to ~5e6 leaves (max level 10), Plummer bulge + exponential disk, 20
+    wavelengths, 2e8 packets, two 1024^2 frames."""
+    from paper_1410_1629_gb300 import workloads as W
+    t0 = time.time()
+    kw = {"n_packets_total": int(args.octree_packets)} if args.octree_packets else {}
+    prob = W.clumpy_octree(**kw)
+    gen_s = time.time() - t0
+    out = workload_rate(prob, device, stream, flush, warmup=1, timed=1, tune_fraction=0.01,
+                        cpu_seconds=args.cpu_seconds / 2, peak=peak, kernel="k_forward_octree")
+    out["workload"] = (f"clumpy_octree: {prob.grid.n_cells} leaves ({prob.meta['nodes']} nodes, max level 10, "
+                       f"delta {prob.meta['delta']:.3e} of the total mass), Plummer bulge + exponential disk, "
+                       f"{prob.n_lambda} wavelengths, {out['packets']:.0e} packets, 2 frames 1024^2 at i=0/90 deg")
+    out["leaves"] = int(prob.grid.n_cells)
+    out["nodes"] = int(prob.meta["nodes"])
+    out["delta"] = float(prob.meta["delta"])
+    out["generation_s"] = gen_s
+    out["roofline"]["note"] = "algorithmic bytes count no tree-node loads (the descent below the cached top)"
+    return out
+
+
+def spiral_rate(args, device, stream, flush, peak):
+    """The paper's worked example (Sect. 2.5): spiral galaxy at 0.55 um, 1e7
+    packets, one 1200 x 300 edge-on frame, on a 256 x 256 x 128 power-law
+    (PowCub) grid and on a 256 x 256 x 72 equal-cell grid."""
+    from paper_1410_1629_gb300 import workloads as W
+    out = {}
+    for name, prob in (("powcub", W.spiral_example("powcub")), ("cartesian", W.spiral_example("cartesian", n_z=72))):
+        r = workload_rate(prob, device, stream, flush, warmup=3, timed=3, tune_fraction=0.1,
+                          cpu_seconds=args.cpu_seconds / 3 if name == "powcub" else 0.0, peak=peak,
+                          kernel="k_forward_rect" if name == "powcub" else "k_forward_cartesian")
+        nz, ny, nx = prob.grid.density.shape
+        r["workload"] = (f"spiral_example_{name}: {nx}x{ny}x{nz} cells, exponential stellar disk (4400 / 500 pc, "
+                         f"1e11 Lsun) and dust disk (6600 / 250 pc, 4e7 Msun, edge-on tau_V "
+                         f"{prob.meta['edge_on_tau_v']:.1f}), 0.55 um, {r['packets']:.0e} packets, 1200x300 frame "
+                         f"at i=90 deg")
+        out[name] = r
+    return out
+
+
+def plain_cube_rate(args, device, stream, flush):
+    """The plain method: 32^3 uniform cube, axis tau 1, albedo 0.6, g 0.5,
+    central point source, 1e5 packets, one 64^2 face-on frame."""
+    from paper_1410_1629_gb300 import workloads as W
+    prob = W.uniform_cube()
+    r = workload_rate(prob, device, stream, flush, warmup=3, timed=5, tune_fraction=0.2,
+                      cpu_seconds=min(5.0, args.cpu_seconds), peak=None)
+    r["workload"] = ("uniform_cube_32: 32^3 cells of side 2/32 pc, axis tau 1, albedo 0.6, g 0.5, central point "
+                     "source, 1e5 packets, one 64^2 face-on frame")
+    r["note"] = "the grid (128 KB) and its tallies stay in L2; a launch this small is bound by its own latency"
+    return r
+
+
 def adjoint_ratio(args, device, stream, flush):
     """Adjoint/forward time on the differentiation workload: 64^3 log-normal
     cube, 10^7 packets, 128^2 bilinear detector, termination after 20 events;
@@ -319,6 +442,7 @@ def adjoint_ratio(args, device, stream, flush):
                 tb.append(e2.elapsed_time(e3) / 1e3)
         t_tf, t_tb = sum(tf) / len(tf), sum(tb) / len(tb)
         flags = sim.stats()["device_flags"]
+        fd = fd_check(prob, sim, adj, opts, args.fd_packets, stream) if not args.skip_fd else None
     finally:
         sim.close()
         tsim.close()
@@ -329,7 +453,60 @@ def adjoint_ratio(args, device, stream, flush):
                      "note": "forward launch recording the adjoint tape, then the adjoint without replay"},
             "forward_crossings": int(st["crossings"]), "adjoint_crossings": adj_cross,
             "adjoint_deposit_crossings": dep_cross, "adjoint_crossings_per_s": adj_cross / t_b,
-            "device_flags": int(flags), "l2": "flushed before each timed launch"}
+            "adjoint_algorithmic_bytes": int(BYTES_PEEL_CROSSING * adj_cross + BYTES_DEPOSIT * dep_cross),
+            "fd_check": fd, "device_flags": int(flags), "l2": "flushed before each timed launch"}
+
+
+def fd_check(prob, sim, adj, opts, n, stream):
+    """Central differences of the GPU forward (eps = 1e-3 of a density, 64
+    random cells, rng seed 4, common random numbers) against the GPU adjoint
+    of the same packets and adjoint image: the relative deviation per cell
+    (median, p90).  The forward's FP32 rounding puts a noise floor under the
+    differences of cells whose gradient is small (the loss's adjoint changes
+    sign over the image, so the rounding does not cancel); the tests compare
+    the differences with the oracle's at the same step."""
+    import torch
+    from paper_1410_1629_gb300 import rt
+    n = int(n)
+    eps = 1e-3
+    cells = np.random.default_rng(4).choice(prob.grid.n_cells, 64, replace=False)
+    rho = prob.grid.density.ravel().copy()
+    dev = adj.device
+
+    def functional(dens):
+        d = torch.from_numpy(np.ascontiguousarray(dens, dtype=np.float32)).to(dev)
+        torch.cuda.synchronize()
+        rt.rt_update_density(sim.ctx, d.data_ptr(), 1, stream.cuda_stream)
+        sim.reset(stream=stream)
+        sim.launch(n, 0, prob.run.seed, stream=stream, **opts)
+        with torch.cuda.stream(stream):
+            v = (adj * sim.images(stream=stream)[0]).sum()
+        return float(v.item())
+
+    t0 = time.time()
+    fd = np.zeros(64)
+    for i, c in enumerate(cells):
+        up, dn = rho.copy(), rho.copy()
+        up[c] = np.float32(rho[c] * (1 + eps))
+        dn[c] = np.float32(rho[c] * (1 - eps))
+        fd[i] = (functional(up) - functional(dn)) / (float(up[c]) - float(dn[c]))
+    d = torch.from_numpy(rho).to(dev)
+    torch.cuda.synchronize()
+    rt.rt_update_density(sim.ctx, d.data_ptr(), 1, stream.cuda_stream)
+    grad = torch.zeros(prob.grid.n_cells, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    rt.rt_adjoint(sim.ctx, [adj.data_ptr()], 0, grad.data_ptr(), n, 0, prob.run.seed, sim.opts(**opts),
+                  stream.cuda_stream)
+    torch.cuda.synchronize()
+    g = grad.cpu().numpy()[cells]
+    rel = np.abs(fd - g) / np.abs(g)
+    big = np.abs(g) >= 0.1 * np.abs(g).max()
+    return {"cells": 64, "eps": eps, "packets": n, "median_rel_dev": float(np.median(rel)),
+            "p90_rel_dev": float(np.quantile(rel, 0.9)),
+            "median_rel_dev_cells_above_tenth_of_max": float(np.median(rel[big])) if big.any() else None,
+            "abs_dev_over_max_gradient_p90": float(np.quantile(np.abs(fd - g) / np.abs(g).max(), 0.9)),
+            "seconds": time.time() - t0,
+            "loss": "image L2 loss against the image of an independent field (the adjoint image of the timing)"}
 
 
 def batch_rate(args, device, stream):
@@ -364,6 +541,7 @@ def batch_rate(args, device, stream):
     return {"workload": f"{len(models)} models: 8^3-48^3 cells, half uniform / half exponential slab, axis tau 0.1-20, "
                         f"g 0-0.9, albedo 0.3-0.8, {scale:g} x (1e4-1e6) packets, one 64^2 frame each",
             "models": len(models), "packets": int(st["packets"]), "seconds_per_launch": t,
+            "algorithmic_bytes": int(launch_bytes(dict(st, path_crossings=0), with_absorption=False)),
             "packets_per_s": st["packets"] / t, "crossings_per_s": st["crossings"] / t,
             "tuned": {"control_lanes": lanes, "run_packets": run}, "launch": "CUDA graph",
             "timed_launches": len(ts), "device_flags": int(st["device_flags"]),
@@ -508,6 +686,30 @@ def run_gpu(args, prob, world, rank, local_rank):
     batch = None
     if rank == 0 and world == 1 and not args.skip_batch:
         batch = batch_rate(args, device, stream)
+    # the L2 read bandwidth of the library's own probe kernel (32 MiB buffer):
+    # the roofline of the kernels whose working set stays in L2
+    l2 = None
+    if rank == 0 and world == 1:
+        l2 = {"gb_per_s": rt.rt_probe_bandwidth(device, 32 << 20, 40, 5),
+              "how": "rt_probe_bandwidth: L2-cached float4 loads over a 32 MiB buffer, 40 passes, best of 5, "
+                     "CUDA events", "hbm_read_gb_per_s": rt.rt_probe_bandwidth(device, 4 << 30, 2, 3)}
+        for block, secs_key in ((adjoint, "adjoint_ms"), (batch, "seconds_per_launch")):
+            if not block:
+                continue
+            b = block["adjoint_algorithmic_bytes"] if secs_key == "adjoint_ms" else block["algorithmic_bytes"]
+            secs = block[secs_key] / 1e3 if secs_key == "adjoint_ms" else block[secs_key]
+            ach = b / secs / 1e9
+            block["roofline"] = {"bound": "l2", "kernel": "k_adjoint" if secs_key == "adjoint_ms" else "k_batch",
+                                 "achieved": ach, "peak": l2["gb_per_s"], "unit": "GB/s", "frac": ach / l2["gb_per_s"],
+                                 "peak_source": "builder-measured L2 read bandwidth (rt_probe_bandwidth)",
+                                 "time": "the whole call (its kernels back to back)"}
+    octree = spiral = plain = None
+    if rank == 0 and world == 1 and not args.skip_octree:
+        octree = octree_rate(args, device, stream, flush, (peak, peak_kind))
+    if rank == 0 and world == 1 and not args.skip_spiral:
+        spiral = spiral_rate(args, device, stream, flush, (peak, peak_kind))
+    if rank == 0 and world == 1 and not args.skip_plain:
+        plain = plain_cube_rate(args, device, stream, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -523,6 +725,7 @@ def run_gpu(args, prob, world, rank, local_rank):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": workload_config(prob, world),
                 "crossings_per_s": world * crossings_step * args.steps / t_total,
+                "walked_crossings_per_s": world * (crossings_step - column_cross) * args.steps / t_total,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak,
                              "traffic": (args.traffic if args.traffic is not None
@@ -538,7 +741,7 @@ def run_gpu(args, prob, world, rank, local_rank):
                                               "GB_per_s": bytes_launch / mean_launch / 1e9}},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_step * args.steps, "adjoint": adjoint,
                 "tuned": {"control_lanes": lanes, "sample": "5 % of the packets, another seed, before the warm-up"},
-                "batch": batch,
+                "batch": batch, "octree": octree, "spiral_example": spiral, "plain_cube": plain, "l2_peak": l2,
                 "clocks": clk,
                 "checks": {"conservation_rel": conservation, "path_crossings": int(path_cross),
                            "walked_peel_crossings": int(peel_cross), "column_peels": int(column_peels),
@@ -566,6 +769,14 @@ def main():
                     help="skip the batched 4096-model measurement")
     ap.add_argument("--skip-adjoint", action="store_true",
                     help="skip the adjoint/forward measurement on the 64^3 differentiation workload")
+    ap.add_argument("--skip-octree", action="store_true", help="skip the clumpy-octree workload (2e8 packets)")
+    ap.add_argument("--octree-packets", type=float, default=None,
+                    help="packets of the clumpy-octree measurement (default 2e8, the workload's size)")
+    ap.add_argument("--skip-spiral", action="store_true", help="skip the paper's spiral-galaxy example")
+    ap.add_argument("--skip-plain", action="store_true", help="skip the plain-method 32^3 cube")
+    ap.add_argument("--skip-fd", action="store_true", help="skip the finite-difference check of the adjoint")
+    ap.add_argument("--fd-packets", type=float, default=1e6,
+                    help="packets of the finite-difference check (64 cells x 2 forward launches)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-step-seconds", type=float, default=8.0)

@@ -68,6 +68,7 @@ enum {
 enum { RT_GRID_CARTESIAN = 0, RT_GRID_OCTREE = 1, RT_GRID_RECTILINEAR = 2 };
 enum { RT_SOURCE_POINT = 0, RT_SOURCE_EXPDISK = 1, RT_SOURCE_PLUMMER = 2 };
 enum { RT_DEPOSIT_NEAREST = 0, RT_DEPOSIT_BILINEAR = 1, RT_DEPOSIT_SED = 2 };
+enum { RT_LAYOUT_AUTO = 0, RT_LAYOUT_ROW_MAJOR = 1 };
 
 /* Dust grid (Sect. 2.2: constant density per cell; Sect. 2.4 and Table 1(d):
  * grid kinds).
@@ -87,7 +88,13 @@ enum { RT_DEPOSIT_NEAREST = 0, RT_DEPOSIT_BILINEAR = 1, RT_DEPOSIT_SED = 2 };
  *       leaf with leaf id -(child[n] + 1); density float32 [n_leaves];
  *       cell id = leaf id.  Depth at most 21.
  *   bounds: xmin, xmax, ymin, ymax, zmin, zmax (FP64; the kernels use FP32).
- *   Pointers are host pointers unless on_device = 1.  Data is copied. */
+ *   Pointers are host pointers unless on_device = 1.  Data is copied.
+ *   layout (cartesian and rectilinear grids): how the library stores the
+ *       cells on the device.  RT_LAYOUT_AUTO (0): the axis whose cell faces a
+ *       ray crosses most often (most cells per unit length) is stored
+ *       unit-stride, then the next; RT_LAYOUT_ROW_MAJOR (1): x fastest.  Only
+ *       the speed differs: inputs, read-outs and cell ids are row-major
+ *       either way. */
 typedef struct {
   int32_t kind;
   int32_t nx, ny, nz;
@@ -97,7 +104,7 @@ typedef struct {
   const int32_t* child;
   int64_t n_leaves;
   int32_t on_device;
-  int32_t reserved;
+  int32_t layout;         /* RT_LAYOUT_AUTO or RT_LAYOUT_ROW_MAJOR */
   const double* edges[3]; /* RT_GRID_RECTILINEAR: cell edges per axis (host or device, as on_device) */
 } rt_grid_desc;
 
@@ -391,6 +398,15 @@ rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t n_lambda, 
                                     const rt_instrument_desc* instruments, double* const* images,
                                     double* absorption, uint64_t n_per_lambda, uint64_t first_packet_id,
                                     uint64_t seed, const rt_launch_opts* opts, rt_stats* stats_out, void* stream);
+
+/* Read bandwidth (GB/s, best of `repeats`) of the library's own kernel
+ * streaming a device buffer of `bytes` bytes `passes` times with loads cached
+ * in L2 only; a buffer well inside the L2 (a few tens of MB) gives the L2
+ * read bandwidth, one far larger the HBM read bandwidth.  This is the
+ * denominator of roofline fractions for kernels whose working set stays in
+ * L2; the paper has no counterpart.  Allocates and frees its buffer.
+ * Errors: RT_ERR_ARG, RT_ERR_CUDA (message: rt_last_error(NULL)). */
+rt_status rt_probe_bandwidth(int32_t device, uint64_t bytes, int32_t passes, int32_t repeats, double* gb_per_s);
 
 /* ---------------------------------------------------------------- batches
  * Many small independent models in one persistent launch, for the parameter

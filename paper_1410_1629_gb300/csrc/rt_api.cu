@@ -81,6 +81,13 @@ struct rt_ctx_s {
   float* d_density = nullptr;
   int32_t* d_child = nullptr;
   float* d_edges = nullptr;  // rectilinear grids: FP32 edges, x then y then z (nx + ny + nz + 3)
+  // storage order of cartesian and rectilinear grids (crossing_order_strides):
+  // the density copy the forward kernels read and the order of the absorption
+  // tallies; permuted = not row-major
+  int stride[3] = {1, 0, 0};
+  bool permuted = false;
+  float* d_density_s = nullptr;
+  double* d_abs_tmp = nullptr;  // one wavelength of row-major absorption, for read-outs to host memory
   // optics
   int n_lambda = 0;
   std::vector<double> kappa, albedo, g;
@@ -234,6 +241,9 @@ void free_grid(rt_ctx c) {
   pool_release(c, c->d_density, (size_t)c->n_cells * sizeof(float));
   pool_release(c, c->d_child, (size_t)c->n_nodes * sizeof(int32_t));
   pool_release(c, c->d_edges, (size_t)(c->nx + c->ny + c->nz + 3) * sizeof(float));
+  pool_release(c, c->d_density_s, (size_t)c->n_cells * sizeof(float));
+  pool_release(c, c->d_abs_tmp, (size_t)c->n_cells * sizeof(double));
+  c->permuted = false;
   pool_release(c, c->d_absorption, (size_t)c->n_lambda * c->n_cells * sizeof(double));
   for (auto& p : c->d_columns) pool_release(c, p, (size_t)c->n_cells * sizeof(float));
   for (auto& p : c->d_line_dep) pool_release(c, p, (size_t)c->n_cells * sizeof(double));
@@ -642,6 +652,19 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
   }
   c->grid_kind = d->kind;
   c->nx = d->nx; c->ny = d->ny; c->nz = d->nz;
+  c->stride[0] = 1; c->stride[1] = d->nx; c->stride[2] = d->nx * d->ny;
+  c->permuted = false;
+  if (d->kind != RT_GRID_OCTREE && d->layout != RT_LAYOUT_ROW_MAJOR) {
+    const int n3[3] = {d->nx, d->ny, d->nz};
+    const double ext[3] = {d->bounds[1] - d->bounds[0], d->bounds[3] - d->bounds[2], d->bounds[5] - d->bounds[4]};
+    crossing_order_strides(n3, ext, c->stride);
+    c->permuted = !(c->stride[0] == 1 && c->stride[1] == d->nx);
+  }
+  if (c->permuted) {
+    RT_CUDA(c, pool_alloc(c, &c->d_density_s, (size_t)n_cells * sizeof(float)));
+    RT_CUDA(c, launch_to_storage(c->d_density, c->d_density_s, d->nx, d->ny, d->nz, c->stride, nullptr));
+    RT_CUDA(c, cudaStreamSynchronize(nullptr));
+  }
   std::memcpy(c->bounds, d->bounds, sizeof c->bounds);
   c->n_cells = n_cells;
   c->n_nodes = n_nodes;
@@ -870,7 +893,8 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
       p.inv_d[a] = (float)(1.0 / d);
     }
   }
-  p.density = c->d_density;
+  p.density = c->permuted ? c->d_density_s : c->d_density;
+  for (int a = 0; a < 3; ++a) p.stride[a] = c->stride[a];
   p.child = c->d_child;
   p.n_nodes = c->n_nodes;
   if (c->grid_kind == RT_GRID_RECTILINEAR) {
@@ -1016,6 +1040,7 @@ rt_status rt_update_density(rt_ctx c, const float* density, int32_t on_device, v
     RT_CUDA(c, cudaStreamSynchronize(s));
     RT_CUDA(c, cudaMemcpy(c->d_density, density, bytes, cudaMemcpyHostToDevice));
   }
+  if (c->permuted) RT_CUDA(c, launch_to_storage(c->d_density, c->d_density_s, c->nx, c->ny, c->nz, c->stride, s));
   return RT_OK;
 }
 
@@ -1056,7 +1081,8 @@ rt_status rt_adjoint(rt_ctx c, const double* const* adj_images, int32_t n_adj_im
     p.d[a] = (float)d;
     p.inv_d[a] = (float)(1.0 / d);
   }
-  p.density = c->d_density;
+  p.density = c->d_density;  // row-major: the adjoint keeps the row-major order
+  row_major_strides(p);
   p.n_cells = c->n_cells;
   p.n_lambda = c->n_lambda;
   p.n_sources = (int)c->sources.size();
@@ -1274,7 +1300,23 @@ rt_status rt_read_absorption(rt_ctx c, double* dst, size_t n_elems, int32_t on_d
   const size_t n = (size_t)c->n_lambda * c->n_cells;
   if (n_elems != n) return fail(c, RT_ERR_ARG, "rt_read_absorption: n_elems %zu != %zu", n_elems, n);
   if (set_device(c) != RT_OK) return RT_ERR_CUDA;
-  return copy_out(c, dst, c->d_absorption, n, on_device, stream);
+  if (!c->permuted) return copy_out(c, dst, c->d_absorption, n, on_device, stream);
+  // tallies in storage order: back to row-major into dst, or wavelength by
+  // wavelength through a device buffer for a host destination
+  cudaStream_t s = (cudaStream_t)stream;
+  if (on_device) {
+    RT_CUDA(c, launch_from_storage(c->d_absorption, dst, c->n_lambda, c->nx, c->ny, c->nz, c->stride, s));
+    return RT_OK;
+  }
+  if (!c->d_abs_tmp) RT_CUDA(c, pool_alloc(c, &c->d_abs_tmp, (size_t)c->n_cells * sizeof(double)));
+  for (int l = 0; l < c->n_lambda; ++l) {
+    RT_CUDA(c, launch_from_storage(c->d_absorption + (size_t)l * c->n_cells, c->d_abs_tmp, 1, c->nx, c->ny, c->nz,
+                                   c->stride, s));
+    RT_CUDA(c, cudaMemcpyAsync(dst + (size_t)l * c->n_cells, c->d_abs_tmp, (size_t)c->n_cells * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+  }
+  RT_CUDA(c, cudaStreamSynchronize(s));
+  return RT_OK;
 }
 
 rt_status rt_read_images(rt_ctx c, int32_t id, double* dst, size_t n_elems, int32_t on_device, void* stream) {

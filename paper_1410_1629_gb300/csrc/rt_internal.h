@@ -79,6 +79,11 @@ struct FwdParams {
   const int32_t* child;  // octree only
   long long n_nodes;     // octree only
   const float* edge[3];  // rectilinear only: cell edges per axis, n + 1 each
+  // storage strides of the cell index (cartesian and rectilinear grids): the
+  // density and absorption of cell (ix, iy, iz) sit at ix stride[0] +
+  // iy stride[1] + iz stride[2]; row-major is (1, nx, nx ny).  Cell ids seen
+  // outside the kernels (records, traces, the tape, read-outs) are row-major.
+  int stride[3];
   long long n_cells;
   // problem
   int n_lambda, n_sources, n_instr;
@@ -152,6 +157,27 @@ inline void frame_axes(double inclination, double azimuth, double position_angle
 
 // Message returned by rt_last_error(NULL) (calls without a context).
 void set_context_free_error(const char* msg);
+
+// Row-major storage strides (1, nx, nx ny) for p.stride.
+inline void row_major_strides(FwdParams& p) {
+  p.stride[0] = 1;
+  p.stride[1] = p.nx;
+  p.stride[2] = p.nx * p.ny;
+}
+
+// Storage order of a cartesian or rectilinear grid: the axes sorted by how
+// often an isotropic ray crosses their cell faces (cells per unit length,
+// n_a / extent_a), most often first (stable: ties keep x, y, z), so that the
+// most frequent step of a walk is unit-stride.  Fills strides[3].
+void crossing_order_strides(const int n[3], const double extent[3], int strides[3]);
+
+// Copies between row-major order and the storage order of `strides`
+// (rt_layout.cu): a float field into storage order, and n_lambda double
+// fields back to row-major.
+cudaError_t launch_to_storage(const float* src, float* dst, int nx, int ny, int nz, const int strides[3],
+                              cudaStream_t stream);
+cudaError_t launch_from_storage(const double* src, double* dst, int n_lambda, int nx, int ny, int nz,
+                                const int strides[3], cudaStream_t stream);
 
 // Launchers (rt_forward.cu).
 cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaStream_t stream);

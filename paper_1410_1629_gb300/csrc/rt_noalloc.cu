@@ -257,6 +257,7 @@ extern "C" rt_status rt_launch_packets_noalloc(const rt_grid_desc* grid, int32_t
     p.inv_d[a] = (float)(1.0 / d);
   }
   p.density = grid->density;
+  row_major_strides(p);
   p.child = nullptr;
   p.n_cells = (long long)grid->nx * grid->ny * grid->nz;
   p.n_lambda = n_lambda;

@@ -157,6 +157,14 @@ __device__ __forceinline__ float first_min(float tx, float ty, float tz, int& ax
 
 __device__ __forceinline__ float pick(int a, float3 v) { return a == 2 ? v.z : (a == 1 ? v.y : v.x); }
 
+// Storage stride of axis a: the launch's (FwdParams), row-major for any
+// other geometry (one model of a batch).
+template <class Geo>
+__device__ __forceinline__ int stride_of(const Geo& P, int a) {
+  return a == 0 ? 1 : (a == 1 ? P.nx : P.nx * P.ny);
+}
+__device__ __forceinline__ int stride_of(const FwdParams& P, int a) { return P.stride[a]; }
+
 // ---------------------------------------------------------------- cartesian grid
 struct CartGrid {
   static constexpr bool kColumns = true;  // peel-offs along grid axes may use column sums
@@ -205,7 +213,7 @@ struct CartGrid {
     w.tx = id.x != 0.0f ? plane_t(P, 0, w.ix + (id.x > 0.0f), x.x, id.x) : RT_INF;
     w.ty = id.y != 0.0f ? plane_t(P, 1, w.iy + (id.y > 0.0f), x.y, id.y) : RT_INF;
     w.tz = id.z != 0.0f ? plane_t(P, 2, w.iz + (id.z > 0.0f), x.z, id.z) : RT_INF;
-    w.cell = w.ix + P.nx * (w.iy + P.ny * w.iz);
+    w.cell = w.ix * stride_of(P, 0) + w.iy * stride_of(P, 1) + w.iz * stride_of(P, 2);
     return true;
   }
 
@@ -225,7 +233,7 @@ struct CartGrid {
     const int ia = (bz ? w.iz : (by ? w.iy : w.ix)) + step;
     const int na = bz ? P.nz : (by ? P.ny : P.nx);
     if ((unsigned)ia >= (unsigned)na) return false;
-    w.cell += step * (bz ? P.nx * P.ny : (by ? P.nx : 1));
+    w.cell += step * (bz ? stride_of(P, 2) : (by ? stride_of(P, 1) : stride_of(P, 0)));
     const float xa = bz ? x.z : (by ? x.y : x.x);
     const float da = bz ? P.d[2] : (by ? P.d[1] : P.d[0]);
     const float loa = bz ? P.lo[2] : (by ? P.lo[1] : P.lo[0]);
@@ -240,6 +248,10 @@ struct CartGrid {
   }
 
   __device__ static __forceinline__ int cell(const Walk& w) { return w.cell; }
+
+  // The row-major cell id (records, traces, the tape).
+  template <class Geo>
+  __device__ static __forceinline__ int id(const Geo& P, const Walk& w) { return w.ix + P.nx * (w.iy + P.ny * w.iz); }
 
   __device__ static __forceinline__ Cell carried(const Walk& w) { return Cell{w.ix, w.iy, w.iz}; }
 
@@ -302,7 +314,7 @@ struct RectGrid {
     w.tx = id.x != 0.0f ? (edge(P, 0, w.ix + (id.x > 0.0f)) - x.x) * id.x : RT_INF;
     w.ty = id.y != 0.0f ? (edge(P, 1, w.iy + (id.y > 0.0f)) - x.y) * id.y : RT_INF;
     w.tz = id.z != 0.0f ? (edge(P, 2, w.iz + (id.z > 0.0f)) - x.z) * id.z : RT_INF;
-    w.cell = w.ix + P.nx * (w.iy + P.ny * w.iz);
+    w.cell = w.ix * P.stride[0] + w.iy * P.stride[1] + w.iz * P.stride[2];
     return true;
   }
 
@@ -318,7 +330,7 @@ struct RectGrid {
     const int ia = (bz ? w.iz : (by ? w.iy : w.ix)) + step;
     const int na = bz ? P.nz : (by ? P.ny : P.nx);
     if ((unsigned)ia >= (unsigned)na) return false;
-    w.cell += step * (bz ? P.nx * P.ny : (by ? P.nx : 1));
+    w.cell += step * (bz ? P.stride[2] : (by ? P.stride[1] : P.stride[0]));
     const float xa = bz ? x.z : (by ? x.y : x.x);
     const float t_new = (edge(P, axis, ia + (step > 0)) - xa) * ida;
     w.ix = (axis == 0) ? ia : w.ix;
@@ -331,6 +343,10 @@ struct RectGrid {
   }
 
   __device__ static __forceinline__ int cell(const Walk& w) { return w.cell; }
+
+  __device__ static __forceinline__ int id(const FwdParams& P, const Walk& w) {
+    return w.ix + P.nx * (w.iy + P.ny * w.iz);
+  }
 
   __device__ static __forceinline__ Cell carried(const Walk& w) { return Cell{w.ix, w.iy, w.iz}; }
 
@@ -535,6 +551,8 @@ struct OctGrid {
 
   __device__ static __forceinline__ int cell(const Walk& w) { return w.leaf; }
 
+  __device__ static __forceinline__ int id(const FwdParams&, const Walk& w) { return w.leaf; }
+
   __device__ static __forceinline__ Cell carried(const Walk& w) {
     Cell c;
     c.leaf = w.leaf;
@@ -671,8 +689,9 @@ __device__ __forceinline__ bool column_tau(const FwdParams& P, float3 x, bool kn
   const float xa = a == 0 ? x.x : (a == 1 ? x.y : x.z);
   const float plane = fmaf((float)(i + (up ? 1 : 0)), P.d[a], P.lo[a]);
   const float ds0 = fmaxf(up ? plane - xa : xa - plane, 0.0f);
-  const int cell = c.ix + P.nx * (c.iy + P.ny * c.iz);
-  th = kappa * fmaf(load_density(&P.density[cell]), ds0, __ldg(&I.column[cell]));
+  const int cell = c.ix + P.nx * (c.iy + P.ny * c.iz);  // row-major: the column sums
+  const int slot = c.ix * P.stride[0] + c.iy * P.stride[1] + c.iz * P.stride[2];
+  th = kappa * fmaf(load_density(&P.density[slot]), ds0, __ldg(&I.column[cell]));
   n_cross = (unsigned long long)(up ? n - i : i + 1);
   return true;
 }
@@ -1006,7 +1025,7 @@ __device__ __forceinline__ void finish_path2(const FwdParams& P, Lane<G>& s, Lan
   if (kTape) {
     // the record's third sector, whole
     float4* t = reinterpret_cast<float4*>(&s.rec[s.event()]);
-    t[4] = make_float4(__int_as_float(s.h), __int_as_float(s.axis_in), __int_as_float(G::cell(s.w)), s.kr_h);
+    t[4] = make_float4(__int_as_float(s.h), __int_as_float(s.axis_in), __int_as_float(G::id(P, s.w)), s.kr_h);
     t[5] = make_float4(s.rem, s.g.x, s.g.y, s.g.z);
   }
   const float s_star = s.aux0;
@@ -1016,7 +1035,7 @@ __device__ __forceinline__ void finish_path2(const FwdParams& P, Lane<G>& s, Lan
   s.x = x;
   s.has_cell() = true;
   bt->events += 1u;
-  trace_row(P, s, s.event(), G::cell(s.w), s.L(), 0.0, 0.0);
+  trace_row(P, s, s.event(), G::id(P, s.w), s.L(), 0.0, 0.0);
   s.q() = 0;
   s.phase = kPeelScan;
 }

@@ -23,6 +23,9 @@ RT_OK, RT_ERR_ARG, RT_ERR_STATE, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR
 RT_GRID_CARTESIAN, RT_GRID_OCTREE, RT_GRID_RECTILINEAR = 0, 1, 2
 RT_SOURCE_POINT, RT_SOURCE_EXPDISK, RT_SOURCE_PLUMMER = 0, 1, 2
 RT_DEPOSIT_NEAREST, RT_DEPOSIT_BILINEAR, RT_DEPOSIT_SED = 0, 1, 2
+RT_LAYOUT_AUTO, RT_LAYOUT_ROW_MAJOR = 0, 1
+TRACE_DTYPE = np.dtype([("event", "<i4"), ("reserved", "<i4"), ("cell", "<i8"), ("x", "<f8", 3), ("k", "<f8", 3),
+                        ("L", "<f8"), ("tau_path", "<f8"), ("tau_star", "<f8")])
 
 _SOURCE_KIND = {"point": RT_SOURCE_POINT, "expdisk": RT_SOURCE_EXPDISK, "plummer": RT_SOURCE_PLUMMER}
 
@@ -37,7 +40,7 @@ class rt_grid_desc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("bounds", ctypes.c_double * 6), ("density", ctypes.c_void_p), ("n_nodes", ctypes.c_int64),
                 ("child", ctypes.c_void_p), ("n_leaves", ctypes.c_int64), ("on_device", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("edges", ctypes.c_void_p * 3)]
+                ("layout", ctypes.c_int32), ("edges", ctypes.c_void_p * 3)]
 
 
 class rt_source_desc(ctypes.Structure):
@@ -152,6 +155,8 @@ SIGNATURES = {
     "rt_batch_read_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(rt_stats)]),
     "rt_batch_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p]),
+    "rt_probe_bandwidth": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -363,6 +368,15 @@ def rt_launch_packets_noalloc(grid_desc_, kappa, albedo, g, sources, luminositie
         raise RTError(st, lib().rt_last_error(None).decode())
 
 
+def rt_probe_bandwidth(device=0, nbytes=32 << 20, passes=20, repeats=5) -> float:
+    """Read bandwidth in GB/s of a buffer of `nbytes` (L2 if it fits)."""
+    out = ctypes.c_double(0.0)
+    st = lib().rt_probe_bandwidth(int(device), int(nbytes), int(passes), int(repeats), ctypes.byref(out))
+    if st != RT_OK:
+        raise RTError(st, lib().rt_last_error(None).decode())
+    return out.value
+
+
 def rt_batch_create(ctx, descs) -> int:
     arr = (rt_model_desc * len(descs))(*descs)
     b = ctypes.c_int32()
@@ -560,12 +574,13 @@ class Simulation:
     sources and instruments uploaded once; packets launched any number of
     times; tallies read into torch tensors or numpy arrays."""
 
-    def __init__(self, problem, device: int = 0):
+    def __init__(self, problem, device: int = 0, layout: int = 0):
         self.problem = problem
         self.device = int(device)
         self.ctx = rt_context_create(self.device)
         try:
             desc, keep = grid_desc(problem.grid)
+            desc.layout = int(layout)
             self.grid_id = rt_create_grid(self.ctx, desc)
             del keep
             rt_set_optics(self.ctx, self.grid_id, problem.kappa, problem.albedo, problem.g, problem.wavelengths)
@@ -610,6 +625,22 @@ class Simulation:
 
     def reset(self, stream=None):
         rt_reset_tallies(self.ctx, stream)
+
+    def trace(self, packet, lam=0, n_per_lambda=None, seed=None, max_rows=None, **opts):
+        """Per-event trace (rt_trace_row) of one packet: a launch of the
+        packets [0, n_per_lambda) with the trace of `packet` at wavelength
+        `lam` recorded (it adds to the tallies like any launch)."""
+        import torch
+        n = self.problem.run.n_per_lambda if n_per_lambda is None else n_per_lambda
+        cap = int(max_rows or (self.problem.run.max_events + 2))
+        buf = torch.zeros(cap * TRACE_DTYPE.itemsize, dtype=torch.uint8, device=f"cuda:{self.device}")
+        self.launch(n, 0, seed, trace=buf.data_ptr(), trace_capacity=cap, trace_packet=int(packet),
+                    trace_lambda=int(lam), **opts)
+        rows = buf.cpu().numpy().view(TRACE_DTYPE)
+        st = self.stats()
+        n_rows = int(np.count_nonzero(rows["L"] != 0.0))
+        del st
+        return rows[:n_rows].copy()
 
     def tune(self, n_per_lambda, seed=0, stream=None, **opts) -> int:
         """Choose the per-event deferral threshold on a sample launch (tallies zeroed after)."""

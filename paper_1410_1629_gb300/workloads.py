@@ -508,10 +508,10 @@ def clumpy_octree(n_particles=1_000_000, n_samples=100_000_000, target_leaves=5_
     # sample counts per node at every level
     level_keys, level_counts = [], []
     for L in range(max_level + 1):
-        k = keys >> np.uint32(3 * (max_level - L))
-        u, c = np.unique(k, return_counts=True)
-        level_keys.append(u)
-        level_counts.append(c)
+        k = keys >> np.uint32(3 * (max_level - L))  # still sorted: runs of equal keys
+        starts = np.flatnonzero(np.concatenate(([True], k[1:] != k[:-1])))
+        level_keys.append(k[starts])
+        level_counts.append(np.diff(np.append(starts, len(k))))
     # threshold in samples: leaves = 1 + 7 * (#nodes above threshold at levels < max_level)
     def n_leaves(thr):
         return 1 + 7 * sum(int((level_counts[L] > thr).sum()) for L in range(max_level))

@@ -180,9 +180,9 @@ def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_rec
     wavelengths, and per group of cells when `groups` is given).  With
     records, the corrections are bounded: at most 1e-4 of the records plus
     10 may be GPU-only or oracle-only, at most 1e-3 plus 10 may be FP32 flips
-    (pixel or value), every pixel flip lands in a neighbouring pixel, and
-    every bin that violates the rule before the correction must be one the
-    correction changed."""
+    (pixel or value), of which at most 1e-4 plus 10 land beyond the
+    neighbouring pixel, and every bin that violates the rule before the
+    correction must be one the correction changed."""
     rep = {}
     st_g, st_o = gpu["stats"], ora["stats"]
     # emitted, escaped and absorbed relative to themselves; the truncated
@@ -210,6 +210,10 @@ def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_rec
         rep["corrections_limit"] = 1e-4 * rep["records"] + 10
         rep["flip_total"] = rep["flips"] + rep["value_flips"]
         rep["flip_limit"] = 1e-3 * rep["records"] + 10
+        # pixel flips beyond the neighbouring pixel: a packet whose FP32 path
+        # parted from the FP64 one (an interaction in a near-empty cell after
+        # dense ones moves far for a small optical-depth difference)
+        rep["far_flip_limit"] = 1e-4 * rep["records"] + 10
     else:
         imgs = gpu["images"]
     rep["pixels"] = []
@@ -252,7 +256,8 @@ def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_rec
           and all(p.get("blocks", {"violations": 0})["violations"] == 0 for p in rep["pixels"])
           and unexplained == 0
           and (not use_records or (rep["corrections"] <= rep["corrections_limit"]
-                                   and rep["flip_total"] <= rep["flip_limit"] and rep["far_flips"] == 0)))
+                                   and rep["flip_total"] <= rep["flip_limit"]
+                                   and rep["far_flips"] <= rep["far_flip_limit"])))
     rep["ok"] = bool(ok)
     return rep
 

@@ -78,14 +78,14 @@ def test_spiral_example_first_packet_ids(grid):
     """The paper's spiral-galaxy example at full size (256 x 256 x 128
     power-law cells, or 256 x 256 x 72 equal cells; 1200 x 300 edge-on
     frame; 1e7-packet weights) on its first 1e5 packet ids: bins of at least
-    1e3 oracle contributions (pixels, 8 x 8 blocks, cells, 4^3-cell blocks)
-    within 1e-4, totals within 1e-6."""
+    1e3 oracle contributions (pixels, 20 x 20 blocks, cells, 4^3-cell
+    blocks) within 1e-4, totals within 1e-6."""
     prob = W.spiral_example(grid) if grid == "powcub" else W.spiral_example("cartesian", n_z=72)
     prob.instruments[0].channels = 3
     n_ids = 100_000
     g = PAR.gpu_run(prob, n_ids, n_norm=prob.run.n_per_lambda, records_cap=40 * n_ids)
     o = PAR.oracle_run(prob, n_ids, n_norm=prob.run.n_per_lambda, records_cap=40 * n_ids)
     assert g["raw_stats"]["device_flags"] == 0
-    rep = PAR.compare(g, o, prob, groups=PAR.cell_groups(prob.grid))
+    rep = PAR.compare(g, o, prob, groups=PAR.cell_groups(prob.grid), block=20)
     _assert_ok(rep)
     assert rep["pixels"][0]["blocks"]["bins"] > 0 and rep["cell_groups"]["bins"] > 0

@@ -84,22 +84,25 @@ def test_changed_cell_fails(runs):
     assert not rep["ok"] and rep["cells"]["violations"] == 1
 
 
-def test_far_pixel_moves_fail(runs):
-    """A record whose GPU pixel is far from the oracle's is not an FP32 flip."""
+def test_far_pixel_moves_are_bounded(runs):
+    """Records whose GPU pixel is far from the oracle's (parted paths) are
+    repaired like flips, but only up to 1e-4 of the records plus 10."""
     prob, r = runs
     g = _gpu_like(r)
-    i = int(np.argmax(g["records"]["value"]))
-    rec = g["records"][i]
     nx = prob.instruments[0].nx
-    old = int(rec["pixel"])
-    new = (old + 5 * nx + 5) % (nx * nx)
-    for ch in (0, 1 if rec["event"] == 0 else 2):
-        img = g["images"][rec["instr"]][ch, rec["lam"]].reshape(-1)
-        img[old] -= rec["value"]
-        img[new] += rec["value"]
-    g["records"]["pixel"][i] = new
+    n_far = int(1e-4 * len(g["records"]) + 10) + 5
+    sel = np.argsort(g["records"]["value"])[::-1][:n_far]
+    for i in sel:
+        rec = g["records"][i]
+        old = int(rec["pixel"])
+        new = (old + 5 * nx + 5) % (nx * nx)
+        for ch in (0, 1 if rec["event"] == 0 else 2):
+            img = g["images"][rec["instr"]][ch, rec["lam"]].reshape(-1)
+            img[old] -= rec["value"]
+            img[new] += rec["value"]
+        g["records"]["pixel"][i] = new
     rep = PAR.compare(g, r, prob)
-    assert rep["far_flips"] == 1 and not rep["ok"]
+    assert rep["far_flips"] == n_far and rep["far_flips"] > rep["far_flip_limit"] and not rep["ok"]
 
 
 def test_value_flips_are_bounded(runs):
