@@ -474,9 +474,11 @@ def fd_check(prob, sim, adj, opts, n, stream):
     dev = adj.device
 
     def functional(dens):
+        # the copy runs on torch's stream, where the buffer was made, and is
+        # waited for before the buffer can be released
         d = torch.from_numpy(np.ascontiguousarray(dens, dtype=np.float32)).to(dev)
+        rt.rt_update_density(sim.ctx, d.data_ptr(), 1, torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
-        rt.rt_update_density(sim.ctx, d.data_ptr(), 1, stream.cuda_stream)
         sim.reset(stream=stream)
         sim.launch(n, 0, prob.run.seed, stream=stream, **opts)
         with torch.cuda.stream(stream):
@@ -491,8 +493,8 @@ def fd_check(prob, sim, adj, opts, n, stream):
         dn[c] = np.float32(rho[c] * (1 - eps))
         fd[i] = (functional(up) - functional(dn)) / (float(up[c]) - float(dn[c]))
     d = torch.from_numpy(rho).to(dev)
+    rt.rt_update_density(sim.ctx, d.data_ptr(), 1, torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
-    rt.rt_update_density(sim.ctx, d.data_ptr(), 1, stream.cuda_stream)
     grad = torch.zeros(prob.grid.n_cells, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
     rt.rt_adjoint(sim.ctx, [adj.data_ptr()], 0, grad.data_ptr(), n, 0, prob.run.seed, sim.opts(**opts),

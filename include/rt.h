@@ -69,6 +69,7 @@ enum { RT_GRID_CARTESIAN = 0, RT_GRID_OCTREE = 1, RT_GRID_RECTILINEAR = 2 };
 enum { RT_SOURCE_POINT = 0, RT_SOURCE_EXPDISK = 1, RT_SOURCE_PLUMMER = 2 };
 enum { RT_DEPOSIT_NEAREST = 0, RT_DEPOSIT_BILINEAR = 1, RT_DEPOSIT_SED = 2 };
 enum { RT_LAYOUT_AUTO = 0, RT_LAYOUT_ROW_MAJOR = 1 };
+enum { RT_EMITTER_SOURCES = 0, RT_EMITTER_DUST = 1 };
 
 /* Dust grid (Sect. 2.2: constant density per cell; Sect. 2.4 and Table 1(d):
  * grid kinds).
@@ -206,7 +207,11 @@ typedef struct {
                            and deposits; only the order of the FP64 image additions differs.   */
   int32_t time_parts;   /* 1: record CUDA events around the parts of this launch on its stream,
                            read back by rt_read_launch_times                               */
-  int32_t reserved;
+  int32_t emitter;      /* RT_EMITTER_SOURCES (0): the sources emit; RT_EMITTER_DUST (1): the dust
+                           cells emit their thermal luminosity (rt_set_dust_emission), a cell
+                           drawn in proportion to its luminosity at the packet's wavelength, a
+                           uniform position in it, an isotropic direction; a wavelength at which
+                           the dust emits nothing launches packets of zero weight that end at once */
 } rt_launch_opts;
 
 /* Tallies since the last rt_reset_tallies. */
@@ -268,7 +273,8 @@ rt_status rt_add_sources(rt_ctx ctx, int32_t n, const rt_source_desc* sources);
  * RT_ERR_STATE (no optics), RT_ERR_OOM. */
 rt_status rt_add_instruments(rt_ctx ctx, int32_t n, const rt_instrument_desc* instruments, int32_t* ids);
 
-/* Run n_per_lambda packets at every wavelength, with packet ids
+/* Run n_per_lambda packets at every wavelength (from the sources, or from the
+ * dust with opts->emitter = RT_EMITTER_DUST), with packet ids
  * [first_packet_id, first_packet_id + n_per_lambda), Philox key (seed,
  * opts->model_id).  Tallies accumulate across launches until
  * rt_reset_tallies, so id ranges can be split over launches.  Asynchronous
@@ -303,6 +309,50 @@ rt_status rt_reset_tallies(rt_ctx ctx, void* stream);
  * asynchronous on stream; 0: host pointer, returns when the copy is done.
  * Errors: RT_ERR_ARG (size mismatch), RT_ERR_STATE, RT_ERR_CUDA. */
 rt_status rt_read_absorption(rt_ctx ctx, double* dst, size_t n_elems, int32_t dst_on_device, void* stream);
+
+/* ---------------------------------------------------------------- panchromatic mode
+ * A panchromatic simulation (Sect. 2.1, 2.2: oligochromatic vs panchromatic)
+ * integrates the absorbed luminosity over the wavelength grid to find the
+ * dust temperature and adds the dust's thermal emission.  Equilibrium
+ * emission of one grain type: cell c at temperature T emits
+ *   S m_c sum_l kabs_l dlambda_l beta_l(T),   beta_l(T) = lambda_l^-5 / (exp(C2 / (lambda_l T)) - 1),
+ * m_c = rho_c V_c its dust mass, kabs_l = kappa_l (1 - albedo_l), lambda in um
+ * (rt_set_optics's wavelengths, at least two, increasing), C2 = hc/k =
+ * 14387.77 um K, dlambda_l the widths of bins centred on the wavelengths on a
+ * logarithmic scale (inner borders at geometric means, outer borders
+ * mirrored), and S = emission_scale, the caller's factor for the Planck
+ * constant 2hc^2, 4 pi and the units of luminosity, mass and length.
+ * Cartesian and rectilinear grids. */
+
+/* Equilibrium temperature of every cell: the T at which it emits the
+ * luminosity it absorbed summed over the wavelengths, found by bisection in
+ * ln T between t_min and t_max (64 halvings).  absorption: row-major float64
+ * [n_lambda][n_cells] (host, or device with absorption_on_device = 1), or
+ * NULL for the context's absorption tallies.  temperature: float64 [n_cells]
+ * (host, or device with dst_on_device = 1): 0 for cells without dust or
+ * without absorbed luminosity, t_max for cells that would need more and
+ * t_min for cells that would need less (counted in *n_clamped if not NULL).
+ * Synchronous.
+ * Errors: RT_ERR_STATE (no grid or optics, no wavelengths), RT_ERR_ARG
+ * (octree grid, scale <= 0, bad range), RT_ERR_CUDA, RT_ERR_OOM. */
+rt_status rt_dust_temperature(rt_ctx ctx, double emission_scale, double t_min, double t_max,
+                              const double* absorption, int32_t absorption_on_device, double* temperature,
+                              int32_t dst_on_device, int32_t* n_clamped, void* stream);
+
+/* Thermal emission of the dust at the temperatures [n_cells] (host, or
+ * device with on_device = 1; e.g. from rt_dust_temperature): per cell and
+ * wavelength S m_c kabs_l dlambda_l beta_l(T_c), and its running sums over
+ * the cells, from which launches with opts.emitter = RT_EMITTER_DUST draw
+ * the emitting cell.  Packet weights are the per-wavelength totals over
+ * n_norm.  Kept until the optics, grid or emission change.  Synchronous.
+ * Errors: as rt_dust_temperature. */
+rt_status rt_set_dust_emission(rt_ctx ctx, const double* temperature, int32_t on_device, double emission_scale,
+                               void* stream);
+
+/* The thermal emission set by rt_set_dust_emission, float64
+ * [n_lambda][n_cells] row-major; n_elems must match.  Conventions of
+ * rt_read_absorption.  Errors: RT_ERR_STATE (none set), RT_ERR_ARG. */
+rt_status rt_read_dust_emission(rt_ctx ctx, double* dst, size_t n_elems, int32_t dst_on_device, void* stream);
 
 /* Copy instrument `instrument_id`'s image, float64 [channels][n_lambda][ny][nx],
  * into dst; n_elems must match.  Same conventions as rt_read_absorption. */

@@ -69,7 +69,8 @@ class OrProblem(ctypes.Structure):
                 ("n_instr", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("kappa", ctypes.POINTER(ctypes.c_double)), ("albedo", ctypes.POINTER(ctypes.c_double)),
                 ("g", ctypes.POINTER(ctypes.c_double)), ("sources", ctypes.POINTER(OrSource)),
-                ("lum", ctypes.POINTER(ctypes.c_double)), ("instr", ctypes.POINTER(OrInstrument))]
+                ("lum", ctypes.POINTER(ctypes.c_double)), ("instr", ctypes.POINTER(OrInstrument)),
+                ("dust_lum", ctypes.POINTER(ctypes.c_double))]
 
 
 class OrOpts(ctypes.Structure):
@@ -142,6 +143,14 @@ def lib():
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int32,
                                          ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+            L.or_dust_temperature.restype = ctypes.c_int32
+            L.or_dust_temperature.argtypes = [ctypes.POINTER(OrProblem), ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+            L.or_dust_emission.restype = ctypes.c_int32
+            L.or_dust_emission.argtypes = [ctypes.POINTER(OrProblem), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_double)]
             L.or_vjp.restype = ctypes.c_int32
             L.or_vjp.argtypes = [ctypes.POINTER(OrProblem), ctypes.POINTER(OrOpts),
                                  ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
@@ -212,6 +221,11 @@ class _Marshalled:
         p.sources = srcs
         p.lum = _ptr(lum, ctypes.c_double)
         p.instr = instr
+        dust = getattr(problem, "dust_lum", None)
+        if dust is not None:
+            dl = np.ascontiguousarray(dust, dtype=np.float64).reshape(nl, dens.size)
+            self.keep.append(dl)
+            p.dust_lum = _ptr(dl, ctypes.c_double)
         self.problem = p
         self.n_lambda = nl
         self.n_cells = dens.size
@@ -425,3 +439,31 @@ def interaction(problem, x, k, u, lam=0, start_cell=-1):
     f = lib().or_interaction(ctypes.byref(m.problem), xx, kk, int(start_cell), int(lam), float(u), ox,
                              ctypes.byref(oc), ot)
     return np.array(ox[:]), int(oc.value), float(ot[0]), float(ot[1]), int(f)
+
+
+def dust_temperature(problem, absorption, scale, t_min=1.0, t_max=1e4):
+    """Equilibrium dust temperature per cell from the absorbed luminosity
+    [n_lambda, n_cells] (panchromatic mode).  Returns (T [n_cells], cells
+    held at t_min or t_max)."""
+    m = _Marshalled(problem)
+    lam = np.ascontiguousarray(problem.wavelengths, dtype=np.float64)
+    ab = np.ascontiguousarray(absorption, dtype=np.float64)
+    T = np.zeros(m.n_cells, dtype=np.float64)
+    rc = lib().or_dust_temperature(ctypes.byref(m.problem), _ptr(lam, ctypes.c_double), _ptr(ab, ctypes.c_double),
+                                   float(scale), float(t_min), float(t_max), _ptr(T, ctypes.c_double))
+    if rc < 0:
+        raise ValueError("or_dust_temperature: bad arguments")
+    return T, int(rc)
+
+
+def dust_emission(problem, T, scale):
+    """Thermal emission [n_lambda, n_cells] of the cells at temperatures T."""
+    m = _Marshalled(problem)
+    lam = np.ascontiguousarray(problem.wavelengths, dtype=np.float64)
+    TT = np.ascontiguousarray(T, dtype=np.float64)
+    out = np.zeros((m.n_lambda, m.n_cells), dtype=np.float64)
+    rc = lib().or_dust_emission(ctypes.byref(m.problem), _ptr(lam, ctypes.c_double), _ptr(TT, ctypes.c_double),
+                                float(scale), _ptr(out, ctypes.c_double))
+    if rc < 0:
+        raise ValueError("or_dust_emission: bad arguments")
+    return out

@@ -202,6 +202,8 @@ typedef struct {
   const or_source* sources;
   const double* lum;  // [n_sources][n_lambda]
   const or_instrument* instr;
+  const double* dust_lum;  // [n_lambda][n_cells]: thermal emission of the dust cells, emitted instead of the
+                           // sources (panchromatic mode), or NULL
 } or_problem;
 
 typedef struct {
@@ -548,6 +550,9 @@ struct Problem {
   std::vector<or_source> sources;
   std::vector<double> lum;  // [n_sources][n_lambda]
   std::vector<Frame> frames;
+  // dust emission instead of the sources: per wavelength the running sum of
+  // the cells' luminosities in cell order (empty: the sources emit)
+  std::vector<std::vector<double>> dust_cum;
 };
 
 Problem make_problem(const or_problem& in) {
@@ -571,6 +576,17 @@ Problem make_problem(const or_problem& in) {
   P.sources.assign(in.sources, in.sources + in.n_sources);
   P.lum.assign(in.lum, in.lum + (size_t)in.n_sources * in.n_lambda);
   for (int i = 0; i < in.n_instr; ++i) P.frames.push_back(make_frame(in.instr[i]));
+  if (in.dust_lum) {
+    const int64_t nc = G.n_cells();
+    P.dust_cum.assign((size_t)in.n_lambda, std::vector<double>((size_t)nc));
+    for (int l = 0; l < in.n_lambda; ++l) {
+      double run = 0.0;
+      for (int64_t c = 0; c < nc; ++c) {
+        run += in.dust_lum[(size_t)l * nc + c];
+        P.dust_cum[(size_t)l][(size_t)c] = run;
+      }
+    }
+  }
   return P;
 }
 
@@ -691,10 +707,28 @@ struct Transport {
 
   // Emission position and direction (Sect. 3.4: the source geometry draws a
   // random position from its density; the emission is isotropic).
-  void emit(uint64_t pid, int lam, V3d& x, V3d& k) {
+  void emit(uint64_t pid, int lam, V3d& x, V3d& k, int64_t* cell_out = nullptr) {
     double u[8];
     draw4(pid, lam, 0, 0, O.seed, O.model_id, u);
     draw4(pid, lam, 0, 1, O.seed, O.model_id, u + 4);
+    if (!P.dust_cum.empty()) {
+      // thermal dust emission: the cell with probability proportional to its
+      // luminosity at this wavelength (the first cell whose running sum
+      // exceeds u times the total), a uniform position inside it, an
+      // isotropic direction
+      const std::vector<double>& cum = P.dust_cum[(size_t)lam];
+      const double target = u[0] * cum.back();
+      const int64_t c = (int64_t)(std::upper_bound(cum.begin(), cum.end(), target) - cum.begin());
+      const int64_t cell = std::min<int64_t>(c, (int64_t)cum.size() - 1);
+      const Box b = P.grid.cell_box(cell);
+      x = {b.lo[0] + u[1] * (b.hi[0] - b.lo[0]), b.lo[1] + u[2] * (b.hi[1] - b.lo[1]),
+           b.lo[2] + u[3] * (b.hi[2] - b.lo[2])};
+      if (cell_out) *cell_out = cell;
+      double mu = 2.0 * u[6] - 1.0, st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
+      double ph = 2.0 * M_PI * u[7];
+      k = {st * std::cos(ph), st * std::sin(ph), mu};
+      return;
+    }
     // source component proportional to its luminosity at this wavelength
     size_t ns = P.sources.size();
     double total = 0.0;
@@ -843,15 +877,20 @@ struct Transport {
 
   void run_packet(uint64_t pid, int lam) {
     double Ltot = 0.0;
-    for (size_t s = 0; s < P.sources.size(); ++s) Ltot += P.lum[s * P.n_lambda + lam];
+    if (!P.dust_cum.empty()) {
+      Ltot = P.dust_cum[(size_t)lam].back();
+    } else {
+      for (size_t s = 0; s < P.sources.size(); ++s) Ltot += P.lum[s * P.n_lambda + lam];
+    }
     const double L0 = Ltot / (double)O.n_norm;
+    if (L0 == 0.0 && !P.dust_cum.empty()) return;  // the dust emits nothing at this wavelength
     const double kap = P.kappa[lam], alb = P.albedo[lam], g = P.g[lam];
     V3d x0, k;
-    emit(pid, lam, x0, k);
+    int64_t cell = -1;
+    emit(pid, lam, x0, k, &cell);
     V3<T> x = {T(x0.x), T(x0.y), T(x0.z)};
     T L = T(L0);
     t_emitted = t_emitted + L;
-    int64_t cell = -1;
     trace_row(0, -1, x, k, L, 0.0, 0.0);
     if (O.peel_emission) peel(x, cell, lam, L, false, k, pid, 0);
     for (int j = 1;; ++j) {
@@ -894,6 +933,58 @@ struct Transport {
     }
   }
 };
+
+// ---------------------------------------------------------------- panchromatic mode
+// A panchromatic simulation (Sect. 2.1, 2.2) integrates the absorbed energy
+// over a wavelength range to find the dust temperature and adds the dust's
+// thermal emission.  Equilibrium only: one grain type, each cell at the
+// temperature at which it emits what it absorbs.
+//   * wavelength bins: the grid points are bin centres on a logarithmic
+//     scale, the inner borders their geometric means, the outer borders
+//     mirrored; widths dlambda_l;
+//   * emission of cell c at temperature T: S m_c sum_l kabs_l dlambda_l
+//     beta_l(T), m_c = rho_c V_c, kabs_l = kappa_l (1 - albedo_l), beta_l(T) =
+//     lambda_l^-5 / (exp(C2 / (lambda_l T)) - 1) the Planck function per unit
+//     wavelength up to its constant (lambda in um, C2 = hc/k in um K), S the
+//     caller's scale (the Planck constant 2hc^2, 4 pi and the units);
+//   * the temperature: bisection in ln T between t_min and t_max (64 halvings)
+//     on emission = sum_l absorbed_l[c]; no absorption or no dust: T = 0;
+//     emission short of the absorption at t_max: T = t_max, beyond it at
+//     t_min: T = t_min (both counted).
+constexpr double kC2 = 14387.768775039337;  // hc / k in um K
+
+std::vector<double> bin_widths(const double* lambda, int n) {
+  std::vector<double> b((size_t)n + 1), w((size_t)n);
+  for (int l = 1; l < n; ++l) b[(size_t)l] = std::sqrt(lambda[l - 1] * lambda[l]);
+  b[0] = lambda[0] * std::sqrt(lambda[0] / lambda[1]);
+  b[(size_t)n] = lambda[n - 1] * std::sqrt(lambda[n - 1] / lambda[n - 2]);
+  for (int l = 0; l < n; ++l) w[(size_t)l] = b[(size_t)l + 1] - b[(size_t)l];
+  return w;
+}
+
+double planck_shape(double lambda_um, double T) {
+  return 1.0 / (std::pow(lambda_um, 5.0) * std::expm1(kC2 / (lambda_um * T)));
+}
+
+double cell_mass(const Grid& G, int64_t c) {
+  const Box b = G.cell_box(c);
+  return (double)G.density[c] * ((b.hi[0] - b.lo[0]) * (b.hi[1] - b.lo[1]) * (b.hi[2] - b.lo[2]));
+}
+
+// S kabs_l dlambda_l for every wavelength.
+std::vector<double> emission_weights(const Problem& P, const double* lambda, double scale) {
+  const std::vector<double> w = bin_widths(lambda, P.n_lambda);
+  std::vector<double> out((size_t)P.n_lambda);
+  for (int l = 0; l < P.n_lambda; ++l)
+    out[(size_t)l] = scale * P.kappa[(size_t)l] * (1.0 - P.albedo[(size_t)l]) * w[(size_t)l];
+  return out;
+}
+
+double cell_emission(const std::vector<double>& wts, const double* lambda, double mass, double T) {
+  double sum = 0.0;
+  for (size_t l = 0; l < wts.size(); ++l) sum += wts[l] * planck_shape(lambda[l], T);
+  return mass * sum;
+}
 
 int64_t total_packets(const Problem& P, const or_opts& O) { return (int64_t)O.n_per_lambda * P.n_lambda; }
 
@@ -973,7 +1064,7 @@ int64_t or_locate(const or_problem* prob, const double p[3], const double k[3], 
 // Full transport run.  Returns 0 on success, < 0 on bad arguments.
 int32_t or_run(const or_problem* prob, const or_opts* opts, or_output* out) {
   if (!prob || !opts || !out || opts->n_per_lambda == 0 || opts->n_norm == 0 || prob->n_lambda <= 0 ||
-      prob->n_sources <= 0)
+      (prob->n_sources <= 0 && !prob->dust_lum))
     return -1;
   Problem P = make_problem(*prob);
   const or_opts& O = *opts;
@@ -1115,6 +1206,63 @@ int32_t or_interaction(const or_problem* prob, const double x[3], const double k
   out_tau[0] = tau_path;
   out_tau[1] = tau_star;
   return (fallback ? 1 : 0) | (clamped ? 2 : 0);
+}
+
+// Equilibrium dust temperature of every cell from the absorbed luminosity
+// absorption [n_lambda][n_cells] (panchromatic mode; see the notes above
+// bin_widths).  Returns the number of cells held at t_min or t_max, or -1 on bad
+// arguments (fewer than two wavelengths, an octree grid, t range empty).
+int32_t or_dust_temperature(const or_problem* prob, const double* lambda, const double* absorption, double scale,
+                            double t_min, double t_max, double* T_out) {
+  if (!prob || !lambda || !absorption || !T_out || prob->n_lambda < 2 || prob->grid.kind == 1 ||
+      !(t_min > 0 && t_max > t_min) || !(scale > 0))
+    return -1;
+  Problem P = make_problem(*prob);
+  const int64_t nc = P.grid.n_cells();
+  const std::vector<double> wts = emission_weights(P, lambda, scale);
+  int32_t clamped = 0;
+  for (int64_t c = 0; c < nc; ++c) {
+    double absorbed = 0.0;
+    for (int l = 0; l < P.n_lambda; ++l) absorbed += absorption[(size_t)l * nc + c];
+    const double m = cell_mass(P.grid, c);
+    if (!(absorbed > 0.0) || !(m > 0.0) || !(cell_emission(wts, lambda, m, t_max) > 0.0)) {
+      T_out[c] = 0.0;
+      continue;
+    }
+    if (cell_emission(wts, lambda, m, t_max) < absorbed) {
+      T_out[c] = t_max;
+      ++clamped;
+      continue;
+    }
+    if (cell_emission(wts, lambda, m, t_min) >= absorbed) {
+      T_out[c] = t_min;
+      ++clamped;
+      continue;
+    }
+    double lo = std::log(t_min), hi = std::log(t_max);
+    for (int it = 0; it < 64; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (cell_emission(wts, lambda, m, std::exp(mid)) < absorbed) lo = mid; else hi = mid;
+    }
+    T_out[c] = std::exp(0.5 * (lo + hi));
+  }
+  return clamped;
+}
+
+// Thermal emission of every cell at the temperatures T [n_cells] (T = 0: no
+// emission): lum_out [n_lambda][n_cells] = S m_c kabs_l dlambda_l beta_l(T_c).
+int32_t or_dust_emission(const or_problem* prob, const double* lambda, const double* T, double scale,
+                         double* lum_out) {
+  if (!prob || !lambda || !T || !lum_out || prob->n_lambda < 2 || prob->grid.kind == 1 || !(scale > 0)) return -1;
+  Problem P = make_problem(*prob);
+  const int64_t nc = P.grid.n_cells();
+  const std::vector<double> wts = emission_weights(P, lambda, scale);
+  for (int64_t c = 0; c < nc; ++c) {
+    const double m = cell_mass(P.grid, c);
+    for (int l = 0; l < P.n_lambda; ++l)
+      lum_out[(size_t)l * nc + c] = T[c] > 0.0 ? m * wts[(size_t)l] * planck_shape(lambda[l], T[c]) : 0.0;
+  }
+  return 0;
 }
 
 // Vector-Jacobian product by forward-mode dual numbers, one seeded cell at a

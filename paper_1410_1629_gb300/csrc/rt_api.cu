@@ -88,6 +88,18 @@ struct rt_ctx_s {
   bool permuted = false;
   float* d_density_s = nullptr;
   double* d_abs_tmp = nullptr;  // one wavelength of row-major absorption, for read-outs to host memory
+  double* d_planes64 = nullptr; // FP64 cell planes x, y, z (cartesian and rectilinear grids)
+  // panchromatic mode: wavelengths (um), the dust temperatures and thermal
+  // emission [n_lambda][n_cells] with its running sums, their per-wavelength
+  // totals, and whether launches may emit from the dust
+  std::vector<double> lambda_um;
+  double* d_dust_T = nullptr;
+  double* d_dust_lum = nullptr;
+  double* d_dust_cum = nullptr;
+  double* d_dust_tiles = nullptr;
+  unsigned* d_dust_clamped = nullptr;
+  std::vector<double> dust_total;
+  bool dust_ready = false;
   // optics
   int n_lambda = 0;
   std::vector<double> kappa, albedo, g;
@@ -243,6 +255,8 @@ void free_grid(rt_ctx c) {
   pool_release(c, c->d_edges, (size_t)(c->nx + c->ny + c->nz + 3) * sizeof(float));
   pool_release(c, c->d_density_s, (size_t)c->n_cells * sizeof(float));
   pool_release(c, c->d_abs_tmp, (size_t)c->n_cells * sizeof(double));
+  pool_release(c, c->d_planes64, (size_t)(c->nx + c->ny + c->nz + 3) * sizeof(double));
+  pool_release(c, c->d_dust_T, (size_t)c->n_cells * sizeof(double));
   c->permuted = false;
   pool_release(c, c->d_absorption, (size_t)c->n_lambda * c->n_cells * sizeof(double));
   for (auto& p : c->d_columns) pool_release(c, p, (size_t)c->n_cells * sizeof(float));
@@ -273,6 +287,11 @@ void free_problem(rt_ctx c) {
   c->instr.clear();
   c->sources.clear();
   pool_release(c, c->d_absorption, (size_t)c->n_lambda * c->n_cells * sizeof(double));
+  pool_release(c, c->d_dust_lum, (size_t)c->n_lambda * c->n_cells * sizeof(double));
+  pool_release(c, c->d_dust_cum, (size_t)c->n_lambda * c->n_cells * sizeof(double));
+  pool_release(c, c->d_dust_tiles, (size_t)c->n_lambda * dust_tiles(c->n_cells) * sizeof(double));
+  c->dust_ready = false;
+  c->dust_total.clear();
   c->n_lambda = 0;
   c->tables_dirty = true;
   c->tape_valid = false;
@@ -660,6 +679,27 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
     crossing_order_strides(n3, ext, c->stride);
     c->permuted = !(c->stride[0] == 1 && c->stride[1] == d->nx);
   }
+  if (d->kind != RT_GRID_OCTREE) {
+    // FP64 planes: cartesian lo + i (hi - lo) / n, rectilinear the edges
+    std::vector<double> planes;
+    const int n3[3] = {d->nx, d->ny, d->nz};
+    for (int a = 0; a < 3; ++a) {
+      std::vector<double> e((size_t)n3[a] + 1);
+      if (d->kind == RT_GRID_RECTILINEAR) {
+        if (d->on_device) {
+          RT_CUDA(c, cudaMemcpy(e.data(), d->edges[a], e.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        } else {
+          std::memcpy(e.data(), d->edges[a], e.size() * sizeof(double));
+        }
+      } else {
+        const double lo = d->bounds[2 * a], step = (d->bounds[2 * a + 1] - lo) / n3[a];
+        for (int i = 0; i <= n3[a]; ++i) e[(size_t)i] = lo + i * step;
+      }
+      planes.insert(planes.end(), e.begin(), e.end());
+    }
+    RT_CUDA(c, pool_alloc(c, &c->d_planes64, planes.size() * sizeof(double)));
+    RT_CUDA(c, cudaMemcpy(c->d_planes64, planes.data(), planes.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
   if (c->permuted) {
     RT_CUDA(c, pool_alloc(c, &c->d_density_s, (size_t)n_cells * sizeof(float)));
     RT_CUDA(c, launch_to_storage(c->d_density, c->d_density_s, d->nx, d->ny, d->nz, c->stride, nullptr));
@@ -679,7 +719,6 @@ rt_status rt_set_optics(rt_ctx c, int32_t grid_id, int32_t n_lambda, const doubl
                         const double* albedo, const double* g) {
   if (!c) return RT_ERR_ARG;
   c->err.clear();
-  (void)lambda;
   if (!c->has_grid) return fail(c, RT_ERR_STATE, "rt_set_optics: no grid");
   if (grid_id != 0) return fail(c, RT_ERR_ARG, "rt_set_optics: unknown grid id %d", grid_id);
   if (n_lambda < 1 || n_lambda > kMaxLambda) return fail(c, RT_ERR_ARG, "rt_set_optics: n_lambda must be 1..%d", kMaxLambda);
@@ -692,6 +731,8 @@ rt_status rt_set_optics(rt_ctx c, int32_t grid_id, int32_t n_lambda, const doubl
   if (set_device(c) != RT_OK) return RT_ERR_CUDA;
   free_problem(c);
   c->n_lambda = n_lambda;
+  c->lambda_um.clear();
+  if (lambda) c->lambda_um.assign(lambda, lambda + n_lambda);
   c->kappa.assign(kappa, kappa + n_lambda);
   c->albedo.assign(albedo, albedo + n_lambda);
   c->g.assign(g, g + n_lambda);
@@ -856,22 +897,34 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   if (!c) return RT_ERR_ARG;
   c->err.clear();
   if (!c->has_grid || c->n_lambda == 0) return fail(c, RT_ERR_STATE, "rt_launch_packets: grid and optics required");
-  if (c->sources.empty()) return fail(c, RT_ERR_STATE, "rt_launch_packets: no sources");
   if (seed >> 32) return fail(c, RT_ERR_ARG, "rt_launch_packets: seed must be < 2^32");
   rt_launch_opts o;
   rt_default_opts(&o);
   if (opts) o = *opts;
+  if (o.emitter != RT_EMITTER_SOURCES && o.emitter != RT_EMITTER_DUST)
+    return fail(c, RT_ERR_ARG, "rt_launch_packets: unknown emitter %d", o.emitter);
+  const bool dust = o.emitter == RT_EMITTER_DUST;
+  if (dust && !c->dust_ready) return fail(c, RT_ERR_STATE, "rt_launch_packets: no dust emission set");
+  if (dust && o.tape) return fail(c, RT_ERR_ARG, "rt_launch_packets: the adjoint tape needs the sources as emitter");
+  if (!dust && c->sources.empty()) return fail(c, RT_ERR_STATE, "rt_launch_packets: no sources");
+  // luminosity per wavelength of the emitter
+  std::vector<double> lum_total((size_t)c->n_lambda, 0.0);
+  for (int l = 0; l < c->n_lambda; ++l) {
+    if (dust) {
+      lum_total[(size_t)l] = c->dust_total[(size_t)l];
+    } else {
+      for (auto& src : c->sources) lum_total[(size_t)l] += src.lum[l];
+    }
+  }
   if (o.max_events < 1) return fail(c, RT_ERR_ARG, "rt_launch_packets: max_events must be >= 1");
   if (!(o.w_min >= 0 && o.w_min < 1)) return fail(c, RT_ERR_ARG, "rt_launch_packets: w_min must be in [0, 1)");
   if (o.control_lanes < 0 || o.control_lanes > 32)
     return fail(c, RT_ERR_ARG, "rt_launch_packets: control_lanes must be in [0, 32]");
   if ((o.records && o.records_capacity < 0) || (o.trace && o.trace_capacity < 0))
     return fail(c, RT_ERR_ARG, "rt_launch_packets: negative record or trace capacity");
-  for (int l = 0; l < c->n_lambda; ++l) {
-    double tot = 0;
-    for (auto& s : c->sources) tot += s.lum[l];
-    if (!(tot > 0)) return fail(c, RT_ERR_ARG, "rt_launch_packets: zero total luminosity at wavelength %d", l);
-  }
+  for (int l = 0; l < c->n_lambda; ++l)
+    if (!dust && !(lum_total[(size_t)l] > 0))
+      return fail(c, RT_ERR_ARG, "rt_launch_packets: zero total luminosity at wavelength %d", l);
   if (n_per_lambda == 0) return RT_OK;
   const unsigned long long n_total = n_per_lambda * (unsigned long long)c->n_lambda;
   if (n_total / (unsigned long long)c->n_lambda != n_per_lambda || n_total > (1ull << 62))
@@ -935,11 +988,10 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   p.control_min = o.control_lanes ? o.control_lanes : (c->control_lanes ? c->control_lanes : 16);
   p.inv_n_per_lambda = (float)(1.0 / (double)n_per_lambda);
   for (int l = 0; l < c->n_lambda; ++l) {
-    double tot = 0.0;
-    for (auto& src : c->sources) tot += src.lum[l];
-    p.L0[l] = tot / (double)p.n_norm;
+    p.L0[l] = lum_total[(size_t)l] / (double)p.n_norm;
     p.L_cut[l] = o.w_min * p.L0[l];
   }
+  p.dust_cum = dust ? c->d_dust_cum : nullptr;
   p.profile = reinterpret_cast<unsigned long long*>(o.profile);
   p.flags = c->d_flags;
   p.use_columns = c->grid_kind == RT_GRID_CARTESIAN && !o.walk_peels;
@@ -1016,11 +1068,7 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
     c->tape_peel_e = o.peel_emission; c->tape_peel_s = o.peel_scatter; c->tape_model = (int)o.model_id;
   }
   // every packet starts with L0 = L_tot / n_norm
-  for (int l = 0; l < c->n_lambda; ++l) {
-    double tot = 0.0;
-    for (auto& src : c->sources) tot += src.lum[l];
-    c->emitted += (double)n_per_lambda * (tot / (double)p.n_norm);
-  }
+  for (int l = 0; l < c->n_lambda; ++l) c->emitted += (double)n_per_lambda * p.L0[l];
   return RT_OK;
 }
 
@@ -1317,6 +1365,130 @@ rt_status rt_read_absorption(rt_ctx c, double* dst, size_t n_elems, int32_t on_d
   }
   RT_CUDA(c, cudaStreamSynchronize(s));
   return RT_OK;
+}
+
+namespace {
+
+// Checks shared by the panchromatic calls; fills the per-wavelength weights
+// S kappa_l (1 - albedo_l) dlambda_l (bins centred on the wavelengths on a
+// logarithmic scale: inner borders at geometric means, outer ones mirrored).
+rt_status dust_setup(rt_ctx c, const char* who, double scale, std::vector<double>& w) {
+  if (!c->has_grid || c->n_lambda == 0) return fail(c, RT_ERR_STATE, "%s: grid and optics required", who);
+  if (c->grid_kind == RT_GRID_OCTREE) return fail(c, RT_ERR_ARG, "%s: cartesian or rectilinear grids only", who);
+  if (c->n_lambda < 2 || (int)c->lambda_um.size() != c->n_lambda)
+    return fail(c, RT_ERR_STATE, "%s: rt_set_optics needs the wavelengths (at least two, in um)", who);
+  for (int l = 0; l < c->n_lambda; ++l)
+    if (!(is_finite(c->lambda_um[l]) && c->lambda_um[l] > 0 && (l == 0 || c->lambda_um[l] > c->lambda_um[l - 1])))
+      return fail(c, RT_ERR_ARG, "%s: wavelengths must be positive and increasing", who);
+  if (!(is_finite(scale) && scale > 0)) return fail(c, RT_ERR_ARG, "%s: emission scale must be > 0", who);
+  const int n = c->n_lambda;
+  const std::vector<double>& lam = c->lambda_um;
+  std::vector<double> b((size_t)n + 1);
+  for (int l = 1; l < n; ++l) b[(size_t)l] = std::sqrt(lam[l - 1] * lam[l]);
+  b[0] = lam[0] * std::sqrt(lam[0] / lam[1]);
+  b[(size_t)n] = lam[n - 1] * std::sqrt(lam[n - 1] / lam[n - 2]);
+  w.assign((size_t)n, 0.0);
+  for (int l = 0; l < n; ++l) w[(size_t)l] = scale * c->kappa[l] * (1.0 - c->albedo[l]) * (b[(size_t)l + 1] - b[(size_t)l]);
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  return RT_OK;
+}
+
+}  // namespace
+
+rt_status rt_dust_temperature(rt_ctx c, double emission_scale, double t_min, double t_max, const double* absorption,
+                              int32_t absorption_on_device, double* temperature, int32_t dst_on_device,
+                              int32_t* n_clamped, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  std::vector<double> w;
+  rt_status st = dust_setup(c, "rt_dust_temperature", emission_scale, w);
+  if (st != RT_OK) return st;
+  if (!temperature) return fail(c, RT_ERR_ARG, "rt_dust_temperature: null destination");
+  if (!(t_min > 0 && t_max > t_min && is_finite(t_max)))
+    return fail(c, RT_ERR_ARG, "rt_dust_temperature: need 0 < t_min < t_max");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nc = (size_t)c->n_cells, nl = (size_t)c->n_lambda;
+  if (!c->d_dust_T) RT_CUDA(c, pool_alloc(c, &c->d_dust_T, nc * sizeof(double)));
+  if (!c->d_dust_clamped) RT_CUDA(c, cudaMalloc(&c->d_dust_clamped, sizeof(unsigned)));
+  RT_CUDA(c, cudaMemsetAsync(c->d_dust_clamped, 0, sizeof(unsigned), s));
+  const double* src = c->d_absorption;
+  int stored = 1;
+  double* staged = nullptr;
+  if (absorption) {
+    stored = 0;
+    if (absorption_on_device) {
+      src = absorption;
+    } else {
+      RT_CUDA(c, cudaMalloc(&staged, nl * nc * sizeof(double)));
+      cudaError_t e = cudaMemcpyAsync(staged, absorption, nl * nc * sizeof(double), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        cudaFree(staged);
+        return cuda_fail(c, e, "rt_dust_temperature: absorption upload");
+      }
+      src = staged;
+    }
+  }
+  cudaError_t e = launch_dust_temperature(c->n_lambda, c->nx, c->ny, c->nz, c->stride, c->d_planes64, c->d_density,
+                                          w.data(), c->lambda_um.data(), src, stored, t_min, t_max, c->d_dust_T,
+                                          c->d_dust_clamped, s);
+  unsigned clamped = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&clamped, c->d_dust_clamped, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(temperature, c->d_dust_T, nc * sizeof(double),
+                        dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (staged) cudaFree(staged);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rt_dust_temperature");
+  if (n_clamped) *n_clamped = (int32_t)clamped;
+  return RT_OK;
+}
+
+rt_status rt_set_dust_emission(rt_ctx c, const double* temperature, int32_t on_device, double emission_scale,
+                               void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  std::vector<double> w;
+  rt_status st = dust_setup(c, "rt_set_dust_emission", emission_scale, w);
+  if (st != RT_OK) return st;
+  if (!temperature) return fail(c, RT_ERR_ARG, "rt_set_dust_emission: null temperatures");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nc = (size_t)c->n_cells, nl = (size_t)c->n_lambda;
+  c->dust_ready = false;
+  c->tape_valid = false;
+  if (!c->d_dust_T) RT_CUDA(c, pool_alloc(c, &c->d_dust_T, nc * sizeof(double)));
+  if (!c->d_dust_lum) RT_CUDA(c, pool_alloc(c, &c->d_dust_lum, nl * nc * sizeof(double)));
+  if (!c->d_dust_cum) RT_CUDA(c, pool_alloc(c, &c->d_dust_cum, nl * nc * sizeof(double)));
+  if (!c->d_dust_tiles) RT_CUDA(c, pool_alloc(c, &c->d_dust_tiles, nl * dust_tiles(c->n_cells) * sizeof(double)));
+  if (temperature != c->d_dust_T) {
+    RT_CUDA(c, cudaMemcpyAsync(c->d_dust_T, temperature, nc * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (!on_device) RT_CUDA(c, cudaStreamSynchronize(s));  // the caller may reuse its host array
+  }
+  RT_CUDA(c, launch_dust_emission(c->n_lambda, c->nx, c->ny, c->nz, c->stride, c->d_planes64, c->d_density, w.data(),
+                                  c->lambda_um.data(), c->d_dust_T, c->d_dust_lum, c->d_dust_cum, c->d_dust_tiles, s));
+  // the per-wavelength totals (the last running sums) set the packet weights
+  c->dust_total.assign(nl, 0.0);
+  for (size_t l = 0; l < nl; ++l)
+    RT_CUDA(c, cudaMemcpyAsync(&c->dust_total[l], c->d_dust_cum + l * nc + nc - 1, sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+  RT_CUDA(c, cudaStreamSynchronize(s));
+  for (size_t l = 0; l < nl; ++l)
+    if (!(is_finite(c->dust_total[l]) && c->dust_total[l] >= 0))
+      return fail(c, RT_ERR_ARG, "rt_set_dust_emission: non-finite emission at wavelength %zu", l);
+  c->dust_ready = true;
+  return RT_OK;
+}
+
+rt_status rt_read_dust_emission(rt_ctx c, double* dst, size_t n_elems, int32_t on_device, void* stream) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (!c->dust_ready) return fail(c, RT_ERR_STATE, "rt_read_dust_emission: no dust emission set");
+  if (!dst) return fail(c, RT_ERR_ARG, "rt_read_dust_emission: null destination");
+  const size_t n = (size_t)c->n_lambda * c->n_cells;
+  if (n_elems != n) return fail(c, RT_ERR_ARG, "rt_read_dust_emission: n_elems %zu != %zu", n_elems, n);
+  if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+  return copy_out(c, dst, c->d_dust_lum, n, on_device, stream);
 }
 
 rt_status rt_read_images(rt_ctx c, int32_t id, double* dst, size_t n_elems, int32_t on_device, void* stream) {

@@ -124,6 +124,10 @@ struct FwdParams {
   unsigned long long* peel_count;  // records asked for (beyond peel_cap the kernel walks them itself)
   unsigned* peel_hist;             // [n_instr][n_cells + 1]: records per sort key
   ulonglong2* peel_tag;            // [peel_cap] packet id and event of each record (debug records on), or null
+  // panchromatic mode: packets emitted by the dust instead of the sources;
+  // per wavelength the running sums of the cells' thermal luminosities over
+  // the row-major cells ([n_lambda][n_cells]), or null
+  const double* dust_cum;
 };
 
 enum DeviceFlag : int { kFlagCellRange = 1, kFlagOctreeDepth = 2, kFlagWalkSteps = 4, kFlagNoInteraction = 8 };
@@ -178,6 +182,21 @@ cudaError_t launch_to_storage(const float* src, float* dst, int nx, int ny, int 
                               cudaStream_t stream);
 cudaError_t launch_from_storage(const double* src, double* dst, int n_lambda, int nx, int ny, int nz,
                                 const int strides[3], cudaStream_t stream);
+
+// Panchromatic mode (rt_dust.cu): equilibrium temperatures T [n_cells] from
+// the absorbed luminosity (stored = 1: the context's tallies in the storage
+// order of `stride`; 0: a row-major [n_lambda][n_cells] field), and the
+// thermal emission lum [n_lambda][n_cells] with its running sums cum over the
+// cells (tile_sum: n_lambda * dust_tiles(n_cells) doubles).  planes: FP64
+// cell planes x, y, z; w: S kappa_l (1 - albedo_l) dlambda_l; lambda in um.
+cudaError_t launch_dust_temperature(int n_lambda, int nx, int ny, int nz, const int stride[3], const double* planes,
+                                    const float* density, const double* w, const double* lambda,
+                                    const double* absorbed, int stored, double t_min, double t_max, double* T,
+                                    unsigned* clamped, cudaStream_t s);
+cudaError_t launch_dust_emission(int n_lambda, int nx, int ny, int nz, const int stride[3], const double* planes,
+                                 const float* density, const double* w, const double* lambda, const double* T,
+                                 double* lum, double* cum, double* tile_sum, cudaStream_t s);
+long long dust_tiles(long long n_cells);
 
 // Launchers (rt_forward.cu).
 cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaStream_t stream);

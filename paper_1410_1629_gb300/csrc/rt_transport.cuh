@@ -168,6 +168,7 @@ __device__ __forceinline__ int stride_of(const FwdParams& P, int a) { return P.s
 // ---------------------------------------------------------------- cartesian grid
 struct CartGrid {
   static constexpr bool kColumns = true;  // peel-offs along grid axes may use column sums
+  static constexpr bool kIndexCells = true;  // cells indexed by (ix, iy, iz) between planes
   struct Cell {
     int ix, iy, iz;
   };
@@ -253,6 +254,11 @@ struct CartGrid {
   template <class Geo>
   __device__ static __forceinline__ int id(const Geo& P, const Walk& w) { return w.ix + P.nx * (w.iy + P.ny * w.iz); }
 
+  // Plane i of axis a.
+  __device__ static __forceinline__ float plane(const FwdParams& P, int a, int i) {
+    return fmaf((float)i, P.d[a], P.lo[a]);
+  }
+
   __device__ static __forceinline__ Cell carried(const Walk& w) { return Cell{w.ix, w.iy, w.iz}; }
 
   // Keep x inside cell c.
@@ -272,6 +278,7 @@ struct CartGrid {
 // copies of the FP64 edges); a position is located by binary search.
 struct RectGrid {
   static constexpr bool kColumns = false;
+  static constexpr bool kIndexCells = true;
   using Cell = CartGrid::Cell;
   using Walk = CartGrid::Walk;
   struct Scratch {};
@@ -348,6 +355,8 @@ struct RectGrid {
     return w.ix + P.nx * (w.iy + P.ny * w.iz);
   }
 
+  __device__ static __forceinline__ float plane(const FwdParams& P, int a, int i) { return edge(P, a, i); }
+
   __device__ static __forceinline__ Cell carried(const Walk& w) { return Cell{w.ix, w.iy, w.iz}; }
 
   __device__ static __forceinline__ void clamp(const FwdParams& P, const Cell& c, float3& x) {
@@ -368,6 +377,7 @@ __shared__ int S_STACK[kBlock * kOctStack];
 
 struct OctGrid {
   static constexpr bool kColumns = false;
+  static constexpr bool kIndexCells = false;
   struct Cell {
     int leaf;
     float lo[3], hi[3];
@@ -907,6 +917,45 @@ __device__ __forceinline__ void emit(const FwdParams& P, unsigned long long pid,
   k_out = make_float3(st * cp, st * sp, mu);
 }
 
+// Emission by the dust (panchromatic mode): the cell with probability
+// proportional to its thermal luminosity at this wavelength (the first cell
+// whose running sum exceeds u times the total, FP64), a uniform position in
+// it (FP32, kept inside its planes), an isotropic direction; the cell is
+// known to the first walks.
+template <class G>
+__device__ __forceinline__ void emit_dust(const FwdParams& P, unsigned long long pid, int lam, float3& x_out,
+                                          float3& k_out, typename G::Cell& cell) {
+  if constexpr (G::kIndexCells) {
+    const uint4 r0 = draw_block(pid, lam, 0, 0, P.seed, P.model);
+    const uint4 r1 = draw_block(pid, lam, 0, 1, P.seed, P.model);
+    const double* cum = P.dust_cum + (size_t)lam * P.n_cells;
+    const double target = u01(r0.x) * cum[P.n_cells - 1];
+    long long lo = 0, hi = P.n_cells - 1;
+    while (lo < hi) {
+      const long long mid = (lo + hi) >> 1;
+      if (cum[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    const int c = (int)lo;
+    cell.ix = c % P.nx;
+    cell.iy = (c / P.nx) % P.ny;
+    cell.iz = c / (P.nx * P.ny);
+    const int idx[3] = {cell.ix, cell.iy, cell.iz};
+    const float u[3] = {u01f(r0.y), u01f(r0.z), u01f(r0.w)};
+    float p[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float lo_a = G::plane(P, a, idx[a]), hi_a = G::plane(P, a, idx[a] + 1);
+      p[a] = fminf(fmaxf(fmaf(u[a], hi_a - lo_a, lo_a), lo_a), hi_a);
+    }
+    x_out = make_float3(p[0], p[1], p[2]);
+    const float mu = u01f_signed(r1.z);
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+    float sp, cp;
+    sincospif(2.0f * u01f(r1.w), &sp, &cp);
+    k_out = make_float3(st * cp, st * sp, mu);
+  }
+}
+
 // Ask for walk `phase` from the lane's position along d; walks start in the
 // last stage of a control round, from one place in the code.
 template <class G>
@@ -968,11 +1017,25 @@ __device__ __forceinline__ void fetch(const FwdParams& P, Lane<G>& s, unsigned l
   s.lam = lam;
   s.pid() = P.first_id + (w - (unsigned long long)lam * P.n_per_lambda);
   const double L0 = P.L0[lam];
+  if (L0 == 0.0) {  // no emission at this wavelength (dust that emits nothing here)
+    bt->packets += 1u;
+    s.phase = kFetch;
+    return;
+  }
   s.kappa = S_LAM[lam].kappa;
   s.L() = L0;
   s.event() = 0;
   s.has_cell() = false;
-  emit(P, s.pid(), s.lam, s.x, s.k());
+  if constexpr (G::kIndexCells) {
+    if (P.dust_cum) {
+      emit_dust<G>(P, s.pid(), s.lam, s.x, s.k(), s.cell());
+      s.has_cell() = true;
+    } else {
+      emit(P, s.pid(), s.lam, s.x, s.k());
+    }
+  } else {
+    emit(P, s.pid(), s.lam, s.x, s.k());
+  }
   bt->packets += 1u;
   trace_row(P, s, 0, -1, L0, 0.0, 0.0);
   if (kTape) {

@@ -24,6 +24,7 @@ RT_GRID_CARTESIAN, RT_GRID_OCTREE, RT_GRID_RECTILINEAR = 0, 1, 2
 RT_SOURCE_POINT, RT_SOURCE_EXPDISK, RT_SOURCE_PLUMMER = 0, 1, 2
 RT_DEPOSIT_NEAREST, RT_DEPOSIT_BILINEAR, RT_DEPOSIT_SED = 0, 1, 2
 RT_LAYOUT_AUTO, RT_LAYOUT_ROW_MAJOR = 0, 1
+RT_EMITTER_SOURCES, RT_EMITTER_DUST = 0, 1
 TRACE_DTYPE = np.dtype([("event", "<i4"), ("reserved", "<i4"), ("cell", "<i8"), ("x", "<f8", 3), ("k", "<f8", 3),
                         ("L", "<f8"), ("tau_path", "<f8"), ("tau_star", "<f8")])
 
@@ -84,7 +85,7 @@ class rt_launch_opts(ctypes.Structure):
                 ("trace", ctypes.c_void_p), ("trace_capacity", ctypes.c_int64), ("trace_packet", ctypes.c_uint64),
                 ("trace_lambda", ctypes.c_int32), ("control_lanes", ctypes.c_int32),
                 ("profile", ctypes.c_void_p), ("tape", ctypes.c_int32), ("inline_peels", ctypes.c_int32),
-                ("time_parts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("time_parts", ctypes.c_int32), ("emitter", ctypes.c_int32)]
 
 
 class rt_stats(ctypes.Structure):
@@ -157,6 +158,13 @@ SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p]),
     "rt_probe_bandwidth": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_double)]),
+    "rt_dust_temperature": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
+    "rt_set_dust_emission": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+                                              ctypes.c_void_p]),
+    "rt_read_dust_emission": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
+                                               ctypes.c_void_p]),
 }
 
 _lib = None
@@ -375,6 +383,27 @@ def rt_probe_bandwidth(device=0, nbytes=32 << 20, passes=20, repeats=5) -> float
     if st != RT_OK:
         raise RTError(st, lib().rt_last_error(None).decode())
     return out.value
+
+
+def rt_dust_temperature(ctx, emission_scale, t_min=1.0, t_max=1e4, absorption_ptr=0, absorption_on_device=0,
+                        dst_ptr=0, dst_on_device=0, stream=None) -> int:
+    """Equilibrium dust temperatures into dst_ptr; returns the cells held at t_max."""
+    n = ctypes.c_int32(0)
+    _check(ctx, lib().rt_dust_temperature(ctx, float(emission_scale), float(t_min), float(t_max),
+                                          ctypes.c_void_p(int(absorption_ptr) or None), int(absorption_on_device),
+                                          ctypes.c_void_p(int(dst_ptr)), int(dst_on_device), ctypes.byref(n),
+                                          _stream_ptr(stream)))
+    return n.value
+
+
+def rt_set_dust_emission(ctx, temperature_ptr, on_device, emission_scale, stream=None):
+    _check(ctx, lib().rt_set_dust_emission(ctx, ctypes.c_void_p(int(temperature_ptr)), int(on_device),
+                                           float(emission_scale), _stream_ptr(stream)))
+
+
+def rt_read_dust_emission(ctx, dst_ptr, n_elems, on_device, stream=None):
+    _check(ctx, lib().rt_read_dust_emission(ctx, ctypes.c_void_p(int(dst_ptr)), int(n_elems), int(on_device),
+                                            _stream_ptr(stream)))
 
 
 def rt_batch_create(ctx, descs) -> int:
@@ -625,6 +654,31 @@ class Simulation:
 
     def reset(self, stream=None):
         rt_reset_tallies(self.ctx, stream)
+
+    def dust_temperature(self, emission_scale, t_min=1.0, t_max=1e4, absorption=None):
+        """Equilibrium dust temperatures (float64 numpy array [n_cells]) from
+        the context's absorption tallies or a row-major absorption field
+        [n_lambda, n_cells]; returns (T, cells held at t_max)."""
+        T = np.zeros(self.n_cells, dtype=np.float64)
+        keep = None
+        ptr = 0
+        if absorption is not None:
+            keep = np.ascontiguousarray(absorption, dtype=np.float64)
+            ptr = keep.ctypes.data
+        n = rt_dust_temperature(self.ctx, emission_scale, t_min, t_max, ptr, 0, T.ctypes.data, 0)
+        del keep
+        return T, n
+
+    def set_dust_emission(self, temperature, emission_scale):
+        """Thermal emission of the dust at the temperatures [n_cells]; launches
+        with emitter=RT_EMITTER_DUST then emit from the dust."""
+        T = np.ascontiguousarray(temperature, dtype=np.float64)
+        rt_set_dust_emission(self.ctx, T.ctypes.data, 0, emission_scale)
+
+    def dust_emission(self):
+        out = np.zeros((self.n_lambda, self.n_cells), dtype=np.float64)
+        rt_read_dust_emission(self.ctx, out.ctypes.data, out.size, 0)
+        return out
 
     def trace(self, packet, lam=0, n_per_lambda=None, seed=None, max_rows=None, **opts):
         """Per-event trace (rt_trace_row) of one packet: a launch of the

@@ -109,6 +109,9 @@ class Problem:
     instruments: List[Instrument]
     run: Run
     meta: dict = field(default_factory=dict)
+    # panchromatic mode: thermal emission of the dust cells [n_lambda, n_cells],
+    # emitted instead of the sources (None: the sources emit)
+    dust_lum: Optional[np.ndarray] = None
 
     @property
     def n_lambda(self) -> int:
@@ -320,6 +323,45 @@ def spiral_example(grid="powcub", n_xy=256, n_z=128, xy_ratio=20.0, z_ratio=50.0
               "face_on_tau_v": float(KAPPA_V_PC2_MSUN * mass / (2.0 * math.pi * h_r * h_r)),
               "edge_on_tau_v": float(KAPPA_V_PC2_MSUN * mass / (2.0 * math.pi * h_r * h_z))},
     )
+
+
+def panchromatic_optics(wavelengths_um, kappa_v):
+    """Synthetic optics over a UV-to-submillimetre grid, x = ln(lambda / 0.55
+    um): kappa = kappa_V exp(-1.3 x), albedo = clip(0.6 - 0.1 x^2, 0, 0.8)
+    (no scattering far in the infrared), g = clip(0.6 - 0.15 x, 0, 0.9)."""
+    x = np.log(np.asarray(wavelengths_um, dtype=np.float64) / 0.55)
+    return kappa_v * np.exp(-1.3 * x), np.clip(0.6 - 0.1 * x * x, 0.0, 0.8), np.clip(0.6 - 0.15 * x, 0.0, 0.9)
+
+
+def stellar_spectrum(wavelengths_um, t_star=5800.0, total=1.0):
+    """Luminosity per wavelength bin of a blackbody star of temperature
+    t_star (bins centred on the wavelengths on a logarithmic scale), scaled
+    to `total`."""
+    lam = np.asarray(wavelengths_um, dtype=np.float64)
+    edges = np.sqrt(lam[1:] * lam[:-1])
+    edges = np.concatenate([[lam[0] ** 2 / edges[0]], edges, [lam[-1] ** 2 / edges[-1]]])
+    shape = 1.0 / (lam ** 5 * np.expm1(14387.768775039337 / (lam * t_star)))
+    spec = shape * np.diff(edges)
+    return total * spec / spec.sum()
+
+
+def panchromatic_disk(n_cells=64, n_lambda=24, n_pix=64, n_packets_total=2_400_000, face_on_tau_v=0.5,
+                      emission_scale=1e11, channels=1) -> Problem:
+    """The disk galaxy over a panchromatic wavelength grid (Sect. 2.1, 2.2):
+    ``n_lambda`` wavelengths log-spaced from 0.1 to 1000 um, the stars a
+    5800 K blackbody of unit total luminosity, synthetic optics without
+    scattering far in the infrared (panchromatic_optics), three frames at 0,
+    60 and 90 degrees and an SED instrument at 60 degrees.  ``emission_scale``
+    (meta) is the dust emission's scale S for rt_dust_temperature: chosen so
+    that the dust of this model settles at a few tens of kelvin."""
+    base = disk_galaxy(n_cells=n_cells, n_lambda=3, n_pix=n_pix, face_on_tau_v=face_on_tau_v, channels=channels)
+    wl = np.geomspace(0.1, 1000.0, n_lambda)
+    kappa, albedo, g = panchromatic_optics(wl, face_on_tau_v / (2.0 * 0.2))
+    src = replace(base.sources[0], lum=stellar_spectrum(wl))
+    instr = base.instruments + [sed_instrument(60.0, channels=channels)]
+    return replace(base, name=f"panchromatic_disk_{n_cells}", wavelengths=wl, kappa=kappa, albedo=albedo, g=g,
+                   sources=[src], instruments=instr, run=Run(n_per_lambda=max(1, n_packets_total // n_lambda)),
+                   meta={"emission_scale": float(emission_scale), "t_star": 5800.0})
 
 
 def lognormal_cube(n_cells=64, sigma_ln=1.0, mean_axis_tau=2.0, smooth_cells=2.0, seed=4,

@@ -148,9 +148,11 @@ def block_sum(a, b):
     return a.reshape(a.shape[:-2] + (ny // b, b, nx // b, b)).sum(axis=(-3, -1))
 
 
-def cell_groups(grid, block=4):
-    """Group id of every cell for coarser absorption bins: cartesian grids in
-    block^3 cubes of cells, octrees by the parent node of the leaf."""
+def cell_groups(grid, block=4, level=None):
+    """Group id of every cell for coarser absorption bins: cartesian and
+    rectilinear grids in block^3 cubes of cells; octrees by the leaf's
+    ancestor at depth `level` (the parent node when level is None; a leaf
+    shallower than `level` is its own group)."""
     if grid.kind in ("cartesian", "rectilinear"):
         nx, ny, nz = grid.shape
         iz, iy, ix = np.meshgrid(np.arange(nz) // block, np.arange(ny) // block, np.arange(nx) // block,
@@ -158,12 +160,25 @@ def cell_groups(grid, block=4):
         gx, gy = (nx + block - 1) // block, (ny + block - 1) // block
         return (ix + gx * (iy + gy * iz)).reshape(-1)
     child = np.asarray(grid.child, dtype=np.int64)
-    groups = np.zeros(grid.n_cells, dtype=np.int64)
-    parents = np.flatnonzero(child >= 0)
+    n = len(child)
+    parent = np.full(n, -1, dtype=np.int64)
+    depth = np.zeros(n, dtype=np.int64)
+    # children follow their parents in the node array: one pass in order
+    inner = np.flatnonzero(child >= 0)
     for o in range(8):
-        kids = child[parents] + o
-        leaf = child[kids] < 0
-        groups[-child[kids[leaf]] - 1] = parents[leaf]
+        parent[child[inner] + o] = inner
+    for node in inner:  # depths, parents first
+        depth[child[node]:child[node] + 8] = depth[node] + 1
+    leaves = np.flatnonzero(child < 0)
+    anc = leaves.copy() if level is not None else parent[leaves].clip(0)
+    if level is not None:
+        for _ in range(int(depth.max())):
+            up = depth[anc] > level
+            if not up.any():
+                break
+            anc = np.where(up, parent[anc], anc)
+    groups = np.zeros(grid.n_cells, dtype=np.int64)
+    groups[-child[leaves] - 1] = anc
     return groups
 
 

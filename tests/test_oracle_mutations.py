@@ -57,6 +57,17 @@ MUTATIONS = {
     # rectilinear grid planes read one edge off
     "rect_plane_index": ("return kind == 2 ? edges[axis][(size_t)i] :",
                          "return kind == 2 ? edges[axis][(size_t)(i > 0 ? i - 1 : 0)] :", "test_oracle_rectilinear.py"),
+    # Planck function with the wrong power of the wavelength
+    "planck_power": ("return 1.0 / (std::pow(lambda_um, 5.0) * std::expm1(kC2 / (lambda_um * T)));",
+                     "return 1.0 / (std::pow(lambda_um, 4.0) * std::expm1(kC2 / (lambda_um * T)));",
+                     "test_oracle_panchromatic.py"),
+    # dust emission from the extinction instead of the absorption coefficient
+    "emission_albedo": ("scale * P.kappa[(size_t)l] * (1.0 - P.albedo[(size_t)l]) * w[(size_t)l]",
+                        "scale * P.kappa[(size_t)l] * w[(size_t)l]", "test_oracle_panchromatic.py"),
+    # emitting cell drawn uniformly instead of by luminosity
+    "dust_cell_uniform": ("const int64_t cell = std::min<int64_t>(c, (int64_t)cum.size() - 1);",
+                          "const int64_t cell = std::min<int64_t>((int64_t)(u[0] * cum.size()), (int64_t)cum.size() - 1); (void)c;",
+                          "test_oracle_panchromatic.py"),
     # derivative of exp with the wrong sign
     "dual_exp_sign": ("inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, e * a.d}; }",
                       "inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, -e * a.d}; }",
