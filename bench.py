@@ -350,6 +350,68 @@ def spiral_rate(args, device, stream, flush, peak):
     return out
 
 
+def panchromatic_rate(args, device, stream, flush):
+    """Panchromatic mode on the disk galaxy (256^3 cells, 24 wavelengths
+    0.1-1000 um, a 5800 K stellar spectrum): a stellar launch, the
+    equilibrium dust temperatures from its absorption tallies, the thermal
+    emission table, and a launch of dust-emission packets; device times of
+    each step (CUDA events) and the energy balance."""
+    import torch
+    from paper_1410_1629_gb300 import rt
+    from paper_1410_1629_gb300 import workloads as W
+    prob = W.panchromatic_disk(n_cells=args.panchromatic_cells, n_pix=512,
+                               n_packets_total=int(args.panchromatic_packets))
+    S = prob.meta["emission_scale"]
+    n = prob.run.n_per_lambda
+    sim = rt.Simulation(prob, device=device)
+    try:
+        lanes = sim.tune(max(1, n // 20), seed=1, stream=stream.cuda_stream)
+        T = torch.zeros(prob.grid.n_cells, dtype=torch.float64, device=f"cuda:{device}")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        times = {}
+        for i in range(2):  # a warm-up pass, then the timed one
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                sim.reset(stream=stream)
+                ev[0].record(stream)
+                sim.launch(n, 0, 0, stream=stream)
+                ev[1].record(stream)
+            clamped = rt.rt_dust_temperature(sim.ctx, S, 1.0, 1e4, 0, 0, T.data_ptr(), 1, stream.cuda_stream)
+            with torch.cuda.stream(stream):
+                ev[2].record(stream)
+            rt.rt_set_dust_emission(sim.ctx, T.data_ptr(), 1, S, stream.cuda_stream)
+            with torch.cuda.stream(stream):
+                ev[3].record(stream)
+                absorbed_stars = sim.stats()["absorbed"]
+                sim.reset(stream=stream)
+                flush.zero_()
+            e_dust0 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e_dust0.record(stream)
+                sim.launch(n, 0, 1, stream=stream, emitter=rt.RT_EMITTER_DUST)
+                ev[4].record(stream)
+            ev[4].synchronize()
+            times = {"stellar_ms": ev[0].elapsed_time(ev[1]), "temperature_ms": ev[1].elapsed_time(ev[2]),
+                     "emission_table_ms": ev[2].elapsed_time(ev[3]), "dust_launch_ms": e_dust0.elapsed_time(ev[4])}
+        st = sim.stats()
+        Tn = T.cpu().numpy()
+    finally:
+        sim.close()
+    hot = Tn[Tn > 0]
+    packets = n * prob.n_lambda
+    return {"workload": f"panchromatic_disk_{args.panchromatic_cells}: {args.panchromatic_cells}^3 cells, "
+                        f"{prob.n_lambda} wavelengths 0.1-1000 um, 5800 K stars, {packets:.1e} packets per launch, "
+                        "three 512^2 frames and an SED instrument",
+            "packets": int(packets), **times,
+            "stellar_packets_per_s": packets / (times["stellar_ms"] / 1e3),
+            "dust_packets_per_s": packets / (times["dust_launch_ms"] / 1e3),
+            "temperature_K": {"min": float(hot.min()), "median": float(np.median(hot)), "max": float(hot.max())},
+            "cells_held_at_limits": int(clamped),
+            "dust_emitted_over_absorbed": float(st["emitted"] / absorbed_stars),
+            "dust_conservation_rel": abs(st["emitted"] - st["escaped"] - st["absorbed"] - st["truncated"]) / st["emitted"],
+            "tuned": {"control_lanes": lanes}, "device_flags": int(st["device_flags"])}
+
+
 def plain_cube_rate(args, device, stream, flush):
     """The plain method: 32^3 uniform cube, axis tau 1, albedo 0.6, g 0.5,
     central point source, 1e5 packets, one 64^2 face-on frame."""
@@ -692,9 +754,10 @@ def run_gpu(args, prob, world, rank, local_rank):
     # the roofline of the kernels whose working set stays in L2
     l2 = None
     if rank == 0 and world == 1:
-        l2 = {"gb_per_s": rt.rt_probe_bandwidth(device, 32 << 20, 40, 5),
-              "how": "rt_probe_bandwidth: L2-cached float4 loads over a 32 MiB buffer, 40 passes, best of 5, "
-                     "CUDA events", "hbm_read_gb_per_s": rt.rt_probe_bandwidth(device, 4 << 30, 2, 3)}
+        sizes = {f"{m}MiB": rt.rt_probe_bandwidth(device, m << 20, 40, 5) for m in (8, 16, 32, 48)}
+        l2 = {"gb_per_s": max(sizes.values()), "by_buffer": sizes,
+              "how": "rt_probe_bandwidth: L2-cached float4 loads over buffers of 8-48 MiB, 40 passes, best of 5, "
+                     "CUDA events; the best buffer", "hbm_read_gb_per_s": rt.rt_probe_bandwidth(device, 4 << 30, 2, 3)}
         for block, secs_key in ((adjoint, "adjoint_ms"), (batch, "seconds_per_launch")):
             if not block:
                 continue
@@ -712,6 +775,9 @@ def run_gpu(args, prob, world, rank, local_rank):
         spiral = spiral_rate(args, device, stream, flush, (peak, peak_kind))
     if rank == 0 and world == 1 and not args.skip_plain:
         plain = plain_cube_rate(args, device, stream, flush)
+    panchro = None
+    if rank == 0 and world == 1 and not args.skip_panchromatic:
+        panchro = panchromatic_rate(args, device, stream, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -743,7 +809,8 @@ def run_gpu(args, prob, world, rank, local_rank):
                                               "GB_per_s": bytes_launch / mean_launch / 1e9}},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_step * args.steps, "adjoint": adjoint,
                 "tuned": {"control_lanes": lanes, "sample": "5 % of the packets, another seed, before the warm-up"},
-                "batch": batch, "octree": octree, "spiral_example": spiral, "plain_cube": plain, "l2_peak": l2,
+                "batch": batch, "octree": octree, "spiral_example": spiral, "plain_cube": plain,
+                "panchromatic": panchro, "l2_peak": l2,
                 "clocks": clk,
                 "checks": {"conservation_rel": conservation, "path_crossings": int(path_cross),
                            "walked_peel_crossings": int(peel_cross), "column_peels": int(column_peels),
@@ -776,6 +843,10 @@ def main():
                     help="packets of the clumpy-octree measurement (default 2e8, the workload's size)")
     ap.add_argument("--skip-spiral", action="store_true", help="skip the paper's spiral-galaxy example")
     ap.add_argument("--skip-plain", action="store_true", help="skip the plain-method 32^3 cube")
+    ap.add_argument("--skip-panchromatic", action="store_true", help="skip the panchromatic disk galaxy")
+    ap.add_argument("--panchromatic-cells", type=int, default=256, help="cells per axis of the panchromatic disk")
+    ap.add_argument("--panchromatic-packets", type=float, default=2.4e7,
+                    help="packets per launch of the panchromatic disk (stellar and dust launches)")
     ap.add_argument("--skip-fd", action="store_true", help="skip the finite-difference check of the adjoint")
     ap.add_argument("--fd-packets", type=float, default=1e6,
                     help="packets of the finite-difference check (64 cells x 2 forward launches)")

@@ -212,6 +212,10 @@ typedef struct {
                            drawn in proportion to its luminosity at the packet's wavelength, a
                            uniform position in it, an isotropic direction; a wavelength at which
                            the dust emits nothing launches packets of zero weight that end at once */
+  int32_t blocks_per_sm; /* resident blocks of 256 threads per SM of the persistent transport grid
+                            (0 = the value rt_tune chose, else as many as fit: 4 cartesian,
+                            3 octree); the grid is this times the SM count                   */
+  int32_t reserved;
 } rt_launch_opts;
 
 /* Tallies since the last rt_reset_tallies. */
@@ -283,13 +287,15 @@ rt_status rt_add_instruments(rt_ctx ctx, int32_t n, const rt_instrument_desc* in
 rt_status rt_launch_packets(rt_ctx ctx, uint64_t n_per_lambda, uint64_t first_packet_id, uint64_t seed,
                             const rt_launch_opts* opts, void* stream);
 
-/* Choose the per-event deferral threshold (opts->control_lanes) for this
- * context's problem: times a launch of n_per_lambda packets per wavelength
- * for each of 8, 12, 16, 20, 24, 28 lanes (other options from opts or the
- * defaults) and keeps the fastest for later launches with control_lanes 0;
- * written to *control_lanes if not NULL.  The threshold only reorders work:
- * results are the same to FP64 summation order.  The tallies are zeroed
- * afterwards.  Synchronous.  Errors: as rt_launch_packets. */
+/* Choose the per-event deferral threshold (opts->control_lanes) and the
+ * resident blocks per SM (opts->blocks_per_sm) for this context's problem:
+ * times a launch of n_per_lambda packets per wavelength for each of 8, 12,
+ * 16, 20, 24, 28 lanes at the most resident blocks, then for the best
+ * threshold with one and two blocks per SM fewer (other options from opts or
+ * the defaults), and keeps the fastest pair for later launches with 0 in
+ * those fields; the threshold is written to *control_lanes if not NULL.
+ * Both only reorder work: results are the same to FP64 summation order.  The
+ * tallies are zeroed afterwards.  Synchronous.  Errors: as rt_launch_packets. */
 rt_status rt_tune(rt_ctx ctx, uint64_t n_per_lambda, uint64_t seed, const rt_launch_opts* opts,
                   int32_t* control_lanes, void* stream);
 

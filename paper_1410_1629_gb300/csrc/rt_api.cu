@@ -129,6 +129,7 @@ struct rt_ctx_s {
   unsigned long long* d_adj_max = nullptr;
   std::vector<Batch*> batches;  // by id; null after rt_batch_destroy
   int control_lanes = 0;        // chosen by rt_tune for launches with control_lanes 0 (0: none)
+  int blocks_per_sm = 0;        // chosen by rt_tune for launches with blocks_per_sm 0 (0: as many as fit)
   int adjoint_lanes = 0;        // chosen by rt_adjoint_tune for rt_adjoint (0: none)
   double* d_tune_grad = nullptr;  // rt_adjoint_tune's scratch gradient
   size_t tune_grad_cells = 0;
@@ -364,7 +365,7 @@ rt_status upload_tables(rt_ctx c, cudaStream_t s) {
     I.channels = d.channels;
     I.image = c->instr[q].d_image;
     int axis = 0, dir = 0;
-    if (c->grid_kind == RT_GRID_CARTESIAN && frame_axis(I, axis, dir)) {
+    if (c->grid_kind != RT_GRID_OCTREE && frame_axis(I, axis, dir)) {
       const int k = 2 * axis + (dir > 0 ? 1 : 0);
       if (!c->d_columns[k]) RT_CUDA(c, pool_alloc(c, &c->d_columns[k], (size_t)c->n_cells * sizeof(float)));
       I.column = c->d_columns[k];
@@ -394,6 +395,11 @@ rt_status upload_tables(rt_ctx c, cudaStream_t s) {
 }
 
 bool is_finite(double v) { return std::isfinite(v); }
+
+// The FP64 planes of one axis (cartesian and rectilinear grids).
+const double* axis_planes(rt_ctx c, int axis) {
+  return c->d_planes64 + (axis == 0 ? 0 : (axis == 1 ? c->nx + 1 : c->nx + c->ny + 2));
+}
 
 void free_batch(Batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -986,6 +992,8 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   p.trace_packet = o.trace_packet;
   p.trace_lambda = o.trace_lambda;
   p.control_min = o.control_lanes ? o.control_lanes : (c->control_lanes ? c->control_lanes : 16);
+  if (o.blocks_per_sm < 0) return fail(c, RT_ERR_ARG, "rt_launch_packets: blocks_per_sm must be >= 0");
+  p.blocks_per_sm = o.blocks_per_sm ? o.blocks_per_sm : c->blocks_per_sm;
   p.inv_n_per_lambda = (float)(1.0 / (double)n_per_lambda);
   for (int l = 0; l < c->n_lambda; ++l) {
     p.L0[l] = lum_total[(size_t)l] / (double)p.n_norm;
@@ -994,7 +1002,7 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   p.dust_cum = dust ? c->d_dust_cum : nullptr;
   p.profile = reinterpret_cast<unsigned long long*>(o.profile);
   p.flags = c->d_flags;
-  p.use_columns = c->grid_kind == RT_GRID_CARTESIAN && !o.walk_peels;
+  p.use_columns = c->grid_kind != RT_GRID_OCTREE && !o.walk_peels;
   cudaEvent_t* ev = nullptr;
   if (o.time_parts) {
     for (auto& e : c->part_ev)
@@ -1029,6 +1037,7 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
       if (!c->columns_used[k]) continue;
       const int axis = k / 2;
       cudaError_t ec = launch_columns(c->d_density, c->nx, c->ny, c->nz, axis, (k & 1) ? 1 : -1, p.d[axis],
+                                      c->grid_kind == RT_GRID_RECTILINEAR ? axis_planes(c, axis) : nullptr,
                                       c->d_columns[k], s);
       if (ec != cudaSuccess) return cuda_fail(c, ec, "column sums");
     }
@@ -1212,7 +1221,8 @@ rt_status rt_adjoint(rt_ctx c, const double* const* adj_images, int32_t n_adj_im
       const int axis = k / 2;
       if (!c->d_line_dep[k]) RT_CUDA(c, pool_alloc(c, &c->d_line_dep[k], (size_t)c->n_cells * sizeof(double)));
       line_dep[k] = c->d_line_dep[k];
-      e = launch_columns(c->d_density, c->nx, c->ny, c->nz, axis, (k & 1) ? 1 : -1, p.d[axis], c->d_columns[k], s);
+      e = launch_columns(c->d_density, c->nx, c->ny, c->nz, axis, (k & 1) ? 1 : -1, p.d[axis], nullptr,
+                         c->d_columns[k], s);
       if (e != cudaSuccess) return cuda_fail(c, e, "column sums");
     }
   }
@@ -1234,8 +1244,10 @@ rt_status rt_tune(rt_ctx c, uint64_t n_per_lambda, uint64_t seed, const rt_launc
   o.records = nullptr;
   o.trace = nullptr;
   o.profile = nullptr;
+  o.blocks_per_sm = 0;
   if (set_device(c) != RT_OK) return RT_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
+  c->blocks_per_sm = 0;  // the threshold is timed with the most resident blocks
   const int cand[] = {8, 12, 16, 20, 24, 28};
   cudaEvent_t e0, e1;
   RT_CUDA(c, cudaEventCreate(&e0));
@@ -1261,10 +1273,34 @@ rt_status rt_tune(rt_ctx c, uint64_t n_per_lambda, uint64_t seed, const rt_launc
       best_lanes = lanes;
     }
   }
+  // then the resident blocks per SM at that threshold: the most that fit
+  // (0), one and two fewer
+  int best_blocks = 0;
+  o.control_lanes = best_lanes;
+  const int max_blocks = c->grid_kind == RT_GRID_OCTREE ? 3 : 4;
+  for (int blocks = max_blocks - 1; st == RT_OK && blocks >= max_blocks - 2 && blocks >= 1; --blocks) {
+    o.blocks_per_sm = blocks;
+    cudaError_t e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) st = rt_launch_packets(c, n_per_lambda, 0, seed, &o, stream);
+    if (st != RT_OK) break;
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(c, e, "rt_tune");
+      break;
+    }
+    if (ms < best) {
+      best = ms;
+      best_blocks = blocks;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != RT_OK) return st;
   c->control_lanes = best_lanes;
+  c->blocks_per_sm = best_blocks;
   if (control_lanes) *control_lanes = best_lanes;
   return rt_reset_tallies(c, stream);
 }

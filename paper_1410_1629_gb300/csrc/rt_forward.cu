@@ -28,6 +28,7 @@ cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaS
                                                     tr::kBlock, 0);
   if (e != cudaSuccess) return e;
   per_sm = per_sm < 1 ? 1 : per_sm;
+  if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;
   unsigned long long blocks = (unsigned long long)num_sms * per_sm;
   const unsigned long long useful = (p.n_total + tr::kBlock - 1) / tr::kBlock;
   if (blocks > useful) blocks = useful;
@@ -44,9 +45,10 @@ namespace {
 
 // One thread per grid line along `axis`: the density integral from the far
 // face of each cell to the boundary the ray meets (direction dir), summed in
-// FP64 from that boundary inwards.
+// FP64 from that boundary inwards.  Cell widths along the axis: d, or the
+// differences of the FP64 planes `planes` (rectilinear grids) when given.
 __global__ void k_columns(const float* __restrict__ density, int nx, int ny, int nz, int axis, int dir, double d,
-                          float* __restrict__ out) {
+                          const double* __restrict__ planes, float* __restrict__ out) {
   const long long n_lines = axis == 0 ? (long long)ny * nz : (axis == 1 ? (long long)nx * nz : (long long)nx * ny);
   for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < n_lines;
        L += (long long)gridDim.x * blockDim.x) {
@@ -64,20 +66,20 @@ __global__ void k_columns(const float* __restrict__ density, int nx, int ny, int
       const int j = dir > 0 ? n - 1 - k : k;
       const long long c = base + (long long)j * stride;
       out[c] = (float)acc;
-      acc += (double)density[c] * d;
+      acc += (double)density[c] * (planes ? planes[j + 1] - planes[j] : d);
     }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_columns(const float* density, int nx, int ny, int nz, int axis, int dir, float d, float* out,
-                           cudaStream_t stream) {
+cudaError_t launch_columns(const float* density, int nx, int ny, int nz, int axis, int dir, float d,
+                           const double* planes, float* out, cudaStream_t stream) {
   const long long n_lines = axis == 0 ? (long long)ny * nz : (axis == 1 ? (long long)nx * nz : (long long)nx * ny);
   const int block = 256;
   long long blocks = (n_lines + block - 1) / block;
   if (blocks > 65535) blocks = 65535;
-  k_columns<<<(unsigned)blocks, block, 0, stream>>>(density, nx, ny, nz, axis, dir, (double)d, out);
+  k_columns<<<(unsigned)blocks, block, 0, stream>>>(density, nx, ny, nz, axis, dir, (double)d, planes, out);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t 
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward_octree, tr::kBlock, 0);
   if (e != cudaSuccess) return e;
   per_sm = per_sm < 1 ? 1 : per_sm;
+  if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;
   unsigned long long blocks = (unsigned long long)num_sms * per_sm;
   const unsigned long long useful = (p.n_total + tr::kBlock - 1) / tr::kBlock;
   if (blocks > useful) blocks = useful;

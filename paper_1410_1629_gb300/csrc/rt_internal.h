@@ -110,6 +110,7 @@ struct FwdParams {
   unsigned long long trace_packet;
   int trace_lambda;
   int control_min;  // lanes that must wait for per-event work before a warp runs it
+  int blocks_per_sm;  // resident blocks of the persistent grid per SM (0: as many as fit)
   float inv_n_per_lambda;          // 1 / n_per_lambda (estimate of a packet's wavelength index)
   double L0[kMaxLambda];           // packet weight at emission, L_tot / n_norm, per wavelength
   double L_cut[kMaxLambda];        // w_min * L0 per wavelength
@@ -202,9 +203,10 @@ long long dust_tiles(long long n_cells);
 cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaStream_t stream);
 // Per-line suffix sums for peel-offs along axis `axis` in direction dir
 // (+1 / -1): out[c] = sum over the cells j beyond c on c's grid line of
-// rho_j d, accumulated in FP64 from the boundary (rt_forward.cu).
-cudaError_t launch_columns(const float* density, int nx, int ny, int nz, int axis, int dir, float d, float* out,
-                           cudaStream_t stream);
+// rho_j d_j, accumulated in FP64 from the boundary (rt_forward.cu); d_j = d,
+// or the width between the FP64 planes of the axis when `planes` is given.
+cudaError_t launch_columns(const float* density, int nx, int ny, int nz, int axis, int dir, float d,
+                           const double* planes, float* out, cudaStream_t stream);
 cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t stream);
 cudaError_t launch_forward_rect(const FwdParams& p, int num_sms, cudaStream_t stream);
 // The sorted peel-off pass after a forward launch with p.peel set

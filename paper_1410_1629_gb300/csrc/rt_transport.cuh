@@ -80,6 +80,32 @@ __device__ __forceinline__ double widen(float f) {
   return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(u << 29));
 }
 
+// f 2^e in FP64 for a positive FP32 f, with integer operations (the widening
+// above with the exponent moved by e); zero for results below FP64's normal
+// range and for zero or non-finite f.
+__device__ __forceinline__ double widen_exp(float f, int e) {
+  const unsigned u = __float_as_uint(f);
+  const int be = (int)((u >> 23) & 0xffu);
+  if (be == 0 || be == 0xff) return be == 0 && (u & 0x7fffffu) ? ldexp((double)f, e) : 0.0;
+  const int de = be - 127 + 1023 + e;  // biased FP64 exponent of the result
+  if (de <= 0) return 0.0;
+  const unsigned hi = ((unsigned)de << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// A positive FP64 value v as m 2^e with m in [1/2, 1) cut to FP32 (integer
+// operations); zero gives m = 0, e = 0.
+__device__ __forceinline__ float split_exp(double v, int& e) {
+  const long long b = __double_as_longlong(v);
+  const int be = (int)((b >> 52) & 0x7ff);
+  if (be == 0 || v <= 0.0) {
+    e = 0;
+    return 0.0f;
+  }
+  e = be - 1022;  // v = (1.m / 2) 2^(be - 1022)
+  return __uint_as_float((126u << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
+}
+
 // FP64 to FP32 by cutting the significand to 24 bits, with integer
 // operations; zero and values outside the normal FP32 range take the
 // ordinary conversion.
@@ -130,6 +156,24 @@ __device__ __forceinline__ void add_absorption(double* p, double v) {
       : "memory");
 }
 
+// atomicAdd(addr, v), where the lanes of the warp that add to the same
+// address at the same time first sum their values in lane order and one of
+// them issues the atomic: the lanes of a batch warp carry packets of one
+// small model, whose peel-offs from a central point source all reach one
+// pixel.  (In the transport kernel the extra registers cost a spill.)
+__device__ __forceinline__ void add_aggregated(double* addr, double v) {
+  const unsigned act = __activemask();
+  const unsigned grp = __match_any_sync(act, (unsigned long long)addr);
+  const unsigned lane = threadIdx.x & 31u;
+  if (grp == (1u << lane)) {
+    atomicAdd(addr, v);
+    return;
+  }
+  double sum = 0.0;
+  for (unsigned m = grp; m; m &= m - 1u) sum += __shfl_sync(grp, v, __ffs(m) - 1);
+  if ((int)lane == __ffs(grp) - 1) atomicAdd(addr, sum);
+}
+
 // 1 - exp(-x) for x >= 0 with a relative error below 5e-7: the alternating
 // series through x^8 for x < 1/4 (truncation below 1e-10), 1 - exp(-x) above.
 __device__ __forceinline__ float one_minus_exp_neg(float x) {
@@ -169,6 +213,7 @@ __device__ __forceinline__ int stride_of(const FwdParams& P, int a) { return P.s
 struct CartGrid {
   static constexpr bool kColumns = true;  // peel-offs along grid axes may use column sums
   static constexpr bool kIndexCells = true;  // cells indexed by (ix, iy, iz) between planes
+  static constexpr bool kSortedPass = true;  // walked peel-offs may go to the sorted pass
   struct Cell {
     int ix, iy, iz;
   };
@@ -259,6 +304,13 @@ struct CartGrid {
     return fmaf((float)i, P.d[a], P.lo[a]);
   }
 
+  // The cell of a point inside the grid.
+  __device__ static __forceinline__ void locate_cell(const FwdParams& P, float3 x, Cell& c) {
+    c.ix = min(max(__float2int_rd((x.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
+    c.iy = min(max(__float2int_rd((x.y - P.lo[1]) * P.inv_d[1]), 0), P.ny - 1);
+    c.iz = min(max(__float2int_rd((x.z - P.lo[2]) * P.inv_d[2]), 0), P.nz - 1);
+  }
+
   __device__ static __forceinline__ Cell carried(const Walk& w) { return Cell{w.ix, w.iy, w.iz}; }
 
   // Keep x inside cell c.
@@ -277,8 +329,9 @@ struct CartGrid {
 // cartesian one with the plane positions read from the edge arrays (FP32
 // copies of the FP64 edges); a position is located by binary search.
 struct RectGrid {
-  static constexpr bool kColumns = false;
+  static constexpr bool kColumns = true;
   static constexpr bool kIndexCells = true;
+  static constexpr bool kSortedPass = false;
   using Cell = CartGrid::Cell;
   using Walk = CartGrid::Walk;
   struct Scratch {};
@@ -357,6 +410,12 @@ struct RectGrid {
 
   __device__ static __forceinline__ float plane(const FwdParams& P, int a, int i) { return edge(P, a, i); }
 
+  __device__ static __forceinline__ void locate_cell(const FwdParams& P, float3 x, Cell& c) {
+    c.ix = locate(P, 0, x.x, P.nx);
+    c.iy = locate(P, 1, x.y, P.ny);
+    c.iz = locate(P, 2, x.z, P.nz);
+  }
+
   __device__ static __forceinline__ Cell carried(const Walk& w) { return Cell{w.ix, w.iy, w.iz}; }
 
   __device__ static __forceinline__ void clamp(const FwdParams& P, const Cell& c, float3& x) {
@@ -378,6 +437,7 @@ __shared__ int S_STACK[kBlock * kOctStack];
 struct OctGrid {
   static constexpr bool kColumns = false;
   static constexpr bool kIndexCells = false;
+  static constexpr bool kSortedPass = false;
   struct Cell {
     int leaf;
     float lo[3], hi[3];
@@ -588,6 +648,10 @@ __shared__ double S_WEIGHT[kBlock];
 __shared__ float3 S_DIR[kBlock];
 __shared__ float2 S_HG[kBlock];
 __shared__ int S_EVENT[kBlock], S_INSTR_Q[kBlock], S_WPHASE[kBlock];
+// binary exponent of the first forced-path walk's deposit weight: the weight
+// is aux0 2^S_DEPEXP with aux0 in [1/2, 1), so that absorption deposits keep
+// FP64's range whatever the packet weight (FP32 alone spans 1e-38 .. 3e38)
+__shared__ int S_DEPEXP[kBlock];
 __shared__ bool S_HAS_CELL[kBlock];
 __shared__ CartGrid::Cell S_CELL_CART[kBlock];
 __shared__ OctGrid::Cell S_CELL_OCT[kBlock];
@@ -680,6 +744,7 @@ __device__ __forceinline__ float3 instr_dir(const DevInstr& I) { return make_flo
 // it on the same grid line.  The walk's crossings (n_cross) are counted all
 // the same.  known: x lies in cell cc.  False when the position is outside the
 // grid (the walk then finds the entry).
+template <class G>
 __device__ __forceinline__ bool column_tau(const FwdParams& P, float3 x, bool known, const CartGrid::Cell& cc,
                                            const DevInstr& I, float kappa, float& th,
                                            unsigned long long& n_cross) {
@@ -688,16 +753,14 @@ __device__ __forceinline__ bool column_tau(const FwdParams& P, float3 x, bool kn
     c = cc;
   } else {
     if (!inside_box(P, x)) return false;
-    c.ix = min(max(__float2int_rd((x.x - P.lo[0]) * P.inv_d[0]), 0), P.nx - 1);
-    c.iy = min(max(__float2int_rd((x.y - P.lo[1]) * P.inv_d[1]), 0), P.ny - 1);
-    c.iz = min(max(__float2int_rd((x.z - P.lo[2]) * P.inv_d[2]), 0), P.nz - 1);
+    G::locate_cell(P, x, c);
   }
   const int a = I.axis;
   const bool up = I.dir > 0;
   const int i = a == 0 ? c.ix : (a == 1 ? c.iy : c.iz);
   const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
   const float xa = a == 0 ? x.x : (a == 1 ? x.y : x.z);
-  const float plane = fmaf((float)(i + (up ? 1 : 0)), P.d[a], P.lo[a]);
+  const float plane = G::plane(P, a, i + (up ? 1 : 0));
   const float ds0 = fmaxf(up ? plane - xa : xa - plane, 0.0f);
   const int cell = c.ix + P.nx * (c.iy + P.ny * c.iz);  // row-major: the column sums
   const int slot = c.ix * P.stride[0] + c.iy * P.stride[1] + c.iz * P.stride[2];
@@ -709,7 +772,7 @@ __device__ __forceinline__ bool column_tau(const FwdParams& P, float3 x, bool kn
 template <class G>
 __device__ __forceinline__ bool column_peel(const FwdParams& P, Lane<G>& s, const DevInstr& I, LaneTally* bt) {
   unsigned long long nc;
-  if (!column_tau(P, s.x, s.has_cell(), s.cell(), I, s.kappa, s.th, nc)) return false;
+  if (!column_tau<G>(P, s.x, s.has_cell(), s.cell(), I, s.kappa, s.th, nc)) return false;
   s.tl = 0.0f;
   s.walking = false;
   bt->crossings += nc;
@@ -969,7 +1032,7 @@ __device__ __forceinline__ void request_walk(Lane<G>& s, int phase, float3 d) {
 // weight (1 - albedo) L.
 template <class G>
 __device__ __forceinline__ void request_path(Lane<G>& s) {
-  s.aux0 = cut(S_LAM[s.lam].one_minus_albedo * s.L());
+  s.aux0 = split_exp(S_LAM[s.lam].one_minus_albedo * s.L(), S_DEPEXP[threadIdx.x]);
   request_walk(s, kPath1, s.k());
 }
 
@@ -1120,7 +1183,7 @@ __device__ __forceinline__ void peel_scan(const FwdParams& P, Lane<G>& s, LaneTa
         s.phase = phase;
         return;
       }
-      if (P.peel && defer_peel(P, s, I, emission)) {
+      if (P.peel && G::kSortedPass && defer_peel(P, s, I, emission)) {
         // walked and deposited by the sorted pass; on to the next instrument
         bt->peeloffs += 1u;
         s.q() += 1;
@@ -1247,8 +1310,13 @@ __device__ __forceinline__ void walk_step(const FwdParams& P, Lane<G>& s, unsign
   }
   if (path1 && dt > 0.0f) {
     // continuous absorption: (1 - albedo) L exp(-tau_before) (1 - exp(-dtau))
-    const float dep = s.aux0 * __expf(-s.th) * one_minus_exp_neg(dt);
-    add_absorption(&P.absorption[(size_t)s.lam * P.n_cells + G::cell(w)], widen(dep));
+    // exp(-tau_before) = 2^-y, y = k + f with k = floor(y): the integer
+    // part joins the weight's exponent, so deep deposits do not underflow
+    const float y = s.th * 1.44269504f;
+    const float k = floorf(y);
+    const float dep = s.aux0 * exp2f(k - y) * one_minus_exp_neg(dt);
+    add_absorption(&P.absorption[(size_t)s.lam * P.n_cells + G::cell(w)],
+                   widen_exp(dep, S_DEPEXP[threadIdx.x] - (int)k));
   }
   s.th = nh;
   s.tl = nl;

@@ -85,7 +85,8 @@ class rt_launch_opts(ctypes.Structure):
                 ("trace", ctypes.c_void_p), ("trace_capacity", ctypes.c_int64), ("trace_packet", ctypes.c_uint64),
                 ("trace_lambda", ctypes.c_int32), ("control_lanes", ctypes.c_int32),
                 ("profile", ctypes.c_void_p), ("tape", ctypes.c_int32), ("inline_peels", ctypes.c_int32),
-                ("time_parts", ctypes.c_int32), ("emitter", ctypes.c_int32)]
+                ("time_parts", ctypes.c_int32), ("emitter", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class rt_stats(ctypes.Structure):
