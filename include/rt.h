@@ -65,7 +65,7 @@ enum {
   RT_ERR_DEVICE_FLAG = -6   /* a kernel's own bounds check fired; results are not valid        */
 };
 
-enum { RT_GRID_CARTESIAN = 0, RT_GRID_OCTREE = 1, RT_GRID_RECTILINEAR = 2 };
+enum { RT_GRID_CARTESIAN = 0, RT_GRID_OCTREE = 1, RT_GRID_RECTILINEAR = 2, RT_GRID_BINTREE = 3 };
 enum { RT_SOURCE_POINT = 0, RT_SOURCE_EXPDISK = 1, RT_SOURCE_PLUMMER = 2 };
 enum { RT_DEPOSIT_NEAREST = 0, RT_DEPOSIT_BILINEAR = 1, RT_DEPOSIT_SED = 2 };
 enum { RT_LAYOUT_AUTO = 0, RT_LAYOUT_ROW_MAJOR = 1 };
@@ -82,6 +82,14 @@ enum { RT_EMITTER_SOURCES = 0, RT_EMITTER_DUST = 1 };
  *       grid of Table 1(d) is the case of power-law spaced edges.  Density
  *       and cell ids as for RT_GRID_CARTESIAN.  Not supported by rt_adjoint,
  *       the adjoint tape, batches or rt_launch_packets_noalloc.
+ *   kind RT_GRID_BINTREE: a k-d tree (the BinTree grid of Table 1(d)):
+ *       node 0 the root; child[n] >= 0 is the index of the first of n's two
+ *       contiguous children (the lower, then the upper half of n's box split
+ *       at its midpoint along split_axis[n], 0 = x, 1 = y, 2 = z),
+ *       child[n] < 0 marks a leaf with leaf id -(child[n] + 1); density
+ *       float32 [n_leaves]; cell id = leaf id; depth at most 96, node
+ *       indices below 2^29.  Peel-offs walk their rays; not supported by the
+ *       adjoint, batches, the allocation-free call or the dust emission.
  *   kind RT_GRID_OCTREE: recursive 2x2x2 subdivision of `bounds` at box
  *       midpoints; child int32 [n_nodes], node 0 the root: child[n] >= 0 is
  *       the index of the first of n's eight contiguous children (octant
@@ -107,6 +115,7 @@ typedef struct {
   int32_t on_device;
   int32_t layout;         /* RT_LAYOUT_AUTO or RT_LAYOUT_ROW_MAJOR */
   const double* edges[3]; /* RT_GRID_RECTILINEAR: cell edges per axis (host or device, as on_device) */
+  const int8_t* split_axis; /* RT_GRID_BINTREE: split axis per node (host or device, as on_device) */
 } rt_grid_desc;
 
 /* Emission component (Sect. 2.2 stellar system, Sect. 3.4 position sampling,

@@ -47,7 +47,7 @@ class OrGrid(ctypes.Structure):
                 ("nz", ctypes.c_int32), ("bounds", ctypes.c_double * 6),
                 ("density", ctypes.POINTER(ctypes.c_float)), ("n_nodes", ctypes.c_int64),
                 ("child", ctypes.POINTER(ctypes.c_int32)), ("n_leaves", ctypes.c_int64),
-                ("edges", ctypes.POINTER(ctypes.c_double) * 3)]
+                ("edges", ctypes.POINTER(ctypes.c_double) * 3), ("split_axis", ctypes.POINTER(ctypes.c_int8))]
 
 
 class OrSource(ctypes.Structure):
@@ -188,12 +188,16 @@ class _Marshalled:
                     self.keep.append(e)
                     og.edges[a] = _ptr(e, ctypes.c_double)
         else:
-            og.kind = 1
+            og.kind = 1 if grid.kind == "octree" else 3
             child = np.ascontiguousarray(grid.child, dtype=np.int32)
             self.keep.append(child)
             og.child = _ptr(child, ctypes.c_int32)
             og.n_nodes = child.size
             og.n_leaves = dens.size
+            if grid.kind == "bintree":
+                axis = np.ascontiguousarray(grid.split_axis, dtype=np.int8)
+                self.keep.append(axis)
+                og.split_axis = _ptr(axis, ctypes.c_int8)
         nl = len(problem.kappa)
         kappa = np.ascontiguousarray(problem.kappa, dtype=np.float64)
         albedo = np.ascontiguousarray(problem.albedo, dtype=np.float64)

@@ -164,7 +164,7 @@ template <class T> void set_comp(V3<T>& a, int axis, T v) {
 extern "C" {
 
 typedef struct {
-  int32_t kind;  // 0 = cartesian, 1 = octree, 2 = rectilinear
+  int32_t kind;  // 0 = cartesian, 1 = octree, 2 = rectilinear, 3 = k-d tree
   int32_t nx, ny, nz;
   double bounds[6];  // xmin, xmax, ymin, ymax, zmin, zmax
   const float* density;  // cartesian, rectilinear [nz][ny][nx] (x fastest); octree: per leaf
@@ -172,6 +172,7 @@ typedef struct {
   const int32_t* child;  // octree: >= 0 first child index; < 0 leaf -(leaf+1)
   int64_t n_leaves;
   const double* edges[3];  // rectilinear: cell edges per axis, n + 1 each
+  const int8_t* split_axis;  // k-d tree: split axis of every node (0, 1, 2)
 } or_grid;
 
 typedef struct {
@@ -360,17 +361,20 @@ struct Grid {
   const float* density;
   const int32_t* child;
   int64_t n_nodes, n_leaves;
-  std::vector<Box> leaf_box;  // octree: box of every leaf
+  const int8_t* split_axis = nullptr;  // k-d tree: split axis per node
+  std::vector<Box> leaf_box;  // trees: box of every leaf
   std::vector<double> edges[3];  // rectilinear: cell edges per axis
 
-  int64_t n_cells() const { return kind == 1 ? n_leaves : (int64_t)n[0] * n[1] * n[2]; }
+  // octree (kind 1) and k-d tree (kind 3): cells are the leaves of a tree
+  bool tree() const { return kind == 1 || kind == 3; }
+  int64_t n_cells() const { return tree() ? n_leaves : (int64_t)n[0] * n[1] * n[2]; }
 
   // Plane positions: cartesian lo + i * (hi - lo) / n; rectilinear the
   // given edges (Table 1(d): PowCub grids space them by a power law).
   double plane(int axis, int i) const { return kind == 2 ? edges[axis][(size_t)i] : lo[axis] + i * d[axis]; }
 
   Box cell_box(int64_t cell) const {
-    if (kind == 1) return leaf_box[(size_t)cell];
+    if (tree()) return leaf_box[(size_t)cell];
     int64_t ix = cell % n[0], iy = (cell / n[0]) % n[1], iz = cell / ((int64_t)n[0] * n[1]);
     int64_t idx[3] = {ix, iy, iz};
     Box b;
@@ -378,13 +382,24 @@ struct Grid {
     return b;
   }
 
-  // Octree point location.  For every axis a point on a splitting plane goes
-  // to the child that a ray travelling along k enters there (upper child if
-  // k_a >= 0, lower child if k_a < 0).
-  int64_t octree_locate(const double p[3], const V3d& k, Box* box) const {
+  // Tree point location.  An octree node splits its box at the midpoints of
+  // all three axes (eight children, octant bit a set for the upper half of
+  // axis a); a k-d tree node (Table 1(d): BinTree) at the midpoint of its
+  // split axis (two children, lower then upper).  A point on a splitting
+  // plane goes to the child that a ray travelling along k enters there (the
+  // upper one if k_a >= 0, the lower one if k_a < 0).
+  int64_t tree_locate(const double p[3], const V3d& k, Box* box) const {
     double blo[3] = {lo[0], lo[1], lo[2]}, bhi[3] = {hi[0], hi[1], hi[2]};
     int64_t node = 0;
     while (child[node] >= 0) {
+      if (kind == 3) {
+        const int a = split_axis[node];
+        const double mid = 0.5 * (blo[a] + bhi[a]);
+        const bool upper = comp(k, a) < 0 ? (p[a] > mid) : (p[a] >= mid);
+        if (upper) blo[a] = mid; else bhi[a] = mid;
+        node = child[node] + (upper ? 1 : 0);
+        continue;
+      }
       int oct = 0;
       for (int a = 0; a < 3; ++a) {
         double mid = 0.5 * (blo[a] + bhi[a]);
@@ -408,6 +423,16 @@ struct Grid {
       stack.pop_back();
       int32_t c = child[it.node];
       if (c < 0) { leaf_box[(size_t)(-(int64_t)c - 1)] = it.b; continue; }
+      if (kind == 3) {
+        const int a = split_axis[it.node];
+        const double mid = 0.5 * (it.b.lo[a] + it.b.hi[a]);
+        Box lower = it.b, upper = it.b;
+        lower.hi[a] = mid;
+        upper.lo[a] = mid;
+        stack.push_back({(int64_t)c, lower});
+        stack.push_back({(int64_t)c + 1, upper});
+        continue;
+      }
       for (int oct = 0; oct < 8; ++oct) {
         Box b;
         for (int a = 0; a < 3; ++a) {
@@ -472,7 +497,7 @@ void grid_path(const Grid& G, const V3<T>& x, const V3d& k, int64_t start_cell,
       t = (T(plane) - comp(x, entry_axis)) / T(ka);
     }
   }
-  if (G.kind != 1) {
+  if (!G.tree()) {
     // cartesian and rectilinear: indices of the current cell
     int64_t idx[3];
     if (cell >= 0) {
@@ -513,7 +538,7 @@ void grid_path(const Grid& G, const V3<T>& x, const V3d& k, int64_t start_cell,
       double p[3];
       for (int a = 0; a < 3; ++a) p[a] = xv[a] + val(t) * comp(k, a);
       if (entry_axis >= 0) p[entry_axis] = comp(k, entry_axis) > 0 ? G.lo[entry_axis] : G.hi[entry_axis];
-      leaf = G.octree_locate(p, k, &box);
+      leaf = G.tree_locate(p, k, &box);
     }
     while (true) {
       int axis = -1;
@@ -537,7 +562,7 @@ void grid_path(const Grid& G, const V3<T>& x, const V3d& k, int64_t start_cell,
       for (int a = 0; a < 3; ++a)
         p[a] = std::min(box.hi[a], std::max(box.lo[a], val(comp(x, a)) + val(t) * comp(k, a)));
       p[axis] = plane;
-      leaf = G.octree_locate(p, k, &box);
+      leaf = G.tree_locate(p, k, &box);
     }
   }
 }
@@ -568,7 +593,8 @@ Problem make_problem(const or_problem& in) {
   G.child = in.grid.child;
   G.n_nodes = in.grid.n_nodes;
   G.n_leaves = in.grid.n_leaves;
-  if (G.kind == 1) G.build_leaf_boxes();
+  G.split_axis = in.grid.split_axis;
+  if (G.tree()) G.build_leaf_boxes();
   P.n_lambda = in.n_lambda;
   P.kappa.assign(in.kappa, in.kappa + in.n_lambda);
   P.albedo.assign(in.albedo, in.albedo + in.n_lambda);
@@ -1051,8 +1077,8 @@ int64_t or_locate(const or_problem* prob, const double p[3], const double k[3], 
   Problem P = make_problem(*prob);
   Box b;
   int64_t c;
-  if (P.grid.kind == 1) {
-    c = P.grid.octree_locate(p, V3d{k[0], k[1], k[2]}, &b);
+  if (P.grid.tree()) {
+    c = P.grid.tree_locate(p, V3d{k[0], k[1], k[2]}, &b);
   } else {
     c = P.grid.cart_locate(p);
     b = P.grid.cell_box(c);
@@ -1214,7 +1240,7 @@ int32_t or_interaction(const or_problem* prob, const double x[3], const double k
 // arguments (fewer than two wavelengths, an octree grid, t range empty).
 int32_t or_dust_temperature(const or_problem* prob, const double* lambda, const double* absorption, double scale,
                             double t_min, double t_max, double* T_out) {
-  if (!prob || !lambda || !absorption || !T_out || prob->n_lambda < 2 || prob->grid.kind == 1 ||
+  if (!prob || !lambda || !absorption || !T_out || prob->n_lambda < 2 || prob->grid.kind == 1 || prob->grid.kind == 3 ||
       !(t_min > 0 && t_max > t_min) || !(scale > 0))
     return -1;
   Problem P = make_problem(*prob);
@@ -1253,7 +1279,7 @@ int32_t or_dust_temperature(const or_problem* prob, const double* lambda, const 
 // emission): lum_out [n_lambda][n_cells] = S m_c kabs_l dlambda_l beta_l(T_c).
 int32_t or_dust_emission(const or_problem* prob, const double* lambda, const double* T, double scale,
                          double* lum_out) {
-  if (!prob || !lambda || !T || !lum_out || prob->n_lambda < 2 || prob->grid.kind == 1 || !(scale > 0)) return -1;
+  if (!prob || !lambda || !T || !lum_out || prob->n_lambda < 2 || prob->grid.kind == 1 || prob->grid.kind == 3 || !(scale > 0)) return -1;
   Problem P = make_problem(*prob);
   const int64_t nc = P.grid.n_cells();
   const std::vector<double> wts = emission_weights(P, lambda, scale);

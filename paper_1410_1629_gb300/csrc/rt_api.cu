@@ -267,6 +267,9 @@ void free_grid(rt_ctx c) {
   c->has_grid = false;
 }
 
+// Grids whose cells are (ix, iy, iz) between planes: cartesian, rectilinear.
+bool indexed_cells(int kind) { return kind == RT_GRID_CARTESIAN || kind == RT_GRID_RECTILINEAR; }
+
 // The grid axis (and direction) a frame looks along exactly, or false.
 bool frame_axis(const DevInstr& I, int& axis, int& dir) {
   int n = 0;
@@ -365,7 +368,7 @@ rt_status upload_tables(rt_ctx c, cudaStream_t s) {
     I.channels = d.channels;
     I.image = c->instr[q].d_image;
     int axis = 0, dir = 0;
-    if (c->grid_kind != RT_GRID_OCTREE && frame_axis(I, axis, dir)) {
+    if (indexed_cells(c->grid_kind) && frame_axis(I, axis, dir)) {
       const int k = 2 * axis + (dir > 0 ? 1 : 0);
       if (!c->d_columns[k]) RT_CUDA(c, pool_alloc(c, &c->d_columns[k], (size_t)c->n_cells * sizeof(float)));
       I.column = c->d_columns[k];
@@ -633,32 +636,47 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
       }
     }
   } else if (d->kind == RT_GRID_CARTESIAN) {
-  } else if (d->kind == RT_GRID_OCTREE) {
+  } else if (d->kind == RT_GRID_OCTREE || d->kind == RT_GRID_BINTREE) {
     if (!d->child || d->n_nodes <= 0 || d->n_leaves <= 0)
-      return fail(c, RT_ERR_ARG, "rt_create_grid: octree needs child[] and counts > 0");
-    if (d->n_nodes > (1ll << 31) - 1 || d->n_leaves > (1ll << 31) - 1)
-      return fail(c, RT_ERR_ARG, "rt_create_grid: octree too large for int32 indices");
+      return fail(c, RT_ERR_ARG, "rt_create_grid: a tree needs child[] and counts > 0");
+    if (d->kind == RT_GRID_BINTREE && !d->split_axis)
+      return fail(c, RT_ERR_ARG, "rt_create_grid: a k-d tree needs split_axis[]");
+    const long long limit = d->kind == RT_GRID_BINTREE ? (1ll << 29) - 2 : (1ll << 31) - 1;
+    if (d->n_nodes > limit || d->n_leaves > (1ll << 31) - 1)
+      return fail(c, RT_ERR_ARG, "rt_create_grid: tree too large for int32 indices");
     n_cells = d->n_leaves;
     n_nodes = d->n_nodes;
   } else {
     return fail(c, RT_ERR_ARG, "rt_create_grid: unknown grid kind %d", d->kind);
   }
   std::vector<int32_t> child_host;
-  if (d->kind == RT_GRID_OCTREE) {
-    // validate the tree on the host: every child block in range, every leaf id in range
+  if (d->kind == RT_GRID_OCTREE || d->kind == RT_GRID_BINTREE) {
+    // validate the tree on the host: every child block in range (after its
+    // parent), every leaf id in range, k-d tree split axes 0..2; k-d tree
+    // nodes go to the device as (first child << 2) | axis
+    const bool bin = d->kind == RT_GRID_BINTREE;
+    const long long kids = bin ? 2 : 8;
     child_host.resize((size_t)n_nodes);
+    std::vector<int8_t> axis_host(bin ? (size_t)n_nodes : 0);
     if (d->on_device) {
       if (set_device(c) != RT_OK) return RT_ERR_CUDA;
       RT_CUDA(c, cudaMemcpy(child_host.data(), d->child, n_nodes * sizeof(int32_t), cudaMemcpyDeviceToHost));
+      if (bin) RT_CUDA(c, cudaMemcpy(axis_host.data(), d->split_axis, (size_t)n_nodes, cudaMemcpyDeviceToHost));
     } else {
       std::memcpy(child_host.data(), d->child, n_nodes * sizeof(int32_t));
+      if (bin) std::memcpy(axis_host.data(), d->split_axis, (size_t)n_nodes);
     }
     for (long long i = 0; i < n_nodes; ++i) {
       const long long v = child_host[i];
-      if (v >= 0 && (v == 0 || v + 8 > n_nodes))
+      if (v >= 0 && (v <= i || v + kids > n_nodes))
         return fail(c, RT_ERR_ARG, "rt_create_grid: node %lld has child block %lld out of range", i, v);
       if (v < 0 && (-v - 1) >= n_cells)
         return fail(c, RT_ERR_ARG, "rt_create_grid: node %lld has leaf id %lld out of range", i, -v - 1);
+      if (bin && v >= 0) {
+        if (axis_host[(size_t)i] < 0 || axis_host[(size_t)i] > 2)
+          return fail(c, RT_ERR_ARG, "rt_create_grid: node %lld has split axis %d", i, (int)axis_host[(size_t)i]);
+        child_host[(size_t)i] = (int32_t)((v << 2) | axis_host[(size_t)i]);
+      }
     }
   }
   if (set_device(c) != RT_OK) return RT_ERR_CUDA;
@@ -671,7 +689,7 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
     RT_CUDA(c, pool_alloc(c, &c->d_edges, edges_f.size() * sizeof(float)));
     RT_CUDA(c, cudaMemcpy(c->d_edges, edges_f.data(), edges_f.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
-  if (d->kind == RT_GRID_OCTREE) {
+  if (d->kind == RT_GRID_OCTREE || d->kind == RT_GRID_BINTREE) {
     RT_CUDA(c, pool_alloc(c, &c->d_child, (size_t)n_nodes * sizeof(int32_t)));
     RT_CUDA(c, cudaMemcpy(c->d_child, child_host.data(), (size_t)n_nodes * sizeof(int32_t), cudaMemcpyHostToDevice));
   }
@@ -679,13 +697,13 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
   c->nx = d->nx; c->ny = d->ny; c->nz = d->nz;
   c->stride[0] = 1; c->stride[1] = d->nx; c->stride[2] = d->nx * d->ny;
   c->permuted = false;
-  if (d->kind != RT_GRID_OCTREE && d->layout != RT_LAYOUT_ROW_MAJOR) {
+  if (indexed_cells(d->kind) && d->layout != RT_LAYOUT_ROW_MAJOR) {
     const int n3[3] = {d->nx, d->ny, d->nz};
     const double ext[3] = {d->bounds[1] - d->bounds[0], d->bounds[3] - d->bounds[2], d->bounds[5] - d->bounds[4]};
     crossing_order_strides(n3, ext, c->stride);
     c->permuted = !(c->stride[0] == 1 && c->stride[1] == d->nx);
   }
-  if (d->kind != RT_GRID_OCTREE) {
+  if (indexed_cells(d->kind)) {
     // FP64 planes: cartesian lo + i (hi - lo) / n, rectilinear the edges
     std::vector<double> planes;
     const int n3[3] = {d->nx, d->ny, d->nz};
@@ -1002,7 +1020,7 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   p.dust_cum = dust ? c->d_dust_cum : nullptr;
   p.profile = reinterpret_cast<unsigned long long*>(o.profile);
   p.flags = c->d_flags;
-  p.use_columns = c->grid_kind != RT_GRID_OCTREE && !o.walk_peels;
+  p.use_columns = indexed_cells(c->grid_kind) && !o.walk_peels;
   cudaEvent_t* ev = nullptr;
   if (o.time_parts) {
     for (auto& e : c->part_ev)
@@ -1277,7 +1295,8 @@ rt_status rt_tune(rt_ctx c, uint64_t n_per_lambda, uint64_t seed, const rt_launc
   // (0), one and two fewer
   int best_blocks = 0;
   o.control_lanes = best_lanes;
-  const int max_blocks = c->grid_kind == RT_GRID_OCTREE ? 3 : 4;
+  // the kernels' launch bounds
+  const int max_blocks = (c->grid_kind == RT_GRID_OCTREE || c->grid_kind == RT_GRID_BINTREE) ? 3 : 4;
   for (int blocks = max_blocks - 1; st == RT_OK && blocks >= max_blocks - 2 && blocks >= 1; --blocks) {
     o.blocks_per_sm = blocks;
     cudaError_t e = cudaEventRecord(e0, s);
@@ -1410,7 +1429,7 @@ namespace {
 // logarithmic scale: inner borders at geometric means, outer ones mirrored).
 rt_status dust_setup(rt_ctx c, const char* who, double scale, std::vector<double>& w) {
   if (!c->has_grid || c->n_lambda == 0) return fail(c, RT_ERR_STATE, "%s: grid and optics required", who);
-  if (c->grid_kind == RT_GRID_OCTREE) return fail(c, RT_ERR_ARG, "%s: cartesian or rectilinear grids only", who);
+  if (!indexed_cells(c->grid_kind)) return fail(c, RT_ERR_ARG, "%s: cartesian or rectilinear grids only", who);
   if (c->n_lambda < 2 || (int)c->lambda_um.size() != c->n_lambda)
     return fail(c, RT_ERR_STATE, "%s: rt_set_optics needs the wavelengths (at least two, in um)", who);
   for (int l = 0; l < c->n_lambda; ++l)

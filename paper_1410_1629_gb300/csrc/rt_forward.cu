@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(tr::kBlock, RT_TAPE_MIN_BLOCKS) k_forward_cart
 cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaStream_t stream) {
   if (grid_kind == RT_GRID_OCTREE) return launch_forward_octree(p, num_sms, stream);
   if (grid_kind == RT_GRID_RECTILINEAR) return launch_forward_rect(p, num_sms, stream);
+  if (grid_kind == RT_GRID_BINTREE) return launch_forward_bintree(p, num_sms, stream);
   cudaError_t e = cudaMemsetAsync(p.work_counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
   int per_sm = 0;

@@ -76,7 +76,7 @@ struct FwdParams {
   int pad0;
   float lo[3], hi[3], d[3], inv_d[3];
   const float* density;
-  const int32_t* child;  // octree only
+  const int32_t* child;  // octree: child[] as given; k-d tree: node words (first child << 2 | axis, or -(leaf + 1))
   long long n_nodes;     // octree only
   const float* edge[3];  // rectilinear only: cell edges per axis, n + 1 each
   // storage strides of the cell index (cartesian and rectilinear grids): the
@@ -209,6 +209,7 @@ cudaError_t launch_columns(const float* density, int nx, int ny, int nz, int axi
                            const double* planes, float* out, cudaStream_t stream);
 cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t stream);
 cudaError_t launch_forward_rect(const FwdParams& p, int num_sms, cudaStream_t stream);
+cudaError_t launch_forward_bintree(const FwdParams& p, int num_sms, cudaStream_t stream);
 // The sorted peel-off pass after a forward launch with p.peel set
 // (rt_forward.cu): scan of p.peel_hist (n_keys entries, tile totals in
 // tile_sum: (n_keys + 4095) / 4096 entries), the permutation that orders the

@@ -638,6 +638,137 @@ struct OctGrid {
   }
 };
 
+// ---------------------------------------------------------------- k-d tree grid
+// A node halves its box at the midpoint of one axis (Table 1(d): BinTree).
+// Device node word: (first child << 2) | split axis for an inner node (the
+// lower child first, the upper one next), -(leaf + 1) for a leaf.  A point
+// on a splitting plane belongs to the child the ray enters, as in octrees.
+// The walk locates the next leaf from the root at the exit point of the
+// current one (the first kChildCache node words sit in shared memory).
+constexpr int kMaxBinDepth = 96;
+
+struct BinGrid {
+  static constexpr bool kColumns = false;
+  static constexpr bool kIndexCells = false;
+  static constexpr bool kSortedPass = false;
+  using Cell = OctGrid::Cell;  // the leaf and its box
+  struct Walk {
+    int leaf;
+    float t;
+    float lo[3], hi[3];
+  };
+  struct Scratch {};
+
+  __device__ static __forceinline__ int word(const FwdParams& P, int node) {
+    return node < kChildCache ? S_CHILD[node] : __ldg(&P.child[node]);
+  }
+
+  // Descend from the root to the leaf holding p (direction d breaks ties).
+  __device__ static __forceinline__ bool locate(const FwdParams& P, float3 p, float3 d, Walk& w) {
+    float lx = P.lo[0], ly = P.lo[1], lz = P.lo[2], hx = P.hi[0], hy = P.hi[1], hz = P.hi[2];
+    int node = 0;
+    for (int depth = 0; depth <= kMaxBinDepth; ++depth) {
+      const int v = word(P, node);
+      if (v < 0) {
+        w.leaf = -v - 1;
+        w.lo[0] = lx; w.lo[1] = ly; w.lo[2] = lz;
+        w.hi[0] = hx; w.hi[1] = hy; w.hi[2] = hz;
+        return true;
+      }
+      const int a = v & 3;
+      const float la = a == 0 ? lx : (a == 1 ? ly : lz), ha = a == 0 ? hx : (a == 1 ? hy : hz);
+      const float pa = a == 0 ? p.x : (a == 1 ? p.y : p.z), da = a == 0 ? d.x : (a == 1 ? d.y : d.z);
+      const float mid = 0.5f * (la + ha);
+      const bool upper = da < 0.0f ? (pa > mid) : (pa >= mid);
+      lx = (a == 0 && upper) ? mid : lx;
+      ly = (a == 1 && upper) ? mid : ly;
+      lz = (a == 2 && upper) ? mid : lz;
+      hx = (a == 0 && !upper) ? mid : hx;
+      hy = (a == 1 && !upper) ? mid : hy;
+      hz = (a == 2 && !upper) ? mid : hz;
+      node = (v >> 2) + (upper ? 1 : 0);
+    }
+    atomicOr(P.flags, kFlagOctreeDepth);
+    w.leaf = 0;
+    return false;
+  }
+
+  __device__ static __forceinline__ bool init(const FwdParams& P, float3 x, float3 d, float3 id, bool known,
+                                              const Cell& c, Walk& w, Scratch&) {
+    w.t = 0.0f;
+    if (known) {
+      // the known leaf: descend to its box centre, strictly inside every
+      // ancestor's chosen half
+      const float3 ctr = make_float3(0.5f * (c.lo[0] + c.hi[0]), 0.5f * (c.lo[1] + c.hi[1]), 0.5f * (c.lo[2] + c.hi[2]));
+      if (!locate(P, ctr, d, w)) return false;
+      if (w.leaf != c.leaf) atomicOr(P.flags, kFlagCellRange);
+      return true;
+    }
+    int entry = -1;
+    float3 p = x;
+    if (!inside_box(P, x)) {
+      const float3 ik = make_float3(id.x != 0.0f ? id.x : RT_INF, id.y != 0.0f ? id.y : RT_INF,
+                                    id.z != 0.0f ? id.z : RT_INF);
+      if (!ray_box_entry(P, x, d, ik, w.t, entry)) return false;
+      p = make_float3(fmaf(w.t, d.x, x.x), fmaf(w.t, d.y, x.y), fmaf(w.t, d.z, x.z));
+      if (entry == 0) p.x = d.x > 0.0f ? P.lo[0] : P.hi[0];
+      if (entry == 1) p.y = d.y > 0.0f ? P.lo[1] : P.hi[1];
+      if (entry == 2) p.z = d.z > 0.0f ? P.lo[2] : P.hi[2];
+    }
+    return locate(P, p, d, w);
+  }
+
+  __device__ static __forceinline__ float exit(const Walk& w, float3 x, float3 id, int& axis) {
+    const float tx = id.x != 0.0f ? ((id.x > 0.0f ? w.hi[0] : w.lo[0]) - x.x) * id.x : RT_INF;
+    const float ty = id.y != 0.0f ? ((id.y > 0.0f ? w.hi[1] : w.lo[1]) - x.y) * id.y : RT_INF;
+    const float tz = id.z != 0.0f ? ((id.z > 0.0f ? w.hi[2] : w.lo[2]) - x.z) * id.z : RT_INF;
+    return first_min(tx, ty, tz, axis);
+  }
+
+  // Into the neighbouring leaf through face `axis`: the exit point with the
+  // other coordinates kept inside the current leaf (the walk never steps
+  // back across a face), located from the root.
+  __device__ static __forceinline__ bool advance(const FwdParams& P, float3 x, float3 d, float3, int axis, Walk& w,
+                                                 Scratch&) {
+    const float da = pick(axis, d);
+    const float plane = da > 0.0f ? (axis == 0 ? w.hi[0] : (axis == 1 ? w.hi[1] : w.hi[2]))
+                                  : (axis == 0 ? w.lo[0] : (axis == 1 ? w.lo[1] : w.lo[2]));
+    const float dom_lo = axis == 0 ? P.lo[0] : (axis == 1 ? P.lo[1] : P.lo[2]);
+    const float dom_hi = axis == 0 ? P.hi[0] : (axis == 1 ? P.hi[1] : P.hi[2]);
+    if ((da > 0.0f && plane >= dom_hi) || (da < 0.0f && plane <= dom_lo)) return false;
+    float3 p = make_float3(fminf(fmaxf(fmaf(w.t, d.x, x.x), w.lo[0]), w.hi[0]),
+                           fminf(fmaxf(fmaf(w.t, d.y, x.y), w.lo[1]), w.hi[1]),
+                           fminf(fmaxf(fmaf(w.t, d.z, x.z), w.lo[2]), w.hi[2]));
+    if (axis == 0) p.x = plane; else if (axis == 1) p.y = plane; else p.z = plane;
+    const int old = w.leaf;
+    const float t = w.t;
+    if (!locate(P, p, d, w)) return false;
+    w.t = t;
+    if (w.leaf == old) {  // the exit point cannot lie in the leaf it leaves
+      atomicOr(P.flags, kFlagWalkSteps);
+      return false;
+    }
+    return true;
+  }
+
+  __device__ static __forceinline__ int cell(const Walk& w) { return w.leaf; }
+  __device__ static __forceinline__ int id(const FwdParams&, const Walk& w) { return w.leaf; }
+
+  __device__ static __forceinline__ Cell carried(const Walk& w) {
+    Cell c;
+    c.leaf = w.leaf;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { c.lo[a] = w.lo[a]; c.hi[a] = w.hi[a]; }
+    return c;
+  }
+
+  __device__ static __forceinline__ void clamp(const FwdParams&, const Cell& c, float3& x) {
+    x.x = fminf(fmaxf(x.x, c.lo[0]), c.hi[0]);
+    x.y = fminf(fmaxf(x.y, c.lo[1]), c.hi[1]);
+    x.z = fminf(fmaxf(x.z, c.lo[2]), c.hi[2]);
+  }
+};
+
 // ---------------------------------------------------------------- lane state
 // The lane state that only the per-event work touches lives in per-thread
 // slots of shared memory (structure of arrays: the lanes of a warp hit
@@ -664,6 +795,8 @@ template <>
 __device__ __forceinline__ OctGrid::Cell& cell_slot<OctGrid>() { return S_CELL_OCT[threadIdx.x]; }
 template <>
 __device__ __forceinline__ RectGrid::Cell& cell_slot<RectGrid>() { return S_CELL_CART[threadIdx.x]; }
+template <>
+__device__ __forceinline__ BinGrid::Cell& cell_slot<BinGrid>() { return S_CELL_OCT[threadIdx.x]; }
 
 template <class G>
 struct Lane {
@@ -1343,6 +1476,8 @@ __device__ __forceinline__ CartGrid::Scratch lane_scratch<CartGrid>() { return C
 template <>
 __device__ __forceinline__ RectGrid::Scratch lane_scratch<RectGrid>() { return RectGrid::Scratch{}; }
 template <>
+__device__ __forceinline__ BinGrid::Scratch lane_scratch<BinGrid>() { return BinGrid::Scratch{}; }
+template <>
 __device__ __forceinline__ OctGrid::Scratch lane_scratch<OctGrid>() {
   return OctGrid::Scratch{&S_STACK[threadIdx.x * kOctStack]};
 }
@@ -1353,6 +1488,11 @@ template <>
 __device__ __forceinline__ void load_grid_cache<CartGrid>(const FwdParams&) {}
 template <>
 __device__ __forceinline__ void load_grid_cache<RectGrid>(const FwdParams&) {}
+template <>
+__device__ __forceinline__ void load_grid_cache<BinGrid>(const FwdParams& P) {
+  const int n = P.n_nodes < kChildCache ? (int)P.n_nodes : kChildCache;
+  for (int i = threadIdx.x; i < n; i += kBlock) S_CHILD[i] = P.child[i];
+}
 template <>
 __device__ __forceinline__ void load_grid_cache<OctGrid>(const FwdParams& P) {
   const int n = P.n_nodes < kChildCache ? (int)P.n_nodes : kChildCache;

@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build
 
 RT_OK, RT_ERR_ARG, RT_ERR_STATE, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_DEVICE_FLAG = 0, -1, -2, -3, -4, -5, -6
-RT_GRID_CARTESIAN, RT_GRID_OCTREE, RT_GRID_RECTILINEAR = 0, 1, 2
+RT_GRID_CARTESIAN, RT_GRID_OCTREE, RT_GRID_RECTILINEAR, RT_GRID_BINTREE = 0, 1, 2, 3
 RT_SOURCE_POINT, RT_SOURCE_EXPDISK, RT_SOURCE_PLUMMER = 0, 1, 2
 RT_DEPOSIT_NEAREST, RT_DEPOSIT_BILINEAR, RT_DEPOSIT_SED = 0, 1, 2
 RT_LAYOUT_AUTO, RT_LAYOUT_ROW_MAJOR = 0, 1
@@ -41,7 +41,7 @@ class rt_grid_desc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("bounds", ctypes.c_double * 6), ("density", ctypes.c_void_p), ("n_nodes", ctypes.c_int64),
                 ("child", ctypes.c_void_p), ("n_leaves", ctypes.c_int64), ("on_device", ctypes.c_int32),
-                ("layout", ctypes.c_int32), ("edges", ctypes.c_void_p * 3)]
+                ("layout", ctypes.c_int32), ("edges", ctypes.c_void_p * 3), ("split_axis", ctypes.c_void_p)]
 
 
 class rt_source_desc(ctypes.Structure):
@@ -469,12 +469,16 @@ def grid_desc(grid, on_device_arrays=None):
                 keep.append(e)
                 d.edges[a] = e.ctypes.data
     else:
-        d.kind = RT_GRID_OCTREE
+        d.kind = RT_GRID_OCTREE if grid.kind == "octree" else RT_GRID_BINTREE
         child = np.ascontiguousarray(grid.child, dtype=np.int32)
         keep.append(child)
         d.child = child.ctypes.data
         d.n_nodes = child.size
         d.n_leaves = dens.size
+        if grid.kind == "bintree":
+            axis = np.ascontiguousarray(grid.split_axis, dtype=np.int8)
+            keep.append(axis)
+            d.split_axis = axis.ctypes.data
     return d, keep
 
 

@@ -34,14 +34,18 @@ import numpy as np
 class Grid:
     """Dust grid.  ``kind`` is ``"cartesian"`` (density float32 [nz, ny, nx],
     x fastest), ``"rectilinear"`` (the same with cell edges per axis in
-    ``edges``: three float64 arrays of n + 1 increasing values) or
+    ``edges``: three float64 arrays of n + 1 increasing values),
     ``"octree"`` (``child`` int32 per node: index of the first of eight
-    children, or -(leaf + 1) for a leaf; density float32 per leaf)."""
+    children, or -(leaf + 1) for a leaf; density float32 per leaf) or
+    ``"bintree"`` (a k-d tree: ``child`` as for octrees but with two
+    children, lower then upper half of the node's box split at its midpoint
+    along ``split_axis`` int8 per node)."""
     kind: str
     bounds: np.ndarray  # float64 [xmin, xmax, ymin, ymax, zmin, zmax]
     density: np.ndarray
     child: Optional[np.ndarray] = None
     edges: Optional[list] = None
+    split_axis: Optional[np.ndarray] = None  # k-d tree ("bintree"): split axis per node
 
     @property
     def n_cells(self) -> int:
@@ -490,6 +494,53 @@ def build_octree(bounds, refine, leaf_value, max_level):
     return g, llo, lhi
 
 
+def build_bintree(bounds, refine, leaf_value, max_depth, axis_of=None):
+    """k-d tree by recursive halving of boxes (Table 1(d): BinTree), built
+    level by level.  ``axis_of(lo, hi, depth) -> int[N]`` gives the split
+    axis of each node (default: the axes in turn, z, y, x, z, ..., i.e. the
+    order of the bits of a Morton key from the top); ``refine`` and
+    ``leaf_value`` as for :func:`build_octree`.  Returns (Grid, leaf lo,
+    leaf hi)."""
+    b = np.asarray(bounds, dtype=np.float64)
+    lo = b[[0, 2, 4]][None, :].copy()
+    hi = b[[1, 3, 5]][None, :].copy()
+    child_parts, axis_parts, leaf_lo, leaf_hi = [], [], [], []
+    n_before = 0
+    n_leaves = 0
+    depth = 0
+    while lo.shape[0]:
+        n = lo.shape[0]
+        split = np.zeros(n, dtype=bool) if depth >= max_depth else np.asarray(refine(lo, hi, depth), dtype=bool)
+        axis = (np.full(n, 2 - depth % 3) if axis_of is None else np.asarray(axis_of(lo, hi, depth))).astype(np.int8)
+        child = np.empty(n, dtype=np.int64)
+        n_split = int(split.sum())
+        child[split] = n_before + n + 2 * np.arange(n_split)
+        child[~split] = -(n_leaves + np.arange(n - n_split) + 1)
+        n_leaves += n - n_split
+        child_parts.append(child)
+        axis_parts.append(np.where(split, axis, 0).astype(np.int8))
+        leaf_lo.append(lo[~split])
+        leaf_hi.append(hi[~split])
+        plo, phi, pax = lo[split], hi[split], axis[split].astype(np.int64)
+        mid = 0.5 * (plo[np.arange(n_split), pax] + phi[np.arange(n_split), pax])
+        clo = np.repeat(plo, 2, axis=0)
+        chi = np.repeat(phi, 2, axis=0)
+        rows = np.arange(n_split)
+        chi[2 * rows, pax] = mid       # lower child
+        clo[2 * rows + 1, pax] = mid   # upper child
+        n_before += n
+        lo, hi = clo, chi
+        depth += 1
+    child = np.concatenate(child_parts)
+    if child.max(initial=0) > np.iinfo(np.int32).max or n_leaves > np.iinfo(np.int32).max:
+        raise ValueError("k-d tree too large for int32 node indices")
+    llo, lhi = np.concatenate(leaf_lo), np.concatenate(leaf_hi)
+    dens = np.asarray(leaf_value(llo, lhi), dtype=np.float32)
+    g = Grid("bintree", _f64(bounds), np.ascontiguousarray(dens), child.astype(np.int32),
+             split_axis=np.concatenate(axis_parts))
+    return g, llo, lhi
+
+
 def octree_problem_like(problem: Problem, grid: Grid) -> Problem:
     return replace(problem, grid=grid)
 
@@ -504,22 +555,12 @@ def _spread3(v):
     return v
 
 
-def clumpy_octree(n_particles=1_000_000, n_samples=100_000_000, target_leaves=5_000_000, max_level=10, seed=3,
-                  n_lambda=20, n_pix=1024, n_packets_total=200_000_000, half=20.0, chunk=10_000_000, channels=1):
-    """Clumpy dust on an adaptive octree (Sect. 2.4).
-
-    ``n_particles`` Gaussian clumps: centres drawn from a double-exponential
-    dust disk (h_R = 6 kpc, h_z = 0.2 kpc), widths log-uniform in 20-200 pc,
-    masses log-normal (sigma_ln = 1.5), total mass 1.  The mixture is binned
-    by drawing ``n_samples`` points from it (Morton keys at ``max_level``); a
-    node is refined while its mass exceeds delta * M_tot, with delta chosen by
-    bisection so that the tree has about ``target_leaves`` leaves.  Leaf
-    density = binned mass / leaf volume.  kappa_V makes the equivalent smooth
-    disk's face-on central optical depth 0.5.  Sources: Plummer bulge
-    (a = 1 kpc, 30 %) and exponential disk (h_R = 4, h_z = 0.35 kpc, 70 %).
-    Two ``n_pix``^2 frames at inclinations 0 and 90 degrees."""
-    if max_level > 10:
-        raise ValueError("max_level <= 10 (30-bit Morton keys)")
+def _clumpy_samples(n_particles, n_samples, max_level, seed, half, chunk):
+    """Gaussian dust clumps and the Morton keys (max_level bits per axis) of
+    n_samples points drawn from their mass, sorted; the clumps' centres from
+    a double-exponential dust disk (h_R = 6, h_z = 0.2 kpc), widths
+    log-uniform in 20-200 pc, masses log-normal (sigma_ln = 1.5), total 1.
+    Returns (keys, kept): samples outside the box are dropped."""
     rng = np.random.default_rng(seed)
     R = rng.gamma(2.0, 6.0, n_particles)
     ph = rng.uniform(0.0, 2 * math.pi, n_particles)
@@ -545,15 +586,100 @@ def clumpy_octree(n_particles=1_000_000, n_samples=100_000_000, target_leaves=5_
         iz = ((pz[inside] + half) * (n_side / (2 * half))).astype(np.int64).clip(0, n_side - 1)
         keys.append((_spread3(ix) | (_spread3(iy) << np.uint64(1)) | (_spread3(iz) << np.uint64(2))).astype(np.uint32))
         kept += int(inside.sum())
-    keys = np.sort(np.concatenate(keys))
+    return np.sort(np.concatenate(keys)), kept
+
+
+def _prefix_counts(keys, n_bits, depths):
+    """Sample counts per key prefix: for each depth d the distinct values of
+    keys >> (n_bits - d) and their counts (runs of the sorted keys)."""
+    out_k, out_c = [], []
+    for d in depths:
+        k = keys >> np.uint32(n_bits - d)
+        starts = np.flatnonzero(np.concatenate(([True], k[1:] != k[:-1])))
+        out_k.append(k[starts])
+        out_c.append(np.diff(np.append(starts, len(k))))
+    return out_k, out_c
+
+
+def clumpy_bintree(n_particles=20_000, n_samples=400_000, target_leaves=20_000, max_level=7, seed=3, n_lambda=4,
+                   n_pix=64, n_packets_total=80_000, half=20.0, chunk=10_000_000, channels=1):
+    """The clumpy medium of :func:`clumpy_octree` on a k-d tree (Table 1(d):
+    BinTree): nodes halved along z, y, x in turn (the bits of a Morton key
+    from the top), refined while their sampled mass exceeds delta M_tot, up
+    to 3 max_level splits; delta chosen by bisection for about
+    ``target_leaves`` leaves."""
+    keys, kept = _clumpy_samples(n_particles, n_samples, max_level, seed, half, chunk)
+    n_bits = 3 * max_level
+    weight = 1.0 / n_samples
+    lk, lc = _prefix_counts(keys, n_bits, range(n_bits + 1))
+
+    def n_leaves(thr):
+        return 1 + sum(int((lc[d] > thr).sum()) for d in range(n_bits))
+    lo_t, hi_t = 0.0, float(lc[0].max())
+    for _ in range(60):
+        mid = 0.5 * (lo_t + hi_t)
+        if n_leaves(mid) > target_leaves:
+            lo_t = mid
+        else:
+            hi_t = mid
+    thr = hi_t
+    n_side = 1 << max_level
+
+    def count_of(lo, depth):
+        cell = np.rint((lo + half) / (2 * half) * n_side).astype(np.int64)
+        full = _spread3(cell[:, 0]) | (_spread3(cell[:, 1]) << np.uint64(1)) | (_spread3(cell[:, 2]) << np.uint64(2))
+        k = (full >> np.uint64(n_bits - depth)).astype(np.uint32)
+        u, c = lk[depth], lc[depth]
+        pos = np.searchsorted(u, k)
+        pos_c = np.minimum(pos, len(u) - 1)
+        return np.where((pos < len(u)) & (u[pos_c] == k), c[pos_c], 0)
+
+    def leaf_value(lo, hi):
+        vol = np.prod(hi - lo, axis=1)
+        depth = np.rint(np.log2((2 * half) ** 3 / vol)).astype(np.int64)
+        out = np.zeros(len(lo))
+        for d in np.unique(depth):
+            sel = depth == d
+            out[sel] = count_of(lo[sel], int(d)) * weight / vol[sel]
+        return out
+
+    grid, _, _ = build_bintree([-half, half] * 3, lambda lo, hi, d: count_of(lo, d) > thr, leaf_value, n_bits)
+    wl = np.geomspace(0.15, 2.2, n_lambda)
+    kappa, albedo, g = synthetic_optics(wl, 0.5 * 2 * math.pi * 6.0 ** 2)
+    instr = [Instrument(math.radians(inc), -math.pi / 2, 0.0, n_pix, n_pix, half, half, channels=channels)
+             for inc in (0.0, 90.0)]
+    return Problem(
+        name=f"clumpy_bintree_{grid.n_cells}",
+        grid=grid, wavelengths=wl, kappa=kappa, albedo=albedo, g=g,
+        sources=[Source("plummer", (0.0, 0.0, 0.0), np.full(n_lambda, 0.3), scale_r=1.0),
+                 Source("expdisk", (0.0, 0.0, 0.0), np.full(n_lambda, 0.7), scale_r=4.0, scale_z=0.35)],
+        instruments=instr,
+        run=Run(n_per_lambda=max(1, int(n_packets_total) // n_lambda)),
+        meta={"delta": thr * weight, "leaves": grid.n_cells, "nodes": int(grid.child.size),
+              "samples_inside": kept, "seed": seed},
+    )
+
+
+def clumpy_octree(n_particles=1_000_000, n_samples=100_000_000, target_leaves=5_000_000, max_level=10, seed=3,
+                  n_lambda=20, n_pix=1024, n_packets_total=200_000_000, half=20.0, chunk=10_000_000, channels=1):
+    """Clumpy dust on an adaptive octree (Sect. 2.4).
+
+    ``n_particles`` Gaussian clumps: centres drawn from a double-exponential
+    dust disk (h_R = 6 kpc, h_z = 0.2 kpc), widths log-uniform in 20-200 pc,
+    masses log-normal (sigma_ln = 1.5), total mass 1.  The mixture is binned
+    by drawing ``n_samples`` points from it (Morton keys at ``max_level``); a
+    node is refined while its mass exceeds delta * M_tot, with delta chosen by
+    bisection so that the tree has about ``target_leaves`` leaves.  Leaf
+    density = binned mass / leaf volume.  kappa_V makes the equivalent smooth
+    disk's face-on central optical depth 0.5.  Sources: Plummer bulge
+    (a = 1 kpc, 30 %) and exponential disk (h_R = 4, h_z = 0.35 kpc, 70 %).
+    Two ``n_pix``^2 frames at inclinations 0 and 90 degrees."""
+    if max_level > 10:
+        raise ValueError("max_level <= 10 (30-bit Morton keys)")
+    keys, kept = _clumpy_samples(n_particles, n_samples, max_level, seed, half, chunk)
     weight = 1.0 / n_samples  # mass per sample (M_tot = 1, outside samples dropped)
     # sample counts per node at every level
-    level_keys, level_counts = [], []
-    for L in range(max_level + 1):
-        k = keys >> np.uint32(3 * (max_level - L))  # still sorted: runs of equal keys
-        starts = np.flatnonzero(np.concatenate(([True], k[1:] != k[:-1])))
-        level_keys.append(k[starts])
-        level_counts.append(np.diff(np.append(starts, len(k))))
+    level_keys, level_counts = _prefix_counts(keys, 3 * max_level, [3 * L for L in range(max_level + 1)])
     # threshold in samples: leaves = 1 + 7 * (#nodes above threshold at levels < max_level)
     def n_leaves(thr):
         return 1 + 7 * sum(int((level_counts[L] > thr).sum()) for L in range(max_level))

@@ -150,9 +150,9 @@ def block_sum(a, b):
 
 def cell_groups(grid, block=4, level=None):
     """Group id of every cell for coarser absorption bins: cartesian and
-    rectilinear grids in block^3 cubes of cells; octrees by the leaf's
-    ancestor at depth `level` (the parent node when level is None; a leaf
-    shallower than `level` is its own group)."""
+    rectilinear grids in block^3 cubes of cells; trees (octree, k-d tree) by
+    the leaf's ancestor at depth `level` (the parent node when level is
+    None; a leaf shallower than `level` is its own group)."""
     if grid.kind in ("cartesian", "rectilinear"):
         nx, ny, nz = grid.shape
         iz, iy, ix = np.meshgrid(np.arange(nz) // block, np.arange(ny) // block, np.arange(nx) // block,
@@ -160,15 +160,16 @@ def cell_groups(grid, block=4, level=None):
         gx, gy = (nx + block - 1) // block, (ny + block - 1) // block
         return (ix + gx * (iy + gy * iz)).reshape(-1)
     child = np.asarray(grid.child, dtype=np.int64)
+    kids = 2 if grid.kind == "bintree" else 8
     n = len(child)
     parent = np.full(n, -1, dtype=np.int64)
     depth = np.zeros(n, dtype=np.int64)
     # children follow their parents in the node array: one pass in order
     inner = np.flatnonzero(child >= 0)
-    for o in range(8):
+    for o in range(kids):
         parent[child[inner] + o] = inner
     for node in inner:  # depths, parents first
-        depth[child[node]:child[node] + 8] = depth[node] + 1
+        depth[child[node]:child[node] + kids] = depth[node] + 1
     leaves = np.flatnonzero(child < 0)
     anc = leaves.copy() if level is not None else parent[leaves].clip(0)
     if level is not None:

@@ -106,3 +106,27 @@ def test_powcub_column_sums_equal_walked_peel_offs():
     np.testing.assert_allclose(summed["absorption"], walked["absorption"], rtol=1e-12, atol=1e-30)
     for a, b in zip(summed["images"], walked["images"]):
         np.testing.assert_allclose(a, b, rtol=2e-5, atol=1e-12 * b.max())
+
+
+@pytest.mark.parametrize("case", ["random_axes", "clumpy"])
+def test_bintree_parity(case):
+    """k-d tree grids (Table 1(d): BinTree): a random tree with random split
+    axes under a uniform-cube problem, and the clumpy medium refined by mass
+    with the axes in turn (~2e4 leaves, Plummer bulge + exponential disk,
+    four wavelengths, two frames), against the oracle."""
+    if case == "random_axes":
+        rng = np.random.default_rng(11)
+        grid, _, _ = W.build_bintree([-1, 1] * 3, lambda lo, hi, d: rng.uniform(size=len(lo)) < (0.95 if d < 3 else 0.7),
+                                     lambda lo, hi: rng.lognormal(0.0, 1.0, len(lo)), 12,
+                                     axis_of=lambda lo, hi, d: rng.integers(0, 3, len(lo)))
+        prob = W.replace(W.uniform_cube(axis_tau=2.0, channels=3), grid=grid)
+        n = 50000
+    else:
+        prob = W.clumpy_bintree(channels=3)
+        n = prob.run.n_per_lambda
+    g = PAR.gpu_run(prob, n, records_cap=8_000_000)
+    o = PAR.oracle_run(prob, n, records_cap=8_000_000)
+    assert g["raw_stats"]["device_flags"] == 0
+    rep = PAR.compare(g, o, prob, groups=PAR.cell_groups(prob.grid))
+    _assert_ok(rep)
+    assert rep["crossings_rel"] < 1e-4

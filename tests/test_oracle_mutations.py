@@ -68,6 +68,9 @@ MUTATIONS = {
     "dust_cell_uniform": ("const int64_t cell = std::min<int64_t>(c, (int64_t)cum.size() - 1);",
                           "const int64_t cell = std::min<int64_t>((int64_t)(u[0] * cum.size()), (int64_t)cum.size() - 1); (void)c;",
                           "test_oracle_panchromatic.py"),
+    # k-d tree children taken in the wrong order
+    "bintree_child_order": ("node = child[node] + (upper ? 1 : 0);", "node = child[node] + (upper ? 0 : 1);",
+                            "test_oracle_bintree.py"),
     # derivative of exp with the wrong sign
     "dual_exp_sign": ("inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, e * a.d}; }",
                       "inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, -e * a.d}; }",
