@@ -262,6 +262,7 @@ def workload_rate(prob, device, stream, flush, warmup, timed, tune_fraction=0.05
     sim = rt.Simulation(prob, device=device)
     try:
         lanes = sim.tune(max(1, int(n * tune_fraction)), seed=prob.run.seed + 1, stream=stream.cuda_stream)
+        blocks_per_sm = sim.tuned()[1]
         times, parts = [], []
         for i in range(warmup + timed):
             with torch.cuda.stream(stream):
@@ -291,7 +292,8 @@ def workload_rate(prob, device, stream, flush, warmup, timed, tune_fraction=0.05
     out = {"packets": int(packets), "seconds_per_launch": t, "packets_per_s": packets / t,
            "crossings_per_s": st["crossings"] / t,
            "walked_crossings_per_s": (st["crossings"] - st["column_crossings"]) / t,
-           "timed_launches": len(times), "tuned": {"control_lanes": lanes},
+           "timed_launches": len(times),
+           "tuned": {"control_lanes": lanes, "blocks_per_sm": blocks_per_sm or "as many as fit"},
            "kernel_ms": kern_ms, "peel_walks_ms": walks_ms,
            "conservation_rel": abs(st["emitted"] - st["escaped"] - st["absorbed"] - st["truncated"]) / st["emitted"],
            "device_flags": int(st["device_flags"]), "l2": "flushed before each timed launch (256 MiB write)"}
@@ -630,6 +632,7 @@ def run_gpu(args, prob, world, rank, local_rank):
     # set-up: the per-event deferral threshold, timed on a 5 % sample with
     # another seed (the tallies are zeroed afterwards)
     lanes = sim.tune(max(1, n // 20), seed=prob.run.seed + 1, stream=stream.cuda_stream)
+    blocks_per_sm = sim.tuned()[1]
 
     def step(ev0, ev1):
         with torch.cuda.stream(stream):
@@ -808,7 +811,8 @@ def run_gpu(args, prob, world, rank, local_rank):
                              "whole_launch": {"ms": 1e3 * mean_launch, "algorithmic_bytes": int(bytes_launch),
                                               "GB_per_s": bytes_launch / mean_launch / 1e9}},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_step * args.steps, "adjoint": adjoint,
-                "tuned": {"control_lanes": lanes, "sample": "5 % of the packets, another seed, before the warm-up"},
+                "tuned": {"control_lanes": lanes, "blocks_per_sm": blocks_per_sm or "as many as fit",
+                          "sample": "5 % of the packets, another seed, before the warm-up"},
                 "batch": batch, "octree": octree, "spiral_example": spiral, "plain_cube": plain,
                 "panchromatic": panchro, "l2_peak": l2,
                 "clocks": clk,

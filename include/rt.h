@@ -308,6 +308,12 @@ rt_status rt_launch_packets(rt_ctx ctx, uint64_t n_per_lambda, uint64_t first_pa
 rt_status rt_tune(rt_ctx ctx, uint64_t n_per_lambda, uint64_t seed, const rt_launch_opts* opts,
                   int32_t* control_lanes, void* stream);
 
+/* The launch shape that launches with 0 in opts->control_lanes and
+ * opts->blocks_per_sm use: the values rt_tune kept (before any rt_tune: 16
+ * lanes and 0, i.e. as many resident blocks as fit).  Either pointer may be
+ * NULL.  Errors: RT_ERR_ARG (ctx NULL). */
+rt_status rt_tuned(rt_ctx ctx, int32_t* control_lanes, int32_t* blocks_per_sm);
+
 /* The same for rt_adjoint: times rt_adjoint with these adjoint inputs (into
  * a scratch gradient the context owns) for 12, 16, ..., 32 lanes and keeps
  * the fastest for rt_adjoint calls with control_lanes 0.  Synchronous.

@@ -1324,6 +1324,14 @@ rt_status rt_tune(rt_ctx c, uint64_t n_per_lambda, uint64_t seed, const rt_launc
   return rt_reset_tallies(c, stream);
 }
 
+rt_status rt_tuned(rt_ctx c, int32_t* control_lanes, int32_t* blocks_per_sm) {
+  if (!c) return RT_ERR_ARG;
+  c->err.clear();
+  if (control_lanes) *control_lanes = c->control_lanes ? c->control_lanes : 16;
+  if (blocks_per_sm) *blocks_per_sm = c->blocks_per_sm;
+  return RT_OK;
+}
+
 rt_status rt_adjoint_tune(rt_ctx c, const double* const* adj_images, int32_t n_adj_images,
                           const double* adj_absorption, uint64_t n_per_lambda, uint64_t seed,
                           const rt_launch_opts* opts, int32_t* control_lanes, void* stream) {

@@ -8,10 +8,11 @@
 //   m_c = rho_c V_c, w_l = kappa_l (1 - albedo_l) dlambda_l (the host's
 //   per-wavelength weights, S folded in), beta_l(T) = lambda_l^-5 /
 //   (exp(C2 / (lambda_l T)) - 1), lambda in um, C2 = hc/k in um K.
-//   The temperature solves emission = absorbed luminosity by bisection in
-//   ln T (64 halvings of [ln t_min, ln t_max]); no absorption or no dust: 0;
-//   short of the absorption at t_max: t_max, beyond it at t_min: t_min
-//   (both counted).
+//   The temperature solves emission = absorbed luminosity in ln T between
+//   ln t_min and ln t_max (Newton steps kept in a bisection bracket: a
+//   single-precision estimate, then double precision to 1e-15); no absorption or
+//   no dust: 0; short of the absorption at t_max: t_max, beyond it at t_min:
+//   t_min (both counted).
 // All of it is FP64: it runs once per temperature update, not per crossing.
 #include "rt_internal.h"
 
@@ -27,13 +28,12 @@ struct DustArgs {
   int stride[3];          // storage strides of the absorption tallies
   const double* planes;   // FP64 cell planes: x [nx + 1], y [ny + 1], z [nz + 1]
   const float* density;   // row-major
-  double w[kMaxLambda];   // S kabs_l dlambda_l
-  double lambda[kMaxLambda];
+  double a[kMaxLambda];   // S kabs_l dlambda_l / lambda_l^5
+  double b[kMaxLambda];   // C2 / lambda_l
+  float af[kMaxLambda];   // a_l / max a_l
+  float bf[kMaxLambda];   // b_l
+  double ln_a_max;
 };
-
-__device__ __forceinline__ double planck_shape(double lambda_um, double T) {
-  return 1.0 / (pow(lambda_um, 5.0) * expm1(kC2 / (lambda_um * T)));
-}
 
 __device__ __forceinline__ double cell_mass(const DustArgs& A, long long c, int& ix, int& iy, int& iz) {
   ix = (int)(c % A.nx);
@@ -46,10 +46,41 @@ __device__ __forceinline__ double cell_mass(const DustArgs& A, long long c, int&
   return (double)A.density[c] * V;
 }
 
-__device__ __forceinline__ double emission(const DustArgs& A, double mass, double T) {
-  double sum = 0.0;
-  for (int l = 0; l < A.n_lambda; ++l) sum += A.w[l] * planck_shape(A.lambda[l], T);
-  return mass * sum;
+// Emission per unit mass at T, sum_l a_l / (exp(b_l / T) - 1), and its
+// derivative with respect to ln T; Real is double, or float with the a_l
+// scaled by 1 / max a_l (a first estimate of the root only).
+template <class Real>
+__device__ __forceinline__ Real emission(int n, const Real* a, const Real* b, Real T, Real* d_dlnT = nullptr) {
+  Real sum = 0, der = 0;
+  for (int l = 0; l < n; ++l) {
+    const Real x = b[l] / T;
+    const Real em1 = expm1(x);
+    const Real t = a[l] / em1;
+    sum += t;
+    if (d_dlnT) der += t * x * (Real(1) + Real(1) / em1);
+  }
+  if (d_dlnT) *d_dlnT = der;
+  return sum;
+}
+
+// Root of ln E(exp(u)) = target in u within [lo, hi]: Newton steps, replaced by
+// the bracket's midpoint where they leave it, until a step (or the bracket)
+// is below tol relative to max(1, |u|).
+template <class Real>
+__device__ __forceinline__ Real solve_ln_t(int n, const Real* a, const Real* b, Real target, Real lo, Real hi,
+                                           Real u, Real tol, int max_it) {
+  for (int it = 0; it < max_it; ++it) {
+    Real der;
+    const Real e = emission(n, a, b, exp(u), &der);
+    const Real f = log(e) - target;
+    if (f < Real(0)) lo = u; else hi = u;
+    const Real un = u - f * e / der;
+    const Real scale = fmax(Real(1), fabs(u));
+    if (fabs(un - u) <= tol * scale) return un;
+    u = un >= lo && un <= hi ? un : Real(0.5) * (lo + hi);
+    if (hi - lo <= tol * scale) break;
+  }
+  return u;
 }
 
 // absorbed: row-major [n_lambda][n_cells] (a caller's field) or, when
@@ -65,7 +96,7 @@ __global__ void k_dust_temperature(const DustArgs A, const double* __restrict__ 
                                   : c;
     double ab = 0.0;
     for (int l = 0; l < A.n_lambda; ++l) ab += absorbed[(size_t)l * A.n_cells + slot];
-    const double top = emission(A, m, t_max);
+    const double top = m * emission(A.n_lambda, A.a, A.b, t_max);
     if (!(ab > 0.0) || !(m > 0.0) || !(top > 0.0)) {
       T[c] = 0.0;
       continue;
@@ -75,17 +106,21 @@ __global__ void k_dust_temperature(const DustArgs A, const double* __restrict__ 
       atomicAdd(clamped, 1u);
       continue;
     }
-    if (emission(A, m, t_min) >= ab) {
+    if (m * emission(A.n_lambda, A.a, A.b, t_min) >= ab) {
       T[c] = t_min;
       atomicAdd(clamped, 1u);
       continue;
     }
-    double lo = log(t_min), hi = log(t_max);
-    for (int it = 0; it < 64; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (emission(A, m, exp(mid)) < ab) lo = mid; else hi = mid;
-    }
-    T[c] = exp(0.5 * (lo + hi));
+    // the root of ln(m E(T)) = ln(absorbed) in u = ln T: a single-precision
+    // estimate to 1e-6, then double-precision steps to 1e-15 (the root the
+    // oracle's bisection converges to)
+    const double lo = log(t_min), hi = log(t_max);
+    const double target = log(ab / m);
+    const float u32 = solve_ln_t<float>(A.n_lambda, A.af, A.bf, (float)(target - A.ln_a_max), (float)lo,
+                                        (float)hi, (float)(0.5 * (lo + hi)), 1e-6f, 60);
+    const double u0 = (double)u32 > lo && (double)u32 < hi ? (double)u32 : 0.5 * (lo + hi);
+    const double u = solve_ln_t<double>(A.n_lambda, A.a, A.b, target, lo, hi, u0, 1e-15, 200);
+    T[c] = exp(u);
   }
 }
 
@@ -97,7 +132,7 @@ __global__ void k_dust_luminosity(const DustArgs A, const double* __restrict__ T
     int ix, iy, iz;
     const double m = cell_mass(A, c, ix, iy, iz);
     const double t = T[c];
-    lum[(size_t)l * A.n_cells + c] = t > 0.0 ? m * A.w[l] * planck_shape(A.lambda[l], t) : 0.0;
+    lum[(size_t)l * A.n_cells + c] = t > 0.0 ? m * (A.a[l] / expm1(A.b[l] / t)) : 0.0;
   }
 }
 
@@ -195,9 +230,18 @@ DustArgs make_args(int n_lambda, int nx, int ny, int nz, const int stride[3], co
   for (int a = 0; a < 3; ++a) A.stride[a] = stride[a];
   A.planes = planes;
   A.density = density;
+  double a_max = 0.0;
   for (int l = 0; l < kMaxLambda; ++l) {
-    A.w[l] = l < n_lambda ? w[l] : 0.0;
-    A.lambda[l] = l < n_lambda ? lambda[l] : 1.0;
+    const double lam = l < n_lambda ? lambda[l] : 1.0;
+    A.a[l] = l < n_lambda ? w[l] / (lam * lam * lam * lam * lam) : 0.0;
+    A.b[l] = kC2 / lam;
+    a_max = A.a[l] > a_max ? A.a[l] : a_max;
+  }
+  if (!(a_max > 0.0)) a_max = 1.0;
+  A.ln_a_max = std::log(a_max);
+  for (int l = 0; l < kMaxLambda; ++l) {
+    A.af[l] = (float)(A.a[l] / a_max);
+    A.bf[l] = (float)A.b[l];
   }
   return A;
 }

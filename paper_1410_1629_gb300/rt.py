@@ -127,6 +127,7 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "rt_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(rt_launch_opts),
                                  ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
+    "rt_tuned": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "rt_read_absorption": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
                                             ctypes.c_void_p]),
     "rt_read_images": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
@@ -287,6 +288,13 @@ def rt_tune(ctx, n_per_lambda, seed=0, opts=None, stream=None) -> int:
     _check(ctx, lib().rt_tune(ctx, int(n_per_lambda), int(seed), ctypes.byref(o), ctypes.byref(lanes),
                               _stream_ptr(stream)))
     return lanes.value
+
+
+def rt_tuned(ctx):
+    """(control_lanes, blocks_per_sm) that untuned-field launches use (blocks 0: as many as fit)."""
+    lanes, blocks = ctypes.c_int32(), ctypes.c_int32()
+    _check(ctx, lib().rt_tuned(ctx, ctypes.byref(lanes), ctypes.byref(blocks)))
+    return lanes.value, blocks.value
 
 
 def rt_reset_tallies(ctx, stream=None):
@@ -704,6 +712,10 @@ class Simulation:
     def tune(self, n_per_lambda, seed=0, stream=None, **opts) -> int:
         """Choose the per-event deferral threshold on a sample launch (tallies zeroed after)."""
         return rt_tune(self.ctx, n_per_lambda, seed, self.opts(**opts), stream)
+
+    def tuned(self):
+        """(control_lanes, blocks_per_sm) chosen by tune (blocks 0: as many as fit)."""
+        return rt_tuned(self.ctx)
 
     def image_shape(self, q):
         ins = self.problem.instruments[q]
