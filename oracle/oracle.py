@@ -47,7 +47,8 @@ class OrGrid(ctypes.Structure):
                 ("nz", ctypes.c_int32), ("bounds", ctypes.c_double * 6),
                 ("density", ctypes.POINTER(ctypes.c_float)), ("n_nodes", ctypes.c_int64),
                 ("child", ctypes.POINTER(ctypes.c_int32)), ("n_leaves", ctypes.c_int64),
-                ("edges", ctypes.POINTER(ctypes.c_double) * 3), ("split_axis", ctypes.POINTER(ctypes.c_int8))]
+                ("edges", ctypes.POINTER(ctypes.c_double) * 3), ("split_axis", ctypes.POINTER(ctypes.c_int8)),
+                ("sites", ctypes.POINTER(ctypes.c_double)), ("offsets", ctypes.POINTER(ctypes.c_int64))]
 
 
 class OrSource(ctypes.Structure):
@@ -187,6 +188,17 @@ class _Marshalled:
                     e = np.ascontiguousarray(grid.edges[a], dtype=np.float64)
                     self.keep.append(e)
                     og.edges[a] = _ptr(e, ctypes.c_double)
+        elif grid.kind == "voronoi":
+            og.kind = 4
+            sites = np.ascontiguousarray(grid.sites, dtype=np.float64)
+            offsets = np.ascontiguousarray(grid.offsets, dtype=np.int64)
+            nbr = np.ascontiguousarray(grid.child, dtype=np.int32)
+            self.keep += [sites, offsets, nbr]
+            og.sites = _ptr(sites, ctypes.c_double)
+            og.offsets = _ptr(offsets, ctypes.c_int64)
+            og.child = _ptr(nbr, ctypes.c_int32)
+            og.n_nodes = nbr.size
+            og.n_leaves = dens.size
         else:
             og.kind = 1 if grid.kind == "octree" else 3
             child = np.ascontiguousarray(grid.child, dtype=np.int32)

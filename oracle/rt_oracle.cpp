@@ -20,7 +20,11 @@
 //   * Sect. 2.3: per wavelength an extinction coefficient, an albedo
 //     (scattering / extinction) and an asymmetry parameter g that fixes the
 //     phase function (taken as Henyey-Greenstein).
-//   * Sect. 2.4: cartesian grids and octrees (recursive 2x2x2 subdivision).
+//   * Sect. 2.4 and Table 1(d): cartesian grids, rectilinear grids (PowCub:
+//     cell edges spaced by a power law), octrees (recursive 2x2x2
+//     subdivision), k-d trees (BinTree: halving along one axis per node) and
+//     Voronoi grids (each cell the part of the domain nearest to its
+//     generating site, walked across the bisecting planes of its neighbours).
 //   * Sect. 3.4: a source geometry draws random emission positions from its
 //     density (point, double-exponential disk, Plummer sphere; Table 1(a)).
 // The paper does not spell out the transport algorithm (it says so in
@@ -164,7 +168,7 @@ template <class T> void set_comp(V3<T>& a, int axis, T v) {
 extern "C" {
 
 typedef struct {
-  int32_t kind;  // 0 = cartesian, 1 = octree, 2 = rectilinear, 3 = k-d tree
+  int32_t kind;  // 0 = cartesian, 1 = octree, 2 = rectilinear, 3 = k-d tree, 4 = Voronoi
   int32_t nx, ny, nz;
   double bounds[6];  // xmin, xmax, ymin, ymax, zmin, zmax
   const float* density;  // cartesian, rectilinear [nz][ny][nx] (x fastest); octree: per leaf
@@ -173,6 +177,8 @@ typedef struct {
   int64_t n_leaves;
   const double* edges[3];  // rectilinear: cell edges per axis, n + 1 each
   const int8_t* split_axis;  // k-d tree: split axis of every node (0, 1, 2)
+  const double* sites;       // Voronoi: generating site of every cell [n_leaves][3]
+  const int64_t* offsets;    // Voronoi: neighbours of cell c are child[offsets[c] .. offsets[c + 1])
 } or_grid;
 
 typedef struct {
@@ -362,12 +368,30 @@ struct Grid {
   const int32_t* child;
   int64_t n_nodes, n_leaves;
   const int8_t* split_axis = nullptr;  // k-d tree: split axis per node
+  const double* sites = nullptr;       // Voronoi: site of every cell
+  const int64_t* offsets = nullptr;    // Voronoi: neighbour list of every cell in child
   std::vector<Box> leaf_box;  // trees: box of every leaf
   std::vector<double> edges[3];  // rectilinear: cell edges per axis
 
   // octree (kind 1) and k-d tree (kind 3): cells are the leaves of a tree
   bool tree() const { return kind == 1 || kind == 3; }
-  int64_t n_cells() const { return tree() ? n_leaves : (int64_t)n[0] * n[1] * n[2]; }
+  // Voronoi (kind 4; Table 1(d): VoronoiDustGrid): cell c is the part of the
+  // domain closer to site c than to any other site
+  bool voronoi() const { return kind == 4; }
+  int64_t n_cells() const { return tree() || voronoi() ? n_leaves : (int64_t)n[0] * n[1] * n[2]; }
+
+  // The cell of p in a Voronoi grid: the nearest site, by comparing every
+  // site (the lowest index among equally near ones).
+  int64_t nearest_site(const double p[3]) const {
+    int64_t best = 0;
+    double best_d2 = INFINITY;
+    for (int64_t c = 0; c < n_leaves; ++c) {
+      const double* s = sites + 3 * c;
+      const double d2 = (p[0] - s[0]) * (p[0] - s[0]) + (p[1] - s[1]) * (p[1] - s[1]) + (p[2] - s[2]) * (p[2] - s[2]);
+      if (d2 < best_d2) { best_d2 = d2; best = c; }
+    }
+    return best;
+  }
 
   // Plane positions: cartesian lo + i * (hi - lo) / n; rectilinear the
   // given edges (Table 1(d): PowCub grids space them by a power law).
@@ -497,6 +521,50 @@ void grid_path(const Grid& G, const V3<T>& x, const V3d& k, int64_t start_cell,
       t = (T(plane) - comp(x, entry_axis)) / T(ka);
     }
   }
+  if (G.voronoi()) {
+    // Voronoi: the cell boundary between sites c and j is their bisecting
+    // plane, {y : (y - m) . (s_j - s_c) = 0} with m the midpoint; the ray
+    // leaves cell c at the first such plane it meets heading towards s_j
+    // (k . (s_j - s_c) > 0) among c's neighbours, or at the domain boundary
+    // if that comes first.  The first minimal plane wins ties.
+    T t_box = T(INFINITY);
+    for (int a = 0; a < 3; ++a) {
+      double ka = comp(k, a);
+      if (ka == 0.0) continue;
+      T ta = (T(ka > 0 ? G.hi[a] : G.lo[a]) - comp(x, a)) / T(ka);
+      if (val(ta) < val(t_box)) t_box = ta;
+    }
+    if (cell < 0) {
+      double p[3];
+      for (int a = 0; a < 3; ++a) p[a] = xv[a] + val(t) * comp(k, a);
+      if (entry_axis >= 0) p[entry_axis] = comp(k, entry_axis) > 0 ? G.lo[entry_axis] : G.hi[entry_axis];
+      cell = G.nearest_site(p);
+    }
+    // a straight line meets each convex cell once: more segments than cells
+    // cannot happen
+    for (int64_t step = 0; step <= G.n_leaves; ++step) {
+      const double* sc = G.sites + 3 * cell;
+      int64_t next = -1;
+      T texit = t_box;
+      for (int64_t f = G.offsets[cell]; f < G.offsets[cell + 1]; ++f) {
+        const int64_t j = G.child[f];
+        const double* sj = G.sites + 3 * j;
+        const double nrm[3] = {sj[0] - sc[0], sj[1] - sc[1], sj[2] - sc[2]};
+        const double den = k.x * nrm[0] + k.y * nrm[1] + k.z * nrm[2];
+        if (!(den > 0.0)) continue;
+        const T num = (T(0.5 * (sc[0] + sj[0])) - x.x) * T(nrm[0]) + (T(0.5 * (sc[1] + sj[1])) - x.y) * T(nrm[1]) +
+                      (T(0.5 * (sc[2] + sj[2])) - x.z) * T(nrm[2]);
+        const T tj = num / T(den);
+        if (val(tj) < val(texit)) { texit = tj; next = j; }
+      }
+      if (val(texit) < val(t)) texit = t;
+      out.push_back({cell, t, texit});
+      t = texit;
+      if (next < 0) break;
+      cell = next;
+    }
+    return;
+  }
   if (!G.tree()) {
     // cartesian and rectilinear: indices of the current cell
     int64_t idx[3];
@@ -594,6 +662,8 @@ Problem make_problem(const or_problem& in) {
   G.n_nodes = in.grid.n_nodes;
   G.n_leaves = in.grid.n_leaves;
   G.split_axis = in.grid.split_axis;
+  G.sites = in.grid.sites;
+  G.offsets = in.grid.offsets;
   if (G.tree()) G.build_leaf_boxes();
   P.n_lambda = in.n_lambda;
   P.kappa.assign(in.kappa, in.kappa + in.n_lambda);
@@ -890,6 +960,13 @@ struct Transport {
   // few ulps outside).  *clamped reports whether a coordinate was moved.
   void move_to(V3<T>& x, const V3d& k, const T& s_star, int64_t cell, bool* clamped) {
     x = {x.x + s_star * T(k.x), x.y + s_star * T(k.y), x.z + s_star * T(k.z)};
+    if (P.grid.voronoi()) {
+      // a Voronoi cell is no box: the point stays where it is; a walk from a
+      // point a rounding error outside its cell takes a zero-length segment
+      // there (exit distances are clamped to the start)
+      if (clamped) *clamped = false;
+      return;
+    }
     Box b = P.grid.cell_box(cell);
     bool moved = false;
     for (int a = 0; a < 3; ++a) {
@@ -1072,12 +1149,16 @@ int64_t or_path(const or_problem* prob, const double x[3], const double k[3], in
   return (int64_t)segs.size();
 }
 
-// Leaf / cell containing p (octree tie rule along k; cartesian floor rule).
+// Leaf / cell containing p (octree tie rule along k; cartesian floor rule;
+// Voronoi: the nearest site, box = the domain).
 int64_t or_locate(const or_problem* prob, const double p[3], const double k[3], double box[6]) {
   Problem P = make_problem(*prob);
   Box b;
   int64_t c;
-  if (P.grid.tree()) {
+  if (P.grid.voronoi()) {
+    c = P.grid.nearest_site(p);
+    for (int a = 0; a < 3; ++a) { b.lo[a] = P.grid.lo[a]; b.hi[a] = P.grid.hi[a]; }
+  } else if (P.grid.tree()) {
     c = P.grid.tree_locate(p, V3d{k[0], k[1], k[2]}, &b);
   } else {
     c = P.grid.cart_locate(p);
@@ -1090,7 +1171,7 @@ int64_t or_locate(const or_problem* prob, const double p[3], const double k[3], 
 // Full transport run.  Returns 0 on success, < 0 on bad arguments.
 int32_t or_run(const or_problem* prob, const or_opts* opts, or_output* out) {
   if (!prob || !opts || !out || opts->n_per_lambda == 0 || opts->n_norm == 0 || prob->n_lambda <= 0 ||
-      (prob->n_sources <= 0 && !prob->dust_lum))
+      (prob->n_sources <= 0 && !prob->dust_lum) || (prob->dust_lum && prob->grid.kind == 4))
     return -1;
   Problem P = make_problem(*prob);
   const or_opts& O = *opts;
@@ -1241,7 +1322,7 @@ int32_t or_interaction(const or_problem* prob, const double x[3], const double k
 int32_t or_dust_temperature(const or_problem* prob, const double* lambda, const double* absorption, double scale,
                             double t_min, double t_max, double* T_out) {
   if (!prob || !lambda || !absorption || !T_out || prob->n_lambda < 2 || prob->grid.kind == 1 || prob->grid.kind == 3 ||
-      !(t_min > 0 && t_max > t_min) || !(scale > 0))
+      prob->grid.kind == 4 || !(t_min > 0 && t_max > t_min) || !(scale > 0))
     return -1;
   Problem P = make_problem(*prob);
   const int64_t nc = P.grid.n_cells();
@@ -1279,7 +1360,9 @@ int32_t or_dust_temperature(const or_problem* prob, const double* lambda, const 
 // emission): lum_out [n_lambda][n_cells] = S m_c kabs_l dlambda_l beta_l(T_c).
 int32_t or_dust_emission(const or_problem* prob, const double* lambda, const double* T, double scale,
                          double* lum_out) {
-  if (!prob || !lambda || !T || !lum_out || prob->n_lambda < 2 || prob->grid.kind == 1 || prob->grid.kind == 3 || !(scale > 0)) return -1;
+  if (!prob || !lambda || !T || !lum_out || prob->n_lambda < 2 || prob->grid.kind == 1 || prob->grid.kind == 3 ||
+      prob->grid.kind == 4 || !(scale > 0))
+    return -1;
   Problem P = make_problem(*prob);
   const int64_t nc = P.grid.n_cells();
   const std::vector<double> wts = emission_weights(P, lambda, scale);

@@ -20,6 +20,11 @@ SKIRT paper, Sect. 2.5 and its ski file, and the component table, Table 1):
 * ``batch_models``: many small independent models for the batched launcher.
 * ``spiral_example``: the paper's worked spiral-galaxy example (Sect. 2.5)
   on a 3D power-law (PowCub) or equal-cell grid.
+* ``clumpy_bintree``: the clumpy medium on a k-d tree (Table 1(d): BinTree).
+* ``voronoi_disk``: the disk galaxy's dust on a Voronoi grid whose sites
+  follow the dust density (Table 1(d): VoronoiDustGrid; Sect. 2.4).
+* ``panchromatic_disk``: a stellar spectrum and dust that re-emits what it
+  absorbs at its equilibrium temperature (Sect. 2.2, panchromatic mode).
 """
 from __future__ import annotations
 
@@ -39,13 +44,18 @@ class Grid:
     children, or -(leaf + 1) for a leaf; density float32 per leaf) or
     ``"bintree"`` (a k-d tree: ``child`` as for octrees but with two
     children, lower then upper half of the node's box split at its midpoint
-    along ``split_axis`` int8 per node)."""
+    along ``split_axis`` int8 per node) or ``"voronoi"`` (cell c holds the
+    points of the domain nearest to ``sites[c]``; ``child`` int32 lists the
+    neighbours of every cell, cell c's in ``child[offsets[c]:offsets[c+1]]``;
+    density float32 per cell)."""
     kind: str
     bounds: np.ndarray  # float64 [xmin, xmax, ymin, ymax, zmin, zmax]
     density: np.ndarray
     child: Optional[np.ndarray] = None
     edges: Optional[list] = None
     split_axis: Optional[np.ndarray] = None  # k-d tree ("bintree"): split axis per node
+    sites: Optional[np.ndarray] = None  # Voronoi: float64 [n, 3] generating sites
+    offsets: Optional[np.ndarray] = None  # Voronoi: int64 [n + 1], neighbours of c in child[offsets[c]:offsets[c+1]]
 
     @property
     def n_cells(self) -> int:
@@ -539,6 +549,106 @@ def build_bintree(bounds, refine, leaf_value, max_depth, axis_of=None):
     g = Grid("bintree", _f64(bounds), np.ascontiguousarray(dens), child.astype(np.int32),
              split_axis=np.concatenate(axis_parts))
     return g, llo, lhi
+
+
+def voronoi_grid(bounds, sites, density, mirror_depth=3.0) -> Grid:
+    """Voronoi grid (Table 1(d): VoronoiDustGrid; Sect. 2.4): cell c is the
+    part of the domain nearer to ``sites[c]`` than to any other site.  The
+    neighbour lists come from a Delaunay triangulation (scipy) of the sites
+    and of their mirror images across each domain face for the sites within
+    ``mirror_depth`` mean spacings of it.  A mirror image is never nearer
+    than its site to a point inside the domain, so every pair of cells that
+    share a face inside the domain stays a Delaunay pair and is listed; the
+    images only remove pairs whose common face lies outside.  A listed pair
+    without a face inside the domain costs a walk one plane test and
+    changes nothing.  Sites must lie strictly inside the domain."""
+    from scipy.spatial import Delaunay
+    b = np.asarray(bounds, dtype=np.float64).reshape(3, 2)
+    sites = np.ascontiguousarray(sites, dtype=np.float64)
+    n = len(sites)
+    if not np.all((sites > b[:, 0]) & (sites < b[:, 1])):
+        raise ValueError("Voronoi sites must lie strictly inside the domain")
+    h = mirror_depth * (np.prod(b[:, 1] - b[:, 0]) / n) ** (1.0 / 3.0)
+    pts = [sites]
+    for a in range(3):
+        for wall in b[a]:
+            near = np.abs(sites[:, a] - wall) < h
+            m = sites[near].copy()
+            m[:, a] = 2.0 * wall - m[:, a]
+            pts.append(m)
+    indptr, indices = Delaunay(np.concatenate(pts)).vertex_neighbor_vertices
+    row = np.repeat(np.arange(n), np.diff(indptr[:n + 1]))
+    col = indices[:indptr[n]]
+    keep = col < n
+    row, col = row[keep], col[keep]
+    order = np.lexsort((col, row))
+    counts = np.bincount(row, minlength=n)
+    offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    return Grid("voronoi", _f64(bounds), np.ascontiguousarray(density, dtype=np.float32).ravel(),
+                child=col[order].astype(np.int32), sites=sites, offsets=offsets)
+
+
+def voronoi_lattice(grid: Grid) -> Grid:
+    """The Voronoi grid whose sites are the cell centres of a cartesian grid
+    (row-major order), with the six face neighbours of every cell as its
+    neighbour lists: its cells are the cartesian cells, so transport on it
+    must equal transport on the cartesian grid."""
+    nx, ny, nz = grid.shape
+    xs, ys, zs = cell_centres(grid.bounds, (nx, ny, nz))
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    sites = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    iz, iy, ix = (a.ravel() for a in np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij"))
+    cols = []
+    for (dx, dy, dz) in ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)):
+        jx, jy, jz = ix + dx, iy + dy, iz + dz
+        ok = (jx >= 0) & (jx < nx) & (jy >= 0) & (jy < ny) & (jz >= 0) & (jz < nz)
+        cols.append(np.where(ok, jx + nx * (jy + ny * jz), -1))
+    cols = np.stack(cols, axis=1)
+    counts = (cols >= 0).sum(axis=1)
+    offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    return Grid("voronoi", _f64(grid.bounds), np.ascontiguousarray(grid.density, dtype=np.float32).ravel(),
+                child=cols[cols >= 0].astype(np.int32), sites=sites, offsets=offsets)
+
+
+def voronoi_disk(n_sites=20_000, n_lambda=3, n_pix=64, n_packets_total=60_000, face_on_tau_v=0.5, seed=7,
+                 uniform_fraction=0.1, channels=1) -> Problem:
+    """The disk galaxy (:func:`disk_galaxy`: domain, stars, optics, frames at
+    0, 60 and 90 degrees) on a Voronoi grid whose sites are drawn from its
+    dust density, as in the Voronoi grid of the paper's grid figure (Sect.
+    2.4): radius R from the exponential disk's surface density (R e^{-R/6}),
+    |z| exponential with scale 0.2 kpc, a uniform share ``uniform_fraction``
+    over the whole domain; each cell takes the density at its site."""
+    bounds = [-25.0, 25.0, -25.0, 25.0, -3.0, 3.0]
+    rng = np.random.default_rng(seed)
+    n_uniform = int(round(uniform_fraction * n_sites))
+    parts, have = [], 0
+    while have < n_sites - n_uniform:
+        m = 2 * (n_sites - n_uniform - have) + 16
+        R = rng.gamma(2.0, 6.0, m)
+        phi = rng.uniform(0.0, 2.0 * math.pi, m)
+        z = rng.laplace(0.0, 0.2, m)
+        p = np.stack([R * np.cos(phi), R * np.sin(phi), z], axis=1)
+        p = p[(np.abs(p[:, 0]) < 25.0) & (np.abs(p[:, 1]) < 25.0) & (np.abs(p[:, 2]) < 3.0)]
+        parts.append(p[:n_sites - n_uniform - have])
+        have += len(parts[-1])
+    lo, hi = np.array([-25.0, -25.0, -3.0]), np.array([25.0, 25.0, 3.0])
+    parts.append(lo + rng.uniform(0.0, 1.0, (n_uniform, 3)) * (hi - lo))
+    sites = np.concatenate(parts)
+    R = np.hypot(sites[:, 0], sites[:, 1])
+    dens = np.exp(-R / 6.0 - np.abs(sites[:, 2]) / 0.2)
+    wl = np.geomspace(0.15, 2.2, n_lambda)
+    kappa, albedo, g = synthetic_optics(wl, face_on_tau_v / (2.0 * 0.2))
+    instr = [Instrument(math.radians(inc), -math.pi / 2, 0.0, n_pix, n_pix, 25.0, 25.0, channels=channels)
+             for inc in (0.0, 60.0, 90.0)]
+    grid = voronoi_grid(bounds, sites, dens)
+    return Problem(
+        name=f"voronoi_disk_{n_sites}",
+        grid=grid, wavelengths=wl, kappa=kappa, albedo=albedo, g=g,
+        sources=[Source("expdisk", (0.0, 0.0, 0.0), np.ones(n_lambda), scale_r=4.0, scale_z=0.35)],
+        instruments=instr,
+        run=Run(n_per_lambda=max(1, int(n_packets_total) // n_lambda)),
+        meta={"sites": n_sites, "neighbours_per_cell": float(grid.child.size) / n_sites, "seed": seed},
+    )
 
 
 def octree_problem_like(problem: Problem, grid: Grid) -> Problem:

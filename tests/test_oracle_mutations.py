@@ -71,6 +71,12 @@ MUTATIONS = {
     # k-d tree children taken in the wrong order
     "bintree_child_order": ("node = child[node] + (upper ? 1 : 0);", "node = child[node] + (upper ? 0 : 1);",
                             "test_oracle_bintree.py"),
+    # Voronoi walk ignoring the last face of every cell
+    "voronoi_last_face": ("for (int64_t f = G.offsets[cell]; f < G.offsets[cell + 1]; ++f) {",
+                          "for (int64_t f = G.offsets[cell]; f + 1 < G.offsets[cell + 1]; ++f) {",
+                          "test_oracle_voronoi.py"),
+    # Voronoi bisecting plane through the cell's own site instead of the midpoint
+    "voronoi_plane_offset": ("(T(0.5 * (sc[0] + sj[0])) - x.x)", "(T(sc[0]) - x.x)", "test_oracle_voronoi.py"),
     # derivative of exp with the wrong sign
     "dual_exp_sign": ("inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, e * a.d}; }",
                       "inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, -e * a.d}; }",
