@@ -65,7 +65,7 @@ enum {
   RT_ERR_DEVICE_FLAG = -6   /* a kernel's own bounds check fired; results are not valid        */
 };
 
-enum { RT_GRID_CARTESIAN = 0, RT_GRID_OCTREE = 1, RT_GRID_RECTILINEAR = 2, RT_GRID_BINTREE = 3 };
+enum { RT_GRID_CARTESIAN = 0, RT_GRID_OCTREE = 1, RT_GRID_RECTILINEAR = 2, RT_GRID_BINTREE = 3, RT_GRID_VORONOI = 4 };
 enum { RT_SOURCE_POINT = 0, RT_SOURCE_EXPDISK = 1, RT_SOURCE_PLUMMER = 2 };
 enum { RT_DEPOSIT_NEAREST = 0, RT_DEPOSIT_BILINEAR = 1, RT_DEPOSIT_SED = 2 };
 enum { RT_LAYOUT_AUTO = 0, RT_LAYOUT_ROW_MAJOR = 1 };
@@ -96,6 +96,20 @@ enum { RT_EMITTER_SOURCES = 0, RT_EMITTER_DUST = 1 };
  *       o = bit0 x-upper | bit1 y-upper | bit2 z-upper), child[n] < 0 marks a
  *       leaf with leaf id -(child[n] + 1); density float32 [n_leaves];
  *       cell id = leaf id.  Depth at most 21.
+ *   kind RT_GRID_VORONOI: the Voronoi grid of Table 1(d) (Sect. 2.4): cell c
+ *       is the part of the domain nearer to site c than to any other site.
+ *       n_leaves sites, sites FP64 [n_leaves][3], inside `bounds`, no two
+ *       equal; the neighbours of cell c are child[offsets[c] ..
+ *       offsets[c + 1]) (offsets int64 [n_leaves + 1], offsets[0] = 0,
+ *       offsets[n_leaves] = n_nodes, ids in range, none equal to c).  The
+ *       lists must hold every cell that shares a face with c inside the
+ *       domain (the Delaunay neighbours of the sites do); extra entries only
+ *       cost time.  density float32 [n_leaves]; cell id = site index.  The
+ *       library keeps per face the FP32 unit normal and distance of the
+ *       bisecting plane, and locates points by a descent to the nearest site
+ *       from a bucket grid's seeds.  At most 2^31 - 1 sites and list
+ *       entries.  Peel-offs walk their rays; not supported by the adjoint,
+ *       batches, the allocation-free call or the dust emission.
  *   bounds: xmin, xmax, ymin, ymax, zmin, zmax (FP64; the kernels use FP32).
  *   Pointers are host pointers unless on_device = 1.  Data is copied.
  *   layout (cartesian and rectilinear grids): how the library stores the
@@ -116,6 +130,8 @@ typedef struct {
   int32_t layout;         /* RT_LAYOUT_AUTO or RT_LAYOUT_ROW_MAJOR */
   const double* edges[3]; /* RT_GRID_RECTILINEAR: cell edges per axis (host or device, as on_device) */
   const int8_t* split_axis; /* RT_GRID_BINTREE: split axis per node (host or device, as on_device) */
+  const double* sites;      /* RT_GRID_VORONOI: sites [n_leaves][3] (host or device, as on_device) */
+  const int64_t* offsets;   /* RT_GRID_VORONOI: neighbour list offsets [n_leaves + 1] (host or device) */
 } rt_grid_desc;
 
 /* Emission component (Sect. 2.2 stellar system, Sect. 3.4 position sampling,
@@ -222,8 +238,9 @@ typedef struct {
                            uniform position in it, an isotropic direction; a wavelength at which
                            the dust emits nothing launches packets of zero weight that end at once */
   int32_t blocks_per_sm; /* resident blocks of 256 threads per SM of the persistent transport grid
-                            (0 = the value rt_tune chose, else as many as fit: 4 cartesian,
-                            3 octree); the grid is this times the SM count                   */
+                            (0 = the value rt_tune chose, else as many as fit: 4 cartesian and
+                            rectilinear, 3 octree, k-d tree and Voronoi); the grid is this times
+                            the SM count */
   int32_t reserved;
 } rt_launch_opts;
 

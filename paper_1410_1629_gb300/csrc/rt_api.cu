@@ -81,6 +81,13 @@ struct rt_ctx_s {
   float* d_density = nullptr;
   int32_t* d_child = nullptr;
   float* d_edges = nullptr;  // rectilinear grids: FP32 edges, x then y then z (nx + ny + nz + 3)
+  // Voronoi grids: sites, face offsets, face planes (neighbour ids in
+  // d_child, n_nodes faces), bucket seeds
+  float4* d_site = nullptr;
+  int* d_face_off = nullptr;
+  float4* d_face = nullptr;
+  int* d_bucket_seed = nullptr;
+  int vb_n[3] = {1, 1, 1};
   // storage order of cartesian and rectilinear grids (crossing_order_strides):
   // the density copy the forward kernels read and the order of the absorption
   // tallies; permuted = not row-major
@@ -254,6 +261,12 @@ void free_grid(rt_ctx c) {
   pool_release(c, c->d_density, (size_t)c->n_cells * sizeof(float));
   pool_release(c, c->d_child, (size_t)c->n_nodes * sizeof(int32_t));
   pool_release(c, c->d_edges, (size_t)(c->nx + c->ny + c->nz + 3) * sizeof(float));
+  if (c->grid_kind == RT_GRID_VORONOI) {
+    pool_release(c, c->d_site, (size_t)c->n_cells * sizeof(float4));
+    pool_release(c, c->d_face_off, (size_t)(c->n_cells + 1) * sizeof(int));
+    pool_release(c, c->d_face, (size_t)c->n_nodes * sizeof(float4));
+    pool_release(c, c->d_bucket_seed, (size_t)c->vb_n[0] * c->vb_n[1] * c->vb_n[2] * sizeof(int));
+  }
   pool_release(c, c->d_density_s, (size_t)c->n_cells * sizeof(float));
   pool_release(c, c->d_abs_tmp, (size_t)c->n_cells * sizeof(double));
   pool_release(c, c->d_planes64, (size_t)(c->nx + c->ny + c->nz + 3) * sizeof(double));
@@ -646,8 +659,99 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
       return fail(c, RT_ERR_ARG, "rt_create_grid: tree too large for int32 indices");
     n_cells = d->n_leaves;
     n_nodes = d->n_nodes;
+  } else if (d->kind == RT_GRID_VORONOI) {
+    if (!d->child || !d->sites || !d->offsets || d->n_leaves <= 0 || d->n_nodes < 0)
+      return fail(c, RT_ERR_ARG, "rt_create_grid: a Voronoi grid needs sites[], offsets[], child[] and n_leaves > 0");
+    if (d->n_leaves > (1ll << 31) - 2 || d->n_nodes > (1ll << 31) - 1)
+      return fail(c, RT_ERR_ARG, "rt_create_grid: Voronoi grid too large for int32 indices");
+    n_cells = d->n_leaves;
+    n_nodes = d->n_nodes;
   } else {
     return fail(c, RT_ERR_ARG, "rt_create_grid: unknown grid kind %d", d->kind);
+  }
+  // Voronoi grids: sites and lists checked on the host; per face the unit
+  // normal towards the neighbour and the distance of the bisecting plane
+  // from the site (FP64, stored FP32); per bucket the nearest site to its
+  // centre, by greedy descent from the previous bucket's
+  std::vector<float4> vor_site, vor_face;
+  std::vector<int> vor_off, vor_seed;
+  int vb_n[3] = {1, 1, 1};
+  if (d->kind == RT_GRID_VORONOI) {
+    std::vector<double> site((size_t)n_cells * 3);
+    std::vector<int64_t> off((size_t)n_cells + 1);
+    std::vector<int32_t> nbr((size_t)n_nodes);
+    if (d->on_device) {
+      if (set_device(c) != RT_OK) return RT_ERR_CUDA;
+      RT_CUDA(c, cudaMemcpy(site.data(), d->sites, site.size() * sizeof(double), cudaMemcpyDeviceToHost));
+      RT_CUDA(c, cudaMemcpy(off.data(), d->offsets, off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+      RT_CUDA(c, cudaMemcpy(nbr.data(), d->child, nbr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(site.data(), d->sites, site.size() * sizeof(double));
+      std::memcpy(off.data(), d->offsets, off.size() * sizeof(int64_t));
+      std::memcpy(nbr.data(), d->child, nbr.size() * sizeof(int32_t));
+    }
+    if (off[0] != 0 || off[(size_t)n_cells] != n_nodes)
+      return fail(c, RT_ERR_ARG, "rt_create_grid: Voronoi offsets must run from 0 to n_nodes");
+    for (long long i = 0; i < n_cells; ++i) {
+      for (int a = 0; a < 3; ++a) {
+        const double v = site[(size_t)(3 * i + a)];
+        if (!(is_finite(v) && v >= d->bounds[2 * a] && v <= d->bounds[2 * a + 1]))
+          return fail(c, RT_ERR_ARG, "rt_create_grid: Voronoi site %lld outside the domain", i);
+      }
+      if (off[(size_t)i + 1] < off[(size_t)i])
+        return fail(c, RT_ERR_ARG, "rt_create_grid: Voronoi offsets decrease at %lld", i);
+    }
+    vor_site.resize((size_t)n_cells);
+    for (long long i = 0; i < n_cells; ++i)
+      vor_site[(size_t)i] = make_float4((float)site[(size_t)(3 * i)], (float)site[(size_t)(3 * i + 1)],
+                                        (float)site[(size_t)(3 * i + 2)], 0.0f);
+    vor_off.resize((size_t)n_cells + 1);
+    vor_face.resize((size_t)n_nodes);
+    for (long long i = 0; i < n_cells; ++i) {
+      vor_off[(size_t)i] = (int)off[(size_t)i];
+      const double* si = &site[(size_t)(3 * i)];
+      for (int64_t f = off[(size_t)i]; f < off[(size_t)i + 1]; ++f) {
+        const long long j = nbr[(size_t)f];
+        if (j < 0 || j >= n_cells || j == i)
+          return fail(c, RT_ERR_ARG, "rt_create_grid: Voronoi cell %lld lists neighbour %lld", i, j);
+        const double* sj = &site[(size_t)(3 * j)];
+        const double v[3] = {sj[0] - si[0], sj[1] - si[1], sj[2] - si[2]};
+        const double len = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (!(len > 0.0)) return fail(c, RT_ERR_ARG, "rt_create_grid: Voronoi sites %lld and %lld coincide", i, j);
+        vor_face[(size_t)f] = make_float4((float)(v[0] / len), (float)(v[1] / len), (float)(v[2] / len),
+                                          (float)(0.5 * len));
+      }
+    }
+    vor_off[(size_t)n_cells] = (int)n_nodes;
+    // buckets: about one per two sites, cubic in shape, at most 256 per axis
+    const double ext[3] = {d->bounds[1] - d->bounds[0], d->bounds[3] - d->bounds[2], d->bounds[5] - d->bounds[4]};
+    const double h = std::cbrt(ext[0] * ext[1] * ext[2] / std::max(1.0, 0.5 * (double)n_cells));
+    for (int a = 0; a < 3; ++a) vb_n[a] = (int)std::min(256.0, std::max(1.0, std::round(ext[a] / h)));
+    vor_seed.resize((size_t)vb_n[0] * vb_n[1] * vb_n[2]);
+    long long cur = 0;
+    for (int k = 0; k < vb_n[2]; ++k)
+      for (int j = 0; j < vb_n[1]; ++j)
+        for (int i = 0; i < vb_n[0]; ++i) {
+          const double q[3] = {d->bounds[0] + (i + 0.5) * ext[0] / vb_n[0], d->bounds[2] + (j + 0.5) * ext[1] / vb_n[1],
+                               d->bounds[4] + (k + 0.5) * ext[2] / vb_n[2]};
+          auto d2 = [&](long long s) {
+            const double* p = &site[(size_t)(3 * s)];
+            return (p[0] - q[0]) * (p[0] - q[0]) + (p[1] - q[1]) * (p[1] - q[1]) + (p[2] - q[2]) * (p[2] - q[2]);
+          };
+          long long steps = 0;
+          for (;; ++steps) {
+            if (steps > n_cells) return fail(c, RT_ERR_ARG, "rt_create_grid: Voronoi neighbour lists inconsistent");
+            double best = d2(cur);
+            long long move = -1;
+            for (int64_t f = off[(size_t)cur]; f < off[(size_t)cur + 1]; ++f) {
+              const double dj = d2(nbr[(size_t)f]);
+              if (dj < best) { best = dj; move = nbr[(size_t)f]; }
+            }
+            if (move < 0) break;
+            cur = move;
+          }
+          vor_seed[(size_t)i + (size_t)vb_n[0] * ((size_t)j + (size_t)vb_n[1] * k)] = (int)cur;
+        }
   }
   std::vector<int32_t> child_host;
   if (d->kind == RT_GRID_OCTREE || d->kind == RT_GRID_BINTREE) {
@@ -693,6 +797,20 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
     RT_CUDA(c, pool_alloc(c, &c->d_child, (size_t)n_nodes * sizeof(int32_t)));
     RT_CUDA(c, cudaMemcpy(c->d_child, child_host.data(), (size_t)n_nodes * sizeof(int32_t), cudaMemcpyHostToDevice));
   }
+  if (d->kind == RT_GRID_VORONOI) {
+    RT_CUDA(c, pool_alloc(c, &c->d_child, (size_t)std::max<long long>(n_nodes, 1) * sizeof(int32_t)));
+    if (n_nodes > 0) RT_CUDA(c, cudaMemcpy(c->d_child, d->child, (size_t)n_nodes * sizeof(int32_t), kind));
+    RT_CUDA(c, pool_alloc(c, &c->d_site, vor_site.size() * sizeof(float4)));
+    RT_CUDA(c, cudaMemcpy(c->d_site, vor_site.data(), vor_site.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    RT_CUDA(c, pool_alloc(c, &c->d_face_off, vor_off.size() * sizeof(int)));
+    RT_CUDA(c, cudaMemcpy(c->d_face_off, vor_off.data(), vor_off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    RT_CUDA(c, pool_alloc(c, &c->d_face, (size_t)std::max<long long>(n_nodes, 1) * sizeof(float4)));
+    if (n_nodes > 0)
+      RT_CUDA(c, cudaMemcpy(c->d_face, vor_face.data(), vor_face.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    RT_CUDA(c, pool_alloc(c, &c->d_bucket_seed, vor_seed.size() * sizeof(int)));
+    RT_CUDA(c, cudaMemcpy(c->d_bucket_seed, vor_seed.data(), vor_seed.size() * sizeof(int), cudaMemcpyHostToDevice));
+    for (int a = 0; a < 3; ++a) c->vb_n[a] = vb_n[a];
+  }
   c->grid_kind = d->kind;
   c->nx = d->nx; c->ny = d->ny; c->nz = d->nz;
   c->stride[0] = 1; c->stride[1] = d->nx; c->stride[2] = d->nx * d->ny;
@@ -731,7 +849,7 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
   }
   std::memcpy(c->bounds, d->bounds, sizeof c->bounds);
   c->n_cells = n_cells;
-  c->n_nodes = n_nodes;
+  c->n_nodes = d->kind == RT_GRID_VORONOI ? std::max<long long>(n_nodes, 1) : n_nodes;  // as allocated
   c->has_grid = true;
   c->tables_dirty = true;
   c->tape_valid = false;
@@ -974,6 +1092,17 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   for (int a = 0; a < 3; ++a) p.stride[a] = c->stride[a];
   p.child = c->d_child;
   p.n_nodes = c->n_nodes;
+  if (c->grid_kind == RT_GRID_VORONOI) {
+    p.site = c->d_site;
+    p.face_off = c->d_face_off;
+    p.face = c->d_face;
+    p.bucket_seed = c->d_bucket_seed;
+    for (int a = 0; a < 3; ++a) {
+      p.vb_n[a] = c->vb_n[a];
+      p.vb_inv[a] = (float)(c->vb_n[a] / (c->bounds[2 * a + 1] - c->bounds[2 * a]));
+    }
+    p.max_walk = (int)std::min<long long>(c->n_cells + 64, (1ll << 31) - 1);
+  }
   if (c->grid_kind == RT_GRID_RECTILINEAR) {
     p.edge[0] = c->d_edges;
     p.edge[1] = c->d_edges + c->nx + 1;
@@ -1296,7 +1425,8 @@ rt_status rt_tune(rt_ctx c, uint64_t n_per_lambda, uint64_t seed, const rt_launc
   int best_blocks = 0;
   o.control_lanes = best_lanes;
   // the kernels' launch bounds
-  const int max_blocks = (c->grid_kind == RT_GRID_OCTREE || c->grid_kind == RT_GRID_BINTREE) ? 3 : 4;
+  const int max_blocks =
+      (c->grid_kind == RT_GRID_OCTREE || c->grid_kind == RT_GRID_BINTREE || c->grid_kind == RT_GRID_VORONOI) ? 3 : 4;
   for (int blocks = max_blocks - 1; st == RT_OK && blocks >= max_blocks - 2 && blocks >= 1; --blocks) {
     o.blocks_per_sm = blocks;
     cudaError_t e = cudaEventRecord(e0, s);

@@ -22,6 +22,7 @@ cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaS
   if (grid_kind == RT_GRID_OCTREE) return launch_forward_octree(p, num_sms, stream);
   if (grid_kind == RT_GRID_RECTILINEAR) return launch_forward_rect(p, num_sms, stream);
   if (grid_kind == RT_GRID_BINTREE) return launch_forward_bintree(p, num_sms, stream);
+  if (grid_kind == RT_GRID_VORONOI) return launch_forward_voronoi(p, num_sms, stream);
   cudaError_t e = cudaMemsetAsync(p.work_counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
   int per_sm = 0;

@@ -79,6 +79,18 @@ struct FwdParams {
   const int32_t* child;  // octree: child[] as given; k-d tree: node words (first child << 2 | axis, or -(leaf + 1))
   long long n_nodes;     // octree only
   const float* edge[3];  // rectilinear only: cell edges per axis, n + 1 each
+  // Voronoi grids: sites (x, y, z, 0), the faces of cell c at
+  // [face_off[c], face_off[c + 1]) as (unit normal towards the neighbour,
+  // distance of the bisecting plane from the site) with the neighbour's id in
+  // child[], and per bucket of a uniform bucket grid the site nearest to its
+  // centre (bucket (i, j, k) at i + vb_n[0] (j + vb_n[1] k))
+  const float4* site;
+  const int* face_off;
+  const float4* face;
+  const int* bucket_seed;
+  int vb_n[3];
+  float vb_inv[3];  // buckets per unit length per axis
+  int max_walk;     // cells one Voronoi walk or point location may visit before the walk flag
   // storage strides of the cell index (cartesian and rectilinear grids): the
   // density and absorption of cell (ix, iy, iz) sit at ix stride[0] +
   // iy stride[1] + iz stride[2]; row-major is (1, nx, nx ny).  Cell ids seen
@@ -210,6 +222,7 @@ cudaError_t launch_columns(const float* density, int nx, int ny, int nz, int axi
 cudaError_t launch_forward_octree(const FwdParams& p, int num_sms, cudaStream_t stream);
 cudaError_t launch_forward_rect(const FwdParams& p, int num_sms, cudaStream_t stream);
 cudaError_t launch_forward_bintree(const FwdParams& p, int num_sms, cudaStream_t stream);
+cudaError_t launch_forward_voronoi(const FwdParams& p, int num_sms, cudaStream_t stream);
 // The sorted peel-off pass after a forward launch with p.peel set
 // (rt_forward.cu): scan of p.peel_hist (n_keys entries, tile totals in
 // tile_sum: (n_keys + 4095) / 4096 entries), the permutation that orders the

@@ -769,6 +769,138 @@ struct BinGrid {
   }
 };
 
+// ---------------------------------------------------------------- Voronoi grid
+// Cell c holds the points nearer to site c than to any other site (Table
+// 1(d): VoronoiDustGrid; Sect. 2.4).  Its boundary with neighbour j is their
+// bisecting plane, kept per face as the unit normal n towards s_j and the
+// plane's distance h from s_c.  On entering a cell the walk finds the first
+// plane ahead, t_f = (h - (x - s_c) . n) / (d . n) over the faces with
+// d . n > 0, or the domain boundary if that comes first (the first minimal
+// face wins ties, as in the oracle); a straight line meets each convex cell
+// once, so a walk visiting more cells than the grid holds (P.max_walk) is
+// stopped and flagged.  A point is located by a greedy descent from the site
+// nearest to its bucket's centre: move to the nearest neighbour nearer to
+// the point until none is; on a neighbour graph that holds every face inside
+// the domain this ends at the nearest site.
+struct VorGrid {
+  static constexpr bool kColumns = false;
+  static constexpr bool kIndexCells = false;
+  static constexpr bool kSortedPass = false;
+  using Cell = OctGrid::Cell;  // the cell id in .leaf (the box is not used)
+  struct Walk {
+    int leaf;   // current cell
+    int next;   // the cell beyond the exit face, -1 for the domain boundary
+    float t;    // entry parameter of the current segment
+    float te;   // exit parameter
+    float t_box;  // where the ray leaves the domain
+    int steps;  // cells entered after the first
+  };
+  struct Scratch {};
+
+  __device__ static __forceinline__ float dist2(float3 p, float4 s) {
+    const float dx = p.x - s.x, dy = p.y - s.y, dz = p.z - s.z;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  }
+
+  __device__ static __forceinline__ int locate(const FwdParams& P, float3 p) {
+    const int bx = min(max(__float2int_rd((p.x - P.lo[0]) * P.vb_inv[0]), 0), P.vb_n[0] - 1);
+    const int by = min(max(__float2int_rd((p.y - P.lo[1]) * P.vb_inv[1]), 0), P.vb_n[1] - 1);
+    const int bz = min(max(__float2int_rd((p.z - P.lo[2]) * P.vb_inv[2]), 0), P.vb_n[2] - 1);
+    int c = __ldg(&P.bucket_seed[bx + P.vb_n[0] * (by + P.vb_n[1] * bz)]);
+    for (int it = 0; it < P.max_walk; ++it) {
+      float best = dist2(p, __ldg(&P.site[c]));
+      int move = -1;
+      const int f1 = __ldg(&P.face_off[c + 1]);
+      for (int f = __ldg(&P.face_off[c]); f < f1; ++f) {
+        const int j = __ldg(&P.child[f]);
+        const float dj = dist2(p, __ldg(&P.site[j]));
+        if (dj < best) { best = dj; move = j; }
+      }
+      if (move < 0) return c;
+      c = move;
+    }
+    atomicOr(P.flags, kFlagWalkSteps);
+    return c;
+  }
+
+  // The exit of the current cell along x + t d: parameter and next cell.
+  __device__ static __forceinline__ void find_exit(const FwdParams& P, float3 x, float3 d, Walk& w) {
+    const float4 s = __ldg(&P.site[w.leaf]);
+    const float rx = x.x - s.x, ry = x.y - s.y, rz = x.z - s.z;
+    float best = w.t_box;
+    int face = -1;
+    const int f1 = __ldg(&P.face_off[w.leaf + 1]);
+    for (int f = __ldg(&P.face_off[w.leaf]); f < f1; ++f) {
+      const float4 n = __ldg(&P.face[f]);
+      const float den = fmaf(d.x, n.x, fmaf(d.y, n.y, d.z * n.z));
+      if (den > 0.0f) {
+        const float tf = (n.w - fmaf(rx, n.x, fmaf(ry, n.y, rz * n.z))) / den;
+        if (tf < best) { best = tf; face = f; }
+      }
+    }
+    w.te = best;
+    w.next = face >= 0 ? __ldg(&P.child[face]) : -1;
+  }
+
+  __device__ static __forceinline__ bool init(const FwdParams& P, float3 x, float3 d, float3 id, bool known,
+                                              const Cell& c, Walk& w, Scratch&) {
+    w.t = 0.0f;
+    w.steps = 0;
+    const float tx = id.x != 0.0f ? ((id.x > 0.0f ? P.hi[0] : P.lo[0]) - x.x) * id.x : RT_INF;
+    const float ty = id.y != 0.0f ? ((id.y > 0.0f ? P.hi[1] : P.lo[1]) - x.y) * id.y : RT_INF;
+    const float tz = id.z != 0.0f ? ((id.z > 0.0f ? P.hi[2] : P.lo[2]) - x.z) * id.z : RT_INF;
+    w.t_box = fminf(tx, fminf(ty, tz));
+    if (known) {
+      w.leaf = c.leaf;
+    } else {
+      int entry = -1;
+      float3 p = x;
+      if (!inside_box(P, x)) {
+        const float3 ik = make_float3(id.x != 0.0f ? id.x : RT_INF, id.y != 0.0f ? id.y : RT_INF,
+                                      id.z != 0.0f ? id.z : RT_INF);
+        if (!ray_box_entry(P, x, d, ik, w.t, entry)) return false;
+        p = make_float3(fmaf(w.t, d.x, x.x), fmaf(w.t, d.y, x.y), fmaf(w.t, d.z, x.z));
+        if (entry == 0) p.x = d.x > 0.0f ? P.lo[0] : P.hi[0];
+        if (entry == 1) p.y = d.y > 0.0f ? P.lo[1] : P.hi[1];
+        if (entry == 2) p.z = d.z > 0.0f ? P.lo[2] : P.hi[2];
+      }
+      w.leaf = locate(P, p);
+    }
+    find_exit(P, x, d, w);
+    return true;
+  }
+
+  __device__ static __forceinline__ float exit(const Walk& w, float3, float3, int& axis) {
+    axis = 0;
+    return w.te;
+  }
+
+  __device__ static __forceinline__ bool advance(const FwdParams& P, float3 x, float3 d, float3, int, Walk& w,
+                                                 Scratch&) {
+    if (w.next < 0) return false;
+    if (++w.steps > P.max_walk) {
+      atomicOr(P.flags, kFlagWalkSteps);
+      return false;
+    }
+    w.leaf = w.next;
+    find_exit(P, x, d, w);
+    return true;
+  }
+
+  __device__ static __forceinline__ int cell(const Walk& w) { return w.leaf; }
+  __device__ static __forceinline__ int id(const FwdParams&, const Walk& w) { return w.leaf; }
+
+  __device__ static __forceinline__ Cell carried(const Walk& w) {
+    Cell c;
+    c.leaf = w.leaf;
+    return c;
+  }
+
+  // A Voronoi cell is no box: the position stays where it is (a walk from a
+  // point a rounding error outside its cell takes a zero-length segment).
+  __device__ static __forceinline__ void clamp(const FwdParams&, const Cell&, float3&) {}
+};
+
 // ---------------------------------------------------------------- lane state
 // The lane state that only the per-event work touches lives in per-thread
 // slots of shared memory (structure of arrays: the lanes of a warp hit
@@ -797,6 +929,8 @@ template <>
 __device__ __forceinline__ RectGrid::Cell& cell_slot<RectGrid>() { return S_CELL_CART[threadIdx.x]; }
 template <>
 __device__ __forceinline__ BinGrid::Cell& cell_slot<BinGrid>() { return S_CELL_OCT[threadIdx.x]; }
+template <>
+__device__ __forceinline__ VorGrid::Cell& cell_slot<VorGrid>() { return S_CELL_OCT[threadIdx.x]; }
 
 template <class G>
 struct Lane {
@@ -1478,6 +1612,8 @@ __device__ __forceinline__ RectGrid::Scratch lane_scratch<RectGrid>() { return R
 template <>
 __device__ __forceinline__ BinGrid::Scratch lane_scratch<BinGrid>() { return BinGrid::Scratch{}; }
 template <>
+__device__ __forceinline__ VorGrid::Scratch lane_scratch<VorGrid>() { return VorGrid::Scratch{}; }
+template <>
 __device__ __forceinline__ OctGrid::Scratch lane_scratch<OctGrid>() {
   return OctGrid::Scratch{&S_STACK[threadIdx.x * kOctStack]};
 }
@@ -1488,6 +1624,8 @@ template <>
 __device__ __forceinline__ void load_grid_cache<CartGrid>(const FwdParams&) {}
 template <>
 __device__ __forceinline__ void load_grid_cache<RectGrid>(const FwdParams&) {}
+template <>
+__device__ __forceinline__ void load_grid_cache<VorGrid>(const FwdParams&) {}
 template <>
 __device__ __forceinline__ void load_grid_cache<BinGrid>(const FwdParams& P) {
   const int n = P.n_nodes < kChildCache ? (int)P.n_nodes : kChildCache;

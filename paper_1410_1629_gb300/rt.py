@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build
 
 RT_OK, RT_ERR_ARG, RT_ERR_STATE, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_DEVICE_FLAG = 0, -1, -2, -3, -4, -5, -6
-RT_GRID_CARTESIAN, RT_GRID_OCTREE, RT_GRID_RECTILINEAR, RT_GRID_BINTREE = 0, 1, 2, 3
+RT_GRID_CARTESIAN, RT_GRID_OCTREE, RT_GRID_RECTILINEAR, RT_GRID_BINTREE, RT_GRID_VORONOI = 0, 1, 2, 3, 4
 RT_SOURCE_POINT, RT_SOURCE_EXPDISK, RT_SOURCE_PLUMMER = 0, 1, 2
 RT_DEPOSIT_NEAREST, RT_DEPOSIT_BILINEAR, RT_DEPOSIT_SED = 0, 1, 2
 RT_LAYOUT_AUTO, RT_LAYOUT_ROW_MAJOR = 0, 1
@@ -41,7 +41,8 @@ class rt_grid_desc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("bounds", ctypes.c_double * 6), ("density", ctypes.c_void_p), ("n_nodes", ctypes.c_int64),
                 ("child", ctypes.c_void_p), ("n_leaves", ctypes.c_int64), ("on_device", ctypes.c_int32),
-                ("layout", ctypes.c_int32), ("edges", ctypes.c_void_p * 3), ("split_axis", ctypes.c_void_p)]
+                ("layout", ctypes.c_int32), ("edges", ctypes.c_void_p * 3), ("split_axis", ctypes.c_void_p),
+                ("sites", ctypes.c_void_p), ("offsets", ctypes.c_void_p)]
 
 
 class rt_source_desc(ctypes.Structure):
@@ -476,6 +477,15 @@ def grid_desc(grid, on_device_arrays=None):
                 e = np.ascontiguousarray(grid.edges[a], dtype=np.float64)
                 keep.append(e)
                 d.edges[a] = e.ctypes.data
+    elif grid.kind == "voronoi":
+        d.kind = RT_GRID_VORONOI
+        sites = np.ascontiguousarray(grid.sites, dtype=np.float64)
+        offsets = np.ascontiguousarray(grid.offsets, dtype=np.int64)
+        nbr = np.ascontiguousarray(grid.child, dtype=np.int32)
+        keep += [sites, offsets, nbr]
+        d.sites, d.offsets, d.child = sites.ctypes.data, offsets.ctypes.data, nbr.ctypes.data
+        d.n_nodes = nbr.size
+        d.n_leaves = dens.size
     else:
         d.kind = RT_GRID_OCTREE if grid.kind == "octree" else RT_GRID_BINTREE
         child = np.ascontiguousarray(grid.child, dtype=np.int32)

@@ -152,7 +152,14 @@ def cell_groups(grid, block=4, level=None):
     """Group id of every cell for coarser absorption bins: cartesian and
     rectilinear grids in block^3 cubes of cells; trees (octree, k-d tree) by
     the leaf's ancestor at depth `level` (the parent node when level is
-    None; a leaf shallower than `level` is its own group)."""
+    None; a leaf shallower than `level` is its own group); Voronoi grids by
+    the box of a coarse 8^3 (or `level`^3) division of the domain that holds
+    the cell's site."""
+    if grid.kind == "voronoi":
+        bins = 8 if level is None else int(level)
+        b = np.asarray(grid.bounds, dtype=np.float64).reshape(3, 2)
+        idx = np.floor((grid.sites - b[:, 0]) / (b[:, 1] - b[:, 0]) * bins).astype(np.int64).clip(0, bins - 1)
+        return idx[:, 0] + bins * (idx[:, 1] + bins * idx[:, 2])
     if grid.kind in ("cartesian", "rectilinear"):
         nx, ny, nz = grid.shape
         iz, iy, ix = np.meshgrid(np.arange(nz) // block, np.arange(ny) // block, np.arange(nx) // block,

@@ -54,7 +54,7 @@ def test_null_context_is_rejected():
 
 def test_struct_sizes_match_the_header():
     # int32 x4 + 6 doubles + ptr + int64 + ptr + int64 + 2 int32 + 3 ptr + ptr
-    assert ctypes.sizeof(rt.rt_grid_desc) == 16 + 48 + 8 + 8 + 8 + 8 + 8 + 24 + 8
+    assert ctypes.sizeof(rt.rt_grid_desc) == 16 + 48 + 8 + 8 + 8 + 8 + 8 + 24 + 8 + 16
     assert ctypes.sizeof(rt.rt_record) == 40 == rt.RECORD_DTYPE.itemsize
     assert ctypes.sizeof(rt.rt_instrument_desc) == 24 + 8 + 32 + 8
     assert ctypes.sizeof(rt.rt_stats) == 32 + 72 + 8
