@@ -960,14 +960,12 @@ struct Transport {
   // few ulps outside).  *clamped reports whether a coordinate was moved.
   void move_to(V3<T>& x, const V3d& k, const T& s_star, int64_t cell, bool* clamped) {
     x = {x.x + s_star * T(k.x), x.y + s_star * T(k.y), x.z + s_star * T(k.z)};
-    if (P.grid.voronoi()) {
-      // a Voronoi cell is no box: the point stays where it is; a walk from a
-      // point a rounding error outside its cell takes a zero-length segment
-      // there (exit distances are clamped to the start)
-      if (clamped) *clamped = false;
-      return;
-    }
-    Box b = P.grid.cell_box(cell);
+    // the interaction cell's box; a Voronoi cell is no box: the point is
+    // kept inside the domain only (a walk from a point a rounding error
+    // outside its cell takes a zero-length segment there, exit distances
+    // being clamped to the start)
+    Box b = P.grid.voronoi() ? Box{{P.grid.lo[0], P.grid.lo[1], P.grid.lo[2]}, {P.grid.hi[0], P.grid.hi[1], P.grid.hi[2]}}
+                             : P.grid.cell_box(cell);
     bool moved = false;
     for (int a = 0; a < 3; ++a) {
       T xa = comp(x, a);

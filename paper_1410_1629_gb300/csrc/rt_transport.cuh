@@ -896,9 +896,14 @@ struct VorGrid {
     return c;
   }
 
-  // A Voronoi cell is no box: the position stays where it is (a walk from a
-  // point a rounding error outside its cell takes a zero-length segment).
-  __device__ static __forceinline__ void clamp(const FwdParams&, const Cell&, float3&) {}
+  // A Voronoi cell is no box: the position is kept inside the domain only (a
+  // walk from a point a rounding error outside its cell takes a zero-length
+  // segment there).
+  __device__ static __forceinline__ void clamp(const FwdParams& P, const Cell&, float3& x) {
+    x.x = fminf(fmaxf(x.x, P.lo[0]), P.hi[0]);
+    x.y = fminf(fmaxf(x.y, P.lo[1]), P.hi[1]);
+    x.z = fminf(fmaxf(x.z, P.lo[2]), P.hi[2]);
+  }
 };
 
 // ---------------------------------------------------------------- lane state
@@ -911,10 +916,6 @@ __shared__ double S_WEIGHT[kBlock];
 __shared__ float3 S_DIR[kBlock];
 __shared__ float2 S_HG[kBlock];
 __shared__ int S_EVENT[kBlock], S_INSTR_Q[kBlock], S_WPHASE[kBlock];
-// binary exponent of the first forced-path walk's deposit weight: the weight
-// is aux0 2^S_DEPEXP with aux0 in [1/2, 1), so that absorption deposits keep
-// FP64's range whatever the packet weight (FP32 alone spans 1e-38 .. 3e38)
-__shared__ int S_DEPEXP[kBlock];
 __shared__ bool S_HAS_CELL[kBlock];
 __shared__ CartGrid::Cell S_CELL_CART[kBlock];
 __shared__ OctGrid::Cell S_CELL_OCT[kBlock];
@@ -956,7 +957,11 @@ struct Lane {
   typename G::Walk w;   // the walk: its current cell and exit data
   float rho;            // density of the walk's current cell (loaded one crossing ahead)
   float th, tl;         // optical depth of the current walk (pair sum)
-  float aux0, aux1;     // path 1: deposit weight; path 2: tau* as a float pair, then s*
+  // path 1: the deposit weight (1 - albedo) L as aux0 2^e, e the integer in
+  // aux1's bits: e = 0 and aux0 the FP32 weight while that lies in
+  // [1e-30, 1e30], else aux0 in [1/2, 1), so that deposits keep FP64's range
+  // whatever the weight; path 2: tau* as a float pair, then s*
+  float aux0, aux1;
   // adjoint tape (launches that record one): plane sums of the current path
   // walk, entry axis of its segment, crossings so far, the interaction's
   // crossing index, kappa rho and remainder, the unit exponent of weights
@@ -1299,7 +1304,10 @@ __device__ __forceinline__ void request_walk(Lane<G>& s, int phase, float3 d) {
 // weight (1 - albedo) L.
 template <class G>
 __device__ __forceinline__ void request_path(Lane<G>& s) {
-  s.aux0 = split_exp(S_LAM[s.lam].one_minus_albedo * s.L(), S_DEPEXP[threadIdx.x]);
+  const double wdep = S_LAM[s.lam].one_minus_albedo * s.L();
+  int e = 0;
+  s.aux0 = wdep >= 1e-30 && wdep <= 1e30 ? cut(wdep) : split_exp(wdep, e);
+  s.aux1 = __int_as_float(e);
   request_walk(s, kPath1, s.k());
 }
 
@@ -1577,13 +1585,17 @@ __device__ __forceinline__ void walk_step(const FwdParams& P, Lane<G>& s, unsign
   }
   if (path1 && dt > 0.0f) {
     // continuous absorption: (1 - albedo) L exp(-tau_before) (1 - exp(-dtau))
-    // exp(-tau_before) = 2^-y, y = k + f with k = floor(y): the integer
-    // part joins the weight's exponent, so deep deposits do not underflow
-    const float y = s.th * 1.44269504f;
-    const float k = floorf(y);
-    const float dep = s.aux0 * exp2f(k - y) * one_minus_exp_neg(dt);
-    add_absorption(&P.absorption[(size_t)s.lam * P.n_cells + G::cell(w)],
-                   widen_exp(dep, S_DEPEXP[threadIdx.x] - (int)k));
+    double* const a = &P.absorption[(size_t)s.lam * P.n_cells + G::cell(w)];
+    const int e = __float_as_int(s.aux1);
+    if (e == 0 && s.th < 64.0f) {
+      add_absorption(a, widen(s.aux0 * __expf(-s.th) * one_minus_exp_neg(dt)));
+    } else {
+      // exp(-tau_before) = 2^-y, y = k + f with k = floor(y): the integer
+      // part joins the weight's exponent, so deep deposits do not underflow
+      const float y = s.th * 1.44269504f;
+      const float k = floorf(y);
+      add_absorption(a, widen_exp(s.aux0 * exp2f(k - y) * one_minus_exp_neg(dt), e - (int)k));
+    }
   }
   s.th = nh;
   s.tl = nl;
