@@ -333,6 +333,43 @@ def octree_rate(args, device, stream, flush, peak):
     return out
 
 
+def grid_kinds_rate(args, device, stream, flush, peak):
+    """The adaptive grids of Table 1(d) beside the octree: the clumpy medium
+    on a k-d tree (BinTree: ~2e5 leaves, 8 wavelengths, 8e6 packets, two
+    512^2 frames) and the disk galaxy on a Voronoi grid whose sites follow
+    its dust (1e5 sites, 3 wavelengths, 3e6 packets, three 256^2 frames).
+    Algorithmic bytes as for the other grids (density and absorption per
+    crossing); the Voronoi walk also reads each crossed cell's face planes
+    (site, offsets and ~15 faces of 20 B), reported beside it."""
+    from paper_1410_1629_gb300 import workloads as W
+    out = {}
+    t0 = time.time()
+    kd = W.clumpy_bintree(n_particles=100_000, n_samples=5_000_000, target_leaves=200_000, max_level=8, n_lambda=8,
+                          n_pix=512, n_packets_total=8_000_000)
+    gen = time.time() - t0
+    r = workload_rate(kd, device, stream, flush, warmup=2, timed=2, tune_fraction=0.05, peak=peak,
+                      kernel="k_forward_bintree")
+    r["workload"] = (f"clumpy_bintree: {kd.grid.n_cells} leaves ({kd.meta['nodes']} nodes, delta "
+                     f"{kd.meta['delta']:.2e}), Plummer bulge + exponential disk, {kd.n_lambda} wavelengths, "
+                     f"{r['packets']:.0e} packets, 2 frames 512^2 at i=0/90 deg")
+    r["generation_s"] = gen
+    out["bintree"] = r
+    t0 = time.time()
+    vor = W.voronoi_disk(n_sites=100_000, n_lambda=3, n_pix=256, n_packets_total=3_000_000)
+    gen = time.time() - t0
+    r = workload_rate(vor, device, stream, flush, warmup=2, timed=2, tune_fraction=0.05, peak=peak,
+                      kernel="k_forward_voronoi")
+    nb = vor.meta["neighbours_per_cell"]
+    r["workload"] = (f"voronoi_disk: {vor.grid.n_cells} sites (90 % following the dust, {nb:.1f} neighbours per "
+                     f"cell), disk galaxy stars and optics, {vor.n_lambda} wavelengths, {r['packets']:.0e} packets, "
+                     f"3 frames 256^2 at i=0/60/90 deg")
+    r["neighbours_per_cell"] = nb
+    r["face_bytes_per_crossing"] = 16 + 8 + 20 * nb
+    r["generation_s"] = gen
+    out["voronoi"] = r
+    return out
+
+
 def spiral_rate(args, device, stream, flush, peak):
     """The paper's worked example (Sect. 2.5): spiral galaxy at 0.55 um, 1e7
     packets, one 1200 x 300 edge-on frame, on a 256 x 256 x 128 power-law
@@ -771,9 +808,11 @@ def run_gpu(args, prob, world, rank, local_rank):
                                  "achieved": ach, "peak": l2["gb_per_s"], "unit": "GB/s", "frac": ach / l2["gb_per_s"],
                                  "peak_source": "builder-measured L2 read bandwidth (rt_probe_bandwidth)",
                                  "time": "the whole call (its kernels back to back)"}
-    octree = spiral = plain = None
+    octree = spiral = plain = grids = None
     if rank == 0 and world == 1 and not args.skip_octree:
         octree = octree_rate(args, device, stream, flush, (peak, peak_kind))
+    if rank == 0 and world == 1 and not args.skip_grids:
+        grids = grid_kinds_rate(args, device, stream, flush, (peak, peak_kind))
     if rank == 0 and world == 1 and not args.skip_spiral:
         spiral = spiral_rate(args, device, stream, flush, (peak, peak_kind))
     if rank == 0 and world == 1 and not args.skip_plain:
@@ -813,7 +852,7 @@ def run_gpu(args, prob, world, rank, local_rank):
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_step * args.steps, "adjoint": adjoint,
                 "tuned": {"control_lanes": lanes, "blocks_per_sm": blocks_per_sm or "as many as fit",
                           "sample": "5 % of the packets, another seed, before the warm-up"},
-                "batch": batch, "octree": octree, "spiral_example": spiral, "plain_cube": plain,
+                "batch": batch, "octree": octree, "grids": grids, "spiral_example": spiral, "plain_cube": plain,
                 "panchromatic": panchro, "l2_peak": l2,
                 "clocks": clk,
                 "checks": {"conservation_rel": conservation, "path_crossings": int(path_cross),
@@ -845,6 +884,8 @@ def main():
     ap.add_argument("--skip-octree", action="store_true", help="skip the clumpy-octree workload (2e8 packets)")
     ap.add_argument("--octree-packets", type=float, default=None,
                     help="packets of the clumpy-octree measurement (default 2e8, the workload's size)")
+    ap.add_argument("--skip-grids", action="store_true",
+                    help="skip the k-d tree and Voronoi workloads")
     ap.add_argument("--skip-spiral", action="store_true", help="skip the paper's spiral-galaxy example")
     ap.add_argument("--skip-plain", action="store_true", help="skip the plain-method 32^3 cube")
     ap.add_argument("--skip-panchromatic", action="store_true", help="skip the panchromatic disk galaxy")

@@ -916,6 +916,8 @@ __shared__ double S_WEIGHT[kBlock];
 __shared__ float3 S_DIR[kBlock];
 __shared__ float2 S_HG[kBlock];
 __shared__ int S_EVENT[kBlock], S_INSTR_Q[kBlock], S_WPHASE[kBlock];
+// binary exponent of a path-1 deposit weight outside [1e-30, 1e30] (aux1 < 0)
+__shared__ int S_DEPEXP[kBlock];
 __shared__ bool S_HAS_CELL[kBlock];
 __shared__ CartGrid::Cell S_CELL_CART[kBlock];
 __shared__ OctGrid::Cell S_CELL_OCT[kBlock];
@@ -957,10 +959,12 @@ struct Lane {
   typename G::Walk w;   // the walk: its current cell and exit data
   float rho;            // density of the walk's current cell (loaded one crossing ahead)
   float th, tl;         // optical depth of the current walk (pair sum)
-  // path 1: the deposit weight (1 - albedo) L as aux0 2^e, e the integer in
-  // aux1's bits: e = 0 and aux0 the FP32 weight while that lies in
-  // [1e-30, 1e30], else aux0 in [1/2, 1), so that deposits keep FP64's range
-  // whatever the weight; path 2: tau* as a float pair, then s*
+  // path 1: the deposit weight (1 - albedo) L as aux0 2^e: aux0 the FP32
+  // weight (e = 0) while that lies in [1e-30, 1e30], with aux1 = 64, the
+  // optical depth below which a deposit takes the plain FP32 product; else
+  // aux0 in [1/2, 1) and e in S_DEPEXP, aux1 = -1 (every deposit carries the
+  // exponent), so that deposits keep FP64's range whatever the weight;
+  // path 2: tau* as a float pair, then s*
   float aux0, aux1;
   // adjoint tape (launches that record one): plane sums of the current path
   // walk, entry axis of its segment, crossings so far, the interaction's
@@ -1305,9 +1309,11 @@ __device__ __forceinline__ void request_walk(Lane<G>& s, int phase, float3 d) {
 template <class G>
 __device__ __forceinline__ void request_path(Lane<G>& s) {
   const double wdep = S_LAM[s.lam].one_minus_albedo * s.L();
+  const bool plain = wdep >= 1e-30 && wdep <= 1e30;
   int e = 0;
-  s.aux0 = wdep >= 1e-30 && wdep <= 1e30 ? cut(wdep) : split_exp(wdep, e);
-  s.aux1 = __int_as_float(e);
+  s.aux0 = plain ? cut(wdep) : split_exp(wdep, e);
+  s.aux1 = plain ? 64.0f : -1.0f;
+  S_DEPEXP[threadIdx.x] = e;
   request_walk(s, kPath1, s.k());
 }
 
@@ -1586,15 +1592,14 @@ __device__ __forceinline__ void walk_step(const FwdParams& P, Lane<G>& s, unsign
   if (path1 && dt > 0.0f) {
     // continuous absorption: (1 - albedo) L exp(-tau_before) (1 - exp(-dtau))
     double* const a = &P.absorption[(size_t)s.lam * P.n_cells + G::cell(w)];
-    const int e = __float_as_int(s.aux1);
-    if (e == 0 && s.th < 64.0f) {
+    if (s.th < s.aux1) {
       add_absorption(a, widen(s.aux0 * __expf(-s.th) * one_minus_exp_neg(dt)));
     } else {
       // exp(-tau_before) = 2^-y, y = k + f with k = floor(y): the integer
       // part joins the weight's exponent, so deep deposits do not underflow
       const float y = s.th * 1.44269504f;
       const float k = floorf(y);
-      add_absorption(a, widen_exp(s.aux0 * exp2f(k - y) * one_minus_exp_neg(dt), e - (int)k));
+      add_absorption(a, widen_exp(s.aux0 * exp2f(k - y) * one_minus_exp_neg(dt), S_DEPEXP[threadIdx.x] - (int)k));
     }
   }
   s.th = nh;

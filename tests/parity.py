@@ -71,7 +71,9 @@ def flip_corrected_images(gpu, ora, problem, value_flip_rtol=1e-2):
     """GPU images (every channel) with the FP32 flips undone, per record:
 
     * a pixel flip (the record's pixel differs from the oracle's) has its
-      contribution moved to the oracle's pixel;
+      contribution moved to the oracle's pixel, with the oracle's value when
+      the values also differ by more than value_flip_rtol (the packet's FP32
+      path parted from the FP64 one: counted as a value flip too);
     * a value flip (same pixel, value off by more than value_flip_rtol: the
       FP32 position fell on the other side of a cell face, so the peel-off
       ray runs through other cells) has its contribution replaced by the
@@ -90,6 +92,7 @@ def flip_corrected_images(gpu, ora, problem, value_flip_rtol=1e-2):
     flip = g["pixel"][ig] != o["pixel"][io]
     rel = np.abs(g["value"][ig] - o["value"][io]) / np.maximum(np.abs(o["value"][io]), 1e-300)
     vflip = ~flip & (rel > value_flip_rtol)
+    both = flip & (rel > value_flip_rtol)
     only_g = np.setdiff1d(np.arange(len(g)), ig)
     only_o = np.setdiff1d(np.arange(len(o)), io)
     imgs = [im.copy() for im in gpu["images"]]  # [channels, n_lambda, ny, nx]
@@ -104,13 +107,13 @@ def flip_corrected_images(gpu, ora, problem, value_flip_rtol=1e-2):
             touched[q].add((ch, int(lam) * plane + int(pix)))
 
     far = 0
-    for a, b in zip(ig[flip], io[flip]):
+    for a, b, both_ab in zip(ig[flip], io[flip], both[flip]):
         q, lam, ev = g["instr"][a], g["lam"][a], g["event"][a]
         nx = imgs[q].shape[-1]
         pg, po = int(g["pixel"][a]), int(o["pixel"][b])
         far += max(abs(pg % nx - po % nx), abs(pg // nx - po // nx)) > 1
         add(q, lam, ev, pg, -g["value"][a])
-        add(q, lam, ev, po, g["value"][a])
+        add(q, lam, ev, po, o["value"][b] if both_ab else g["value"][a])
     for a, b in zip(ig[vflip], io[vflip]):
         add(g["instr"][a], g["lam"][a], g["event"][a], g["pixel"][a], o["value"][b] - g["value"][a])
     for a in only_g:
@@ -123,6 +126,7 @@ def flip_corrected_images(gpu, ora, problem, value_flip_rtol=1e-2):
                                  "gpu": float(g["value"][ig[w]]), "oracle": float(o["value"][io[w]])}
                                 for w in worst if rel[w] > 1e-3],
               "records": int(len(o)), "flips": int(flip.sum()), "value_flips": int(vflip.sum()),
+              "pixel_and_value_flips": int(both.sum()),
               "far_flips": int(far), "gpu_only": int(len(only_g)), "oracle_only": int(len(only_o)),
               "record_rel_p999": float(np.quantile(rel, 0.999)) if len(rel) else 0.0,
               "record_rel_max": float(rel.max()) if len(rel) else 0.0, "touched": touched}
@@ -212,9 +216,12 @@ def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_rec
     # remainder (a small fraction) relative to the emitted luminosity
     scale = np.array([st_o[0], st_o[1], st_o[2], st_o[0]])
     rep["totals_rel"] = (np.abs(st_g - st_o) / np.abs(scale).clip(1e-300)).tolist()
-    img_tot_g = sum(im[0].sum() for im in gpu["images"])
     img_tot_o = sum(im[0].sum() for im in ora["images"])
-    rep["image_total_rel"] = float(abs(img_tot_g - img_tot_o) / img_tot_o) if img_tot_o else float(img_tot_g != 0)
+
+    def image_total_rel(images):
+        tot = sum(im[0].sum() for im in images)
+        return float(abs(tot - img_tot_o) / img_tot_o) if img_tot_o else float(tot != 0)
+    rep["image_total_rel"] = image_total_rel(gpu["images"])
     rep["absorption_total_rel"] = float(abs(gpu["absorption"].sum() - ora["absorption"].sum())
                                         / ora["absorption"].sum()) if ora["absorption"].sum() > 0 else 0.0
     rep["conservation_gpu"] = float(abs(st_g[0] - st_g[1] - st_g[2] - st_g[3]) / st_g[0])
@@ -226,6 +233,11 @@ def compare(gpu, ora, problem, min_count=1000, rtol=1e-4, tot_rtol=1e-6, use_rec
         imgs, rrep = flip_corrected_images(gpu, ora, problem)
         touched = rrep.pop("touched")
         rep.update(rrep)
+        # the image total after the corrections (the uncorrected one stays in
+        # image_total_rel_raw): a packet whose path parted moves its later
+        # records' values, which the records repair
+        rep["image_total_rel_raw"] = rep["image_total_rel"]
+        rep["image_total_rel"] = image_total_rel(imgs)
         # records one side lacks: at most 1e-4 of them (plus 10); FP32 flips
         # (pixel or value): at most 2e-3 (plus 10; a packet that interacts
         # close to a cell face flips with the FP32 position, and the clumpy

@@ -118,3 +118,28 @@ def test_value_flips_are_bounded(runs):
     g["records"]["value"][sel] *= 1.5
     rep = PAR.compare(g, r, prob)
     assert rep["value_flips"] == len(sel) and rep["flip_total"] > rep["flip_limit"] and not rep["ok"]
+
+
+def test_pixel_and_value_flips_take_the_oracle_value(runs):
+    """A record whose pixel and value both differ (a packet whose FP32 path
+    parted) is moved to the oracle's pixel with the oracle's value: a few of
+    them pass and are counted as value flips as well; the uncorrected image
+    total is kept beside the corrected one."""
+    prob, r = runs
+    g = _gpu_like(r)
+    nx = g["images"][0].shape[-1]
+    sel = np.arange(7, len(g["records"]), 4000)[:5]
+    for i in sel:
+        rec = g["records"][i]
+        old, new = int(rec["pixel"]), int(rec["pixel"]) ^ 1  # the horizontal neighbour
+        for ch in (0, 1 if rec["event"] == 0 else 2):
+            img = g["images"][rec["instr"]][ch, rec["lam"]].reshape(-1)
+            img[old] -= rec["value"]
+            img[new] += 3.0 * rec["value"]
+        g["records"]["pixel"][i] = new
+        g["records"]["value"][i] *= 3.0
+    rep = PAR.compare(g, r, prob)
+    assert rep["pixel_and_value_flips"] == len(sel) and rep["flips"] == len(sel)
+    assert rep["image_total_rel"] < 1e-12 < rep["image_total_rel_raw"]
+    assert all(p["corrected"]["max_rel"] < 1e-12 for p in rep["pixels"])
+    assert nx > 1
