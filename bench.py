@@ -49,11 +49,12 @@ KERNEL_SOURCES = ["paper_1410_1629_gb300/csrc/rt_forward.cu", "paper_1410_1629_g
 
 
 def column_tables(prob):
-    """Column-sum tables a cartesian launch builds: one per distinct grid axis
-    and direction among the frames that look exactly along an axis (sines
-    and cosines within 1e-15 of 0 or 1 taken as exact, as the library does)."""
+    """Column-sum tables a cartesian or rectilinear launch builds: one per
+    distinct grid axis and direction among the frames that look exactly along
+    an axis (sines and cosines within 1e-15 of 0 or 1 taken as exact, as the
+    library does)."""
     import math
-    if prob.grid.kind != "cartesian":
+    if prob.grid.kind not in ("cartesian", "rectilinear"):
         return 0
 
     def snap(v):
@@ -115,10 +116,21 @@ def captured_traffic(packets, workload_name="disk_galaxy", kernel="k_forward_car
 
 
 def workload(packets=None, name="disk_galaxy"):
+    """The headline workload, or another one for profiling runs (the grid
+    kinds of the extra bench blocks at their sizes there)."""
     from paper_1410_1629_gb300 import workloads as W
     kw = {"n_packets_total": int(packets)} if packets else {}
     if name == "clumpy_octree":
         return W.clumpy_octree(**kw)
+    if name == "clumpy_bintree":
+        kw.setdefault("n_packets_total", 8_000_000)
+        return W.clumpy_bintree(n_particles=100_000, n_samples=5_000_000, target_leaves=200_000, max_level=8,
+                                n_lambda=8, n_pix=512, **kw)
+    if name == "voronoi_disk":
+        kw.setdefault("n_packets_total", 3_000_000)
+        return W.voronoi_disk(n_sites=100_000, n_lambda=3, n_pix=256, **kw)
+    if name == "spiral_powcub":
+        return W.spiral_example("powcub", n_packets=int(packets) if packets else 10_000_000)
     return W.disk_galaxy(**kw)
 
 
@@ -131,6 +143,12 @@ def workload_config(prob, world):
                             f"packets/step per GPU, 2 frames 1024^2 at i=0/90 deg",
                 "grid": "octree float32 leaves", "n_lambda": prob.n_lambda,
                 "packets_per_step_per_gpu": int(packets),
+                "l2": "flushed between timed steps (256 MiB write)",
+                "parallelism": f"packet-id ranges sharded over {world} GPU(s), no collective on the data path"}
+    if prob.grid.kind != "cartesian":
+        return {"workload": f"{prob.name}: {prob.grid.kind} grid of {prob.grid.n_cells} cells, {prob.n_lambda} "
+                            f"wavelengths, {packets:.0e} packets/step per GPU",
+                "grid": prob.grid.kind, "n_lambda": prob.n_lambda, "packets_per_step_per_gpu": int(packets),
                 "l2": "flushed between timed steps (256 MiB write)",
                 "parallelism": f"packet-id ranges sharded over {world} GPU(s), no collective on the data path"}
     return {"workload": f"edge-on disk galaxy: 256^3 cartesian grid, 10 wavelengths 0.15-2.2 um, {packets:.0e} "
@@ -584,7 +602,9 @@ def fd_check(prob, sim, adj, opts, n, stream):
         sim.launch(n, 0, prob.run.seed, stream=stream, **opts)
         with torch.cuda.stream(stream):
             v = (adj * sim.images(stream=stream)[0]).sum()
-        return float(v.item())
+            # read on the stream that computed it (outside this block the
+            # copy would run on torch's default stream, ahead of the sum)
+            return float(v.item())
 
     t0 = time.time()
     fd = np.zeros(64)
@@ -730,8 +750,8 @@ def run_gpu(args, prob, world, rank, local_rank):
     bytes_transport = bytes_launch - bytes_walks
     part_ms = {k: statistics.mean(p[k] for p in parts) for k in parts[0]}
     part_bytes = {"column_sums": 0, "transport": bytes_transport, "peel_order": 0, "peel_walks": bytes_walks}
-    names = {"column_sums": "k_columns", "transport": "k_forward_" + ("octree" if prob.grid.kind == "octree"
-                                                                         else "cartesian"),
+    kernel_of = {"octree": "octree", "bintree": "bintree", "voronoi": "voronoi", "rectilinear": "rect"}
+    names = {"column_sums": "k_columns", "transport": "k_forward_" + kernel_of.get(prob.grid.kind, "cartesian"),
              "peel_order": "k_peel_scan_tiles + k_peel_scan_sums + k_peel_scatter", "peel_walks": "k_peel_sorted"}
     top = max(part_ms, key=part_ms.get)
     achieved = part_bytes[top] / (part_ms[top] / 1e3) / 1e9
@@ -898,8 +918,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-step-seconds", type=float, default=8.0)
-    ap.add_argument("--workload", default="disk_galaxy", choices=["disk_galaxy", "clumpy_octree"],
-                    help="disk_galaxy (the headline workload) or clumpy_octree")
+    ap.add_argument("--workload", default="disk_galaxy",
+                    choices=["disk_galaxy", "clumpy_octree", "clumpy_bintree", "voronoi_disk", "spiral_powcub"],
+                    help="disk_galaxy (the headline workload); the others are for profiling runs")
     ap.add_argument("--packets", type=float, default=None,
                     help="packets per step (default 1e8, the workload's size); smaller values are for profiling")
     ap.add_argument("--traffic", type=float, default=None,

@@ -213,7 +213,8 @@ typedef struct {
   int32_t trace_lambda;
   int32_t control_lanes; /* per-event work of a warp waits until this many of its lanes need it
                             (1..32; 0 = library choice)                                    */
-  uint64_t* profile;    /* device buffer of 8 counters accumulated by the cartesian kernel, or
+  uint64_t* profile;    /* device buffer of 8 counters accumulated by the cartesian kernel (a
+                           separately compiled instance; ignored with a tape or on other grids), or
                            NULL: loop iterations, walking lanes summed over iterations,
                            per-event rounds, lanes served summed over rounds, clock cycles in
                            per-event work, clock cycles in the walk, packets, reserved      */

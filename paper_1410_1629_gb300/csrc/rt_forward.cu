@@ -16,6 +16,10 @@ __global__ void __launch_bounds__(tr::kBlock, RT_FWD_MIN_BLOCKS) k_forward_carte
 __global__ void __launch_bounds__(tr::kBlock, RT_TAPE_MIN_BLOCKS) k_forward_cartesian_tape(const FwdParams P) {
   tr::forward_body<tr::CartGrid, true>(P);
 }
+// The launch with execution counters (P.profile set, no tape).
+__global__ void __launch_bounds__(tr::kBlock, RT_FWD_MIN_BLOCKS) k_forward_cartesian_prof(const FwdParams P) {
+  tr::forward_body<tr::CartGrid, false, true>(P);
+}
 }  // namespace
 
 cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaStream_t stream) {
@@ -26,8 +30,10 @@ cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaS
   cudaError_t e = cudaMemsetAsync(p.work_counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p.tape ? k_forward_cartesian_tape : k_forward_cartesian,
-                                                    tr::kBlock, 0);
+  const bool prof = p.profile != nullptr && !p.tape;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, p.tape ? k_forward_cartesian_tape : (prof ? k_forward_cartesian_prof : k_forward_cartesian), tr::kBlock,
+      0);
   if (e != cudaSuccess) return e;
   per_sm = per_sm < 1 ? 1 : per_sm;
   if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;
@@ -37,6 +43,8 @@ cudaError_t launch_forward(const FwdParams& p, int grid_kind, int num_sms, cudaS
   if (blocks < 1) blocks = 1;
   if (p.tape) {
     k_forward_cartesian_tape<<<(unsigned)blocks, tr::kBlock, 0, stream>>>(p);
+  } else if (prof) {
+    k_forward_cartesian_prof<<<(unsigned)blocks, tr::kBlock, 0, stream>>>(p);
   } else {
     k_forward_cartesian<<<(unsigned)blocks, tr::kBlock, 0, stream>>>(p);
   }

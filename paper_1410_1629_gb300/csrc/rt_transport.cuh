@@ -1654,7 +1654,10 @@ __device__ __forceinline__ void load_grid_cache<OctGrid>(const FwdParams& P) {
   for (int i = threadIdx.x; i < n; i += kBlock) S_CHILD[i] = P.child[i];
 }
 
-template <class G, bool kTape = false>
+// kProf: the kernel keeps the optional execution counters of P.profile (a
+// separate instantiation: the counters' ballots and clock reads cost the
+// plain kernel ~4 % of its time).
+template <class G, bool kTape = false, bool kProf = false>
 __device__ __forceinline__ void forward_body(const FwdParams& P) {
   __shared__ LaneTally tally[kBlock];
   for (int i = threadIdx.x; i < P.n_instr; i += kBlock) S_INSTR[i] = P.instr[i];
@@ -1673,7 +1676,7 @@ __device__ __forceinline__ void forward_body(const FwdParams& P) {
   s.walking = false;
   unsigned n_path = 0, n_peel = 0;
   // optional execution counters (warp leader only)
-  const bool prof = P.profile != nullptr && lane == 0;
+  const bool prof = kProf && P.profile != nullptr && lane == 0;
   // iterations, walking lanes, rounds, lanes served, cycles in control, in
   // the walk: per warp in shared memory (no registers held across the loop)
   __shared__ unsigned long long prof_c[kBlock / 32][6];
@@ -1698,7 +1701,7 @@ __device__ __forceinline__ void forward_body(const FwdParams& P) {
     }
     long long t1 = 0;
     if (prof) { t1 = clock64(); pc[4] += t1 - t0; }
-    const unsigned stepping = __ballot_sync(0xffffffffu, s.walking);
+    const unsigned stepping = kProf ? __ballot_sync(0xffffffffu, s.walking) : 0u;
     if (s.walking) walk_step<G, kTape>(P, s, n_path, n_peel, sc);
     if (prof) { pc[1] += __popc(stepping); pc[5] += clock64() - t1; }
   }
