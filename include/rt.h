@@ -217,7 +217,7 @@ typedef struct {
                            separately compiled instance; ignored with a tape or on other grids), or
                            NULL: loop iterations, walking lanes summed over iterations,
                            per-event rounds, lanes served summed over rounds, clock cycles in
-                           per-event work, clock cycles in the walk, packets, reserved      */
+                           per-event work, clock cycles in the walk; two reserved (zero)    */
   int32_t tape;         /* 1: record the adjoint tape of this launch in the context (cartesian
                            grids; 160 B x (max_events + 1) per packet), so that an rt_adjoint
                            of the same packets (same n_per_lambda, first_packet_id, seed and

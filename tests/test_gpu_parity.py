@@ -229,6 +229,29 @@ def test_control_lanes_do_not_change_results():
         assert np.array_equal(g["counters"], ref["counters"])
 
 
+def test_execution_counters_instance():
+    """A launch with execution counters (its own kernel instance) gives the
+    same results as the plain one, and its counters add up: every walked
+    crossing is one walking lane in one loop iteration (face-on frame only:
+    column sums, no sorted pass), each round serves at least one lane."""
+    import torch
+    prob = W.uniform_cube(n_cells=24, n_pix=32, channels=3)
+    n = 20000
+    plain = PAR.gpu_run(prob, n)
+    prof = torch.zeros(8, dtype=torch.int64, device="cuda")
+    counted = PAR.gpu_run(prob, n, profile=prof.data_ptr())
+    for a, b in zip(counted["images"], plain["images"]):
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-20)
+    np.testing.assert_allclose(counted["absorption"], plain["absorption"], rtol=1e-12, atol=1e-20)
+    assert np.array_equal(counted["counters"], plain["counters"])
+    c = prof.cpu().numpy()
+    st = counted["raw_stats"]
+    assert st["sorted_peels"] == 0
+    assert c[1] == st["crossings"] - st["column_crossings"]
+    assert c[0] >= c[1] / 32 and c[2] > 0 and c[3] >= c[2] and c[4] > 0 and c[5] > 0
+    assert c[6] == 0 and c[7] == 0
+
+
 @pytest.mark.parametrize("problem", ["disk", "cube"])
 def test_column_sums_equal_walked_peel_offs(problem):
     """Peel-offs towards frames along the grid axes (here face-on along +z and
