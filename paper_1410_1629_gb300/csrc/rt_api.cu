@@ -88,6 +88,7 @@ struct rt_ctx_s {
   float4* d_face = nullptr;
   int* d_bucket_seed = nullptr;
   int vb_n[3] = {1, 1, 1};
+  bool oct_exact = false;  // octree boxes exact binary fractions (FwdParams::oct_exact)
   // storage order of cartesian and rectilinear grids (crossing_order_strides):
   // the density copy the forward kernels read and the order of the absorption
   // tallies; permuted = not row-major
@@ -614,6 +615,32 @@ void rt_default_opts(rt_launch_opts* o) {
   o->peel_scatter = 1;
 }
 
+namespace {
+
+// Whether every box of an octree of depth dmax over `bounds` has corners
+// that FP32 represents exactly, with exact halvings and doublings: on each
+// axis the finest box size q = extent / 2^dmax is an FP32 number, the lower
+// bound an integer multiple n0 q, and (|n0| + 2^dmax) c < 2^23 for q = c 2^e
+// with c odd (every corner is then n c 2^e, and sums of two corners stay
+// below 2^24 c 2^e).
+bool octree_boxes_exact(const double bounds[6], int dmax) {
+  for (int a = 0; a < 3; ++a) {
+    const double lo = bounds[2 * a], hi = bounds[2 * a + 1], ext = hi - lo;
+    const double q = std::ldexp(ext, -dmax);
+    if ((double)(float)q != q || std::ldexp(q, dmax) != ext || lo + ext != hi) return false;
+    const double n0 = lo / q;
+    if (n0 != std::floor(n0) || n0 * q != lo) return false;
+    int e = 0;
+    const double m = std::frexp(q, &e);
+    unsigned long long cq = (unsigned long long)std::ldexp(m, 53);
+    while (cq && !(cq & 1ull)) cq >>= 1;
+    if (!((std::fabs(n0) + std::ldexp(1.0, dmax)) * (double)cq < 8388608.0)) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
 rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
   if (!c) return RT_ERR_ARG;
   c->err.clear();
@@ -754,6 +781,7 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
         }
   }
   std::vector<int32_t> child_host;
+  int oct_depth = 0;  // octrees: the deepest leaf's depth
   if (d->kind == RT_GRID_OCTREE || d->kind == RT_GRID_BINTREE) {
     // validate the tree on the host: every child block in range (after its
     // parent), every leaf id in range, k-d tree split axes 0..2; k-d tree
@@ -770,10 +798,15 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
       std::memcpy(child_host.data(), d->child, n_nodes * sizeof(int32_t));
       if (bin) std::memcpy(axis_host.data(), d->split_axis, (size_t)n_nodes);
     }
+    std::vector<int> node_depth(bin ? 0 : (size_t)n_nodes, 0);
     for (long long i = 0; i < n_nodes; ++i) {
       const long long v = child_host[i];
       if (v >= 0 && (v <= i || v + kids > n_nodes))
         return fail(c, RT_ERR_ARG, "rt_create_grid: node %lld has child block %lld out of range", i, v);
+      if (!bin && v >= 0) {
+        for (long long k = 0; k < kids; ++k) node_depth[(size_t)(v + k)] = node_depth[(size_t)i] + 1;
+        oct_depth = std::max(oct_depth, node_depth[(size_t)i] + 1);
+      }
       if (v < 0 && (-v - 1) >= n_cells)
         return fail(c, RT_ERR_ARG, "rt_create_grid: node %lld has leaf id %lld out of range", i, -v - 1);
       if (bin && v >= 0) {
@@ -812,6 +845,7 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
     for (int a = 0; a < 3; ++a) c->vb_n[a] = vb_n[a];
   }
   c->grid_kind = d->kind;
+  c->oct_exact = d->kind == RT_GRID_OCTREE && oct_depth <= 21 && octree_boxes_exact(d->bounds, oct_depth);
   c->nx = d->nx; c->ny = d->ny; c->nz = d->nz;
   c->stride[0] = 1; c->stride[1] = d->nx; c->stride[2] = d->nx * d->ny;
   c->permuted = false;
@@ -1092,6 +1126,7 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   for (int a = 0; a < 3; ++a) p.stride[a] = c->stride[a];
   p.child = c->d_child;
   p.n_nodes = c->n_nodes;
+  p.oct_exact = c->oct_exact ? 1 : 0;
   if (c->grid_kind == RT_GRID_VORONOI) {
     p.site = c->d_site;
     p.face_off = c->d_face_off;

@@ -78,6 +78,10 @@ struct FwdParams {
   const float* density;
   const int32_t* child;  // octree: child[] as given; k-d tree: node words (first child << 2 | axis, or -(leaf + 1))
   long long n_nodes;     // octree only
+  // octree boxes are exact binary fractions of the domain (every box corner
+  // at any depth is representable and every halving exact): a box can be
+  // rebuilt upwards from a leaf (size doubled) instead of down from the root
+  int oct_exact;
   const float* edge[3];  // rectilinear only: cell edges per axis, n + 1 each
   // Voronoi grids: sites (x, y, z, 0), the faces of cell c at
   // [face_off[c], face_off[c + 1]) as (unit normal towards the neighbour,

@@ -585,12 +585,28 @@ struct OctGrid {
       // trailing ones (up) / zeros (down) of the leaf's coordinate
       const int tb = da > 0.0f ? __clz(~top) : __clz(top);
       const int part = old_depth - 1 - tb;
-      for (; depth < part; ++depth) {
-        const int oct = (int)((old_path >> (3 * depth)) & 7ull);
+      if (P.oct_exact) {
+        // exact boxes: up from the leaf, each level doubling the box on the
+        // side away from the child's octant (tb + 1 levels instead of part)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float mid = 0.5f * (lo[a] + hi[a]);
-          if ((oct >> a) & 1) lo[a] = mid; else hi[a] = mid;
+        for (int a = 0; a < 3; ++a) { lo[a] = w.lo[a]; hi[a] = w.hi[a]; }
+        for (int l = old_depth - 1; l >= part; --l) {
+          const int oct = (int)((old_path >> (3 * l)) & 7ull);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float size = hi[a] - lo[a];
+            if ((oct >> a) & 1) lo[a] -= size; else hi[a] += size;
+          }
+        }
+        depth = part;
+      } else {
+        for (; depth < part; ++depth) {
+          const int oct = (int)((old_path >> (3 * depth)) & 7ull);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float mid = 0.5f * (lo[a] + hi[a]);
+            if ((oct >> a) & 1) lo[a] = mid; else hi[a] = mid;
+          }
         }
       }
 #pragma unroll
