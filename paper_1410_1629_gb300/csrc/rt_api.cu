@@ -1460,8 +1460,7 @@ rt_status rt_tune(rt_ctx c, uint64_t n_per_lambda, uint64_t seed, const rt_launc
   int best_blocks = 0;
   o.control_lanes = best_lanes;
   // the kernels' launch bounds
-  const int max_blocks =
-      (c->grid_kind == RT_GRID_OCTREE || c->grid_kind == RT_GRID_BINTREE || c->grid_kind == RT_GRID_VORONOI) ? 3 : 4;
+  const int max_blocks = (c->grid_kind == RT_GRID_OCTREE || c->grid_kind == RT_GRID_BINTREE) ? 3 : 4;
   for (int blocks = max_blocks - 1; st == RT_OK && blocks >= max_blocks - 2 && blocks >= 1; --blocks) {
     o.blocks_per_sm = blocks;
     cudaError_t e = cudaEventRecord(e0, s);

@@ -3,8 +3,10 @@
 // instantiated with the walk across the cells' bisecting planes.
 #include "rt_transport.cuh"
 
+// four resident blocks of 256 fit the Voronoi walk in 64 registers without
+// spills: more warps to hide the L2 latency of the face-plane loads
 #ifndef RT_VOR_MIN_BLOCKS
-#define RT_VOR_MIN_BLOCKS 3
+#define RT_VOR_MIN_BLOCKS 4
 #endif
 
 namespace rtk {
