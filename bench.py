@@ -365,7 +365,7 @@ def grid_kinds_rate(args, device, stream, flush, peak):
     kd = W.clumpy_bintree(n_particles=100_000, n_samples=5_000_000, target_leaves=200_000, max_level=8, n_lambda=8,
                           n_pix=512, n_packets_total=8_000_000)
     gen = time.time() - t0
-    r = workload_rate(kd, device, stream, flush, warmup=2, timed=2, tune_fraction=0.05, peak=peak,
+    r = workload_rate(kd, device, stream, flush, warmup=2, timed=2, tune_fraction=0.2, peak=peak,
                       kernel="k_forward_bintree")
     r["workload"] = (f"clumpy_bintree: {kd.grid.n_cells} leaves ({kd.meta['nodes']} nodes, delta "
                      f"{kd.meta['delta']:.2e}), Plummer bulge + exponential disk, {kd.n_lambda} wavelengths, "
@@ -375,7 +375,7 @@ def grid_kinds_rate(args, device, stream, flush, peak):
     t0 = time.time()
     vor = W.voronoi_disk(n_sites=100_000, n_lambda=3, n_pix=256, n_packets_total=3_000_000)
     gen = time.time() - t0
-    r = workload_rate(vor, device, stream, flush, warmup=2, timed=2, tune_fraction=0.05, peak=peak,
+    r = workload_rate(vor, device, stream, flush, warmup=2, timed=2, tune_fraction=0.2, peak=peak,
                       kernel="k_forward_voronoi")
     nb = vor.meta["neighbours_per_cell"]
     r["workload"] = (f"voronoi_disk: {vor.grid.n_cells} sites (90 % following the dust, {nb:.1f} neighbours per "

@@ -89,6 +89,9 @@ struct rt_ctx_s {
   int* d_bucket_seed = nullptr;
   int vb_n[3] = {1, 1, 1};
   bool oct_exact = false;  // octree boxes exact binary fractions (FwdParams::oct_exact)
+  // k-d trees: leaf ropes [n_cells][6] and node boxes [n_nodes][2] (FwdParams)
+  int32_t* d_rope = nullptr;
+  float4* d_node_box = nullptr;
   // storage order of cartesian and rectilinear grids (crossing_order_strides):
   // the density copy the forward kernels read and the order of the absorption
   // tallies; permuted = not row-major
@@ -261,6 +264,10 @@ void free_grid(rt_ctx c) {
   cudaDeviceSynchronize();  // no kernel may still read the released buffers
   pool_release(c, c->d_density, (size_t)c->n_cells * sizeof(float));
   pool_release(c, c->d_child, (size_t)c->n_nodes * sizeof(int32_t));
+  if (c->grid_kind == RT_GRID_BINTREE) {
+    pool_release(c, c->d_rope, (size_t)c->n_cells * 6 * sizeof(int32_t));
+    pool_release(c, c->d_node_box, (size_t)c->n_nodes * 2 * sizeof(float4));
+  }
   pool_release(c, c->d_edges, (size_t)(c->nx + c->ny + c->nz + 3) * sizeof(float));
   if (c->grid_kind == RT_GRID_VORONOI) {
     pool_release(c, c->d_site, (size_t)c->n_cells * sizeof(float4));
@@ -781,6 +788,8 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
         }
   }
   std::vector<int32_t> child_host;
+  std::vector<int32_t> rope_host;     // k-d trees: leaf ropes
+  std::vector<float4> node_box_host;  // k-d trees: node boxes
   int oct_depth = 0;  // octrees: the deepest leaf's depth
   if (d->kind == RT_GRID_OCTREE || d->kind == RT_GRID_BINTREE) {
     // validate the tree on the host: every child block in range (after its
@@ -815,6 +824,50 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
         child_host[(size_t)i] = (int32_t)((v << 2) | axis_host[(size_t)i]);
       }
     }
+    if (bin) {
+      // node boxes with the device's FP32 halving, and the ropes: going down,
+      // the lower child's rope across its upper face on the split axis is the
+      // upper child and the other way round; the other faces inherit
+      rope_host.assign((size_t)n_cells * 6, -1);
+      node_box_host.resize((size_t)n_nodes * 2);
+      struct Item {
+        long long node;
+        float lo[3], hi[3];
+        int32_t r[6];
+      };
+      std::vector<Item> stack;
+      Item root;
+      root.node = 0;
+      for (int a = 0; a < 3; ++a) {
+        root.lo[a] = (float)d->bounds[2 * a];
+        root.hi[a] = (float)d->bounds[2 * a + 1];
+      }
+      for (int f = 0; f < 6; ++f) root.r[f] = -1;
+      stack.push_back(root);
+      while (!stack.empty()) {
+        const Item it = stack.back();
+        stack.pop_back();
+        node_box_host[2 * (size_t)it.node] = make_float4(it.lo[0], it.lo[1], it.lo[2], 0.0f);
+        node_box_host[2 * (size_t)it.node + 1] = make_float4(it.hi[0], it.hi[1], it.hi[2], 0.0f);
+        const int32_t v = child_host[(size_t)it.node];
+        if (v < 0) {
+          for (int f = 0; f < 6; ++f) rope_host[(size_t)(-(long long)v - 1) * 6 + f] = it.r[f];
+          continue;
+        }
+        const int a = v & 3;
+        const long long first = (long long)(v >> 2);
+        const float mid = 0.5f * (it.lo[a] + it.hi[a]);
+        Item lower = it, upper = it;
+        lower.node = first;
+        lower.hi[a] = mid;
+        lower.r[2 * a + 1] = (int32_t)(first + 1);
+        upper.node = first + 1;
+        upper.lo[a] = mid;
+        upper.r[2 * a] = (int32_t)first;
+        stack.push_back(lower);
+        stack.push_back(upper);
+      }
+    }
   }
   if (set_device(c) != RT_OK) return RT_ERR_CUDA;
   free_problem(c);
@@ -829,6 +882,13 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
   if (d->kind == RT_GRID_OCTREE || d->kind == RT_GRID_BINTREE) {
     RT_CUDA(c, pool_alloc(c, &c->d_child, (size_t)n_nodes * sizeof(int32_t)));
     RT_CUDA(c, cudaMemcpy(c->d_child, child_host.data(), (size_t)n_nodes * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
+  if (d->kind == RT_GRID_BINTREE) {
+    RT_CUDA(c, pool_alloc(c, &c->d_rope, rope_host.size() * sizeof(int32_t)));
+    RT_CUDA(c, cudaMemcpy(c->d_rope, rope_host.data(), rope_host.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    RT_CUDA(c, pool_alloc(c, &c->d_node_box, node_box_host.size() * sizeof(float4)));
+    RT_CUDA(c, cudaMemcpy(c->d_node_box, node_box_host.data(), node_box_host.size() * sizeof(float4),
+                          cudaMemcpyHostToDevice));
   }
   if (d->kind == RT_GRID_VORONOI) {
     RT_CUDA(c, pool_alloc(c, &c->d_child, (size_t)std::max<long long>(n_nodes, 1) * sizeof(int32_t)));
@@ -1127,6 +1187,8 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   p.child = c->d_child;
   p.n_nodes = c->n_nodes;
   p.oct_exact = c->oct_exact ? 1 : 0;
+  p.rope = c->d_rope;
+  p.node_box = c->d_node_box;
   if (c->grid_kind == RT_GRID_VORONOI) {
     p.site = c->d_site;
     p.face_off = c->d_face_off;

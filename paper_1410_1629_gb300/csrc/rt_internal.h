@@ -77,6 +77,11 @@ struct FwdParams {
   float lo[3], hi[3], d[3], inv_d[3];
   const float* density;
   const int32_t* child;  // octree: child[] as given; k-d tree: node words (first child << 2 | axis, or -(leaf + 1))
+  // k-d trees: per leaf and face (2 axis + (exit towards +axis)) the node
+  // across that face whose box covers the face (-1: the domain boundary), and
+  // every node's box (FP32, lo then hi, as the descent halves it)
+  const int32_t* rope;
+  const float4* node_box;
   long long n_nodes;     // octree only
   // octree boxes are exact binary fractions of the domain (every box corner
   // at any depth is representable and every halving exact): a box can be

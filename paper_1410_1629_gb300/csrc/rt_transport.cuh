@@ -659,8 +659,13 @@ struct OctGrid {
 // Device node word: (first child << 2) | split axis for an inner node (the
 // lower child first, the upper one next), -(leaf + 1) for a leaf.  A point
 // on a splitting plane belongs to the child the ray enters, as in octrees.
-// The walk locates the next leaf from the root at the exit point of the
-// current one (the first kChildCache node words sit in shared memory).
+// The walk finds the next leaf at the exit point of the current one by a
+// descent from the leaf's rope for the face it leaves through (the node
+// across that face that covers it: the sibling of the ancestor whose split
+// made the face), or from the root when the exit point lies on an edge of
+// the leaf (the tie rule may then part the paths higher up).  Both give the
+// leaf the root descent gives.  The first kChildCache node words sit in
+// shared memory.
 constexpr int kMaxBinDepth = 96;
 
 struct BinGrid {
@@ -681,8 +686,12 @@ struct BinGrid {
 
   // Descend from the root to the leaf holding p (direction d breaks ties).
   __device__ static __forceinline__ bool locate(const FwdParams& P, float3 p, float3 d, Walk& w) {
-    float lx = P.lo[0], ly = P.lo[1], lz = P.lo[2], hx = P.hi[0], hy = P.hi[1], hz = P.hi[2];
-    int node = 0;
+    return descend(P, 0, P.lo[0], P.lo[1], P.lo[2], P.hi[0], P.hi[1], P.hi[2], p, d, w);
+  }
+
+  // Descend from `node` (box lo/hi) to the leaf holding p.
+  __device__ static __forceinline__ bool descend(const FwdParams& P, int node, float lx, float ly, float lz, float hx,
+                                                 float hy, float hz, float3 p, float3 d, Walk& w) {
     for (int depth = 0; depth <= kMaxBinDepth; ++depth) {
       const int v = word(P, node);
       if (v < 0) {
@@ -758,7 +767,20 @@ struct BinGrid {
     if (axis == 0) p.x = plane; else if (axis == 1) p.y = plane; else p.z = plane;
     const int old = w.leaf;
     const float t = w.t;
-    if (!locate(P, p, d, w)) return false;
+    const bool inside = (axis == 0 || (p.x > w.lo[0] && p.x < w.hi[0])) &&
+                        (axis == 1 || (p.y > w.lo[1] && p.y < w.hi[1])) &&
+                        (axis == 2 || (p.z > w.lo[2] && p.z < w.hi[2]));
+    // the start of the descent (one loop for both starts: lanes of a warp
+    // that start differently still descend together)
+    int node = 0;
+    float4 lo = make_float4(P.lo[0], P.lo[1], P.lo[2], 0.0f), hi = make_float4(P.hi[0], P.hi[1], P.hi[2], 0.0f);
+    if (inside) {
+      node = __ldg(&P.rope[(size_t)old * 6 + 2 * axis + (da > 0.0f ? 1 : 0)]);
+      if (node < 0) return false;
+      lo = __ldg(&P.node_box[2 * (size_t)node]);
+      hi = __ldg(&P.node_box[2 * (size_t)node + 1]);
+    }
+    if (!descend(P, node, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, p, d, w)) return false;
     w.t = t;
     if (w.leaf == old) {  // the exit point cannot lie in the leaf it leaves
       atomicOr(P.flags, kFlagWalkSteps);
