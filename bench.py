@@ -347,8 +347,25 @@ def octree_rate(args, device, stream, flush, peak):
     out["nodes"] = int(prob.meta["nodes"])
     out["delta"] = float(prob.meta["delta"])
     out["generation_s"] = gen_s
-    out["roofline"]["note"] = "algorithmic bytes count no tree-node loads (the descent below the cached top)"
+    depth = leaf_depths(prob.grid.child)
+    out["leaf_depth"] = {"mean": float(depth.mean()), "max": int(depth.max()),
+                         "share_by_depth": {int(d): float(c) / len(depth)
+                                            for d, c in zip(*np.unique(depth, return_counts=True))}}
+    out["roofline"]["note"] = ("algorithmic bytes count no tree-node loads: a walk's re-descent reads one 4 B "
+                               "child word per level below the common ancestor, the first 1024 words (the top "
+                               "three levels) from shared memory")
     return out
+
+
+def leaf_depths(child):
+    """Depth of every leaf of an octree given as its child array (children
+    after their parents)."""
+    child = np.asarray(child, dtype=np.int64)
+    depth = np.zeros(len(child), dtype=np.int64)
+    inner = np.flatnonzero(child >= 0)
+    for node in inner:  # parents first, so each parent's depth is final
+        depth[child[node]:child[node] + 8] = depth[node] + 1
+    return depth[child < 0]
 
 
 def grid_kinds_rate(args, device, stream, flush, peak):

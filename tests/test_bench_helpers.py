@@ -53,3 +53,16 @@ def test_kernel_hash_ignores_comments_only():
     assert bench.source_code("int x;\nint z;\n", "k.cu") != bench.source_code(a, "k.cu")
     # other files are hashed whole
     assert bench.source_code("x = 1  # c\n", "build.py") == "x = 1  # c\n"
+
+
+def test_leaf_depths_of_an_octree():
+    """Leaf depths from the child array: a full octree of depth 2, and one
+    whose lowest octant alone is refined on to depth 3."""
+    full, _, _ = W.build_octree([-1, 1] * 3, lambda lo, hi, l: np.ones(len(lo), bool),
+                                lambda lo, hi: np.ones(len(lo)), 2)
+    d = bench.leaf_depths(full.child)
+    assert len(d) == 64 and np.all(d == 2)
+    mixed, _, _ = W.build_octree([-1, 1] * 3, lambda lo, hi, l: (l == 0) | np.all(hi <= 0.0, axis=1),
+                                 lambda lo, hi: np.ones(len(lo)), 3)
+    d = bench.leaf_depths(mixed.child)
+    assert np.bincount(d).tolist() == [0, 7, 0, 64]
