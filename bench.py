@@ -817,6 +817,7 @@ def run_gpu(args, prob, world, rank, local_rank):
         d2h = sum(b.numel() for b in img_host) * 8 + ab_host.numel() * 8
         e2e = {"value": world * packets_step * len(e2e_times) / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": len(e2e_times),
+               "step_seconds": [round(x, 4) for x in e2e_times],
                "includes": "rt_create_grid from pinned host density, optics, sources, instruments, launch, "
                            "rt_read_images and rt_read_absorption to pinned host memory"}
     sim.close()
