@@ -1536,7 +1536,9 @@ rt_status rt_tune(rt_ctx c, uint64_t n_per_lambda, uint64_t seed, const rt_launc
       st = cuda_fail(c, e, "rt_tune");
       break;
     }
-    if (ms < best) {
+    // fewer blocks must win clearly: one sample launch per candidate, and a
+    // small sample's timing noise should not cost the full occupancy
+    if (ms < 0.97f * best) {
       best = ms;
       best_blocks = blocks;
     }

@@ -109,7 +109,7 @@ __device__ __forceinline__ void deposit(const DevModel& M, const BLane& s, bool 
   if (!I.bilinear) {
     const float fix = floorf(fx), fiy = floorf(fy);
     if (!(fix >= 0.0f && fiy >= 0.0f && fix < (float)I.nx && fiy < (float)I.ny)) return;
-    tr::add_aggregated(&I.image[(size_t)(int)fiy * I.nx + (int)fix], value);
+    atomicAdd(&I.image[(size_t)(int)fiy * I.nx + (int)fix], value);
     return;
   }
   const float gx = fx - 0.5f, gy = fy - 0.5f;

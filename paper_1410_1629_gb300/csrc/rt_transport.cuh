@@ -156,24 +156,6 @@ __device__ __forceinline__ void add_absorption(double* p, double v) {
       : "memory");
 }
 
-// atomicAdd(addr, v), where the lanes of the warp that add to the same
-// address at the same time first sum their values in lane order and one of
-// them issues the atomic: the lanes of a batch warp carry packets of one
-// small model, whose peel-offs from a central point source all reach one
-// pixel.  (In the transport kernel the extra registers cost a spill.)
-__device__ __forceinline__ void add_aggregated(double* addr, double v) {
-  const unsigned act = __activemask();
-  const unsigned grp = __match_any_sync(act, (unsigned long long)addr);
-  const unsigned lane = threadIdx.x & 31u;
-  if (grp == (1u << lane)) {
-    atomicAdd(addr, v);
-    return;
-  }
-  double sum = 0.0;
-  for (unsigned m = grp; m; m &= m - 1u) sum += __shfl_sync(grp, v, __ffs(m) - 1);
-  if ((int)lane == __ffs(grp) - 1) atomicAdd(addr, sum);
-}
-
 // 1 - exp(-x) for x >= 0 with a relative error below 5e-7: the alternating
 // series through x^8 for x < 1/4 (truncation below 1e-10), 1 - exp(-x) above.
 __device__ __forceinline__ float one_minus_exp_neg(float x) {
