@@ -86,7 +86,8 @@ enum { RT_EMITTER_SOURCES = 0, RT_EMITTER_DUST = 1 };
  *       node 0 the root; child[n] >= 0 is the index of the first of n's two
  *       contiguous children (the lower, then the upper half of n's box split
  *       at its midpoint along split_axis[n], 0 = x, 1 = y, 2 = z),
- *       child[n] < 0 marks a leaf with leaf id -(child[n] + 1); density
+ *       child[n] < 0 marks a leaf with leaf id -(child[n] + 1), each id in
+ *       [0, n_leaves) exactly once; density
  *       float32 [n_leaves]; cell id = leaf id; depth at most 96, node
  *       indices below 2^29.  Peel-offs walk their rays; not supported by the
  *       adjoint, batches, the allocation-free call or the dust emission.
@@ -94,8 +95,8 @@ enum { RT_EMITTER_SOURCES = 0, RT_EMITTER_DUST = 1 };
  *       midpoints; child int32 [n_nodes], node 0 the root: child[n] >= 0 is
  *       the index of the first of n's eight contiguous children (octant
  *       o = bit0 x-upper | bit1 y-upper | bit2 z-upper), child[n] < 0 marks a
- *       leaf with leaf id -(child[n] + 1); density float32 [n_leaves];
- *       cell id = leaf id.  Depth at most 21.
+ *       leaf with leaf id -(child[n] + 1), each id in [0, n_leaves) exactly
+ *       once; density float32 [n_leaves]; cell id = leaf id.  Depth at most 21.
  *   kind RT_GRID_VORONOI: the Voronoi grid of Table 1(d) (Sect. 2.4): cell c
  *       is the part of the domain nearer to site c than to any other site.
  *       n_leaves sites, sites FP64 [n_leaves][3], inside `bounds`, no two

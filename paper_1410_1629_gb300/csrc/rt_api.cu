@@ -808,6 +808,8 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
       if (bin) std::memcpy(axis_host.data(), d->split_axis, (size_t)n_nodes);
     }
     std::vector<int> node_depth(bin ? 0 : (size_t)n_nodes, 0);
+    std::vector<unsigned char> leaf_seen((size_t)n_cells, 0);
+    long long leaves_found = 0;
     for (long long i = 0; i < n_nodes; ++i) {
       const long long v = child_host[i];
       if (v >= 0 && (v <= i || v + kids > n_nodes))
@@ -818,12 +820,20 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
       }
       if (v < 0 && (-v - 1) >= n_cells)
         return fail(c, RT_ERR_ARG, "rt_create_grid: node %lld has leaf id %lld out of range", i, -v - 1);
+      if (v < 0) {
+        // every leaf id once: the k-d tree walk keys its ropes by leaf id
+        if (leaf_seen[(size_t)(-v - 1)]) return fail(c, RT_ERR_ARG, "rt_create_grid: leaf id %lld appears twice", -v - 1);
+        leaf_seen[(size_t)(-v - 1)] = 1;
+        ++leaves_found;
+      }
       if (bin && v >= 0) {
         if (axis_host[(size_t)i] < 0 || axis_host[(size_t)i] > 2)
           return fail(c, RT_ERR_ARG, "rt_create_grid: node %lld has split axis %d", i, (int)axis_host[(size_t)i]);
         child_host[(size_t)i] = (int32_t)((v << 2) | axis_host[(size_t)i]);
       }
     }
+    if (leaves_found != n_cells)
+      return fail(c, RT_ERR_ARG, "rt_create_grid: %lld leaves in the tree for n_leaves = %lld", leaves_found, n_cells);
     if (bin) {
       // node boxes with the device's FP32 halving, and the ropes: going down,
       // the lower child's rope across its upper face on the split axis is the

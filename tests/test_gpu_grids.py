@@ -130,3 +130,30 @@ def test_bintree_parity(case):
     rep = PAR.compare(g, o, prob, groups=PAR.cell_groups(prob.grid))
     _assert_ok(rep)
     assert rep["crossings_rel"] < 1e-4
+
+
+@pytest.mark.parametrize("kind", ["bintree", "octree"])
+def test_tree_leaf_ids_are_checked(kind):
+    """Every leaf id of a tree appears once: a repeated id and a tree with
+    fewer leaves than n_leaves are rejected; the unchanged tree is accepted."""
+    if kind == "bintree":
+        grid, _, _ = W.build_bintree([-1, 1] * 3, lambda lo, hi, d: np.ones(len(lo), bool),
+                                     lambda lo, hi: np.ones(len(lo)), 4)
+    else:
+        grid, _, _ = W.build_octree([-1, 1] * 3, lambda lo, hi, l: np.ones(len(lo), bool),
+                                    lambda lo, hi: np.ones(len(lo)), 2)
+    ctx = rt.rt_context_create(0)
+    try:
+        leaves = np.flatnonzero(np.asarray(grid.child) < 0)
+        dup = np.array(grid.child)
+        dup[leaves[1]] = dup[leaves[0]]
+        short = W.replace(grid, density=np.concatenate([grid.density, np.ones(3, np.float32)]))
+        for bad in (W.replace(grid, child=dup), short):
+            d, keep = rt.grid_desc(bad)
+            with pytest.raises(rt.RTError) as e:
+                rt.rt_create_grid(ctx, d)
+            assert e.value.status == rt.RT_ERR_ARG
+        d, keep = rt.grid_desc(grid)
+        rt.rt_create_grid(ctx, d)
+    finally:
+        rt.rt_context_destroy(ctx)
