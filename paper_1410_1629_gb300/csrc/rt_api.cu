@@ -694,7 +694,7 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
     n_cells = d->n_leaves;
     n_nodes = d->n_nodes;
   } else if (d->kind == RT_GRID_VORONOI) {
-    if (!d->child || !d->sites || !d->offsets || d->n_leaves <= 0 || d->n_nodes < 0)
+    if ((!d->child && d->n_nodes > 0) || !d->sites || !d->offsets || d->n_leaves <= 0 || d->n_nodes < 0)
       return fail(c, RT_ERR_ARG, "rt_create_grid: a Voronoi grid needs sites[], offsets[], child[] and n_leaves > 0");
     if (d->n_leaves > (1ll << 31) - 2 || d->n_nodes > (1ll << 31) - 1)
       return fail(c, RT_ERR_ARG, "rt_create_grid: Voronoi grid too large for int32 indices");
@@ -718,11 +718,11 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
       if (set_device(c) != RT_OK) return RT_ERR_CUDA;
       RT_CUDA(c, cudaMemcpy(site.data(), d->sites, site.size() * sizeof(double), cudaMemcpyDeviceToHost));
       RT_CUDA(c, cudaMemcpy(off.data(), d->offsets, off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
-      RT_CUDA(c, cudaMemcpy(nbr.data(), d->child, nbr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+      if (n_nodes > 0) RT_CUDA(c, cudaMemcpy(nbr.data(), d->child, nbr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
     } else {
       std::memcpy(site.data(), d->sites, site.size() * sizeof(double));
       std::memcpy(off.data(), d->offsets, off.size() * sizeof(int64_t));
-      std::memcpy(nbr.data(), d->child, nbr.size() * sizeof(int32_t));
+      if (n_nodes > 0) std::memcpy(nbr.data(), d->child, nbr.size() * sizeof(int32_t));
     }
     if (off[0] != 0 || off[(size_t)n_cells] != n_nodes)
       return fail(c, RT_ERR_ARG, "rt_create_grid: Voronoi offsets must run from 0 to n_nodes");

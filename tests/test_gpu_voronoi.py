@@ -97,3 +97,29 @@ def test_voronoi_grid_arguments_are_checked():
         rt.rt_create_grid(ctx, d)
     finally:
         rt.rt_context_destroy(ctx)
+
+
+@pytest.mark.parametrize("n_sites", [1, 2])
+def test_voronoi_degenerate_grids(n_sites):
+    """One site (the whole domain is one cell, no faces: the walk meets only
+    the domain boundary) and two sites (one bisecting plane), against the
+    oracle; the one-site grid also against the one-cell cartesian grid."""
+    cart = W.uniform_cube(n_cells=1, n_pix=16, axis_tau=2.0, channels=3, source_pos=(0.2, -0.1, 0.05))
+    if n_sites == 1:
+        grid = W.Grid("voronoi", np.array([-1.0, 1.0] * 3), np.ones(1, np.float32), child=np.zeros(0, np.int32),
+                      sites=np.array([[0.1, 0.2, -0.3]]), offsets=np.array([0, 0], np.int64))
+    else:
+        grid = W.Grid("voronoi", np.array([-1.0, 1.0] * 3), np.array([1.0, 3.0], np.float32),
+                      child=np.array([1, 0], np.int32), sites=np.array([[-0.4, 0.1, 0.0], [0.5, -0.2, 0.3]]),
+                      offsets=np.array([0, 1, 2], np.int64))
+    prob = W.replace(cart, grid=grid)
+    n = 20000
+    g = PAR.gpu_run(prob, n, records_cap=2_000_000)
+    o = PAR.oracle_run(prob, n, records_cap=2_000_000)
+    assert g["raw_stats"]["device_flags"] == 0
+    _assert_ok(PAR.compare(g, o, prob))
+    if n_sites == 1:
+        c = PAR.gpu_run(cart, n)
+        for a, b in zip(g["images"], c["images"]):
+            np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-9 * b.max())
+        np.testing.assert_allclose(g["stats"], c["stats"], rtol=1e-6)
