@@ -159,6 +159,32 @@ def _raw_run(ctx, prob, n):
     return imgs, ab, rt.rt_read_stats(ctx).as_dict()
 
 
+def test_degenerate_sizes():
+    """Edge cases of the launch: no packets (tallies stay zero), a grid of
+    one cell, a packet count that fills no warp or block evenly, a frame of
+    one pixel and a ragged 5 x 3 frame, against the oracle."""
+    prob = W.uniform_cube(n_cells=1, channels=3)
+    prob.instruments = [W.Instrument(0.0, 0.0, 0.0, 1, 1, 1.0, 1.0, channels=3),
+                        W.Instrument(math.radians(30.0), 0.2, 0.1, 5, 3, 1.2, 0.9, channels=3)]
+    sim = rt.Simulation(prob)
+    try:
+        sim.launch(0, 0, 0)
+        st = sim.stats()
+        assert st["emitted"] == 0.0 and st["escaped"] == 0.0 and st["absorbed"] == 0.0 and st["packets"] == 0
+        assert all(float(t.abs().sum()) == 0.0 for t in sim.images())
+        assert float(sim.absorption().abs().sum()) == 0.0
+    finally:
+        sim.close()
+    n = 4999
+    g = PAR.gpu_run(prob, n, records_cap=40 * n)
+    o = PAR.oracle_run(prob, n, records_cap=40 * n)
+    rep = PAR.compare(g, o, prob)
+    _assert_ok(rep)
+    assert int(g["counters"][3]) == n
+    # the one-pixel frame catches every peel-off: its bin holds them all
+    assert rep["pixels"][0]["corrected"]["bins"] >= 1
+
+
 def test_problem_rebuilt_on_one_context():
     """Set-up calls release the problem's device buffers to a pool of the
     context and later set-ups of the same sizes reuse them: a problem rebuilt
