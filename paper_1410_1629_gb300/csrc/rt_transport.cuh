@@ -546,10 +546,12 @@ struct OctGrid {
     // axes, the old path and the new one part at the level where the face
     // plane splits an ancestor: with i the leaf's integer coordinate along
     // `axis` at its depth D, level D - 1 - (trailing ones of i) going up,
-    // D - 1 - (trailing zeros of i) going down.  The ancestor's box there is
+    // D - 1 - (trailing zeros of i) going down.  With exact boxes the new path is
+    // then followed from there by its bits; otherwise the ancestor's box is
     // rebuilt by halving along the old path (the same arithmetic as the
-    // descent).  Otherwise (a coordinate on a face of the leaf: the tie rule
-    // may part the paths earlier) the path is replayed from the root.
+    // descent) and the exit point descends from it.  When a coordinate lies
+    // on a face of the leaf (the tie rule may part the paths earlier) the
+    // path is replayed from the root.
     const bool in_x = axis == 0 || (p.x > w.lo[0] && p.x < w.hi[0]);
     const bool in_y = axis == 1 || (p.y > w.lo[1] && p.y < w.hi[1]);
     const bool in_z = axis == 2 || (p.z > w.lo[2] && p.z < w.hi[2]);
@@ -568,19 +570,52 @@ struct OctGrid {
       const int tb = da > 0.0f ? __clz(~top) : __clz(top);
       const int part = old_depth - 1 - tb;
       if (P.oct_exact) {
-        // exact boxes: up from the leaf, each level doubling the box on the
-        // side away from the child's octant (tb + 1 levels instead of part)
+        // exact boxes: below the parting level the new path is the old one
+        // with the bit of `axis` flipped (in the other axes the exit point
+        // lies strictly inside the leaf, so it keeps the old octants), and it
+        // is followed without position tests down to the old depth or to a
+        // leaf above it.  The box: the old leaf's, moved across the face, then
+        // doubled on the side away from each octant up to the level reached.
+        const int flip = 1 << axis;
+        int node = sc.stack[part];
+        int c = child(P, node);
+        unsigned long long path = part > 0 ? (old_path & ((1ull << (3 * part)) - 1ull)) : 0ull;
+        depth = part;
+        while (c >= 0 && depth < old_depth) {
+          const int oct = (int)((old_path >> (3 * depth)) & 7ull) ^ flip;
+          path |= (unsigned long long)oct << (3 * depth);
+          node = c + oct;
+          depth += 1;
+          sc.stack[depth] = node;
+          c = child(P, node);
+        }
 #pragma unroll
-        for (int a = 0; a < 3; ++a) { lo[a] = w.lo[a]; hi[a] = w.hi[a]; }
-        for (int l = old_depth - 1; l >= part; --l) {
-          const int oct = (int)((old_path >> (3 * l)) & 7ull);
+        for (int a = 0; a < 3; ++a) {
+          lo[a] = w.lo[a];
+          hi[a] = w.hi[a];
+          if (a == axis) {
+            const float size = hi[a] - lo[a];
+            if (da > 0.0f) { lo[a] = hi[a]; hi[a] += size; } else { hi[a] = lo[a]; lo[a] -= size; }
+          }
+        }
+        for (int l = old_depth - 1; l >= depth; --l) {
+          const int oct = (int)((old_path >> (3 * l)) & 7ull) ^ flip;
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             const float size = hi[a] - lo[a];
             if ((oct >> a) & 1) lo[a] -= size; else hi[a] += size;
           }
         }
-        depth = part;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { w.lo[a] = lo[a]; w.hi[a] = hi[a]; }
+        w.depth = depth;
+        w.path = path;
+        if (c < 0) {
+          w.leaf = -c - 1;
+          return true;
+        }
+        // a finer neighbour: on by the exit point below the old depth
+        return descend(P, p, d, w, sc);
       } else {
         for (; depth < part; ++depth) {
           const int oct = (int)((old_path >> (3 * depth)) & 7ull);
