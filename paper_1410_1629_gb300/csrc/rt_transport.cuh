@@ -885,12 +885,21 @@ struct VorGrid {
     float best = w.t_box;
     int face = -1;
     const int f1 = __ldg(&P.face_off[w.leaf + 1]);
-    for (int f = __ldg(&P.face_off[w.leaf]); f < f1; ++f) {
-      const float4 n = __ldg(&P.face[f]);
-      const float den = fmaf(d.x, n.x, fmaf(d.y, n.y, d.z * n.z));
-      if (den > 0.0f) {
-        const float tf = (n.w - fmaf(rx, n.x, fmaf(ry, n.y, rz * n.z))) / den;
-        if (tf < best) { best = tf; face = f; }
+    // three face planes loaded at once (a plane past the last face reads as
+    // zero: d.n = 0, never an exit), tested in face order: three L2 loads in
+    // flight per lane instead of one (190 -> 142 ms on the 1e5-site disk; four
+    // spill at 64 registers)
+    for (int f = __ldg(&P.face_off[w.leaf]); f < f1; f += 3) {
+      float4 n[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) n[k] = f + k < f1 ? __ldg(&P.face[f + k]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float den = fmaf(d.x, n[k].x, fmaf(d.y, n[k].y, d.z * n[k].z));
+        if (den > 0.0f) {
+          const float tf = (n[k].w - fmaf(rx, n[k].x, fmaf(ry, n[k].y, rz * n[k].z))) / den;
+          if (tf < best) { best = tf; face = f + k; }
+        }
       }
     }
     w.te = best;
