@@ -318,9 +318,10 @@ rt_status rt_launch_packets(rt_ctx ctx, uint64_t n_per_lambda, uint64_t first_pa
 /* Choose the per-event deferral threshold (opts->control_lanes) and the
  * resident blocks per SM (opts->blocks_per_sm) for this context's problem:
  * times a launch of n_per_lambda packets per wavelength for each of 8, 12,
- * 16, 20, 24, 28 lanes at the most resident blocks, then for the best
- * threshold with one and two blocks per SM fewer (kept only if at least 3 %
- * faster; other options from opts or the defaults), and keeps the fastest
+ * 16, 20, 24, 28 lanes at the most resident blocks, then, when the sample
+ * holds at least 8 packets per resident thread at the most blocks, for the
+ * best threshold with one and two blocks per SM fewer (kept only if at least
+ * 3 % faster; other options from opts or the defaults), and keeps the fastest
  * pair for later launches with 0 in
  * those fields; the threshold is written to *control_lanes if not NULL.
  * Both only reorder work: results are the same to FP64 summation order.  The

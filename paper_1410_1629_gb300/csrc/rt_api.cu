@@ -1528,12 +1528,21 @@ rt_status rt_tune(rt_ctx c, uint64_t n_per_lambda, uint64_t seed, const rt_launc
     }
   }
   // then the resident blocks per SM at that threshold: the most that fit
-  // (0), one and two fewer
+  // (0), one and two fewer.  Only on a sample of at least kTuneBlockPackets
+  // packets per resident thread: on fewer, the launch time is the slowest
+  // packet's and fewer resident threads (less contention) win on the sample
+  // while they lose on the full run.
   int best_blocks = 0;
   o.control_lanes = best_lanes;
   // the kernels' launch bounds
   const int max_blocks = (c->grid_kind == RT_GRID_OCTREE || c->grid_kind == RT_GRID_BINTREE) ? 3 : 4;
-  for (int blocks = max_blocks - 1; st == RT_OK && blocks >= max_blocks - 2 && blocks >= 1; --blocks) {
+  constexpr unsigned long long kTuneBlockPackets = 8;
+  constexpr unsigned long long kTransportThreads = 256;  // threads per block of the transport kernels
+  const unsigned long long resident =
+      (unsigned long long)c->num_sms * (unsigned long long)max_blocks * kTransportThreads;
+  const bool search_blocks = n_per_lambda * (unsigned long long)c->n_lambda >= kTuneBlockPackets * resident;
+  for (int blocks = max_blocks - 1; search_blocks && st == RT_OK && blocks >= max_blocks - 2 && blocks >= 1;
+       --blocks) {
     o.blocks_per_sm = blocks;
     cudaError_t e = cudaEventRecord(e0, s);
     if (e == cudaSuccess) st = rt_launch_packets(c, n_per_lambda, 0, seed, &o, stream);

@@ -866,10 +866,20 @@ struct VorGrid {
       float best = dist2(p, __ldg(&P.site[c]));
       int move = -1;
       const int f1 = __ldg(&P.face_off[c + 1]);
-      for (int f = __ldg(&P.face_off[c]); f < f1; ++f) {
-        const int j = __ldg(&P.child[f]);
-        const float dj = dist2(p, __ldg(&P.site[j]));
-        if (dj < best) { best = dj; move = j; }
+      // three neighbours at once, as in the face loop of the walk (past the
+      // last face the cell itself, never nearer than itself)
+      for (int f = __ldg(&P.face_off[c]); f < f1; f += 3) {
+        int j[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) j[k] = f + k < f1 ? __ldg(&P.child[f + k]) : c;
+        float4 sj[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sj[k] = __ldg(&P.site[j[k]]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float dj = dist2(p, sj[k]);
+          if (dj < best) { best = dj; move = j[k]; }
+        }
       }
       if (move < 0) return c;
       c = move;

@@ -367,8 +367,9 @@ def test_sorted_peel_pass_records_match_inline():
 def test_tuner_keeps_results():
     """rt_tune picks a deferral threshold and resident blocks on a sample and
     zeroes the tallies (rt_tuned reports both; before tuning 16 lanes and as
-    many blocks as fit); a launch afterwards equals an untuned launch to FP64
-    summation order."""
+    many blocks as fit; a sample of fewer than 8 packets per resident thread
+    keeps as many blocks as fit); a launch afterwards equals an untuned
+    launch to FP64 summation order."""
     prob = W.disk_galaxy(n_cells=32, n_lambda=2, n_pix=32)
     ref = PAR.gpu_run(prob, 5000)
     sim = rt.Simulation(prob)
@@ -376,7 +377,7 @@ def test_tuner_keeps_results():
         assert sim.tuned() == (16, 0)
         lanes = sim.tune(2000, seed=3)
         assert lanes in (8, 12, 16, 20, 24, 28)
-        assert sim.tuned()[0] == lanes and sim.tuned()[1] in (0, 2, 3)
+        assert sim.tuned() == (lanes, 0)
         assert sim.stats()["packets"] == 0
         got = PAR.gpu_run(prob, 5000, sim=sim)
     finally:
