@@ -1666,6 +1666,17 @@ rt_status rt_read_absorption(rt_ctx c, double* dst, size_t n_elems, int32_t on_d
     RT_CUDA(c, launch_from_storage(c->d_absorption, dst, c->n_lambda, c->nx, c->ny, c->nz, c->stride, s));
     return RT_OK;
   }
+  // page-locked host memory that the device addresses: the kernel writes the
+  // row-major field into it directly (no staging buffer, no second pass)
+  cudaPointerAttributes at{};
+  const cudaError_t pe = cudaPointerGetAttributes(&at, dst);
+  if (pe != cudaSuccess) cudaGetLastError();
+  if (pe == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+    RT_CUDA(c, launch_from_storage(c->d_absorption, static_cast<double*>(at.devicePointer), c->n_lambda, c->nx, c->ny,
+                                   c->nz, c->stride, s));
+    RT_CUDA(c, cudaStreamSynchronize(s));
+    return RT_OK;
+  }
   if (!c->d_abs_tmp) RT_CUDA(c, pool_alloc(c, &c->d_abs_tmp, (size_t)c->n_cells * sizeof(double)));
   for (int l = 0; l < c->n_lambda; ++l) {
     RT_CUDA(c, launch_from_storage(c->d_absorption + (size_t)l * c->n_cells, c->d_abs_tmp, 1, c->nx, c->ny, c->nz,

@@ -517,3 +517,30 @@ def test_storage_order_only_changes_speed():
     rb = np.sort(b["records"], order=["pid", "lam", "event", "instr"])
     assert np.array_equal(ra, rb)
     assert np.array_equal(a["trace"], b["trace"]) and len(a["trace"]) > 1
+
+
+def test_absorption_read_paths_agree():
+    """rt_read_absorption un-permutes the storage order into a device buffer,
+    into page-locked host memory directly (the device writes it), or
+    through a device staging buffer into pageable host memory: the same
+    bytes every way, with a wavelength count that leaves the grid of the
+    conversion kernel ragged."""
+    prob = W.disk_galaxy(n_cells=41, n_lambda=3, n_pix=32)
+    sim = rt.Simulation(prob)
+    try:
+        sim.launch(3000, 0, 0)
+        n = prob.n_lambda * prob.grid.n_cells
+        dev = torch.empty(n, dtype=torch.float64, device="cuda")
+        rt.rt_read_absorption(sim.ctx, dev.data_ptr(), n, 1, None)
+        torch.cuda.synchronize()
+        pinned = torch.full((n,), -1.0, dtype=torch.float64).pin_memory()
+        rt.rt_read_absorption(sim.ctx, pinned.data_ptr(), n, 0, None)
+        page = np.full(n, -1.0)
+        rt.rt_read_absorption(sim.ctx, page.ctypes.data, n, 0, None)
+        ref = dev.cpu().numpy()
+        assert np.count_nonzero(ref) > n // 2
+        assert np.array_equal(pinned.numpy(), ref) and np.array_equal(page, ref)
+        with pytest.raises(rt.RTError):
+            rt.rt_read_absorption(sim.ctx, pinned.data_ptr(), n - 1, 0, None)
+    finally:
+        sim.close()
