@@ -19,6 +19,11 @@
 
 #include "rt_internal.h"
 
+namespace rtk {
+// rt_layout.cu: n doubles from device memory to memory the device addresses.
+cudaError_t launch_copy_f64(const double* src, double* dst, long long n, cudaStream_t stream);
+}  // namespace rtk
+
 using namespace rtk;
 
 namespace {
@@ -1639,14 +1644,33 @@ rt_status rt_reset_tallies(rt_ctx c, void* stream) {
   return zero_tallies(c, (cudaStream_t)stream);
 }
 
+// The device address of page-locked host memory the device can write, or
+// null (pageable or unknown memory).
+static double* device_view(double* host) {
+  cudaPointerAttributes at{};
+  const cudaError_t e = cudaPointerGetAttributes(&at, host);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? static_cast<double*>(at.devicePointer) : nullptr;
+}
+
+// Host destinations: page-locked memory the device addresses is written by
+// a copy kernel (the copy engine's first copy after a long launch was
+// measured up to 15 times slower than the next), other memory by a copy.
 static rt_status copy_out(rt_ctx c, double* dst, const double* src, size_t n, int32_t on_device, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (on_device) {
     RT_CUDA(c, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return RT_OK;
+  }
+  if (double* view = device_view(dst)) {
+    RT_CUDA(c, launch_copy_f64(src, view, (long long)n, s));
   } else {
     RT_CUDA(c, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(c, cudaStreamSynchronize(s));
   }
+  RT_CUDA(c, cudaStreamSynchronize(s));
   return RT_OK;
 }
 
@@ -1668,12 +1692,8 @@ rt_status rt_read_absorption(rt_ctx c, double* dst, size_t n_elems, int32_t on_d
   }
   // page-locked host memory that the device addresses: the kernel writes the
   // row-major field into it directly (no staging buffer, no second pass)
-  cudaPointerAttributes at{};
-  const cudaError_t pe = cudaPointerGetAttributes(&at, dst);
-  if (pe != cudaSuccess) cudaGetLastError();
-  if (pe == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
-    RT_CUDA(c, launch_from_storage(c->d_absorption, static_cast<double*>(at.devicePointer), c->n_lambda, c->nx, c->ny,
-                                   c->nz, c->stride, s));
+  if (double* view = device_view(dst)) {
+    RT_CUDA(c, launch_from_storage(c->d_absorption, view, c->n_lambda, c->nx, c->ny, c->nz, c->stride, s));
     RT_CUDA(c, cudaStreamSynchronize(s));
     return RT_OK;
   }

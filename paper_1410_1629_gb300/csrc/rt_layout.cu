@@ -44,6 +44,13 @@ __global__ void k_from_storage(const double* __restrict__ src, double* __restric
     d[r] = s[storage_index(r, nx, ny, s0, s1, s2)];
 }
 
+// A plain copy of n doubles (coalesced loads and stores): the device writing
+// page-locked host memory that it addresses.
+__global__ void k_copy_f64(const double* __restrict__ src, double* __restrict__ dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
 unsigned blocks_for(long long n) {
   const long long b = (n + 255) / 256;
   return (unsigned)std::min<long long>(b, 4096);
@@ -63,6 +70,12 @@ cudaError_t launch_from_storage(const double* src, double* dst, int n_lambda, in
   const long long n = (long long)nx * ny * nz;
   dim3 grid(blocks_for(n), (unsigned)n_lambda);
   k_from_storage<<<grid, 256, 0, stream>>>(src, dst, nx, ny, n, strides[0], strides[1], strides[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_f64(const double* src, double* dst, long long n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  k_copy_f64<<<blocks_for(n), 256, 0, stream>>>(src, dst, n);
   return cudaGetLastError();
 }
 

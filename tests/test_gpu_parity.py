@@ -522,9 +522,9 @@ def test_storage_order_only_changes_speed():
 def test_absorption_read_paths_agree():
     """rt_read_absorption un-permutes the storage order into a device buffer,
     into page-locked host memory directly (the device writes it), or
-    through a device staging buffer into pageable host memory: the same
-    bytes every way, with a wavelength count that leaves the grid of the
-    conversion kernel ragged."""
+    through a device staging buffer into pageable host memory, on a grid
+    whose cell count leaves the conversion kernel's last block ragged; the
+    same bytes every way, and the same for rt_read_images."""
     prob = W.disk_galaxy(n_cells=41, n_lambda=3, n_pix=32)
     sim = rt.Simulation(prob)
     try:
@@ -542,5 +542,19 @@ def test_absorption_read_paths_agree():
         assert np.array_equal(pinned.numpy(), ref) and np.array_equal(page, ref)
         with pytest.raises(rt.RTError):
             rt.rt_read_absorption(sim.ctx, pinned.data_ptr(), n - 1, 0, None)
+        # images: a copy into device memory, a copy kernel into page-locked
+        # memory, the copy engine into pageable memory
+        for q in range(len(prob.instruments)):
+            m = int(np.prod(sim.image_shape(q)))
+            dev = torch.empty(m, dtype=torch.float64, device="cuda")
+            rt.rt_read_images(sim.ctx, q, dev.data_ptr(), m, 1, None)
+            torch.cuda.synchronize()
+            pinned = torch.full((m,), -1.0, dtype=torch.float64).pin_memory()
+            rt.rt_read_images(sim.ctx, q, pinned.data_ptr(), m, 0, None)
+            page = np.full(m, -1.0)
+            rt.rt_read_images(sim.ctx, q, page.ctypes.data, m, 0, None)
+            ref = dev.cpu().numpy()
+            assert np.count_nonzero(ref) > 0
+            assert np.array_equal(pinned.numpy(), ref) and np.array_equal(page, ref)
     finally:
         sim.close()
