@@ -349,7 +349,8 @@ rt_status rt_reset_tallies(rt_ctx ctx, void* stream);
 /* Copy the absorbed luminosity, float64 [n_lambda][n_cells], into dst.
  * n_elems must equal n_lambda * n_cells.  dst_on_device = 1: device pointer,
  * asynchronous on stream; 0: host pointer, returns when the copy is done
- * (page-locked host memory that the device addresses is written by the
+ * (on a device that reaches all host memory, cudaDevAttrPageableMemoryAccess,
+ * a destination that starts and ends in page-locked memory is written by the
  * device directly; other host memory through a device staging buffer).
  * Errors: RT_ERR_ARG (size mismatch), RT_ERR_STATE, RT_ERR_CUDA. */
 rt_status rt_read_absorption(rt_ctx ctx, double* dst, size_t n_elems, int32_t dst_on_device, void* stream);

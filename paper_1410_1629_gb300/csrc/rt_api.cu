@@ -75,6 +75,7 @@ struct Batch {
 struct rt_ctx_s {
   int device = 0;
   int num_sms = 0;
+  int pageable_access = 0;  // the device reaches pageable host memory (cudaDevAttrPageableMemoryAccess)
   std::string err;
   // grid
   bool has_grid = false;
@@ -579,6 +580,7 @@ rt_status rt_context_create(int32_t device, rt_ctx* out) {
   c->device = device;
   e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->pageable_access, cudaDevAttrPageableMemoryAccess, device);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, 4 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 9 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_work, 2 * sizeof(unsigned long long));
@@ -1644,9 +1646,9 @@ rt_status rt_reset_tallies(rt_ctx c, void* stream) {
   return zero_tallies(c, (cudaStream_t)stream);
 }
 
-// The device address of page-locked host memory the device can write, or
-// null (pageable or unknown memory).
-static double* device_view(double* host) {
+// The device address of page-locked host memory that the device can write,
+// or null (pageable or unknown memory).
+static double* pinned_view(const double* host) {
   cudaPointerAttributes at{};
   const cudaError_t e = cudaPointerGetAttributes(&at, host);
   if (e != cudaSuccess) {
@@ -1656,16 +1658,27 @@ static double* device_view(double* host) {
   return at.type == cudaMemoryTypeHost ? static_cast<double*>(at.devicePointer) : nullptr;
 }
 
-// Host destinations: page-locked memory the device addresses is written by
-// a copy kernel (the copy engine's first copy after a long launch was
-// measured up to 15 times slower than the next), other memory by a copy.
+// Where a kernel may write n doubles of host memory at `host` directly: on a
+// device that reaches all host memory (every address of the range is then
+// legal for it), when the range starts and ends in page-locked memory (the
+// writes then run at the link's speed); else null.
+static double* device_view(rt_ctx c, double* host, size_t n) {
+  if (!c->pageable_access || n == 0) return nullptr;
+  double* first = pinned_view(host);
+  if (!first || first != host || pinned_view(host + (n - 1)) != host + (n - 1)) return nullptr;
+  return first;
+}
+
+// Host destinations: a copy kernel writes them where device_view allows (the
+// copy engine's first copy after a long launch was measured up to 15 times
+// slower than the next), the copy engine elsewhere.
 static rt_status copy_out(rt_ctx c, double* dst, const double* src, size_t n, int32_t on_device, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (on_device) {
     RT_CUDA(c, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return RT_OK;
   }
-  if (double* view = device_view(dst)) {
+  if (double* view = device_view(c, dst, n)) {
     RT_CUDA(c, launch_copy_f64(src, view, (long long)n, s));
   } else {
     RT_CUDA(c, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1690,9 +1703,9 @@ rt_status rt_read_absorption(rt_ctx c, double* dst, size_t n_elems, int32_t on_d
     RT_CUDA(c, launch_from_storage(c->d_absorption, dst, c->n_lambda, c->nx, c->ny, c->nz, c->stride, s));
     return RT_OK;
   }
-  // page-locked host memory that the device addresses: the kernel writes the
-  // row-major field into it directly (no staging buffer, no second pass)
-  if (double* view = device_view(dst)) {
+  // host memory that device_view allows: the kernel writes the row-major
+  // field into it directly (no staging buffer, no second pass)
+  if (double* view = device_view(c, dst, n)) {
     RT_CUDA(c, launch_from_storage(c->d_absorption, view, c->n_lambda, c->nx, c->ny, c->nz, c->stride, s));
     RT_CUDA(c, cudaStreamSynchronize(s));
     return RT_OK;
