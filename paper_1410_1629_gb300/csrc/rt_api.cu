@@ -20,6 +20,9 @@
 #include "rt_internal.h"
 
 namespace rtk {
+// Zero entries after the Voronoi neighbour and face arrays (the walk reads
+// lists in batches of three).
+constexpr long long kVorPad = 2;
 // rt_layout.cu: n doubles from device memory to memory the device addresses.
 cudaError_t launch_copy_f64(const double* src, double* dst, long long n, cudaStream_t stream);
 }  // namespace rtk
@@ -908,13 +911,19 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
                           cudaMemcpyHostToDevice));
   }
   if (d->kind == RT_GRID_VORONOI) {
-    RT_CUDA(c, pool_alloc(c, &c->d_child, (size_t)std::max<long long>(n_nodes, 1) * sizeof(int32_t)));
+    // neighbour ids and face planes with kVorPad zero entries after the last
+    // list: the walk loads a cell's list three entries at a time (entries
+    // past its end are masked, and the padding keeps them inside the arrays)
+    const size_t n_alloc = (size_t)n_nodes + kVorPad;
+    RT_CUDA(c, pool_alloc(c, &c->d_child, n_alloc * sizeof(int32_t)));
+    RT_CUDA(c, cudaMemset(c->d_child, 0, n_alloc * sizeof(int32_t)));
     if (n_nodes > 0) RT_CUDA(c, cudaMemcpy(c->d_child, d->child, (size_t)n_nodes * sizeof(int32_t), kind));
     RT_CUDA(c, pool_alloc(c, &c->d_site, vor_site.size() * sizeof(float4)));
     RT_CUDA(c, cudaMemcpy(c->d_site, vor_site.data(), vor_site.size() * sizeof(float4), cudaMemcpyHostToDevice));
     RT_CUDA(c, pool_alloc(c, &c->d_face_off, vor_off.size() * sizeof(int)));
     RT_CUDA(c, cudaMemcpy(c->d_face_off, vor_off.data(), vor_off.size() * sizeof(int), cudaMemcpyHostToDevice));
-    RT_CUDA(c, pool_alloc(c, &c->d_face, (size_t)std::max<long long>(n_nodes, 1) * sizeof(float4)));
+    RT_CUDA(c, pool_alloc(c, &c->d_face, n_alloc * sizeof(float4)));
+    RT_CUDA(c, cudaMemset(c->d_face, 0, n_alloc * sizeof(float4)));
     if (n_nodes > 0)
       RT_CUDA(c, cudaMemcpy(c->d_face, vor_face.data(), vor_face.size() * sizeof(float4), cudaMemcpyHostToDevice));
     RT_CUDA(c, pool_alloc(c, &c->d_bucket_seed, vor_seed.size() * sizeof(int)));
@@ -960,7 +969,7 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
   }
   std::memcpy(c->bounds, d->bounds, sizeof c->bounds);
   c->n_cells = n_cells;
-  c->n_nodes = d->kind == RT_GRID_VORONOI ? std::max<long long>(n_nodes, 1) : n_nodes;  // as allocated
+  c->n_nodes = d->kind == RT_GRID_VORONOI ? n_nodes + kVorPad : n_nodes;  // as allocated
   c->has_grid = true;
   c->tables_dirty = true;
   c->tape_valid = false;
