@@ -241,7 +241,7 @@ typedef struct {
                            the dust emits nothing launches packets of zero weight that end at once */
   int32_t blocks_per_sm; /* resident blocks of 256 threads per SM of the persistent transport grid
                             (0 = the value rt_tune chose, else as many as fit: 4 cartesian,
-                            rectilinear and Voronoi, 3 octree and k-d tree); the grid is this
+                            rectilinear, k-d tree and Voronoi, 3 octree); the grid is this
                             times the SM count */
   int32_t reserved;
 } rt_launch_opts;

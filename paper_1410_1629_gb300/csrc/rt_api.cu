@@ -1551,7 +1551,7 @@ rt_status rt_tune(rt_ctx c, uint64_t n_per_lambda, uint64_t seed, const rt_launc
   int best_blocks = 0;
   o.control_lanes = best_lanes;
   // the kernels' launch bounds
-  const int max_blocks = (c->grid_kind == RT_GRID_OCTREE || c->grid_kind == RT_GRID_BINTREE) ? 3 : 4;
+  const int max_blocks = c->grid_kind == RT_GRID_OCTREE ? 3 : 4;
   constexpr unsigned long long kTuneBlockPackets = 8;
   constexpr unsigned long long kTransportThreads = 256;  // threads per block of the transport kernels
   const unsigned long long resident =

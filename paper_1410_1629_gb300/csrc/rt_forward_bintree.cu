@@ -3,8 +3,11 @@
 // the k-d tree cell walk.
 #include "rt_transport.cuh"
 
+// four resident blocks of 256 (64 registers; 8 B of spills) hide more of the
+// L2 latency of the node-word loads than three without spills: 350 -> 316 ms
+// on the clumpy 2e5-leaf tree
 #ifndef RT_BIN_MIN_BLOCKS
-#define RT_BIN_MIN_BLOCKS 3
+#define RT_BIN_MIN_BLOCKS 4
 #endif
 
 namespace rtk {
