@@ -96,7 +96,8 @@ enum { RT_EMITTER_SOURCES = 0, RT_EMITTER_DUST = 1 };
  *       the index of the first of n's eight contiguous children (octant
  *       o = bit0 x-upper | bit1 y-upper | bit2 z-upper), child[n] < 0 marks a
  *       leaf with leaf id -(child[n] + 1), each id in [0, n_leaves) exactly
- *       once; density float32 [n_leaves]; cell id = leaf id.  Depth at most 21.
+ *       once; density float32 [n_leaves]; cell id = leaf id.  Depth at most 21
+ *       (deeper trees are rejected with RT_ERR_ARG).
  *   kind RT_GRID_VORONOI: the Voronoi grid of Table 1(d) (Sect. 2.4): cell c
  *       is the part of the domain nearer to site c than to any other site.
  *       n_leaves sites, sites FP64 [n_leaves][3], inside `bounds`, no two
@@ -240,8 +241,8 @@ typedef struct {
                            uniform position in it, an isotropic direction; a wavelength at which
                            the dust emits nothing launches packets of zero weight that end at once */
   int32_t blocks_per_sm; /* resident blocks of 256 threads per SM of the persistent transport grid
-                            (0 = the value rt_tune chose, else as many as fit: 4 cartesian,
-                            rectilinear, k-d tree and Voronoi, 3 octree); the grid is this
+                            (0 = the value rt_tune chose, else as many as fit: 4, or 3 for
+                            octrees deeper than 10 levels); the grid is this
                             times the SM count */
   int32_t reserved;
 } rt_launch_opts;

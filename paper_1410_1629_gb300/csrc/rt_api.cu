@@ -98,6 +98,7 @@ struct rt_ctx_s {
   int* d_bucket_seed = nullptr;
   int vb_n[3] = {1, 1, 1};
   bool oct_exact = false;  // octree boxes exact binary fractions (FwdParams::oct_exact)
+  int oct_depth = 0;       // octrees: the deepest leaf's depth
   // k-d trees: leaf ropes [n_cells][6] and node boxes [n_nodes][2] (FwdParams)
   int32_t* d_rope = nullptr;
   float4* d_node_box = nullptr;
@@ -844,6 +845,8 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
     }
     if (leaves_found != n_cells)
       return fail(c, RT_ERR_ARG, "rt_create_grid: %lld leaves in the tree for n_leaves = %lld", leaves_found, n_cells);
+    if (!bin && oct_depth > kMaxOctreeDepth)
+      return fail(c, RT_ERR_ARG, "rt_create_grid: octree depth %d above %d", oct_depth, kMaxOctreeDepth);
     if (bin) {
       // node boxes with the device's FP32 halving, and the ropes: going down,
       // the lower child's rope across its upper face on the split axis is the
@@ -932,6 +935,7 @@ rt_status rt_create_grid(rt_ctx c, const rt_grid_desc* d, int32_t* grid_id) {
   }
   c->grid_kind = d->kind;
   c->oct_exact = d->kind == RT_GRID_OCTREE && oct_depth <= 21 && octree_boxes_exact(d->bounds, oct_depth);
+  c->oct_depth = d->kind == RT_GRID_OCTREE ? oct_depth : 0;
   c->nx = d->nx; c->ny = d->ny; c->nz = d->nz;
   c->stride[0] = 1; c->stride[1] = d->nx; c->stride[2] = d->nx * d->ny;
   c->permuted = false;
@@ -1213,6 +1217,7 @@ rt_status rt_launch_packets(rt_ctx c, uint64_t n_per_lambda, uint64_t first_pack
   p.child = c->d_child;
   p.n_nodes = c->n_nodes;
   p.oct_exact = c->oct_exact ? 1 : 0;
+  p.oct_levels = c->oct_depth + 1;
   p.rope = c->d_rope;
   p.node_box = c->d_node_box;
   if (c->grid_kind == RT_GRID_VORONOI) {
@@ -1551,7 +1556,7 @@ rt_status rt_tune(rt_ctx c, uint64_t n_per_lambda, uint64_t seed, const rt_launc
   int best_blocks = 0;
   o.control_lanes = best_lanes;
   // the kernels' launch bounds
-  const int max_blocks = c->grid_kind == RT_GRID_OCTREE ? 3 : 4;
+  const int max_blocks = 4;
   constexpr unsigned long long kTuneBlockPackets = 8;
   constexpr unsigned long long kTransportThreads = 256;  // threads per block of the transport kernels
   const unsigned long long resident =

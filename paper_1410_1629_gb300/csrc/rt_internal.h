@@ -87,6 +87,7 @@ struct FwdParams {
   // at any depth is representable and every halving exact): a box can be
   // rebuilt upwards from a leaf (size doubled) instead of down from the root
   int oct_exact;
+  int oct_levels;  // octrees: ancestor-stack entries per lane (the deepest leaf's depth + 1)
   const float* edge[3];  // rectilinear only: cell edges per axis, n + 1 each
   // Voronoi grids: sites (x, y, z, 0), the faces of cell c at
   // [face_off[c], face_off[c + 1]) as (unit normal towards the neighbour,

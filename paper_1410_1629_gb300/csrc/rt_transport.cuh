@@ -414,7 +414,9 @@ constexpr int kOctStack = kMaxOctreeDepth + 1;  // path stack: depths 0..21 (3 p
 constexpr int kChildCache = 1024;                // first child[] entries kept in shared memory
 
 __shared__ int S_CHILD[kChildCache];
-__shared__ int S_STACK[kBlock * kOctStack];
+// the octree kernel's per-lane ancestor stacks, P.oct_levels entries each
+// (dynamic shared memory sized by the tree's depth)
+extern __shared__ int S_OCT_STACK[];
 
 struct OctGrid {
   static constexpr bool kColumns = false;
@@ -466,7 +468,7 @@ struct OctGrid {
         w.leaf = -c - 1;
         return true;
       }
-      if (w.depth + 1 >= kOctStack) {
+      if (w.depth + 1 >= P.oct_levels) {
         atomicOr(P.flags, kFlagOctreeDepth);
         w.leaf = 0;
         return false;
@@ -1695,18 +1697,18 @@ __device__ __forceinline__ void walk_step(const FwdParams& P, Lane<G>& s, unsign
 }
 
 template <class G>
-__device__ __forceinline__ typename G::Scratch lane_scratch();
+__device__ __forceinline__ typename G::Scratch lane_scratch(const FwdParams& P);
 template <>
-__device__ __forceinline__ CartGrid::Scratch lane_scratch<CartGrid>() { return CartGrid::Scratch{}; }
+__device__ __forceinline__ CartGrid::Scratch lane_scratch<CartGrid>(const FwdParams&) { return CartGrid::Scratch{}; }
 template <>
-__device__ __forceinline__ RectGrid::Scratch lane_scratch<RectGrid>() { return RectGrid::Scratch{}; }
+__device__ __forceinline__ RectGrid::Scratch lane_scratch<RectGrid>(const FwdParams&) { return RectGrid::Scratch{}; }
 template <>
-__device__ __forceinline__ BinGrid::Scratch lane_scratch<BinGrid>() { return BinGrid::Scratch{}; }
+__device__ __forceinline__ BinGrid::Scratch lane_scratch<BinGrid>(const FwdParams&) { return BinGrid::Scratch{}; }
 template <>
-__device__ __forceinline__ VorGrid::Scratch lane_scratch<VorGrid>() { return VorGrid::Scratch{}; }
+__device__ __forceinline__ VorGrid::Scratch lane_scratch<VorGrid>(const FwdParams&) { return VorGrid::Scratch{}; }
 template <>
-__device__ __forceinline__ OctGrid::Scratch lane_scratch<OctGrid>() {
-  return OctGrid::Scratch{&S_STACK[threadIdx.x * kOctStack]};
+__device__ __forceinline__ OctGrid::Scratch lane_scratch<OctGrid>(const FwdParams& P) {
+  return OctGrid::Scratch{&S_OCT_STACK[threadIdx.x * P.oct_levels]};
 }
 
 template <class G>
@@ -1738,7 +1740,7 @@ __device__ __forceinline__ void forward_body(const FwdParams& P) {
   for (int i = threadIdx.x; i < P.n_lambda; i += kBlock) S_LAM[i] = P.lam[i];
   load_grid_cache<G>(P);
   __syncthreads();
-  typename G::Scratch sc = lane_scratch<G>();
+  typename G::Scratch sc = lane_scratch<G>(P);
   LaneTally* bt = &tally[threadIdx.x];
   bt->escaped = bt->absorbed = bt->truncated = 0.0;
   bt->crossings = bt->path_crossings = bt->column_crossings = 0ull;

@@ -157,3 +157,33 @@ def test_tree_leaf_ids_are_checked(kind):
         rt.rt_create_grid(ctx, d)
     finally:
         rt.rt_context_destroy(ctx)
+
+
+def _chain_octree(depth):
+    """An octree whose first child is split at every level down to `depth`."""
+    n_nodes = 1 + 8 * depth
+    child = np.empty(n_nodes, np.int32)
+    leaf = 0
+    for node in range(n_nodes):
+        level_first = node == 0 or (node - 1) % 8 == 0
+        if level_first and (node == 0 or (node - 1) // 8 + 1 < depth):
+            child[node] = 1 + 8 * (0 if node == 0 else (node - 1) // 8 + 1)
+        else:
+            child[node] = -(leaf + 1)
+            leaf += 1
+    return W.Grid(kind="octree", bounds=[-1.0, 1.0] * 3, density=np.ones(leaf, np.float32), child=child)
+
+
+def test_octree_depth_is_checked():
+    """Octrees deeper than 21 levels (the walk's 3 path bits per level in 64
+    bits) are rejected at grid creation; 21 levels are accepted."""
+    ctx = rt.rt_context_create(0)
+    try:
+        d, keep = rt.grid_desc(_chain_octree(22))
+        with pytest.raises(rt.RTError) as e:
+            rt.rt_create_grid(ctx, d)
+        assert e.value.status == rt.RT_ERR_ARG
+        d, keep = rt.grid_desc(_chain_octree(21))
+        rt.rt_create_grid(ctx, d)
+    finally:
+        rt.rt_context_destroy(ctx)
