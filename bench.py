@@ -38,11 +38,11 @@ BYTES_PATH_CROSSING, BYTES_PEEL_CROSSING, BYTES_DEPOSIT = 20, 4, 16
 BYTES_COLUMN_PEEL = 8
 # DRAM bytes (read + write) per packet of the transport kernel, from an ncu
 # capture of one 2e6-packet launch of this workload (dram__bytes_read.sum
-# 32.541 GB + dram__bytes_write.sum 13.389 GB), valid only for the kernel
+# 32.522 GB + dram__bytes_write.sum 13.386 GB), valid only for the kernel
 # code whose hash is given (kernel_sources_hash: the sources without their
 # comments); the per-launch traffic is this figure times the packets.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "f325fbe64e211d0c", "kernel": "k_forward_cartesian",
-                   "bytes_per_packet": (32541056768 + 13389014528) / 2e6}
+TRAFFIC_CAPTURE = {"sources_sha256_16": "67f73aa7b8b72c0a", "kernel": "k_forward_cartesian",
+                   "bytes_per_packet": (32522363904 + 13386474752) / 2e6}
 KERNEL_SOURCES = ["paper_1410_1629_gb300/csrc/rt_forward.cu", "paper_1410_1629_gb300/csrc/rt_device.cuh",
                   "paper_1410_1629_gb300/csrc/rt_internal.h", "paper_1410_1629_gb300/csrc/rt_transport.cuh",
                   "paper_1410_1629_gb300/build.py"]
