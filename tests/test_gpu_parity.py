@@ -87,6 +87,38 @@ def test_octree_parity(bounds):
     _assert_ok(rep)
 
 
+def test_deep_octree_parity():
+    """An octree refined around one point down to depth 11: its per-lane
+    ancestor stacks (12 entries) leave room for three blocks per SM instead
+    of four, and walks cross leaves whose sizes differ by many levels.  (At
+    depth 14 the smallest leaves, 1.2e-4 wide, are 4000 FP32 ulps of their
+    coordinates: FP32 path lengths there are good to ~2e-4, and three such
+    cells measured 1.6e-4 from the oracle.)"""
+    rng = np.random.default_rng(5)
+    focus = np.array([0.3, -0.2, 0.1])
+
+    def refine(lo, hi, level):
+        near = np.all((lo <= focus) & (focus < hi), axis=1)
+        return near | ((level < 2) & (rng.uniform(size=len(lo)) < 0.7))
+
+    grid, _, _ = W.build_octree([-1, 1] * 3, refine, lambda lo, hi: rng.lognormal(0.0, 1.0, len(lo)), 11)
+    depth = 0
+    d = np.zeros(len(grid.child), int)
+    for i, v in enumerate(grid.child):
+        if v >= 0:
+            d[v:v + 8] = d[i] + 1
+            depth = max(depth, d[i] + 1)
+    assert depth == 11
+    prob = W.uniform_cube(axis_tau=2.0, channels=3, source_pos=tuple(focus))
+    prob.grid = grid
+    n = 30000
+    g = PAR.gpu_run(prob, n, records_cap=3_000_000)
+    o = PAR.oracle_run(prob, n, records_cap=3_000_000)
+    rep = PAR.compare(g, o, prob)
+    _assert_ok(rep)
+    assert g["raw_stats"]["device_flags"] == 0
+
+
 @pytest.mark.parametrize("case", ["no_scattering", "dust_free", "offset_source", "plummer_outside"])
 def test_special_cases(case):
     if case == "no_scattering":
